@@ -1,0 +1,409 @@
+"""CPU oracle for the ELM-FBPINN RRQR-filtered, right-preconditioned solver.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may import this package; the CUDA library never
+does.  The numerics live in ``rfm_oracle.c`` (plain FP64 loops written from the
+paper); this module only marshals numpy arrays through ctypes and strings the
+steps of Algorithm 2 together.
+
+Parity status of each function (what pins it) is listed in the design doc; every
+function here is pinned by a ``-m "not gpu"`` test in tests/test_oracle_*.py.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+from typing import List, Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rfm_oracle.c")
+_SO = os.path.join(_HERE, "_build", "librfm_oracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, no host-specific flags)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(_SO), exist_ok=True)
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-ffp-contract=off",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class Problem(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("pde", C.c_int32), ("family", C.c_int32), ("n_modes", C.c_int32),
+                ("S", C.c_int32 * 3), ("n", C.c_int32 * 3), ("K", C.c_int32), ("pad0", C.c_int32),
+                ("delta", C.c_double), ("kappa", C.c_double), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("lam", C.c_double * 2), ("fam", C.c_double * 64)]
+
+
+class System(C.Structure):
+    _fields_ = [("J", C.c_int64), ("N", C.c_int64), ("m", C.c_void_p), ("roff", C.c_void_p),
+                ("grow", C.c_void_p), ("coff", C.c_void_p), ("aoff", C.c_void_p), ("Roff", C.c_void_p),
+                ("r", C.c_void_p), ("Ahat", C.c_void_p), ("R", C.c_void_p), ("mode", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        P = C.POINTER(Problem)
+        vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+        sig = {
+            "orc_num_interior": (i64, [P]), "orc_num_boundary": (i64, [P]), "orc_num_set": (i64, [P, C.c_int]),
+            "orc_num_subdomains": (i64, [P]), "orc_row_point": (None, [P, i64, vp, vp]),
+            "orc_subdomain": (None, [P, i64, vp, vp]), "orc_window_hat": (dbl, [P, i64, vp, vp, vp]),
+            "orc_window": (dbl, [P, i64, vp, vp, vp]), "orc_exact": (dbl, [P, vp]),
+            "orc_source": (dbl, [P, vp]), "orc_bdata": (dbl, [P, vp]),
+            "orc_block_rows": (i64, [P, i64, vp]), "orc_assemble_block": (None, [P, vp, i64, vp, i64, vp]),
+            "orc_rhs": (None, [P, vp]), "orc_assemble_dense": (None, [P, vp, vp]),
+            "orc_qrcp": (C.c_int, [C.c_int, C.c_int, vp, C.c_int, dbl, vp, vp, vp]),
+            "orc_form_q": (None, [C.c_int, C.c_int, vp, C.c_int, vp, vp]),
+            "orc_trsv_upper": (None, [C.c_int, vp, C.c_int, vp]),
+            "orc_trsv_upper_t": (None, [C.c_int, vp, C.c_int, vp]),
+            "orc_op_apply": (None, [C.POINTER(System), vp, vp]),
+            "orc_op_apply_t": (None, [C.POINTER(System), vp, vp]),
+            "orc_lsqr": (C.c_int, [C.POINTER(System), vp, vp, dbl, dbl, C.c_int, vp, vp, vp]),
+            "orc_coefficients": (None, [i64, C.c_int, vp, vp, vp, vp, vp, vp, vp]),
+            "orc_eval": (None, [P, vp, vp, i64, vp, vp]),
+            "orc_exact_many": (None, [P, i64, vp, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def problem_struct(p) -> Problem:
+    """ctypes struct from a synth.Problem."""
+    s = Problem()
+    s.dim, s.pde, s.family, s.n_modes = p.dim, p.pde, p.family, p.n_modes
+    for i in range(3):
+        s.S[i] = int(p.S[i]) if i < p.dim else 1
+        s.n[i] = int(p.n[i]) if i < p.dim else 1
+        s.lo[i] = float(p.lo[i])
+        s.hi[i] = float(p.hi[i])
+    s.K = p.K
+    s.delta, s.kappa = float(p.delta), float(p.kappa)
+    s.lam[0], s.lam[1] = float(p.lam[0]), float(p.lam[1])
+    fv = p.fam_vector()
+    for i in range(64):
+        s.fam[i] = fv[i]
+    return s
+
+
+# ---------------------------------------------------------------------------
+# geometry
+# ---------------------------------------------------------------------------
+
+def sizes(p):
+    s = problem_struct(p)
+    L = lib()
+    NI, NB = L.orc_num_interior(C.byref(s)), L.orc_num_boundary(C.byref(s))
+    return dict(N_I=NI, N_B=NB, N=NI + NB, J=L.orc_num_subdomains(C.byref(s)), K=p.K)
+
+
+def row_points(p, rows=None):
+    s = problem_struct(p)
+    L = lib()
+    if rows is None:
+        rows = np.arange(sizes(p)["N"])
+    X = np.zeros((len(rows), 3))
+    kinds = np.zeros(len(rows), dtype=np.int32)
+    x = np.zeros(3)
+    k = C.c_int()
+    for i, r in enumerate(rows):
+        L.orc_row_point(C.byref(s), int(r), _p(x), C.byref(k))
+        X[i] = x
+        kinds[i] = k.value
+    return X[:, : p.dim], kinds
+
+
+def subdomain(p, j):
+    s = problem_struct(p)
+    mu, sg = np.zeros(3), np.zeros(3)
+    lib().orc_subdomain(C.byref(s), int(j), _p(mu), _p(sg))
+    return mu[: p.dim], sg[: p.dim]
+
+
+def window(p, j, x, normalised=True):
+    """(w, grad w, pure second partials) of subdomain j at point x."""
+    s = problem_struct(p)
+    xx = np.zeros(3)
+    xx[: p.dim] = x
+    dw, d2w = np.zeros(3), np.zeros(3)
+    f = lib().orc_window if normalised else lib().orc_window_hat
+    w = f(C.byref(s), int(j), _p(xx), _p(dw), _p(d2w))
+    return w, dw[: p.dim].copy(), d2w[: p.dim].copy()
+
+
+def exact(p, X):
+    s = problem_struct(p)
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, p.dim)
+    u = np.zeros(len(X))
+    lib().orc_exact_many(C.byref(s), len(X), _p(X), _p(u))
+    return u
+
+
+def source(p, x):
+    s = problem_struct(p)
+    xx = np.zeros(3)
+    xx[: p.dim] = x
+    return lib().orc_source(C.byref(s), _p(xx))
+
+
+# ---------------------------------------------------------------------------
+# assembly
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Blocks:
+    grow: List[np.ndarray]      # global row indices of each block (ascending)
+    M: List[np.ndarray]         # blocks m_j x K (Fortran order)
+    h: np.ndarray               # right-hand side over all rows
+    N: int
+
+
+def block_rows(p, j) -> np.ndarray:
+    s = problem_struct(p)
+    L = lib()
+    m = L.orc_block_rows(C.byref(s), int(j), None)
+    g = np.zeros(m, dtype=np.int64)
+    L.orc_block_rows(C.byref(s), int(j), _p(g))
+    return g
+
+
+def assemble(p, params: np.ndarray, blocks=None) -> Blocks:
+    """Per-block assembly of M (Eq. (6)) and h (Eq. (5))."""
+    s = problem_struct(p)
+    L = lib()
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    J = L.orc_num_subdomains(C.byref(s))
+    idx = range(J) if blocks is None else blocks
+    grows, Ms = [], []
+    for j in idx:
+        g = block_rows(p, j)
+        Mj = np.zeros((len(g), p.K), order="F")
+        L.orc_assemble_block(C.byref(s), _p(params), int(j), _p(g), len(g), Mj.ctypes.data_as(C.c_void_p))
+        grows.append(g)
+        Ms.append(Mj)
+    N = sizes(p)["N"]
+    h = np.zeros(N)
+    L.orc_rhs(C.byref(s), _p(h))
+    return Blocks(grows, Ms, h, N)
+
+
+def assemble_dense(p, params):
+    s = problem_struct(p)
+    z = sizes(p)
+    M = np.zeros((z["N"], z["J"] * p.K), order="F")
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    lib().orc_assemble_dense(C.byref(s), _p(params), M.ctypes.data_as(C.c_void_p))
+    h = np.zeros(z["N"])
+    lib().orc_rhs(C.byref(s), _p(h))
+    return M, h
+
+
+# ---------------------------------------------------------------------------
+# filtering
+# ---------------------------------------------------------------------------
+
+@dataclass
+class QRCP:
+    rank: int
+    perm: np.ndarray      # original column index of each pivoted column
+    tau: np.ndarray
+    QR: np.ndarray        # R above the diagonal, reflectors below (Fortran order)
+    r11: float
+
+    @property
+    def R(self):
+        r = self.rank
+        return np.triu(self.QR[:r, :r])
+
+    def Q(self):
+        m = self.QR.shape[0]
+        Q = np.zeros((m, self.rank), order="F")
+        if self.rank:
+            lib().orc_form_q(m, self.rank, self.QR.ctypes.data_as(C.c_void_p), m, _p(self.tau),
+                             Q.ctypes.data_as(C.c_void_p))
+        return Q
+
+
+def qrcp(A: np.ndarray, tol: float) -> QRCP:
+    """sigma-RRQR of one block (Algorithm 1, threshold relative to |R_11|)."""
+    m, n = A.shape
+    W = np.array(A, dtype=np.float64, order="F", copy=True)
+    perm = np.zeros(n, dtype=np.int32)
+    tau = np.zeros(max(1, min(m, n)))
+    r11 = C.c_double()
+    r = lib().orc_qrcp(m, n, W.ctypes.data_as(C.c_void_p), m, float(tol), _p(perm), _p(tau), C.byref(r11))
+    return QRCP(r, perm, tau, W, r11.value)
+
+
+def trsv(R: np.ndarray, x: np.ndarray, trans=False) -> np.ndarray:
+    R = np.asfortranarray(R, dtype=np.float64)
+    z = np.array(x, dtype=np.float64, copy=True)
+    f = lib().orc_trsv_upper_t if trans else lib().orc_trsv_upper
+    f(R.shape[0], R.ctypes.data_as(C.c_void_p), R.shape[0], _p(z))
+    return z
+
+
+# ---------------------------------------------------------------------------
+# filtered system, LSQR (Algorithm 2)
+# ---------------------------------------------------------------------------
+
+class FilteredSystem:
+    """Filtered blocks and their factors, packed for the oracle's operator.
+
+    mode 0: Ahat S^-1 (Sec. 3.2); mode 1: the stored matrix as it is (either
+    Ahat without preconditioner, or explicit Q_hat by Proposition 3.1)."""
+
+    def __init__(self, N: int, grows, Ahats, Rs, mode=0, perms=None, K=None):
+        self.N, self.J = N, len(grows)
+        self.mode = mode
+        self.m = np.array([len(g) for g in grows], dtype=np.int64)
+        self.r = np.array([A.shape[1] for A in Ahats], dtype=np.int32)
+        self.roff = np.concatenate([[0], np.cumsum(self.m)[:-1]]).astype(np.int64)
+        self.coff = np.concatenate([[0], np.cumsum(self.r)[:-1]]).astype(np.int64)
+        self.grow = np.concatenate(grows).astype(np.int64) if grows else np.zeros(0, np.int64)
+        sizesA = self.m * self.r
+        self.aoff = np.concatenate([[0], np.cumsum(sizesA)[:-1]]).astype(np.int64)
+        self.Ahat = np.concatenate([np.asfortranarray(A).ravel(order="F") for A in Ahats] + [np.zeros(1)])
+        rr = self.r.astype(np.int64) ** 2
+        self.Roff = np.concatenate([[0], np.cumsum(rr)[:-1]]).astype(np.int64)
+        self.Rv = np.concatenate([np.asfortranarray(R).ravel(order="F") for R in Rs] + [np.zeros(1)]) \
+            if Rs is not None else np.zeros(1)
+        self.perms = perms
+        self.K = K
+        self.n = int(self.r.sum())
+        self._s = System(self.J, self.N, self.m.ctypes.data, self.roff.ctypes.data, self.grow.ctypes.data,
+                         self.coff.ctypes.data, self.aoff.ctypes.data, self.Roff.ctypes.data,
+                         self.r.ctypes.data, self.Ahat.ctypes.data, self.Rv.ctypes.data, mode)
+
+    def matvec(self, x):
+        out = np.zeros(self.N)
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        lib().orc_op_apply(C.byref(self._s), _p(x), _p(out))
+        return out
+
+    def rmatvec(self, y):
+        out = np.zeros(self.n + 1)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        lib().orc_op_apply_t(C.byref(self._s), _p(y), _p(out))
+        return out[: self.n]
+
+    def lsqr(self, h, y0=None, atol=1e-10, btol=1e-10, max_iter=10000, history=False):
+        y = np.zeros(self.n + 1)
+        st = np.zeros(6)
+        hist = np.zeros(max_iter + 1) if history else None
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        y0p = None
+        if y0 is not None:
+            y0a = np.zeros(self.n + 1)
+            y0a[: self.n] = y0
+            y0p = _p(y0a)
+        lib().orc_lsqr(C.byref(self._s), _p(h), y0p, float(atol), float(btol), int(max_iter), _p(y), _p(st),
+                       _p(hist) if history else None)
+        out = dict(y=y[: self.n], itn=int(st[0]), istop=int(st[1]), rnorm=st[2], arnorm=st[3],
+                   anorm=st[4], ynorm=st[5])
+        if history:
+            out["rhist"] = hist[: int(st[0]) + 1]
+        return out
+
+    def coefficients(self, y):
+        """a = S^-1 y scattered to the J*K layout with zeros at dropped columns."""
+        a = np.zeros(self.J * self.K)
+        perm = np.ascontiguousarray(np.concatenate(self.perms), dtype=np.int32)
+        yy = np.zeros(self.n + 1)
+        yy[: self.n] = y
+        lib().orc_coefficients(self.J, self.K, self.r.ctypes.data, _p(perm), self.coff.ctypes.data,
+                               self.Roff.ctypes.data, self.Rv.ctypes.data, _p(yy), _p(a))
+        return a
+
+
+def filter_blocks(B: Blocks, tol: float, store_q=False):
+    """Algorithm 1 over all blocks: returns per-block QRCP results."""
+    return [qrcp(M, tol) for M in B.M]
+
+
+def build_system(B: Blocks, F, mode=0, K=None) -> FilteredSystem:
+    """Algorithm 2's operator: mode 0 = Ahat S^-1 with R from the filter;
+    mode 1 = explicit Q_hat blocks (Proposition 3.1); mode 2 = Ahat alone."""
+    K = K if K is not None else B.M[0].shape[1]
+    perms = []
+    for f in F:
+        p = np.array(f.perm, dtype=np.int32)
+        perms.append(p)
+    if mode == 1:
+        mats = [f.Q() for f in F]
+        return FilteredSystem(B.N, B.grow, mats, None, mode=1, perms=perms, K=K)
+    Ahats = [np.asfortranarray(M[:, f.perm[: f.rank]]) for M, f in zip(B.M, F)]
+    if mode == 2:
+        return FilteredSystem(B.N, B.grow, Ahats, None, mode=1, perms=perms, K=K)
+    Rs = [f.R for f in F]
+    return FilteredSystem(B.N, B.grow, Ahats, Rs, mode=0, perms=perms, K=K)
+
+
+def coefficients_from(F, sysR: FilteredSystem, y):
+    return sysR.coefficients(y)
+
+
+# ---------------------------------------------------------------------------
+# evaluation
+# ---------------------------------------------------------------------------
+
+def test_grid(p, n_test=None):
+    nt = list(n_test if n_test is not None else p.n_test)
+    axes = [p.lo[i] + (np.arange(nt[i]) + 0.5) * (p.hi[i] - p.lo[i]) / nt[i] for i in range(p.dim)]
+    mesh = np.meshgrid(*axes, indexing="ij")
+    # dimension 0 fastest
+    return np.stack([m.transpose(list(range(p.dim))[::-1]).ravel() for m in mesh], axis=1)
+
+
+def evaluate(p, params, a, X):
+    s = problem_struct(p)
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, p.dim)
+    u = np.zeros(len(X))
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    lib().orc_eval(C.byref(s), _p(params), _p(a), len(X), _p(X), _p(u))
+    return u
+
+
+def errors(u_hat, u):
+    """relative L2 error and the normalised L1 error e_L1 of Sec. 4.2."""
+    d = u_hat - u
+    return dict(rel_l2=float(np.linalg.norm(d) / np.linalg.norm(u)),
+                e_l1=float(np.mean(np.abs(d)) / np.std(u)))
+
+
+def solve(p, params, tol=1e-10, atol=1e-10, btol=1e-10, max_iter=10000, mode=0, fp32_matrix=False,
+          y0=None, history=False):
+    """Algorithm 2 end to end: assemble, filter, LSQR on the preconditioned
+    system, a = S^-1 y with zeros at dropped columns.  fp32_matrix rounds the
+    assembled blocks (and h) to FP32 first, as the mixed-precision GPU path
+    does, then continues in FP64."""
+    B = assemble(p, params)
+    if fp32_matrix:
+        B = Blocks(B.grow, [np.asfortranarray(M.astype(np.float32).astype(np.float64)) for M in B.M],
+                   B.h.astype(np.float32).astype(np.float64), B.N)
+    F = filter_blocks(B, tol)
+    S = build_system(B, F, mode=0)
+    res = S.lsqr(B.h, y0=y0, atol=atol, btol=btol, max_iter=max_iter, history=history)
+    a = S.coefficients(res["y"])
+    return dict(blocks=B, filt=F, system=S, a=a, **res)
