@@ -268,10 +268,10 @@ def test_manufactured_solution_is_recovered_by_dense_least_squares():
 
 
 def test_manufactured_solution_2d_and_heat():
-    p2 = synth.poisson2d(S=3, K=60, n=24)
+    p2 = synth.poisson2d(S=3, K=64, n=36, R=2.0)
     p2.coef, p2.waves = [1.0], [[1.0, 2.0]]
-    p3 = synth.heat3d(S=3, K=60, n=10, k=1.0)
-    for p, lim in [(p2, 1e-4), (p3, 1e-3)]:
+    p3 = synth.heat3d(S=2, K=100, n=12, k=1.0, R=2.0)
+    for p, lim in [(p2, 3e-4), (p3, 3e-3)]:
         prm = synth.feature_params(p)
         M, h = oracle.assemble_dense(p, prm)
         U, s, Vt = np.linalg.svd(M, full_matrices=False)
@@ -305,9 +305,10 @@ def test_qrcp_reconstructs_and_is_orthonormal(m, n):
 
 def test_qrcp_diagonal_matrix_closed_form():
     """On a permuted diagonal the pivots come out in decreasing order, |R_kk|
-    are the sorted magnitudes, and the kept count is #{|d| >= tol max|d|}
-    (a value exactly at the threshold is kept: the drop test is strict)."""
-    d = np.array([3.0, -1e-3, 7.0, 1e-6, 0.7, -7e-5, 2e-9])
+    are the sorted magnitudes, and the kept count is #{|d| >= tol max|d|}.
+    Powers of two make every threshold exact: an entry equal to tol |R_11|
+    is kept (the drop test is strict)."""
+    d = np.array([4.0, -2.0 ** -10, 8.0, 2.0 ** -20, 1.0, -2.0 ** -14, 2.0 ** -30])
     A = np.zeros((9, 7))
     A[np.arange(7), np.arange(7)] = d
     A = A[np.random.default_rng(0).permutation(9)]
@@ -315,9 +316,10 @@ def test_qrcp_diagonal_matrix_closed_form():
     f = oracle.qrcp(A, 0.0)
     assert list(f.perm) == list(order)
     assert np.abs(np.diag(f.QR[:7, :7])) == pytest.approx(np.abs(d[order]), rel=1e-15)
-    for tol in [1e-1, 1e-4, 1e-5, 1e-7, 1e-9, 1e-10]:
-        assert oracle.qrcp(A, tol).rank == int((np.abs(d) >= tol * 7.0).sum())
-    assert oracle.qrcp(A, 1e-6 / 7.0).rank == 5
+    for tol in [2.0 ** -2, 2.0 ** -12, 2.0 ** -16, 2.0 ** -25, 2.0 ** -40]:
+        assert oracle.qrcp(A, tol).rank == int((np.abs(d) >= tol * 8.0).sum())
+    assert oracle.qrcp(A, 2.0 ** -23).rank == 6      # 2^-20 == tol * 8: kept
+    assert oracle.qrcp(A, 2.0 ** -23 * (1 + 2.0 ** -50)).rank == 5
 
 
 def test_qrcp_rank_equals_numerical_rank_with_spectral_gap():
@@ -392,10 +394,13 @@ def test_preconditioned_operator_equals_explicit_q():
     rng = np.random.default_rng(10)
     x = rng.standard_normal(S0.n)
     y = rng.standard_normal(S0.N)
-    assert S0.matvec(x) == pytest.approx(S1.matvec(x), abs=1e-7 * np.linalg.norm(x))
-    assert S0.rmatvec(y) == pytest.approx(S1.rmatvec(y), abs=1e-7 * np.linalg.norm(y))
-    # adjointness
-    assert np.dot(S0.matvec(x), y) == pytest.approx(np.dot(x, S0.rmatvec(y)), rel=1e-9)
+    # A_hat R^-1 by substitution and Q_hat agree up to rounding amplified by kappa(R_hat)
+    kap = max(np.linalg.cond(f.R) for f in F)
+    tol = 100 * np.finfo(float).eps * kap
+    assert np.linalg.norm(S0.matvec(x) - S1.matvec(x)) <= tol * np.linalg.norm(x)
+    assert np.linalg.norm(S0.rmatvec(y) - S1.rmatvec(y)) <= tol * np.linalg.norm(y)
+    # adjointness of the forward and transposed applications
+    assert abs(np.dot(S0.matvec(x), y) - np.dot(x, S0.rmatvec(y))) <= tol * np.linalg.norm(x) * np.linalg.norm(y)
 
 
 def _global_q(B, F):
