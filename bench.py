@@ -1,0 +1,412 @@
+"""Benchmark: solve time to a fixed error for the RRQR-filtered, preconditioned
+ELM-FBPINN solver on one GB300 (and N independent instances on N GPUs).
+
+Workload (N = 1): 2D Poisson on [0,1]^2, u = sin2pix sin2piy + 0.05
+sin30pix sin30piy, 20 x 20 subdomains (overlap ratio 1.25), 300 tanh features
+each, 360 x 360 cell-centred interior grid (the paper's S*ceil(K^(1/d)) rule)
+plus 1440 boundary points, filter threshold 1e-10.
+
+A step is one pass of the whole path over one instance:
+  assemble (FP32) -> RRQR filter (FP64 QRCP, Q_hat rounded to FP32) ->
+  LSQR on Q_hat (FP32 products, FP64 vectors and scalars) for the iteration
+  count that reaches the target error -> a = S^-1 y -> u_hat and its error on
+  the 400 x 400 test grid.
+The target error and the iteration counts come from an untimed calibration
+that records LSQR iterates every 10 iterations and evaluates each one; the
+target is the tightest value of a fixed ladder that both the mixed path and
+the plain FP64 path (FP64 assembly, FP64 kept columns with R^-1 substitution,
+zero start) reach.  Both paths are timed; "value" is the mixed path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+TARGET_LADDER = [1e-6, 2e-6, 5e-6, 1e-5, 2e-5, 5e-5, 1e-4, 2e-4, 5e-4, 1e-3, 2e-3, 5e-3, 1e-2]
+TOL = 1e-10
+SNAP_EVERY = 10
+CAL_ITERS = 3000
+# Nominal FP64 rate derived from the unit count and clock: 152 SMs x 4 FP64
+# flop/clk/SM (2 DFMA lanes) x 2.07 GHz = 1258 GFLOP/s (a DFMA probe measured
+# 1194 GFLOP/s on this part).
+FP64_PEAK_GFLOPS = 152 * 4 * 2.07
+# DRAM traffic per launch from ncu captures (profiles/); None until captured
+# for the current kernel version.
+NCU_TRAFFIC = {}
+
+
+def workload():
+    return synth.poisson2d()
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------------------
+# accounting
+# ---------------------------------------------------------------------------
+
+def qrcp_flops(m: np.ndarray, K: int, r: np.ndarray) -> float:
+    """Algorithmic flops of the Householder steps taken: sum_i<k 4 (m-i)(K-i)."""
+    tot = 0.0
+    for mj, rj in zip(m, r):
+        i = np.arange(int(rj), dtype=np.float64)
+        tot += float(np.sum(4.0 * (mj - i) * (K - i)))
+    return tot
+
+
+def formq_flops(m: np.ndarray, r: np.ndarray) -> float:
+    tot = 0.0
+    for mj, rj in zip(m, r):
+        i = np.arange(int(rj), dtype=np.float64)
+        tot += float(np.sum(4.0 * (mj - i) * (rj - i)))
+    return tot
+
+
+def lsqr_bytes_per_iter(m, r, N, val_bytes):
+    nnz = float(np.sum(m * r))
+    return 2.0 * nnz * val_bytes + 2.0 * (N + float(np.sum(r))) * 8.0
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, path):
+        self.path = path
+        self.p = None
+
+    def __enter__(self):
+        try:
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.f = open(self.path, "w")
+            dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={dev}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = []
+        for k, nm in enumerate(names):
+            if any(r[5 + k].strip().lower() == "active" for r in rows if len(r) > 5 + k):
+                reasons.append(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2506_17626_gb300 import build as B
+    B.build()
+    import paper_2506_17626_gb300 as R
+    from paper_2506_17626_gb300 import _native as N
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+
+    p = workload()
+    if world > 1:           # independent instances, one per rank (weak scaling)
+        p.seed = p.seed + rank
+    prm = synth.feature_params(p)
+    h_prm = torch.from_numpy(prm.ravel()).pin_memory()
+    d_prm = h_prm.to(dev)
+    Xt = torch.from_numpy(oracle_free_test_grid(p)).to(dev)
+
+    def make(asm, op):
+        S = R.System([p], asm=asm, op=op, tol=TOL, device=str(dev))
+        return S
+
+    paths = {"mixed": make("fp32", "q32"), "fp64": make("fp64", "ar64")}
+
+    # ---- calibration (untimed): error after every SNAP_EVERY iterations
+    curves = {}
+    for name, S in paths.items():
+        S.assemble(d_prm)
+        S.filter()
+        cap = CAL_ITERS // SNAP_EVERY
+        snap = torch.zeros((cap, S.sizes["n_cols"]), dtype=torch.float64, device=dev)
+        a, rep = S.solve(atol=0, btol=0, max_iter=CAL_ITERS, snap=snap, snap_every=SNAP_EVERY)
+        errs = []
+        for s in range(cap):
+            a_s = S.coefficients(snap[s])
+            _, err = S.evaluate(d_prm, a_s, [Xt])
+            e = err.cpu().numpy()
+            errs.append(float(np.sqrt(e[0] / e[1])))
+        curves[name] = np.array(errs)
+        log(f"[cal] {name}: min rel L2 {curves[name].min():.3e} at it {SNAP_EVERY * (1 + int(curves[name].argmin()))}")
+    target = None
+    for t in TARGET_LADDER:
+        if all((c <= t).any() for c in curves.values()):
+            target = t
+            break
+    if target is None:
+        target = float(max(c.min() for c in curves.values())) * 1.01
+    kstar = {n: SNAP_EVERY * (1 + int(np.argmax(c <= target))) for n, c in curves.items()}
+    log(f"[cal] target {target:g}, iterations {kstar}")
+
+    # ---- timed steps
+    st = torch.cuda.current_stream()
+
+    def step(S, k, e2e=False):
+        if e2e:
+            d_prm.copy_(h_prm, non_blocking=True)
+        S.assemble(d_prm)
+        S.filter()
+        a, rep = S.solve(atol=0, btol=0, max_iter=k)
+        _, err = S.evaluate(d_prm, a, [Xt])
+        if e2e:
+            a_h = torch.empty(a.numel(), dtype=torch.float64, pin_memory=True)
+            e_h = torch.empty(err.numel(), dtype=torch.float64, pin_memory=True)
+            a_h.copy_(a, non_blocking=True)
+            e_h.copy_(err, non_blocking=True)
+            return a, err, a_h, e_h
+        return a, err
+
+    def timed(S, k, steps, warm, e2e=False, prof=False):
+        for _ in range(warm):
+            step(S, k, e2e)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if prof:
+            N.profile_reset()
+            N.profile_enable(True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        ev[0].record(st)
+        outs = None
+        for i in range(steps):
+            outs = step(S, k, e2e)
+            ev[i + 1].record(st)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        prof_data = None
+        if prof:
+            N.profile_enable(False)
+            prof_data = N.profile_read()
+        per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+        return per, outs, prof_data
+
+    with Clocks(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp",
+                             "bench_clocks.csv")) as clk:
+        per_mixed, outs, prof = timed(paths["mixed"], kstar["mixed"], args.steps, args.warmup, prof=True)
+    per_fp64, outs64, prof64 = timed(paths["fp64"], kstar["fp64"], args.steps, args.warmup, prof=True)
+    per_e2e, outs_e2e, _ = timed(paths["mixed"], kstar["mixed"], args.steps, max(1, args.warmup // 2), e2e=True)
+
+    def mx(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms_mixed = mx(float(np.mean(per_mixed)))
+    ms_fp64 = mx(float(np.mean(per_fp64)))
+    ms_e2e = mx(float(np.mean(per_e2e)))
+    err_m = outs[1].cpu().numpy()
+    err_f = outs64[1].cpu().numpy()
+    rel_m = float(np.sqrt(err_m[0] / err_m[1]))
+    rel_f = float(np.sqrt(err_f[0] / err_f[1]))
+
+    # ---- roofline of the dominant kernel (mixed path)
+    S = paths["mixed"]
+    ranks = S.filter().cpu().numpy()
+    m = np.array([S.block_info(j)[0] for j in range(S.sizes["n_blocks"])])
+    K = p.K
+    steps = args.steps
+    tot = {k: v for k, v in prof.items()}
+    dom = max(tot, key=lambda k: tot[k][1])
+    launches = sum(v[0] for v in tot.values())
+    per_launch_ms = {k: v[1] / v[0] for k, v in tot.items()}
+    roof = None
+    if dom == "k_qrcp":
+        fl = qrcp_flops(m, K, ranks)
+        ach = fl / (per_launch_ms[dom] * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                "frac": ach / (FP64_PEAK_GFLOPS / 1e3), "peak_source": "derived FP64: 152 SMs x 4 flop/clk x 2.07 GHz",
+                "algorithmic_per_launch": fl}
+    elif dom == "k_form_q":
+        fl = formq_flops(m, ranks)
+        ach = fl / (per_launch_ms[dom] * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                "frac": ach / (FP64_PEAK_GFLOPS / 1e3), "peak_source": "derived FP64: 152 SMs x 4 flop/clk x 2.07 GHz",
+                "algorithmic_per_launch": fl}
+    else:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        by = lsqr_bytes_per_iter(m, ranks, S.sizes["n_rows"], 4) * kstar["mixed"]
+        ach = by / (per_launch_ms[dom] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                "algorithmic_per_launch": by}
+    roof["traffic"] = NCU_TRAFFIC.get(dom)
+    qr_gflops = qrcp_flops(m, K, ranks) / (per_launch_ms["k_qrcp"] * 1e-3) / 1e9
+    lsqr_ms = per_launch_ms["k_lsqr"]
+    spmv_gbs = lsqr_bytes_per_iter(m, ranks, S.sizes["n_rows"], 4) * kstar["mixed"] / (lsqr_ms * 1e-3) / 1e9
+
+    clocks = clk.summary()
+    out = {
+        "metric": "solve time to fixed error (mixed FP32/FP64, zero start)",
+        "value": ms_mixed, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_mixed, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "2D Poisson 20x20 subdomains, delta 1.25, K=300, 360^2 interior + 1440 boundary "
+                               "rows, filter tol 1e-10, error on 400^2 test grid",
+                   "target_rel_l2": target, "iterations": kstar, "rel_l2_reached": {"mixed": rel_m, "fp64": rel_f},
+                   "l2_flush": "none: working set (M, QR work, Q_hat > 1.5 GB) exceeds L2 every step",
+                   "parallelism": f"independent instances x{world}" if world > 1 else "1 instance"},
+        "fp64_zero_start_ms": ms_fp64,
+        "qr_gflops": qr_gflops, "spmv_gbs": spmv_gbs,
+        "kernels_ms_per_step": {k: v[1] / steps for k, v in tot.items()},
+        "roofline": roof,
+        "e2e": {"value": ms_e2e, "unit": "ms", "h2d_bytes_per_step": int(h_prm.numel() * 8),
+                "d2h_bytes_per_step": int(S.sizes["n_cols"] * 8 + 4 * 8)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(p, prm, kstar["fp64"], budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def oracle_free_test_grid(p):
+    """400 x 400 cell-centred test grid (dimension 0 fastest)."""
+    nt = list(p.n_test)
+    axes = [p.lo[i] + (np.arange(nt[i]) + 0.5) * (p.hi[i] - p.lo[i]) / nt[i] for i in range(p.dim)]
+    g = np.meshgrid(*axes, indexing="ij")
+    return np.ascontiguousarray(np.stack([a.transpose(list(range(p.dim))[::-1]).ravel() for a in g], axis=1))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (bounded sample)
+# ---------------------------------------------------------------------------
+
+def cpu_baseline(p, prm, iters, budget_s=20.0, stride=None):
+    """The oracle (single-threaded FP64 C, as it stands) on every stride-th
+    block of the workload: assembly, QRCP and 10 LSQR iterations of the
+    sampled-block subsystem, plus evaluation at every 10th test point; each
+    part scaled to the full workload (blocks x J/sample, iterations x the FP64
+    path's iteration count, points x 10)."""
+    import oracle
+    J = p.J
+    stride = stride or 2
+    blocks = list(range(0, J, stride))
+    t0 = time.perf_counter()
+    Bk = oracle.assemble(p, prm, blocks=blocks)
+    t_asm = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    F = oracle.filter_blocks(Bk, TOL)
+    t_qr = time.perf_counter() - t0
+    Ssub = oracle.build_system(Bk, F, mode=0)
+    t0 = time.perf_counter()
+    Ssub.lsqr(Bk.h, atol=0, btol=0, max_iter=10)
+    t_it = (time.perf_counter() - t0) / 10
+    X = oracle_free_test_grid(p)[::10]
+    a = np.zeros(J * p.K)
+    t0 = time.perf_counter()
+    oracle.evaluate(p, prm, a, X)
+    t_ev = (time.perf_counter() - t0) * 10
+    scale = J / len(blocks)
+    total_s = (t_asm + t_qr) * scale + t_it * scale * iters + t_ev
+    return {"value": total_s * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": f"{len(blocks)} of {J} blocks (every {stride}th): assembly + QRCP + 10 LSQR iterations on "
+                      f"the sampled subsystem scaled x{scale:g} and to {iters} iterations; evaluation at every "
+                      f"10th of the 400^2 test points scaled x10",
+            "parts_s": {"assembly": t_asm * scale, "qrcp": t_qr * scale, "lsqr": t_it * scale * iters,
+                        "eval": t_ev}}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle as it stands, one bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    p = workload()
+    prm = synth.feature_params(p)
+    iters = args.ref_iters
+    vals = []
+    for s in range(args.warmup + args.steps):
+        r = cpu_baseline(p, prm, iters, stride=8)
+        if s >= args.warmup:
+            vals.append(r["value"])
+    v = float(np.mean(vals))
+    out = {"impl": "reference", "metric": "solve time to fixed error (mixed FP32/FP64, zero start)",
+           "value": v, "unit": "ms", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "2D Poisson 20x20 subdomains, delta 1.25, K=300, 360^2 interior + 1440 boundary "
+                                  "rows, filter tol 1e-10, error on 400^2 test grid", "lsqr_iterations": iters},
+           "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": r["sample"]},
+           "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--ref-iters", type=int, default=300,
+                    help="LSQR iteration count the reference arm extrapolates to")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

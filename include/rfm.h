@@ -1,0 +1,243 @@
+/*
+ * rfm.h -- C ABI of the GB300 (sm_103a) library for ELM-FBPINNs with local
+ * RRQR filtering and right preconditioning (van Beek, Dolean, Moseley, "Local
+ * Feature Filtering for Scalable and Well-Conditioned Domain-Decomposed Random
+ * Feature Methods").
+ *
+ * The path has four calls that follow the paper's problem statement:
+ *   rfm_assemble     the block-sparse least-squares system M a = h of
+ *                    Sec. 2.1 (Eqs. (1)-(5)) in the block form of Eq. (6);
+ *   rfm_rrqr_filter  Algorithm 1: per block, Householder QR with column
+ *                    pivoting stopped at |R_kk| < tol |R_11| (Sec. 3.1), and
+ *                    the preconditioner factors of Sec. 3.2;
+ *   rfm_lsqr_solve   Algorithm 2: LSQR (Paige and Saunders 1982) on the
+ *                    right-preconditioned system M_hat S^-1 y = h, then
+ *                    a = S^-1 y with zeros at dropped columns;
+ *   rfm_eval         the ansatz of Eq. (1) at query points and the error
+ *                    measures of Sec. 4.2.
+ *
+ * Conventions for every call:
+ *  - All device memory belongs to the caller.  A system (one or more problem
+ *    instances solved side by side) lives in one caller-allocated device
+ *    workspace of rfm_problem_size()'s workspace_bytes; the library carves
+ *    it and keeps nothing between calls.  The same instance list, count and
+ *    rfm_config must be passed to every call on a workspace.
+ *  - Calls are asynchronous on the given CUDA stream (NULL = legacy default
+ *    stream): results are valid once the stream has reached the call.  No
+ *    call synchronises the host, allocates device memory, or runs numerics on
+ *    the host.  Host-side work is limited to O(J + grid size) layout
+ *    bookkeeping and one small upload in rfm_assemble.
+ *  - Every call returns an rfm_status; on failure rfm_last_error() (per host
+ *    thread) describes it.  No C++ exception crosses the ABI.
+ *  - Device pointers must be aligned to 16 bytes and the workspace to 256.
+ */
+#ifndef RFM_H
+#define RFM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RFM_ABI_VERSION 1
+
+typedef enum {
+    RFM_OK = 0,
+    RFM_EINVAL = 1,     /* bad argument or problem description */
+    RFM_ECUDA = 2,      /* a CUDA runtime call failed (message in rfm_last_error) */
+    RFM_ENUMERIC = 3,   /* NaN/Inf met in a recurrence scalar */
+    RFM_ETIMEOUT = 4,   /* a bounded device-side wait gave up (see rfm_lsqr_opts.timeout_ms) */
+    RFM_ENOSPACE = 5    /* workspace smaller than rfm_problem_size() asks for */
+} rfm_status;
+
+/* PDE kinds: RFM_PDE_POISSON is -Laplace(u) = f with Dirichlet data on every
+ * face; RFM_PDE_HEAT is u_t - kappa Laplace_x(u) = f where the last coordinate
+ * is time, with Dirichlet data on the spatial faces (boundary set 0) and
+ * initial data on t = lo (boundary set 1). */
+enum { RFM_PDE_POISSON = 0, RFM_PDE_HEAT = 1 };
+
+/* Manufactured data families (fam[] layout):
+ *  RFM_FAM_SINPROD       u = sum_m fam[4m] prod_i sin(fam[4m+1+i] pi x_i);
+ *                        f = -Laplace u, g = u.
+ *  RFM_FAM_HEAT_SINPROD  u = sum_m fam[4m] exp(-kappa pi^2 |k_m|^2 t)
+ *                        prod_{spatial i} sin(fam[4m+1+i] pi x_i); f = 0, g = u.
+ *  RFM_FAM_PARAM5        f = sin(a pi x) sin(b pi y) + c sin(d pi x + e pi y),
+ *                        g = 0 with (a,b,c,d,e) = fam[0..4]; no closed form. */
+enum { RFM_FAM_SINPROD = 0, RFM_FAM_HEAT_SINPROD = 1, RFM_FAM_PARAM5 = 2 };
+
+/* One problem instance (Sec. 2.1 and the common settings of Sec. 4.2).
+ *  dim            1..3; the box is prod_i [lo[i], hi[i]].
+ *  S[i]           subdomains along dimension i (>= 2); J = prod S[i],
+ *                 numbered lexicographically with dimension 0 fastest.
+ *  delta          overlap ratio of Sec. 4.2 (subdomain width / centre
+ *                 spacing): centre lo + (hi-lo) j/(S-1), half-width
+ *                 (hi-lo) delta / (2 (S-1)).
+ *  K              random tanh features per subdomain.
+ *  n[i]           cell-centred interior collocation points per dimension;
+ *                 boundary rows sit on each face at the interior grid of the
+ *                 other dimensions.  Row order: interior (dimension 0
+ *                 fastest), then faces (dim 0 lo, dim 0 hi, dim 1 lo, ...).
+ *  lam[l]         loss weight of boundary set l (Eq. (3)).
+ *  family, n_modes, fam[]: the data, see above. */
+typedef struct rfm_problem {
+    int32_t dim, pde, family, n_modes;
+    int32_t S[3], n[3];
+    int32_t K, reserved0;
+    double delta, kappa;
+    double lo[3], hi[3];
+    double lam[2];
+    double fam[64];
+} rfm_problem;
+
+/* Arithmetic of the assembly. */
+enum { RFM_ASM_FP64 = 0, RFM_ASM_FP32 = 1 };
+
+/* LSQR operator (all are the same preconditioned operator of Algorithm 2 up
+ * to rounding, except RFM_OP_PLAIN):
+ *  RFM_OP_AR64    M_hat S^-1 applied as the FP64 kept columns followed by
+ *                 FP64 substitution with R_hat_j (Sec. 3.2).
+ *  RFM_OP_Q32     the explicit orthonormal blocks Q_hat_j of Proposition 3.1,
+ *                 formed in FP64 from the reflectors and stored in FP32;
+ *                 FP32 products with FP32 accumulation, FP64 vectors and
+ *                 scalars (mixed precision).
+ *  RFM_OP_Q64     Q_hat_j kept in FP64.
+ *  RFM_OP_PLAIN   the unfiltered, unpreconditioned M in FP64 (the paper's
+ *                 plain-LSQR baseline of Sec. 4.3); the filter call then only
+ *                 records the blocks. */
+enum { RFM_OP_AR64 = 0, RFM_OP_Q32 = 1, RFM_OP_Q64 = 2, RFM_OP_PLAIN = 3 };
+
+typedef struct rfm_config {
+    int32_t asm_prec;   /* RFM_ASM_FP64 or RFM_ASM_FP32 */
+    int32_t op;         /* RFM_OP_* */
+    double tol;         /* relative drop threshold sigma of Algorithm 1 */
+} rfm_config;
+
+/* Sizes of a system (sums over its instances). */
+typedef struct rfm_sizes {
+    int64_t n_inst;
+    int64_t n_blocks;        /* sum of J over instances */
+    int64_t n_rows;          /* sum of N = N_I + N_B */
+    int64_t n_cols;          /* sum of J K (the layout of a and y) */
+    int64_t block_rows;      /* sum over blocks of |I_j| */
+    int64_t max_block_rows;  /* max |I_j| */
+    int64_t max_K;
+    int64_t workspace_bytes; /* device bytes the caller must provide */
+} rfm_sizes;
+
+/* Host only.  Validates the instances and computes the system's sizes.
+ * Errors: RFM_EINVAL for an invalid instance (dim outside 1..3, S < 2, K < 1
+ * or > 1024, n < 1, delta <= 0, a subdomain with no collocation point, or a
+ * block taller than 4194304 rows). */
+rfm_status rfm_problem_size(const rfm_problem *probs, int n_inst, const rfm_config *cfg, rfm_sizes *out);
+
+/* Assembly (Sec. 2.1, Eqs. (1)-(6)).  For every block j the dense local
+ * matrix M_j = M restricted to I_j x K_j, with I_j = {r : w_j(x_r) != 0}:
+ * interior rows N[w_j phi_jk](x)/sqrt(N_I), boundary rows
+ * sqrt(lam_l/N_B^(l)) w_j phi_jk(x), and h = [f/sqrt(N_I); sqrt(lam_l/N_B^(l)) g].
+ * Features phi_jk = tanh(sum_i w_i (x_i - mu_i)/sig_i + b) with (w, b) read
+ * from d_params: per instance J*K*(dim+1) doubles, (j, k, [w_1..w_d, b])
+ * row-major, instances concatenated in order.  Windows: the normalised
+ * cosine window of Sec. 4.2.  Writes the workspace only. */
+rfm_status rfm_assemble(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const double *d_params,
+                        void *d_ws, size_t ws_bytes, void *stream);
+
+/* Filtering and preconditioner factors (Algorithm 1, Sec. 3.1-3.2).  Per
+ * block: Householder QR with column pivoting in FP64 (pivot = largest
+ * trailing column norm, norms downdated in FP64 with recomputation when
+ * cancellation makes the downdate unreliable; ties to the lowest original
+ * index), stopped at the first step whose |R_kk| is zero or below
+ * cfg->tol * |R_11|.  Keeps r_j columns; then prepares the operator that
+ * cfg->op names (kept columns, or Q_hat_j from the reflectors).
+ * d_rank (nullable, n_blocks int32) receives r_j; d_perm (nullable,
+ * n_blocks*K int32) the pivoted column order (first r_j entries = kept). */
+rfm_status rfm_rrqr_filter(const rfm_problem *probs, int n_inst, const rfm_config *cfg, void *d_ws, size_t ws_bytes,
+                           int32_t *d_rank, int32_t *d_perm, void *stream);
+
+typedef struct rfm_lsqr_opts {
+    double atol, btol;   /* stopping tolerances of Paige and Saunders (0 = run max_iter) */
+    int32_t max_iter;
+    int32_t timeout_ms;  /* bound on every device-side wait; 0 = 10000 */
+    double *d_snap;      /* nullable: iterate snapshots, snap_cap x n_cols doubles; after
+                            iteration i = s*snap_every (s = 1..snap_cap) y_i is written to
+                            row s-1 (kept slots only; the caller clears the buffer) */
+    int32_t snap_every, snap_cap;
+} rfm_lsqr_opts;
+
+/* Report per instance (written to device memory):
+ *   itn, istop (0 exact start, 1 residual test, 2 normal-equation test,
+ *   7 iteration limit), rnorm, arnorm, anorm, ynorm, bnorm estimates. */
+typedef struct rfm_lsqr_report {
+    double itn, istop, rnorm, arnorm, anorm, ynorm, bnorm, status;
+} rfm_lsqr_report;
+
+/* LSQR on min ||M_hat S^-1 y - h|| for every instance at once (each with its
+ * own scalars and stopping test), then a = S^-1 y scattered to the J*K layout
+ * with zeros at dropped columns (Algorithm 2).
+ *  d_y0     nullable warm start (n_cols doubles, per block the first r_j of
+ *           each K-slot used); the iteration runs on the residual system.
+ *  d_y      nullable output y (n_cols doubles, same layout).
+ *  d_a      output coefficients (n_cols doubles).
+ *  d_report n_inst rfm_lsqr_report.
+ * Stopping (per instance): ||r|| <= btol ||h|| + atol ||A||_F ||y||, or
+ * ||A^T r|| <= atol ||A||_F ||r||, or max_iter, with the norm estimates of
+ * the 1982 paper and ||y|| computed exactly.
+ * Returns RFM_ETIMEOUT if a device-side grid barrier waited longer than
+ * timeout_ms (the kernel then stops at that barrier; results are invalid),
+ * RFM_ENUMERIC is reported through report.status. */
+rfm_status rfm_lsqr_solve(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const rfm_lsqr_opts *opts,
+                          const double *d_y0, double *d_y, double *d_a, rfm_lsqr_report *d_report,
+                          void *d_ws, size_t ws_bytes, void *stream);
+
+/* a = S^-1 y (Algorithm 2's last step) for an arbitrary y in the n_cols
+ * layout: per block a_j[perm[c]] = (R_hat_j^-1 y_j)[c] for kept c, 0 at
+ * dropped columns (RFM_OP_PLAIN: a = y).  Requires a filtered workspace. */
+rfm_status rfm_coefficients(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const double *d_y,
+                            double *d_a, void *d_ws, size_t ws_bytes, void *stream);
+
+/* Ansatz of Eq. (1), u_hat(x) = sum_j w_j(x) sum_k a_jk phi_jk(x), in FP64 at
+ * query points, and error sums against the family's closed-form u.
+ *  d_x      points, 3 doubles each (unused coordinates ignored), instances
+ *           concatenated; h_pt_off host array of n_inst+1 offsets.
+ *  d_u      output u_hat per point.
+ *  d_err    nullable, 4 doubles per instance: sum (u_hat-u)^2, sum u^2,
+ *           sum |u_hat-u|, sum u (relative L2 and e_L1 of Sec. 4.2 follow).
+ * Uses the workspace (it must have been assembled) for its reduction scratch. */
+rfm_status rfm_eval(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const double *d_params,
+                    const double *d_a, const double *d_x, const int64_t *h_pt_off, double *d_u, double *d_err,
+                    void *d_ws, size_t ws_bytes, void *stream);
+
+/* Device-side copies of the assembled blocks for inspection and tests:
+ * block b's M_j (|I_j| x K, column-major with leading dimension *ld) starts at
+ * element offset *moff of the M arena, and its rows are the global rows
+ * grow[roff .. roff+|I_j|).  Host only. */
+rfm_status rfm_block_info(const rfm_problem *probs, int n_inst, const rfm_config *cfg, int64_t block,
+                          int64_t *m, int64_t *ld, int64_t *moff, int64_t *roff);
+
+/* Device pointers into the workspace (views for tests and for the warm
+ * start): which = 0 M arena (FP64 or FP32 by asm_prec), 1 h (FP64, n_rows),
+ * 2 grow (int32, block_rows; global row index across instances),
+ * 3 QR work (FP64, R above the diagonal, reflectors below), 4 r11 (FP64 per
+ * block), 5 operator arena (Q32: FP32; others FP64). */
+rfm_status rfm_workspace_view(const rfm_problem *probs, int n_inst, const rfm_config *cfg, void *d_ws, int which,
+                              void **ptr);
+
+/* Kernel timing for profiling (process-wide, host side).  While enabled,
+ * every kernel the library launches is bracketed by CUDA events on its
+ * stream.  rfm_profile_read waits for the recorded events and returns up to
+ * max entries (name, launches, total milliseconds) aggregated by kernel name
+ * since the last reset; the return value is the number of entries.  Events
+ * are created with cudaEventCreate (no device memory).  Not for use inside
+ * stream capture. */
+rfm_status rfm_profile_enable(int on);
+rfm_status rfm_profile_reset(void);
+int rfm_profile_read(const char **names, int64_t *launches, double *ms, int max);
+
+const char *rfm_last_error(void);
+int rfm_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

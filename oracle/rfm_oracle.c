@@ -701,18 +701,27 @@ void orc_coefficients(int64_t J, int K, const int32_t *r, const int32_t *perm, c
 /* evaluation (Eq. (1)) and errors (Sec. 4.2)                                */
 /* ------------------------------------------------------------------------ */
 
-/* u_hat(x) = sum_j w_j(x) sum_k a_jk phi_jk(x) at npts points X (npts x dim). */
+/* u_hat(x) = sum_j w_j(x) sum_k a_jk phi_jk(x) at npts points X (npts x dim).
+ * The normalising sum W(x) = sum_l hat_w_l(x) is the same for every j at a
+ * point, so it is formed once per point (same terms, same order as in
+ * orc_window) and w_j = hat_w_j / W. */
 void orc_eval(const orc_problem *P, const double *params, const double *a, int64_t npts,
               const double *X, double *u) {
     int64_t J = orc_num_subdomains(P);
     for (int64_t p = 0; p < npts; ++p) {
         double x[3] = {0, 0, 0};
         for (int i = 0; i < P->dim; ++i) x[i] = X[p * P->dim + i];
+        double W = 0.0;
+        for (int64_t l = 0; l < J; ++l) {
+            double dw[3], d2w[3];
+            W += orc_window_hat(P, l, x, dw, d2w);
+        }
         double s = 0.0;
         for (int64_t j = 0; j < J; ++j) {
             double dw[3], d2w[3];
-            double w = orc_window(P, j, x, dw, d2w);
-            if (w == 0.0) continue;
+            double h = orc_window_hat(P, j, x, dw, d2w);
+            if (h == 0.0 || W == 0.0) continue;
+            double w = h / W;
             double mu[3], sig[3];
             orc_subdomain(P, j, mu, sig);
             double sj = 0.0;

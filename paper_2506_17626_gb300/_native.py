@@ -1,0 +1,136 @@
+"""ctypes view of the C ABI in include/rfm.h (argument marshalling only).
+
+The library is required: importing the binding without a built librfm.so
+raises, and there is no CPU fallback for any call.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librfm.so")
+
+RFM_OK, RFM_EINVAL, RFM_ECUDA, RFM_ENUMERIC, RFM_ETIMEOUT, RFM_ENOSPACE = range(6)
+STATUS = {0: "RFM_OK", 1: "RFM_EINVAL", 2: "RFM_ECUDA", 3: "RFM_ENUMERIC", 4: "RFM_ETIMEOUT", 5: "RFM_ENOSPACE"}
+ASM = {"fp64": 0, "fp32": 1}
+OPS = {"ar64": 0, "q32": 1, "q64": 2, "plain": 3}
+
+
+class RfmProblem(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("pde", C.c_int32), ("family", C.c_int32), ("n_modes", C.c_int32),
+                ("S", C.c_int32 * 3), ("n", C.c_int32 * 3), ("K", C.c_int32), ("reserved0", C.c_int32),
+                ("delta", C.c_double), ("kappa", C.c_double), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("lam", C.c_double * 2), ("fam", C.c_double * 64)]
+
+
+class RfmConfig(C.Structure):
+    _fields_ = [("asm_prec", C.c_int32), ("op", C.c_int32), ("tol", C.c_double)]
+
+
+class RfmSizes(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("n_inst", "n_blocks", "n_rows", "n_cols", "block_rows",
+                                         "max_block_rows", "max_K", "workspace_bytes")]
+
+
+class RfmLsqrOpts(C.Structure):
+    _fields_ = [("atol", C.c_double), ("btol", C.c_double), ("max_iter", C.c_int32), ("timeout_ms", C.c_int32),
+                ("d_snap", C.c_void_p), ("snap_every", C.c_int32), ("snap_cap", C.c_int32)]
+
+
+REPORT_FIELDS = ("itn", "istop", "rnorm", "arnorm", "anorm", "ynorm", "bnorm", "status")
+
+EXPORTS = ["rfm_problem_size", "rfm_assemble", "rfm_rrqr_filter", "rfm_lsqr_solve", "rfm_coefficients",
+           "rfm_eval", "rfm_block_info", "rfm_workspace_view", "rfm_profile_enable", "rfm_profile_reset",
+           "rfm_profile_read", "rfm_last_error", "rfm_abi_version"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load librfm.so (raises OSError when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} is missing: build it with paper_2506_17626_gb300.build.build() "
+                      "(there is no fallback implementation)")
+    L = C.CDLL(path)
+    P = C.POINTER(RfmProblem)
+    CF = C.POINTER(RfmConfig)
+    vp, i32, i64, st = C.c_void_p, C.c_int32, C.c_int64, C.c_int
+    sigs = {
+        "rfm_problem_size": [P, C.c_int, CF, C.POINTER(RfmSizes)],
+        "rfm_assemble": [P, C.c_int, CF, vp, vp, C.c_size_t, vp],
+        "rfm_rrqr_filter": [P, C.c_int, CF, vp, C.c_size_t, vp, vp, vp],
+        "rfm_lsqr_solve": [P, C.c_int, CF, C.POINTER(RfmLsqrOpts), vp, vp, vp, vp, vp, C.c_size_t, vp],
+        "rfm_eval": [P, C.c_int, CF, vp, vp, vp, vp, vp, vp, vp, C.c_size_t, vp],
+        "rfm_coefficients": [P, C.c_int, CF, vp, vp, vp, C.c_size_t, vp],
+        "rfm_block_info": [P, C.c_int, CF, i64, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)],
+        "rfm_workspace_view": [P, C.c_int, CF, vp, C.c_int, C.POINTER(vp)],
+    }
+    for name, args in sigs.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = st
+    L.rfm_profile_enable.argtypes = [C.c_int]
+    L.rfm_profile_enable.restype = C.c_int
+    L.rfm_profile_reset.argtypes = []
+    L.rfm_profile_reset.restype = C.c_int
+    L.rfm_profile_read.argtypes = [C.POINTER(C.c_char_p), C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int]
+    L.rfm_profile_read.restype = C.c_int
+    L.rfm_last_error.restype = C.c_char_p
+    L.rfm_last_error.argtypes = []
+    L.rfm_abi_version.restype = C.c_int
+    L.rfm_abi_version.argtypes = []
+    _lib = L
+    return L
+
+
+class RfmError(RuntimeError):
+    def __init__(self, call, code, msg):
+        super().__init__(f"{call} -> {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def check(call: str, code: int):
+    if code != RFM_OK:
+        raise RfmError(call, code, load().rfm_last_error().decode(errors="replace"))
+
+
+def problem_struct(p) -> RfmProblem:
+    """C struct from any object with the problem attributes (dim, pde, S, n, ...)."""
+    s = RfmProblem()
+    s.dim, s.pde, s.family = int(p.dim), int(p.pde), int(p.family)
+    s.n_modes = int(p.n_modes)
+    for i in range(3):
+        s.S[i] = int(p.S[i]) if i < min(p.dim, len(p.S)) else 1
+        s.n[i] = int(p.n[i]) if i < min(p.dim, len(p.n)) else 1
+        s.lo[i] = float(p.lo[i])
+        s.hi[i] = float(p.hi[i])
+    s.K = int(p.K)
+    s.delta, s.kappa = float(p.delta), float(p.kappa)
+    s.lam[0], s.lam[1] = float(p.lam[0]), float(p.lam[1])
+    fv = p.fam_vector()
+    for i in range(64):
+        s.fam[i] = float(fv[i])
+    return s
+
+
+def profile_enable(on: bool = True):
+    load().rfm_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    load().rfm_profile_reset()
+
+
+def profile_read() -> dict:
+    """{kernel name: (launches, total ms)} since the last reset (waits for the events)."""
+    L = load()
+    n = L.rfm_profile_read(None, None, None, 0)
+    names = (C.c_char_p * max(n, 1))()
+    cnt = (C.c_int64 * max(n, 1))()
+    ms = (C.c_double * max(n, 1))()
+    n = L.rfm_profile_read(names, cnt, ms, n)
+    return {names[i].decode(): (int(cnt[i]), float(ms[i])) for i in range(n)}

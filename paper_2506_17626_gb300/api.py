@@ -1,0 +1,166 @@
+"""Python face of the library: same calls as include/rfm.h, PyTorch for device
+memory and streams.  Every numerical step runs in the CUDA kernels of
+librfm.so; this module only allocates the workspace and passes pointers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import torch
+
+from . import _native as N
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class System:
+    """One or more problem instances solved side by side in one workspace.
+
+    asm: "fp64" | "fp32" (assembly arithmetic); op: "ar64" (FP64 kept columns
+    with R^-1 substitution), "q32" (explicit Q_hat in FP32, mixed precision),
+    "q64" (explicit Q_hat in FP64), "plain" (no filter, no preconditioner);
+    tol: relative drop threshold of the filter.
+    """
+
+    def __init__(self, problems, asm: str = "fp64", op: str = "ar64", tol: float = 1e-10,
+                 device: str = "cuda"):
+        self.problems = list(problems) if isinstance(problems, (list, tuple)) else [problems]
+        self.n = len(self.problems)
+        self._probs = (N.RfmProblem * self.n)(*[N.problem_struct(p) for p in self.problems])
+        self._cfg = N.RfmConfig(N.ASM[asm], N.OPS[op], float(tol))
+        self.asm, self.op, self.tol = asm, op, tol
+        self.lib = N.load()
+        sz = N.RfmSizes()
+        N.check("rfm_problem_size", self.lib.rfm_problem_size(self._probs, self.n, C.byref(self._cfg), C.byref(sz)))
+        self.sizes = {f: getattr(sz, f) for f, _ in N.RfmSizes._fields_}
+        self.device = torch.device(device)
+        self.ws = torch.empty(self.sizes["workspace_bytes"] + 256, dtype=torch.uint8, device=self.device)
+        base = self.ws.data_ptr()
+        self._ws_off = (-base) % 256
+        self.ws_ptr = base + self._ws_off
+        self.ws_bytes = self.sizes["workspace_bytes"]
+
+    # -- the four calls of the path -------------------------------------------------
+    def assemble(self, params: torch.Tensor):
+        """params: FP64 device tensor, all instances' (J, K, dim+1) arrays concatenated."""
+        assert params.is_cuda and params.dtype == torch.float64 and params.is_contiguous()
+        self._params = params
+        N.check("rfm_assemble", self.lib.rfm_assemble(self._probs, self.n, C.byref(self._cfg), _ptr(params),
+                                                      C.c_void_p(self.ws_ptr), self.ws_bytes, _stream()))
+
+    def filter(self, want_perm: bool = False):
+        nb = self.sizes["n_blocks"]
+        rank = torch.empty(nb, dtype=torch.int32, device=self.device) if self.op != "plain" else None
+        perm = torch.empty(self.sizes["n_cols"], dtype=torch.int32, device=self.device) if want_perm else None
+        N.check("rfm_rrqr_filter", self.lib.rfm_rrqr_filter(self._probs, self.n, C.byref(self._cfg),
+                                                            C.c_void_p(self.ws_ptr), self.ws_bytes, _ptr(rank),
+                                                            _ptr(perm), _stream()))
+        return (rank, perm) if want_perm else rank
+
+    def solve(self, atol=1e-10, btol=1e-10, max_iter=10000, y0: Optional[torch.Tensor] = None,
+              timeout_ms: int = 10000, want_y: bool = False, snap: Optional[torch.Tensor] = None,
+              snap_every: int = 0):
+        """LSQR of Algorithm 2.  snap: optional (cap, n_cols) FP64 tensor that
+        receives y after every snap_every-th iteration."""
+        nc = self.sizes["n_cols"]
+        a = torch.empty(nc, dtype=torch.float64, device=self.device)
+        y = torch.empty(nc, dtype=torch.float64, device=self.device) if want_y else None
+        rep = torch.empty(self.n * 8, dtype=torch.float64, device=self.device)
+        cap = 0 if snap is None else snap.shape[0]
+        if snap is not None:
+            assert snap.is_cuda and snap.dtype == torch.float64 and snap.shape[1] == nc and snap.is_contiguous()
+        opts = N.RfmLsqrOpts(float(atol), float(btol), int(max_iter), int(timeout_ms),
+                             _ptr(snap), int(snap_every if snap is not None else 0), int(cap))
+        if y0 is not None:
+            assert y0.is_cuda and y0.dtype == torch.float64 and y0.numel() == nc
+        N.check("rfm_lsqr_solve", self.lib.rfm_lsqr_solve(self._probs, self.n, C.byref(self._cfg), C.byref(opts),
+                                                          _ptr(y0), _ptr(y), _ptr(a), _ptr(rep),
+                                                          C.c_void_p(self.ws_ptr), self.ws_bytes, _stream()))
+        return (a, rep, y) if want_y else (a, rep)
+
+    def coefficients(self, y: torch.Tensor) -> torch.Tensor:
+        """a = S^-1 y with zeros at dropped columns (Algorithm 2, last step)."""
+        a = torch.empty(self.sizes["n_cols"], dtype=torch.float64, device=self.device)
+        N.check("rfm_coefficients", self.lib.rfm_coefficients(self._probs, self.n, C.byref(self._cfg), _ptr(y),
+                                                              _ptr(a), C.c_void_p(self.ws_ptr), self.ws_bytes,
+                                                              _stream()))
+        return a
+
+    def evaluate(self, params: torch.Tensor, a: torch.Tensor, X: Sequence[torch.Tensor], with_error=True):
+        """u_hat at points X[s] (n_s x dim FP64 tensors, one per instance); error sums per instance."""
+        pts = []
+        offs = [0]
+        for x in X:
+            x3 = torch.zeros((x.shape[0], 3), dtype=torch.float64, device=self.device)
+            x3[:, : x.shape[1]] = x
+            pts.append(x3)
+            offs.append(offs[-1] + x.shape[0])
+        Xc = torch.cat(pts).contiguous()
+        u = torch.empty(offs[-1], dtype=torch.float64, device=self.device)
+        err = torch.zeros(4 * self.n, dtype=torch.float64, device=self.device) if with_error else None
+        off_arr = (C.c_int64 * (self.n + 1))(*offs)
+        N.check("rfm_eval", self.lib.rfm_eval(self._probs, self.n, C.byref(self._cfg), _ptr(params), _ptr(a),
+                                              _ptr(Xc), off_arr, _ptr(u), _ptr(err), C.c_void_p(self.ws_ptr),
+                                              self.ws_bytes, _stream()))
+        return [u[offs[i]:offs[i + 1]] for i in range(self.n)], err
+
+    # -- views for tests --------------------------------------------------------------
+    def view(self, which: int) -> int:
+        p = C.c_void_p()
+        N.check("rfm_workspace_view", self.lib.rfm_workspace_view(self._probs, self.n, C.byref(self._cfg),
+                                                                  C.c_void_p(self.ws_ptr), which, C.byref(p)))
+        return p.value
+
+    def _tensor_at(self, ptr: int, count: int, dtype) -> torch.Tensor:
+        off = ptr - self.ws.data_ptr()
+        es = torch.empty(0, dtype=dtype).element_size()
+        assert off % es == 0
+        return self.ws[off: off + count * es].view(dtype)
+
+    def block_info(self, b: int):
+        m, ld, moff, roff = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        N.check("rfm_block_info", self.lib.rfm_block_info(self._probs, self.n, C.byref(self._cfg), int(b),
+                                                          C.byref(m), C.byref(ld), C.byref(moff), C.byref(roff)))
+        return m.value, ld.value, moff.value, roff.value
+
+    def _K_of_block(self, b: int) -> int:
+        for p in self.problems:
+            if b < p.J:
+                return p.K
+            b -= p.J
+        raise IndexError(b)
+
+    def block_matrix(self, b: int, which: int = 0) -> torch.Tensor:
+        """Block b of an (ldm x K) arena (0 = M, 3 = QR work, 5 = operator), as an m x K view."""
+        m, ld, moff, roff = self.block_info(b)
+        K = self._K_of_block(b)
+        if which == 0:
+            dt = torch.float32 if self.asm == "fp32" else torch.float64
+        elif which == 5:
+            dt = torch.float32 if self.op == "q32" else torch.float64
+        else:
+            dt = torch.float64
+        base = self._tensor_at(self.view(which) + moff * torch.empty(0, dtype=dt).element_size(), ld * K, dt)
+        return base.view(K, ld).t()[:m]
+
+    def block_rows(self, b: int) -> torch.Tensor:
+        m, ld, moff, roff = self.block_info(b)
+        return self._tensor_at(self.view(2), self.sizes["block_rows"], torch.int32)[roff: roff + m]
+
+    def rhs(self) -> torch.Tensor:
+        return self._tensor_at(self.view(1), self.sizes["n_rows"], torch.float64)
+
+    def r11(self) -> torch.Tensor:
+        return self._tensor_at(self.view(4), self.sizes["n_blocks"], torch.float64)
+
+
+def report_dict(rep: torch.Tensor, i: int = 0) -> dict:
+    r = rep.view(-1, 8)[i].tolist()
+    return {k: (int(v) if k in ("itn", "istop", "status") else v) for k, v in zip(N.REPORT_FIELDS, r)}

@@ -1,0 +1,265 @@
+// api.cu -- the extern "C" entry points declared in include/rfm.h.
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "common.cuh"
+#include "prof.cuh"
+
+namespace rfm {
+const char *last_error();
+rfm_status launch_assemble(const HostPlan &P, void *ws, const double *params, cudaStream_t st);
+rfm_status launch_filter(const HostPlan &P, void *ws, double tol, cudaStream_t st);
+rfm_status launch_lsqr(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, const double *y0, double *y_out,
+                       double *a_out, rfm_lsqr_report *rep, cudaStream_t st);
+rfm_status launch_coefficients(const HostPlan &P, void *ws, const double *y, double *a_out, cudaStream_t st);
+rfm_status launch_eval(const HostPlan &P, void *ws, const double *params, const double *a, const double *X,
+                       const int64_t *pt_off, double *u, double *err, cudaStream_t st);
+
+namespace {
+// RAII holder of a host plan for one call.
+struct Plan {
+    HostPlan p;
+    bool ok = false;
+    rfm_status rc = RFM_OK;
+    Plan(const rfm_problem *probs, int n, const rfm_config *cfg) {
+        char err[512] = {0};
+        rc = build_plan(probs, n, cfg, &p, err, sizeof(err));
+        ok = rc == RFM_OK;
+        if (!ok) set_error("%s", err);
+    }
+    ~Plan() {
+        if (ok) free_plan(&p);
+    }
+};
+
+rfm_status check_ws(const Layout &L, const void *ws, size_t bytes) {
+    if (!ws) {
+        set_error("workspace pointer is NULL");
+        return RFM_EINVAL;
+    }
+    if (((uintptr_t)ws & 255) != 0) {
+        set_error("workspace must be 256-byte aligned");
+        return RFM_EINVAL;
+    }
+    if (bytes < L.total) {
+        set_error("workspace has %zu bytes, the system needs %zu", bytes, L.total);
+        return RFM_ENOSPACE;
+    }
+    return RFM_OK;
+}
+}  // namespace
+}  // namespace rfm
+
+using namespace rfm;
+
+#define RFM_GUARD_BEGIN try {
+#define RFM_GUARD_END                                   \
+    }                                                   \
+    catch (const std::bad_alloc &) {                    \
+        set_error("host allocation failed");            \
+        return RFM_EINVAL;                              \
+    }                                                   \
+    catch (...) {                                       \
+        set_error("unexpected host exception");         \
+        return RFM_EINVAL;                              \
+    }
+
+extern "C" {
+
+int rfm_abi_version(void) { return RFM_ABI_VERSION; }
+
+const char *rfm_last_error(void) { return rfm::last_error(); }
+
+rfm_status rfm_problem_size(const rfm_problem *probs, int n_inst, const rfm_config *cfg, rfm_sizes *out) {
+    RFM_GUARD_BEGIN
+    if (!out) {
+        set_error("rfm_problem_size: out is NULL");
+        return RFM_EINVAL;
+    }
+    Plan P(probs, n_inst, cfg);
+    if (!P.ok) return P.rc;
+    const Layout &L = P.p.L;
+    out->n_inst = L.n_inst;
+    out->n_blocks = L.n_blocks;
+    out->n_rows = L.n_rows;
+    out->n_cols = L.n_cols;
+    out->block_rows = L.block_rows;
+    out->max_block_rows = L.max_m;
+    out->max_K = L.max_K;
+    out->workspace_bytes = (int64_t)L.total;
+    return RFM_OK;
+    RFM_GUARD_END
+}
+
+rfm_status rfm_assemble(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const double *d_params,
+                        void *d_ws, size_t ws_bytes, void *stream) {
+    RFM_GUARD_BEGIN
+    Plan P(probs, n_inst, cfg);
+    if (!P.ok) return P.rc;
+    const Layout &L = P.p.L;
+    rfm_status rc = check_ws(L, d_ws, ws_bytes);
+    if (rc != RFM_OK) return rc;
+    if (!d_params) {
+        set_error("rfm_assemble: d_params is NULL");
+        return RFM_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    RFM_CUDA_CHECK(cudaMemcpyAsync(ws_ptr<void>(d_ws, L.off_inst), P.p.inst, sizeof(InstRec) * L.n_inst,
+                                   cudaMemcpyHostToDevice, st));
+    if (L.n_blocks)
+        RFM_CUDA_CHECK(cudaMemcpyAsync(ws_ptr<void>(d_ws, L.off_blk), P.p.blk, sizeof(BlkRec) * L.n_blocks,
+                                       cudaMemcpyHostToDevice, st));
+    if (L.n_tiles) {
+        RFM_CUDA_CHECK(cudaMemcpyAsync(ws_ptr<void>(d_ws, L.off_tile), P.p.tile_blk, sizeof(int32_t) * L.n_tiles,
+                                       cudaMemcpyHostToDevice, st));
+        RFM_CUDA_CHECK(cudaMemcpyAsync(ws_ptr<int32_t>(d_ws, L.off_tile) + L.n_tiles, P.p.tile_row,
+                                       sizeof(int32_t) * L.n_tiles, cudaMemcpyHostToDevice, st));
+    }
+    if (L.n_cov)
+        RFM_CUDA_CHECK(cudaMemcpyAsync(ws_ptr<void>(d_ws, L.off_cov), P.p.cov, sizeof(int32_t) * L.n_cov,
+                                       cudaMemcpyHostToDevice, st));
+    return launch_assemble(P.p, d_ws, d_params, st);
+    RFM_GUARD_END
+}
+
+rfm_status rfm_rrqr_filter(const rfm_problem *probs, int n_inst, const rfm_config *cfg, void *d_ws, size_t ws_bytes,
+                           int32_t *d_rank, int32_t *d_perm, void *stream) {
+    RFM_GUARD_BEGIN
+    Plan P(probs, n_inst, cfg);
+    if (!P.ok) return P.rc;
+    const Layout &L = P.p.L;
+    rfm_status rc = check_ws(L, d_ws, ws_bytes);
+    if (rc != RFM_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (L.op != RFM_OP_PLAIN) {
+        rc = launch_filter(P.p, d_ws, cfg->tol, st);
+        if (rc != RFM_OK) return rc;
+    }
+    if (d_rank && L.n_blocks) {
+        if (L.op == RFM_OP_PLAIN) {
+            set_error("rfm_rrqr_filter: no ranks with RFM_OP_PLAIN");
+            return RFM_EINVAL;
+        }
+        RFM_CUDA_CHECK(cudaMemcpyAsync(d_rank, ws_ptr<void>(d_ws, L.off_rank), sizeof(int32_t) * L.n_blocks,
+                                       cudaMemcpyDeviceToDevice, st));
+    }
+    if (d_perm && L.n_cols && L.op != RFM_OP_PLAIN)
+        RFM_CUDA_CHECK(cudaMemcpyAsync(d_perm, ws_ptr<void>(d_ws, L.off_perm), sizeof(int32_t) * L.n_cols,
+                                       cudaMemcpyDeviceToDevice, st));
+    return RFM_OK;
+    RFM_GUARD_END
+}
+
+rfm_status rfm_lsqr_solve(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const rfm_lsqr_opts *opts,
+                          const double *d_y0, double *d_y, double *d_a, rfm_lsqr_report *d_report, void *d_ws,
+                          size_t ws_bytes, void *stream) {
+    RFM_GUARD_BEGIN
+    Plan P(probs, n_inst, cfg);
+    if (!P.ok) return P.rc;
+    const Layout &L = P.p.L;
+    rfm_status rc = check_ws(L, d_ws, ws_bytes);
+    if (rc != RFM_OK) return rc;
+    if (!opts || !d_a || opts->max_iter < 0 || !(opts->atol >= 0.0) || !(opts->btol >= 0.0)) {
+        set_error("rfm_lsqr_solve: need opts (max_iter >= 0, atol, btol >= 0) and d_a");
+        return RFM_EINVAL;
+    }
+    return launch_lsqr(P.p, d_ws, opts, d_y0, d_y, d_a, d_report, (cudaStream_t)stream);
+    RFM_GUARD_END
+}
+
+rfm_status rfm_coefficients(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const double *d_y,
+                            double *d_a, void *d_ws, size_t ws_bytes, void *stream) {
+    RFM_GUARD_BEGIN
+    Plan P(probs, n_inst, cfg);
+    if (!P.ok) return P.rc;
+    rfm_status rc = check_ws(P.p.L, d_ws, ws_bytes);
+    if (rc != RFM_OK) return rc;
+    if (!d_y || !d_a) {
+        set_error("rfm_coefficients: null argument");
+        return RFM_EINVAL;
+    }
+    return launch_coefficients(P.p, d_ws, d_y, d_a, (cudaStream_t)stream);
+    RFM_GUARD_END
+}
+
+rfm_status rfm_profile_enable(int on) {
+    prof_enable(on != 0);
+    return RFM_OK;
+}
+
+rfm_status rfm_profile_reset(void) {
+    prof_reset();
+    return RFM_OK;
+}
+
+int rfm_profile_read(const char **names, int64_t *launches, double *ms, int max) {
+    try {
+        return prof_read(names, launches, ms, max);
+    } catch (...) {
+        return -1;
+    }
+}
+
+rfm_status rfm_eval(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const double *d_params,
+                    const double *d_a, const double *d_x, const int64_t *h_pt_off, double *d_u, double *d_err,
+                    void *d_ws, size_t ws_bytes, void *stream) {
+    RFM_GUARD_BEGIN
+    Plan P(probs, n_inst, cfg);
+    if (!P.ok) return P.rc;
+    const Layout &L = P.p.L;
+    rfm_status rc = check_ws(L, d_ws, ws_bytes);
+    if (rc != RFM_OK) return rc;
+    if (!d_params || !d_a || !d_x || !h_pt_off || !d_u) {
+        set_error("rfm_eval: null argument");
+        return RFM_EINVAL;
+    }
+    return launch_eval(P.p, d_ws, d_params, d_a, d_x, h_pt_off, d_u, d_err, (cudaStream_t)stream);
+    RFM_GUARD_END
+}
+
+rfm_status rfm_block_info(const rfm_problem *probs, int n_inst, const rfm_config *cfg, int64_t block, int64_t *m,
+                          int64_t *ld, int64_t *moff, int64_t *roff) {
+    RFM_GUARD_BEGIN
+    Plan P(probs, n_inst, cfg);
+    if (!P.ok) return P.rc;
+    if (block < 0 || block >= P.p.L.n_blocks) {
+        set_error("rfm_block_info: block %lld out of range", (long long)block);
+        return RFM_EINVAL;
+    }
+    const BlkRec &B = P.p.blk[block];
+    if (m) *m = B.m;
+    if (ld) *ld = B.ldm;
+    if (moff) *moff = B.moff;
+    if (roff) *roff = B.roff;
+    return RFM_OK;
+    RFM_GUARD_END
+}
+
+rfm_status rfm_workspace_view(const rfm_problem *probs, int n_inst, const rfm_config *cfg, void *d_ws, int which,
+                              void **ptr) {
+    RFM_GUARD_BEGIN
+    Plan P(probs, n_inst, cfg);
+    if (!P.ok) return P.rc;
+    const Layout &L = P.p.L;
+    size_t off;
+    switch (which) {
+        case 0: off = L.off_M; break;
+        case 1: off = L.off_h; break;
+        case 2: off = L.off_grow; break;
+        case 3: off = L.off_W; break;
+        case 4: off = L.off_r11; break;
+        case 5: off = L.op == RFM_OP_Q32 ? L.off_q32 : L.off_op; break;
+        default: set_error("rfm_workspace_view: unknown view %d", which); return RFM_EINVAL;
+    }
+    if (!ptr) {
+        set_error("rfm_workspace_view: ptr is NULL");
+        return RFM_EINVAL;
+    }
+    *ptr = ws_ptr<void>(d_ws, off);
+    return RFM_OK;
+    RFM_GUARD_END
+}
+
+}  // extern "C"

@@ -1,0 +1,127 @@
+// eval.cu -- the ansatz of Eq. (1) at query points and the error sums of
+// Sec. 4.2 (relative L2 and the normalised L1 error e_L1).
+//
+// One warp per point: the covering subdomains along each dimension are found
+// from the box test around the nearest centre; for every covering subdomain
+// the lanes split the K features (sum_k a_jk tanh(...)), the sum is weighted
+// by the normalised window (product of 1D factors) and reduced in the warp.
+// Error sums are reduced per CTA in a fixed order, then per instance.
+#include "device.cuh"
+#include "prof.cuh"
+
+namespace rfm {
+
+constexpr int kEvalCtas = 1024;
+
+__global__ void __launch_bounds__(256) k_eval(const InstRec *__restrict__ insts, int s, const double *__restrict__ params,
+                                              const double *__restrict__ a, const double *__restrict__ X, int64_t npts,
+                                              double *__restrict__ u_out, double *__restrict__ part) {
+    const InstRec &I = insts[s];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ double red[8][4];
+    double e2 = 0.0, u2 = 0.0, e1 = 0.0, u1 = 0.0;
+    const int d = I.dim;
+    for (int64_t p = (int64_t)blockIdx.x * 8 + warp; p < npts; p += (int64_t)gridDim.x * 8) {
+        double x[3] = {X[3 * p], X[3 * p + 1], X[3 * p + 2]};
+        int jlo[3] = {0, 0, 0}, jn[3] = {1, 1, 1};
+        for (int i = 0; i < d; ++i) {
+            const double sp = (I.hi[i] - I.lo[i]) / (double)(I.S[i] - 1);
+            int c = (int)floor((x[i] - I.lo[i]) / sp + 0.5);
+            const int H = (int)ceil(I.delta) + 1;
+            int a0 = c - H < 0 ? 0 : c - H, a1 = c + H > I.S[i] - 1 ? I.S[i] - 1 : c + H;
+            int first = -1, cnt = 0;
+            for (int l = a0; l <= a1; ++l) {
+                double mu, sig;
+                sub_geom(I.lo[i], I.hi[i], I.S[i], I.delta, l, &mu, &sig);
+                if (fabs(x[i] - mu) < sig) {
+                    if (first < 0) first = l;
+                    ++cnt;
+                }
+            }
+            jlo[i] = first < 0 ? 0 : first;
+            jn[i] = cnt;
+        }
+        double uh = 0.0;
+        const int ncomb = jn[0] * jn[1] * jn[2];
+        for (int cmb = 0; cmb < ncomb; ++cmb) {
+            int jd[3], q = cmb;
+            int64_t j = 0, stride = 1;
+            for (int i = 0; i < 3; ++i) {
+                jd[i] = jlo[i] + q % jn[i];
+                q /= jn[i];
+                if (i < d) {
+                    j += jd[i] * stride;
+                    stride *= I.S[i];
+                }
+            }
+            double mu[3] = {0, 0, 0}, sig[3] = {1, 1, 1};
+            for (int i = 0; i < d; ++i) sub_geom(I.lo[i], I.hi[i], I.S[i], I.delta, jd[i], &mu[i], &sig[i]);
+            const double *prm = params + I.prm_off + j * I.K * (d + 1);
+            const double *aj = a + I.col0 + j * I.K;
+            double sj = 0.0;
+            for (int k = lane; k < I.K; k += 32) {
+                const double *pk = prm + (int64_t)k * (d + 1);
+                double z = pk[d];
+                for (int i = 0; i < d; ++i) z += pk[i] * ((x[i] - mu[i]) / sig[i]);
+                sj = fma(aj[k], tanh(z), sj);
+            }
+            for (int o = 16; o; o >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o);
+            double w, dw[3], d2w[3];
+            window_nd(I, jd, x, &w, dw, d2w);
+            uh = fma(w, sj, uh);
+        }
+        if (lane == 0) {
+            u_out[p] = uh;
+            const double ue = fam_exact(I, x);
+            const double df = uh - ue;
+            e2 += df * df;
+            u2 += ue * ue;
+            e1 += fabs(df);
+            u1 += ue;
+        }
+    }
+    if (lane == 0) {
+        red[warp][0] = e2; red[warp][1] = u2; red[warp][2] = e1; red[warp][3] = u1;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[w][threadIdx.x];
+        part[((int64_t)s * kEvalCtas + blockIdx.x) * 4 + threadIdx.x] = t;
+    }
+}
+
+__global__ void k_eval_finish(const double *__restrict__ part, int s, int nctas, double *__restrict__ err) {
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int c = 0; c < nctas; ++c) t += part[((int64_t)s * kEvalCtas + c) * 4 + threadIdx.x];
+        err[4 * s + threadIdx.x] = t;
+    }
+}
+
+rfm_status launch_eval(const HostPlan &P, void *ws, const double *params, const double *a, const double *X,
+                       const int64_t *pt_off, double *u, double *err, cudaStream_t st) {
+    const Layout &L = P.L;
+    const InstRec *dI = ws_ptr<InstRec>(ws, L.off_inst);
+    double *part = ws_ptr<double>(ws, L.off_evpart);
+    for (int s = 0; s < L.n_inst; ++s) {
+        const int64_t n = pt_off[s + 1] - pt_off[s];
+        if (n < 0) {
+            set_error("rfm_eval: point offsets must be non-decreasing");
+            return RFM_EINVAL;
+        }
+        int g = (int)((n + 7) / 8);
+        g = g < 1 ? 1 : (g > kEvalCtas ? kEvalCtas : g);
+        { ProfScope ps("k_eval", st);
+        k_eval<<<g, 256, 0, st>>>(dI, s, params, a, X + 3 * pt_off[s], n, u + pt_off[s], part); }
+        RFM_CUDA_CHECK(cudaGetLastError());
+        if (err) {
+            ProfScope ps("k_eval_finish", st);
+            k_eval_finish<<<1, 32, 0, st>>>(part, s, g, err);
+            RFM_CUDA_CHECK(cudaGetLastError());
+        }
+    }
+    return RFM_OK;
+}
+
+}  // namespace rfm

@@ -1,0 +1,667 @@
+// lsqr.cu -- LSQR (Paige and Saunders 1982) on the filtered, right-
+// preconditioned system of Algorithm 2, for every instance of a system at
+// once, in one persistent cooperative launch.
+//
+// Operator of block b (rows I_b, kept columns r_b):
+//   AR64:  Op_b = Ahat_b R_b^-1 (FP64 kept columns, FP64 substitution; Sec. 3.2)
+//   Q32 / Q64: Op_b = Q_hat_b (Proposition 3.1), FP32 or FP64 storage
+//   PLAIN: Op_b = M_b, all K columns (no filtering, no preconditioner)
+// Forward products y = sum_b V_b^T Op_b x_b are formed per block into
+// block-row partials t, then summed per global row over the fixed row list.
+//
+// One iteration = three phases separated by grid barriers:
+//   F (blocks): finish the previous iteration's column updates of the block's
+//      slots (v = vt/alpha; y += phi/rho w; w = v - theta/rho w) and form
+//      t = Op_b v_b;
+//   R (rows):   u~ = sum t - alpha u (u = u~/beta kept unnormalised), ||u~||^2;
+//   T (blocks): vt = Op_b^T (u~/beta_new) - beta_new v, ||vt||^2.
+// The reductions are per-CTA partials in a fixed order, summed by every CTA in
+// the same fixed order after the barrier, so every CTA holds bit-identical
+// scalars and takes the same stopping decision.  Every barrier wait is bounded
+// (globaltimer); on expiry the kernel records RFM_ETIMEOUT and all CTAs leave
+// at their next barrier.
+#include <cooperative_groups.h>
+
+#include "device.cuh"
+#include "prof.cuh"
+
+namespace rfm {
+
+struct LsqrArgs {
+    const InstRec *insts;
+    const BlkRec *blks;
+    int n_blocks, n_inst;
+    const void *A;           // operator arena (TA)
+    const double *W;         // R_hat (AR64)
+    const int32_t *rank;     // kept columns per block (nullptr: all K)
+    const int32_t *grow, *rowlist;
+    const double *h, *y0;
+    double *u, *v, *vt, *w, *y, *t, *part;
+    LsqrScal *scal;
+    unsigned *bar;           // [0] arrivals, [1] generation, [2] error
+    double atol, btol;
+    int max_iter;
+    uint64_t timeout_ns;
+    int64_t n_row_tiles;
+    double *snap;            // iterate snapshots (nullable)
+    int snap_every, snap_cap;
+    int64_t n_cols;
+};
+
+constexpr int kThreads = 256;
+constexpr int kRowTile = 256;
+constexpr int kRowChunk = 2048;
+
+// Bounded grid barrier.  Returns false when any CTA has reported an error.
+__device__ bool grid_sync(unsigned *bar, uint64_t timeout_ns) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = bar + 1;
+        volatile unsigned *verr = bar + 2;
+        unsigned g = *vgen;
+        __threadfence();
+        unsigned arrived = atomicAdd(bar, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            uint64_t t0 = global_ns();
+            unsigned spins = 0;
+            while (*vgen == g) {
+                if (*verr) break;
+                __nanosleep(64);
+                if ((++spins & 255u) == 0 && global_ns() - t0 > timeout_ns) {
+                    atomicCAS(bar + 2, 0u, (unsigned)RFM_ETIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    volatile unsigned *verr = bar + 2;
+    return *verr == 0;
+}
+
+// Sum of one double over the CTA in a fixed order (result valid in thread 0).
+__device__ double cta_sum(double x, double *scratch) {
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) scratch[warp] = x;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kThreads / 32; ++w) s += scratch[w];
+    return s;
+}
+
+// Back substitution R x = x (R upper r x r, column-major ld, FP64), x in
+// shared memory; 32-wide diagonal tiles solved by warp 0 with the tile in
+// registers, off-diagonal updates by the whole CTA.
+__device__ void tri_solve_upper(const double *__restrict__ R, int ld, int r, double *x) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int nt = (r + 31) / 32;
+    for (int T = nt - 1; T >= 0; --T) {
+        const int c0 = T * 32, nc = min(32, r - c0);
+        if (tid < 32) {
+            double row[32];
+            const int i = c0 + lane;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) row[j] = (lane < nc && j < nc) ? R[(int64_t)(c0 + j) * ld + i] : 0.0;
+            double xi = lane < nc ? x[i] : 0.0;
+#pragma unroll
+            for (int j = 31; j >= 0; --j) {
+                if (j < nc) {
+                    if (lane == j) xi = xi / row[j];
+                    double xj = __shfl_sync(0xffffffffu, xi, j);
+                    if (lane < j) xi = fma(-row[j], xj, xi);
+                }
+            }
+            if (lane < nc) x[i] = xi;
+        }
+        __syncthreads();
+        for (int i = tid; i < c0; i += kThreads) {
+            double s = x[i];
+            for (int j = 0; j < nc; ++j) s = fma(-R[(int64_t)(c0 + j) * ld + i], x[c0 + j], s);
+            x[i] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// Forward substitution R^T x = x.
+__device__ void tri_solve_upper_t(const double *__restrict__ R, int ld, int r, double *x) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int nt = (r + 31) / 32;
+    for (int T = 0; T < nt; ++T) {
+        const int c0 = T * 32, nc = min(32, r - c0);
+        if (tid < 32) {
+            double col[32];
+            const int i = c0 + lane;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) col[j] = (lane < nc && j < nc) ? R[(int64_t)i * ld + c0 + j] : 0.0;
+            double xi = lane < nc ? x[i] : 0.0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j < nc) {
+                    if (lane == j) xi = xi / col[j];
+                    double xj = __shfl_sync(0xffffffffu, xi, j);
+                    if (lane > j) xi = fma(-col[j], xj, xi);
+                }
+            }
+            if (lane < nc) x[i] = xi;
+        }
+        __syncthreads();
+        for (int i = c0 + nc + tid; i < r; i += kThreads) {
+            double s = x[i];
+            const double *Rc = R + (int64_t)i * ld + c0;
+            for (int j = 0; j < nc; ++j) s = fma(-Rc[j], x[c0 + j], s);
+            x[i] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// Per-instance sums of the partial array part[s * G + cta] (same order in
+// every CTA).  Warp w reduces instances w, w+8, ...
+__device__ void reduce_partials(const double *part, int n_inst, double *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, G = gridDim.x;
+    for (int s = warp; s < n_inst; s += kThreads / 32) {
+        double x = 0.0;
+        for (int c = lane; c < G; c += 32) x += part[(int64_t)s * G + c];
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) out[s] = x;
+    }
+    __syncthreads();
+}
+
+template <typename TA>
+struct Smem {
+    double x[kMaxK];           // block column vector (v, p or z)
+    TA xa[kMaxK];              // the same in operator precision
+    TA ub[kRowChunk];          // gathered u~ / beta of a row chunk
+    double acc[kMaxInst];      // this CTA's per-instance partial sums
+    double red[kThreads / 32];
+    double tmp[kMaxInst];
+    LsqrScal sc[kMaxInst > 64 ? 64 : kMaxInst];
+};
+
+template <typename TA, bool TRI>
+__global__ void __launch_bounds__(kThreads) k_lsqr(LsqrArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<TA> &S = *reinterpret_cast<Smem<TA> *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, G = gridDim.x, cta = blockIdx.x;
+    const int ni = a.n_inst;
+    const TA *Aop = reinterpret_cast<const TA *>(a.A);
+    LsqrScal *sc = S.sc;  // local copy of the scalars (identical in every CTA)
+    bool ok = true;
+
+    auto blk_rank = [&](int b) { return a.rank ? a.rank[b] : a.blks[b].K; };
+    auto clear_acc = [&]() {
+        for (int s = tid; s < ni; s += kThreads) S.acc[s] = 0.0;
+        __syncthreads();
+    };
+    auto flush_acc = [&](int which) {
+        __syncthreads();
+        for (int s = tid; s < ni; s += kThreads) a.part[((int64_t)which * ni + s) * G + cta] = S.acc[s];
+    };
+
+    // forward product t_b = Op_b x_b for the block (x already in S.x / S.xa)
+    auto block_forward = [&](const BlkRec &B, int r) {
+        const TA *Ab = Aop + B.moff;
+        for (int i = tid; i < B.m; i += kThreads) {
+            TA s = (TA)0;
+            int c = 0;
+            for (; c + 4 <= r; c += 4) {
+                s += Ab[(int64_t)c * B.ldm + i] * S.xa[c];
+                s += Ab[(int64_t)(c + 1) * B.ldm + i] * S.xa[c + 1];
+                s += Ab[(int64_t)(c + 2) * B.ldm + i] * S.xa[c + 2];
+                s += Ab[(int64_t)(c + 3) * B.ldm + i] * S.xa[c + 3];
+            }
+            for (; c < r; ++c) s += Ab[(int64_t)c * B.ldm + i] * S.xa[c];
+            a.t[B.roff + i] = (double)s;
+        }
+    };
+    // transpose product S.x[c] = sum_i Op_b[i, c] * u~[grow[i]] * inv_beta
+    auto block_transpose = [&](const BlkRec &B, int r, double inv_beta) {
+        const TA *Ab = Aop + B.moff;
+        for (int c = tid; c < r; c += kThreads) S.x[c] = 0.0;
+        for (int i0 = 0; i0 < B.m; i0 += kRowChunk) {
+            const int n = min(kRowChunk, B.m - i0);
+            __syncthreads();
+            for (int i = tid; i < n; i += kThreads) S.ub[i] = (TA)(a.u[a.grow[B.roff + i0 + i]] * inv_beta);
+            __syncthreads();
+            for (int c = warp; c < r; c += kThreads / 32) {
+                const TA *col = Ab + (int64_t)c * B.ldm + i0;
+                TA s = (TA)0;
+                for (int i = lane; i < n; i += 32) s += col[i] * S.ub[i];
+                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) S.x[c] += (double)s;
+            }
+        }
+        __syncthreads();
+    };
+    auto stage_x = [&](int r) {
+        for (int c = tid; c < r; c += kThreads) S.xa[c] = (TA)S.x[c];
+        __syncthreads();
+    };
+
+    // ------------------------------------------------------------ init
+    for (int s = tid; s < ni && s < 64; s += kThreads) {
+        LsqrScal z;
+        memset(&z, 0, sizeof(z));
+        sc[s] = z;
+    }
+    __syncthreads();
+    // I1: t = Op P y0 (when warm-starting); y = y0 or 0
+    for (int b = cta; b < a.n_blocks; b += G) {
+        const BlkRec &B = a.blks[b];
+        const int r = blk_rank(b), K = B.K;
+        for (int c = tid; c < K; c += kThreads) {
+            double yv = (a.y0 && c < r) ? a.y0[B.coff + c] : 0.0;
+            a.y[B.coff + c] = yv;
+            a.w[B.coff + c] = 0.0;
+            a.v[B.coff + c] = 0.0;
+            if (c < r) S.x[c] = yv;
+        }
+        __syncthreads();
+        if (a.y0) {
+            if (TRI) tri_solve_upper(a.W + B.moff, B.ldm, r, S.x);
+            stage_x(r);
+            block_forward(B, r);
+        }
+        __syncthreads();
+    }
+    ok = grid_sync(a.bar, a.timeout_ns);
+    // I2: u~ = h - t-sums, partials of ||u~||^2 (slot 0) and ||h||^2 (slot 1)
+    clear_acc();
+    __shared__ double hacc[kMaxInst];
+    for (int s = tid; s < ni; s += kThreads) hacc[s] = 0.0;
+    __syncthreads();
+    for (int64_t T = cta; T < a.n_row_tiles; T += G) {
+        // map tile to instance
+        int s = 0;
+        int64_t tcount = 0;
+        for (; s < ni; ++s) {
+            int64_t nt = (a.insts[s].N + kRowTile - 1) / kRowTile;
+            if (T < tcount + nt) break;
+            tcount += nt;
+        }
+        const InstRec &I = a.insts[s];
+        const int64_t r = (T - tcount) * kRowTile + tid;
+        double uu = 0.0, hh = 0.0;
+        if (r < I.N) {
+            const int64_t gr = I.row0 + r;
+            double acc = 0.0;
+            if (a.y0) {
+                const int32_t *lst = a.rowlist + I.rl_off + r * I.C;
+                for (int e = 0; e < I.C; ++e) {
+                    int q = lst[e];
+                    if (q >= 0) acc += a.t[q];
+                }
+            }
+            double hv = a.h[gr];
+            double uv = hv - acc;
+            a.u[gr] = uv;
+            uu = uv * uv;
+            hh = hv * hv;
+        }
+        double s1 = cta_sum(uu, S.red);
+        double s2 = cta_sum(hh, S.red);
+        if (tid == 0) { S.acc[s] += s1; hacc[s] += s2; }
+    }
+    flush_acc(0);
+    for (int s = tid; s < ni; s += kThreads) a.part[((int64_t)1 * ni + s) * G + cta] = hacc[s];
+    ok = ok && grid_sync(a.bar, a.timeout_ns);
+    if (!ok) return;
+    reduce_partials(a.part, ni, S.tmp);
+    for (int s = tid; s < ni; s += kThreads) sc[s].beta = sqrt(S.tmp[s]);
+    reduce_partials(a.part + (int64_t)ni * G, ni, S.tmp);
+    for (int s = tid; s < ni; s += kThreads) sc[s].bnorm = sqrt(S.tmp[s]);
+    __syncthreads();
+    // I3: vt = Op^T (u~/beta), ||vt||^2
+    clear_acc();
+    for (int b = cta; b < a.n_blocks; b += G) {
+        const BlkRec &B = a.blks[b];
+        const int r = blk_rank(b);
+        const double beta = sc[B.inst].beta;
+        block_transpose(B, r, beta > 0.0 ? 1.0 / beta : 0.0);
+        if (TRI) tri_solve_upper_t(a.W + B.moff, B.ldm, r, S.x);
+        double part = 0.0;
+        for (int c = tid; c < r; c += kThreads) {
+            a.vt[B.coff + c] = S.x[c];
+            part += S.x[c] * S.x[c];
+        }
+        double sum = cta_sum(part, S.red);
+        if (tid == 0) S.acc[B.inst] += sum;
+        __syncthreads();
+    }
+    flush_acc(2);
+    ok = grid_sync(a.bar, a.timeout_ns);
+    if (!ok) return;
+    reduce_partials(a.part + (int64_t)2 * ni * G, ni, S.tmp);
+    for (int s = tid; s < ni; s += kThreads) {
+        LsqrScal &q = sc[s];
+        q.alpha = sqrt(S.tmp[s]);
+        q.phibar = q.beta;
+        q.rhobar = q.alpha;
+        q.rnorm = q.beta;
+        q.arnorm = q.alpha * q.beta;
+        q.istop = 7;
+        q.itn = 0;
+        q.done = (q.beta == 0.0 || q.alpha == 0.0) ? 1 : 0;
+        if (q.done) q.istop = 0;
+        q.status = 0;
+    }
+    __syncthreads();
+
+    // ------------------------------------------------------------ loop
+    bool first = true;
+    for (;;) {
+        // F: column updates of the previous iteration, then t = Op v
+        clear_acc();
+        for (int b = cta; b < a.n_blocks; b += G) {
+            const BlkRec &B = a.blks[b];
+            const LsqrScal &q = sc[B.inst];
+            const int r = blk_rank(b);
+            double ypart = 0.0;
+            if (!q.done || first) {
+                const double ia = q.alpha > 0.0 ? 1.0 / q.alpha : 0.0;
+                for (int c = tid; c < r; c += kThreads) {
+                    const int64_t o = B.coff + c;
+                    const double vn = a.vt[o] * ia;
+                    double wv, yv = a.y[o];
+                    if (first) {
+                        wv = vn;
+                    } else {
+                        yv = fma(q.phi_rho, a.w[o], yv);
+                        wv = fma(-q.theta_rho, a.w[o], vn);
+                        a.y[o] = yv;
+                        if (a.snap && q.itn % a.snap_every == 0 && q.itn / a.snap_every <= a.snap_cap)
+                            a.snap[(int64_t)(q.itn / a.snap_every - 1) * a.n_cols + o] = yv;
+                    }
+                    a.w[o] = wv;
+                    a.v[o] = vn;
+                    S.x[c] = vn;
+                    ypart += yv * yv;
+                }
+            } else {
+                for (int c = tid; c < r; c += kThreads) {
+                    double yv = a.y[B.coff + c];
+                    ypart += yv * yv;
+                }
+            }
+            double ysum = cta_sum(ypart, S.red);
+            if (tid == 0) S.acc[B.inst] += ysum;
+            __syncthreads();
+            if (!q.done) {
+                if (TRI) tri_solve_upper(a.W + B.moff, B.ldm, r, S.x);
+                stage_x(r);
+                block_forward(B, r);
+            }
+            __syncthreads();
+        }
+        flush_acc(0);
+        ok = grid_sync(a.bar, a.timeout_ns);
+        if (!ok) break;
+        // stopping test of the iteration just completed (identical in every CTA)
+        reduce_partials(a.part, ni, S.tmp);
+        __shared__ int s_all_done;
+        if (tid == 0) s_all_done = 1;
+        __syncthreads();
+        for (int s = tid; s < ni; s += kThreads) {
+            LsqrScal &q = sc[s];
+            if (q.done) continue;
+            q.ynorm = sqrt(S.tmp[s]);
+            if (!first) {
+                if (q.rnorm <= a.btol * q.bnorm + a.atol * sqrt(q.anorm2) * q.ynorm) { q.done = 1; q.istop = 1; }
+                else if (q.arnorm <= a.atol * sqrt(q.anorm2) * q.rnorm) { q.done = 1; q.istop = 2; }
+            }
+            if (!q.done && q.itn >= a.max_iter) { q.done = 1; q.istop = 7; }
+            if (!q.done) { q.itn += 1; atomicAnd(&s_all_done, 0); }
+        }
+        __syncthreads();
+        first = false;
+        if (s_all_done) break;
+        // R: u~ = sum t - alpha u~/beta
+        clear_acc();
+        for (int64_t T = cta; T < a.n_row_tiles; T += G) {
+            int s = 0;
+            int64_t tcount = 0;
+            for (; s < ni; ++s) {
+                int64_t nt = (a.insts[s].N + kRowTile - 1) / kRowTile;
+                if (T < tcount + nt) break;
+                tcount += nt;
+            }
+            const LsqrScal &q = sc[s];
+            if (q.done) continue;
+            const InstRec &I = a.insts[s];
+            const int64_t r = (T - tcount) * kRowTile + tid;
+            double uu = 0.0;
+            if (r < I.N) {
+                const int64_t gr = I.row0 + r;
+                const int32_t *lst = a.rowlist + I.rl_off + r * I.C;
+                double acc = 0.0;
+                for (int e = 0; e < I.C; ++e) {
+                    int qq = lst[e];
+                    if (qq >= 0) acc += a.t[qq];
+                }
+                const double ab = q.beta > 0.0 ? q.alpha / q.beta : 0.0;
+                double uv = fma(-ab, a.u[gr], acc);
+                a.u[gr] = uv;
+                uu = uv * uv;
+            }
+            double s1 = cta_sum(uu, S.red);
+            if (tid == 0) S.acc[s] += s1;
+        }
+        flush_acc(1);
+        ok = grid_sync(a.bar, a.timeout_ns);
+        if (!ok) break;
+        reduce_partials(a.part + (int64_t)ni * G, ni, S.tmp);
+        // T: vt = Op^T (u~/beta_new) - beta_new v
+        clear_acc();
+        for (int b = cta; b < a.n_blocks; b += G) {
+            const BlkRec &B = a.blks[b];
+            const LsqrScal &q = sc[B.inst];
+            if (q.done) continue;
+            const int r = blk_rank(b);
+            const double bn = sqrt(S.tmp[B.inst]);
+            block_transpose(B, r, bn > 0.0 ? 1.0 / bn : 0.0);
+            if (TRI) tri_solve_upper_t(a.W + B.moff, B.ldm, r, S.x);
+            double part = 0.0;
+            for (int c = tid; c < r; c += kThreads) {
+                const int64_t o = B.coff + c;
+                double x = fma(-bn, a.v[o], S.x[c]);
+                a.vt[o] = x;
+                part += x * x;
+            }
+            double sum = cta_sum(part, S.red);
+            if (tid == 0) S.acc[B.inst] += sum;
+            __syncthreads();
+        }
+        flush_acc(2);
+        ok = grid_sync(a.bar, a.timeout_ns);
+        if (!ok) break;
+        // plane rotation and estimates (identical in every CTA)
+        double *bsum = S.tmp;   // still holds ||u~||^2 per instance
+        __shared__ double s_alpha[kMaxInst];
+        reduce_partials(a.part + (int64_t)2 * ni * G, ni, s_alpha);
+        for (int s = tid; s < ni; s += kThreads) {
+            LsqrScal &q = sc[s];
+            if (q.done) continue;
+            const double beta = sqrt(bsum[s]);
+            const double alpha = sqrt(s_alpha[s]);
+            q.anorm2 += q.alpha * q.alpha + beta * beta;
+            const double rho = sqrt(q.rhobar * q.rhobar + beta * beta);
+            const double c = rho > 0.0 ? q.rhobar / rho : 1.0;
+            const double sn = rho > 0.0 ? beta / rho : 0.0;
+            const double theta = sn * alpha;
+            q.rhobar = -c * alpha;
+            const double phi = c * q.phibar;
+            q.phibar = sn * q.phibar;
+            q.phi_rho = rho > 0.0 ? phi / rho : 0.0;
+            q.theta_rho = rho > 0.0 ? theta / rho : 0.0;
+            q.rnorm = q.phibar;
+            q.arnorm = q.phibar * alpha * fabs(c);
+            q.c = c;
+            q.alpha = alpha;
+            q.beta = beta;
+            if (!isfinite(q.phibar) || !isfinite(q.rhobar) || !isfinite(q.phi_rho) || !isfinite(q.anorm2)) {
+                q.done = 1;
+                q.status = RFM_ENUMERIC;
+            }
+        }
+        __syncthreads();
+    }
+    if (cta == 0) {
+        for (int s = tid; s < ni; s += kThreads) {
+            const LsqrScal &q = sc[s];
+            LsqrScal &o = a.scal[s];
+            o = q;
+            o.anorm2 = q.anorm2;
+        }
+    }
+}
+
+// a = S^-1 y scattered to the J*K layout with zeros at dropped columns.
+__global__ void __launch_bounds__(kThreads) k_coefficients(const BlkRec *__restrict__ blks, const double *__restrict__ W,
+                                                           const int32_t *__restrict__ rank,
+                                                           const int32_t *__restrict__ perm,
+                                                           const double *__restrict__ y, double *__restrict__ out,
+                                                           int tri) {
+    __shared__ double x[kMaxK];
+    const BlkRec &B = blks[blockIdx.x];
+    const int r = rank ? rank[blockIdx.x] : B.K;
+    for (int c = threadIdx.x; c < B.K; c += kThreads) {
+        out[B.coff + c] = 0.0;
+        if (c < r) x[c] = y[B.coff + c];
+    }
+    __syncthreads();
+    if (tri) tri_solve_upper(W + B.moff, B.ldm, r, x);
+    for (int c = threadIdx.x; c < r; c += kThreads) {
+        const int col = perm ? perm[B.coff + c] : c;
+        out[B.coff + col] = x[c];
+    }
+}
+
+__global__ void k_report(const LsqrScal *__restrict__ sc, int n, rfm_lsqr_report *__restrict__ rep, const unsigned *bar) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const LsqrScal &q = sc[s];
+    rep[s].itn = q.itn;
+    rep[s].istop = q.istop;
+    rep[s].rnorm = q.rnorm;
+    rep[s].arnorm = q.arnorm;
+    rep[s].anorm = sqrt(q.anorm2);
+    rep[s].ynorm = q.ynorm;
+    rep[s].bnorm = q.bnorm;
+    rep[s].status = bar[2] ? (double)bar[2] : (double)q.status;
+}
+
+rfm_status launch_coefficients(const HostPlan &P, void *ws, const double *y, double *a_out, cudaStream_t st) {
+    const Layout &L = P.L;
+    if (L.n_blocks == 0) return RFM_OK;
+    const bool plain = L.op == RFM_OP_PLAIN;
+    ProfScope ps("k_coefficients", st);
+    k_coefficients<<<(unsigned)L.n_blocks, kThreads, 0, st>>>(
+        ws_ptr<BlkRec>(ws, L.off_blk), ws_ptr<double>(ws, L.off_W), plain ? nullptr : ws_ptr<int32_t>(ws, L.off_rank),
+        plain ? nullptr : ws_ptr<int32_t>(ws, L.off_perm), y, a_out, plain ? 0 : 1);
+    RFM_CUDA_CHECK(cudaGetLastError());
+    return RFM_OK;
+}
+
+template <typename TA, bool TRI>
+static rfm_status run_lsqr(const HostPlan &P, void *ws, LsqrArgs &args, cudaStream_t st) {
+    int dev = 0, nsm = 0, per = 0;
+    RFM_CUDA_CHECK(cudaGetDevice(&dev));
+    RFM_CUDA_CHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const size_t sm = sizeof(Smem<TA>);
+    RFM_CUDA_CHECK(cudaFuncSetAttribute(k_lsqr<TA, TRI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    RFM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lsqr<TA, TRI>, kThreads, sm));
+    if (per < 1) {
+        set_error("LSQR kernel does not fit on an SM");
+        return RFM_ECUDA;
+    }
+    int G = nsm * per;
+    if (G > kMaxPersistCtas) G = kMaxPersistCtas;
+    void *kargs[] = {&args};
+    ProfScope ps("k_lsqr", st);
+    RFM_CUDA_CHECK(cudaLaunchCooperativeKernel((const void *)k_lsqr<TA, TRI>, dim3(G), dim3(kThreads), kargs, sm, st));
+    return RFM_OK;
+}
+
+rfm_status launch_lsqr(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, const double *y0, double *y_out,
+                       double *a_out, rfm_lsqr_report *rep, cudaStream_t st) {
+    const Layout &L = P.L;
+    if (P.L.n_inst > 64) {
+        set_error("rfm_lsqr_solve: at most 64 instances per system");
+        return RFM_EINVAL;
+    }
+    LsqrArgs A;
+    memset(&A, 0, sizeof(A));
+    A.insts = ws_ptr<InstRec>(ws, L.off_inst);
+    A.blks = ws_ptr<BlkRec>(ws, L.off_blk);
+    A.n_blocks = (int)L.n_blocks;
+    A.n_inst = L.n_inst;
+    const bool plain = L.op == RFM_OP_PLAIN;
+    A.rank = plain ? nullptr : ws_ptr<int32_t>(ws, L.off_rank);
+    A.W = ws_ptr<double>(ws, L.off_W);
+    A.grow = ws_ptr<int32_t>(ws, L.off_grow);
+    A.rowlist = ws_ptr<int32_t>(ws, L.off_rowlist);
+    A.h = ws_ptr<double>(ws, L.off_h);
+    A.y0 = y0;
+    A.u = ws_ptr<double>(ws, L.off_u);
+    A.v = ws_ptr<double>(ws, L.off_v);
+    A.vt = ws_ptr<double>(ws, L.off_vt);
+    A.w = ws_ptr<double>(ws, L.off_w);
+    A.y = ws_ptr<double>(ws, L.off_y);
+    A.t = ws_ptr<double>(ws, L.off_t);
+    A.part = ws_ptr<double>(ws, L.off_part);
+    A.scal = ws_ptr<LsqrScal>(ws, L.off_scal);
+    A.bar = ws_ptr<unsigned>(ws, L.off_bar);
+    A.atol = opts->atol;
+    A.btol = opts->btol;
+    A.max_iter = opts->max_iter;
+    A.timeout_ns = (uint64_t)(opts->timeout_ms > 0 ? opts->timeout_ms : 10000) * 1000000ull;
+    int64_t nt = 0;
+    for (int s = 0; s < L.n_inst; ++s) nt += (P.inst[s].N + kRowTile - 1) / kRowTile;
+    A.n_row_tiles = nt;
+    A.n_cols = L.n_cols;
+    if (opts->d_snap && opts->snap_every > 0 && opts->snap_cap > 0) {
+        A.snap = opts->d_snap;
+        A.snap_every = opts->snap_every;
+        A.snap_cap = opts->snap_cap;
+    }
+    RFM_CUDA_CHECK(cudaMemsetAsync(A.bar, 0, 256, st));
+    rfm_status rc;
+    if (L.op == RFM_OP_Q32) {
+        A.A = ws_ptr<float>(ws, L.off_q32);
+        rc = run_lsqr<float, false>(P, ws, A, st);
+    } else if (L.op == RFM_OP_Q64) {
+        A.A = ws_ptr<double>(ws, L.off_op);
+        rc = run_lsqr<double, false>(P, ws, A, st);
+    } else if (L.op == RFM_OP_AR64) {
+        A.A = ws_ptr<double>(ws, L.off_op);
+        rc = run_lsqr<double, true>(P, ws, A, st);
+    } else if (L.asm_prec == RFM_ASM_FP32) {
+        A.A = ws_ptr<float>(ws, L.off_M);
+        rc = run_lsqr<float, false>(P, ws, A, st);
+    } else {
+        A.A = ws_ptr<double>(ws, L.off_M);
+        rc = run_lsqr<double, false>(P, ws, A, st);
+    }
+    if (rc != RFM_OK) return rc;
+    if (y_out) RFM_CUDA_CHECK(cudaMemcpyAsync(y_out, A.y, sizeof(double) * L.n_cols, cudaMemcpyDeviceToDevice, st));
+    rc = launch_coefficients(P, ws, A.y, a_out, st);
+    if (rc != RFM_OK) return rc;
+    if (rep) {
+        ProfScope ps("k_report", st);
+        k_report<<<(L.n_inst + 63) / 64, 64, 0, st>>>(A.scal, L.n_inst, rep, A.bar);
+        RFM_CUDA_CHECK(cudaGetLastError());
+    }
+    return RFM_OK;
+}
+
+}  // namespace rfm

@@ -1,0 +1,259 @@
+"""GPU path against the CPU oracle, element by element, through the C ABI.
+
+Cases span several 32-row tiles per block with ragged tails, 1D/2D/(2+1)D,
+the paper's heavy overlap (delta = 2.9), several filter thresholds and all
+LSQR operators.  Tolerances:
+  assembly FP64 1e-12 of the block's largest entry (different but correctly
+  rounded tanh/sin/cos); FP32 assembly 3e-5 of it (FP32 arithmetic on inputs
+  of magnitude <= ~16);
+  kept sets exact (FP64);
+  LSQR y within 1e-8 relative (FP64 operators, fixed iteration count), 1e-5
+  (FP32 Q_hat, mixed precision) when the filter threshold is >= 1e-6.
+Why the threshold matters: a column of Q_hat with a small pivot R_kk is only
+determined to eps |R_11| / |R_kk| <= eps / tol by any backward-stable QR, so
+two correct FP64 implementations give operators that differ by up to
+eps / tol (2e-8 at tol = 1e-8) and iterates that differ by that times the
+Krylov amplification.  Below tol = 1e-6 the tests therefore compare the
+rotation-invariant quantities (residual estimates, the evaluated solution).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rfm():
+    from paper_2506_17626_gb300 import build
+    build.build()
+    import paper_2506_17626_gb300 as R
+    return R
+
+
+CASES = {
+    "p1d": lambda: synth.poisson1d(S=6, K=24, n=150),
+    "p2d": lambda: synth.poisson2d(S=5, K=40, n=30),
+    "heat": lambda: synth.heat3d(S=3, K=30, n=9),
+    "p2d_d29": lambda: synth.poisson2d(S=4, K=20, n=17, delta=2.9),
+}
+
+_ORACLE = {}
+
+
+def oracle_blocks(name):
+    if name not in _ORACLE:
+        p = CASES[name]()
+        prm = synth.feature_params(p)
+        _ORACLE[name] = (p, prm, oracle.assemble(p, prm))
+    return _ORACLE[name]
+
+
+def gpu_system(rfm, p, prm, asm="fp64", op="ar64", tol=1e-10):
+    S = rfm.System([p], asm=asm, op=op, tol=tol)
+    d = torch.from_numpy(np.ascontiguousarray(prm).ravel()).cuda()
+    S.assemble(d)
+    return S, d
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("asm", ["fp64", "fp32"])
+def test_assembly_matches_oracle(rfm, name, asm):
+    p, prm, B = oracle_blocks(name)
+    S, _ = gpu_system(rfm, p, prm, asm=asm)
+    torch.cuda.synchronize()
+    tol = 1e-12 if asm == "fp64" else 3e-5
+    for j in range(p.J):
+        rows = S.block_rows(j).cpu().numpy()
+        assert np.array_equal(rows, B.grow[j]), j
+        Mg = S.block_matrix(j).double().cpu().numpy()
+        Mo = B.M[j]
+        scale = np.abs(Mo).max()
+        assert np.abs(Mg - Mo).max() <= tol * scale, (j, np.abs(Mg - Mo).max() / scale)
+    h = S.rhs().cpu().numpy()
+    assert np.abs(h - B.h).max() <= 1e-13 * np.abs(B.h).max()
+
+
+def _oracle_filter(name, tol):
+    p, prm, B = oracle_blocks(name)
+    return p, prm, B, oracle.filter_blocks(B, tol)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("tol", [1e-10, 1e-6, 1e-2])
+def test_filter_kept_sets_match_oracle(rfm, name, tol):
+    p, prm, B, F = _oracle_filter(name, tol)
+    S, _ = gpu_system(rfm, p, prm, op="ar64", tol=tol)
+    rank, perm = S.filter(want_perm=True)
+    rank = rank.cpu().numpy()
+    perm = perm.cpu().numpy().reshape(p.J, p.K)
+    r11 = S.r11().cpu().numpy()
+    for j, f in enumerate(F):
+        assert rank[j] == f.rank, (j, rank[j], f.rank)
+        assert set(perm[j, : rank[j]]) == set(f.perm[: f.rank]), j
+        assert r11[j] == pytest.approx(f.r11, rel=1e-12)
+        W = S.block_matrix(j, which=3).cpu().numpy()
+        r = f.rank
+        Rg, Ro = np.triu(W[:r, :r]), f.R
+        if list(perm[j, :r]) == list(f.perm[:r]):
+            assert np.abs(Rg - Ro).max() <= 1e-10 * f.r11, j
+
+
+@pytest.mark.parametrize("name", ["p1d", "p2d", "heat"])
+def test_explicit_q_matches_oracle(rfm, name):
+    p, prm, B, F = _oracle_filter(name, 1e-8)
+    eps = np.finfo(float).eps
+    for op, base in [("q64", 0.0), ("q32", 2e-7)]:
+        S, _ = gpu_system(rfm, p, prm, op=op, tol=1e-8)
+        S.filter()
+        torch.cuda.synchronize()
+        for j, f in enumerate(F):
+            Qg = S.block_matrix(j, which=5)[:, : f.rank].double().cpu().numpy()
+            Qo = f.Q()
+            bound = base + 100 * eps * f.r11 / np.abs(np.diag(f.R))
+            assert np.all(np.abs(Qg - Qo).max(axis=0) <= bound), (op, j)
+            # orthonormal columns in their own storage precision
+            assert np.abs(Qg.T @ Qg - np.eye(f.rank)).max() <= (1e-12 if op == "q64" else 1e-5)
+
+
+def _gpu_y_compact(S, y, F, K):
+    y = y.cpu().numpy()
+    return np.concatenate([y[j * K: j * K + f.rank] for j, f in enumerate(F)])
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("tol", [1e-6, 1e-4])
+@pytest.mark.parametrize("op,rtol", [("ar64", 1e-8), ("q64", 1e-8), ("q32", 1e-5)])
+def test_lsqr_fixed_iterations_match_oracle(rfm, name, tol, op, rtol):
+    p, prm, B, F = _oracle_filter(name, tol)
+    So = oracle.build_system(B, F, mode=0)
+    k = 30
+    ref = So.lsqr(B.h, atol=0, btol=0, max_iter=k)
+    S, _ = gpu_system(rfm, p, prm, op=op, tol=tol)
+    S.filter()
+    a, rep, y = S.solve(atol=0, btol=0, max_iter=k, want_y=True)
+    yg = _gpu_y_compact(S, y, F, p.K)
+    r = rfm.report_dict(rep)
+    assert r["itn"] == k and r["istop"] == 7 and r["status"] == 0
+    assert np.linalg.norm(yg - ref["y"]) <= rtol * np.linalg.norm(ref["y"])
+    assert r["rnorm"] == pytest.approx(ref["rnorm"], rel=rtol)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("op,rtol", [("ar64", 1e-7), ("q64", 1e-7), ("q32", 1e-6)])
+def test_lsqr_residual_estimates_at_small_threshold(rfm, name, op, rtol):
+    tol = 1e-8
+    p, prm, B, F = _oracle_filter(name, tol)
+    So = oracle.build_system(B, F, mode=0)
+    k = 20
+    ref = So.lsqr(B.h, atol=0, btol=0, max_iter=k)
+    S, _ = gpu_system(rfm, p, prm, op=op, tol=tol)
+    S.filter()
+    a, rep = S.solve(atol=0, btol=0, max_iter=k)
+    r = rfm.report_dict(rep)
+    assert r["rnorm"] == pytest.approx(ref["rnorm"], rel=rtol)
+    assert r["anorm"] == pytest.approx(ref["anorm"], rel=rtol)
+
+
+@pytest.mark.parametrize("name", ["p1d", "p2d", "heat"])
+@pytest.mark.parametrize("op", ["ar64", "q32"])
+def test_lsqr_converged_solution_and_stopping(rfm, name, op):
+    tol = 1e-6
+    p, prm, B, F = _oracle_filter(name, tol)
+    So = oracle.build_system(B, F, mode=0)
+    ref = So.lsqr(B.h, atol=1e-9, btol=1e-9, max_iter=5000)
+    S, d = gpu_system(rfm, p, prm, op=op, tol=tol)
+    S.filter()
+    a, rep = S.solve(atol=1e-9, btol=1e-9, max_iter=5000)
+    r = rfm.report_dict(rep)
+    assert r["istop"] == ref["istop"] and r["status"] == 0
+    assert abs(r["itn"] - ref["itn"]) <= max(2, ref["itn"] // 20)
+    assert r["rnorm"] == pytest.approx(ref["rnorm"], rel=1e-3 if op == "q32" else 1e-6)
+    # the solution evaluated on the test grid
+    X = oracle.test_grid(p, [min(40, t) for t in p.n_test])
+    uo = oracle.evaluate(p, prm, So.coefficients(ref["y"]), X)
+    ug, err = S.evaluate(d, a, [torch.from_numpy(X).cuda()])
+    ug = ug[0].cpu().numpy()
+    assert np.linalg.norm(ug - uo) <= (1e-4 if op == "q32" else 1e-7) * np.linalg.norm(uo)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_eval_matches_oracle(rfm, name):
+    p, prm, B = oracle_blocks(name)
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal(p.J * p.K)
+    X = oracle.test_grid(p, [7] * p.dim)
+    X = np.concatenate([X, rng.uniform(0, 1, (50, p.dim)), np.zeros((1, p.dim)), np.ones((1, p.dim))])
+    uo = oracle.evaluate(p, prm, a, X)
+    S, d = gpu_system(rfm, p, prm)
+    ug, err = S.evaluate(d, torch.from_numpy(a).cuda(), [torch.from_numpy(X).cuda()])
+    ug = ug[0].cpu().numpy()
+    assert np.abs(ug - uo).max() <= 1e-12 * max(1.0, np.abs(uo).max())
+    ue = oracle.exact(p, X)
+    e = err.cpu().numpy()
+    assert e[0] == pytest.approx(np.sum((ug - ue) ** 2), rel=1e-10)
+    assert e[1] == pytest.approx(np.sum(ue ** 2), rel=1e-10)
+    assert e[2] == pytest.approx(np.sum(np.abs(ug - ue)), rel=1e-10)
+    assert e[3] == pytest.approx(np.sum(ue), rel=1e-9, abs=1e-12)
+
+
+def test_plain_operator_matches_unfiltered_oracle(rfm):
+    p, prm, B = oracle_blocks("p1d")
+    full = oracle.FilteredSystem(B.N, B.grow, [np.asfortranarray(M) for M in B.M], None, mode=1,
+                                 perms=[np.arange(p.K, dtype=np.int32)] * p.J, K=p.K)
+    # M itself has kappa ~ 1e16, so LSQR iterates on it become chaotic after a
+    # few steps in any arithmetic; compare the early iterates.
+    ref = full.lsqr(B.h, atol=0, btol=0, max_iter=5)
+    S, _ = gpu_system(rfm, p, prm, op="plain")
+    S.filter()
+    a, rep, y = S.solve(atol=0, btol=0, max_iter=5, want_y=True)
+    assert np.linalg.norm(y.cpu().numpy() - ref["y"]) <= 1e-12 * np.linalg.norm(ref["y"])
+    assert np.array_equal(a.cpu().numpy(), y.cpu().numpy())
+
+
+def test_instances_side_by_side_match_single_runs(rfm):
+    names = ["p1d", "p2d", "heat"]
+    probs = [oracle_blocks(n)[0] for n in names]
+    prms = [oracle_blocks(n)[1] for n in names]
+    Sm = rfm.System(probs, op="ar64", tol=1e-8)
+    Sm.assemble(torch.from_numpy(np.concatenate([q.ravel() for q in prms])).cuda())
+    Sm.filter()
+    am, repm = Sm.solve(atol=0, btol=0, max_iter=25)
+    off = 0
+    for p, prm in zip(probs, prms):
+        S1, _ = gpu_system(rfm, p, prm, op="ar64", tol=1e-8)
+        S1.filter()
+        a1, rep1 = S1.solve(atol=0, btol=0, max_iter=25)
+        n = p.J * p.K
+        seg = am[off: off + n].cpu().numpy()
+        assert np.linalg.norm(seg - a1.cpu().numpy()) <= 1e-9 * np.linalg.norm(a1.cpu().numpy())
+        off += n
+
+
+def test_warm_start_from_solution_stops_immediately(rfm):
+    tol = 1e-8
+    p, prm, B, F = _oracle_filter("p1d", tol)
+    So = oracle.build_system(B, F, mode=0)
+    ref = So.lsqr(B.h, atol=1e-12, btol=1e-12, max_iter=20000)
+    S, _ = gpu_system(rfm, p, prm, op="ar64", tol=tol)
+    S.filter()
+    y0 = torch.zeros(p.J * p.K, dtype=torch.float64, device="cuda")
+    c = 0
+    for j, f in enumerate(F):
+        y0[j * p.K: j * p.K + f.rank] = torch.from_numpy(ref["y"][c: c + f.rank])
+        c += f.rank
+    a, rep = S.solve(atol=1e-6, btol=1e-6, max_iter=100, y0=y0)
+    r = rfm.report_dict(rep)
+    assert r["itn"] <= 2 and r["istop"] in (0, 1, 2)
+
+
+def test_repeated_calls_are_deterministic(rfm):
+    p, prm, B = oracle_blocks("p2d")
+    S, _ = gpu_system(rfm, p, prm, op="q32", tol=1e-8)
+    S.filter()
+    a1, _ = S.solve(atol=0, btol=0, max_iter=20)
+    a2, _ = S.solve(atol=0, btol=0, max_iter=20)
+    assert torch.equal(a1, a2)
