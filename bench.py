@@ -4,7 +4,9 @@ ELM-FBPINN solver on one GB300 (and N independent instances on N GPUs).
 Workload (N = 1): 2D Poisson on [0,1]^2, u = sin2pix sin2piy + 0.05
 sin30pix sin30piy, 20 x 20 subdomains (overlap ratio 1.25), 300 tanh features
 each, 360 x 360 cell-centred interior grid (the paper's S*ceil(K^(1/d)) rule)
-plus 1440 boundary points, filter threshold 1e-10.
+plus 1440 boundary points, filter threshold 1e-6 on both paths (a threshold
+below the FP32 rounding level of the assembled matrix would keep rounding-noise
+columns on the mixed path).
 
 A step is one pass of the whole path over one instance:
   assemble (FP32) -> RRQR filter (FP64 QRCP, Q_hat rounded to FP32) ->
@@ -12,10 +14,11 @@ A step is one pass of the whole path over one instance:
   count that reaches the target error -> a = S^-1 y -> u_hat and its error on
   the 400 x 400 test grid.
 The target error and the iteration counts come from an untimed calibration
-that records LSQR iterates every 10 iterations and evaluates each one; the
-target is the tightest value of a fixed ladder that both the mixed path and
-the plain FP64 path (FP64 assembly, FP64 kept columns with R^-1 substitution,
-zero start) reach.  Both paths are timed; "value" is the mixed path.
+that records LSQR iterates every 100 iterations up to the paper's budget of
+10,000 iterations and evaluates each one; the target is the tightest value of
+a fixed ladder that both the mixed path and the plain FP64 path (FP64
+assembly, FP64 kept columns with R^-1 substitution, zero start) reach.  Both
+paths are timed; "value" is the mixed path.
 """
 from __future__ import annotations
 
@@ -33,10 +36,11 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-TARGET_LADDER = [1e-6, 2e-6, 5e-6, 1e-5, 2e-5, 5e-5, 1e-4, 2e-4, 5e-4, 1e-3, 2e-3, 5e-3, 1e-2]
-TOL = 1e-10
-SNAP_EVERY = 10
-CAL_ITERS = 3000
+TARGET_LADDER = [1e-6, 2e-6, 5e-6, 1e-5, 2e-5, 5e-5, 1e-4, 2e-4, 5e-4, 1e-3, 2e-3, 5e-3, 1e-2, 2e-2, 5e-2,
+                 0.1, 0.2, 0.3, 0.5, 0.7, 0.8, 0.9, 0.95, 0.99]
+TOL = 1e-6
+SNAP_EVERY = 100
+CAL_ITERS = 10000
 # Nominal FP64 rate derived from the unit count and clock: 152 SMs x 4 FP64
 # flop/clk/SM (2 DFMA lanes) x 2.07 GHz = 1258 GFLOP/s (a DFMA probe measured
 # 1194 GFLOP/s on this part).
@@ -163,7 +167,7 @@ def run_gpu(args):
     paths = {"mixed": make("fp32", "q32"), "fp64": make("fp64", "ar64")}
 
     # ---- calibration (untimed): error after every SNAP_EVERY iterations
-    curves = {}
+    curves, conv = {}, {}
     for name, S in paths.items():
         S.assemble(d_prm)
         S.filter()
@@ -177,6 +181,9 @@ def run_gpu(args):
             e = err.cpu().numpy()
             errs.append(float(np.sqrt(e[0] / e[1])))
         curves[name] = np.array(errs)
+        conv[name] = {"min_rel_l2": float(curves[name].min()),
+                      "at_iteration": SNAP_EVERY * (1 + int(curves[name].argmin())),
+                      "rel_l2_at_10000": float(curves[name][-1]), "kept_columns": int(S.filter().sum().item())}
         log(f"[cal] {name}: min rel L2 {curves[name].min():.3e} at it {SNAP_EVERY * (1 + int(curves[name].argmin()))}")
     target = None
     for t in TARGET_LADDER:
@@ -296,8 +303,9 @@ def run_gpu(args):
         "ms_per_step": ms_mixed, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "2D Poisson 20x20 subdomains, delta 1.25, K=300, 360^2 interior + 1440 boundary "
-                               "rows, filter tol 1e-10, error on 400^2 test grid",
+                               "rows, filter tol 1e-6, error on 400^2 test grid",
                    "target_rel_l2": target, "iterations": kstar, "rel_l2_reached": {"mixed": rel_m, "fp64": rel_f},
+                   "convergence_10000_iterations": conv,
                    "l2_flush": "none: working set (M, QR work, Q_hat > 1.5 GB) exceeds L2 every step",
                    "parallelism": f"independent instances x{world}" if world > 1 else "1 instance"},
         "fp64_zero_start_ms": ms_fp64,
@@ -385,7 +393,7 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "2D Poisson 20x20 subdomains, delta 1.25, K=300, 360^2 interior + 1440 boundary "
-                                  "rows, filter tol 1e-10, error on 400^2 test grid", "lsqr_iterations": iters},
+                                  "rows, filter tol 1e-6, error on 400^2 test grid", "lsqr_iterations": iters},
            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": r["sample"]},
            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

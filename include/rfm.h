@@ -234,6 +234,14 @@ rfm_status rfm_profile_enable(int on);
 rfm_status rfm_profile_reset(void);
 int rfm_profile_read(const char **names, int64_t *launches, double *ms, int max);
 
+/* Process-wide options (host side).
+ *  RFM_OPT_FILTER_KERNEL: 0 (default) chooses per system: the cluster kernel
+ *    (block held in the distributed shared memory of a cluster of up to 8
+ *    CTAs) when the largest block fits, else the global-memory kernel;
+ *    1 forces the global-memory kernel (for comparison and testing). */
+enum { RFM_OPT_FILTER_KERNEL = 0 };
+rfm_status rfm_set_option(int option, int value);
+
 const char *rfm_last_error(void);
 int rfm_abi_version(void);
 

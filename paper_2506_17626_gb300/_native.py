@@ -42,7 +42,7 @@ REPORT_FIELDS = ("itn", "istop", "rnorm", "arnorm", "anorm", "ynorm", "bnorm", "
 
 EXPORTS = ["rfm_problem_size", "rfm_assemble", "rfm_rrqr_filter", "rfm_lsqr_solve", "rfm_coefficients",
            "rfm_eval", "rfm_block_info", "rfm_workspace_view", "rfm_profile_enable", "rfm_profile_reset",
-           "rfm_profile_read", "rfm_last_error", "rfm_abi_version"]
+           "rfm_profile_read", "rfm_set_option", "rfm_last_error", "rfm_abi_version"]
 
 _lib = None
 
@@ -73,6 +73,8 @@ def load(path: str = LIB_PATH):
         f = getattr(L, name)
         f.argtypes = args
         f.restype = st
+    L.rfm_set_option.argtypes = [C.c_int, C.c_int]
+    L.rfm_set_option.restype = C.c_int
     L.rfm_profile_enable.argtypes = [C.c_int]
     L.rfm_profile_enable.restype = C.c_int
     L.rfm_profile_reset.argtypes = []
@@ -134,3 +136,8 @@ def profile_read() -> dict:
     ms = (C.c_double * max(n, 1))()
     n = L.rfm_profile_read(names, cnt, ms, n)
     return {names[i].decode(): (int(cnt[i]), float(ms[i])) for i in range(n)}
+
+
+def set_filter_kernel(global_memory: bool):
+    """Force the global-memory QR kernel (True) or let the library choose (False)."""
+    check("rfm_set_option", load().rfm_set_option(0, 1 if global_memory else 0))

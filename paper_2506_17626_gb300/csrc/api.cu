@@ -14,6 +14,7 @@ rfm_status launch_filter(const HostPlan &P, void *ws, double tol, cudaStream_t s
 rfm_status launch_lsqr(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, const double *y0, double *y_out,
                        double *a_out, rfm_lsqr_report *rep, cudaStream_t st);
 rfm_status launch_coefficients(const HostPlan &P, void *ws, const double *y, double *a_out, cudaStream_t st);
+void set_force_global_filter(int on);
 rfm_status launch_eval(const HostPlan &P, void *ws, const double *params, const double *a, const double *X,
                        const int64_t *pt_off, double *u, double *err, cudaStream_t st);
 
@@ -182,6 +183,15 @@ rfm_status rfm_coefficients(const rfm_problem *probs, int n_inst, const rfm_conf
     }
     return launch_coefficients(P.p, d_ws, d_y, d_a, (cudaStream_t)stream);
     RFM_GUARD_END
+}
+
+rfm_status rfm_set_option(int option, int value) {
+    if (option == RFM_OPT_FILTER_KERNEL && (value == 0 || value == 1)) {
+        set_force_global_filter(value);
+        return RFM_OK;
+    }
+    set_error("rfm_set_option: unknown option %d or value %d", option, value);
+    return RFM_EINVAL;
 }
 
 rfm_status rfm_profile_enable(int on) {
