@@ -50,7 +50,15 @@ FP64_PEAK_GFLOPS = 152 * 4 * 2.07
 NCU_TRAFFIC = {}
 
 
-def workload():
+def workload(case: str = "full"):
+    """The 20x20x300 workload; "small" keeps its block shapes (same spacing,
+    same points per block) on 10 x 10 subdomains of the box [0, 9/19]^2, for
+    profiler captures."""
+    if case == "small":
+        p = synth.poisson2d(S=10, n=180)
+        p.hi = (9.0 / 19.0, 9.0 / 19.0, 1.0)
+        p.n_test = [180, 180]
+        return p
     return synth.poisson2d()
 
 
@@ -152,7 +160,7 @@ def run_gpu(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     dev = torch.device("cuda", local)
 
-    p = workload()
+    p = workload(args.case)
     if world > 1:           # independent instances, one per rank (weak scaling)
         p.seed = p.seed + rank
     prm = synth.feature_params(p)
@@ -168,7 +176,7 @@ def run_gpu(args):
 
     # ---- calibration (untimed): error after every SNAP_EVERY iterations
     curves, conv = {}, {}
-    for name, S in paths.items():
+    for name, S in (paths.items() if args.iters_mixed is None else []):
         S.assemble(d_prm)
         S.filter()
         cap = CAL_ITERS // SNAP_EVERY
@@ -186,14 +194,18 @@ def run_gpu(args):
                       "rel_l2_at_10000": float(curves[name][-1]), "kept_columns": int(S.filter().sum().item())}
         log(f"[cal] {name}: min rel L2 {curves[name].min():.3e} at it {SNAP_EVERY * (1 + int(curves[name].argmin()))}")
     target = None
-    for t in TARGET_LADDER:
-        if all((c <= t).any() for c in curves.values()):
-            target = t
-            break
-    if target is None:
-        target = float(max(c.min() for c in curves.values())) * 1.01
-    kstar = {n: SNAP_EVERY * (1 + int(np.argmax(c <= target))) for n, c in curves.items()}
-    log(f"[cal] target {target:g}, iterations {kstar}")
+    if args.iters_mixed is not None:
+        kstar = {"mixed": args.iters_mixed, "fp64": args.iters_fp64 or args.iters_mixed}
+        target = args.target
+    else:
+        for t in TARGET_LADDER:
+            if all((c <= t).any() for c in curves.values()):
+                target = t
+                break
+        if target is None:
+            target = float(max(c.min() for c in curves.values())) * 1.01
+        kstar = {n: SNAP_EVERY * (1 + int(np.argmax(c <= target))) for n, c in curves.items()}
+    log(f"[cal] target {target}, iterations {kstar}")
 
     # ---- timed steps
     st = torch.cuda.current_stream()
@@ -272,8 +284,11 @@ def run_gpu(args):
     launches = sum(v[0] for v in tot.values())
     per_launch_ms = {k: v[1] / v[0] for k, v in tot.items()}
     roof = None
-    if dom == "k_qrcp":
-        fl = qrcp_flops(m, K, ranks)
+    qr_name = "k_qrcp_cluster" if "k_qrcp_cluster" in per_launch_ms else "k_qrcp"
+    fused_q = qr_name == "k_qrcp_cluster"     # Q_hat accumulated in the same kernel
+    qr_alg = qrcp_flops(m, K, ranks) + (formq_flops(m, ranks) if fused_q else 0.0)
+    if dom == qr_name:
+        fl = qr_alg
         ach = fl / (per_launch_ms[dom] * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
                 "frac": ach / (FP64_PEAK_GFLOPS / 1e3), "peak_source": "derived FP64: 152 SMs x 4 flop/clk x 2.07 GHz",
@@ -292,7 +307,7 @@ def run_gpu(args):
                 "frac": ach / peaks["hbm_gbs"], "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                 "algorithmic_per_launch": by}
     roof["traffic"] = NCU_TRAFFIC.get(dom)
-    qr_gflops = qrcp_flops(m, K, ranks) / (per_launch_ms["k_qrcp"] * 1e-3) / 1e9
+    qr_gflops = qr_alg / (per_launch_ms[qr_name] * 1e-3) / 1e9
     lsqr_ms = per_launch_ms["k_lsqr"]
     spmv_gbs = lsqr_bytes_per_iter(m, ranks, S.sizes["n_rows"], 4) * kstar["mixed"] / (lsqr_ms * 1e-3) / 1e9
 
@@ -409,6 +424,11 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-iters", type=int, default=300,
                     help="LSQR iteration count the reference arm extrapolates to")
+    ap.add_argument("--iters-mixed", type=int, default=None, help="skip calibration: LSQR iterations (mixed)")
+    ap.add_argument("--iters-fp64", type=int, default=None, help="skip calibration: LSQR iterations (FP64)")
+    ap.add_argument("--target", type=float, default=None, help="target recorded when calibration is skipped")
+    ap.add_argument("--case", default="full", choices=["full", "small"],
+                    help="small: 10x10 subdomains with the same block shapes (profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -50,7 +50,49 @@ struct LsqrArgs {
 
 constexpr int kThreads = 256;
 constexpr int kRowTile = 256;
-constexpr int kRowChunk = 2048;
+constexpr int kRowChunk = 4096;     // rows of a block held in shared memory at once
+constexpr int kStages = 3;          // bulk-copy ring depth
+constexpr int kStageBytes = 20480;  // bytes per ring stage
+
+// ---- bulk asynchronous copies into shared memory, completed on mbarriers ----
+__device__ inline unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ inline void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ inline void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ inline void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Waits for the given phase parity of an mbarrier; false after timeout_ns.
+__device__ inline bool mbar_wait(uint64_t *bar, unsigned parity, uint64_t timeout_ns) {
+    const uint64_t t0 = global_ns();
+    unsigned spins = 0;
+    for (;;) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((++spins & 63u) == 0 && global_ns() - t0 > timeout_ns) return false;
+    }
+}
+
+// Staging ring in dynamic shared memory (after the scalar state).
+struct Ring {
+    uint64_t bar[kStages];
+    unsigned uses[kStages];
+};
 
 // Bounded grid barrier.  Returns false when any CTA has reported an error.
 __device__ bool grid_sync(unsigned *bar, uint64_t timeout_ns) {
@@ -208,45 +250,143 @@ __global__ void __launch_bounds__(kThreads) k_lsqr(LsqrArgs a) {
         for (int s = tid; s < ni; s += kThreads) a.part[((int64_t)which * ni + s) * G + cta] = S.acc[s];
     };
 
-    // forward product t_b = Op_b x_b for the block (x already in S.x / S.xa)
-    auto block_forward = [&](const BlkRec &B, int r) {
-        const TA *Ab = Aop + B.moff;
-        for (int i = tid; i < B.m; i += kThreads) {
-            TA s = (TA)0;
-            int c = 0;
-            for (; c + 4 <= r; c += 4) {
-                s += Ab[(int64_t)c * B.ldm + i] * S.xa[c];
-                s += Ab[(int64_t)(c + 1) * B.ldm + i] * S.xa[c + 1];
-                s += Ab[(int64_t)(c + 2) * B.ldm + i] * S.xa[c + 2];
-                s += Ab[(int64_t)(c + 3) * B.ldm + i] * S.xa[c + 3];
+    // ---- staging ring (after Smem<TA> in dynamic shared memory)
+    unsigned char *ring_base = smem_raw + ((sizeof(Smem<TA>) + 127) / 128) * 128;
+    Ring &RG = *reinterpret_cast<Ring *>(ring_base);
+    unsigned char *stage_mem = ring_base + 128;
+    if (tid == 0) {
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(&RG.bar[i], 1);
+            RG.uses[i] = 0;
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+
+    // Column chunks of a block: cw columns (contiguous, cw*ldm elements).
+    auto chunk_cols = [&](const BlkRec &B) {
+        int cw = kStageBytes / (B.ldm * (int)sizeof(TA));
+        return cw < 1 ? 1 : cw;
+    };
+    // Sequence of (block, chunk) of this CTA over the blocks accepted by
+    // `take`, streamed through the ring; per block: on_start (uniform), per
+    // chunk on_chunk(B, r, c0, nc, tile), at the end on_end(B, r).
+    auto stream = [&](auto take, auto on_start, auto on_chunk, auto on_end) {
+        // issue cursor
+        int ib = cta, ic = 0;
+        auto adv_issue = [&]() {
+            while (ib < a.n_blocks) {
+                const int r = blk_rank(ib);
+                if (take(ib) && r > 0) {
+                    const int cw = chunk_cols(a.blks[ib]);
+                    if (ic * cw < r) return true;
+                }
+                ib += G;
+                ic = 0;
             }
-            for (; c < r; ++c) s += Ab[(int64_t)c * B.ldm + i] * S.xa[c];
-            a.t[B.roff + i] = (double)s;
+            return false;
+        };
+        auto issue = [&](int stage) {
+            if (!adv_issue()) return;
+            if (tid == 0) {
+                const BlkRec &B = a.blks[ib];
+                const int r = blk_rank(ib), cw = chunk_cols(B);
+                const int c0 = ic * cw, nc = min(cw, r - c0);
+                const unsigned bytes = (unsigned)(nc * B.ldm * (int)sizeof(TA));
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&RG.bar[stage], bytes);
+                bulk_g2s(stage_mem + (size_t)stage * kStageBytes, Aop + B.moff + (int64_t)c0 * B.ldm, bytes,
+                         &RG.bar[stage]);
+            }
+            ++ic;
+        };
+        for (int st = 0; st < kStages; ++st) issue(st);
+        int j = 0;
+        for (int b = cta; b < a.n_blocks; b += G) {
+            const int r = blk_rank(b);
+            if (!take(b) || r <= 0) continue;
+            const BlkRec &B = a.blks[b];
+            on_start(B, r);
+            const int cw = chunk_cols(B);
+            for (int c0 = 0; c0 < r; c0 += cw, ++j) {
+                const int stage = j % kStages;
+                const unsigned par = RG.uses[stage] & 1u;
+                if (!mbar_wait(&RG.bar[stage], par, a.timeout_ns)) {
+                    if (tid == 0) atomicCAS(a.bar + 2, 0u, (unsigned)RFM_ETIMEOUT);
+                }
+                const TA *tile = reinterpret_cast<const TA *>(stage_mem + (size_t)stage * kStageBytes);
+                on_chunk(B, r, c0, min(cw, r - c0), tile);
+                __syncthreads();
+                if (tid == 0) RG.uses[stage] += 1;
+                __syncthreads();
+                issue(stage);
+            }
+            on_end(B, r);
         }
     };
-    // transpose product S.x[c] = sum_i Op_b[i, c] * u~[grow[i]] * inv_beta
-    auto block_transpose = [&](const BlkRec &B, int r, double inv_beta) {
-        const TA *Ab = Aop + B.moff;
-        for (int c = tid; c < r; c += kThreads) S.x[c] = 0.0;
-        for (int i0 = 0; i0 < B.m; i0 += kRowChunk) {
-            const int n = min(kRowChunk, B.m - i0);
-            __syncthreads();
-            for (int i = tid; i < n; i += kThreads) S.ub[i] = (TA)(a.u[a.grow[B.roff + i0 + i]] * inv_beta);
-            __syncthreads();
-            for (int c = warp; c < r; c += kThreads / 32) {
-                const TA *col = Ab + (int64_t)c * B.ldm + i0;
-                TA s = (TA)0;
-                for (int i = lane; i < n; i += 32) s += col[i] * S.ub[i];
-                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                if (lane == 0) S.x[c] += (double)s;
-            }
-        }
-        __syncthreads();
+
+    // t_b = Op_b x_b for every accepted block; x_b from xsrc (the block's K-slot)
+    auto forward_all = [&](auto take, const double *xsrc) {
+        // blocks without kept columns contribute zero to their rows
+        for (int b = cta; b < a.n_blocks; b += G)
+            if (take(b) && blk_rank(b) <= 0)
+                for (int i = tid; i < a.blks[b].m; i += kThreads) a.t[a.blks[b].roff + i] = 0.0;
+        stream(
+            take,
+            [&](const BlkRec &B, int r) {
+                for (int c = tid; c < r; c += kThreads) S.x[c] = xsrc[B.coff + c];
+                __syncthreads();
+                if (TRI) tri_solve_upper(a.W + B.moff, B.ldm, r, S.x);
+                for (int c = tid; c < r; c += kThreads) S.xa[c] = (TA)S.x[c];
+                for (int i = tid; i < B.m; i += kThreads) S.ub[i] = (TA)0;
+                __syncthreads();
+            },
+            [&](const BlkRec &B, int r, int c0, int nc, const TA *tile) {
+                for (int i = tid; i < B.m; i += kThreads) {
+                    TA s = S.ub[i];
+                    int c = 0;
+                    for (; c + 4 <= nc; c += 4) {
+                        s += tile[(c + 0) * B.ldm + i] * S.xa[c0 + c + 0];
+                        s += tile[(c + 1) * B.ldm + i] * S.xa[c0 + c + 1];
+                        s += tile[(c + 2) * B.ldm + i] * S.xa[c0 + c + 2];
+                        s += tile[(c + 3) * B.ldm + i] * S.xa[c0 + c + 3];
+                    }
+                    for (; c < nc; ++c) s += tile[c * B.ldm + i] * S.xa[c0 + c];
+                    S.ub[i] = s;
+                }
+            },
+            [&](const BlkRec &B, int r) {
+                for (int i = tid; i < B.m; i += kThreads) a.t[B.roff + i] = (double)S.ub[i];
+                __syncthreads();
+            });
     };
-    auto stage_x = [&](int r) {
-        for (int c = tid; c < r; c += kThreads) S.xa[c] = (TA)S.x[c];
-        __syncthreads();
+    // S.x = Op_b^T (u~ / beta) per accepted block, then on_end(B, r) with it
+    auto transpose_all = [&](auto take, auto inv_beta_of, auto on_end) {
+        stream(
+            take,
+            [&](const BlkRec &B, int r) {
+                const double ib = inv_beta_of(B);
+                for (int i = tid; i < B.m; i += kThreads) S.ub[i] = (TA)(a.u[a.grow[B.roff + i]] * ib);
+                __syncthreads();
+            },
+            [&](const BlkRec &B, int r, int c0, int nc, const TA *tile) {
+                for (int c = warp; c < nc; c += kThreads / 32) {
+                    const TA *col = tile + c * B.ldm;
+                    TA s = (TA)0;
+                    for (int i = lane; i < B.m; i += 32) s += col[i] * S.ub[i];
+                    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                    if (lane == 0) S.x[c0 + c] = (double)s;
+                }
+            },
+            [&](const BlkRec &B, int r) {
+                __syncthreads();
+                if (TRI) tri_solve_upper_t(a.W + B.moff, B.ldm, r, S.x);
+                on_end(B, r);
+            });
     };
+    auto all_blocks = [&](int) { return true; };
+    auto live_blocks = [&](int b) { return !sc[a.blks[b].inst].done; };
 
     // ------------------------------------------------------------ init
     for (int s = tid; s < ni && s < 64; s += kThreads) {
@@ -255,25 +395,19 @@ __global__ void __launch_bounds__(kThreads) k_lsqr(LsqrArgs a) {
         sc[s] = z;
     }
     __syncthreads();
-    // I1: t = Op P y0 (when warm-starting); y = y0 or 0
+    // I1: y = y0 or 0, and t = Op P y0 when warm-starting
     for (int b = cta; b < a.n_blocks; b += G) {
         const BlkRec &B = a.blks[b];
         const int r = blk_rank(b), K = B.K;
         for (int c = tid; c < K; c += kThreads) {
-            double yv = (a.y0 && c < r) ? a.y0[B.coff + c] : 0.0;
-            a.y[B.coff + c] = yv;
+            a.y[B.coff + c] = (a.y0 && c < r) ? a.y0[B.coff + c] : 0.0;
             a.w[B.coff + c] = 0.0;
             a.v[B.coff + c] = 0.0;
-            if (c < r) S.x[c] = yv;
         }
-        __syncthreads();
-        if (a.y0) {
-            if (TRI) tri_solve_upper(a.W + B.moff, B.ldm, r, S.x);
-            stage_x(r);
-            block_forward(B, r);
-        }
-        __syncthreads();
     }
+    __syncthreads();
+    if (a.y0) forward_all(all_blocks, a.y);
+    __syncthreads();
     ok = grid_sync(a.bar, a.timeout_ns);
     // I2: u~ = h - t-sums, partials of ||u~||^2 (slot 0) and ||h||^2 (slot 1)
     clear_acc();
@@ -323,21 +457,22 @@ __global__ void __launch_bounds__(kThreads) k_lsqr(LsqrArgs a) {
     __syncthreads();
     // I3: vt = Op^T (u~/beta), ||vt||^2
     clear_acc();
-    for (int b = cta; b < a.n_blocks; b += G) {
-        const BlkRec &B = a.blks[b];
-        const int r = blk_rank(b);
-        const double beta = sc[B.inst].beta;
-        block_transpose(B, r, beta > 0.0 ? 1.0 / beta : 0.0);
-        if (TRI) tri_solve_upper_t(a.W + B.moff, B.ldm, r, S.x);
-        double part = 0.0;
-        for (int c = tid; c < r; c += kThreads) {
-            a.vt[B.coff + c] = S.x[c];
-            part += S.x[c] * S.x[c];
-        }
-        double sum = cta_sum(part, S.red);
-        if (tid == 0) S.acc[B.inst] += sum;
-        __syncthreads();
-    }
+    transpose_all(
+        all_blocks,
+        [&](const BlkRec &B) {
+            const double beta = sc[B.inst].beta;
+            return beta > 0.0 ? 1.0 / beta : 0.0;
+        },
+        [&](const BlkRec &B, int r) {
+            double part = 0.0;
+            for (int c = tid; c < r; c += kThreads) {
+                a.vt[B.coff + c] = S.x[c];
+                part += S.x[c] * S.x[c];
+            }
+            double sum = cta_sum(part, S.red);
+            if (tid == 0) S.acc[B.inst] += sum;
+            __syncthreads();
+        });
     flush_acc(2);
     ok = grid_sync(a.bar, a.timeout_ns);
     if (!ok) return;
@@ -384,7 +519,6 @@ __global__ void __launch_bounds__(kThreads) k_lsqr(LsqrArgs a) {
                     }
                     a.w[o] = wv;
                     a.v[o] = vn;
-                    S.x[c] = vn;
                     ypart += yv * yv;
                 }
             } else {
@@ -396,13 +530,8 @@ __global__ void __launch_bounds__(kThreads) k_lsqr(LsqrArgs a) {
             double ysum = cta_sum(ypart, S.red);
             if (tid == 0) S.acc[B.inst] += ysum;
             __syncthreads();
-            if (!q.done) {
-                if (TRI) tri_solve_upper(a.W + B.moff, B.ldm, r, S.x);
-                stage_x(r);
-                block_forward(B, r);
-            }
-            __syncthreads();
         }
+        forward_all(live_blocks, a.v);
         flush_acc(0);
         ok = grid_sync(a.bar, a.timeout_ns);
         if (!ok) break;
@@ -462,25 +591,25 @@ __global__ void __launch_bounds__(kThreads) k_lsqr(LsqrArgs a) {
         reduce_partials(a.part + (int64_t)ni * G, ni, S.tmp);
         // T: vt = Op^T (u~/beta_new) - beta_new v
         clear_acc();
-        for (int b = cta; b < a.n_blocks; b += G) {
-            const BlkRec &B = a.blks[b];
-            const LsqrScal &q = sc[B.inst];
-            if (q.done) continue;
-            const int r = blk_rank(b);
-            const double bn = sqrt(S.tmp[B.inst]);
-            block_transpose(B, r, bn > 0.0 ? 1.0 / bn : 0.0);
-            if (TRI) tri_solve_upper_t(a.W + B.moff, B.ldm, r, S.x);
-            double part = 0.0;
-            for (int c = tid; c < r; c += kThreads) {
-                const int64_t o = B.coff + c;
-                double x = fma(-bn, a.v[o], S.x[c]);
-                a.vt[o] = x;
-                part += x * x;
-            }
-            double sum = cta_sum(part, S.red);
-            if (tid == 0) S.acc[B.inst] += sum;
-            __syncthreads();
-        }
+        transpose_all(
+            live_blocks,
+            [&](const BlkRec &B) {
+                const double bn = sqrt(S.tmp[B.inst]);
+                return bn > 0.0 ? 1.0 / bn : 0.0;
+            },
+            [&](const BlkRec &B, int r) {
+                const double bn = sqrt(S.tmp[B.inst]);
+                double part = 0.0;
+                for (int c = tid; c < r; c += kThreads) {
+                    const int64_t o = B.coff + c;
+                    double x = fma(-bn, a.v[o], S.x[c]);
+                    a.vt[o] = x;
+                    part += x * x;
+                }
+                double sum = cta_sum(part, S.red);
+                if (tid == 0) S.acc[B.inst] += sum;
+                __syncthreads();
+            });
         flush_acc(2);
         ok = grid_sync(a.bar, a.timeout_ns);
         if (!ok) break;
@@ -577,7 +706,14 @@ static rfm_status run_lsqr(const HostPlan &P, void *ws, LsqrArgs &args, cudaStre
     int dev = 0, nsm = 0, per = 0;
     RFM_CUDA_CHECK(cudaGetDevice(&dev));
     RFM_CUDA_CHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const size_t sm = sizeof(Smem<TA>);
+    const size_t sm = ((sizeof(Smem<TA>) + 127) / 128) * 128 + 128 + (size_t)kStages * kStageBytes;
+    // one column of the tallest block must fit in a ring stage, all its rows in the row buffer
+    const int64_t ld_max = (P.L.max_m + kLdAlign - 1) / kLdAlign * kLdAlign;
+    if (ld_max * (int64_t)sizeof(TA) > kStageBytes || P.L.max_m > kRowChunk) {
+        set_error("rfm_lsqr_solve: blocks of %lld rows exceed the LSQR kernel's staging (%d rows)",
+                  (long long)P.L.max_m, (int)(kStageBytes / sizeof(TA)));
+        return RFM_EINVAL;
+    }
     RFM_CUDA_CHECK(cudaFuncSetAttribute(k_lsqr<TA, TRI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     RFM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lsqr<TA, TRI>, kThreads, sm));
     if (per < 1) {

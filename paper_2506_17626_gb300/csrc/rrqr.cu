@@ -236,21 +236,27 @@ namespace rfm {
 // ---------------------------------------------------------------------------
 // Cluster variant: the block lives in the shared memory of a cluster of C
 // CTAs (thread-block cluster, distributed shared memory), distributed by
-// columns: column position c belongs to CTA c mod C, slot c / C.  Per step:
-//   argmax of the trailing norms (each CTA over its columns, then every CTA
-//   reads the C candidates through DSMEM and takes the same winner), column
-//   swap between the two owners through DSMEM, reflector formed by the owner
-//   of column k, every CTA copies v from the owner's shared memory and updates
-//   its own trailing columns.  Three cluster barriers per step; no global
-//   memory traffic inside the factorisation.  Q_hat (when wanted) is then
-//   accumulated backwards in the same shared memory, each CTA on its own
-//   columns, reading the reflectors back from global memory.
+// columns: original column c belongs to CTA c mod C, slot c / C, and never
+// moves.  Pivoting retires the chosen column in place and records its
+// position.  One cluster barrier per step:
+//   - each CTA publishes its best non-retired column (trailing norm, original
+//     index), double-buffered by step parity;
+//   - after the barrier one warp reads the C candidates through DSMEM and
+//     every CTA takes the same winner;
+//   - every CTA copies the winner's column (rows k..m) through DSMEM, forms
+//     the same reflector from it (same data, same order: bit-identical), and
+//     updates its own non-retired columns;
+//   - the owner writes beta and v into the retired column after the next
+//     barrier, when no CTA can still be reading it.
+// No global memory traffic inside the factorisation.  Q_hat (when wanted) is
+// then accumulated backwards in the same shared memory, each CTA on its own
+// columns, prefetching the next reflector from global memory.
 // ---------------------------------------------------------------------------
 namespace cg = cooperative_groups;
 
 struct Cand {
     double v;
-    int p, c;
+    int p, slot;
 };
 
 template <typename TM, int C>
@@ -267,18 +273,19 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
     extern __shared__ __align__(16) double sm[];
     double *A = sm;                                  // nloc_max x ld_loc
     double *vbuf = A + (size_t)nloc_max * ld_loc;     // ld_loc
-    double *cn = vbuf + ld_loc;                      // nloc_max
+    double *vbuf2 = vbuf + ld_loc;                   // ld_loc (Q prefetch)
+    double *cn = vbuf2 + ld_loc;                     // nloc_max
     double *cn0 = cn + nloc_max;                     // nloc_max
-    int *perm = (int *)(cn0 + nloc_max);             // nloc_max
-    __shared__ Cand cand;
+    int *pos = (int *)(cn0 + nloc_max);              // nloc_max: position of the column, -1 while trailing
+    __shared__ Cand cand[2];
     __shared__ Cand red[8];
-    __shared__ double s_nx, s_tau, s_meta[2];
-    __shared__ int s_pmeta;
+    __shared__ Cand s_win;
+    __shared__ double s_red[8];
+    __shared__ int s_ndrop;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nloc = (K - cr + C - 1) / C;   // columns owned by this CTA
     double *Wb = W + B.moff;
 
-    // load owned columns (FP64) and their exact norms
     for (int l = warp; l < nloc; l += 8) {
         const int c = cr + C * l;
         const TM *src = M + B.moff + (int64_t)c * ld;
@@ -292,7 +299,7 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
         if (lane == 0) {
             cn[l] = sqrt(s);
             cn0[l] = cn[l];
-            perm[l] = c;
+            pos[l] = -1;
         }
     }
     __syncthreads();
@@ -300,122 +307,84 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
     const double tol3z = sqrt(2.220446049250313e-16);
     double R11 = 0.0;
     int rank = steps;
+    int pend_slot = -1, pend_k = 0;   // owner's deferred write of the last reflector
+    double pend_beta = 0.0;
     for (int k = 0; k < steps; ++k) {
-        // 1. local candidate among owned positions c >= k
+        // 1. best non-retired column of this CTA
         double bv = -1.0;
-        int bp = 0x7fffffff, bc = k;
-        const int l0 = (k - cr + C - 1) / C > 0 ? (k - cr + C - 1) / C : 0;  // first slot with position >= k
-        for (int l = l0 + tid; l < nloc; l += 256) {
-            const int c = cr + C * l;
-            if (better(cn[l], perm[l], bv, bp)) { bv = cn[l]; bp = perm[l]; bc = c; }
-        }
+        int bp = 0x7fffffff, bl = -1;
+        for (int l = tid; l < nloc; l += 256)
+            if (pos[l] < 0 && better(cn[l], cr + C * l, bv, bp)) { bv = cn[l]; bp = cr + C * l; bl = l; }
         for (int o = 16; o; o >>= 1) {
             double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
             int p2 = __shfl_xor_sync(0xffffffffu, bp, o);
-            int c2 = __shfl_xor_sync(0xffffffffu, bc, o);
-            if (better(v2, p2, bv, bp)) { bv = v2; bp = p2; bc = c2; }
+            int l2 = __shfl_xor_sync(0xffffffffu, bl, o);
+            if (better(v2, p2, bv, bp)) { bv = v2; bp = p2; bl = l2; }
         }
-        if (lane == 0) red[warp] = Cand{bv, bp, bc};
+        if (lane == 0) red[warp] = Cand{bv, bp, bl};
         __syncthreads();
         if (tid == 0) {
             Cand t = red[0];
             for (int w = 1; w < 8; ++w)
                 if (better(red[w].v, red[w].p, t.v, t.p)) t = red[w];
-            cand = t;
+            cand[k & 1] = t;
         }
         cl.sync();
-        // 2. winner over the cluster (same in every CTA)
-        Cand win = *cl.map_shared_rank(&cand, 0);
-        for (int r = 1; r < C; ++r) {
-            Cand t = *cl.map_shared_rank(&cand, r);
-            if (better(t.v, t.p, win.v, win.p)) win = t;
+        // deferred write of the previous reflector into its (retired) column
+        if (pend_slot >= 0) {
+            double *x = A + (size_t)pend_slot * ld_loc;
+            for (int i = pend_k + 1 + tid; i < m; i += 256) x[i] = vbuf[i];
+            if (tid == 0) x[pend_k] = pend_beta;
+            pend_slot = -1;
         }
-        const int piv = win.c;
-        const int ok = k % C, lk = k / C, op = piv % C, lp = piv / C;
-        // 3. swap positions k and piv
-        if (piv != k) {
-            if (ok == op) {
-                if (cr == ok) {
-                    for (int i = tid; i < m; i += 256) {
-                        double t = A[(size_t)lk * ld_loc + i];
-                        A[(size_t)lk * ld_loc + i] = A[(size_t)lp * ld_loc + i];
-                        A[(size_t)lp * ld_loc + i] = t;
-                    }
-                    if (tid == 0) {
-                        double t = cn[lk]; cn[lk] = cn[lp]; cn[lp] = t;
-                        t = cn0[lk]; cn0[lk] = cn0[lp]; cn0[lp] = t;
-                        int q = perm[lk]; perm[lk] = perm[lp]; perm[lp] = q;
-                    }
-                }
-                cl.sync();
-            } else {
-                // fetch the partner's column into vbuf, then write it after the barrier
-                const int mine = cr == ok ? lk : lp, other_cta = cr == ok ? op : ok, other_slot = cr == ok ? lp : lk;
-                const bool part = cr == ok || cr == op;
-                if (part) {
-                    const double *rA = cl.map_shared_rank(A, other_cta);
-                    for (int i = tid; i < m; i += 256) vbuf[i] = rA[(size_t)other_slot * ld_loc + i];
-                    if (tid == 0) {
-                        s_meta[0] = cl.map_shared_rank(cn, other_cta)[other_slot];
-                        s_meta[1] = cl.map_shared_rank(cn0, other_cta)[other_slot];
-                        s_pmeta = cl.map_shared_rank(perm, other_cta)[other_slot];
-                    }
-                }
-                cl.sync();
-                if (part) {
-                    for (int i = tid; i < m; i += 256) A[(size_t)mine * ld_loc + i] = vbuf[i];
-                    if (tid == 0) {
-                        cn[mine] = s_meta[0];
-                        cn0[mine] = s_meta[1];
-                        perm[mine] = s_pmeta;
-                    }
-                }
-                __syncthreads();
+        // 2. winner over the cluster
+        if (warp == 0) {
+            Cand t = Cand{-1.0, 0x7fffffff, -1};
+            int owner = 0;
+            if (lane < C) t = cl.map_shared_rank(&cand[k & 1], lane)[0];
+            int o = lane;
+            for (int sh = 16; sh; sh >>= 1) {
+                double v2 = __shfl_xor_sync(0xffffffffu, t.v, sh);
+                int p2 = __shfl_xor_sync(0xffffffffu, t.p, sh);
+                int l2 = __shfl_xor_sync(0xffffffffu, t.slot, sh);
+                int o2 = __shfl_xor_sync(0xffffffffu, o, sh);
+                if (better(v2, p2, t.v, t.p)) { t.v = v2; t.p = p2; t.slot = l2; o = o2; }
             }
-        }
-        // 4. reflector by the owner of position k
-        if (cr == ok) {
-            double s = 0.0;
-            const double *x = A + (size_t)lk * ld_loc;
-            for (int i = k + tid; i < m; i += 256) s = fma(x[i], x[i], s);
-            for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) red[warp].v = s;
-            __syncthreads();
-            if (tid == 0) {
-                double t = 0.0;
-                for (int w = 0; w < 8; ++w) t += red[w].v;
-                s_nx = sqrt(t);
-            }
-            __syncthreads();
-        }
-        cl.sync();
-        const double nx = *cl.map_shared_rank(&s_nx, ok);
-        if (k == 0) R11 = nx;
-        if (nx == 0.0 || nx < tol * R11) { rank = k; break; }
-        if (cr == ok) {
-            double *x = A + (size_t)lk * ld_loc;
-            const double alpha = x[k];
-            const double beta = alpha >= 0.0 ? -nx : nx;
-            const double scale = 1.0 / (alpha - beta);
-            for (int i = k + 1 + tid; i < m; i += 256) x[i] *= scale;
-            __syncthreads();
-            if (tid == 0) {
-                x[k] = beta;
-                s_tau = (beta - alpha) / beta;
-                tau[B.coff + k] = s_tau;
-            }
-        }
-        cl.sync();
-        // 5. every CTA copies v (rows k+1..m) and tau from the owner
-        const double tk = *cl.map_shared_rank(&s_tau, ok);
-        {
-            const double *rx = cl.map_shared_rank(A, ok) + (size_t)lk * ld_loc;
-            for (int i = k + 1 + tid; i < m; i += 256) vbuf[i] = rx[i];
+            owner = o;
+            if (lane == 0) s_win = Cand{t.v, owner, t.slot};
         }
         __syncthreads();
-        // 6. update owned trailing columns c > k, downdate their norms
-        const int l1 = (k + 1 - cr + C - 1) / C > 0 ? (k + 1 - cr + C - 1) / C : 0;
-        for (int l = l1 + warp; l < nloc; l += 8) {
+        const int own = s_win.p, wsl = s_win.slot;   // owner CTA and its slot
+        // 3. copy the pivot column (rows k..m) from its owner
+        {
+            const double *rx = cl.map_shared_rank(A, own) + (size_t)wsl * ld_loc;
+            for (int i = k + tid; i < m; i += 256) vbuf[i] = rx[i];
+        }
+        __syncthreads();
+        // 4. exact norm and reflector (computed identically in every CTA)
+        double s = 0.0;
+        for (int i = k + tid; i < m; i += 256) s = fma(vbuf[i], vbuf[i], s);
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) s_red[warp] = s;
+        __syncthreads();
+        double t2 = 0.0;
+        for (int w = 0; w < 8; ++w) t2 += s_red[w];
+        const double nx = sqrt(t2);
+        if (k == 0) R11 = nx;
+        if (nx == 0.0 || nx < tol * R11) { rank = k; break; }
+        const double alpha = vbuf[k];
+        const double beta = alpha >= 0.0 ? -nx : nx;
+        const double scale = 1.0 / (alpha - beta);
+        const double tk = (beta - alpha) / beta;
+        __syncthreads();
+        for (int i = k + 1 + tid; i < m; i += 256) vbuf[i] *= scale;
+        if (cr == own && tid == 0) pos[wsl] = k;
+        if (cr == 0 && tid == 0) tau[B.coff + k] = tk;
+        __syncthreads();
+        if (cr == own) { pend_slot = wsl; pend_k = k; pend_beta = beta; }
+        // 5. update own trailing columns, downdate their norms
+        for (int l = warp; l < nloc; l += 8) {
+            if (pos[l] >= 0) continue;
             double *a = A + (size_t)l * ld_loc;
             double d = 0.0;
             for (int i = k + 1 + lane; i < m; i += 32) d = fma(vbuf[i], a[i], d);
@@ -447,48 +416,86 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
         }
         __syncthreads();
     }
-    // write R and the reflectors of the owned columns, the permutation, rank
-    for (int l = warp; l < nloc; l += 8) {
-        const int c = cr + C * l;
-        for (int i = lane; i < m; i += 32) Wb[(int64_t)c * ld + i] = A[(size_t)l * ld_loc + i];
+    // every CTA has finished reading pivot columns; finish the last deferred write
+    cl.sync();
+    if (pend_slot >= 0) {
+        double *x = A + (size_t)pend_slot * ld_loc;
+        for (int i = pend_k + 1 + tid; i < m; i += 256) x[i] = vbuf[i];
+        if (tid == 0) x[pend_k] = pend_beta;
     }
-    for (int l = tid; l < nloc; l += 256) perm_out[B.coff + cr + C * l] = perm[l];
+    // positions of the dropped columns: rank + (dropped columns of lower CTAs) + local order
+    if (tid == 0) {
+        int nd = 0;
+        for (int l = 0; l < nloc; ++l) nd += pos[l] < 0;
+        s_ndrop = nd;
+    }
+    cl.sync();
+    if (tid == 0) {
+        int base = rank;
+        for (int r = 0; r < cr; ++r) base += *cl.map_shared_rank(&s_ndrop, r);
+        for (int l = 0; l < nloc; ++l)
+            if (pos[l] < 0) pos[l] = base++;
+    }
+    __syncthreads();
+    for (int l = warp; l < nloc; l += 8) {
+        const int p = pos[l];
+        for (int i = lane; i < m; i += 32) Wb[(int64_t)p * ld + i] = A[(size_t)l * ld_loc + i];
+    }
+    for (int l = tid; l < nloc; l += 256) perm_out[B.coff + pos[l]] = cr + C * l;
     if (cr == 0 && tid == 0) {
         rank_out[b] = rank;
         r11_out[b] = R11;
     }
-    if (!Qout && !Q32) {
-        cl.sync();
-        return;
-    }
-    // Q_hat = H_0 ... H_{r-1} [I_r; 0], owned columns c < r, in shared memory
-    cl.sync();  // every owner has written its reflectors to global memory
-    __threadfence();
+    cl.sync();   // reflectors in global memory; no DSMEM access after this point
+    if (!Qout && !Q32) return;
+    // Q_hat = H_0 ... H_{r-1} [I_r; 0], owned columns c < r (c mod C == cr)
     const int r = rank;
     const int nq = (r - cr + C - 1) / C > 0 ? (r - cr + C - 1) / C : 0;
     for (int l = warp; l < nq; l += 8) {
         const int c = cr + C * l;
         for (int i = lane; i < m; i += 32) A[(size_t)l * ld_loc + i] = (i == c) ? 1.0 : 0.0;
     }
+    double *cur = vbuf, *nxt = vbuf2;
+    if (r > 0) {
+        const double *v = Wb + (int64_t)(r - 1) * ld;
+        for (int i = r + tid; i < m; i += 256) cur[i] = v[i];
+    }
     __syncthreads();
     for (int k = r - 1; k >= 0; --k) {
-        const double *v = Wb + (int64_t)k * ld;
-        for (int i = k + 1 + tid; i < m; i += 256) vbuf[i] = v[i];
-        __syncthreads();
+        // prefetch reflector k-1 into registers while reflector k is applied
+        double pre[4];
+        if (k > 0) {
+            const double *v = Wb + (int64_t)(k - 1) * ld;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = k + tid + 256 * j;
+                pre[j] = i < m ? v[i] : 0.0;
+            }
+        }
         const double tk = tau[B.coff + k];
         const int lq = (k - cr + C - 1) / C > 0 ? (k - cr + C - 1) / C : 0;
         for (int l = lq + warp; l < nq; l += 8) {
             double *q = A + (size_t)l * ld_loc;
             double d = 0.0;
-            for (int i = k + 1 + lane; i < m; i += 32) d = fma(vbuf[i], q[i], d);
+            for (int i = k + 1 + lane; i < m; i += 32) d = fma(cur[i], q[i], d);
             for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
             const double qk = q[k];
             d = tk * (qk + d);
-            for (int i = k + 1 + lane; i < m; i += 32) q[i] = fma(-d, vbuf[i], q[i]);
+            for (int i = k + 1 + lane; i < m; i += 32) q[i] = fma(-d, cur[i], q[i]);
             __syncwarp();
             if (lane == 0) q[k] = qk - d;
         }
+        if (k > 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = k + tid + 256 * j;
+                if (i < m) nxt[i] = pre[j];
+            }
+            const double *v = Wb + (int64_t)(k - 1) * ld;   // rows beyond the register prefetch
+            for (int i = k + tid + 4 * 256; i < m; i += 256) nxt[i] = v[i];
+        }
         __syncthreads();
+        double *t = cur; cur = nxt; nxt = t;
     }
     for (int l = warp; l < nq; l += 8) {
         const int c = cr + C * l;
@@ -530,7 +537,7 @@ static rfm_status launch_cluster(const HostPlan &P, void *ws, double tol, int nl
 static size_t cluster_smem(int64_t max_m, int64_t max_K, int C, int *nloc, int *ldl) {
     *ldl = (int)((max_m + 1) / 2 * 2);
     *nloc = (int)((max_K + C - 1) / C);
-    return ((size_t)(*nloc) * (*ldl) + (size_t)(*ldl)) * 8 + (size_t)(*nloc) * 20 + 64;
+    return ((size_t)(*nloc) * (*ldl) + 2 * (size_t)(*ldl)) * 8 + (size_t)(*nloc) * 20 + 64;
 }
 
 template <typename TM>
