@@ -120,7 +120,8 @@ typedef struct rfm_sizes {
     int64_t n_blocks;        /* sum of J over instances */
     int64_t n_rows;          /* sum of N = N_I + N_B */
     int64_t n_cols;          /* sum of J K (the layout of a and y) */
-    int64_t block_rows;      /* sum over blocks of |I_j| */
+    int64_t block_rows;      /* sum over blocks of |I_j| rounded up to a multiple of 32
+                                (block rows are laid out at that padded stride) */
     int64_t max_block_rows;  /* max |I_j| */
     int64_t max_K;
     int64_t workspace_bytes; /* device bytes the caller must provide */
@@ -163,6 +164,10 @@ typedef struct rfm_lsqr_opts {
                             iteration i = s*snap_every (s = 1..snap_cap) y_i is written to
                             row s-1 (kept slots only; the caller clears the buffer) */
     int32_t snap_every, snap_cap;
+    double *d_phase_ms;  /* nullable, 4 doubles: milliseconds the first CTA spent in each
+                            part of the iterations (products A x and row updates, row sums,
+                            products A^T u, scalar updates), each up to the exit of the
+                            grid barrier that closes it; for profiling */
 } rfm_lsqr_opts;
 
 /* Report per instance (written to device memory):

@@ -35,7 +35,8 @@ class RfmSizes(C.Structure):
 
 class RfmLsqrOpts(C.Structure):
     _fields_ = [("atol", C.c_double), ("btol", C.c_double), ("max_iter", C.c_int32), ("timeout_ms", C.c_int32),
-                ("d_snap", C.c_void_p), ("snap_every", C.c_int32), ("snap_cap", C.c_int32)]
+                ("d_snap", C.c_void_p), ("snap_every", C.c_int32), ("snap_cap", C.c_int32),
+                ("d_phase_ms", C.c_void_p)]
 
 
 REPORT_FIELDS = ("itn", "istop", "rnorm", "arnorm", "anorm", "ynorm", "bnorm", "status")

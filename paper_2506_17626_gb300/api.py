@@ -66,7 +66,7 @@ class System:
 
     def solve(self, atol=1e-10, btol=1e-10, max_iter=10000, y0: Optional[torch.Tensor] = None,
               timeout_ms: int = 10000, want_y: bool = False, snap: Optional[torch.Tensor] = None,
-              snap_every: int = 0):
+              snap_every: int = 0, phase_ms: Optional[torch.Tensor] = None):
         """LSQR of Algorithm 2.  snap: optional (cap, n_cols) FP64 tensor that
         receives y after every snap_every-th iteration."""
         nc = self.sizes["n_cols"]
@@ -77,7 +77,7 @@ class System:
         if snap is not None:
             assert snap.is_cuda and snap.dtype == torch.float64 and snap.shape[1] == nc and snap.is_contiguous()
         opts = N.RfmLsqrOpts(float(atol), float(btol), int(max_iter), int(timeout_ms),
-                             _ptr(snap), int(snap_every if snap is not None else 0), int(cap))
+                             _ptr(snap), int(snap_every if snap is not None else 0), int(cap), _ptr(phase_ms))
         if y0 is not None:
             assert y0.is_cuda and y0.dtype == torch.float64 and y0.numel() == nc
         N.check("rfm_lsqr_solve", self.lib.rfm_lsqr_solve(self._probs, self.n, C.byref(self._cfg), C.byref(opts),

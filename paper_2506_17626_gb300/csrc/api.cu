@@ -121,6 +121,12 @@ rfm_status rfm_assemble(const rfm_problem *probs, int n_inst, const rfm_config *
     if (L.n_cov)
         RFM_CUDA_CHECK(cudaMemcpyAsync(ws_ptr<void>(d_ws, L.off_cov), P.p.cov, sizeof(int32_t) * L.n_cov,
                                        cudaMemcpyHostToDevice, st));
+    if (L.n_fwd_items)
+        RFM_CUDA_CHECK(cudaMemcpyAsync(ws_ptr<void>(d_ws, L.off_fwd_items), P.p.fwd_items,
+                                       sizeof(int32_t) * 2 * L.n_fwd_items, cudaMemcpyHostToDevice, st));
+    if (L.n_col_items)
+        RFM_CUDA_CHECK(cudaMemcpyAsync(ws_ptr<void>(d_ws, L.off_col_items), P.p.col_items,
+                                       sizeof(int32_t) * 2 * L.n_col_items, cudaMemcpyHostToDevice, st));
     return launch_assemble(P.p, d_ws, d_params, st);
     RFM_GUARD_END
 }

@@ -55,7 +55,12 @@ __global__ void __launch_bounds__(256) k_assemble(const InstRec *__restrict__ in
     }
     __syncthreads();
     const int lr = r0 + lane;
-    if (lr >= B.m) return;
+    if (lr >= B.m) {
+        // padding rows up to the leading dimension hold zeros
+        if (lr < B.ldm)
+            for (int k = wy; k < B.K; k += 8) M[B.moff + lr + (int64_t)k * B.ldm] = (T)0;
+        return;
+    }
     const int d = I.dim;
     const T c0 = s_c0[lane];
     T c1[3], c2[3], sx[3], isg[3];
@@ -92,7 +97,7 @@ __global__ void __launch_bounds__(32) k_rowmap(const InstRec *__restrict__ insts
                                                const int32_t *__restrict__ tile_blk,
                                                const int32_t *__restrict__ tile_row,
                                                const int32_t *__restrict__ cov, int32_t *__restrict__ grow,
-                                               int32_t *__restrict__ rowlist) {
+                                               int32_t *__restrict__ rowlist, int32_t *__restrict__ qblk) {
     const int tile = blockIdx.x;
     const BlkRec &B = blks[tile_blk[tile]];
     const InstRec &I = insts[B.inst];
@@ -109,6 +114,7 @@ __global__ void __launch_bounds__(32) k_rowmap(const InstRec *__restrict__ insts
     }
     const int64_t q = B.roff + lr;
     grow[q] = (int32_t)(I.row0 + r);
+    qblk[q] = tile_blk[tile];
     rowlist[I.rl_off + r * I.C + e] = (int32_t)q;
 }
 
@@ -134,7 +140,8 @@ rfm_status launch_assemble(const HostPlan &P, void *ws, const double *params, cu
     if (L.n_tiles > 0) {
         { ProfScope ps("k_rowmap", st);
         k_rowmap<<<(unsigned)L.n_tiles, 32, 0, st>>>(dI, dB, dTB, dTR, dCov, ws_ptr<int32_t>(ws, L.off_grow),
-                                                      ws_ptr<int32_t>(ws, L.off_rowlist)); }
+                                                      ws_ptr<int32_t>(ws, L.off_rowlist),
+                                                      ws_ptr<int32_t>(ws, L.off_qblk)); }
         RFM_CUDA_CHECK(cudaGetLastError());
         ProfScope ps("k_assemble", st);
         if (L.asm_prec == RFM_ASM_FP32)

@@ -54,6 +54,12 @@ struct BlkRec {
     double mu[3], sig[3];
 };
 
+// A live column item of the LSQR kernels: columns c0 .. c0+nc of block b.
+struct ColItem {
+    int32_t b, c0, nc, m, ldm, inst;
+    int64_t moff, coff, roff;
+};
+
 // Persistent LSQR scalars, one per instance.
 struct LsqrScal {
     double alpha, beta, rhobar, phibar, anorm2, bnorm;
@@ -64,12 +70,18 @@ struct LsqrScal {
 // Offsets (bytes) of every array of a system inside the workspace.
 struct Layout {
     int n_inst;
-    int64_t n_blocks, n_rows, n_cols, block_rows, max_m, max_K, n_rowlist, n_tiles, n_cov;
+    int64_t n_blocks, n_rows, n_cols, block_rows, max_m, max_K, n_rowlist, n_tiles, n_cov;  // block_rows: padded
     size_t off_inst, off_blk, off_tile, off_cov;       // records
     size_t off_M, off_h, off_grow, off_rowlist;         // assembly
     size_t off_W, off_tau, off_perm, off_rank, off_r11, off_op, off_q32;  // filter
     size_t off_u, off_v, off_vt, off_w, off_y, off_t, off_part, off_scal, off_bar;  // lsqr
     size_t off_evpart;                                  // eval scratch
+    int64_t n_fwd_items, n_col_items;                   // LSQR tile work items
+    size_t off_fwd_items, off_col_items;
+    size_t off_items, off_nitems, off_tpart, off_qblk;  // live column items, per-item row partials, block of each block row
+    size_t off_tu;                                      // u~ on the block rows in operator precision
+    size_t off_fitems, off_nfitems;                     // live forward items (128-row tiles)
+    int64_t n_slots;                                    // column items per block at most (ceil(max_K / 8))
     size_t total;
     int asm_prec, op;
 };
@@ -84,7 +96,12 @@ struct HostPlan {
     int32_t *tile_blk;   // n_tiles: block of each 32-row tile
     int32_t *tile_row;   // n_tiles: first block-local row of the tile
     int32_t *cov;        // per-dimension cover tables: first covering subdomain, count (pairs)
+    int32_t *fwd_items;  // (block, first row) of every 128-row tile
+    int32_t *col_items;  // (block, first column) of every 8-column tile
 };
+
+constexpr int kFwdRows = 128;  // rows of a forward (A x) work item (one warp)
+constexpr int kColTile = 8;    // columns of a transpose (A^T u) work item (one warp)
 
 // Builds the plan (validates, computes records and layout).  Returns RFM_OK or
 // RFM_EINVAL with the reason in err.

@@ -46,6 +46,8 @@ struct LsqrArgs {
     double *snap;            // iterate snapshots (nullable)
     int snap_every, snap_cap;
     int64_t n_cols;
+    double *phase_ms;        // per-phase times of CTA 0 (nullable)
+    int64_t n_block_rows;
 };
 
 constexpr int kThreads = 256;
@@ -211,8 +213,18 @@ __device__ void tri_solve_upper_t(const double *__restrict__ R, int ld, int r, d
 __device__ void reduce_partials(const double *part, int n_inst, double *out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, G = gridDim.x;
     for (int s = warp; s < n_inst; s += kThreads / 32) {
+        const double *p = part + (int64_t)s * G;
         double x = 0.0;
-        for (int c = lane; c < G; c += 32) x += part[(int64_t)s * G + c];
+        for (int c0 = 0; c0 < G; c0 += 32 * 8) {
+            double v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {     // all loads in flight before the adds
+                const int c = c0 + 32 * k + lane;
+                v[k] = c < G ? p[c] : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) x += v[k];
+        }
         for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         if (lane == 0) out[s] = x;
     }
@@ -689,6 +701,551 @@ __global__ void k_report(const LsqrScal *__restrict__ sc, int n, rfm_lsqr_report
     rep[s].status = bar[2] ? (double)bar[2] : (double)q.status;
 }
 
+
+// ---------------------------------------------------------------------------
+// Tile variant for the explicit operators (Q_hat in FP32 or FP64, or the
+// unfiltered M): the work of a phase is split into small tiles spread over
+// every CTA, so all SMs stream the operator at once.
+//   forward item  = 64 rows of one block:   t[rows] = Op_b[rows, :] v_b
+//   column item   = 8 columns of one block: vt[cols] = Op_b[:, cols]^T u~ / beta - beta v
+// Each thread of a forward item owns 16 bytes of rows (4 FP32 / 2 FP64) and a
+// column group, reads the operator with 16-byte vector loads, and the column
+// groups are summed in shared memory.  A column item gathers the block's u~
+// into shared memory once and reduces one column per warp.  The column
+// updates of the Givens step (y, w) are elementwise and ride in the forward
+// phase; ||y||^2 rides in the column phase, so the stopping test of iteration
+// i is taken at the third barrier of round i+1 (with iteration i's estimates).
+// ---------------------------------------------------------------------------
+template <typename TA>
+struct TileSmem {
+    double wacc[2][kThreads / 32][64];          // per-warp partials per instance (alpha^2, ||y||^2)
+    double acc_b[kMaxInst], hacc[kMaxInst];
+    double tmp[kMaxInst], tmp2[kMaxInst], yy[kMaxInst];
+    double wred[2][8];
+    LsqrScal sc[64];
+};
+
+// Four rows of a column owned by one lane: FP32 one 16-byte load of rows
+// r0+4l..r0+4l+3; FP64 two 16-byte loads of rows r0+2l, +1 and r0+64+2l, +1.
+// Each 16-byte part is loaded only when its first row lies below the column's
+// leading dimension ldm (a multiple of 32, so the whole part then does too).
+template <typename TA>
+struct Rows4;
+template <>
+struct Rows4<float> {
+    __device__ static int row(int r0, int lane, int v) { return r0 + 4 * lane + v; }
+    __device__ static void store(float *p, int r0, int lane, int ldm, const float *s) {
+        const int i = r0 + 4 * lane;
+        if (i < ldm) *reinterpret_cast<float4 *>(p + i) = make_float4(s[0], s[1], s[2], s[3]);
+    }
+    __device__ static void load_rw(const float *p, int r0, int lane, int ldm, float *q) {
+        const int i = r0 + 4 * lane;
+        float4 t = i < ldm ? *reinterpret_cast<const float4 *>(p + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        q[0] = t.x; q[1] = t.y; q[2] = t.z; q[3] = t.w;
+    }
+    __device__ static void load(const float *col, int r0, int lane, int ldm, float *q) {
+        const int i = r0 + 4 * lane;
+        const bool in = i < ldm;
+        float4 t = __ldg(reinterpret_cast<const float4 *>(col + (in ? i : ldm - 4)));   // always a valid address
+        q[0] = in ? t.x : 0.f; q[1] = in ? t.y : 0.f; q[2] = in ? t.z : 0.f; q[3] = in ? t.w : 0.f;
+    }
+};
+template <>
+struct Rows4<double> {
+    __device__ static int row(int r0, int lane, int v) { return r0 + (v < 2 ? 2 * lane + v : 64 + 2 * lane + v - 2); }
+    __device__ static void store(double *p, int r0, int lane, int ldm, const double *s) {
+        const int i0 = r0 + 2 * lane, i1 = r0 + 64 + 2 * lane;
+        if (i0 < ldm) *reinterpret_cast<double2 *>(p + i0) = make_double2(s[0], s[1]);
+        if (i1 < ldm) *reinterpret_cast<double2 *>(p + i1) = make_double2(s[2], s[3]);
+    }
+    __device__ static void load_rw(const double *p, int r0, int lane, int ldm, double *q) {
+        const int i0 = r0 + 2 * lane, i1 = r0 + 64 + 2 * lane;
+        double2 t0 = i0 < ldm ? *reinterpret_cast<const double2 *>(p + i0) : make_double2(0.0, 0.0);
+        double2 t1 = i1 < ldm ? *reinterpret_cast<const double2 *>(p + i1) : make_double2(0.0, 0.0);
+        q[0] = t0.x; q[1] = t0.y; q[2] = t1.x; q[3] = t1.y;
+    }
+    __device__ static void load(const double *col, int r0, int lane, int ldm, double *q) {
+        const int i0 = r0 + 2 * lane, i1 = r0 + 64 + 2 * lane;
+        const bool in0 = i0 < ldm, in1 = i1 < ldm;
+        double2 t0 = __ldg(reinterpret_cast<const double2 *>(col + (in0 ? i0 : ldm - 2)));
+        double2 t1 = __ldg(reinterpret_cast<const double2 *>(col + (in1 ? i1 : ldm - 2)));
+        q[0] = in0 ? t0.x : 0.0; q[1] = in0 ? t0.y : 0.0;
+        q[2] = in1 ? t1.x : 0.0; q[3] = in1 ? t1.y : 0.0;
+    }
+};
+
+// Live column items in block order: block b contributes ceil(r_b / 8) items.
+// One CTA, deterministic prefix sum.
+__global__ void __launch_bounds__(1024) k_build_items(const BlkRec *__restrict__ blks, int n_blocks,
+                                                      const int32_t *__restrict__ rank, ColItem *__restrict__ items,
+                                                      int *__restrict__ n_items, ColItem *__restrict__ fitems,
+                                                      int *__restrict__ n_fitems) {
+    __shared__ int scan[1024];
+    __shared__ int carry;
+    const int tid = threadIdx.x;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n_blocks; base += 1024) {
+        const int b = base + tid;
+        int cnt = 0;
+        if (b < n_blocks) {
+            const int r = rank ? rank[b] : blks[b].K;
+            cnt = (r + kColTile - 1) / kColTile;
+        }
+        scan[tid] = cnt;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            const int v = tid >= off ? scan[tid - off] : 0;
+            __syncthreads();
+            scan[tid] += v;
+            __syncthreads();
+        }
+        const int start = carry + scan[tid] - cnt;
+        if (b < n_blocks) {
+            const BlkRec &B = blks[b];
+            const int r = rank ? rank[b] : B.K;
+            for (int k = 0; k < cnt; ++k) {
+                ColItem it;
+                it.b = b;
+                it.c0 = k * kColTile;
+                it.nc = min(kColTile, r - it.c0);
+                it.m = B.m;
+                it.ldm = B.ldm;
+                it.inst = B.inst;
+                it.moff = B.moff;
+                it.coff = B.coff;
+                it.roff = B.roff;
+                items[start + k] = it;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) carry += scan[1023];
+        __syncthreads();
+    }
+    if (tid == 0) *n_items = carry;
+    // forward items: every 128-row tile of every block with kept columns (nc = r)
+    __syncthreads();
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n_blocks; base += 1024) {
+        const int b = base + tid;
+        int cnt = 0, r = 0;
+        if (b < n_blocks) {
+            r = rank ? rank[b] : blks[b].K;
+            cnt = (blks[b].m + 127) / 128;   // also without kept columns: the tile writes zeros
+        }
+        scan[tid] = cnt;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            const int v = tid >= off ? scan[tid - off] : 0;
+            __syncthreads();
+            scan[tid] += v;
+            __syncthreads();
+        }
+        const int start = carry + scan[tid] - cnt;
+        if (b < n_blocks) {
+            const BlkRec &B = blks[b];
+            for (int k = 0; k < cnt; ++k) {
+                ColItem it;
+                it.b = b;
+                it.c0 = k * 128;        // first row of the tile
+                it.nc = r;              // kept columns
+                it.m = B.m;
+                it.ldm = B.ldm;
+                it.inst = B.inst;
+                it.moff = B.moff;
+                it.coff = B.coff;
+                it.roff = B.roff;
+                fitems[start + k] = it;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) carry += scan[1023];
+        __syncthreads();
+    }
+    if (tid == 0) *n_fitems = carry;
+}
+
+template <typename TA>
+__global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const ColItem *__restrict__ items,
+                                                         const int *__restrict__ n_items_p,
+                                                         const ColItem *__restrict__ fitems,
+                                                         const int *__restrict__ n_fitems_p, TA *__restrict__ tu) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TileSmem<TA> &S = *reinterpret_cast<TileSmem<TA> *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, G = gridDim.x, cta = blockIdx.x;
+    const int nwarps = kThreads / 32;
+    // worker index: consecutive items go to different CTAs (spread over every SM)
+    const int64_t gwarp = (int64_t)warp * G + cta, twarps = (int64_t)G * nwarps;
+    const int ni = a.n_inst;
+    const int64_t n_items = *n_items_p, n_fitems = *n_fitems_p;
+    const TA *Aop = reinterpret_cast<const TA *>(a.A);
+    LsqrScal *sc = S.sc;
+    bool ok = true;
+    auto blk_rank = [&](int b) { return a.rank ? __ldg(a.rank + b) : a.blks[b].K; };
+    auto clear = [&](double *p) {
+        for (int s = tid; s < ni; s += kThreads) p[s] = 0.0;
+    };
+    auto flush = [&](const double *p, int which) {
+        for (int s = tid; s < ni; s += kThreads) a.part[((int64_t)which * ni + s) * G + cta] = p[s];
+    };
+    auto clear_w = [&]() {
+        for (int i = tid; i < 2 * nwarps * 64; i += kThreads) (&S.wacc[0][0][0])[i] = 0.0;
+    };
+    auto flush_w = [&](int k, int which) {
+        for (int s = tid; s < ni; s += kThreads) {
+            double t = 0.0;
+            for (int w = 0; w < nwarps; ++w) t += S.wacc[k][w][s];
+            a.part[((int64_t)which * ni + s) * G + cta] = t;
+        }
+    };
+
+    // forward items (one warp each): t[rows] = Op_b[rows, :] x_b for a 128-row
+    // tile, 8 columns per round trip, x = src * scale(inst)
+    auto forward = [&](auto take, const double *src, auto scale_of) {
+        for (int64_t k = gwarp; k < n_fitems; k += twarps) {
+            const ColItem it = fitems[k];
+            if (!take(it.inst)) continue;
+            const double xs = scale_of(it.inst);
+            const int r0 = it.c0, r = it.nc;
+            const TA *base = Aop + it.moff;
+            const double *xb = src + it.coff;
+            TA acc[4] = {(TA)0, (TA)0, (TA)0, (TA)0};
+            constexpr int CW = kColTile;   // columns per round trip
+            int c = 0;
+            for (; c + CW <= r; c += CW) {
+                TA q[CW][4];
+                TA x[CW];
+#pragma unroll
+                for (int j = 0; j < CW; ++j) Rows4<TA>::load(base + (int64_t)(c + j) * it.ldm, r0, lane, it.ldm, q[j]);
+#pragma unroll
+                for (int j = 0; j < CW; ++j) x[j] = (TA)(xb[c + j] * xs);   // written in-kernel: coherent loads
+#pragma unroll
+                for (int j = 0; j < CW; ++j)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[v] += q[j][v] * x[j];
+            }
+            for (; c < r; ++c) {
+                TA q[4];
+                Rows4<TA>::load(base + (int64_t)c * it.ldm, r0, lane, it.ldm, q);
+                const TA x = (TA)(xb[c] * xs);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[v] += q[v] * x;
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int i = Rows4<TA>::row(r0, lane, v);
+                if (i < it.m) a.t[it.roff + i] = (double)acc[v];
+            }
+        }
+    };
+    // forward product of block row q
+    auto row_partials = [&](int64_t q) { return a.t[q]; };
+    // column items: z_c = Op_b[:, c]^T u~ (u~ of the block rows in t)
+    auto columns = [&](auto take, auto per_col) {
+        for (int64_t k = gwarp; k < n_items; k += twarps) {
+            const ColItem it = items[k];
+            if (!take(it.inst)) continue;
+            TA acc[kColTile];
+#pragma unroll
+            for (int j = 0; j < kColTile; ++j) acc[j] = (TA)0;
+            const TA *base = Aop + it.moff + (int64_t)it.c0 * it.ldm;
+            constexpr int H = sizeof(TA) == 4 ? 2 : 1;   // 128-row chunks per round trip (64 registers of loads)
+            for (int r0 = 0; r0 < it.m; r0 += 128 * H) {
+                TA uv[H][4];
+                TA q[H][kColTile][4];
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    Rows4<TA>::load_rw(tu + it.roff, r0 + 128 * h, lane, it.ldm, uv[h]);
+#pragma unroll
+                    for (int j = 0; j < kColTile; ++j) {
+                        if (j < it.nc && r0 + 128 * h < it.m) {
+                            Rows4<TA>::load(base + (int64_t)j * it.ldm, r0 + 128 * h, lane, it.ldm, q[h][j]);
+                        } else {
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) q[h][j][v] = (TA)0;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < H; ++h)
+#pragma unroll
+                    for (int j = 0; j < kColTile; ++j)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) acc[j] += q[h][j][v] * uv[h][v];
+            }
+            double mine = 0.0;
+#pragma unroll
+            for (int j = 0; j < kColTile; ++j) {
+                TA s = acc[j];
+                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == j) mine = (double)s;
+            }
+            double pa = 0.0, py = 0.0;
+            if (lane < it.nc) per_col(it.inst, it.coff + it.c0 + lane, mine, &pa, &py);
+            for (int o = 16; o; o >>= 1) {
+                pa += __shfl_xor_sync(0xffffffffu, pa, o);
+                py += __shfl_xor_sync(0xffffffffu, py, o);
+            }
+            if (lane == 0) {
+                S.wacc[0][warp][it.inst] += pa;
+                S.wacc[1][warp][it.inst] += py;
+            }
+        }
+    };
+    // elementwise over the kept column slots
+    auto each_column = [&](auto take, auto fn) {
+        const int64_t total = n_items * kColTile;
+        for (int64_t f = (int64_t)cta * kThreads + tid; f < total; f += (int64_t)G * kThreads) {
+            const ColItem &it = items[f / kColTile];
+            const int j = (int)(f % kColTile);
+            if (j >= it.nc || !take(it.inst)) continue;
+            fn(it.inst, it.coff + it.c0 + j);
+        }
+    };
+    auto all_inst = [&](int) { return true; };
+    auto live = [&](int s) { return !sc[s].done; };
+    auto row_tile_inst = [&](int64_t T, int64_t *tcount) {
+        int s = 0;
+        int64_t tc = 0;
+        for (; s < ni; ++s) {
+            int64_t nt = (a.insts[s].N + kRowTile - 1) / kRowTile;
+            if (T < tc + nt) break;
+            tc += nt;
+        }
+        *tcount = tc;
+        return s;
+    };
+
+    // ------------------------------------------------------------ init
+    for (int s = tid; s < ni; s += kThreads) {
+        LsqrScal z;
+        memset(&z, 0, sizeof(z));
+        sc[s] = z;
+    }
+    __syncthreads();
+    each_column(all_inst, [&](int inst, int64_t o) {
+        a.y[o] = a.y0 ? a.y0[o] : 0.0;
+        a.w[o] = 0.0;
+    });
+    if (a.y0) forward(all_inst, a.y0, [](int) { return 1.0; });
+    ok = grid_sync(a.bar, a.timeout_ns);
+    // u~ = h - (Op y0), ||u~||^2, ||h||^2; u~ copied onto the block rows
+    clear(S.acc_b);
+    clear(S.hacc);
+    __syncthreads();
+    for (int64_t T = cta; T < a.n_row_tiles; T += G) {
+        int64_t tc;
+        const int s = row_tile_inst(T, &tc);
+        const InstRec &I = a.insts[s];
+        const int64_t r = (T - tc) * kRowTile + tid;
+        double uu = 0.0, hh = 0.0;
+        if (r < I.N) {
+            const int64_t gr = I.row0 + r;
+            const int32_t *lst = a.rowlist + I.rl_off + r * I.C;
+            double acc = 0.0;
+            if (a.y0)
+                for (int e = 0; e < I.C; ++e) {
+                    int q = lst[e];
+                    if (q >= 0) acc += row_partials(q);
+                }
+            const double hv = a.h[gr], uv = hv - acc;
+            a.u[gr] = uv;
+            for (int e = 0; e < I.C; ++e) {
+                int q = lst[e];
+                if (q >= 0) tu[q] = (TA)uv;
+            }
+            uu = uv * uv;
+            hh = hv * hv;
+        }
+        double s1 = cta_sum(uu, S.wred[0]);
+        double s2 = cta_sum(hh, S.wred[0]);
+        if (tid == 0) { S.acc_b[s] += s1; S.hacc[s] += s2; }
+    }
+    __syncthreads();
+    flush(S.acc_b, 1);
+    flush(S.hacc, 0);
+    ok = ok && grid_sync(a.bar, a.timeout_ns);
+    if (!ok) return;
+    reduce_partials(a.part + (int64_t)ni * G, ni, S.tmp);
+    reduce_partials(a.part, ni, S.tmp2);
+    for (int s = tid; s < ni; s += kThreads) {
+        sc[s].beta = sqrt(S.tmp[s]);
+        sc[s].bnorm = sqrt(S.tmp2[s]);
+    }
+    __syncthreads();
+    // vt = Op^T u~ / beta, ||vt||^2
+    clear_w();
+    __syncthreads();
+    columns(all_inst, [&](int inst, int64_t o, double z, double *pa, double *py) {
+        const double beta = sc[inst].beta;
+        const double x = beta > 0.0 ? z / beta : 0.0;
+        a.vt[o] = x;
+        *pa = x * x;
+    });
+    __syncthreads();
+    flush_w(0, 2);
+    ok = grid_sync(a.bar, a.timeout_ns);
+    if (!ok) return;
+    reduce_partials(a.part + (int64_t)2 * ni * G, ni, S.tmp);
+    for (int s = tid; s < ni; s += kThreads) {
+        LsqrScal &q = sc[s];
+        q.alpha = sqrt(S.tmp[s]);
+        q.phibar = q.beta;
+        q.rhobar = q.alpha;
+        q.rnorm = q.beta;
+        q.arnorm = q.alpha * q.beta;
+        q.istop = 7;
+        q.itn = 0;
+        q.done = (q.beta == 0.0 || q.alpha == 0.0) ? 1 : 0;
+        if (q.done) q.istop = 0;
+    }
+    __syncthreads();
+
+    // ------------------------------------------------------------ rounds
+    // Round n: F applies iteration n-1's update of y, w (n = 1: w = v_1) and
+    // forms Op v_n; R and T continue the bidiagonalisation; at the third
+    // barrier iteration n-1 is tested, then iteration n's rotation is formed.
+    uint64_t tph = global_ns();
+    double ph[4] = {0.0, 0.0, 0.0, 0.0};
+    auto mark = [&](int k) {
+        const uint64_t t = global_ns();
+        ph[k] += (double)(t - tph) * 1e-6;
+        tph = t;
+    };
+    for (int n = 1;; ++n) {
+        const bool first = n == 1;
+        // F
+        each_column(live, [&](int inst, int64_t o) {
+            const LsqrScal &q = sc[inst];
+            const double vn = a.vt[o] * (q.alpha > 0.0 ? 1.0 / q.alpha : 0.0);
+            if (first) {
+                a.w[o] = vn;
+            } else {
+                const double wo = a.w[o];
+                const double yv = fma(q.phi_rho, wo, a.y[o]);
+                a.y[o] = yv;
+                a.w[o] = fma(-q.theta_rho, wo, vn);
+                if (a.snap && q.itn % a.snap_every == 0 && q.itn / a.snap_every <= a.snap_cap)
+                    a.snap[(int64_t)(q.itn / a.snap_every - 1) * a.n_cols + o] = yv;
+            }
+        });
+        forward(live, a.vt, [&](int inst) {
+            const double al = sc[inst].alpha;
+            return al > 0.0 ? 1.0 / al : 0.0;
+        });
+        ok = grid_sync(a.bar, a.timeout_ns);
+        mark(0);
+        if (!ok) break;
+        // R: u~ = sum of the block partials - (alpha/beta) u~
+        clear(S.acc_b);
+        __syncthreads();
+        for (int64_t T = cta; T < a.n_row_tiles; T += G) {
+            int64_t tc;
+            const int s = row_tile_inst(T, &tc);
+            const LsqrScal &q = sc[s];
+            if (q.done) continue;
+            const InstRec &I = a.insts[s];
+            const int64_t r = (T - tc) * kRowTile + tid;
+            double uu = 0.0;
+            if (r < I.N) {
+                const int64_t gr = I.row0 + r;
+                const int32_t *lst = a.rowlist + I.rl_off + r * I.C;
+                double acc = 0.0;
+                for (int e = 0; e < I.C; ++e) {
+                    int qq = lst[e];
+                    if (qq >= 0) acc += row_partials(qq);
+                }
+                const double ab = q.beta > 0.0 ? q.alpha / q.beta : 0.0;
+                const double uv = fma(-ab, a.u[gr], acc);
+                a.u[gr] = uv;
+                for (int e = 0; e < I.C; ++e) {
+                    int qq = lst[e];
+                    if (qq >= 0) tu[qq] = (TA)uv;
+                }
+                uu = uv * uv;
+            }
+            double s1 = cta_sum(uu, S.wred[0]);
+            if (tid == 0) S.acc_b[s] += s1;
+        }
+        __syncthreads();
+        flush(S.acc_b, 1);
+        ok = grid_sync(a.bar, a.timeout_ns);
+        mark(1);
+        if (!ok) break;
+        reduce_partials(a.part + (int64_t)ni * G, ni, S.tmp);   // beta_{n+1}^2
+        // T: vt = Op^T u~ / beta_new - beta_new v_n ; ||vt||^2 ; ||y_{n-1}||^2
+        clear_w();
+        __syncthreads();
+        columns(live, [&](int inst, int64_t o, double z, double *pa, double *py) {
+            const LsqrScal &q = sc[inst];
+            const double bn = sqrt(S.tmp[inst]);
+            const double vn = a.vt[o] * (q.alpha > 0.0 ? 1.0 / q.alpha : 0.0);
+            const double x = (bn > 0.0 ? z / bn : 0.0) - bn * vn;
+            a.vt[o] = x;
+            *pa = x * x;
+            const double yv = a.y[o];
+            *py = yv * yv;
+        });
+        __syncthreads();
+        flush_w(0, 2);
+        flush_w(1, 0);
+        ok = grid_sync(a.bar, a.timeout_ns);
+        mark(2);
+        if (!ok) break;
+        reduce_partials(a.part + (int64_t)2 * ni * G, ni, S.tmp2);   // alpha_{n+1}^2
+        reduce_partials(a.part, ni, S.yy);                           // ||y_{n-1}||^2
+        __shared__ int s_all_done;
+        if (tid == 0) s_all_done = 1;
+        __syncthreads();
+        for (int s = tid; s < ni; s += kThreads) {
+            LsqrScal &q = sc[s];
+            if (q.done) continue;
+            if (!first) {
+                q.ynorm = sqrt(S.yy[s]);
+                if (q.rnorm <= a.btol * q.bnorm + a.atol * sqrt(q.anorm2) * q.ynorm) { q.done = 1; q.istop = 1; }
+                else if (q.arnorm <= a.atol * sqrt(q.anorm2) * q.rnorm) { q.done = 1; q.istop = 2; }
+                else if (n - 1 >= a.max_iter) { q.done = 1; q.istop = 7; }
+            } else if (a.max_iter == 0) {
+                q.done = 1;
+                q.istop = 7;
+            }
+            if (q.done) continue;
+            q.itn = n;
+            const double beta = sqrt(S.tmp[s]);
+            const double alpha = sqrt(S.tmp2[s]);
+            q.anorm2 += q.alpha * q.alpha + beta * beta;
+            const double rho = sqrt(q.rhobar * q.rhobar + beta * beta);
+            const double c = rho > 0.0 ? q.rhobar / rho : 1.0;
+            const double sn = rho > 0.0 ? beta / rho : 0.0;
+            const double theta = sn * alpha;
+            q.rhobar = -c * alpha;
+            const double phi = c * q.phibar;
+            q.phibar = sn * q.phibar;
+            q.phi_rho = rho > 0.0 ? phi / rho : 0.0;
+            q.theta_rho = rho > 0.0 ? theta / rho : 0.0;
+            q.rnorm = q.phibar;
+            q.arnorm = q.phibar * alpha * fabs(c);
+            q.c = c;
+            q.alpha = alpha;
+            q.beta = beta;
+            if (!isfinite(q.phibar) || !isfinite(q.rhobar) || !isfinite(q.phi_rho) || !isfinite(q.anorm2)) {
+                q.done = 1;
+                q.status = RFM_ENUMERIC;
+            }
+            atomicAnd(&s_all_done, 0);
+        }
+        __syncthreads();
+        mark(3);
+        if (s_all_done) break;
+    }
+    if (cta == 0) {
+        for (int s = tid; s < ni; s += kThreads) a.scal[s] = sc[s];
+        if (a.phase_ms && tid == 0)
+            for (int k = 0; k < 4; ++k) a.phase_ms[k] = ph[k];
+    }
+}
+
 rfm_status launch_coefficients(const HostPlan &P, void *ws, const double *y, double *a_out, cudaStream_t st) {
     const Layout &L = P.L;
     if (L.n_blocks == 0) return RFM_OK;
@@ -698,6 +1255,40 @@ rfm_status launch_coefficients(const HostPlan &P, void *ws, const double *y, dou
         ws_ptr<BlkRec>(ws, L.off_blk), ws_ptr<double>(ws, L.off_W), plain ? nullptr : ws_ptr<int32_t>(ws, L.off_rank),
         plain ? nullptr : ws_ptr<int32_t>(ws, L.off_perm), y, a_out, plain ? 0 : 1);
     RFM_CUDA_CHECK(cudaGetLastError());
+    return RFM_OK;
+}
+
+template <typename TA>
+static rfm_status run_lsqr_tiles(const HostPlan &P, void *ws, LsqrArgs &args, cudaStream_t st) {
+    int dev = 0, nsm = 0, per = 0;
+    RFM_CUDA_CHECK(cudaGetDevice(&dev));
+    RFM_CUDA_CHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const Layout &L = P.L;
+    ColItem *items = ws_ptr<ColItem>(ws, L.off_items);
+    int *nitems = ws_ptr<int>(ws, L.off_nitems);
+    {
+        ProfScope ps("k_build_items", st);
+        k_build_items<<<1, 1024, 0, st>>>(args.blks, args.n_blocks, args.rank, items, nitems,
+                                          ws_ptr<ColItem>(ws, L.off_fitems), ws_ptr<int>(ws, L.off_nfitems));
+        RFM_CUDA_CHECK(cudaGetLastError());
+    }
+    const size_t sm = sizeof(TileSmem<TA>);
+    RFM_CUDA_CHECK(cudaFuncSetAttribute(k_lsqr_tiles<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    RFM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lsqr_tiles<TA>, kThreads, sm));
+    if (per < 1) {
+        set_error("LSQR kernel does not fit on an SM");
+        return RFM_ECUDA;
+    }
+    int G = nsm * per;
+    if (G > kMaxPersistCtas) G = kMaxPersistCtas;
+    TA *tu = ws_ptr<TA>(ws, L.off_tu);
+    // padding block rows of u~ are never written by the row phase: keep them zero
+    RFM_CUDA_CHECK(cudaMemsetAsync(tu, 0, sizeof(TA) * (size_t)L.block_rows, st));
+    const ColItem *citems = items, *cfitems = ws_ptr<ColItem>(ws, L.off_fitems);
+    const int *cn = nitems, *cfn = ws_ptr<int>(ws, L.off_nfitems);
+    void *kargs[] = {&args, (void *)&citems, (void *)&cn, (void *)&cfitems, (void *)&cfn, (void *)&tu};
+    ProfScope ps("k_lsqr", st);
+    RFM_CUDA_CHECK(cudaLaunchCooperativeKernel((const void *)k_lsqr_tiles<TA>, dim3(G), dim3(kThreads), kargs, sm, st));
     return RFM_OK;
 }
 
@@ -765,6 +1356,8 @@ rfm_status launch_lsqr(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, c
     for (int s = 0; s < L.n_inst; ++s) nt += (P.inst[s].N + kRowTile - 1) / kRowTile;
     A.n_row_tiles = nt;
     A.n_cols = L.n_cols;
+    A.phase_ms = opts->d_phase_ms;
+    A.n_block_rows = L.block_rows;
     if (opts->d_snap && opts->snap_every > 0 && opts->snap_cap > 0) {
         A.snap = opts->d_snap;
         A.snap_every = opts->snap_every;
@@ -774,19 +1367,19 @@ rfm_status launch_lsqr(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, c
     rfm_status rc;
     if (L.op == RFM_OP_Q32) {
         A.A = ws_ptr<float>(ws, L.off_q32);
-        rc = run_lsqr<float, false>(P, ws, A, st);
+        rc = run_lsqr_tiles<float>(P, ws, A, st);
     } else if (L.op == RFM_OP_Q64) {
         A.A = ws_ptr<double>(ws, L.off_op);
-        rc = run_lsqr<double, false>(P, ws, A, st);
+        rc = run_lsqr_tiles<double>(P, ws, A, st);
     } else if (L.op == RFM_OP_AR64) {
         A.A = ws_ptr<double>(ws, L.off_op);
         rc = run_lsqr<double, true>(P, ws, A, st);
     } else if (L.asm_prec == RFM_ASM_FP32) {
         A.A = ws_ptr<float>(ws, L.off_M);
-        rc = run_lsqr<float, false>(P, ws, A, st);
+        rc = run_lsqr_tiles<float>(P, ws, A, st);
     } else {
         A.A = ws_ptr<double>(ws, L.off_M);
-        rc = run_lsqr<double, false>(P, ws, A, st);
+        rc = run_lsqr_tiles<double>(P, ws, A, st);
     }
     if (rc != RFM_OK) return rc;
     if (y_out) RFM_CUDA_CHECK(cudaMemcpyAsync(y_out, A.y, sizeof(double) * L.n_cols, cudaMemcpyDeviceToDevice, st));

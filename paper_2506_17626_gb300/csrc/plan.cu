@@ -56,7 +56,7 @@ rfm_status build_plan(const rfm_problem *probs, int n_inst, const rfm_config *cf
     }
     std::vector<InstRec> inst(n_inst);
     std::vector<BlkRec> blk;
-    std::vector<int32_t> tile_blk, tile_row, cov;
+    std::vector<int32_t> tile_blk, tile_row, cov, fwd_items, col_items;
     int64_t row0 = 0, col0 = 0, prm0 = 0, rl0 = 0, moff = 0, roff = 0, max_m = 0, max_K = 0;
 
     for (int s = 0; s < n_inst; ++s) {
@@ -202,12 +202,20 @@ rfm_status build_plan(const rfm_problem *probs, int n_inst, const rfm_config *cf
             B.roff = roff;
             B.coff = col0 + j * p.K;
             moff += (int64_t)B.ldm * p.K;
-            roff += m;
+            roff += B.ldm;   // block rows at the padded stride: every block starts 128-byte aligned
             max_m = m > max_m ? m : max_m;
             int32_t bi = (int32_t)blk.size();
             for (int64_t r = 0; r < m; r += 32) {
                 tile_blk.push_back(bi);
                 tile_row.push_back((int32_t)r);
+            }
+            for (int64_t r = 0; r < m; r += kFwdRows) {
+                fwd_items.push_back(bi);
+                fwd_items.push_back((int32_t)r);
+            }
+            for (int c = 0; c < p.K; c += kColTile) {
+                col_items.push_back(bi);
+                col_items.push_back(c);
             }
             blk.push_back(B);
         }
@@ -259,6 +267,18 @@ rfm_status build_plan(const rfm_problem *probs, int n_inst, const rfm_config *cf
     L.off_scal = take(sizeof(LsqrScal) * n_inst);
     L.off_bar = take(256);
     L.off_evpart = take(sizeof(double) * 4 * 1024 * n_inst);
+    L.n_fwd_items = (int64_t)fwd_items.size() / 2;
+    L.n_col_items = (int64_t)col_items.size() / 2;
+    L.off_fwd_items = take(sizeof(int32_t) * (fwd_items.size() + 2));
+    L.off_col_items = take(sizeof(int32_t) * (col_items.size() + 2));
+    L.n_slots = (max_K + kColTile - 1) / kColTile;
+    L.off_items = take(sizeof(ColItem) * (L.n_col_items + 1));
+    L.off_nitems = take(256);
+    L.off_tpart = take(sizeof(double) * L.n_slots * roff);
+    L.off_qblk = take(sizeof(int32_t) * (roff + 1));
+    L.off_tu = take(sizeof(double) * (roff + 1));
+    L.off_fitems = take(sizeof(ColItem) * (L.n_fwd_items + 1));
+    L.off_nfitems = take(256);
     L.total = o;
 
     out->inst = (InstRec *)malloc(sizeof(InstRec) * n_inst);
@@ -266,6 +286,10 @@ rfm_status build_plan(const rfm_problem *probs, int n_inst, const rfm_config *cf
     out->tile_blk = (int32_t *)malloc(sizeof(int32_t) * 2 * (tile_blk.size() + 1));
     out->tile_row = out->tile_blk + tile_blk.size();
     out->cov = (int32_t *)malloc(sizeof(int32_t) * (cov.size() + 1));
+    out->fwd_items = (int32_t *)malloc(sizeof(int32_t) * (fwd_items.size() + 2));
+    out->col_items = (int32_t *)malloc(sizeof(int32_t) * (col_items.size() + 2));
+    if (!fwd_items.empty()) memcpy(out->fwd_items, fwd_items.data(), sizeof(int32_t) * fwd_items.size());
+    if (!col_items.empty()) memcpy(out->col_items, col_items.data(), sizeof(int32_t) * col_items.size());
     memcpy(out->inst, inst.data(), sizeof(InstRec) * n_inst);
     if (!blk.empty()) memcpy(out->blk, blk.data(), sizeof(BlkRec) * blk.size());
     if (!tile_blk.empty()) {
@@ -281,6 +305,8 @@ void free_plan(HostPlan *p) {
     free(p->blk);
     free(p->tile_blk);
     free(p->cov);
+    free(p->fwd_items);
+    free(p->col_items);
     memset(p, 0, sizeof(*p));
 }
 

@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256) k_gather_kept(const BlkRec *__restrict__ 
     for (int c = warp; c < r; c += 8) {
         const TM *src = M + B.moff + (int64_t)perm[B.coff + c] * B.ldm;
         double *dst = Op + B.moff + (int64_t)c * B.ldm;
-        for (int i = lane; i < B.m; i += 32) dst[i] = (double)src[i];
+        for (int i = lane; i < B.ldm; i += 32) dst[i] = i < B.m ? (double)src[i] : 0.0;
     }
 }
 
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(256) k_form_q(const BlkRec *__restrict__ blks,
     double *Qb = Q + B.moff;
     const double *Wb = W + B.moff;
     for (int c = warp; c < r; c += 8)
-        for (int i = lane; i < m; i += 32) Qb[(int64_t)c * ld + i] = (i == c) ? 1.0 : 0.0;
+        for (int i = lane; i < ld; i += 32) Qb[(int64_t)c * ld + i] = (i == c && i < m) ? 1.0 : 0.0;
     __syncthreads();
     for (int k = r - 1; k >= 0; --k) {
         const double tk = tau[B.coff + k];
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(256) k_form_q(const BlkRec *__restrict__ blks,
     if (Q32) {
         float *q32 = Q32 + B.moff;
         for (int c = warp; c < r; c += 8)
-            for (int i = lane; i < m; i += 32) q32[(int64_t)c * ld + i] = (float)Qb[(int64_t)c * ld + i];
+            for (int i = lane; i < ld; i += 32) q32[(int64_t)c * ld + i] = i < m ? (float)Qb[(int64_t)c * ld + i] : 0.f;
     }
 }
 
@@ -499,8 +499,8 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
     }
     for (int l = warp; l < nq; l += 8) {
         const int c = cr + C * l;
-        for (int i = lane; i < m; i += 32) {
-            const double qv = A[(size_t)l * ld_loc + i];
+        for (int i = lane; i < ld; i += 32) {     // rows m..ld-1 are padding: zeros
+            const double qv = i < m ? A[(size_t)l * ld_loc + i] : 0.0;
             if (Q32) Q32[B.moff + (int64_t)c * ld + i] = (float)qv;
             else Qout[B.moff + (int64_t)c * ld + i] = qv;
         }

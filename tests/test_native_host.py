@@ -49,13 +49,14 @@ def test_block_row_counts_match_oracle(native, p):
     z = oracle.sizes(p)
     assert sz.n_rows == z["N"] and sz.n_blocks == z["J"] and sz.n_cols == z["J"] * p.K
     rows = [len(oracle.block_rows(p, j)) for j in range(p.J)]
-    assert sz.block_rows == sum(rows) and sz.max_block_rows == max(rows)
+    padded = [(r + 31) // 32 * 32 for r in rows]
+    assert sz.block_rows == sum(padded) and sz.max_block_rows == max(rows)
     L = native.load()
     for j in range(p.J):
         m, ld, moff, roff = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
         assert L.rfm_block_info(arr, 1, C.byref(cfg), j, C.byref(m), C.byref(ld), C.byref(moff), C.byref(roff)) == 0
-        assert m.value == rows[j] and ld.value % 32 == 0 and ld.value >= m.value
-        assert roff.value == sum(rows[:j])
+        assert m.value == rows[j] and ld.value == padded[j]
+        assert roff.value == sum(padded[:j])
 
 
 def test_multi_instance_sizes_add_up(native):
