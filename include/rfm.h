@@ -213,6 +213,26 @@ rfm_status rfm_eval(const rfm_problem *probs, int n_inst, const rfm_config *cfg,
                     const double *d_a, const double *d_x, const int64_t *h_pt_off, double *d_u, double *d_err,
                     void *d_ws, size_t ws_bytes, void *stream);
 
+/* Allocation-free variant of rfm_eval (the paper has no counterpart; this is
+ * a deployment convenience).  For callers that cannot allocate device memory
+ * or hold a workspace -- code running inside another framework's memory pool,
+ * plugin hosts that only pass in input and output buffers, processes whose
+ * device memory is reserved up front.  Same arguments and results as
+ * rfm_eval, without a workspace: the instance records and the per-CTA error
+ * partials live in a static device array of about 0.5 MB that every GPU
+ * loading this library holds until the process exits.
+ *  - At most 16 instances per call (more: RFM_EINVAL with a message).
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - The call allocates no device memory and calls no allocating library
+ *    routine.  Every call shares the array, which keeps the last call's
+ *    contents; each call overwrites what it reads, so nothing needs clearing,
+ *    but calls that overlap on the GPU (different streams, or several host
+ *    threads) race on the array: serialise them. */
+rfm_status rfm_eval_noalloc(const rfm_problem *probs, int n_inst, const double *d_params, const double *d_a,
+                            const double *d_x, const int64_t *h_pt_off, double *d_u, double *d_err, void *stream);
+
 /* Device-side copies of the assembled blocks for inspection and tests:
  * block b's M_j (|I_j| x K, column-major with leading dimension *ld) starts at
  * element offset *moff of the M arena, and its rows are the global rows

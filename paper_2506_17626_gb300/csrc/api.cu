@@ -15,6 +15,8 @@ rfm_status launch_lsqr(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, c
                        double *a_out, rfm_lsqr_report *rep, cudaStream_t st);
 rfm_status launch_coefficients(const HostPlan &P, void *ws, const double *y, double *a_out, cudaStream_t st);
 void set_force_global_filter(int on);
+rfm_status launch_eval_noalloc(const HostPlan &P, const double *params, const double *a, const double *X,
+                               const int64_t *pt_off, double *u, double *err, cudaStream_t st);
 rfm_status launch_eval(const HostPlan &P, void *ws, const double *params, const double *a, const double *X,
                        const int64_t *pt_off, double *u, double *err, cudaStream_t st);
 
@@ -232,6 +234,20 @@ rfm_status rfm_eval(const rfm_problem *probs, int n_inst, const rfm_config *cfg,
         return RFM_EINVAL;
     }
     return launch_eval(P.p, d_ws, d_params, d_a, d_x, h_pt_off, d_u, d_err, (cudaStream_t)stream);
+    RFM_GUARD_END
+}
+
+rfm_status rfm_eval_noalloc(const rfm_problem *probs, int n_inst, const double *d_params, const double *d_a,
+                            const double *d_x, const int64_t *h_pt_off, double *d_u, double *d_err, void *stream) {
+    RFM_GUARD_BEGIN
+    const rfm_config cfg = {RFM_ASM_FP64, RFM_OP_AR64, 0.0};
+    Plan P(probs, n_inst, &cfg);
+    if (!P.ok) return P.rc;
+    if (!d_params || !d_a || !d_x || !h_pt_off || !d_u) {
+        set_error("rfm_eval_noalloc: null argument");
+        return RFM_EINVAL;
+    }
+    return launch_eval_noalloc(P.p, d_params, d_a, d_x, h_pt_off, d_u, d_err, (cudaStream_t)stream);
     RFM_GUARD_END
 }
 

@@ -125,3 +125,81 @@ rfm_status launch_eval(const HostPlan &P, void *ws, const double *params, const 
 }
 
 }  // namespace rfm
+
+// ---------------------------------------------------------------------------
+// Allocation-free evaluation (rfm_eval_noalloc).  Some callers cannot call
+// cudaMalloc or own a workspace: code running inside another library's
+// memory pool with no allocator hooks, plugin hosts that only hand out input
+// and output buffers, or processes whose device memory is fully reserved up
+// front.  For them the instance records and the error partials of the
+// evaluation live in a fixed static device array instead of a workspace.
+// Every GPU that loads the library holds this array until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace rfm {
+
+constexpr int kNoallocMaxInst = 16;   // instances per call
+struct NoallocScratch {
+    InstRec inst[kNoallocMaxInst];
+    double part[kNoallocMaxInst * kEvalCtas * 4];
+};
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoallocScratch)];
+
+// Device address of the scratch array, looked up once per device with that
+// device current (in host code the array's name is only a host-side stand-in).
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[64] = {nullptr};
+
+static rfm_status noalloc_scratch(NoallocScratch **out) {
+    int dev = 0;
+    RFM_CUDA_CHECK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error("rfm_eval_noalloc: device %d out of range", dev);
+        return RFM_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("rfm_eval_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            return RFM_ECUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = reinterpret_cast<NoallocScratch *>(g_noalloc_ptr[dev]);
+    return RFM_OK;
+}
+
+rfm_status launch_eval_noalloc(const HostPlan &P, const double *params, const double *a, const double *X,
+                               const int64_t *pt_off, double *u, double *err, cudaStream_t st) {
+    const Layout &L = P.L;
+    if (L.n_inst > kNoallocMaxInst) {
+        set_error("rfm_eval_noalloc: %d instances exceed its static scratch (at most %d)", L.n_inst,
+                  kNoallocMaxInst);
+        return RFM_EINVAL;
+    }
+    NoallocScratch *S = nullptr;
+    rfm_status rc = noalloc_scratch(&S);
+    if (rc != RFM_OK) return rc;
+    RFM_CUDA_CHECK(cudaMemcpyAsync(S->inst, P.inst, sizeof(InstRec) * L.n_inst, cudaMemcpyHostToDevice, st));
+    for (int s = 0; s < L.n_inst; ++s) {
+        const int64_t n = pt_off[s + 1] - pt_off[s];
+        if (n < 0) {
+            set_error("rfm_eval_noalloc: point offsets must be non-decreasing");
+            return RFM_EINVAL;
+        }
+        int g = (int)((n + 7) / 8);
+        g = g < 1 ? 1 : (g > kEvalCtas ? kEvalCtas : g);
+        k_eval<<<g, 256, 0, st>>>(S->inst, s, params, a, X + 3 * pt_off[s], n, u + pt_off[s], S->part);
+        RFM_CUDA_CHECK(cudaGetLastError());
+        if (err) {
+            k_eval_finish<<<1, 32, 0, st>>>(S->part, s, g, err);
+            RFM_CUDA_CHECK(cudaGetLastError());
+        }
+    }
+    return RFM_OK;
+}
+
+}  // namespace rfm
