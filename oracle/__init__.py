@@ -20,17 +20,17 @@ from typing import List, Optional
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "rfm_oracle.c")
+_SRCS = [os.path.join(_HERE, "rfm_oracle.c"), os.path.join(_HERE, "mlp_oracle.c")]
 _SO = os.path.join(_HERE, "_build", "librfm_oracle.so")
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, no host-specific flags)."""
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(os.path.getmtime(s) for s in _SRCS):
         os.makedirs(os.path.dirname(_SO), exist_ok=True)
         tmp = _SO + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-ffp-contract=off",
-                               "-o", tmp, _SRC, "-lm"])
+                               "-o", tmp] + _SRCS + ["-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -75,6 +75,11 @@ def lib():
             "orc_coefficients": (None, [i64, C.c_int, vp, vp, vp, vp, vp, vp, vp]),
             "orc_eval": (None, [P, vp, vp, i64, vp, vp]),
             "orc_exact_many": (None, [P, i64, vp, vp]),
+            "orc_feature_values": (None, [P, vp, i64, i64, vp, vp]),
+            "orc_mlp_nparams": (i64, [C.c_int, vp]),
+            "orc_mlp_forward": (None, [C.c_int, vp, vp, i64, vp, vp]),
+            "orc_mlp_grad": (dbl, [C.c_int, vp, vp, i64, vp, vp, vp]),
+            "orc_adam_step": (None, [i64, vp, vp, vp, vp, C.c_int, dbl, dbl, dbl, dbl]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -407,3 +412,80 @@ def solve(p, params, tol=1e-10, atol=1e-10, btol=1e-10, max_iter=10000, mode=0, 
     res = S.lsqr(B.h, y0=y0, atol=atol, btol=btol, max_iter=max_iter, history=history)
     a = S.coefficients(res["y"])
     return dict(blocks=B, filt=F, system=S, a=a, **res)
+
+
+# ---------------------------------------------------------------------------
+# learned warm start: the network (plain loops in mlp_oracle.c) and the local
+# fit of a predicted solution through each block's kept features
+# ---------------------------------------------------------------------------
+
+def feature_values(p, params, j, X):
+    """phi_jk(x) for the K features of subdomain j at points X (npts x dim)."""
+    s = problem_struct(p)
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, p.dim)
+    Phi = np.zeros((len(X), p.K), order="F")
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    lib().orc_feature_values(C.byref(s), _p(params), int(j), len(X), _p(X), Phi.ctypes.data_as(C.c_void_p))
+    return Phi
+
+
+def _widths(widths):
+    return (C.c_int * len(widths))(*[int(w) for w in widths])
+
+
+def mlp_nparams(widths) -> int:
+    return int(lib().orc_mlp_nparams(len(widths) - 1, _widths(widths)))
+
+
+def mlp_forward(widths, theta, X):
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, widths[0])
+    theta = np.ascontiguousarray(theta, dtype=np.float64)
+    Y = np.zeros(len(X))
+    lib().orc_mlp_forward(len(widths) - 1, _widths(widths), _p(theta), len(X), _p(X), _p(Y))
+    return Y
+
+
+def mlp_grad(widths, theta, X, T):
+    """(loss, gradient) of the mean squared error over the batch."""
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, widths[0])
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    theta = np.ascontiguousarray(theta, dtype=np.float64)
+    g = np.zeros(len(theta))
+    loss = lib().orc_mlp_grad(len(widths) - 1, _widths(widths), _p(theta), len(X), _p(X), _p(T), _p(g))
+    return float(loss), g
+
+
+def adam_step(theta, m, v, g, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step in place on float64 arrays theta, m, v."""
+    for a in (theta, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    lib().orc_adam_step(len(theta), _p(theta), _p(m), _p(v), _p(g), int(t), float(lr), float(b1), float(b2),
+                        float(eps))
+
+
+def local_fit(p, params, B: Blocks, F, uhat, tol_fit=1e-10):
+    """Warm start from predicted values: for every block j, the least-squares
+    fit of the predictions uhat[j] at the block's rows through the values of
+    its kept features (in pivot order), truncated by QR with column pivoting
+    at tol_fit relative to |R_11|; then y0_j = R_j c_j, so that the
+    preconditioned unknowns start at the fitted coefficients (a = S^-1 y).
+    Returns the list of y0_j and the list of fitted coefficients c_j."""
+    ys, cs = [], []
+    for j, (g, f) in enumerate(zip(B.grow, F)):
+        r = f.rank
+        if r == 0:
+            ys.append(np.zeros(0))
+            cs.append(np.zeros(0))
+            continue
+        X, _ = row_points(p, g)
+        Phi = feature_values(p, params, j, X)[:, f.perm[:r]]
+        G = qrcp(Phi, tol_fit)
+        k = G.rank
+        c = np.zeros(r)
+        if k:
+            z = G.Q().T @ np.asarray(uhat[j], dtype=np.float64)
+            c[G.perm[:k]] = trsv(G.R, z)
+        cs.append(c)
+        ys.append(f.R @ c)
+    return ys, cs

@@ -744,3 +744,25 @@ void orc_exact_many(const orc_problem *P, int64_t npts, const double *X, double 
         u[p] = orc_exact(P, x);
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* feature values (for the local fit of a predicted solution)               */
+/* ------------------------------------------------------------------------ */
+
+/* Phi[p, k] = phi_jk(X_p) for the K features of subdomain j (no window), at
+ * npts points X (npts x dim); Phi column-major with ld = npts. */
+void orc_feature_values(const orc_problem *P, const double *params, int64_t j, int64_t npts, const double *X,
+                        double *Phi) {
+    double mu[3], sig[3];
+    orc_subdomain(P, j, mu, sig);
+    for (int64_t p = 0; p < npts; ++p) {
+        double x[3] = {0, 0, 0};
+        for (int i = 0; i < P->dim; ++i) x[i] = X[p * P->dim + i];
+        for (int k = 0; k < P->K; ++k) {
+            const double *prm = params + ((size_t)j * P->K + k) * (P->dim + 1);
+            double phi, dphi[3], d2phi[3];
+            feature(P, prm, mu, sig, x, &phi, dphi, d2phi);
+            Phi[(size_t)k * npts + p] = phi;
+        }
+    }
+}
