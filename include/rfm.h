@@ -233,6 +233,75 @@ rfm_status rfm_eval(const rfm_problem *probs, int n_inst, const rfm_config *cfg,
 rfm_status rfm_eval_noalloc(const rfm_problem *probs, int n_inst, const double *d_params, const double *d_a,
                             const double *d_x, const int64_t *h_pt_off, double *d_u, double *d_err, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start.  The paper solves every problem from a zero start; these
+ * calls add a starting point predicted by a small network trained on earlier
+ * solutions (a method extension with no counterpart in the paper).  The
+ * prediction u_hat at every block's rows is fitted, block by block, through
+ * the block's kept features, and the fitted coefficients c_j become the LSQR
+ * starting point y0_j = R_j c_j of Algorithm 2's preconditioned unknowns
+ * (pass it as y0 to rfm_lsqr_solve).  The stopping rule of the solve is
+ * unchanged, so a zero start remains the fallback and the judge of the gain.
+ * ------------------------------------------------------------------------ */
+
+/* Network inputs at every block row (rows in the block-row layout of
+ * rfm_block_info: block b's rows at roff .. roff + ldm, padding rows zero):
+ * d_x[row, :] = [ctx of the row's instance (n_ctx floats, from d_ctx, n_inst x
+ * n_ctx row-major), centre of the block (dim), (x - centre) / half-width
+ * (dim)], FP32, row-major with n_ctx + 2 dim columns.  d_pts (optional, may be
+ * NULL) receives the row's point (3 doubles per row, unused coordinates 0).
+ * Needs the records written by rfm_assemble. */
+rfm_status rfm_block_inputs(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const float *d_ctx,
+                            int n_ctx, float *d_x, double *d_pts, void *d_ws, size_t ws_bytes, void *stream);
+
+/* Bytes of the fit workspace of a system (three FP64 block arenas of the
+ * system's block shape plus per-column pivots). */
+rfm_status rfm_fit_size(const rfm_problem *probs, int n_inst, const rfm_config *cfg, size_t *bytes);
+
+/* Per block: the values of the kept features (pivot order of rfm_rrqr_filter)
+ * at the block's rows, factored by QR with column pivoting truncated at
+ * tol_fit |R_11| (the same kernels as Algorithm 1), with explicit Q_hat.
+ * Needs rfm_assemble and rfm_rrqr_filter on d_ws (any operator but PLAIN).
+ * d_fit_ws: 256-byte aligned, rfm_fit_size bytes, owned by the caller. */
+rfm_status rfm_fit_prepare(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const double *d_params,
+                           double tol_fit, void *d_ws, size_t ws_bytes, void *d_fit_ws, size_t fit_bytes,
+                           void *stream);
+
+/* y0 from predictions d_uhat (FP32, block-row layout as rfm_block_inputs):
+ * per block the truncated least-squares coefficients c_j of the predictions
+ * in the kept features, then y0 = R_j c_j in the column-slot layout of
+ * rfm_lsqr_solve (slots beyond a block's rank set to 0). */
+rfm_status rfm_warm_start(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const float *d_uhat,
+                          double *d_y0, void *d_ws, size_t ws_bytes, void *d_fit_ws, size_t fit_bytes, void *stream);
+
+/* The network: fully connected, widths width[0..n_layers], tanh on hidden
+ * layers, one linear output (width[n_layers] = 1); input width 1..32, hidden
+ * widths multiples of 16 up to 128, at most 8 layers.  Parameters FP32, packed
+ * layer by layer: W_l row-major (width[l] x width[l-1]) then b_l. */
+typedef struct {
+    int32_t n_layers;
+    int32_t width[9];
+} rfm_mlp;
+
+/* Parameter count and the workspace bytes of rfm_mlp_grad (any batch size). */
+rfm_status rfm_mlp_size(const rfm_mlp *net, int64_t *n_params, size_t *ws_bytes);
+
+/* d_y[i] = network(d_x[i, :]) for n samples (d_x row-major n x width[0]). */
+rfm_status rfm_mlp_forward(const rfm_mlp *net, const float *d_theta, const float *d_x, int64_t n, float *d_y,
+                           void *stream);
+
+/* Mean squared error (1/n) sum_i (network(x_i) - t_i)^2 over the batch and its
+ * gradient (n_params floats) by backpropagation; d_loss (1 float, may be
+ * NULL).  The per-CTA partial gradients are summed in a fixed order, so the
+ * result is reproducible on a given GPU. */
+rfm_status rfm_mlp_grad(const rfm_mlp *net, const float *d_theta, const float *d_x, const float *d_t, int64_t n,
+                        float *d_grad, float *d_loss, void *d_ws, size_t ws_bytes, void *stream);
+
+/* One Adam step (Kingma and Ba 2015) at step number t >= 1 on n parameters:
+ * moments d_m, d_v and parameters updated in place from gradient d_g. */
+rfm_status rfm_adam_step(int64_t n, float *d_theta, float *d_m, float *d_v, const float *d_g, int t, float lr,
+                         float beta1, float beta2, float eps, void *stream);
+
 /* Device-side copies of the assembled blocks for inspection and tests:
  * block b's M_j (|I_j| x K, column-major with leading dimension *ld) starts at
  * element offset *moff of the M arena, and its rows are the global rows

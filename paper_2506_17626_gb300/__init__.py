@@ -3,7 +3,7 @@ preconditioning: block assembly, batched pivoted QR with threshold dropping,
 and preconditioned LSQR, as hand-written sm_103a CUDA kernels behind the C ABI
 of include/rfm.h.  This package is the thin Python binding over that library.
 """
-from .api import System, report_dict  # noqa: F401
+from .api import Mlp, System, report_dict  # noqa: F401
 from . import _native  # noqa: F401
 
-__all__ = ["System", "report_dict"]
+__all__ = ["Mlp", "System", "report_dict"]

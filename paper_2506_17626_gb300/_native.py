@@ -39,6 +39,18 @@ class RfmLsqrOpts(C.Structure):
                 ("d_phase_ms", C.c_void_p)]
 
 
+class RfmMlp(C.Structure):
+    _fields_ = [("n_layers", C.c_int32), ("width", C.c_int32 * 9)]
+
+
+def mlp_struct(widths) -> RfmMlp:
+    m = RfmMlp()
+    m.n_layers = len(widths) - 1
+    for i, w in enumerate(widths):
+        m.width[i] = int(w)
+    return m
+
+
 REPORT_FIELDS = ("itn", "istop", "rnorm", "arnorm", "anorm", "ynorm", "bnorm", "status")
 
 EXPORTS = ["rfm_problem_size", "rfm_assemble", "rfm_rrqr_filter", "rfm_lsqr_solve", "rfm_coefficients",
@@ -69,6 +81,14 @@ def load(path: str = LIB_PATH):
         "rfm_coefficients": [P, C.c_int, CF, vp, vp, vp, C.c_size_t, vp],
         "rfm_block_info": [P, C.c_int, CF, i64, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)],
         "rfm_workspace_view": [P, C.c_int, CF, vp, C.c_int, C.POINTER(vp)],
+        "rfm_block_inputs": [P, C.c_int, CF, vp, C.c_int, vp, vp, vp, C.c_size_t, vp],
+        "rfm_fit_size": [P, C.c_int, CF, C.POINTER(C.c_size_t)],
+        "rfm_fit_prepare": [P, C.c_int, CF, vp, C.c_double, vp, C.c_size_t, vp, C.c_size_t, vp],
+        "rfm_warm_start": [P, C.c_int, CF, vp, vp, vp, C.c_size_t, vp, C.c_size_t, vp],
+        "rfm_mlp_size": [C.POINTER(RfmMlp), C.POINTER(i64), C.POINTER(C.c_size_t)],
+        "rfm_mlp_forward": [C.POINTER(RfmMlp), vp, vp, i64, vp, vp],
+        "rfm_mlp_grad": [C.POINTER(RfmMlp), vp, vp, vp, i64, vp, vp, vp, C.c_size_t, vp],
+        "rfm_adam_step": [i64, vp, vp, vp, vp, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, vp],
     }
     for name, args in sigs.items():
         f = getattr(L, name)

@@ -111,6 +111,44 @@ class System:
                                               self.ws_bytes, _stream()))
         return [u[offs[i]:offs[i + 1]] for i in range(self.n)], err
 
+    # -- learned warm start -------------------------------------------------------------
+    def block_inputs(self, ctx: Optional[torch.Tensor], want_points: bool = True):
+        """Network inputs at every block row (block-row layout, padding rows
+        zero): [ctx of the instance, block centre, local coordinates], FP32;
+        and the rows' points (block_rows x 3, FP64) when want_points."""
+        n_ctx = 0 if ctx is None else ctx.shape[1]
+        if ctx is not None:
+            assert ctx.is_cuda and ctx.dtype == torch.float32 and ctx.is_contiguous() and ctx.shape[0] == self.n
+        dim = self.problems[0].dim
+        assert all(p.dim == dim for p in self.problems)
+        nr = self.sizes["block_rows"]
+        X = torch.empty((nr, n_ctx + 2 * dim), dtype=torch.float32, device=self.device)
+        pts = torch.empty((nr, 3), dtype=torch.float64, device=self.device) if want_points else None
+        N.check("rfm_block_inputs", self.lib.rfm_block_inputs(self._probs, self.n, C.byref(self._cfg), _ptr(ctx),
+                                                              n_ctx, _ptr(X), _ptr(pts), C.c_void_p(self.ws_ptr),
+                                                              self.ws_bytes, _stream()))
+        return X, pts
+
+    def fit_prepare(self, params: torch.Tensor, tol_fit: float = 1e-10):
+        """Factor the kept features' values per block (after filter())."""
+        nb = C.c_size_t()
+        N.check("rfm_fit_size", self.lib.rfm_fit_size(self._probs, self.n, C.byref(self._cfg), C.byref(nb)))
+        self.fit_bytes = nb.value
+        self.fws = torch.empty(self.fit_bytes + 256, dtype=torch.uint8, device=self.device)
+        self.fws_ptr = self.fws.data_ptr() + (-self.fws.data_ptr()) % 256
+        N.check("rfm_fit_prepare", self.lib.rfm_fit_prepare(self._probs, self.n, C.byref(self._cfg), _ptr(params),
+                                                            float(tol_fit), C.c_void_p(self.ws_ptr), self.ws_bytes,
+                                                            C.c_void_p(self.fws_ptr), self.fit_bytes, _stream()))
+
+    def warm_start(self, uhat: torch.Tensor) -> torch.Tensor:
+        """y0 (column-slot layout) from predictions at the block rows (FP32)."""
+        assert uhat.is_cuda and uhat.dtype == torch.float32 and uhat.numel() >= self.sizes["block_rows"]
+        y0 = torch.empty(self.sizes["n_cols"], dtype=torch.float64, device=self.device)
+        N.check("rfm_warm_start", self.lib.rfm_warm_start(self._probs, self.n, C.byref(self._cfg), _ptr(uhat),
+                                                          _ptr(y0), C.c_void_p(self.ws_ptr), self.ws_bytes,
+                                                          C.c_void_p(self.fws_ptr), self.fit_bytes, _stream()))
+        return y0
+
     # -- views for tests --------------------------------------------------------------
     def view(self, which: int) -> int:
         p = C.c_void_p()
@@ -164,3 +202,42 @@ class System:
 def report_dict(rep: torch.Tensor, i: int = 0) -> dict:
     r = rep.view(-1, 8)[i].tolist()
     return {k: (int(v) if k in ("itn", "istop", "status") else v) for k, v in zip(N.REPORT_FIELDS, r)}
+
+
+class Mlp:
+    """The warm-start network of include/rfm.h (FP32 parameters, tanh hidden
+    layers, scalar linear output); forward, loss gradient and Adam run in the
+    library's kernels."""
+
+    def __init__(self, widths, device: str = "cuda"):
+        self.widths = [int(w) for w in widths]
+        self._net = N.mlp_struct(self.widths)
+        self.lib = N.load()
+        npar, wsb = C.c_int64(), C.c_size_t()
+        N.check("rfm_mlp_size", self.lib.rfm_mlp_size(C.byref(self._net), C.byref(npar), C.byref(wsb)))
+        self.n_params = npar.value
+        self.device = torch.device(device)
+        self._ws = torch.empty(wsb.value + 256, dtype=torch.uint8, device=self.device)
+        self._ws_ptr = self._ws.data_ptr() + (-self._ws.data_ptr()) % 256
+        self._ws_bytes = wsb.value
+
+    def forward(self, theta: torch.Tensor, X: torch.Tensor) -> torch.Tensor:
+        assert theta.dtype == torch.float32 and X.dtype == torch.float32 and X.is_contiguous()
+        Y = torch.empty(X.shape[0], dtype=torch.float32, device=self.device)
+        N.check("rfm_mlp_forward", self.lib.rfm_mlp_forward(C.byref(self._net), _ptr(theta), _ptr(X), X.shape[0],
+                                                            _ptr(Y), _stream()))
+        return Y
+
+    def grad(self, theta: torch.Tensor, X: torch.Tensor, T: torch.Tensor, out: Optional[torch.Tensor] = None,
+             loss: Optional[torch.Tensor] = None):
+        assert X.dtype == torch.float32 and T.dtype == torch.float32 and X.is_contiguous() and T.is_contiguous()
+        g = out if out is not None else torch.empty(self.n_params, dtype=torch.float32, device=self.device)
+        lo = loss if loss is not None else torch.empty(1, dtype=torch.float32, device=self.device)
+        N.check("rfm_mlp_grad", self.lib.rfm_mlp_grad(C.byref(self._net), _ptr(theta), _ptr(X), _ptr(T), X.shape[0],
+                                                      _ptr(g), _ptr(lo), C.c_void_p(self._ws_ptr), self._ws_bytes,
+                                                      _stream()))
+        return g, lo
+
+    def adam_step(self, theta, m, v, g, t: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        N.check("rfm_adam_step", self.lib.rfm_adam_step(theta.numel(), _ptr(theta), _ptr(m), _ptr(v), _ptr(g), int(t),
+                                                        float(lr), float(b1), float(b2), float(eps), _stream()))

@@ -19,6 +19,20 @@ rfm_status launch_eval_noalloc(const HostPlan &P, const double *params, const do
                                const int64_t *pt_off, double *u, double *err, cudaStream_t st);
 rfm_status launch_eval(const HostPlan &P, void *ws, const double *params, const double *a, const double *X,
                        const int64_t *pt_off, double *u, double *err, cudaStream_t st);
+size_t fit_workspace_bytes(const HostPlan &P);
+rfm_status launch_fit_prepare(const HostPlan &P, void *ws, const double *params, double tol_fit, void *fws,
+                              cudaStream_t st);
+rfm_status launch_warm_start(const HostPlan &P, void *ws, void *fws, const float *uhat, double *y0, cudaStream_t st);
+rfm_status launch_block_inputs(const HostPlan &P, void *ws, const float *ctx, int n_ctx, float *X, double *pts,
+                               cudaStream_t st);
+rfm_status mlp_nparams(const rfm_mlp *net, int64_t *np);
+rfm_status mlp_workspace(const rfm_mlp *net, size_t *bytes);
+rfm_status launch_mlp_forward(const rfm_mlp *net, const float *theta, const float *X, int64_t n, float *Y,
+                              cudaStream_t st);
+rfm_status launch_mlp_grad(const rfm_mlp *net, const float *theta, const float *X, const float *T, int64_t n,
+                           float *grad, float *loss, void *ws, size_t ws_bytes, cudaStream_t st);
+rfm_status launch_adam(int64_t n, float *theta, float *m, float *v, const float *g, int t, float lr, float b1,
+                       float b2, float eps, cudaStream_t st);
 
 namespace {
 // RAII holder of a host plan for one call.
@@ -291,6 +305,128 @@ rfm_status rfm_workspace_view(const rfm_problem *probs, int n_inst, const rfm_co
     }
     *ptr = ws_ptr<void>(d_ws, off);
     return RFM_OK;
+    RFM_GUARD_END
+}
+
+rfm_status rfm_block_inputs(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const float *d_ctx,
+                            int n_ctx, float *d_x, double *d_pts, void *d_ws, size_t ws_bytes, void *stream) {
+    RFM_GUARD_BEGIN
+    Plan P(probs, n_inst, cfg);
+    if (!P.ok) return P.rc;
+    rfm_status rc = check_ws(P.p.L, d_ws, ws_bytes);
+    if (rc != RFM_OK) return rc;
+    if (n_ctx < 0 || n_ctx > 64 || (n_ctx > 0 && !d_ctx) || !d_x) {
+        set_error("rfm_block_inputs: need 0 <= n_ctx <= 64, d_ctx when n_ctx > 0, and d_x");
+        return RFM_EINVAL;
+    }
+    return launch_block_inputs(P.p, d_ws, d_ctx, n_ctx, d_x, d_pts, (cudaStream_t)stream);
+    RFM_GUARD_END
+}
+
+rfm_status rfm_fit_size(const rfm_problem *probs, int n_inst, const rfm_config *cfg, size_t *bytes) {
+    RFM_GUARD_BEGIN
+    Plan P(probs, n_inst, cfg);
+    if (!P.ok) return P.rc;
+    if (!bytes) {
+        set_error("rfm_fit_size: bytes is NULL");
+        return RFM_EINVAL;
+    }
+    *bytes = fit_workspace_bytes(P.p);
+    return RFM_OK;
+    RFM_GUARD_END
+}
+
+static rfm_status check_fit_ws(const HostPlan &P, const void *fws, size_t fit_bytes) {
+    if (!fws || ((uintptr_t)fws & 255)) {
+        set_error("fit workspace must be a 256-byte aligned device pointer");
+        return RFM_EINVAL;
+    }
+    if (fit_bytes < fit_workspace_bytes(P)) {
+        set_error("fit workspace has %zu bytes, the system needs %zu", fit_bytes, fit_workspace_bytes(P));
+        return RFM_ENOSPACE;
+    }
+    return RFM_OK;
+}
+
+rfm_status rfm_fit_prepare(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const double *d_params,
+                           double tol_fit, void *d_ws, size_t ws_bytes, void *d_fit_ws, size_t fit_bytes,
+                           void *stream) {
+    RFM_GUARD_BEGIN
+    Plan P(probs, n_inst, cfg);
+    if (!P.ok) return P.rc;
+    rfm_status rc = check_ws(P.p.L, d_ws, ws_bytes);
+    if (rc != RFM_OK) return rc;
+    rc = check_fit_ws(P.p, d_fit_ws, fit_bytes);
+    if (rc != RFM_OK) return rc;
+    if (!d_params || !(tol_fit >= 0.0 && tol_fit < 1.0)) {
+        set_error("rfm_fit_prepare: need d_params and 0 <= tol_fit < 1");
+        return RFM_EINVAL;
+    }
+    return launch_fit_prepare(P.p, d_ws, d_params, tol_fit, d_fit_ws, (cudaStream_t)stream);
+    RFM_GUARD_END
+}
+
+rfm_status rfm_warm_start(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const float *d_uhat,
+                          double *d_y0, void *d_ws, size_t ws_bytes, void *d_fit_ws, size_t fit_bytes, void *stream) {
+    RFM_GUARD_BEGIN
+    Plan P(probs, n_inst, cfg);
+    if (!P.ok) return P.rc;
+    rfm_status rc = check_ws(P.p.L, d_ws, ws_bytes);
+    if (rc != RFM_OK) return rc;
+    rc = check_fit_ws(P.p, d_fit_ws, fit_bytes);
+    if (rc != RFM_OK) return rc;
+    if (!d_uhat || !d_y0) {
+        set_error("rfm_warm_start: null argument");
+        return RFM_EINVAL;
+    }
+    return launch_warm_start(P.p, d_ws, d_fit_ws, d_uhat, d_y0, (cudaStream_t)stream);
+    RFM_GUARD_END
+}
+
+rfm_status rfm_mlp_size(const rfm_mlp *net, int64_t *n_params, size_t *ws_bytes) {
+    RFM_GUARD_BEGIN
+    int64_t np = 0;
+    size_t wb = 0;
+    rfm_status rc = mlp_nparams(net, &np);
+    if (rc != RFM_OK) return rc;
+    rc = mlp_workspace(net, &wb);
+    if (rc != RFM_OK) return rc;
+    if (n_params) *n_params = np;
+    if (ws_bytes) *ws_bytes = wb;
+    return RFM_OK;
+    RFM_GUARD_END
+}
+
+rfm_status rfm_mlp_forward(const rfm_mlp *net, const float *d_theta, const float *d_x, int64_t n, float *d_y,
+                           void *stream) {
+    RFM_GUARD_BEGIN
+    if (!d_theta || (n > 0 && (!d_x || !d_y)) || n < 0) {
+        set_error("rfm_mlp_forward: null argument or negative n");
+        return RFM_EINVAL;
+    }
+    return launch_mlp_forward(net, d_theta, d_x, n, d_y, (cudaStream_t)stream);
+    RFM_GUARD_END
+}
+
+rfm_status rfm_mlp_grad(const rfm_mlp *net, const float *d_theta, const float *d_x, const float *d_t, int64_t n,
+                        float *d_grad, float *d_loss, void *d_ws, size_t ws_bytes, void *stream) {
+    RFM_GUARD_BEGIN
+    if (!d_theta || !d_x || !d_t || !d_grad) {
+        set_error("rfm_mlp_grad: null argument");
+        return RFM_EINVAL;
+    }
+    return launch_mlp_grad(net, d_theta, d_x, d_t, n, d_grad, d_loss, d_ws, ws_bytes, (cudaStream_t)stream);
+    RFM_GUARD_END
+}
+
+rfm_status rfm_adam_step(int64_t n, float *d_theta, float *d_m, float *d_v, const float *d_g, int t, float lr,
+                         float beta1, float beta2, float eps, void *stream) {
+    RFM_GUARD_BEGIN
+    if (!d_theta || !d_m || !d_v || !d_g) {
+        set_error("rfm_adam_step: null argument");
+        return RFM_EINVAL;
+    }
+    return launch_adam(n, d_theta, d_m, d_v, d_g, t, lr, beta1, beta2, eps, (cudaStream_t)stream);
     RFM_GUARD_END
 }
 

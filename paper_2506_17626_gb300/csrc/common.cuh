@@ -111,6 +111,22 @@ void free_plan(HostPlan *p);
 
 void set_error(const char *fmt, ...);
 
+// Buffers of one batched QR-with-threshold pass (rrqr.cu): the system's own
+// filter, or the fit of predicted values through the kept features.
+struct FilterBufs {
+    const BlkRec *blk;
+    const void *M;          // input blocks (FP32 or FP64), ldm x K each
+    double *W, *tau, *r11;  // QR work (R above the diagonal, reflectors below)
+    int32_t *perm, *rank;
+    double *Op;             // FP64 output arena (Q_hat, or the gathered kept columns)
+    double *Q64;            // = Op when Q_hat is wanted in FP64
+    float *Q32;             // Q_hat rounded to FP32
+    bool gather;            // write the kept columns into Op instead of Q_hat
+    bool fit;               // profiling label only
+    int64_t n_blocks, max_m, max_K;
+};
+rfm_status launch_filter_bufs(const FilterBufs &F, bool fp32, double tol, cudaStream_t st);
+
 template <typename T>
 __host__ __device__ inline T *ws_ptr(void *ws, size_t off) {
     return reinterpret_cast<T *>(reinterpret_cast<char *>(ws) + off);

@@ -708,10 +708,11 @@ __global__ void k_report(const LsqrScal *__restrict__ sc, int n, rfm_lsqr_report
 // every CTA, so all SMs stream the operator at once.
 //   forward item  = 64 rows of one block:   t[rows] = Op_b[rows, :] v_b
 //   column item   = 8 columns of one block: vt[cols] = Op_b[:, cols]^T u~ / beta - beta v
-// Each thread of a forward item owns 16 bytes of rows (4 FP32 / 2 FP64) and a
-// column group, reads the operator with 16-byte vector loads, and the column
-// groups are summed in shared memory.  A column item gathers the block's u~
-// into shared memory once and reduces one column per warp.  The column
+// A forward item is one warp over 128 rows: each lane owns four rows (16-byte
+// loads in FP32), the input vector is read in the operator's precision (a
+// copy of vt kept beside it) and the 1/alpha scaling is applied once per row.
+// A column item is one warp over 8 columns, reading u~ in the operator's
+// precision.  The column
 // updates of the Givens step (y, w) are elementwise and ride in the forward
 // phase; ||y||^2 rides in the column phase, so the stopping test of iteration
 // i is taken at the third barrier of round i+1 (with iteration i's estimates).
@@ -723,6 +724,9 @@ struct TileSmem {
     double tmp[kMaxInst], tmp2[kMaxInst], yy[kMaxInst];
     double wred[2][8];
     LsqrScal sc[64];
+    // per-instance factors formed once per phase (no division or square root
+    // in per-element code: GB300's FP64 pipe is narrow)
+    double inv_alpha[64], ab[64], bn[64], inv_bn[64];
 };
 
 // Four rows of a column owned by one lane: FP32 one 16-byte load of rows
@@ -880,6 +884,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
     const int ni = a.n_inst;
     const int64_t n_items = *n_items_p, n_fitems = *n_fitems_p;
     const TA *Aop = reinterpret_cast<const TA *>(a.A);
+    // vt in the operator's precision: the FP64 vector itself, or an FP32 copy
+    // in the v arena (unused by this kernel otherwise)
+    TA *vx = sizeof(TA) == sizeof(double) ? reinterpret_cast<TA *>(a.vt) : reinterpret_cast<TA *>(a.v);
     LsqrScal *sc = S.sc;
     bool ok = true;
     auto blk_rank = [&](int b) { return a.rank ? __ldg(a.rank + b) : a.blks[b].K; };
@@ -902,14 +909,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
 
     // forward items (one warp each): t[rows] = Op_b[rows, :] x_b for a 128-row
     // tile, 8 columns per round trip, x = src * scale(inst)
-    auto forward = [&](auto take, const double *src, auto scale_of) {
+    auto forward = [&](auto take, const TA *src, auto scale_of) {
         for (int64_t k = gwarp; k < n_fitems; k += twarps) {
             const ColItem it = fitems[k];
             if (!take(it.inst)) continue;
             const double xs = scale_of(it.inst);
             const int r0 = it.c0, r = it.nc;
             const TA *base = Aop + it.moff;
-            const double *xb = src + it.coff;
+            const TA *xb = src + it.coff;
             TA acc[4] = {(TA)0, (TA)0, (TA)0, (TA)0};
             constexpr int CW = kColTile;   // columns per round trip
             int c = 0;
@@ -919,7 +926,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
 #pragma unroll
                 for (int j = 0; j < CW; ++j) Rows4<TA>::load(base + (int64_t)(c + j) * it.ldm, r0, lane, it.ldm, q[j]);
 #pragma unroll
-                for (int j = 0; j < CW; ++j) x[j] = (TA)(xb[c + j] * xs);   // written in-kernel: coherent loads
+                for (int j = 0; j < CW; ++j) x[j] = xb[c + j];   // written in-kernel: coherent loads
 #pragma unroll
                 for (int j = 0; j < CW; ++j)
 #pragma unroll
@@ -928,14 +935,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
             for (; c < r; ++c) {
                 TA q[4];
                 Rows4<TA>::load(base + (int64_t)c * it.ldm, r0, lane, it.ldm, q);
-                const TA x = (TA)(xb[c] * xs);
+                const TA x = xb[c];
 #pragma unroll
                 for (int v = 0; v < 4; ++v) acc[v] += q[v] * x;
             }
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 const int i = Rows4<TA>::row(r0, lane, v);
-                if (i < it.m) a.t[it.roff + i] = (double)acc[v];
+                if (i < it.m) a.t[it.roff + i] = (double)acc[v] * xs;
             }
         }
     };
@@ -1027,8 +1034,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
     each_column(all_inst, [&](int inst, int64_t o) {
         a.y[o] = a.y0 ? a.y0[o] : 0.0;
         a.w[o] = 0.0;
+        if (a.y0) vx[o] = (TA)a.y0[o];   // (FP64: vt holds y0 until the first column phase)
     });
-    if (a.y0) forward(all_inst, a.y0, [](int) { return 1.0; });
+    if (a.y0) {
+        ok = grid_sync(a.bar, a.timeout_ns);
+        if (!ok) return;
+        forward(all_inst, vx, [](int) { return 1.0; });
+    }
     ok = grid_sync(a.bar, a.timeout_ns);
     // u~ = h - (Op y0), ||u~||^2, ||h||^2; u~ copied onto the block rows
     clear(S.acc_b);
@@ -1072,15 +1084,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
     for (int s = tid; s < ni; s += kThreads) {
         sc[s].beta = sqrt(S.tmp[s]);
         sc[s].bnorm = sqrt(S.tmp2[s]);
+        S.inv_bn[s] = sc[s].beta > 0.0 ? 1.0 / sc[s].beta : 0.0;
     }
     __syncthreads();
     // vt = Op^T u~ / beta, ||vt||^2
     clear_w();
     __syncthreads();
     columns(all_inst, [&](int inst, int64_t o, double z, double *pa, double *py) {
-        const double beta = sc[inst].beta;
-        const double x = beta > 0.0 ? z / beta : 0.0;
+        const double x = z * S.inv_bn[inst];
         a.vt[o] = x;
+        if (sizeof(TA) != sizeof(double)) vx[o] = (TA)x;
         *pa = x * x;
     });
     __syncthreads();
@@ -1099,6 +1112,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
         q.itn = 0;
         q.done = (q.beta == 0.0 || q.alpha == 0.0) ? 1 : 0;
         if (q.done) q.istop = 0;
+        S.inv_alpha[s] = q.alpha > 0.0 ? 1.0 / q.alpha : 0.0;
+        S.ab[s] = q.beta > 0.0 ? q.alpha / q.beta : 0.0;
     }
     __syncthreads();
 
@@ -1118,7 +1133,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
         // F
         each_column(live, [&](int inst, int64_t o) {
             const LsqrScal &q = sc[inst];
-            const double vn = a.vt[o] * (q.alpha > 0.0 ? 1.0 / q.alpha : 0.0);
+            const double vn = a.vt[o] * S.inv_alpha[inst];
             if (first) {
                 a.w[o] = vn;
             } else {
@@ -1130,10 +1145,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
                     a.snap[(int64_t)(q.itn / a.snap_every - 1) * a.n_cols + o] = yv;
             }
         });
-        forward(live, a.vt, [&](int inst) {
-            const double al = sc[inst].alpha;
-            return al > 0.0 ? 1.0 / al : 0.0;
-        });
+        forward(live, vx, [&](int inst) { return S.inv_alpha[inst]; });
         ok = grid_sync(a.bar, a.timeout_ns);
         mark(0);
         if (!ok) break;
@@ -1156,8 +1168,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
                     int qq = lst[e];
                     if (qq >= 0) acc += row_partials(qq);
                 }
-                const double ab = q.beta > 0.0 ? q.alpha / q.beta : 0.0;
-                const double uv = fma(-ab, a.u[gr], acc);
+                const double uv = fma(-S.ab[s], a.u[gr], acc);
                 a.u[gr] = uv;
                 for (int e = 0; e < I.C; ++e) {
                     int qq = lst[e];
@@ -1174,15 +1185,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
         mark(1);
         if (!ok) break;
         reduce_partials(a.part + (int64_t)ni * G, ni, S.tmp);   // beta_{n+1}^2
+        for (int s = tid; s < ni; s += kThreads) {
+            const double bn = sqrt(S.tmp[s]);
+            S.bn[s] = bn;
+            S.inv_bn[s] = bn > 0.0 ? 1.0 / bn : 0.0;
+        }
+        __syncthreads();
         // T: vt = Op^T u~ / beta_new - beta_new v_n ; ||vt||^2 ; ||y_{n-1}||^2
         clear_w();
         __syncthreads();
         columns(live, [&](int inst, int64_t o, double z, double *pa, double *py) {
-            const LsqrScal &q = sc[inst];
-            const double bn = sqrt(S.tmp[inst]);
-            const double vn = a.vt[o] * (q.alpha > 0.0 ? 1.0 / q.alpha : 0.0);
-            const double x = (bn > 0.0 ? z / bn : 0.0) - bn * vn;
+            const double vn = a.vt[o] * S.inv_alpha[inst];
+            const double x = fma(z, S.inv_bn[inst], -S.bn[inst] * vn);
             a.vt[o] = x;
+            if (sizeof(TA) != sizeof(double)) vx[o] = (TA)x;
             *pa = x * x;
             const double yv = a.y[o];
             *py = yv * yv;
@@ -1229,6 +1245,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
             q.c = c;
             q.alpha = alpha;
             q.beta = beta;
+            S.inv_alpha[s] = alpha > 0.0 ? 1.0 / alpha : 0.0;
+            S.ab[s] = beta > 0.0 ? alpha / beta : 0.0;
             if (!isfinite(q.phibar) || !isfinite(q.rhobar) || !isfinite(q.phi_rho) || !isfinite(q.anorm2)) {
                 q.done = 1;
                 q.status = RFM_ENUMERIC;

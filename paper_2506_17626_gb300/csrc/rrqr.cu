@@ -508,13 +508,11 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
 }
 
 template <typename TM, int C>
-static rfm_status launch_cluster(const HostPlan &P, void *ws, double tol, int nloc, int ldl, size_t smem, double *Qout,
-                                 float *Q32, cudaStream_t st) {
-    const Layout &L = P.L;
+static rfm_status launch_cluster(const FilterBufs &F, double tol, int nloc, int ldl, size_t smem, cudaStream_t st) {
     auto kern = k_qrcp_cluster<TM, C>;
     RFM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(L.n_blocks * C));
+    cfg.gridDim = dim3((unsigned)(F.n_blocks * C));
     cfg.blockDim = dim3(256);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
@@ -525,11 +523,8 @@ static rfm_status launch_cluster(const HostPlan &P, void *ws, double tol, int nl
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    RFM_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, (const BlkRec *)ws_ptr<BlkRec>(ws, L.off_blk),
-                                      (const TM *)ws_ptr<TM>(ws, L.off_M), ws_ptr<double>(ws, L.off_W),
-                                      ws_ptr<double>(ws, L.off_tau), ws_ptr<int32_t>(ws, L.off_perm),
-                                      ws_ptr<int32_t>(ws, L.off_rank), ws_ptr<double>(ws, L.off_r11), tol, nloc, ldl,
-                                      Qout, Q32));
+    RFM_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, F.blk, (const TM *)F.M, F.W, F.tau, F.perm, F.rank, F.r11, tol, nloc,
+                                      ldl, F.Q64, F.Q32));
     return RFM_OK;
 }
 
@@ -541,70 +536,80 @@ static size_t cluster_smem(int64_t max_m, int64_t max_K, int C, int *nloc, int *
 }
 
 template <typename TM>
-static rfm_status launch_filter_t(const HostPlan &P, void *ws, double tol, cudaStream_t st) {
-    const Layout &L = P.L;
-    const unsigned nb = (unsigned)L.n_blocks;
-    BlkRec *dB = ws_ptr<BlkRec>(ws, L.off_blk);
-    double *W = ws_ptr<double>(ws, L.off_W);
-    double *tau = ws_ptr<double>(ws, L.off_tau);
-    int32_t *perm = ws_ptr<int32_t>(ws, L.off_perm);
-    int32_t *rank = ws_ptr<int32_t>(ws, L.off_rank);
-    double *r11 = ws_ptr<double>(ws, L.off_r11);
-    double *Op = ws_ptr<double>(ws, L.off_op);
-    float *Q32 = L.op == RFM_OP_Q32 ? ws_ptr<float>(ws, L.off_q32) : nullptr;
-    double *Q64 = L.op == RFM_OP_Q64 ? Op : nullptr;
+static rfm_status launch_filter_t(const FilterBufs &F, double tol, cudaStream_t st) {
+    const unsigned nb = (unsigned)F.n_blocks;
     const size_t kSmemCap = 220 * 1024;
     int C = 0, nloc = 0, ldl = 0;
     size_t smem = 0;
     for (int c : {1, 2, 4, 8}) {
-        smem = cluster_smem(L.max_m, L.max_K, c, &nloc, &ldl);
+        smem = cluster_smem(F.max_m, F.max_K, c, &nloc, &ldl);
         if (smem <= kSmemCap) { C = c; break; }
     }
     if (C > 0) {
-        ProfScope ps("k_qrcp_cluster", st);
+        ProfScope ps(F.fit ? "k_qrcp_cluster_fit" : "k_qrcp_cluster", st);
         rfm_status rc;
         switch (C) {
-            case 1: rc = launch_cluster<TM, 1>(P, ws, tol, nloc, ldl, smem, Q64, Q32, st); break;
-            case 2: rc = launch_cluster<TM, 2>(P, ws, tol, nloc, ldl, smem, Q64, Q32, st); break;
-            case 4: rc = launch_cluster<TM, 4>(P, ws, tol, nloc, ldl, smem, Q64, Q32, st); break;
-            default: rc = launch_cluster<TM, 8>(P, ws, tol, nloc, ldl, smem, Q64, Q32, st); break;
+            case 1: rc = launch_cluster<TM, 1>(F, tol, nloc, ldl, smem, st); break;
+            case 2: rc = launch_cluster<TM, 2>(F, tol, nloc, ldl, smem, st); break;
+            case 4: rc = launch_cluster<TM, 4>(F, tol, nloc, ldl, smem, st); break;
+            default: rc = launch_cluster<TM, 8>(F, tol, nloc, ldl, smem, st); break;
         }
         if (rc != RFM_OK) return rc;
     } else {
-        const size_t sm = (size_t)L.max_K * (2 * sizeof(double) + sizeof(int));
+        const size_t sm = (size_t)F.max_K * (2 * sizeof(double) + sizeof(int));
         {
-            ProfScope ps("k_qrcp", st);
+            ProfScope ps(F.fit ? "k_qrcp_fit" : "k_qrcp", st);
             RFM_CUDA_CHECK(cudaFuncSetAttribute(k_qrcp<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            k_qrcp<TM><<<nb, 256, sm, st>>>(dB, ws_ptr<TM>(ws, L.off_M), W, tau, perm, rank, r11, tol);
+            k_qrcp<TM><<<nb, 256, sm, st>>>(F.blk, (const TM *)F.M, F.W, F.tau, F.perm, F.rank, F.r11, tol);
             RFM_CUDA_CHECK(cudaGetLastError());
         }
-        if (L.op != RFM_OP_AR64) {
-            ProfScope ps("k_form_q", st);
-            k_form_q<<<nb, 256, 0, st>>>(dB, W, tau, rank, Op, Q32);
+        if (F.Q64 || F.Q32) {
+            ProfScope ps(F.fit ? "k_form_q_fit" : "k_form_q", st);
+            k_form_q<<<nb, 256, 0, st>>>(F.blk, F.W, F.tau, F.rank, F.Op, F.Q32);
             RFM_CUDA_CHECK(cudaGetLastError());
         }
     }
-    if (L.op == RFM_OP_AR64) {
+    if (F.gather) {
         ProfScope ps("k_gather_kept", st);
-        k_gather_kept<TM><<<nb, 256, 0, st>>>(dB, ws_ptr<TM>(ws, L.off_M), perm, rank, Op);
+        k_gather_kept<TM><<<nb, 256, 0, st>>>(F.blk, (const TM *)F.M, F.perm, F.rank, F.Op);
         RFM_CUDA_CHECK(cudaGetLastError());
     }
     return RFM_OK;
 }
 
+static FilterBufs system_bufs(const HostPlan &P, void *ws) {
+    const Layout &L = P.L;
+    FilterBufs F;
+    F.blk = ws_ptr<BlkRec>(ws, L.off_blk);
+    F.M = ws_ptr<char>(ws, L.off_M);
+    F.W = ws_ptr<double>(ws, L.off_W);
+    F.tau = ws_ptr<double>(ws, L.off_tau);
+    F.perm = ws_ptr<int32_t>(ws, L.off_perm);
+    F.rank = ws_ptr<int32_t>(ws, L.off_rank);
+    F.r11 = ws_ptr<double>(ws, L.off_r11);
+    F.Op = ws_ptr<double>(ws, L.off_op);
+    F.Q32 = L.op == RFM_OP_Q32 ? ws_ptr<float>(ws, L.off_q32) : nullptr;
+    F.Q64 = L.op == RFM_OP_Q64 ? F.Op : nullptr;
+    F.gather = L.op == RFM_OP_AR64;
+    F.n_blocks = L.n_blocks;
+    F.max_m = L.max_m;
+    F.max_K = L.max_K;
+    F.fit = false;
+    return F;
+}
+
 // Test hook: force the global-memory kernels (cluster sizes disabled).
 static int g_force_global = 0;
 
+rfm_status launch_filter_bufs(const FilterBufs &F0, bool fp32, double tol, cudaStream_t st) {
+    if (F0.n_blocks == 0) return RFM_OK;
+    FilterBufs F = F0;
+    if (g_force_global) F.max_m = 1 << 30;   // no cluster size fits
+    return fp32 ? launch_filter_t<float>(F, tol, st) : launch_filter_t<double>(F, tol, st);
+}
+
 rfm_status launch_filter(const HostPlan &P, void *ws, double tol, cudaStream_t st) {
-    if (P.L.n_blocks == 0) return RFM_OK;
-    if (g_force_global) {
-        HostPlan Q = P;
-        Q.L.max_m = 1 << 30;   // no cluster size fits
-        return P.L.asm_prec == RFM_ASM_FP32 ? launch_filter_t<float>(Q, ws, tol, st)
-                                            : launch_filter_t<double>(Q, ws, tol, st);
-    }
-    return P.L.asm_prec == RFM_ASM_FP32 ? launch_filter_t<float>(P, ws, tol, st)
-                                        : launch_filter_t<double>(P, ws, tol, st);
+    return launch_filter_bufs(system_bufs(P, ws), P.L.asm_prec == RFM_ASM_FP32, tol, st);
 }
 
 void set_force_global_filter(int on) { g_force_global = on; }

@@ -1,0 +1,218 @@
+"""Learned warm start on the GPU against the oracle, through the C ABI.
+
+Network (FP32 kernels vs the FP64 oracle on the same FP32 parameters and
+inputs, upcast exactly): outputs within 2e-5 of the largest output; the
+gradient within 2e-4 of its largest entry (FP32 sums over 64-sample tiles and
+per-CTA slices); Adam within 1e-6 relative.  Ragged batches, batches spanning
+several tiles per CTA, and widths from 16 to 128 are covered.
+
+Fit: network inputs and row points exactly as the oracle's row points and
+subdomains give them (same FP64 rounding); warm-start coefficients within
+kappa(Phi) * 1e-12 of the oracle's local fit, compared through a = S^-1 y0
+(the rotation-invariant quantity), and the evaluated warm start within 1e-10.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rfm():
+    from paper_2506_17626_gb300 import build
+    build.build()
+    import paper_2506_17626_gb300 as R
+    return R
+
+
+def _net(widths, seed, scale=0.5):
+    rng = np.random.default_rng(seed)
+    n = oracle.mlp_nparams(widths)
+    return rng.standard_normal(n).astype(np.float32) * np.float32(scale)
+
+
+NETS = [[9, 128, 128, 128, 128, 1], [3, 16, 1], [5, 48, 32, 1], [32, 1], [1, 64, 64, 1]]
+
+
+@pytest.mark.parametrize("widths", NETS)
+@pytest.mark.parametrize("n", [1, 63, 200])
+def test_forward_matches_oracle(rfm, widths, n):
+    M = rfm.Mlp(widths)
+    assert M.n_params == oracle.mlp_nparams(widths)
+    th = _net(widths, len(widths) + n, scale=0.3)
+    X = np.random.default_rng(n).uniform(-1, 1, (n, widths[0])).astype(np.float32)
+    y = M.forward(torch.from_numpy(th).cuda(), torch.from_numpy(X).cuda()).cpu().numpy()
+    ref = oracle.mlp_forward(widths, th.astype(np.float64), X.astype(np.float64))
+    assert np.abs(y - ref).max() <= 2e-5 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("widths,n", [([9, 128, 128, 128, 128, 1], 130), ([9, 128, 128, 128, 128, 1], 1000),
+                                      ([3, 16, 1], 7), ([5, 48, 32, 1], 333), ([32, 1], 64),
+                                      ([9, 32, 32, 1], 20011)])
+def test_gradient_matches_oracle(rfm, widths, n):
+    M = rfm.Mlp(widths)
+    th = _net(widths, 11, scale=0.3)
+    rng = np.random.default_rng(n)
+    X = rng.uniform(-1, 1, (n, widths[0])).astype(np.float32)
+    T = rng.standard_normal(n).astype(np.float32)
+    g, lo = M.grad(torch.from_numpy(th).cuda(), torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda())
+    g = g.cpu().numpy()
+    loss, ref = oracle.mlp_grad(widths, th.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
+    assert float(lo.item()) == pytest.approx(loss, rel=1e-5)
+    assert np.abs(g - ref).max() <= 2e-4 * np.abs(ref).max(), np.abs(g - ref).max() / np.abs(ref).max()
+
+
+def test_gradient_is_reproducible(rfm):
+    w = [9, 128, 128, 128, 128, 1]
+    M = rfm.Mlp(w)
+    th = torch.from_numpy(_net(w, 3)).cuda()
+    X = torch.rand((5000, 9), device="cuda")
+    T = torch.rand(5000, device="cuda")
+    g1, _ = M.grad(th, X, T)
+    g2, _ = M.grad(th, X, T)
+    assert torch.equal(g1, g2)
+
+
+def test_adam_matches_oracle(rfm):
+    w = [9, 32, 32, 1]
+    M = rfm.Mlp(w)
+    n = M.n_params
+    rng = np.random.default_rng(2)
+    th = rng.standard_normal(n).astype(np.float32)
+    m = np.zeros(n, np.float32)
+    v = np.zeros(n, np.float32)
+    dth, dm, dv = (torch.from_numpy(a.copy()).cuda() for a in (th, m, v))
+    oth, om, ov = th.astype(np.float64), m.astype(np.float64), v.astype(np.float64)
+    for t in range(1, 4):
+        g = rng.standard_normal(n).astype(np.float32)
+        M.adam_step(dth, dm, dv, torch.from_numpy(g).cuda(), t, lr=1e-2)
+        oracle.adam_step(oth, om, ov, g.astype(np.float64), t, lr=1e-2)
+    assert dth.cpu().numpy() == pytest.approx(oth, rel=1e-6, abs=1e-6)
+    assert dm.cpu().numpy() == pytest.approx(om, rel=1e-5, abs=1e-7)
+
+
+def test_training_on_the_gpu_fits_a_teacher(rfm):
+    w = [2, 32, 32, 1]
+    M = rfm.Mlp(w)
+    rng = np.random.default_rng(7)
+    teacher = rng.standard_normal(M.n_params)
+    X = rng.uniform(-1, 1, (512, 2))
+    T = oracle.mlp_forward(w, teacher, X)
+    dX = torch.from_numpy(X.astype(np.float32)).cuda()
+    dT = torch.from_numpy(T.astype(np.float32)).cuda()
+    th = torch.from_numpy(_net(w, 8, 0.3)).cuda()
+    m, v = torch.zeros_like(th), torch.zeros_like(th)
+    g = torch.empty_like(th)
+    lo = torch.empty(1, device="cuda")
+    M.grad(th, dX, dT, out=g, loss=lo)
+    l0 = float(lo.item())
+    for t in range(1, 801):
+        M.grad(th, dX, dT, out=g, loss=lo)
+        M.adam_step(th, m, v, g, t, lr=3e-3)
+    M.grad(th, dX, dT, out=g, loss=lo)
+    assert float(lo.item()) < 0.02 * l0
+
+
+# ---------------------------------------------------------------------------
+# fit of predicted values through the kept features
+# ---------------------------------------------------------------------------
+
+FIT_CASES = {
+    "p1d": lambda: synth.poisson1d(S=4, K=8, n=60),
+    "p2d": lambda: synth.poisson2d(S=3, K=10, n=12),
+}
+
+
+def _system(rfm, p, prm, op="ar64", tol=1e-10):
+    S = rfm.System([p], asm="fp64", op=op, tol=tol)
+    d = torch.from_numpy(np.ascontiguousarray(prm).ravel()).cuda()
+    S.assemble(d)
+    return S, d
+
+
+@pytest.mark.parametrize("name", list(FIT_CASES))
+def test_block_inputs_are_the_row_points(rfm, name):
+    p = FIT_CASES[name]()
+    prm = synth.feature_params(p)
+    S, d = _system(rfm, p, prm)
+    ctx = torch.tensor([[0.25, -0.5, 2.0]], dtype=torch.float32, device="cuda")
+    X, pts = S.block_inputs(ctx)
+    X, pts = X.cpu().numpy(), pts.cpu().numpy()
+    for j in range(p.J):
+        m, ld, _, roff = S.block_info(j)
+        g = oracle.block_rows(p, j)
+        P, _ = oracle.row_points(p, g)
+        mu, sg = oracle.subdomain(p, j)
+        assert np.array_equal(pts[roff:roff + m, : p.dim], P)
+        assert np.all(pts[roff + m: roff + ld] == 0)
+        xr = X[roff:roff + m]
+        assert np.array_equal(xr[:, :3], np.tile([0.25, -0.5, 2.0], (m, 1)).astype(np.float32))
+        assert np.array_equal(xr[:, 3:3 + p.dim], np.tile(mu.astype(np.float32), (m, 1)))
+        assert np.array_equal(xr[:, 3 + p.dim:], ((P - mu) / sg).astype(np.float32))
+        assert np.all(X[roff + m: roff + ld] == 0)
+
+
+@pytest.mark.parametrize("name", list(FIT_CASES))
+@pytest.mark.parametrize("op", ["ar64", "q32"])
+def test_warm_start_matches_oracle_fit(rfm, name, op):
+    p = FIT_CASES[name]()
+    prm = synth.feature_params(p)
+    tol = 1e-10 if op == "ar64" else 1e-6
+    S, d = _system(rfm, p, prm, op=op, tol=tol)
+    ranks, perm = S.filter(want_perm=True)
+    S.fit_prepare(d, tol_fit=1e-12)
+    # predictions at the block rows: a smooth function plus noise (FP32)
+    X, pts = S.block_inputs(None)
+    pts = pts.cpu().numpy()
+    rng = np.random.default_rng(4)
+    u = (np.sin(3 * pts[:, 0]) + np.cos(2 * pts[:, 1]) + 0.01 * rng.standard_normal(len(pts))).astype(np.float32)
+    y0 = S.warm_start(torch.from_numpy(u).cuda())
+    a_gpu = S.coefficients(y0).cpu().numpy()
+    # oracle: the same kept sets as the GPU filter (FP64 assembly), its own QR
+    B = oracle.assemble(p, prm)
+    F = oracle.filter_blocks(B, tol)
+    ranks = ranks.cpu().numpy()
+    perm = perm.cpu().numpy()
+    for j, f in enumerate(F):
+        assert f.rank == ranks[j]
+        assert np.array_equal(np.sort(f.perm[: f.rank]), np.sort(perm[j * p.K: j * p.K + f.rank]))
+    uh = []
+    for j in range(p.J):
+        m, ld, _, roff = S.block_info(j)
+        uh.append(u[roff:roff + m].astype(np.float64))
+    ys, cs = oracle.local_fit(p, prm, B, F, uh, tol_fit=1e-12)
+    a_orc = oracle.build_system(B, F).coefficients(np.concatenate(ys))
+    kap = 1.0
+    for j, f in enumerate(F):
+        Xj, _ = oracle.row_points(p, B.grow[j])
+        Phi = oracle.feature_values(p, prm, j, Xj)[:, f.perm[: f.rank]]
+        kap = max(kap, np.linalg.cond(Phi))
+    scale = np.abs(a_orc).max()
+    assert np.abs(a_gpu - a_orc).max() <= 1e-12 * kap * scale, (np.abs(a_gpu - a_orc).max() / scale, kap)
+    Xt = torch.from_numpy(oracle.test_grid(p, [20] * p.dim)).cuda()
+    ug, _ = S.evaluate(d, torch.from_numpy(a_gpu).cuda(), [Xt], with_error=False)
+    uo = oracle.evaluate(p, prm, a_orc, Xt.cpu().numpy())
+    assert np.abs(ug[0].cpu().numpy() - uo).max() <= 1e-10 * max(1.0, np.abs(uo).max())
+
+
+def test_warm_start_of_exact_predictions_starts_near_the_solution(rfm):
+    # predictions equal to the exact solution: LSQR from the fit needs fewer
+    # iterations than from zero to the same stopping rule
+    p = synth.poisson1d(S=8, K=60, n=400)
+    prm = synth.feature_params(p)
+    S, d = _system(rfm, p, prm, op="q64", tol=1e-10)
+    S.filter()
+    S.fit_prepare(d, tol_fit=1e-10)
+    _, pts = S.block_inputs(None)
+    u = torch.from_numpy(oracle.exact(p, pts.cpu().numpy()[:, :1]).astype(np.float32)).cuda()
+    y0 = S.warm_start(u)
+    a_cold, rep_cold = S.solve(atol=1e-9, btol=1e-9, max_iter=20000)
+    a_warm, rep_warm = S.solve(atol=1e-9, btol=1e-9, max_iter=20000, y0=y0)
+    from paper_2506_17626_gb300 import report_dict
+    rc, rw = report_dict(rep_cold), report_dict(rep_warm)
+    assert rc["istop"] in (1, 2) and rw["istop"] in (1, 2)
+    assert rw["itn"] < rc["itn"]
