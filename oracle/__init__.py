@@ -464,28 +464,74 @@ def adam_step(theta, m, v, g, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
                         float(eps))
 
 
-def local_fit(p, params, B: Blocks, F, uhat, tol_fit=1e-10):
-    """Warm start from predicted values: for every block j, the least-squares
-    fit of the predictions uhat[j] at the block's rows through the values of
-    its kept features (in pivot order), truncated by QR with column pivoting
-    at tol_fit relative to |R_11|; then y0_j = R_j c_j, so that the
-    preconditioned unknowns start at the fitted coefficients (a = S^-1 y).
-    Returns the list of y0_j and the list of fitted coefficients c_j."""
-    ys, cs = [], []
+def _value_blocks(p, params, B: Blocks, F):
+    """Window-weighted values of every block's kept features (pivot order of
+    the system's filter) at the block's rows, and the window at those rows."""
+    out, ws = [], []
     for j, (g, f) in enumerate(zip(B.grow, F)):
-        r = f.rank
-        if r == 0:
-            ys.append(np.zeros(0))
-            cs.append(np.zeros(0))
-            continue
         X, _ = row_points(p, g)
-        Phi = feature_values(p, params, j, X)[:, f.perm[:r]]
-        G = qrcp(Phi, tol_fit)
-        k = G.rank
+        w = np.array([window(p, j, x)[0] for x in X])
+        Phi = feature_values(p, params, j, X)[:, f.perm[: f.rank]]
+        out.append(np.asfortranarray(w[:, None] * Phi))
+        ws.append(w)
+    return out, ws
+
+
+def local_fit(p, params, B: Blocks, F, uhat, tol_fit=1e-10):
+    """Warm start from predicted values, block by block: for every block j,
+    the least-squares fit of w_j uhat[j] at the block's rows through its
+    window-weighted kept features w_j phi_jk (pivot order), truncated by QR
+    with column pivoting at tol_fit relative to |R_11|; then y0_j = R_j c_j,
+    so that the preconditioned unknowns start at the fitted coefficients
+    (a = S^-1 y).  Returns the list of y0_j and of the coefficients c_j."""
+    V, ws = _value_blocks(p, params, B, F)
+    ys, cs = [], []
+    for j, f in enumerate(F):
+        r = f.rank
         c = np.zeros(r)
-        if k:
-            z = G.Q().T @ np.asarray(uhat[j], dtype=np.float64)
-            c[G.perm[:k]] = trsv(G.R, z)
+        if r:
+            G = qrcp(V[j], tol_fit)
+            k = G.rank
+            if k:
+                z = G.Q().T @ (ws[j] * np.asarray(uhat[j], dtype=np.float64))
+                c[G.perm[:k]] = trsv(G.R, z)
         cs.append(c)
-        ys.append(f.R @ c)
+        ys.append(f.R @ c if r else np.zeros(0))
     return ys, cs
+
+
+def blend(p, B: Blocks, uhat):
+    """u_bar(x_r) = sum_j w_j(x_r) uhat_j(x_r) over the blocks covering row r
+    (the partition of unity applied to the per-block predictions)."""
+    ub = np.zeros(B.N)
+    for j, g in enumerate(B.grow):
+        X, _ = row_points(p, g)
+        w = np.array([window(p, j, x)[0] for x in X])
+        ub[g] += w * np.asarray(uhat[j], dtype=np.float64)
+    return ub
+
+
+def global_fit(p, params, B: Blocks, F, uhat, tol_fit=1e-10, iters=100):
+    """Warm start from predicted values through all blocks at once: the
+    least-squares fit of the blended prediction u_bar at every collocation row
+    by sum_j w_j phi_j c_j over the kept features, solved the paper's way --
+    per block QR with column pivoting of the window-weighted values (threshold
+    tol_fit), LSQR (iters iterations from zero) on the right-preconditioned
+    fitting system, c = R_V^-1 z -- and finally y0_j = R_j c_j.  Returns y0_j,
+    c_j per block and the LSQR result of the fit."""
+    V, _ = _value_blocks(p, params, B, F)
+    G = [qrcp(Vj, tol_fit) for Vj in V]
+    fitsys = FilteredSystem(B.N, B.grow, [g.Q() for g in G], None, mode=1)
+    res = fitsys.lsqr(blend(p, B, uhat), atol=0.0, btol=0.0, max_iter=iters)
+    z = res["y"]
+    ys, cs = [], []
+    off = 0
+    for f, g in zip(F, G):
+        c = np.zeros(f.rank)
+        k = g.rank
+        if k:
+            c[g.perm[:k]] = trsv(g.R, z[off:off + k])
+        off += k
+        cs.append(c)
+        ys.append(f.R @ c if f.rank else np.zeros(0))
+    return ys, cs, res

@@ -185,6 +185,12 @@ def param5(a, b, c, d, e, S=20, K=300, n=200, delta=1.25, R=8.0, seed=0, n_test=
                    n_test=[n_test, n_test], name="param5")
 
 
+def param5_context(fp) -> np.ndarray:
+    """(a, b, c, d, e) scaled by their ranges' upper ends to O(1) network inputs."""
+    a, b, c, d, e = fp
+    return np.array([a / 12.0, b / 12.0, c / 0.5, d / 30.0, e / 30.0], dtype=np.float32)
+
+
 def param5_draw(seed: int) -> List[float]:
     """(a, b, c, d, e) with a, b ~ U[1,12], c ~ U[0,0.5], d, e ~ U[10,30]."""
     u = splitmix64_unit(seed, 5, offset=1 << 41)

@@ -1,8 +1,10 @@
-"""Pins of the oracle's local fit (learned warm start): predictions that the
-kept features represent exactly are recovered exactly; a full-rank fit equals
-numpy's least squares; the partition of unity turns exact local predictions
-into a global approximation of the solution; and LSQR started from the fit
-needs fewer iterations than from zero."""
+"""Pins of the oracle's fits of predicted values (learned warm start): the
+local fit recovers predictions that the kept features represent exactly and
+equals numpy's weighted least squares at full rank; the partition of unity
+turns exact local predictions into the solution; LSQR started from a fit
+needs fewer iterations than from zero; the blend of identical per-block
+predictions is the prediction itself; and the global fit run to convergence
+equals numpy's least squares on the assembled window-weighted value matrix."""
 import numpy as np
 import pytest
 
@@ -57,9 +59,10 @@ def test_full_rank_fit_is_numpy_least_squares():
     ys, cs = oracle.local_fit(p, prm, B, F, uh, tol_fit=1e-14)
     for j, (g, f) in enumerate(zip(B.grow, F)):
         X, _ = oracle.row_points(p, g)
-        Phi = oracle.feature_values(p, prm, j, X)[:, f.perm[: f.rank]]
+        w = np.array([oracle.window(p, j, x)[0] for x in X])
+        Phi = w[:, None] * oracle.feature_values(p, prm, j, X)[:, f.perm[: f.rank]]
         assert np.linalg.matrix_rank(Phi) == f.rank
-        ref = np.linalg.lstsq(Phi, uh[j], rcond=None)[0]
+        ref = np.linalg.lstsq(Phi, w * uh[j], rcond=None)[0]
         kappa = np.linalg.cond(Phi)
         assert cs[j] == pytest.approx(ref, rel=1e-13 * kappa, abs=1e-13 * kappa * np.abs(ref).max())
 
@@ -100,3 +103,37 @@ def test_warm_start_needs_fewer_lsqr_iterations():
     warm = S.lsqr(B.h, y0=np.concatenate(ys), atol=1e-9, btol=1e-9, max_iter=20000)
     assert warm["istop"] in (1, 2) and cold["istop"] in (1, 2)
     assert warm["itn"] < cold["itn"]
+
+
+def test_blend_of_identical_predictions_is_the_prediction():
+    p = synth.poisson2d(S=4, K=6, n=20, delta=2.0)
+    prm, B, F = _setup(p)
+    f = lambda X: np.sin(2 * X[:, 0]) * np.cos(X[:, 1])
+    uh = [f(oracle.row_points(p, g)[0]) for g in B.grow]
+    ub = oracle.blend(p, B, uh)
+    Xr, _ = oracle.row_points(p, np.arange(B.N))
+    assert ub == pytest.approx(f(Xr), rel=1e-13, abs=1e-14)
+
+
+def test_global_fit_converges_to_least_squares_on_the_value_matrix():
+    p = synth.poisson1d(S=4, K=6, n=40)
+    prm, B, F = _setup(p)
+    rng = np.random.default_rng(3)
+    uh = [rng.standard_normal(len(g)) for g in B.grow]
+    ys, cs, res = oracle.global_fit(p, prm, B, F, uh, tol_fit=1e-14, iters=5000)
+    # the assembled N x (sum r_j) matrix of window-weighted kept features
+    cols = sum(f.rank for f in F)
+    A = np.zeros((B.N, cols))
+    c0 = 0
+    for j, (g, f) in enumerate(zip(B.grow, F)):
+        X, _ = oracle.row_points(p, g)
+        w = np.array([oracle.window(p, j, x)[0] for x in X])
+        A[g, c0:c0 + f.rank] = w[:, None] * oracle.feature_values(p, prm, j, X)[:, f.perm[: f.rank]]
+        c0 += f.rank
+    ub = oracle.blend(p, B, uh)
+    assert np.linalg.matrix_rank(A) == cols
+    ref = np.linalg.lstsq(A, ub, rcond=None)[0]
+    got = np.concatenate(cs)
+    kappa = np.linalg.cond(A)
+    assert np.linalg.norm(A @ got - ub) <= np.linalg.norm(A @ ref - ub) * (1 + 1e-8) + 1e-12
+    assert got == pytest.approx(ref, rel=1e-12 * kappa, abs=1e-12 * kappa * np.abs(ref).max())
