@@ -17,8 +17,8 @@ The target error and the iteration counts come from an untimed calibration
 that records LSQR iterates every 100 iterations up to the paper's budget of
 10,000 iterations and evaluates each one; the target is the tightest value of
 a fixed ladder that both the mixed path and the plain FP64 path (FP64
-assembly, FP64 kept columns with R^-1 substitution, zero start) reach.  Both
-paths are timed; "value" is the mixed path.
+assembly, FP64 QRCP, explicit FP64 Q_hat of Proposition 3.1, zero start)
+reach.  Both paths are timed; "value" is the mixed path.
 """
 from __future__ import annotations
 
@@ -172,7 +172,7 @@ def run_gpu(args):
         S = R.System([p], asm=asm, op=op, tol=TOL, device=str(dev))
         return S
 
-    paths = {"mixed": make("fp32", "q32"), "fp64": make("fp64", "ar64")}
+    paths = {"mixed": make("fp32", "q32"), "fp64": make("fp64", "q64")}
 
     # ---- calibration (untimed): error after every SNAP_EVERY iterations
     curves, conv = {}, {}
@@ -422,8 +422,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
-    ap.add_argument("--ref-iters", type=int, default=300,
-                    help="LSQR iteration count the reference arm extrapolates to")
+    ap.add_argument("--ref-iters", type=int, default=2600,
+                    help="LSQR iteration count the reference arm extrapolates to (the calibrated count of the "
+                         "GPU arm on this workload)")
     ap.add_argument("--iters-mixed", type=int, default=None, help="skip calibration: LSQR iterations (mixed)")
     ap.add_argument("--iters-fp64", type=int, default=None, help="skip calibration: LSQR iterations (FP64)")
     ap.add_argument("--target", type=float, default=None, help="target recorded when calibration is skipped")

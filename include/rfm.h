@@ -258,21 +258,30 @@ rfm_status rfm_block_inputs(const rfm_problem *probs, int n_inst, const rfm_conf
  * system's block shape plus per-column pivots). */
 rfm_status rfm_fit_size(const rfm_problem *probs, int n_inst, const rfm_config *cfg, size_t *bytes);
 
-/* Per block: the values of the kept features (pivot order of rfm_rrqr_filter)
- * at the block's rows, factored by QR with column pivoting truncated at
- * tol_fit |R_11| (the same kernels as Algorithm 1), with explicit Q_hat.
+/* Per block: the window-weighted values of the kept features (pivot order of
+ * rfm_rrqr_filter) at the block's rows, factored by QR with column pivoting
+ * truncated at tol_fit |R_11| (the same kernels as Algorithm 1), with explicit
+ * Q_hat.
  * Needs rfm_assemble and rfm_rrqr_filter on d_ws (any operator but PLAIN).
  * d_fit_ws: 256-byte aligned, rfm_fit_size bytes, owned by the caller. */
 rfm_status rfm_fit_prepare(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const double *d_params,
                            double tol_fit, void *d_ws, size_t ws_bytes, void *d_fit_ws, size_t fit_bytes,
                            void *stream);
 
-/* y0 from predictions d_uhat (FP32, block-row layout as rfm_block_inputs):
- * per block the truncated least-squares coefficients c_j of the predictions
- * in the kept features, then y0 = R_j c_j in the column-slot layout of
+/* y0 from predictions d_uhat (FP32, block-row layout as rfm_block_inputs),
+ * multiplied per instance by d_inst_scale[inst] when that is not NULL (a
+ * network trained on targets brought to a common scale).
+ * fit_iters = 0: local fit, per block the truncated least-squares coefficients
+ * c_j of w_j u_hat_j in the window-weighted kept features.  fit_iters > 0:
+ * global fit, the blended prediction sum_j w_j u_hat_j at every collocation
+ * row fitted through all blocks' window-weighted kept features at once by
+ * fit_iters LSQR iterations on the block-preconditioned fitting system (the
+ * system's LSQR scratch is reused: do not overlap with rfm_lsqr_solve on the
+ * same workspace).  Then y0 = R_j c_j in the column-slot layout of
  * rfm_lsqr_solve (slots beyond a block's rank set to 0). */
 rfm_status rfm_warm_start(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const float *d_uhat,
-                          double *d_y0, void *d_ws, size_t ws_bytes, void *d_fit_ws, size_t fit_bytes, void *stream);
+                          const float *d_inst_scale, int fit_iters, double *d_y0, void *d_ws, size_t ws_bytes,
+                          void *d_fit_ws, size_t fit_bytes, void *stream);
 
 /* The network: fully connected, widths width[0..n_layers], tanh on hidden
  * layers, one linear output (width[n_layers] = 1); input width 1..32, hidden
@@ -308,6 +317,11 @@ rfm_status rfm_adam_step(int64_t n, float *d_theta, float *d_m, float *d_v, cons
  * grow[roff .. roff+|I_j|).  Host only. */
 rfm_status rfm_block_info(const rfm_problem *probs, int n_inst, const rfm_config *cfg, int64_t block,
                           int64_t *m, int64_t *ld, int64_t *moff, int64_t *roff);
+
+/* rfm_block_info for every block at once: host arrays of n_blocks entries
+ * (any may be NULL). */
+rfm_status rfm_block_table(const rfm_problem *probs, int n_inst, const rfm_config *cfg, int64_t *m, int64_t *ld,
+                           int64_t *moff, int64_t *roff);
 
 /* Device pointers into the workspace (views for tests and for the warm
  * start): which = 0 M arena (FP64 or FP32 by asm_prec), 1 h (FP64, n_rows),

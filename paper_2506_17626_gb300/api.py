@@ -7,6 +7,7 @@ from __future__ import annotations
 import ctypes as C
 from typing import Optional, Sequence
 
+import numpy as np
 import torch
 
 from . import _native as N
@@ -111,6 +112,14 @@ class System:
                                               self.ws_bytes, _stream()))
         return [u[offs[i]:offs[i + 1]] for i in range(self.n)], err
 
+    def block_table(self):
+        """(m, ld, moff, roff) of every block as int64 numpy arrays."""
+        nb = self.sizes["n_blocks"]
+        arrs = [np.zeros(nb, dtype=np.int64) for _ in range(4)]
+        N.check("rfm_block_table", self.lib.rfm_block_table(self._probs, self.n, C.byref(self._cfg),
+                                                            *[a.ctypes.data_as(C.c_void_p) for a in arrs]))
+        return tuple(arrs)
+
     # -- learned warm start -------------------------------------------------------------
     def block_inputs(self, ctx: Optional[torch.Tensor], want_points: bool = True):
         """Network inputs at every block row (block-row layout, padding rows
@@ -140,13 +149,21 @@ class System:
                                                             float(tol_fit), C.c_void_p(self.ws_ptr), self.ws_bytes,
                                                             C.c_void_p(self.fws_ptr), self.fit_bytes, _stream()))
 
-    def warm_start(self, uhat: torch.Tensor) -> torch.Tensor:
-        """y0 (column-slot layout) from predictions at the block rows (FP32)."""
+    def warm_start(self, uhat: torch.Tensor, fit_iters: int = 0,
+                   inst_scale: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """y0 (column-slot layout) from predictions at the block rows (FP32),
+        optionally multiplied by a per-instance scale (FP32, one per instance):
+        fit_iters = 0 fits block by block, > 0 fits all blocks at once with
+        that many LSQR iterations."""
         assert uhat.is_cuda and uhat.dtype == torch.float32 and uhat.numel() >= self.sizes["block_rows"]
+        if inst_scale is not None:
+            assert inst_scale.is_cuda and inst_scale.dtype == torch.float32 and inst_scale.numel() == self.n
         y0 = torch.empty(self.sizes["n_cols"], dtype=torch.float64, device=self.device)
         N.check("rfm_warm_start", self.lib.rfm_warm_start(self._probs, self.n, C.byref(self._cfg), _ptr(uhat),
-                                                          _ptr(y0), C.c_void_p(self.ws_ptr), self.ws_bytes,
-                                                          C.c_void_p(self.fws_ptr), self.fit_bytes, _stream()))
+                                                          _ptr(inst_scale), int(fit_iters), _ptr(y0),
+                                                          C.c_void_p(self.ws_ptr),
+                                                          self.ws_bytes, C.c_void_p(self.fws_ptr), self.fit_bytes,
+                                                          _stream()))
         return y0
 
     # -- views for tests --------------------------------------------------------------

@@ -22,7 +22,8 @@ rfm_status launch_eval(const HostPlan &P, void *ws, const double *params, const 
 size_t fit_workspace_bytes(const HostPlan &P);
 rfm_status launch_fit_prepare(const HostPlan &P, void *ws, const double *params, double tol_fit, void *fws,
                               cudaStream_t st);
-rfm_status launch_warm_start(const HostPlan &P, void *ws, void *fws, const float *uhat, double *y0, cudaStream_t st);
+rfm_status launch_warm_start(const HostPlan &P, void *ws, void *fws, const float *uhat, const float *iscale,
+                             int fit_iters, double *y0, cudaStream_t st);
 rfm_status launch_block_inputs(const HostPlan &P, void *ws, const float *ctx, int n_ctx, float *X, double *pts,
                                cudaStream_t st);
 rfm_status mlp_nparams(const rfm_mlp *net, int64_t *np);
@@ -283,6 +284,22 @@ rfm_status rfm_block_info(const rfm_problem *probs, int n_inst, const rfm_config
     RFM_GUARD_END
 }
 
+rfm_status rfm_block_table(const rfm_problem *probs, int n_inst, const rfm_config *cfg, int64_t *m, int64_t *ld,
+                           int64_t *moff, int64_t *roff) {
+    RFM_GUARD_BEGIN
+    Plan P(probs, n_inst, cfg);
+    if (!P.ok) return P.rc;
+    for (int64_t b = 0; b < P.p.L.n_blocks; ++b) {
+        const BlkRec &B = P.p.blk[b];
+        if (m) m[b] = B.m;
+        if (ld) ld[b] = B.ldm;
+        if (moff) moff[b] = B.moff;
+        if (roff) roff[b] = B.roff;
+    }
+    return RFM_OK;
+    RFM_GUARD_END
+}
+
 rfm_status rfm_workspace_view(const rfm_problem *probs, int n_inst, const rfm_config *cfg, void *d_ws, int which,
                               void **ptr) {
     RFM_GUARD_BEGIN
@@ -367,7 +384,8 @@ rfm_status rfm_fit_prepare(const rfm_problem *probs, int n_inst, const rfm_confi
 }
 
 rfm_status rfm_warm_start(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const float *d_uhat,
-                          double *d_y0, void *d_ws, size_t ws_bytes, void *d_fit_ws, size_t fit_bytes, void *stream) {
+                          const float *d_inst_scale, int fit_iters, double *d_y0, void *d_ws, size_t ws_bytes,
+                          void *d_fit_ws, size_t fit_bytes, void *stream) {
     RFM_GUARD_BEGIN
     Plan P(probs, n_inst, cfg);
     if (!P.ok) return P.rc;
@@ -379,7 +397,11 @@ rfm_status rfm_warm_start(const rfm_problem *probs, int n_inst, const rfm_config
         set_error("rfm_warm_start: null argument");
         return RFM_EINVAL;
     }
-    return launch_warm_start(P.p, d_ws, d_fit_ws, d_uhat, d_y0, (cudaStream_t)stream);
+    if (fit_iters < 0) {
+        set_error("rfm_warm_start: fit_iters must be >= 0");
+        return RFM_EINVAL;
+    }
+    return launch_warm_start(P.p, d_ws, d_fit_ws, d_uhat, d_inst_scale, fit_iters, d_y0, (cudaStream_t)stream);
     RFM_GUARD_END
 }
 

@@ -78,10 +78,12 @@ struct Layout {
     size_t off_evpart;                                  // eval scratch
     int64_t n_fwd_items, n_col_items;                   // LSQR tile work items
     size_t off_fwd_items, off_col_items;
-    size_t off_items, off_nitems, off_tpart, off_qblk;  // live column items, per-item row partials, block of each block row
+    size_t off_items, off_nitems, off_z, off_qblk;      // live column items, transposed-product scratch, block of each block row
     size_t off_tu;                                      // u~ on the block rows in operator precision
     size_t off_fitems, off_nfitems;                     // live forward items (128-row tiles)
     int64_t n_slots;                                    // column items per block at most (ceil(max_K / 8))
+    int64_t n_t_items;                                  // column chunks of the staged transposed product (bound)
+    size_t off_titems, off_ntitems;
     size_t total;
     int asm_prec, op;
 };
@@ -101,6 +103,14 @@ struct HostPlan {
 };
 
 constexpr int kFwdRows = 128;  // rows of a forward (A x) work item (one warp)
+constexpr int kTStageBytes = 20480;  // bytes of one staged column chunk of the transposed product
+constexpr int kTStages = 3;          // depth of that staging ring
+
+// Columns per staged chunk of a block with leading dimension ldm.
+__host__ __device__ inline int tchunk_cols(int ldm, int elem_bytes) {
+    const int c = kTStageBytes / (ldm * elem_bytes);
+    return c < 1 ? 1 : c;
+}
 constexpr int kColTile = 8;    // columns of a transpose (A^T u) work item (one warp)
 
 // Builds the plan (validates, computes records and layout).  Returns RFM_OK or

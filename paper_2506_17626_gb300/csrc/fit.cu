@@ -2,23 +2,27 @@
 // block's rows to a starting point y0 of the preconditioned LSQR.
 //
 // Per block j with kept features k_1..k_r (pivot order of the system's
-// filter) and predictions u_hat at the block's rows:
-//   Phi_j[i, c] = phi_{j k_c}(x_i)        (feature values, no window)
-//   c_j = argmin ||Phi_j c - u_hat||      (QR with column pivoting of Phi_j,
-//                                          truncated at tol_fit |R_11|)
-//   y0_j = R_j c_j                         (R_j: the system's filter factor)
-// so that a = S^-1 y0 starts at the fitted coefficients.  By the partition of
-// unity, sum_j w_j phi_j c_j reproduces the predictions where every block
-// fits them.  Phi_j and its factors depend only on the decomposition and the
-// features: rfm_fit_prepare forms them once; rfm_warm_start then costs one
-// transposed product with Q_hat(Phi_j) and two triangular passes per block.
+// filter), window w_j and predictions u_hat_j at the block's rows:
+//   V_j[i, c] = w_j(x_i) phi_{j k_c}(x_i)   (window-weighted feature values)
+//   V_j P_j = Q_j R_Vj                      (QR with column pivoting,
+//                                            truncated at tol_fit |R_11|)
+// Local fit (fit_iters = 0): c_j = argmin ||V_j c - w_j u_hat_j||.
+// Global fit (fit_iters > 0): the blended prediction u_bar(x_r) =
+//   sum_j w_j(x_r) u_hat_j(x_r) at every collocation row is fitted by
+//   sum_j V_j c_j through all blocks at once -- LSQR on the right-
+//   preconditioned fitting system [Q_1 ... Q_J] z = u_bar (the explicit
+//   operator of Proposition 3.1 for the value blocks), c_j = P_j R_Vj^-1 z_j.
+// Either way y0_j = R_j c_j with R_j the system's filter factor, so that
+// a = S^-1 y0 starts at the fitted coefficients.  V_j and its factors depend
+// only on the decomposition and the features: rfm_fit_prepare forms them
+// once.
 #include "device.cuh"
 #include "prof.cuh"
 
 namespace rfm {
 
 struct FitLayout {
-    size_t off_phi, off_w, off_q, off_tau, off_perm, off_rank, off_r11, total;
+    size_t off_phi, off_w, off_q, off_tau, off_perm, off_rank, off_r11, off_wrow, off_hbar, off_z, total;
     int64_t melem;
 };
 
@@ -41,20 +45,26 @@ static FitLayout fit_layout(const HostPlan &P) {
     F.off_perm = take((size_t)ncol * 4);
     F.off_rank = take((size_t)nb * 4);
     F.off_r11 = take((size_t)nb * 8);
+    F.off_wrow = take((size_t)P.L.block_rows * 8);
+    F.off_hbar = take((size_t)P.L.n_rows * 8);
+    F.off_z = take((size_t)ncol * 8);
     F.total = o;
     return F;
 }
 
 size_t fit_workspace_bytes(const HostPlan &P) { return fit_layout(P).total; }
 
-// Phi of every block over its kept columns (pivot order), zero columns from
-// the block's rank on and zero padding rows; one CTA per 32-row tile.
+// V of every block over its kept columns (pivot order): window times feature
+// value; zero columns from the block's rank on and zero padding rows; the
+// window of every block row into wrow.  One CTA per 32-row tile.
 __global__ void __launch_bounds__(256) k_fit_values(const InstRec *__restrict__ insts, const BlkRec *__restrict__ blks,
                                                     const int32_t *__restrict__ tile_blk,
                                                     const int32_t *__restrict__ tile_row,
                                                     const double *__restrict__ params, const int32_t *__restrict__ perm,
-                                                    const int32_t *__restrict__ rank, double *__restrict__ Phi) {
+                                                    const int32_t *__restrict__ rank, double *__restrict__ Phi,
+                                                    double *__restrict__ wrow) {
     __shared__ double s_s[32][3];
+    __shared__ double s_w[32];
     __shared__ BlkRec sB;
     __shared__ InstRec sI;
     const int tile = blockIdx.x;
@@ -69,13 +79,17 @@ __global__ void __launch_bounds__(256) k_fit_values(const InstRec *__restrict__ 
     const int r0 = tile_row[tile];
     const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
     if (wy == 0) {
-        double x[3] = {0, 0, 0};
+        double x[3] = {0, 0, 0}, w = 0.0;
         const int lr = r0 + lane;
         if (lr < B.m) {
             int kind, gcov[3];
             block_row_point(I, B, lr, x, &kind, gcov);
+            double dw[3], d2w[3];
+            window_nd(I, B.jd, x, &w, dw, d2w);
         }
         for (int i = 0; i < 3; ++i) s_s[lane][i] = i < I.dim ? (x[i] - B.mu[i]) / B.sig[i] : 0.0;
+        s_w[lane] = w;
+        if (lr < B.ldm) wrow[B.roff + lr] = w;
     }
     __syncthreads();
     const int lr = r0 + lane;
@@ -89,28 +103,53 @@ __global__ void __launch_bounds__(256) k_fit_values(const InstRec *__restrict__ 
             const double *pk = prm + (int64_t)perm[B.coff + c] * (d + 1);
             double z = pk[d];
             for (int i = 0; i < d; ++i) z = fma(pk[i], s_s[lane][i], z);
-            v = tanh(z);
+            v = s_w[lane] * tanh(z);
         }
         out[(int64_t)c * B.ldm] = v;
     }
 }
 
-// One CTA per block: z = Q_hat(Phi)^T u_hat, R(Phi) c' = z, scatter c' by the
-// fit's pivots into c, y0 = R c over the system's kept columns.
-__global__ void __launch_bounds__(256) k_fit_apply(const BlkRec *__restrict__ blks, const double *__restrict__ Qf,
+// c = P_V R_V^-1 z (z: k entries in shared memory, FP64 back substitution),
+// scattered into the system's pivot order, then y0 = R c.
+__device__ void fit_finish_block(const BlkRec &B, int r, int k, const double *Wf, const int32_t *permf,
+                                 const double *W, double *z, double *c, double *y0) {
+    const int tid = threadIdx.x, ld = B.ldm, K = B.K;
+    const double *Rf = Wf + B.moff;
+    for (int j = k - 1; j >= 0; --j) {
+        if (tid == 0) z[j] = z[j] / Rf[(int64_t)j * ld + j];
+        __syncthreads();
+        const double xj = z[j];
+        for (int i = tid; i < j; i += 256) z[i] = fma(-Rf[(int64_t)j * ld + i], xj, z[i]);
+        __syncthreads();
+    }
+    for (int t = tid; t < k; t += 256) c[permf[B.coff + t]] = z[t];
+    __syncthreads();
+    const double *R = W + B.moff;
+    for (int i = tid; i < K; i += 256) {
+        double s = 0.0;
+        if (i < r)
+            for (int j = i; j < r; ++j) s = fma(R[(int64_t)j * ld + i], c[j], s);
+        y0[B.coff + i] = s;
+    }
+}
+
+// Local fit, one CTA per block: z = Q_V^T (w u_hat), then fit_finish_block.
+__global__ void __launch_bounds__(256) k_fit_local(const BlkRec *__restrict__ blks, const double *__restrict__ Qf,
                                                    const double *__restrict__ Wf, const int32_t *__restrict__ permf,
                                                    const int32_t *__restrict__ rankf, const double *__restrict__ W,
-                                                   const int32_t *__restrict__ rank, const float *__restrict__ uhat,
+                                                   const int32_t *__restrict__ rank, const double *__restrict__ wrow,
+                                                   const float *__restrict__ uhat, const float *__restrict__ iscale,
                                                    double *__restrict__ y0) {
     extern __shared__ double fs[];
     const BlkRec &B = blks[blockIdx.x];
     const int m = B.m, ld = B.ldm, K = B.K;
     const int r = rank[blockIdx.x], k = rankf[blockIdx.x];
-    double *u = fs;          // m
+    double *u = fs;          // ld
     double *z = u + ld;      // K
     double *c = z + K;       // K
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < m; i += 256) u[i] = (double)uhat[B.roff + i];
+    const double sc = iscale ? (double)iscale[B.inst] : 1.0;
+    for (int i = tid; i < m; i += 256) u[i] = wrow[B.roff + i] * ((double)uhat[B.roff + i] * sc);
     for (int t = tid; t < K; t += 256) c[t] = 0.0;
     __syncthreads();
     const double *Qb = Qf + B.moff;
@@ -122,24 +161,44 @@ __global__ void __launch_bounds__(256) k_fit_apply(const BlkRec *__restrict__ bl
         if (lane == 0) z[t] = s;
     }
     __syncthreads();
-    // back substitution with R(Phi) (upper triangle of the fit's QR work)
-    const double *Rf = Wf + B.moff;
-    for (int j = k - 1; j >= 0; --j) {
-        if (tid == 0) z[j] = z[j] / Rf[(int64_t)j * ld + j];
-        __syncthreads();
-        const double xj = z[j];
-        for (int i = tid; i < j; i += 256) z[i] = fma(-Rf[(int64_t)j * ld + i], xj, z[i]);
-        __syncthreads();
+    fit_finish_block(B, r, k, Wf, permf, W, z, c, y0);
+}
+
+// Global fit, after LSQR on the fitting system: z per block from zg.
+__global__ void __launch_bounds__(256) k_fit_finish(const BlkRec *__restrict__ blks, const double *__restrict__ Wf,
+                                                    const int32_t *__restrict__ permf, const int32_t *__restrict__ rankf,
+                                                    const double *__restrict__ W, const int32_t *__restrict__ rank,
+                                                    const double *__restrict__ zg, double *__restrict__ y0) {
+    extern __shared__ double fs[];
+    const BlkRec &B = blks[blockIdx.x];
+    const int K = B.K, r = rank[blockIdx.x], k = rankf[blockIdx.x];
+    double *z = fs;       // K
+    double *c = z + K;    // K
+    for (int t = threadIdx.x; t < K; t += 256) {
+        z[t] = t < k ? zg[B.coff + t] : 0.0;
+        c[t] = 0.0;
     }
-    for (int t = tid; t < k; t += 256) c[permf[B.coff + t]] = z[t];
     __syncthreads();
-    // y0 = R c with R the system's filter factor (r x r, upper)
-    const double *R = W + B.moff;
-    for (int i = tid; i < K; i += 256) {
-        double s = 0.0;
-        if (i < r)
-            for (int j = i; j < r; ++j) s = fma(R[(int64_t)j * ld + i], c[j], s);
-        y0[B.coff + i] = s;
+    fit_finish_block(B, r, k, Wf, permf, W, z, c, y0);
+}
+
+// u_bar at every collocation row: sum over the block rows holding it of
+// w_j(x) u_hat_j(x) (same order as the rows' lists).
+__global__ void k_fit_blend(const InstRec *__restrict__ insts, int n_inst, const int32_t *__restrict__ rowlist,
+                            const double *__restrict__ wrow, const float *__restrict__ uhat,
+                            const float *__restrict__ iscale, double *__restrict__ hbar, int64_t n_rows) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_rows; g += (int64_t)gridDim.x * blockDim.x) {
+        int s = 0;
+        while (s + 1 < n_inst && insts[s + 1].row0 <= g) ++s;
+        const InstRec &I = insts[s];
+        const int64_t r = g - I.row0;
+        const int32_t *lst = rowlist + I.rl_off + r * I.C;
+        double acc = 0.0;
+        for (int e = 0; e < I.C; ++e) {
+            const int q = lst[e];
+            if (q >= 0) acc = fma(wrow[q], (double)uhat[q], acc);
+        }
+        hbar[g] = iscale ? acc * (double)iscale[s] : acc;
     }
 }
 
@@ -158,7 +217,7 @@ rfm_status launch_fit_prepare(const HostPlan &P, void *ws, const double *params,
         k_fit_values<<<(unsigned)L.n_tiles, 256, 0, st>>>(
             ws_ptr<InstRec>(ws, L.off_inst), ws_ptr<BlkRec>(ws, L.off_blk), ws_ptr<int32_t>(ws, L.off_tile),
             ws_ptr<int32_t>(ws, L.off_tile) + L.n_tiles, params, ws_ptr<int32_t>(ws, L.off_perm),
-            ws_ptr<int32_t>(ws, L.off_rank), Phi);
+            ws_ptr<int32_t>(ws, L.off_rank), Phi, ws_ptr<double>(fws, F.off_wrow));
         RFM_CUDA_CHECK(cudaGetLastError());
     }
     FilterBufs B;
@@ -180,23 +239,50 @@ rfm_status launch_fit_prepare(const HostPlan &P, void *ws, const double *params,
     return launch_filter_bufs(B, false, tol_fit, st);
 }
 
-rfm_status launch_warm_start(const HostPlan &P, void *ws, void *fws, const float *uhat, double *y0, cudaStream_t st) {
+rfm_status launch_lsqr_on(const HostPlan &P, void *ws, const double *Op, const int32_t *rank, const double *rhs,
+                          int iters, double *z_out, rfm_lsqr_report *rep, cudaStream_t st);
+
+rfm_status launch_warm_start(const HostPlan &P, void *ws, void *fws, const float *uhat, const float *iscale,
+                             int fit_iters, double *y0, cudaStream_t st) {
     const Layout &L = P.L;
     if (L.n_blocks == 0) return RFM_OK;
     const FitLayout F = fit_layout(P);
     const int64_t ldmax = (L.max_m + kLdAlign - 1) / kLdAlign * kLdAlign;
-    const size_t smem = (size_t)(ldmax + 2 * L.max_K) * 8;
-    if (smem > 200 * 1024) {
-        set_error("rfm_warm_start: blocks of %lld rows and %lld features exceed the kernel's shared memory",
-                  (long long)L.max_m, (long long)L.max_K);
-        return RFM_EINVAL;
+    const BlkRec *dB = ws_ptr<BlkRec>(ws, L.off_blk);
+    const double *Wf = ws_ptr<double>(fws, F.off_w);
+    const int32_t *permf = ws_ptr<int32_t>(fws, F.off_perm), *rankf = ws_ptr<int32_t>(fws, F.off_rank);
+    const double *W = ws_ptr<double>(ws, L.off_W);
+    const int32_t *rank = ws_ptr<int32_t>(ws, L.off_rank);
+    if (fit_iters <= 0) {
+        const size_t smem = (size_t)(ldmax + 2 * L.max_K) * 8;
+        if (smem > 200 * 1024) {
+            set_error("rfm_warm_start: blocks of %lld rows and %lld features exceed the local fit's shared memory",
+                      (long long)L.max_m, (long long)L.max_K);
+            return RFM_EINVAL;
+        }
+        ProfScope ps("k_fit_local", st);
+        RFM_CUDA_CHECK(cudaFuncSetAttribute(k_fit_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_fit_local<<<(unsigned)L.n_blocks, 256, smem, st>>>(dB, ws_ptr<double>(fws, F.off_q), Wf, permf, rankf, W,
+                                                             rank, ws_ptr<double>(fws, F.off_wrow), uhat, iscale, y0);
+        RFM_CUDA_CHECK(cudaGetLastError());
+        return RFM_OK;
     }
-    ProfScope ps("k_fit_apply", st);
-    RFM_CUDA_CHECK(cudaFuncSetAttribute(k_fit_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_fit_apply<<<(unsigned)L.n_blocks, 256, smem, st>>>(
-        ws_ptr<BlkRec>(ws, L.off_blk), ws_ptr<double>(fws, F.off_q), ws_ptr<double>(fws, F.off_w),
-        ws_ptr<int32_t>(fws, F.off_perm), ws_ptr<int32_t>(fws, F.off_rank), ws_ptr<double>(ws, L.off_W),
-        ws_ptr<int32_t>(ws, L.off_rank), uhat, y0);
+    double *hbar = ws_ptr<double>(fws, F.off_hbar);
+    double *zg = ws_ptr<double>(fws, F.off_z);
+    {
+        ProfScope ps("k_fit_blend", st);
+        const int64_t n = L.n_rows;
+        const unsigned g = (unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+        k_fit_blend<<<g < 1 ? 1 : g, 256, 0, st>>>(ws_ptr<InstRec>(ws, L.off_inst), L.n_inst,
+                                                    ws_ptr<int32_t>(ws, L.off_rowlist),
+                                                    ws_ptr<double>(fws, F.off_wrow), uhat, iscale, hbar, n);
+        RFM_CUDA_CHECK(cudaGetLastError());
+    }
+    rfm_status rc = launch_lsqr_on(P, ws, ws_ptr<double>(fws, F.off_q), rankf, hbar, fit_iters, zg, nullptr, st);
+    if (rc != RFM_OK) return rc;
+    ProfScope ps("k_fit_finish", st);
+    const size_t smem = (size_t)2 * L.max_K * 8;
+    k_fit_finish<<<(unsigned)L.n_blocks, 256, smem, st>>>(dB, Wf, permf, rankf, W, rank, zg, y0);
     RFM_CUDA_CHECK(cudaGetLastError());
     return RFM_OK;
 }

@@ -704,19 +704,27 @@ __global__ void k_report(const LsqrScal *__restrict__ sc, int n, rfm_lsqr_report
 
 // ---------------------------------------------------------------------------
 // Tile variant for the explicit operators (Q_hat in FP32 or FP64, or the
-// unfiltered M): the work of a phase is split into small tiles spread over
-// every CTA, so all SMs stream the operator at once.
-//   forward item  = 64 rows of one block:   t[rows] = Op_b[rows, :] v_b
-//   column item   = 8 columns of one block: vt[cols] = Op_b[:, cols]^T u~ / beta - beta v
-// A forward item is one warp over 128 rows: each lane owns four rows (16-byte
-// loads in FP32), the input vector is read in the operator's precision (a
-// copy of vt kept beside it) and the 1/alpha scaling is applied once per row.
-// A column item is one warp over 8 columns, reading u~ in the operator's
-// precision.  The column
-// updates of the Givens step (y, w) are elementwise and ride in the forward
-// phase; ||y||^2 rides in the column phase, so the stopping test of iteration
-// i is taken at the third barrier of round i+1 (with iteration i's estimates).
+// unfiltered M): the work of every phase is spread over all CTAs, so all SMs
+// stream the operator at once.
+//   forward (F): one warp per 128 rows of a block, t[rows] = Op_b[rows, :] v_b;
+//     each lane owns four rows (16-byte loads in FP32), the input vector is
+//     read in the operator's precision (a copy of vt kept beside it) and the
+//     1/alpha scaling is applied once per row;
+//   rows (R): u~ = sum of the block partials of each row - (alpha/beta) u~,
+//     copied onto the block rows in the operator's precision;
+//   transposed (T): each CTA owns a contiguous range of column chunks (block
+//     order); a chunk is contiguous in memory (column-major blocks), so it is
+//     copied whole by one bulk asynchronous copy into a ring of shared-memory
+//     stages; one warp reduces one column against the block's u~; the FP64
+//     update vt = z / beta - beta v and the sums ||vt||^2, ||y||^2 then run
+//     over the range with lane-private per-instance accumulators;
+//   scalars (S): the Givens recurrences, redundantly in every CTA.
+// The column updates of the Givens step (y, w) are elementwise and ride in
+// the forward phase; ||y||^2 rides in the transposed phase, so the stopping
+// test of iteration i is taken at the third barrier of round i+1 (with
+// iteration i's estimates).
 // ---------------------------------------------------------------------------
+
 template <typename TA>
 struct TileSmem {
     double wacc[2][kThreads / 32][64];          // per-warp partials per instance (alpha^2, ||y||^2)
@@ -727,6 +735,7 @@ struct TileSmem {
     // per-instance factors formed once per phase (no division or square root
     // in per-element code: GB300's FP64 pipe is narrow)
     double inv_alpha[64], ab[64], bn[64], inv_bn[64];
+    double zseg[kThreads / 32];   // per-warp partial dots of the transposed product
 };
 
 // Four rows of a column owned by one lane: FP32 one 16-byte load of rows
@@ -783,7 +792,8 @@ struct Rows4<double> {
 __global__ void __launch_bounds__(1024) k_build_items(const BlkRec *__restrict__ blks, int n_blocks,
                                                       const int32_t *__restrict__ rank, ColItem *__restrict__ items,
                                                       int *__restrict__ n_items, ColItem *__restrict__ fitems,
-                                                      int *__restrict__ n_fitems) {
+                                                      int *__restrict__ n_fitems, ColItem *__restrict__ titems,
+                                                      int *__restrict__ n_titems, int elem_bytes, int64_t t_cap) {
     __shared__ int scan[1024];
     __shared__ int carry;
     const int tid = threadIdx.x;
@@ -868,13 +878,58 @@ __global__ void __launch_bounds__(1024) k_build_items(const BlkRec *__restrict__
         __syncthreads();
     }
     if (tid == 0) *n_fitems = carry;
+    // staged column chunks of the transposed product: ceil(r / cc) per block
+    __syncthreads();
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n_blocks; base += 1024) {
+        const int b = base + tid;
+        int cnt = 0, r = 0, cc = 1;
+        if (b < n_blocks) {
+            r = rank ? rank[b] : blks[b].K;
+            cc = tchunk_cols(blks[b].ldm, elem_bytes);
+            cnt = (r + cc - 1) / cc;
+        }
+        scan[tid] = cnt;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            const int v = tid >= off ? scan[tid - off] : 0;
+            __syncthreads();
+            scan[tid] += v;
+            __syncthreads();
+        }
+        const int start = carry + scan[tid] - cnt;
+        if (b < n_blocks) {
+            const BlkRec &B = blks[b];
+            for (int k = 0; k < cnt; ++k) {
+                ColItem it;
+                it.b = b;
+                it.c0 = k * cc;
+                it.nc = min(cc, r - it.c0);
+                it.m = B.m;
+                it.ldm = B.ldm;
+                it.inst = B.inst;
+                it.moff = B.moff;
+                it.coff = B.coff;
+                it.roff = B.roff;
+                if (start + k < t_cap) titems[start + k] = it;   // the host sizes t_cap for every case
+            }
+        }
+        __syncthreads();
+        if (tid == 0) carry += scan[1023];
+        __syncthreads();
+    }
+    if (tid == 0) *n_titems = carry < t_cap ? carry : (int)t_cap;
 }
 
 template <typename TA>
 __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const ColItem *__restrict__ items,
                                                          const int *__restrict__ n_items_p,
                                                          const ColItem *__restrict__ fitems,
-                                                         const int *__restrict__ n_fitems_p, TA *__restrict__ tu) {
+                                                         const int *__restrict__ n_fitems_p, TA *__restrict__ tu,
+                                                         const ColItem *__restrict__ titems,
+                                                         const int *__restrict__ n_titems_p, double *__restrict__ zg,
+                                                         int max_ldm) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSmem<TA> &S = *reinterpret_cast<TileSmem<TA> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, G = gridDim.x, cta = blockIdx.x;
@@ -948,58 +1003,132 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
     };
     // forward product of block row q
     auto row_partials = [&](int64_t q) { return a.t[q]; };
-    // column items: z_c = Op_b[:, c]^T u~ (u~ of the block rows in t)
-    auto columns = [&](auto take, auto per_col) {
-        for (int64_t k = gwarp; k < n_items; k += twarps) {
-            const ColItem it = items[k];
+    // ---- transposed product through a bulk-copy ring.  This CTA owns the
+    // contiguous chunk range [u_lo, u_hi) (block order, so consecutive chunks
+    // mostly share a block and its u~).  Chunks are copied whole (they are
+    // contiguous: column-major blocks) into kTStages shared-memory stages; one
+    // warp reduces one column against u~ and stores z; the FP64 epilogue then
+    // runs over the range with lane-private per-instance sums.
+    const int64_t n_tu = *n_titems_p;
+    const int64_t u_lo = n_tu * cta / G, u_hi = n_tu * (cta + 1) / G;
+    unsigned char *ring_base = smem_raw + ((sizeof(TileSmem<TA>) + 127) / 128) * 128;
+    uint64_t *rbar = reinterpret_cast<uint64_t *>(ring_base);
+    unsigned char *stage_mem = ring_base + 128;
+    TA *ubuf = reinterpret_cast<TA *>(stage_mem + (size_t)kTStages * kTStageBytes);
+    unsigned ring_issued = 0, ring_used = 0;   // identical in every thread of the CTA
+    if (tid == 0) {
+        for (int i = 0; i < kTStages; ++i) mbar_init(&rbar[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    auto tphase = [&](auto take, auto epi) {
+        int64_t iu = u_lo;
+        auto issue = [&]() {
+            while (iu < u_hi && !take(titems[iu].inst)) ++iu;
+            if (iu >= u_hi) return;
+            if (tid == 0) {
+                const ColItem &it = titems[iu];
+                const int stage = ring_issued % kTStages;
+                const unsigned bytes = (unsigned)(it.nc * it.ldm * (int)sizeof(TA));
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&rbar[stage], bytes);
+                bulk_g2s(stage_mem + (size_t)stage * kTStageBytes, Aop + it.moff + (int64_t)it.c0 * it.ldm, bytes,
+                         &rbar[stage]);
+            }
+            ++ring_issued;
+            ++iu;
+        };
+        for (int st = 0; st < kTStages; ++st) issue();
+        int cur_b = -1;
+        for (int64_t cu = u_lo; cu < u_hi; ++cu) {
+            const ColItem it = titems[cu];
             if (!take(it.inst)) continue;
-            TA acc[kColTile];
-#pragma unroll
-            for (int j = 0; j < kColTile; ++j) acc[j] = (TA)0;
-            const TA *base = Aop + it.moff + (int64_t)it.c0 * it.ldm;
-            constexpr int H = sizeof(TA) == 4 ? 2 : 1;   // 128-row chunks per round trip (64 registers of loads)
-            for (int r0 = 0; r0 < it.m; r0 += 128 * H) {
-                TA uv[H][4];
-                TA q[H][kColTile][4];
-#pragma unroll
-                for (int h = 0; h < H; ++h) {
-                    Rows4<TA>::load_rw(tu + it.roff, r0 + 128 * h, lane, it.ldm, uv[h]);
-#pragma unroll
-                    for (int j = 0; j < kColTile; ++j) {
-                        if (j < it.nc && r0 + 128 * h < it.m) {
-                            Rows4<TA>::load(base + (int64_t)j * it.ldm, r0 + 128 * h, lane, it.ldm, q[h][j]);
-                        } else {
-#pragma unroll
-                            for (int v = 0; v < 4; ++v) q[h][j][v] = (TA)0;
-                        }
+            if (it.b != cur_b) {
+                __syncthreads();
+                for (int i = tid; i < it.ldm; i += kThreads) ubuf[i] = tu[it.roff + i];   // padding rows are zero
+                __syncthreads();
+                cur_b = it.b;
+            }
+            const int stage = ring_used % kTStages;
+            const unsigned par = (ring_used / kTStages) & 1u;
+            if (!mbar_wait(&rbar[stage], par, a.timeout_ns)) {
+                if (tid == 0) atomicCAS(a.bar + 2, 0u, (unsigned)RFM_ETIMEOUT);
+            }
+            const TA *tile = reinterpret_cast<const TA *>(stage_mem + (size_t)stage * kTStageBytes);
+            // nseg warps per column when the chunk has fewer columns than
+            // warps (each takes every nseg-th strip of 32 vectors of rows)
+            constexpr int VW = sizeof(TA) == 4 ? 4 : 2, STRIP = 32 * VW;
+            const int nseg = it.nc >= kThreads / 32 ? 1 : (kThreads / 32) / it.nc;
+            for (int c0w = warp; c0w < it.nc * nseg; c0w += kThreads / 32) {
+                const int c = c0w / nseg, sg = c0w % nseg;
+                const TA *col = tile + (int64_t)c * it.ldm;
+                TA s4 = (TA)0;
+                if (sizeof(TA) == 4) {
+                    for (int i = VW * lane + STRIP * sg; i < it.ldm; i += STRIP * nseg) {
+                        const float4 q = *reinterpret_cast<const float4 *>(col + i);
+                        const float4 u = *reinterpret_cast<const float4 *>(ubuf + i);
+                        s4 += (TA)(q.x * u.x + q.y * u.y + q.z * u.z + q.w * u.w);
+                    }
+                } else {
+                    for (int i = VW * lane + STRIP * sg; i < it.ldm; i += STRIP * nseg) {
+                        const double2 q = *reinterpret_cast<const double2 *>(col + i);
+                        const double2 u = *reinterpret_cast<const double2 *>(ubuf + i);
+                        s4 += (TA)(q.x * u.x + q.y * u.y);
                     }
                 }
-#pragma unroll
-                for (int h = 0; h < H; ++h)
-#pragma unroll
-                    for (int j = 0; j < kColTile; ++j)
-#pragma unroll
-                        for (int v = 0; v < 4; ++v) acc[j] += q[h][j][v] * uv[h][v];
+                for (int o = 16; o; o >>= 1) s4 += __shfl_xor_sync(0xffffffffu, s4, o);
+                if (nseg == 1) {
+                    if (lane == 0) zg[it.coff + it.c0 + c] = (double)s4;
+                } else if (lane == 0) {
+                    S.zseg[c0w] = (double)s4;
+                }
             }
-            double mine = 0.0;
-#pragma unroll
-            for (int j = 0; j < kColTile; ++j) {
-                TA s = acc[j];
-                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                if (lane == j) mine = (double)s;
+            if (nseg > 1) {
+                __syncthreads();
+                if (tid < it.nc) {
+                    double z = 0.0;
+                    for (int k = 0; k < nseg; ++k) z += S.zseg[tid * nseg + k];
+                    zg[it.coff + it.c0 + tid] = z;
+                }
             }
-            double pa = 0.0, py = 0.0;
-            if (lane < it.nc) per_col(it.inst, it.coff + it.c0 + lane, mine, &pa, &py);
+            __syncthreads();   // every read of this stage is done
+            ++ring_used;
+            issue();
+        }
+        __syncthreads();
+        // epilogue: warp w takes chunks u_lo + w, u_lo + w + 8, ...; lane j
+        // its column j (j < nc <= kTStageBytes / 128); per-instance sums in
+        // lane-private registers, flushed when the instance changes
+        double pa = 0.0, py = 0.0;
+        int cur_inst = -1;
+        auto flush_lane = [&]() {
+            double x = pa, z = py;
             for (int o = 16; o; o >>= 1) {
-                pa += __shfl_xor_sync(0xffffffffu, pa, o);
-                py += __shfl_xor_sync(0xffffffffu, py, o);
+                x += __shfl_xor_sync(0xffffffffu, x, o);
+                z += __shfl_xor_sync(0xffffffffu, z, o);
             }
-            if (lane == 0) {
-                S.wacc[0][warp][it.inst] += pa;
-                S.wacc[1][warp][it.inst] += py;
+            if (lane == 0 && cur_inst >= 0) {
+                S.wacc[0][warp][cur_inst] += x;
+                S.wacc[1][warp][cur_inst] += z;
+            }
+            pa = py = 0.0;
+        };
+        for (int64_t cu = u_lo + warp; cu < u_hi; cu += kThreads / 32) {
+            const ColItem &it = titems[cu];
+            if (!take(it.inst)) continue;
+            if (it.inst != cur_inst) {
+                flush_lane();
+                cur_inst = it.inst;
+            }
+            for (int j = lane; j < it.nc; j += 32) {
+                const int64_t o = it.coff + it.c0 + j;
+                epi(it.inst, o, zg[o], &pa, &py);
             }
         }
+        flush_lane();
     };
+
     // elementwise over the kept column slots
     auto each_column = [&](auto take, auto fn) {
         const int64_t total = n_items * kColTile;
@@ -1090,11 +1219,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
     // vt = Op^T u~ / beta, ||vt||^2
     clear_w();
     __syncthreads();
-    columns(all_inst, [&](int inst, int64_t o, double z, double *pa, double *py) {
+    tphase(all_inst, [&](int inst, int64_t o, double z, double *pa, double *py) {
         const double x = z * S.inv_bn[inst];
         a.vt[o] = x;
         if (sizeof(TA) != sizeof(double)) vx[o] = (TA)x;
-        *pa = x * x;
+        *pa += x * x;
     });
     __syncthreads();
     flush_w(0, 2);
@@ -1194,14 +1323,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
         // T: vt = Op^T u~ / beta_new - beta_new v_n ; ||vt||^2 ; ||y_{n-1}||^2
         clear_w();
         __syncthreads();
-        columns(live, [&](int inst, int64_t o, double z, double *pa, double *py) {
+        tphase(live, [&](int inst, int64_t o, double z, double *pa, double *py) {
             const double vn = a.vt[o] * S.inv_alpha[inst];
             const double x = fma(z, S.inv_bn[inst], -S.bn[inst] * vn);
             a.vt[o] = x;
             if (sizeof(TA) != sizeof(double)) vx[o] = (TA)x;
-            *pa = x * x;
+            *pa += x * x;
             const double yv = a.y[o];
-            *py = yv * yv;
+            *py += yv * yv;
         });
         __syncthreads();
         flush_w(0, 2);
@@ -1284,13 +1413,24 @@ static rfm_status run_lsqr_tiles(const HostPlan &P, void *ws, LsqrArgs &args, cu
     const Layout &L = P.L;
     ColItem *items = ws_ptr<ColItem>(ws, L.off_items);
     int *nitems = ws_ptr<int>(ws, L.off_nitems);
+    ColItem *titems = ws_ptr<ColItem>(ws, L.off_titems);
+    int *ntitems = ws_ptr<int>(ws, L.off_ntitems);
     {
         ProfScope ps("k_build_items", st);
         k_build_items<<<1, 1024, 0, st>>>(args.blks, args.n_blocks, args.rank, items, nitems,
-                                          ws_ptr<ColItem>(ws, L.off_fitems), ws_ptr<int>(ws, L.off_nfitems));
+                                          ws_ptr<ColItem>(ws, L.off_fitems), ws_ptr<int>(ws, L.off_nfitems), titems,
+                                          ntitems, (int)sizeof(TA), L.n_t_items);
         RFM_CUDA_CHECK(cudaGetLastError());
     }
-    const size_t sm = sizeof(TileSmem<TA>);
+    // every staged chunk must fit a stage: one column of the tallest block
+    const int64_t ld_max = (L.max_m + kLdAlign - 1) / kLdAlign * kLdAlign;
+    if (ld_max * (int64_t)sizeof(TA) > kTStageBytes) {
+        set_error("rfm_lsqr_solve: blocks of %lld rows exceed the staged transposed product (%d rows at most)",
+                  (long long)L.max_m, (int)(kTStageBytes / sizeof(TA)));
+        return RFM_EINVAL;
+    }
+    const size_t sm = ((sizeof(TileSmem<TA>) + 127) / 128) * 128 + 128 + (size_t)kTStages * kTStageBytes +
+                      (size_t)ld_max * sizeof(TA);
     RFM_CUDA_CHECK(cudaFuncSetAttribute(k_lsqr_tiles<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     RFM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lsqr_tiles<TA>, kThreads, sm));
     if (per < 1) {
@@ -1302,9 +1442,12 @@ static rfm_status run_lsqr_tiles(const HostPlan &P, void *ws, LsqrArgs &args, cu
     TA *tu = ws_ptr<TA>(ws, L.off_tu);
     // padding block rows of u~ are never written by the row phase: keep them zero
     RFM_CUDA_CHECK(cudaMemsetAsync(tu, 0, sizeof(TA) * (size_t)L.block_rows, st));
-    const ColItem *citems = items, *cfitems = ws_ptr<ColItem>(ws, L.off_fitems);
-    const int *cn = nitems, *cfn = ws_ptr<int>(ws, L.off_nfitems);
-    void *kargs[] = {&args, (void *)&citems, (void *)&cn, (void *)&cfitems, (void *)&cfn, (void *)&tu};
+    const ColItem *citems = items, *cfitems = ws_ptr<ColItem>(ws, L.off_fitems), *ctitems = titems;
+    const int *cn = nitems, *cfn = ws_ptr<int>(ws, L.off_nfitems), *ctn = ntitems;
+    double *zg = ws_ptr<double>(ws, L.off_z);
+    int max_ldm = (int)ld_max;
+    void *kargs[] = {&args, (void *)&citems, (void *)&cn, (void *)&cfitems, (void *)&cfn, (void *)&tu,
+                     (void *)&ctitems, (void *)&ctn, (void *)&zg, (void *)&max_ldm};
     ProfScope ps("k_lsqr", st);
     RFM_CUDA_CHECK(cudaLaunchCooperativeKernel((const void *)k_lsqr_tiles<TA>, dim3(G), dim3(kThreads), kargs, sm, st));
     return RFM_OK;
@@ -1337,14 +1480,8 @@ static rfm_status run_lsqr(const HostPlan &P, void *ws, LsqrArgs &args, cudaStre
     return RFM_OK;
 }
 
-rfm_status launch_lsqr(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, const double *y0, double *y_out,
-                       double *a_out, rfm_lsqr_report *rep, cudaStream_t st) {
+static void fill_args(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, const double *y0, LsqrArgs &A) {
     const Layout &L = P.L;
-    if (P.L.n_inst > 64) {
-        set_error("rfm_lsqr_solve: at most 64 instances per system");
-        return RFM_EINVAL;
-    }
-    LsqrArgs A;
     memset(&A, 0, sizeof(A));
     A.insts = ws_ptr<InstRec>(ws, L.off_inst);
     A.blks = ws_ptr<BlkRec>(ws, L.off_blk);
@@ -1381,6 +1518,17 @@ rfm_status launch_lsqr(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, c
         A.snap_every = opts->snap_every;
         A.snap_cap = opts->snap_cap;
     }
+}
+
+rfm_status launch_lsqr(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, const double *y0, double *y_out,
+                       double *a_out, rfm_lsqr_report *rep, cudaStream_t st) {
+    const Layout &L = P.L;
+    if (P.L.n_inst > 64) {
+        set_error("rfm_lsqr_solve: at most 64 instances per system");
+        return RFM_EINVAL;
+    }
+    LsqrArgs A;
+    fill_args(P, ws, opts, y0, A);
     RFM_CUDA_CHECK(cudaMemsetAsync(A.bar, 0, 256, st));
     rfm_status rc;
     if (L.op == RFM_OP_Q32) {
@@ -1403,6 +1551,37 @@ rfm_status launch_lsqr(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, c
     if (y_out) RFM_CUDA_CHECK(cudaMemcpyAsync(y_out, A.y, sizeof(double) * L.n_cols, cudaMemcpyDeviceToDevice, st));
     rc = launch_coefficients(P, ws, A.y, a_out, st);
     if (rc != RFM_OK) return rc;
+    if (rep) {
+        ProfScope ps("k_report", st);
+        k_report<<<(L.n_inst + 63) / 64, 64, 0, st>>>(A.scal, L.n_inst, rep, A.bar);
+        RFM_CUDA_CHECK(cudaGetLastError());
+    }
+    return RFM_OK;
+}
+
+// LSQR from zero on another explicit FP64 operator with the system's block
+// structure (the fit of predicted values: its own kept counts, right-hand
+// side at the collocation rows); z_out receives the iterate (column slots).
+rfm_status launch_lsqr_on(const HostPlan &P, void *ws, const double *Op, const int32_t *rank, const double *rhs,
+                          int iters, double *z_out, rfm_lsqr_report *rep, cudaStream_t st) {
+    const Layout &L = P.L;
+    if (P.L.n_inst > 64) {
+        set_error("at most 64 instances per system");
+        return RFM_EINVAL;
+    }
+    rfm_lsqr_opts o;
+    memset(&o, 0, sizeof(o));
+    o.max_iter = iters;
+    o.timeout_ms = 10000;
+    LsqrArgs A;
+    fill_args(P, ws, &o, nullptr, A);
+    A.A = Op;
+    A.rank = rank;
+    A.h = rhs;
+    RFM_CUDA_CHECK(cudaMemsetAsync(A.bar, 0, 256, st));
+    rfm_status rc = run_lsqr_tiles<double>(P, ws, A, st);
+    if (rc != RFM_OK) return rc;
+    RFM_CUDA_CHECK(cudaMemcpyAsync(z_out, A.y, sizeof(double) * L.n_cols, cudaMemcpyDeviceToDevice, st));
     if (rep) {
         ProfScope ps("k_report", st);
         k_report<<<(L.n_inst + 63) / 64, 64, 0, st>>>(A.scal, L.n_inst, rep, A.bar);

@@ -274,7 +274,19 @@ rfm_status build_plan(const rfm_problem *probs, int n_inst, const rfm_config *cf
     L.n_slots = (max_K + kColTile - 1) / kColTile;
     L.off_items = take(sizeof(ColItem) * (L.n_col_items + 1));
     L.off_nitems = take(256);
-    L.off_tpart = take(sizeof(double) * L.n_slots * roff);
+    L.off_z = take(sizeof(double) * (col0 + 1));
+    {
+        // bound for either operator precision (8-byte elements give the most
+        // chunks; the fit of predicted values runs an FP64 operator on any system)
+        int64_t nt = 0;
+        for (const BlkRec &B : blk) {
+            const int cc = tchunk_cols(B.ldm, 8);
+            nt += (B.K + cc - 1) / cc;
+        }
+        L.n_t_items = nt;
+    }
+    L.off_titems = take(sizeof(ColItem) * (L.n_t_items + 1));
+    L.off_ntitems = take(256);
     L.off_qblk = take(sizeof(int32_t) * (roff + 1));
     L.off_tu = take(sizeof(double) * (roff + 1));
     L.off_fitems = take(sizeof(ColItem) * (L.n_fwd_items + 1));

@@ -276,7 +276,9 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
     double *vbuf2 = vbuf + ld_loc;                   // ld_loc (Q prefetch)
     double *cn = vbuf2 + ld_loc;                     // nloc_max
     double *cn0 = cn + nloc_max;                     // nloc_max
-    int *pos = (int *)(cn0 + nloc_max);              // nloc_max: position of the column, -1 while trailing
+    double *rk = cn0 + nloc_max;                     // nloc_max: R(k, c) of the step, for the norm downdate
+    int *pos = (int *)(rk + nloc_max);               // nloc_max: position of the column, -1 while trailing
+    int *redo = pos + nloc_max;                      // nloc_max: exact norm needed
     __shared__ Cand cand[2];
     __shared__ Cand red[8];
     __shared__ Cand s_win;
@@ -382,37 +384,66 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
         if (cr == 0 && tid == 0) tau[B.coff + k] = tk;
         __syncthreads();
         if (cr == own) { pend_slot = wsl; pend_k = k; pend_beta = beta; }
-        // 5. update own trailing columns, downdate their norms
-        for (int l = warp; l < nloc; l += 8) {
-            if (pos[l] >= 0) continue;
-            double *a = A + (size_t)l * ld_loc;
-            double d = 0.0;
-            for (int i = k + 1 + lane; i < m; i += 32) d = fma(vbuf[i], a[i], d);
-            for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-            const double akc = a[k];
-            d = tk * (akc + d);
-            for (int i = k + 1 + lane; i < m; i += 32) a[i] = fma(-d, vbuf[i], a[i]);
-            const double rkc = akc - d;
+        // 5. update own trailing columns, two per warp at a time (independent
+        //    reductions overlap); R(k, c) is kept for the downdate
+        for (int l = warp; l < nloc; l += 16) {
+            const int l2 = l + 8;
+            const bool h1 = pos[l] < 0, h2 = l2 < nloc && pos[l2] < 0;
+            if (!h1 && !h2) continue;
+            double *a1 = A + (size_t)l * ld_loc;
+            double *a2 = A + (size_t)(h2 ? l2 : l) * ld_loc;
+            double d1 = 0.0, d2 = 0.0;
+            for (int i = k + 1 + lane; i < m; i += 32) {
+                const double v = vbuf[i];
+                d1 = fma(v, a1[i], d1);
+                d2 = fma(v, a2[i], d2);
+            }
+            for (int o = 16; o; o >>= 1) {
+                d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+                d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+            }
+            const double ak1 = a1[k], ak2 = a2[k];
+            d1 = tk * (ak1 + d1);
+            d2 = tk * (ak2 + d2);
+            if (h1)
+                for (int i = k + 1 + lane; i < m; i += 32) a1[i] = fma(-d1, vbuf[i], a1[i]);
+            if (h2)
+                for (int i = k + 1 + lane; i < m; i += 32) a2[i] = fma(-d2, vbuf[i], a2[i]);
             __syncwarp();
-            if (lane == 0) a[k] = rkc;
+            if (lane == 0) {
+                if (h1) { a1[k] = ak1 - d1; rk[l] = ak1 - d1; }
+                if (h2) { a2[k] = ak2 - d2; rk[l2] = ak2 - d2; }
+            }
+        }
+        __syncthreads();
+        // 6. norm downdate, one thread per column; columns whose downdate has
+        //    lost half the digits are marked for an exact recompute
+        for (int l = tid; l < nloc; l += 256) {
+            if (pos[l] >= 0) continue;
             double cc = cn[l];
-            int recompute = 0;
+            int again = 0;
             if (cc != 0.0) {
-                double t = fabs(rkc) / cc;
+                double t = fabs(rk[l]) / cc;
                 t = (1.0 + t) * (1.0 - t);
                 t = t < 0.0 ? 0.0 : t;
-                double rr = cc / cn0[l];
-                if (t * rr * rr <= tol3z) recompute = 1;
+                const double rr = cc / cn0[l];
+                if (t * rr * rr <= tol3z) again = 1;
                 else cc = cc * sqrt(t);
             }
-            if (recompute) {
-                double e = 0.0;
-                for (int i = k + 1 + lane; i < m; i += 32) e = fma(a[i], a[i], e);
-                for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-                cc = sqrt(e);
-                if (lane == 0) cn0[l] = cc;
+            cn[l] = cc;
+            redo[l] = again;
+        }
+        __syncthreads();
+        for (int l = warp; l < nloc; l += 8) {
+            if (pos[l] >= 0 || !redo[l]) continue;
+            const double *a = A + (size_t)l * ld_loc;
+            double e = 0.0;
+            for (int i = k + 1 + lane; i < m; i += 32) e = fma(a[i], a[i], e);
+            for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+            if (lane == 0) {
+                cn[l] = sqrt(e);
+                cn0[l] = cn[l];
             }
-            if (lane == 0) cn[l] = cc;
         }
         __syncthreads();
     }
@@ -532,7 +563,7 @@ static rfm_status launch_cluster(const FilterBufs &F, double tol, int nloc, int 
 static size_t cluster_smem(int64_t max_m, int64_t max_K, int C, int *nloc, int *ldl) {
     *ldl = (int)((max_m + 1) / 2 * 2);
     *nloc = (int)((max_K + C - 1) / C);
-    return ((size_t)(*nloc) * (*ldl) + 2 * (size_t)(*ldl)) * 8 + (size_t)(*nloc) * 20 + 64;
+    return ((size_t)(*nloc) * (*ldl) + 2 * (size_t)(*ldl)) * 8 + (size_t)(*nloc) * 32 + 64;
 }
 
 template <typename TM>

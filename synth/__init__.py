@@ -191,6 +191,14 @@ def param5_context(fp) -> np.ndarray:
     return np.array([a / 12.0, b / 12.0, c / 0.5, d / 30.0, e / 30.0], dtype=np.float32)
 
 
+def param5_amplitude_scale(fp) -> float:
+    """pi^2 (a^2 + b^2): the inverse amplitude of the dominant part of the
+    solution (-Laplace sin(a pi x) sin(b pi y) = pi^2 (a^2 + b^2) sin sin),
+    used to bring the family's solutions to a common scale."""
+    a, b = fp[0], fp[1]
+    return float(np.pi ** 2 * (a * a + b * b))
+
+
 def param5_draw(seed: int) -> List[float]:
     """(a, b, c, d, e) with a, b ~ U[1,12], c ~ U[0,0.5], d, e ~ U[10,30]."""
     u = splitmix64_unit(seed, 5, offset=1 << 41)
