@@ -334,10 +334,131 @@ def run_gpu(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(p, prm, kstar["fp64"], budget_s=args.cpu_budget)
+    if rank == 0 and world == 1 and args.learned_train > 0:
+        out["learned"] = run_learned(args, dev)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_learned(args, dev):
+    """The learned warm start on the parametric-source family (held-out
+    instances): training solves by the mixed path, the network trained by the
+    library's kernels, then LSQR from zero and from the fitted prediction.
+    Errors are relative L2 on a 100^2 grid against a long FP64 solve."""
+    import math
+    import torch
+    import paper_2506_17626_gb300 as R
+    from paper_2506_17626_gb300.warm import LearnedWarmStart, block_row_mask, instance_row_ranges
+    S_, K_, D_ = 10, 120, 2.9
+    n = S_ * math.ceil(math.sqrt(K_))
+    base = dict(S=S_, K=K_, delta=D_, n=n)
+    fam = lambda seeds: [synth.param5(*synth.param5_draw(s), **base) for s in seeds]
+    ctx = lambda ps: torch.from_numpy(np.stack([synth.param5_context(p.fparams) for p in ps])).to(dev)
+    scl = lambda ps: [synth.param5_amplitude_scale(p.fparams) for p in ps]
+    prm0 = synth.feature_params(fam([0])[0])
+    params = lambda ps: torch.from_numpy(np.tile(prm0.ravel(), len(ps))).to(dev)
+    ax = (np.arange(100) + 0.5) / 100
+    gx, gy = np.meshgrid(ax, ax, indexing="xy")
+    grid = torch.from_numpy(np.stack([gx.ravel(), gy.ravel()], 1)).to(dev)
+
+    def rel(u, r):
+        return [float(torch.linalg.norm(ui - ri) / torch.linalg.norm(ri)) for ui, ri in zip(u, r)]
+
+    ntr, train_iters, epochs = args.learned_train, 3000, args.learned_epochs
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Xs, Ts = [], []
+    tr = fam(range(ntr))
+    for i in range(0, ntr, 32):
+        ps = tr[i:i + 32]
+        S = R.System(ps, asm="fp32", op="q32", tol=TOL, device=str(dev))
+        d = params(ps)
+        S.assemble(d)
+        S.filter()
+        a, _ = S.solve(atol=0, btol=0, max_iter=train_iters)
+        X, T = LearnedWarmStart.samples(S, d, a, ctx(ps), inst_scale=scl(ps))
+        Xs.append(X)
+        Ts.append(T)
+        del S
+    X, T = torch.cat(Xs), torch.cat(Ts)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    W = LearnedWarmStart([9, 128, 128, 128, 128, 1], seed=0, device=str(dev))
+    scale = float(T.abs().max())
+    t0 = time.perf_counter()
+    hist = W.train(X, T / scale, epochs=epochs, batch=4096, lr=2e-3, lr_final=1e-4)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    W.theta[-129:] *= scale
+    n_samples = int(X.shape[0])
+    del X, T, Xs, Ts
+
+    held = fam(range(10000, 10008))
+    d = params(held)
+    Xt = [grid for _ in held]
+    R64 = R.System(held, asm="fp64", op="q64", tol=TOL, device=str(dev))
+    R64.assemble(d)
+    R64.filter()
+    a_ref, _ = R64.solve(atol=0, btol=0, max_iter=10000)
+    u_ref, _ = R64.evaluate(d, a_ref, Xt, with_error=False)
+    S = R.System(held, asm="fp32", op="q32", tol=TOL, device=str(dev))
+    S.assemble(d)
+    S.filter()
+    S.fit_prepare(d, tol_fit=1e-8)
+    # prediction error at the block rows against the reference there
+    _, pts = S.block_inputs(ctx(held))
+    rr = instance_row_ranges(S)
+    ub, _ = R64.evaluate(d, a_ref, [pts[r0:r1, :2].contiguous() for r0, r1 in rr], with_error=False)
+    live = block_row_mask(S)
+    inv = torch.tensor([1.0 / v for v in scl(held)], dtype=torch.float32, device=dev)
+    pred = W.predict(S, ctx(held))
+    scale_rows = torch.cat([torch.full((r1 - r0,), float(inv[i]), device=dev) for i, (r0, r1) in enumerate(rr)])
+    pl = (pred.double() * scale_rows).index_select(0, live)
+    tl = torch.cat(ub).index_select(0, live)
+    pred_err = float(torch.linalg.norm(pl - tl) / torch.linalg.norm(tl))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    y0 = W.warm_start(S, ctx(held), fit_iters=300, inst_scale=inv)
+    ev1.record()
+    torch.cuda.synchronize()
+    t_ws = ev0.elapsed_time(ev1)
+    u0, _ = S.evaluate(d, S.coefficients(y0), Xt, with_error=False)
+    e0 = rel(u0, u_ref)
+    every, iters = 100, 3000
+    curves, ms_it = {}, {}
+    for name, yy in (("zero_start", None), ("learned_start", y0)):
+        snap = torch.zeros((iters // every, S.sizes["n_cols"]), dtype=torch.float64, device=dev)
+        ev0.record()
+        S.solve(atol=0, btol=0, max_iter=iters, snap=snap, snap_every=every, y0=yy)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms_it[name] = ev0.elapsed_time(ev1) / iters
+        curves[name] = np.array([max(rel(S.evaluate(d, S.coefficients(snap[k]), Xt, with_error=False)[0], u_ref))
+                                 for k in range(snap.shape[0])])
+
+    def first(c, th):
+        k = np.nonzero(c <= th)[0]
+        return int(every * (1 + k[0])) if len(k) else None
+
+    return {
+        "workload": f"2D Poisson, f = sin(a pi x) sin(b pi y) + c sin(d pi x + e pi y), {S_}x{S_} subdomains, "
+                    f"overlap ratio {D_}, K={K_}, {n}^2 interior + boundary rows, filter tol {TOL:g}, "
+                    f"mixed path; 8 held-out instances (seeds 10000-10007)",
+        "network": "9 -> 128 x4 (tanh) -> 1, FP32, Adam lr 2e-3 -> 1e-4, batch 4096, targets x pi^2 (a^2+b^2)",
+        "training_solves": ntr, "training_lsqr_iterations": train_iters, "training_samples": n_samples,
+        "epochs": epochs, "data_s": t_data, "train_s": t_train, "train_samples_per_s": n_samples * epochs / t_train,
+        "loss_first_last": [hist[0], hist[-1]],
+        "heldout_prediction_rel_l2_at_block_rows": pred_err,
+        "warm_start_ms": t_ws, "fit_lsqr_iterations": 300,
+        "start_error": {"zero_start": 1.0, "learned_start": max(e0)},
+        "error_after_iterations": {name: {str(it): float(c[it // every - 1]) for it in (100, 500, 1000, 2000, 3000)}
+                                   for name, c in curves.items()},
+        "iterations_to_0.1": {name: first(c, 0.1) for name, c in curves.items()},
+        "ms_per_lsqr_iteration_8_instances": ms_it,
+        "reference": "FP64 explicit-Q LSQR, 10000 iterations, same discretisation",
+    }
 
 
 def oracle_free_test_grid(p):
@@ -428,6 +549,9 @@ def main():
     ap.add_argument("--iters-mixed", type=int, default=None, help="skip calibration: LSQR iterations (mixed)")
     ap.add_argument("--iters-fp64", type=int, default=None, help="skip calibration: LSQR iterations (FP64)")
     ap.add_argument("--target", type=float, default=None, help="target recorded when calibration is skipped")
+    ap.add_argument("--learned-train", type=int, default=384,
+                    help="training solves of the learned warm start section (0 skips it)")
+    ap.add_argument("--learned-epochs", type=int, default=6)
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: 10x10 subdomains with the same block shapes (profiler captures)")
     args = ap.parse_args()

@@ -346,8 +346,14 @@ int rfm_profile_read(const char **names, int64_t *launches, double *ms, int max)
  *  RFM_OPT_FILTER_KERNEL: 0 (default) chooses per system: the cluster kernel
  *    (block held in the distributed shared memory of a cluster of up to 8
  *    CTAs) when the largest block fits, else the global-memory kernel;
- *    1 forces the global-memory kernel (for comparison and testing). */
-enum { RFM_OPT_FILTER_KERNEL = 0 };
+ *    1 forces the global-memory kernel (for comparison and testing).
+ *  RFM_OPT_AUTOTUNE: 1 makes the first rfm_rrqr_filter (and rfm_fit_prepare)
+ *    call for a block shape (largest block rows and features, assembly
+ *    precision, block count) time every cluster size the blocks fit and keep
+ *    the fastest for later calls in the process; that first call waits for
+ *    its own timing runs (it synchronises the stream).  0 (default) takes the
+ *    smallest cluster that holds the largest block. */
+enum { RFM_OPT_FILTER_KERNEL = 0, RFM_OPT_AUTOTUNE = 1 };
 rfm_status rfm_set_option(int option, int value);
 
 const char *rfm_last_error(void);

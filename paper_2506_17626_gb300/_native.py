@@ -163,3 +163,9 @@ def profile_read() -> dict:
 def set_filter_kernel(global_memory: bool):
     """Force the global-memory QR kernel (True) or let the library choose (False)."""
     check("rfm_set_option", load().rfm_set_option(0, 1 if global_memory else 0))
+
+
+def set_autotune(on: bool):
+    """Time every feasible QR cluster size on the first filter call of a block
+    shape and keep the fastest (RFM_OPT_AUTOTUNE)."""
+    check("rfm_set_option", load().rfm_set_option(1, 1 if on else 0))

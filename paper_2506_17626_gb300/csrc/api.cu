@@ -15,6 +15,7 @@ rfm_status launch_lsqr(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, c
                        double *a_out, rfm_lsqr_report *rep, cudaStream_t st);
 rfm_status launch_coefficients(const HostPlan &P, void *ws, const double *y, double *a_out, cudaStream_t st);
 void set_force_global_filter(int on);
+void set_autotune(int on);
 rfm_status launch_eval_noalloc(const HostPlan &P, const double *params, const double *a, const double *X,
                                const int64_t *pt_off, double *u, double *err, cudaStream_t st);
 rfm_status launch_eval(const HostPlan &P, void *ws, const double *params, const double *a, const double *X,
@@ -211,6 +212,10 @@ rfm_status rfm_coefficients(const rfm_problem *probs, int n_inst, const rfm_conf
 rfm_status rfm_set_option(int option, int value) {
     if (option == RFM_OPT_FILTER_KERNEL && (value == 0 || value == 1)) {
         set_force_global_filter(value);
+        return RFM_OK;
+    }
+    if (option == RFM_OPT_AUTOTUNE && (value == 0 || value == 1)) {
+        set_autotune(value);
         return RFM_OK;
     }
     set_error("rfm_set_option: unknown option %d or value %d", option, value);

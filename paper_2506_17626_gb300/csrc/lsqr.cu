@@ -22,6 +22,8 @@
 // at their next barrier.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "device.cuh"
 #include "prof.cuh"
 
@@ -65,6 +67,10 @@ __device__ inline void mbar_init(uint64_t *bar, unsigned count) {
 
 __device__ inline void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ inline void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ inline void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
@@ -735,7 +741,6 @@ struct TileSmem {
     // per-instance factors formed once per phase (no division or square root
     // in per-element code: GB300's FP64 pipe is narrow)
     double inv_alpha[64], ab[64], bn[64], inv_bn[64];
-    double zseg[kThreads / 32];   // per-warp partial dots of the transposed product
 };
 
 // Four rows of a column owned by one lane: FP32 one 16-byte load of rows
@@ -929,7 +934,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
                                                          const int *__restrict__ n_fitems_p, TA *__restrict__ tu,
                                                          const ColItem *__restrict__ titems,
                                                          const int *__restrict__ n_titems_p, double *__restrict__ zg,
-                                                         int max_ldm) {
+                                                         int cc_max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSmem<TA> &S = *reinterpret_cast<TileSmem<TA> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, G = gridDim.x, cta = blockIdx.x;
@@ -1004,129 +1009,164 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
     // forward product of block row q
     auto row_partials = [&](int64_t q) { return a.t[q]; };
     // ---- transposed product through a bulk-copy ring.  This CTA owns the
-    // contiguous chunk range [u_lo, u_hi) (block order, so consecutive chunks
-    // mostly share a block and its u~).  Chunks are copied whole (they are
-    // contiguous: column-major blocks) into kTStages shared-memory stages; one
-    // warp reduces one column against u~ and stores z; the FP64 epilogue then
-    // runs over the range with lane-private per-instance sums.
+    // contiguous chunk range [u_lo, u_hi) (block order).  A chunk is
+    // contiguous in memory (column-major blocks) and is brought in whole by
+    // one bulk asynchronous copy.  Warp 0 is the producer: one lane issues
+    // chunk k into stage k mod kTStages once that stage's previous chunk has
+    // been released.  Warp 1 + s is the consumer of stage s: it waits for the
+    // copy, reduces every column of the chunk against u~ (read from the
+    // L1-cached block-row copy), stores z and releases the stage -- no
+    // CTA-wide barrier per chunk.  Full and empty mbarriers per stage, every
+    // wait bounded.  The FP64 epilogue then runs over the range with
+    // lane-private per-instance sums.
     const int64_t n_tu = *n_titems_p;
     const int64_t u_lo = n_tu * cta / G, u_hi = n_tu * (cta + 1) / G;
     unsigned char *ring_base = smem_raw + ((sizeof(TileSmem<TA>) + 127) / 128) * 128;
-    uint64_t *rbar = reinterpret_cast<uint64_t *>(ring_base);
+    uint64_t *rfull = reinterpret_cast<uint64_t *>(ring_base);
+    uint64_t *rempty = rfull + kTStages;
     unsigned char *stage_mem = ring_base + 128;
-    TA *ubuf = reinterpret_cast<TA *>(stage_mem + (size_t)kTStages * kTStageBytes);
-    unsigned ring_issued = 0, ring_used = 0;   // identical in every thread of the CTA
+    unsigned ring_k = 0;   // chunks this CTA has streamed so far (identical in every thread)
     if (tid == 0) {
-        for (int i = 0; i < kTStages; ++i) mbar_init(&rbar[i], 1);
+        for (int i = 0; i < kTStages; ++i) {
+            mbar_init(&rfull[i], 1);
+            mbar_init(&rempty[i], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
+    // The CTA's chunk descriptors are read 32 at a time, one per lane (a
+    // dependent walk of the list would cost a memory round trip per chunk);
+    // take marks the chunks of live instances, k numbers them in order.
+    auto shfl_item = [&](const ColItem &it, int src) {
+        ColItem o;
+        o.b = __shfl_sync(0xffffffffu, it.b, src);
+        o.c0 = __shfl_sync(0xffffffffu, it.c0, src);
+        o.nc = __shfl_sync(0xffffffffu, it.nc, src);
+        o.m = __shfl_sync(0xffffffffu, it.m, src);
+        o.ldm = __shfl_sync(0xffffffffu, it.ldm, src);
+        o.inst = __shfl_sync(0xffffffffu, it.inst, src);
+        o.moff = __shfl_sync(0xffffffffu, it.moff, src);
+        o.coff = __shfl_sync(0xffffffffu, it.coff, src);
+        o.roff = __shfl_sync(0xffffffffu, it.roff, src);
+        return o;
+    };
+    // for_taken(fn): fn(it, k) for every taken chunk of the range, in order,
+    // called by all 32 lanes of the warp with the same arguments
+    auto for_taken = [&](auto take, auto fn) {
+        unsigned k = 0;
+        for (int64_t base = u_lo; base < u_hi; base += 32) {
+            const int64_t u = base + lane;
+            ColItem mine;
+            mine.inst = -1;
+            bool tk = false;
+            if (u < u_hi) {
+                mine = titems[u];
+                tk = take(mine.inst);
+            }
+            unsigned mask = __ballot_sync(0xffffffffu, tk);
+            while (mask) {
+                const int src = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const ColItem it = shfl_item(mine, src);
+                if (!fn(it, k)) return k + 1;
+                ++k;
+            }
+        }
+        return k;
+    };
     auto tphase = [&](auto take, auto epi) {
-        int64_t iu = u_lo;
-        auto issue = [&]() {
-            while (iu < u_hi && !take(titems[iu].inst)) ++iu;
-            if (iu >= u_hi) return;
-            if (tid == 0) {
-                const ColItem &it = titems[iu];
-                const int stage = ring_issued % kTStages;
-                const unsigned bytes = (unsigned)(it.nc * it.ldm * (int)sizeof(TA));
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(&rbar[stage], bytes);
-                bulk_g2s(stage_mem + (size_t)stage * kTStageBytes, Aop + it.moff + (int64_t)it.c0 * it.ldm, bytes,
-                         &rbar[stage]);
-            }
-            ++ring_issued;
-            ++iu;
-        };
-        for (int st = 0; st < kTStages; ++st) issue();
-        int cur_b = -1;
-        for (int64_t cu = u_lo; cu < u_hi; ++cu) {
-            const ColItem it = titems[cu];
-            if (!take(it.inst)) continue;
-            if (it.b != cur_b) {
-                __syncthreads();
-                for (int i = tid; i < it.ldm; i += kThreads) ubuf[i] = tu[it.roff + i];   // padding rows are zero
-                __syncthreads();
-                cur_b = it.b;
-            }
-            const int stage = ring_used % kTStages;
-            const unsigned par = (ring_used / kTStages) & 1u;
-            if (!mbar_wait(&rbar[stage], par, a.timeout_ns)) {
-                if (tid == 0) atomicCAS(a.bar + 2, 0u, (unsigned)RFM_ETIMEOUT);
-            }
-            const TA *tile = reinterpret_cast<const TA *>(stage_mem + (size_t)stage * kTStageBytes);
-            // nseg warps per column when the chunk has fewer columns than
-            // warps (each takes every nseg-th strip of 32 vectors of rows)
+        if (warp == 0) {
+            bool ok_p = true;
+            for_taken(take, [&](const ColItem &it, unsigned k) {
+                const unsigned K = ring_k + k;
+                const int st = (int)(K % kTStages);
+                if (lane == 0) {
+                    if (K >= (unsigned)kTStages && !mbar_wait(&rempty[st], ((K / kTStages) - 1u) & 1u, a.timeout_ns)) {
+                        atomicCAS(a.bar + 2, 0u, (unsigned)RFM_ETIMEOUT);
+                        ok_p = false;
+                    } else {
+                        const unsigned bytes = (unsigned)(it.nc * it.ldm * (int)sizeof(TA));
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        mbar_expect_tx(&rfull[st], bytes);
+                        bulk_g2s(stage_mem + (size_t)st * kTStageBytes, Aop + it.moff + (int64_t)it.c0 * it.ldm,
+                                 bytes, &rfull[st]);
+                    }
+                }
+                return __shfl_sync(0xffffffffu, ok_p ? 1 : 0, 0) != 0;
+            });
+        } else if (warp <= kTStages) {
+            const unsigned st = (unsigned)(warp - 1);
             constexpr int VW = sizeof(TA) == 4 ? 4 : 2, STRIP = 32 * VW;
-            const int nseg = it.nc >= kThreads / 32 ? 1 : (kThreads / 32) / it.nc;
-            for (int c0w = warp; c0w < it.nc * nseg; c0w += kThreads / 32) {
-                const int c = c0w / nseg, sg = c0w % nseg;
-                const TA *col = tile + (int64_t)c * it.ldm;
-                TA s4 = (TA)0;
-                if (sizeof(TA) == 4) {
-                    for (int i = VW * lane + STRIP * sg; i < it.ldm; i += STRIP * nseg) {
-                        const float4 q = *reinterpret_cast<const float4 *>(col + i);
-                        const float4 u = *reinterpret_cast<const float4 *>(ubuf + i);
-                        s4 += (TA)(q.x * u.x + q.y * u.y + q.z * u.z + q.w * u.w);
-                    }
-                } else {
-                    for (int i = VW * lane + STRIP * sg; i < it.ldm; i += STRIP * nseg) {
-                        const double2 q = *reinterpret_cast<const double2 *>(col + i);
-                        const double2 u = *reinterpret_cast<const double2 *>(ubuf + i);
-                        s4 += (TA)(q.x * u.x + q.y * u.y);
-                    }
+            const TA *tile = reinterpret_cast<const TA *>(stage_mem + (size_t)st * kTStageBytes);
+            for_taken(take, [&](const ColItem &it, unsigned k) {
+                const unsigned K = ring_k + k;
+                if (K % kTStages != st) return true;
+                const bool landed = __all_sync(0xffffffffu, mbar_wait(&rfull[st], (K / kTStages) & 1u, a.timeout_ns));
+                if (!landed) {
+                    if (lane == 0) atomicCAS(a.bar + 2, 0u, (unsigned)RFM_ETIMEOUT);
+                    return false;
                 }
-                for (int o = 16; o; o >>= 1) s4 += __shfl_xor_sync(0xffffffffu, s4, o);
-                if (nseg == 1) {
+                const TA *ub = tu + it.roff;
+                for (int c = 0; c < it.nc; ++c) {
+                    const TA *col = tile + (int64_t)c * it.ldm;
+                    TA s4 = (TA)0;
+                    if (sizeof(TA) == 4) {
+                        for (int i = VW * lane; i < it.ldm; i += STRIP) {
+                            const float4 q = *reinterpret_cast<const float4 *>(col + i);
+                            const float4 w = *reinterpret_cast<const float4 *>(ub + i);
+                            s4 += (TA)(q.x * w.x + q.y * w.y + q.z * w.z + q.w * w.w);
+                        }
+                    } else {
+                        for (int i = VW * lane; i < it.ldm; i += STRIP) {
+                            const double2 q = *reinterpret_cast<const double2 *>(col + i);
+                            const double2 w = *reinterpret_cast<const double2 *>(ub + i);
+                            s4 += (TA)(q.x * w.x + q.y * w.y);
+                        }
+                    }
+                    for (int o = 16; o; o >>= 1) s4 += __shfl_xor_sync(0xffffffffu, s4, o);
                     if (lane == 0) zg[it.coff + it.c0 + c] = (double)s4;
-                } else if (lane == 0) {
-                    S.zseg[c0w] = (double)s4;
                 }
-            }
-            if (nseg > 1) {
-                __syncthreads();
-                if (tid < it.nc) {
-                    double z = 0.0;
-                    for (int k = 0; k < nseg; ++k) z += S.zseg[tid * nseg + k];
-                    zg[it.coff + it.c0 + tid] = z;
-                }
-            }
-            __syncthreads();   // every read of this stage is done
-            ++ring_used;
-            issue();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&rempty[st]);
+                return true;
+            });
         }
         __syncthreads();
-        // epilogue: warp w takes chunks u_lo + w, u_lo + w + 8, ...; lane j
-        // its column j (j < nc <= kTStageBytes / 128); per-instance sums in
-        // lane-private registers, flushed when the instance changes
-        double pa = 0.0, py = 0.0;
-        int cur_inst = -1;
-        auto flush_lane = [&]() {
-            double x = pa, z = py;
-            for (int o = 16; o; o >>= 1) {
-                x += __shfl_xor_sync(0xffffffffu, x, o);
-                z += __shfl_xor_sync(0xffffffffu, z, o);
-            }
-            if (lane == 0 && cur_inst >= 0) {
-                S.wacc[0][warp][cur_inst] += x;
-                S.wacc[1][warp][cur_inst] += z;
-            }
-            pa = py = 0.0;
-        };
-        for (int64_t cu = u_lo + warp; cu < u_hi; cu += kThreads / 32) {
-            const ColItem &it = titems[cu];
-            if (!take(it.inst)) continue;
-            if (it.inst != cur_inst) {
-                flush_lane();
-                cur_inst = it.inst;
-            }
-            for (int j = lane; j < it.nc; j += 32) {
+        // every thread advances the ring count by the chunks taken in this phase
+        unsigned taken = 0;
+        for (int64_t base = u_lo; base < u_hi; base += kThreads) {
+            const int64_t u = base + tid;
+            const bool tk = u < u_hi && take(titems[u].inst);
+            taken += (unsigned)__syncthreads_count(tk);
+        }
+        ring_k += taken;
+        // epilogue over this CTA's columns, one thread per column (all lanes
+        // busy: the FP64 pipe is the limit here), one pass per instance present
+        // in the range so that every per-instance sum has a fixed order
+        const int ccm = cc_max;
+        const int inst_lo = u_lo < u_hi ? titems[u_lo].inst : 0;
+        const int inst_hi = u_lo < u_hi ? titems[u_hi - 1].inst : -1;
+        const int64_t nflat = (u_hi - u_lo) * ccm;
+        for (int si = inst_lo; si <= inst_hi; ++si) {
+            if (!take(si)) continue;
+            double pa = 0.0, py = 0.0;
+            for (int64_t f = tid; f < nflat; f += kThreads) {
+                const ColItem &it = titems[u_lo + f / ccm];
+                const int j = (int)(f % ccm);
+                if (it.inst != si || j >= it.nc) continue;
                 const int64_t o = it.coff + it.c0 + j;
-                epi(it.inst, o, zg[o], &pa, &py);
+                epi(si, o, zg[o], &pa, &py);
+            }
+            for (int o = 16; o; o >>= 1) {
+                pa += __shfl_xor_sync(0xffffffffu, pa, o);
+                py += __shfl_xor_sync(0xffffffffu, py, o);
+            }
+            if (lane == 0) {
+                S.wacc[0][warp][si] += pa;
+                S.wacc[1][warp][si] += py;
             }
         }
-        flush_lane();
     };
 
     // elementwise over the kept column slots
@@ -1429,8 +1469,7 @@ static rfm_status run_lsqr_tiles(const HostPlan &P, void *ws, LsqrArgs &args, cu
                   (long long)L.max_m, (int)(kTStageBytes / sizeof(TA)));
         return RFM_EINVAL;
     }
-    const size_t sm = ((sizeof(TileSmem<TA>) + 127) / 128) * 128 + 128 + (size_t)kTStages * kTStageBytes +
-                      (size_t)ld_max * sizeof(TA);
+    const size_t sm = ((sizeof(TileSmem<TA>) + 127) / 128) * 128 + 128 + (size_t)kTStages * kTStageBytes;
     RFM_CUDA_CHECK(cudaFuncSetAttribute(k_lsqr_tiles<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     RFM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lsqr_tiles<TA>, kThreads, sm));
     if (per < 1) {
@@ -1445,9 +1484,10 @@ static rfm_status run_lsqr_tiles(const HostPlan &P, void *ws, LsqrArgs &args, cu
     const ColItem *citems = items, *cfitems = ws_ptr<ColItem>(ws, L.off_fitems), *ctitems = titems;
     const int *cn = nitems, *cfn = ws_ptr<int>(ws, L.off_nfitems), *ctn = ntitems;
     double *zg = ws_ptr<double>(ws, L.off_z);
-    int max_ldm = (int)ld_max;
+    int cc_max = 1;   // widest chunk of any block (columns per staged copy)
+    for (int64_t b = 0; b < L.n_blocks; ++b) cc_max = std::max(cc_max, tchunk_cols(P.blk[b].ldm, (int)sizeof(TA)));
     void *kargs[] = {&args, (void *)&citems, (void *)&cn, (void *)&cfitems, (void *)&cfn, (void *)&tu,
-                     (void *)&ctitems, (void *)&ctn, (void *)&zg, (void *)&max_ldm};
+                     (void *)&ctitems, (void *)&ctn, (void *)&zg, (void *)&cc_max};
     ProfScope ps("k_lsqr", st);
     RFM_CUDA_CHECK(cudaLaunchCooperativeKernel((const void *)k_lsqr_tiles<TA>, dim3(G), dim3(kThreads), kargs, sm, st));
     return RFM_OK;

@@ -18,6 +18,9 @@
 // for the dot product and one for the update.
 #include <cooperative_groups.h>
 
+#include <mutex>
+#include <vector>
+
 #include "device.cuh"
 #include "prof.cuh"
 
@@ -259,8 +262,11 @@ struct Cand {
     int p, slot;
 };
 
+constexpr int kQT = 256;          // threads of a cluster-QR CTA (measured: 512 was slower on the 2D workload)
+constexpr int kQW = kQT / 32;
+
 template <typename TM, int C>
-__global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__ blks, const TM *__restrict__ M,
+__global__ void __launch_bounds__(kQT) k_qrcp_cluster(const BlkRec *__restrict__ blks, const TM *__restrict__ M,
                                                       double *__restrict__ W, double *__restrict__ tau,
                                                       int32_t *__restrict__ perm_out, int32_t *__restrict__ rank_out,
                                                       double *__restrict__ r11_out, double tol, int nloc_max,
@@ -280,15 +286,15 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
     int *pos = (int *)(rk + nloc_max);               // nloc_max: position of the column, -1 while trailing
     int *redo = pos + nloc_max;                      // nloc_max: exact norm needed
     __shared__ Cand cand[2];
-    __shared__ Cand red[8];
+    __shared__ Cand red[kQW];
     __shared__ Cand s_win;
-    __shared__ double s_red[8];
+    __shared__ double s_red[kQW];
     __shared__ int s_ndrop;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nloc = (K - cr + C - 1) / C;   // columns owned by this CTA
     double *Wb = W + B.moff;
 
-    for (int l = warp; l < nloc; l += 8) {
+    for (int l = warp; l < nloc; l += kQW) {
         const int c = cr + C * l;
         const TM *src = M + B.moff + (int64_t)c * ld;
         double s = 0.0;
@@ -315,7 +321,7 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
         // 1. best non-retired column of this CTA
         double bv = -1.0;
         int bp = 0x7fffffff, bl = -1;
-        for (int l = tid; l < nloc; l += 256)
+        for (int l = tid; l < nloc; l += kQT)
             if (pos[l] < 0 && better(cn[l], cr + C * l, bv, bp)) { bv = cn[l]; bp = cr + C * l; bl = l; }
         for (int o = 16; o; o >>= 1) {
             double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
@@ -327,7 +333,7 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
         __syncthreads();
         if (tid == 0) {
             Cand t = red[0];
-            for (int w = 1; w < 8; ++w)
+            for (int w = 1; w < kQW; ++w)
                 if (better(red[w].v, red[w].p, t.v, t.p)) t = red[w];
             cand[k & 1] = t;
         }
@@ -335,7 +341,7 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
         // deferred write of the previous reflector into its (retired) column
         if (pend_slot >= 0) {
             double *x = A + (size_t)pend_slot * ld_loc;
-            for (int i = pend_k + 1 + tid; i < m; i += 256) x[i] = vbuf[i];
+            for (int i = pend_k + 1 + tid; i < m; i += kQT) x[i] = vbuf[i];
             if (tid == 0) x[pend_k] = pend_beta;
             pend_slot = -1;
         }
@@ -360,17 +366,17 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
         // 3. copy the pivot column (rows k..m) from its owner
         {
             const double *rx = cl.map_shared_rank(A, own) + (size_t)wsl * ld_loc;
-            for (int i = k + tid; i < m; i += 256) vbuf[i] = rx[i];
+            for (int i = k + tid; i < m; i += kQT) vbuf[i] = rx[i];
         }
         __syncthreads();
         // 4. exact norm and reflector (computed identically in every CTA)
         double s = 0.0;
-        for (int i = k + tid; i < m; i += 256) s = fma(vbuf[i], vbuf[i], s);
+        for (int i = k + tid; i < m; i += kQT) s = fma(vbuf[i], vbuf[i], s);
         for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) s_red[warp] = s;
         __syncthreads();
         double t2 = 0.0;
-        for (int w = 0; w < 8; ++w) t2 += s_red[w];
+        for (int w = 0; w < kQW; ++w) t2 += s_red[w];
         const double nx = sqrt(t2);
         if (k == 0) R11 = nx;
         if (nx == 0.0 || nx < tol * R11) { rank = k; break; }
@@ -379,15 +385,15 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
         const double scale = 1.0 / (alpha - beta);
         const double tk = (beta - alpha) / beta;
         __syncthreads();
-        for (int i = k + 1 + tid; i < m; i += 256) vbuf[i] *= scale;
+        for (int i = k + 1 + tid; i < m; i += kQT) vbuf[i] *= scale;
         if (cr == own && tid == 0) pos[wsl] = k;
         if (cr == 0 && tid == 0) tau[B.coff + k] = tk;
         __syncthreads();
         if (cr == own) { pend_slot = wsl; pend_k = k; pend_beta = beta; }
         // 5. update own trailing columns, two per warp at a time (independent
         //    reductions overlap); R(k, c) is kept for the downdate
-        for (int l = warp; l < nloc; l += 16) {
-            const int l2 = l + 8;
+        for (int l = warp; l < nloc; l += 2 * kQW) {
+            const int l2 = l + kQW;
             const bool h1 = pos[l] < 0, h2 = l2 < nloc && pos[l2] < 0;
             if (!h1 && !h2) continue;
             double *a1 = A + (size_t)l * ld_loc;
@@ -418,7 +424,7 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
         __syncthreads();
         // 6. norm downdate, one thread per column; columns whose downdate has
         //    lost half the digits are marked for an exact recompute
-        for (int l = tid; l < nloc; l += 256) {
+        for (int l = tid; l < nloc; l += kQT) {
             if (pos[l] >= 0) continue;
             double cc = cn[l];
             int again = 0;
@@ -434,7 +440,7 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
             redo[l] = again;
         }
         __syncthreads();
-        for (int l = warp; l < nloc; l += 8) {
+        for (int l = warp; l < nloc; l += kQW) {
             if (pos[l] >= 0 || !redo[l]) continue;
             const double *a = A + (size_t)l * ld_loc;
             double e = 0.0;
@@ -451,7 +457,7 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
     cl.sync();
     if (pend_slot >= 0) {
         double *x = A + (size_t)pend_slot * ld_loc;
-        for (int i = pend_k + 1 + tid; i < m; i += 256) x[i] = vbuf[i];
+        for (int i = pend_k + 1 + tid; i < m; i += kQT) x[i] = vbuf[i];
         if (tid == 0) x[pend_k] = pend_beta;
     }
     // positions of the dropped columns: rank + (dropped columns of lower CTAs) + local order
@@ -468,11 +474,11 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
             if (pos[l] < 0) pos[l] = base++;
     }
     __syncthreads();
-    for (int l = warp; l < nloc; l += 8) {
+    for (int l = warp; l < nloc; l += kQW) {
         const int p = pos[l];
         for (int i = lane; i < m; i += 32) Wb[(int64_t)p * ld + i] = A[(size_t)l * ld_loc + i];
     }
-    for (int l = tid; l < nloc; l += 256) perm_out[B.coff + pos[l]] = cr + C * l;
+    for (int l = tid; l < nloc; l += kQT) perm_out[B.coff + pos[l]] = cr + C * l;
     if (cr == 0 && tid == 0) {
         rank_out[b] = rank;
         r11_out[b] = R11;
@@ -482,14 +488,14 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
     // Q_hat = H_0 ... H_{r-1} [I_r; 0], owned columns c < r (c mod C == cr)
     const int r = rank;
     const int nq = (r - cr + C - 1) / C > 0 ? (r - cr + C - 1) / C : 0;
-    for (int l = warp; l < nq; l += 8) {
+    for (int l = warp; l < nq; l += kQW) {
         const int c = cr + C * l;
         for (int i = lane; i < m; i += 32) A[(size_t)l * ld_loc + i] = (i == c) ? 1.0 : 0.0;
     }
     double *cur = vbuf, *nxt = vbuf2;
     if (r > 0) {
         const double *v = Wb + (int64_t)(r - 1) * ld;
-        for (int i = r + tid; i < m; i += 256) cur[i] = v[i];
+        for (int i = r + tid; i < m; i += kQT) cur[i] = v[i];
     }
     __syncthreads();
     for (int k = r - 1; k >= 0; --k) {
@@ -499,13 +505,13 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
             const double *v = Wb + (int64_t)(k - 1) * ld;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int i = k + tid + 256 * j;
+                const int i = k + tid + kQT * j;
                 pre[j] = i < m ? v[i] : 0.0;
             }
         }
         const double tk = tau[B.coff + k];
         const int lq = (k - cr + C - 1) / C > 0 ? (k - cr + C - 1) / C : 0;
-        for (int l = lq + warp; l < nq; l += 8) {
+        for (int l = lq + warp; l < nq; l += kQW) {
             double *q = A + (size_t)l * ld_loc;
             double d = 0.0;
             for (int i = k + 1 + lane; i < m; i += 32) d = fma(cur[i], q[i], d);
@@ -519,16 +525,16 @@ __global__ void __launch_bounds__(256) k_qrcp_cluster(const BlkRec *__restrict__
         if (k > 0) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int i = k + tid + 256 * j;
+                const int i = k + tid + kQT * j;
                 if (i < m) nxt[i] = pre[j];
             }
             const double *v = Wb + (int64_t)(k - 1) * ld;   // rows beyond the register prefetch
-            for (int i = k + tid + 4 * 256; i < m; i += 256) nxt[i] = v[i];
+            for (int i = k + tid + 4 * kQT; i < m; i += kQT) nxt[i] = v[i];
         }
         __syncthreads();
         double *t = cur; cur = nxt; nxt = t;
     }
-    for (int l = warp; l < nq; l += 8) {
+    for (int l = warp; l < nq; l += kQW) {
         const int c = cr + C * l;
         for (int i = lane; i < ld; i += 32) {     // rows m..ld-1 are padding: zeros
             const double qv = i < m ? A[(size_t)l * ld_loc + i] : 0.0;
@@ -544,7 +550,7 @@ static rfm_status launch_cluster(const FilterBufs &F, double tol, int nloc, int 
     RFM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(F.n_blocks * C));
-    cfg.blockDim = dim3(256);
+    cfg.blockDim = dim3(kQT);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute at[1];
@@ -567,6 +573,72 @@ static size_t cluster_smem(int64_t max_m, int64_t max_K, int C, int *nloc, int *
 }
 
 template <typename TM>
+static rfm_status launch_cluster_c(int C, const FilterBufs &F, double tol, cudaStream_t st) {
+    int nloc = 0, ldl = 0;
+    const size_t smem = cluster_smem(F.max_m, F.max_K, C, &nloc, &ldl);
+    switch (C) {
+        case 1: return launch_cluster<TM, 1>(F, tol, nloc, ldl, smem, st);
+        case 2: return launch_cluster<TM, 2>(F, tol, nloc, ldl, smem, st);
+        case 4: return launch_cluster<TM, 4>(F, tol, nloc, ldl, smem, st);
+        default: return launch_cluster<TM, 8>(F, tol, nloc, ldl, smem, st);
+    }
+}
+
+// Cluster-size autotuner: per block shape (largest block rows and features,
+// input precision, block count) the fastest feasible cluster size, timed
+// once with events on the caller's stream and remembered for the process.
+// Every cluster size computes the same factors (per-column arithmetic and
+// pivot ties do not depend on how columns are spread over CTAs), so the last
+// timed run leaves a valid result.
+static int g_autotune = 0;
+struct TuneEntry {
+    int64_t max_m, max_K, n_blocks;
+    int elem, C;
+};
+static std::mutex g_tune_mu;
+static std::vector<TuneEntry> g_tune;
+
+static int cached_cluster(const FilterBufs &F, int elem) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const TuneEntry &e : g_tune)
+        if (e.max_m == F.max_m && e.max_K == F.max_K && e.n_blocks == F.n_blocks && e.elem == elem) return e.C;
+    return 0;
+}
+
+template <typename TM>
+static rfm_status autotune_cluster(const FilterBufs &F, double tol, int C_min, cudaStream_t st, int *best) {
+    cudaEvent_t e0, e1;
+    RFM_CUDA_CHECK(cudaEventCreate(&e0));
+    RFM_CUDA_CHECK(cudaEventCreate(&e1));
+    float best_ms = 0.f;
+    *best = C_min;
+    rfm_status rc = RFM_OK;
+    for (int C = C_min; C <= 8 && rc == RFM_OK; C *= 2) {
+        cudaEventRecord(e0, st);
+        rc = launch_cluster_c<TM>(C, F, tol, st);
+        cudaEventRecord(e1, st);
+        if (rc != RFM_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            set_error("QR autotuner: timing run failed");
+            rc = RFM_ECUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (C == C_min || ms < best_ms) {
+            best_ms = ms;
+            *best = C;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != RFM_OK) return rc;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.push_back(TuneEntry{F.max_m, F.max_K, F.n_blocks, (int)sizeof(TM), *best});
+    return RFM_OK;
+}
+
+template <typename TM>
 static rfm_status launch_filter_t(const FilterBufs &F, double tol, cudaStream_t st) {
     const unsigned nb = (unsigned)F.n_blocks;
     const size_t kSmemCap = 220 * 1024;
@@ -579,11 +651,11 @@ static rfm_status launch_filter_t(const FilterBufs &F, double tol, cudaStream_t 
     if (C > 0) {
         ProfScope ps(F.fit ? "k_qrcp_cluster_fit" : "k_qrcp_cluster", st);
         rfm_status rc;
-        switch (C) {
-            case 1: rc = launch_cluster<TM, 1>(F, tol, nloc, ldl, smem, st); break;
-            case 2: rc = launch_cluster<TM, 2>(F, tol, nloc, ldl, smem, st); break;
-            case 4: rc = launch_cluster<TM, 4>(F, tol, nloc, ldl, smem, st); break;
-            default: rc = launch_cluster<TM, 8>(F, tol, nloc, ldl, smem, st); break;
+        int tuned = g_autotune ? cached_cluster(F, (int)sizeof(TM)) : 0;
+        if (g_autotune && tuned == 0 && C < 8) {
+            rc = autotune_cluster<TM>(F, tol, C, st, &tuned);   // leaves a valid result
+        } else {
+            rc = launch_cluster_c<TM>(tuned ? tuned : C, F, tol, st);
         }
         if (rc != RFM_OK) return rc;
     } else {
@@ -644,5 +716,6 @@ rfm_status launch_filter(const HostPlan &P, void *ws, double tol, cudaStream_t s
 }
 
 void set_force_global_filter(int on) { g_force_global = on; }
+void set_autotune(int on) { g_autotune = on; }
 
 }  // namespace rfm
