@@ -45,9 +45,12 @@ CAL_ITERS = 10000
 # flop/clk/SM (2 DFMA lanes) x 2.07 GHz = 1258 GFLOP/s (a DFMA probe measured
 # 1194 GFLOP/s on this part).
 FP64_PEAK_GFLOPS = 152 * 4 * 2.07
-# DRAM traffic per launch from ncu captures (profiles/); None until captured
-# for the current kernel version.
-NCU_TRAFFIC = {}
+# DRAM traffic from ncu captures of the current kernels (profiles/): per LSQR
+# iteration for k_lsqr ((11.955 + 0.343) GB over a 50-iteration capture, scaled
+# by the launch's iteration count), per launch otherwise; a kernel without an
+# entry reports None.
+NCU_TRAFFIC_PER_ITER = {"k_lsqr": 12.298e9 / 50}
+NCU_TRAFFIC = {"k_qrcp_cluster": 0.842e9}
 
 
 def workload(case: str = "full"):
@@ -306,7 +309,8 @@ def run_gpu(args):
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                 "algorithmic_per_launch": by}
-    roof["traffic"] = NCU_TRAFFIC.get(dom)
+    roof["traffic"] = (NCU_TRAFFIC_PER_ITER[dom] * kstar["mixed"] if dom in NCU_TRAFFIC_PER_ITER
+                       else NCU_TRAFFIC.get(dom))
     qr_gflops = qr_alg / (per_launch_ms[qr_name] * 1e-3) / 1e9
     lsqr_ms = per_launch_ms["k_lsqr"]
     spmv_gbs = lsqr_bytes_per_iter(m, ranks, S.sizes["n_rows"], 4) * kstar["mixed"] / (lsqr_ms * 1e-3) / 1e9

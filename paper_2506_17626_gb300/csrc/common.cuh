@@ -103,8 +103,7 @@ struct HostPlan {
 };
 
 constexpr int kFwdRows = 128;  // rows of a forward (A x) work item (one warp)
-constexpr int kTStageBytes = 20480;  // bytes of one staged column chunk of the transposed product
-constexpr int kTStages = 4;          // depth of that staging ring (one consumer warp per stage)
+constexpr int kTStageBytes = 20480;  // bytes of one staged column chunk of the transposed product (at most)
 
 // Columns per staged chunk of a block with leading dimension ldm.
 __host__ __device__ inline int tchunk_cols(int ldm, int elem_bytes) {

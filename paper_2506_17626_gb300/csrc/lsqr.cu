@@ -734,8 +734,8 @@ __global__ void k_report(const LsqrScal *__restrict__ sc, int n, rfm_lsqr_report
 template <typename TA>
 struct TileSmem {
     double wacc[2][kThreads / 32][64];          // per-warp partials per instance (alpha^2, ||y||^2)
-    double acc_b[kMaxInst], hacc[kMaxInst];
-    double tmp[kMaxInst], tmp2[kMaxInst], yy[kMaxInst];
+    double acc_b[64], hacc[64];   // at most 64 instances per solve
+    double tmp[64], tmp2[64], yy[64];
     double wred[2][8];
     LsqrScal sc[64];
     // per-instance factors formed once per phase (no division or square root
@@ -934,7 +934,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
                                                          const int *__restrict__ n_fitems_p, TA *__restrict__ tu,
                                                          const ColItem *__restrict__ titems,
                                                          const int *__restrict__ n_titems_p, double *__restrict__ zg,
-                                                         int cc_max) {
+                                                         int cc_max, int ns, int stage_bytes) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSmem<TA> &S = *reinterpret_cast<TileSmem<TA> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, G = gridDim.x, cta = blockIdx.x;
@@ -1012,8 +1012,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
     // contiguous chunk range [u_lo, u_hi) (block order).  A chunk is
     // contiguous in memory (column-major blocks) and is brought in whole by
     // one bulk asynchronous copy.  Warp 0 is the producer: one lane issues
-    // chunk k into stage k mod kTStages once that stage's previous chunk has
-    // been released.  Warp 1 + s is the consumer of stage s: it waits for the
+    // chunk k into stage k mod ns once that stage's previous chunk has been
+    // released (ns stages as wide as the widest chunk, as many as fit).  Warp 1 + s is the consumer of stage s: it waits for the
     // copy, reduces every column of the chunk against u~ (read from the
     // L1-cached block-row copy), stores z and releases the stage -- no
     // CTA-wide barrier per chunk.  Full and empty mbarriers per stage, every
@@ -1022,12 +1022,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
     const int64_t n_tu = *n_titems_p;
     const int64_t u_lo = n_tu * cta / G, u_hi = n_tu * (cta + 1) / G;
     unsigned char *ring_base = smem_raw + ((sizeof(TileSmem<TA>) + 127) / 128) * 128;
-    uint64_t *rfull = reinterpret_cast<uint64_t *>(ring_base);
-    uint64_t *rempty = rfull + kTStages;
+    uint64_t *rfull = reinterpret_cast<uint64_t *>(ring_base);   // ns <= 7 stages: 14 mbarriers in 128 bytes
+    uint64_t *rempty = rfull + ns;
     unsigned char *stage_mem = ring_base + 128;
     unsigned ring_k = 0;   // chunks this CTA has streamed so far (identical in every thread)
     if (tid == 0) {
-        for (int i = 0; i < kTStages; ++i) {
+        for (int i = 0; i < ns; ++i) {
             mbar_init(&rfull[i], 1);
             mbar_init(&rempty[i], 1);
         }
@@ -1080,29 +1080,30 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
             bool ok_p = true;
             for_taken(take, [&](const ColItem &it, unsigned k) {
                 const unsigned K = ring_k + k;
-                const int st = (int)(K % kTStages);
+                const int st = (int)(K % (unsigned)ns);
                 if (lane == 0) {
-                    if (K >= (unsigned)kTStages && !mbar_wait(&rempty[st], ((K / kTStages) - 1u) & 1u, a.timeout_ns)) {
+                    if (K >= (unsigned)ns && !mbar_wait(&rempty[st], ((K / (unsigned)ns) - 1u) & 1u, a.timeout_ns)) {
                         atomicCAS(a.bar + 2, 0u, (unsigned)RFM_ETIMEOUT);
                         ok_p = false;
                     } else {
                         const unsigned bytes = (unsigned)(it.nc * it.ldm * (int)sizeof(TA));
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                         mbar_expect_tx(&rfull[st], bytes);
-                        bulk_g2s(stage_mem + (size_t)st * kTStageBytes, Aop + it.moff + (int64_t)it.c0 * it.ldm,
+                        bulk_g2s(stage_mem + (size_t)st * stage_bytes, Aop + it.moff + (int64_t)it.c0 * it.ldm,
                                  bytes, &rfull[st]);
                     }
                 }
                 return __shfl_sync(0xffffffffu, ok_p ? 1 : 0, 0) != 0;
             });
-        } else if (warp <= kTStages) {
+        } else if (warp <= ns) {
             const unsigned st = (unsigned)(warp - 1);
             constexpr int VW = sizeof(TA) == 4 ? 4 : 2, STRIP = 32 * VW;
-            const TA *tile = reinterpret_cast<const TA *>(stage_mem + (size_t)st * kTStageBytes);
+            const TA *tile = reinterpret_cast<const TA *>(stage_mem + (size_t)st * stage_bytes);
             for_taken(take, [&](const ColItem &it, unsigned k) {
                 const unsigned K = ring_k + k;
-                if (K % kTStages != st) return true;
-                const bool landed = __all_sync(0xffffffffu, mbar_wait(&rfull[st], (K / kTStages) & 1u, a.timeout_ns));
+                if (K % (unsigned)ns != st) return true;
+                const bool landed =
+                    __all_sync(0xffffffffu, mbar_wait(&rfull[st], (K / (unsigned)ns) & 1u, a.timeout_ns));
                 if (!landed) {
                     if (lane == 0) atomicCAS(a.bar + 2, 0u, (unsigned)RFM_ETIMEOUT);
                     return false;
@@ -1469,7 +1470,20 @@ static rfm_status run_lsqr_tiles(const HostPlan &P, void *ws, LsqrArgs &args, cu
                   (long long)L.max_m, (int)(kTStageBytes / sizeof(TA)));
         return RFM_EINVAL;
     }
-    const size_t sm = ((sizeof(TileSmem<TA>) + 127) / 128) * 128 + 128 + (size_t)kTStages * kTStageBytes;
+    // ring stages: as wide as the widest chunk of this system, as many as fit
+    // beside the scalar state with two CTAs per SM (at most 7: warps 1-7 consume)
+    int cc_max = 1, stage_bytes = 128;
+    for (int64_t b = 0; b < L.n_blocks; ++b) {
+        const int cc = tchunk_cols(P.blk[b].ldm, (int)sizeof(TA));
+        cc_max = std::max(cc_max, cc);
+        stage_bytes = std::max(stage_bytes, cc * P.blk[b].ldm * (int)sizeof(TA));
+    }
+    stage_bytes = (stage_bytes + 127) / 128 * 128;
+    const size_t fixed = ((sizeof(TileSmem<TA>) + 127) / 128) * 128 + 128;
+    const size_t budget = 112 * 1024;   // per CTA, two CTAs per SM
+    int ns = budget > fixed ? (int)((budget - fixed) / (size_t)stage_bytes) : 0;
+    ns = std::min(7, std::max(2, ns));
+    const size_t sm = fixed + (size_t)ns * stage_bytes;
     RFM_CUDA_CHECK(cudaFuncSetAttribute(k_lsqr_tiles<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     RFM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lsqr_tiles<TA>, kThreads, sm));
     if (per < 1) {
@@ -1484,10 +1498,8 @@ static rfm_status run_lsqr_tiles(const HostPlan &P, void *ws, LsqrArgs &args, cu
     const ColItem *citems = items, *cfitems = ws_ptr<ColItem>(ws, L.off_fitems), *ctitems = titems;
     const int *cn = nitems, *cfn = ws_ptr<int>(ws, L.off_nfitems), *ctn = ntitems;
     double *zg = ws_ptr<double>(ws, L.off_z);
-    int cc_max = 1;   // widest chunk of any block (columns per staged copy)
-    for (int64_t b = 0; b < L.n_blocks; ++b) cc_max = std::max(cc_max, tchunk_cols(P.blk[b].ldm, (int)sizeof(TA)));
     void *kargs[] = {&args, (void *)&citems, (void *)&cn, (void *)&cfitems, (void *)&cfn, (void *)&tu,
-                     (void *)&ctitems, (void *)&ctn, (void *)&zg, (void *)&cc_max};
+                     (void *)&ctitems, (void *)&ctn, (void *)&zg, (void *)&cc_max, (void *)&ns, (void *)&stage_bytes};
     ProfScope ps("k_lsqr", st);
     RFM_CUDA_CHECK(cudaLaunchCooperativeKernel((const void *)k_lsqr_tiles<TA>, dim3(G), dim3(kThreads), kargs, sm, st));
     return RFM_OK;
