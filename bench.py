@@ -49,8 +49,8 @@ FP64_PEAK_GFLOPS = 152 * 4 * 2.07
 # iteration for k_lsqr ((11.955 + 0.343) GB over a 50-iteration capture, scaled
 # by the launch's iteration count), per launch otherwise; a kernel without an
 # entry reports None.
-NCU_TRAFFIC_PER_ITER = {"k_lsqr": 12.298e9 / 50}
-NCU_TRAFFIC = {"k_qrcp_cluster": 0.842e9}
+NCU_TRAFFIC_PER_ITER = {}
+NCU_TRAFFIC = {}
 
 
 def workload(case: str = "full"):
@@ -176,6 +176,9 @@ def run_gpu(args):
         return S
 
     paths = {"mixed": make("fp32", "q32"), "fp64": make("fp64", "q64")}
+    # the QR cluster size is autotuned on the first filter call of each path
+    # (untimed: calibration or warm-up) unless --no-autotune
+    N.set_autotune(not args.no_autotune)
 
     # ---- calibration (untimed): error after every SNAP_EVERY iterations
     curves, conv = {}, {}
@@ -326,7 +329,8 @@ def run_gpu(args):
                    "target_rel_l2": target, "iterations": kstar, "rel_l2_reached": {"mixed": rel_m, "fp64": rel_f},
                    "convergence_10000_iterations": conv,
                    "l2_flush": "none: working set (M, QR work, Q_hat > 1.5 GB) exceeds L2 every step",
-                   "parallelism": f"independent instances x{world}" if world > 1 else "1 instance"},
+                   "parallelism": f"independent instances x{world}" if world > 1 else "1 instance",
+                   "qr_cluster_autotune": not args.no_autotune},
         "fp64_zero_start_ms": ms_fp64,
         "qr_gflops": qr_gflops, "spmv_gbs": spmv_gbs,
         "kernels_ms_per_step": {k: v[1] / steps for k, v in tot.items()},
@@ -553,6 +557,7 @@ def main():
     ap.add_argument("--iters-mixed", type=int, default=None, help="skip calibration: LSQR iterations (mixed)")
     ap.add_argument("--iters-fp64", type=int, default=None, help="skip calibration: LSQR iterations (FP64)")
     ap.add_argument("--target", type=float, default=None, help="target recorded when calibration is skipped")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default QR cluster size")
     ap.add_argument("--learned-train", type=int, default=384,
                     help="training solves of the learned warm start section (0 skips it)")
     ap.add_argument("--learned-epochs", type=int, default=6)

@@ -103,12 +103,11 @@ struct HostPlan {
 };
 
 constexpr int kFwdRows = 128;  // rows of a forward (A x) work item (one warp)
-constexpr int kTStageBytes = 20480;  // bytes of one staged column chunk of the transposed product (at most)
-
-// Columns per staged chunk of a block with leading dimension ldm.
+// Columns per chunk of the transposed product (one warp per chunk).
 __host__ __device__ inline int tchunk_cols(int ldm, int elem_bytes) {
-    const int c = kTStageBytes / (ldm * elem_bytes);
-    return c < 1 ? 1 : c;
+    (void)ldm;
+    (void)elem_bytes;
+    return 8;
 }
 constexpr int kColTile = 8;    // columns of a transpose (A^T u) work item (one warp)
 

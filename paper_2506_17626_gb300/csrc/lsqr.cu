@@ -933,8 +933,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
                                                          const ColItem *__restrict__ fitems,
                                                          const int *__restrict__ n_fitems_p, TA *__restrict__ tu,
                                                          const ColItem *__restrict__ titems,
-                                                         const int *__restrict__ n_titems_p, double *__restrict__ zg,
-                                                         int cc_max, int ns, int stage_bytes) {
+                                                         const int *__restrict__ n_titems_p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSmem<TA> &S = *reinterpret_cast<TileSmem<TA> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, G = gridDim.x, cta = blockIdx.x;
@@ -1008,166 +1007,105 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
     };
     // forward product of block row q
     auto row_partials = [&](int64_t q) { return a.t[q]; };
-    // ---- transposed product through a bulk-copy ring.  This CTA owns the
-    // contiguous chunk range [u_lo, u_hi) (block order).  A chunk is
-    // contiguous in memory (column-major blocks) and is brought in whole by
-    // one bulk asynchronous copy.  Warp 0 is the producer: one lane issues
-    // chunk k into stage k mod ns once that stage's previous chunk has been
-    // released (ns stages as wide as the widest chunk, as many as fit).  Warp 1 + s is the consumer of stage s: it waits for the
-    // copy, reduces every column of the chunk against u~ (read from the
-    // L1-cached block-row copy), stores z and releases the stage -- no
-    // CTA-wide barrier per chunk.  Full and empty mbarriers per stage, every
-    // wait bounded.  The FP64 epilogue then runs over the range with
-    // lane-private per-instance sums.
+    // ---- transposed product: one warp per chunk of up to 8 columns of a
+    // block (chunks in block order, spread over every warp of the grid).  Each
+    // lane keeps 2 x 8 sixteen-byte loads of the operator in flight, the 8
+    // column sums are reduce-scattered in 9 shuffles so that lane 4t holds
+    // column t, and those lanes apply the FP64 update of vt at once (it
+    // overlaps the other warps' loads).  Per-instance sums ||vt||^2, ||y||^2
+    // stay lane-private until the instance changes.
     const int64_t n_tu = *n_titems_p;
-    const int64_t u_lo = n_tu * cta / G, u_hi = n_tu * (cta + 1) / G;
-    unsigned char *ring_base = smem_raw + ((sizeof(TileSmem<TA>) + 127) / 128) * 128;
-    uint64_t *rfull = reinterpret_cast<uint64_t *>(ring_base);   // ns <= 7 stages: 14 mbarriers in 128 bytes
-    uint64_t *rempty = rfull + ns;
-    unsigned char *stage_mem = ring_base + 128;
-    unsigned ring_k = 0;   // chunks this CTA has streamed so far (identical in every thread)
-    if (tid == 0) {
-        for (int i = 0; i < ns; ++i) {
-            mbar_init(&rfull[i], 1);
-            mbar_init(&rempty[i], 1);
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-    // The CTA's chunk descriptors are read 32 at a time, one per lane (a
-    // dependent walk of the list would cost a memory round trip per chunk);
-    // take marks the chunks of live instances, k numbers them in order.
-    auto shfl_item = [&](const ColItem &it, int src) {
-        ColItem o;
-        o.b = __shfl_sync(0xffffffffu, it.b, src);
-        o.c0 = __shfl_sync(0xffffffffu, it.c0, src);
-        o.nc = __shfl_sync(0xffffffffu, it.nc, src);
-        o.m = __shfl_sync(0xffffffffu, it.m, src);
-        o.ldm = __shfl_sync(0xffffffffu, it.ldm, src);
-        o.inst = __shfl_sync(0xffffffffu, it.inst, src);
-        o.moff = __shfl_sync(0xffffffffu, it.moff, src);
-        o.coff = __shfl_sync(0xffffffffu, it.coff, src);
-        o.roff = __shfl_sync(0xffffffffu, it.roff, src);
-        return o;
-    };
-    // for_taken(fn): fn(it, k) for every taken chunk of the range, in order,
-    // called by all 32 lanes of the warp with the same arguments
-    auto for_taken = [&](auto take, auto fn) {
-        unsigned k = 0;
-        for (int64_t base = u_lo; base < u_hi; base += 32) {
-            const int64_t u = base + lane;
-            ColItem mine;
-            mine.inst = -1;
-            bool tk = false;
-            if (u < u_hi) {
-                mine = titems[u];
-                tk = take(mine.inst);
-            }
-            unsigned mask = __ballot_sync(0xffffffffu, tk);
-            while (mask) {
-                const int src = __ffs(mask) - 1;
-                mask &= mask - 1;
-                const ColItem it = shfl_item(mine, src);
-                if (!fn(it, k)) return k + 1;
-                ++k;
-            }
-        }
-        return k;
-    };
     auto tphase = [&](auto take, auto epi) {
-        if (warp == 0) {
-            bool ok_p = true;
-            for_taken(take, [&](const ColItem &it, unsigned k) {
-                const unsigned K = ring_k + k;
-                const int st = (int)(K % (unsigned)ns);
-                if (lane == 0) {
-                    if (K >= (unsigned)ns && !mbar_wait(&rempty[st], ((K / (unsigned)ns) - 1u) & 1u, a.timeout_ns)) {
-                        atomicCAS(a.bar + 2, 0u, (unsigned)RFM_ETIMEOUT);
-                        ok_p = false;
-                    } else {
-                        const unsigned bytes = (unsigned)(it.nc * it.ldm * (int)sizeof(TA));
-                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        mbar_expect_tx(&rfull[st], bytes);
-                        bulk_g2s(stage_mem + (size_t)st * stage_bytes, Aop + it.moff + (int64_t)it.c0 * it.ldm,
-                                 bytes, &rfull[st]);
-                    }
-                }
-                return __shfl_sync(0xffffffffu, ok_p ? 1 : 0, 0) != 0;
-            });
-        } else if (warp <= ns) {
-            const unsigned st = (unsigned)(warp - 1);
-            constexpr int VW = sizeof(TA) == 4 ? 4 : 2, STRIP = 32 * VW;
-            const TA *tile = reinterpret_cast<const TA *>(stage_mem + (size_t)st * stage_bytes);
-            for_taken(take, [&](const ColItem &it, unsigned k) {
-                const unsigned K = ring_k + k;
-                if (K % (unsigned)ns != st) return true;
-                const bool landed =
-                    __all_sync(0xffffffffu, mbar_wait(&rfull[st], (K / (unsigned)ns) & 1u, a.timeout_ns));
-                if (!landed) {
-                    if (lane == 0) atomicCAS(a.bar + 2, 0u, (unsigned)RFM_ETIMEOUT);
-                    return false;
-                }
-                const TA *ub = tu + it.roff;
-                for (int c = 0; c < it.nc; ++c) {
-                    const TA *col = tile + (int64_t)c * it.ldm;
-                    TA s4 = (TA)0;
-                    if (sizeof(TA) == 4) {
-                        for (int i = VW * lane; i < it.ldm; i += STRIP) {
-                            const float4 q = *reinterpret_cast<const float4 *>(col + i);
-                            const float4 w = *reinterpret_cast<const float4 *>(ub + i);
-                            s4 += (TA)(q.x * w.x + q.y * w.y + q.z * w.z + q.w * w.w);
-                        }
-                    } else {
-                        for (int i = VW * lane; i < it.ldm; i += STRIP) {
-                            const double2 q = *reinterpret_cast<const double2 *>(col + i);
-                            const double2 w = *reinterpret_cast<const double2 *>(ub + i);
-                            s4 += (TA)(q.x * w.x + q.y * w.y);
-                        }
-                    }
-                    for (int o = 16; o; o >>= 1) s4 += __shfl_xor_sync(0xffffffffu, s4, o);
-                    if (lane == 0) zg[it.coff + it.c0 + c] = (double)s4;
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&rempty[st]);
-                return true;
-            });
-        }
-        __syncthreads();
-        // every thread advances the ring count by the chunks taken in this phase
-        unsigned taken = 0;
-        for (int64_t base = u_lo; base < u_hi; base += kThreads) {
-            const int64_t u = base + tid;
-            const bool tk = u < u_hi && take(titems[u].inst);
-            taken += (unsigned)__syncthreads_count(tk);
-        }
-        ring_k += taken;
-        // epilogue over this CTA's columns, one thread per column (all lanes
-        // busy: the FP64 pipe is the limit here), one pass per instance present
-        // in the range so that every per-instance sum has a fixed order
-        const int ccm = cc_max;
-        const int inst_lo = u_lo < u_hi ? titems[u_lo].inst : 0;
-        const int inst_hi = u_lo < u_hi ? titems[u_hi - 1].inst : -1;
-        const int64_t nflat = (u_hi - u_lo) * ccm;
-        for (int si = inst_lo; si <= inst_hi; ++si) {
-            if (!take(si)) continue;
-            double pa = 0.0, py = 0.0;
-            for (int64_t f = tid; f < nflat; f += kThreads) {
-                const ColItem &it = titems[u_lo + f / ccm];
-                const int j = (int)(f % ccm);
-                if (it.inst != si || j >= it.nc) continue;
-                const int64_t o = it.coff + it.c0 + j;
-                epi(si, o, zg[o], &pa, &py);
-            }
+        constexpr int VW = sizeof(TA) == 4 ? 4 : 2, STRIP = 32 * VW;
+        double pa = 0.0, py = 0.0;
+        int cur_inst = -1;
+        auto flush_lane = [&]() {
+            double x = pa, z = py;
             for (int o = 16; o; o >>= 1) {
-                pa += __shfl_xor_sync(0xffffffffu, pa, o);
-                py += __shfl_xor_sync(0xffffffffu, py, o);
+                x += __shfl_xor_sync(0xffffffffu, x, o);
+                z += __shfl_xor_sync(0xffffffffu, z, o);
             }
-            if (lane == 0) {
-                S.wacc[0][warp][si] += pa;
-                S.wacc[1][warp][si] += py;
+            if (lane == 0 && cur_inst >= 0) {
+                S.wacc[0][warp][cur_inst] += x;
+                S.wacc[1][warp][cur_inst] += z;
+            }
+            pa = py = 0.0;
+        };
+        const int mycol = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);   // for lane % 4 == 0
+        for (int64_t k = gwarp; k < n_tu; k += twarps) {
+            const ColItem it = titems[k];
+            if (!take(it.inst)) continue;
+            if (it.inst != cur_inst) {
+                flush_lane();
+                cur_inst = it.inst;
+            }
+            const TA *ub = tu + it.roff;
+            for (int g0 = 0; g0 < it.nc; g0 += 8) {
+                const TA *base = Aop + it.moff + (int64_t)(it.c0 + g0) * it.ldm;
+                const int ng = min(8, it.nc - g0);
+                TA acc[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[c] = (TA)0;
+                for (int i0 = 0; i0 < it.ldm; i0 += 2 * STRIP) {
+                    TA w[2][VW], q[8][2][VW];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int i = i0 + STRIP * h + VW * lane;
+                        const bool in = i < it.ldm;
+                        if (sizeof(TA) == 4) {
+                            const float4 t = in ? *reinterpret_cast<const float4 *>(ub + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+                            w[h][0] = (TA)t.x; w[h][1 % VW] = (TA)t.y; w[h][2 % VW] = (TA)t.z; w[h][3 % VW] = (TA)t.w;
+                        } else {
+                            const double2 t = in ? *reinterpret_cast<const double2 *>(ub + i) : make_double2(0.0, 0.0);
+                            w[h][0] = (TA)t.x; w[h][1] = (TA)t.y;
+                        }
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const bool ok = in && c < ng;
+                            const TA *src = base + (int64_t)c * it.ldm + (ok ? i : 0);
+                            if (sizeof(TA) == 4) {
+                                const float4 t = ok ? __ldg(reinterpret_cast<const float4 *>(src)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                                q[c][h][0] = (TA)t.x; q[c][h][1 % VW] = (TA)t.y; q[c][h][2 % VW] = (TA)t.z; q[c][h][3 % VW] = (TA)t.w;
+                            } else {
+                                const double2 t = ok ? __ldg(reinterpret_cast<const double2 *>(src)) : make_double2(0.0, 0.0);
+                                q[c][h][0] = (TA)t.x; q[c][h][1] = (TA)t.y;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+#pragma unroll
+                        for (int c = 0; c < 8; ++c)
+#pragma unroll
+                            for (int v = 0; v < VW; ++v) acc[c] += q[c][h][v] * w[h][v];
+                }
+                // reduce-scatter: lane 4t ends with the full sum of column t
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const bool hi = lane & 16;
+                    const TA send = hi ? acc[j] : acc[j + 4], keep = hi ? acc[j + 4] : acc[j];
+                    acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const bool hi = lane & 8;
+                    const TA send = hi ? acc[j] : acc[j + 2], keep = hi ? acc[j + 2] : acc[j];
+                    acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                }
+                {
+                    const bool hi = lane & 4;
+                    const TA send = hi ? acc[0] : acc[1], keep = hi ? acc[1] : acc[0];
+                    acc[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                }
+                acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 2);
+                acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+                if ((lane & 3) == 0 && mycol < ng) {
+                    const int64_t o = it.coff + it.c0 + g0 + mycol;
+                    epi(it.inst, o, (double)acc[0], &pa, &py);
+                }
             }
         }
+        flush_lane();
     };
 
     // elementwise over the kept column slots
@@ -1463,27 +1401,7 @@ static rfm_status run_lsqr_tiles(const HostPlan &P, void *ws, LsqrArgs &args, cu
                                           ntitems, (int)sizeof(TA), L.n_t_items);
         RFM_CUDA_CHECK(cudaGetLastError());
     }
-    // every staged chunk must fit a stage: one column of the tallest block
-    const int64_t ld_max = (L.max_m + kLdAlign - 1) / kLdAlign * kLdAlign;
-    if (ld_max * (int64_t)sizeof(TA) > kTStageBytes) {
-        set_error("rfm_lsqr_solve: blocks of %lld rows exceed the staged transposed product (%d rows at most)",
-                  (long long)L.max_m, (int)(kTStageBytes / sizeof(TA)));
-        return RFM_EINVAL;
-    }
-    // ring stages: as wide as the widest chunk of this system, as many as fit
-    // beside the scalar state with two CTAs per SM (at most 7: warps 1-7 consume)
-    int cc_max = 1, stage_bytes = 128;
-    for (int64_t b = 0; b < L.n_blocks; ++b) {
-        const int cc = tchunk_cols(P.blk[b].ldm, (int)sizeof(TA));
-        cc_max = std::max(cc_max, cc);
-        stage_bytes = std::max(stage_bytes, cc * P.blk[b].ldm * (int)sizeof(TA));
-    }
-    stage_bytes = (stage_bytes + 127) / 128 * 128;
-    const size_t fixed = ((sizeof(TileSmem<TA>) + 127) / 128) * 128 + 128;
-    const size_t budget = 112 * 1024;   // per CTA, two CTAs per SM
-    int ns = budget > fixed ? (int)((budget - fixed) / (size_t)stage_bytes) : 0;
-    ns = std::min(7, std::max(2, ns));
-    const size_t sm = fixed + (size_t)ns * stage_bytes;
+    const size_t sm = sizeof(TileSmem<TA>);
     RFM_CUDA_CHECK(cudaFuncSetAttribute(k_lsqr_tiles<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     RFM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lsqr_tiles<TA>, kThreads, sm));
     if (per < 1) {
@@ -1497,9 +1415,8 @@ static rfm_status run_lsqr_tiles(const HostPlan &P, void *ws, LsqrArgs &args, cu
     RFM_CUDA_CHECK(cudaMemsetAsync(tu, 0, sizeof(TA) * (size_t)L.block_rows, st));
     const ColItem *citems = items, *cfitems = ws_ptr<ColItem>(ws, L.off_fitems), *ctitems = titems;
     const int *cn = nitems, *cfn = ws_ptr<int>(ws, L.off_nfitems), *ctn = ntitems;
-    double *zg = ws_ptr<double>(ws, L.off_z);
     void *kargs[] = {&args, (void *)&citems, (void *)&cn, (void *)&cfitems, (void *)&cfn, (void *)&tu,
-                     (void *)&ctitems, (void *)&ctn, (void *)&zg, (void *)&cc_max, (void *)&ns, (void *)&stage_bytes};
+                     (void *)&ctitems, (void *)&ctn};
     ProfScope ps("k_lsqr", st);
     RFM_CUDA_CHECK(cudaLaunchCooperativeKernel((const void *)k_lsqr_tiles<TA>, dim3(G), dim3(kThreads), kargs, sm, st));
     return RFM_OK;

@@ -276,8 +276,9 @@ rfm_status build_plan(const rfm_problem *probs, int n_inst, const rfm_config *cf
     L.off_nitems = take(256);
     L.off_z = take(sizeof(double) * (col0 + 1));
     {
-        // bound for either operator precision (8-byte elements give the most
-        // chunks; the fit of predicted values runs an FP64 operator on any system)
+        // chunks of the transposed product over every block's K columns (the
+        // ranks are known only on the device; the fit of predicted values runs
+        // an FP64 operator on any system)
         int64_t nt = 0;
         for (const BlkRec &B : blk) {
             const int cc = tchunk_cols(B.ldm, 8);

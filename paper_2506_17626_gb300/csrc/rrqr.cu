@@ -285,11 +285,14 @@ __global__ void __launch_bounds__(kQT) k_qrcp_cluster(const BlkRec *__restrict__
     double *rk = cn0 + nloc_max;                     // nloc_max: R(k, c) of the step, for the norm downdate
     int *pos = (int *)(rk + nloc_max);               // nloc_max: position of the column, -1 while trailing
     int *redo = pos + nloc_max;                      // nloc_max: exact norm needed
+    int *lives = redo + nloc_max;                    // nloc_max: slots of the trailing columns (any order)
+    int *where = lives + nloc_max;                   // nloc_max: index of a slot in lives
     __shared__ Cand cand[2];
     __shared__ Cand red[kQW];
     __shared__ Cand s_win;
     __shared__ double s_red[kQW];
     __shared__ int s_ndrop;
+    __shared__ int s_nlive;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nloc = (K - cr + C - 1) / C;   // columns owned by this CTA
     double *Wb = W + B.moff;
@@ -308,8 +311,11 @@ __global__ void __launch_bounds__(kQT) k_qrcp_cluster(const BlkRec *__restrict__
             cn[l] = sqrt(s);
             cn0[l] = cn[l];
             pos[l] = -1;
+            lives[l] = l;
+            where[l] = l;
         }
     }
+    if (tid == 0) s_nlive = nloc;
     __syncthreads();
     const int steps = m < K ? m : K;
     const double tol3z = sqrt(2.220446049250313e-16);
@@ -321,8 +327,11 @@ __global__ void __launch_bounds__(kQT) k_qrcp_cluster(const BlkRec *__restrict__
         // 1. best non-retired column of this CTA
         double bv = -1.0;
         int bp = 0x7fffffff, bl = -1;
-        for (int l = tid; l < nloc; l += kQT)
-            if (pos[l] < 0 && better(cn[l], cr + C * l, bv, bp)) { bv = cn[l]; bp = cr + C * l; bl = l; }
+        const int nlive = s_nlive;
+        for (int t = tid; t < nlive; t += kQT) {
+            const int l = lives[t];
+            if (better(cn[l], cr + C * l, bv, bp)) { bv = cn[l]; bp = cr + C * l; bl = l; }
+        }
         for (int o = 16; o; o >>= 1) {
             double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
             int p2 = __shfl_xor_sync(0xffffffffu, bp, o);
@@ -386,27 +395,41 @@ __global__ void __launch_bounds__(kQT) k_qrcp_cluster(const BlkRec *__restrict__
         const double tk = (beta - alpha) / beta;
         __syncthreads();
         for (int i = k + 1 + tid; i < m; i += kQT) vbuf[i] *= scale;
-        if (cr == own && tid == 0) pos[wsl] = k;
+        if (cr == own && tid == 0) {
+            pos[wsl] = k;
+            // retire the pivot slot from the trailing list (swap with the last)
+            const int at = where[wsl], last = lives[s_nlive - 1];
+            lives[at] = last;
+            where[last] = at;
+            s_nlive -= 1;
+        }
         if (cr == 0 && tid == 0) tau[B.coff + k] = tk;
         __syncthreads();
         if (cr == own) { pend_slot = wsl; pend_k = k; pend_beta = beta; }
         // 5. update own trailing columns, two per warp at a time (independent
         //    reductions overlap); R(k, c) is kept for the downdate
-        for (int l = warp; l < nloc; l += 2 * kQW) {
-            const int l2 = l + kQW;
-            const bool h1 = pos[l] < 0, h2 = l2 < nloc && pos[l2] < 0;
-            if (!h1 && !h2) continue;
+        const int nl = s_nlive;
+        for (int t = 2 * warp; t < nl; t += 2 * kQW) {
+            const int l = lives[t];
+            const bool h2 = t + 1 < nl;
+            const int l2 = h2 ? lives[t + 1] : l;
+            const bool h1 = true;
             double *a1 = A + (size_t)l * ld_loc;
-            double *a2 = A + (size_t)(h2 ? l2 : l) * ld_loc;
+            double *a2 = A + (size_t)l2 * ld_loc;
             double d1 = 0.0, d2 = 0.0;
-            for (int i = k + 1 + lane; i < m; i += 32) {
-                const double v = vbuf[i];
-                d1 = fma(v, a1[i], d1);
-                d2 = fma(v, a2[i], d2);
-            }
-            for (int o = 16; o; o >>= 1) {
-                d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-                d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+            if (h2) {
+                for (int i = k + 1 + lane; i < m; i += 32) {
+                    const double v = vbuf[i];
+                    d1 = fma(v, a1[i], d1);
+                    d2 = fma(v, a2[i], d2);
+                }
+                for (int o = 16; o; o >>= 1) {
+                    d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+                    d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+                }
+            } else {
+                for (int i = k + 1 + lane; i < m; i += 32) d1 = fma(vbuf[i], a1[i], d1);
+                for (int o = 16; o; o >>= 1) d1 += __shfl_xor_sync(0xffffffffu, d1, o);
             }
             const double ak1 = a1[k], ak2 = a2[k];
             d1 = tk * (ak1 + d1);
@@ -424,8 +447,8 @@ __global__ void __launch_bounds__(kQT) k_qrcp_cluster(const BlkRec *__restrict__
         __syncthreads();
         // 6. norm downdate, one thread per column; columns whose downdate has
         //    lost half the digits are marked for an exact recompute
-        for (int l = tid; l < nloc; l += kQT) {
-            if (pos[l] >= 0) continue;
+        for (int t = tid; t < nl; t += kQT) {
+            const int l = lives[t];
             double cc = cn[l];
             int again = 0;
             if (cc != 0.0) {
@@ -440,8 +463,9 @@ __global__ void __launch_bounds__(kQT) k_qrcp_cluster(const BlkRec *__restrict__
             redo[l] = again;
         }
         __syncthreads();
-        for (int l = warp; l < nloc; l += kQW) {
-            if (pos[l] >= 0 || !redo[l]) continue;
+        for (int t = warp; t < nl; t += kQW) {
+            const int l = lives[t];
+            if (!redo[l]) continue;
             const double *a = A + (size_t)l * ld_loc;
             double e = 0.0;
             for (int i = k + 1 + lane; i < m; i += 32) e = fma(a[i], a[i], e);
@@ -548,6 +572,7 @@ template <typename TM, int C>
 static rfm_status launch_cluster(const FilterBufs &F, double tol, int nloc, int ldl, size_t smem, cudaStream_t st) {
     auto kern = k_qrcp_cluster<TM, C>;
     RFM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (C > 8) RFM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(F.n_blocks * C));
     cfg.blockDim = dim3(kQT);
@@ -569,7 +594,7 @@ static rfm_status launch_cluster(const FilterBufs &F, double tol, int nloc, int 
 static size_t cluster_smem(int64_t max_m, int64_t max_K, int C, int *nloc, int *ldl) {
     *ldl = (int)((max_m + 1) / 2 * 2);
     *nloc = (int)((max_K + C - 1) / C);
-    return ((size_t)(*nloc) * (*ldl) + 2 * (size_t)(*ldl)) * 8 + (size_t)(*nloc) * 32 + 64;
+    return ((size_t)(*nloc) * (*ldl) + 2 * (size_t)(*ldl)) * 8 + (size_t)(*nloc) * 40 + 64;
 }
 
 template <typename TM>
@@ -580,7 +605,8 @@ static rfm_status launch_cluster_c(int C, const FilterBufs &F, double tol, cudaS
         case 1: return launch_cluster<TM, 1>(F, tol, nloc, ldl, smem, st);
         case 2: return launch_cluster<TM, 2>(F, tol, nloc, ldl, smem, st);
         case 4: return launch_cluster<TM, 4>(F, tol, nloc, ldl, smem, st);
-        default: return launch_cluster<TM, 8>(F, tol, nloc, ldl, smem, st);
+        case 8: return launch_cluster<TM, 8>(F, tol, nloc, ldl, smem, st);
+        default: return launch_cluster<TM, 16>(F, tol, nloc, ldl, smem, st);
     }
 }
 
@@ -613,11 +639,45 @@ static rfm_status autotune_cluster(const FilterBufs &F, double tol, int C_min, c
     float best_ms = 0.f;
     *best = C_min;
     rfm_status rc = RFM_OK;
-    for (int C = C_min; C <= 8 && rc == RFM_OK; C *= 2) {
+    for (int C = C_min; C <= 16; C *= 2) {
+        // 16 CTAs per cluster is a non-portable size: ask whether this device
+        // can place such clusters before timing it
+        if (C > 8) {
+            int nclusters = 0;
+            int nloc = 0, ldl = 0;
+            const size_t smem = cluster_smem(F.max_m, F.max_K, C, &nloc, &ldl);
+            auto kern = k_qrcp_cluster<TM, 16>;
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+                cudaGetLastError();
+                break;
+            }
+            cudaLaunchConfig_t q = {};
+            q.gridDim = dim3(16);
+            q.blockDim = dim3(kQT);
+            q.dynamicSmemBytes = smem;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = 16;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            q.attrs = at;
+            q.numAttrs = 1;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &q) != cudaSuccess || nclusters < 1) {
+                cudaGetLastError();
+                break;
+            }
+        }
         cudaEventRecord(e0, st);
         rc = launch_cluster_c<TM>(C, F, tol, st);
         cudaEventRecord(e1, st);
-        if (rc != RFM_OK) break;
+        if (rc != RFM_OK) {
+            if (C > 8 && C > C_min) {   // an optional size the device refused: the earlier runs' result stands
+                cudaGetLastError();
+                rc = RFM_OK;
+            }
+            break;
+        }
         if (cudaEventSynchronize(e1) != cudaSuccess) {
             set_error("QR autotuner: timing run failed");
             rc = RFM_ECUDA;
@@ -652,7 +712,7 @@ static rfm_status launch_filter_t(const FilterBufs &F, double tol, cudaStream_t 
         ProfScope ps(F.fit ? "k_qrcp_cluster_fit" : "k_qrcp_cluster", st);
         rfm_status rc;
         int tuned = g_autotune ? cached_cluster(F, (int)sizeof(TM)) : 0;
-        if (g_autotune && tuned == 0 && C < 8) {
+        if (g_autotune && tuned == 0) {
             rc = autotune_cluster<TM>(F, tol, C, st, &tuned);   // leaves a valid result
         } else {
             rc = launch_cluster_c<TM>(tuned ? tuned : C, F, tol, st);
