@@ -46,11 +46,11 @@ CAL_ITERS = 10000
 # 1194 GFLOP/s on this part).
 FP64_PEAK_GFLOPS = 152 * 4 * 2.07
 # DRAM traffic from ncu captures of the current kernels (profiles/): per LSQR
-# iteration for k_lsqr ((11.955 + 0.343) GB over a 50-iteration capture, scaled
+# iteration for k_lsqr ((10.690 + 0.283) GB over a 50-iteration capture, scaled
 # by the launch's iteration count), per launch otherwise; a kernel without an
 # entry reports None.
-NCU_TRAFFIC_PER_ITER = {}
-NCU_TRAFFIC = {}
+NCU_TRAFFIC_PER_ITER = {"k_lsqr": (10.690e9 + 0.283e9) / 50}
+NCU_TRAFFIC = {"k_qrcp_cluster": 0.841e9}
 
 
 def workload(case: str = "full"):
