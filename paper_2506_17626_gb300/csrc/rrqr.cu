@@ -3,21 +3,28 @@
 //
 // k_qrcp: one CTA per block, FP64 Householder QR with column pivoting on a
 // working copy W of M_j (column-major, leading dimension ldm).  Step k:
-//   1. pivot = trailing column of largest norm (norms kept in shared memory,
-//      ties to the lowest original index), swapped into place;
+//   1. pivot = trailing column of largest norm (squared norms kept in shared
+//      memory and compared as integers -- non-negative doubles order like
+//      their bit patterns; ties to the lowest original index), swapped into
+//      place;
 //   2. ||W[k:m, k]|| recomputed exactly; stop when it is 0 or < tol |R_11|;
 //   3. reflector beta = -sign(alpha) ||x||, v = x / (alpha - beta), v_0 = 1,
 //      tau = (beta - alpha) / beta (v stored below the diagonal);
-//   4. every trailing column c: s = tau v^T W[k:m, c], W[k:m, c] -= s v
-//      (one warp per column), then its norm is downdated,
-//      ||W[k+1:m, c]||^2 = ||W[k:m, c]||^2 - W[k, c]^2, and recomputed
-//      exactly when cancellation has eaten more than half the digits since
-//      the last exact value (the downdated value's relative error grows like
-//      eps (norm at last recompute / current norm)^2).
+//   4. every trailing column c: W[k:m, c] -= tau v (v^T W[k:m, c]) (one warp
+//      per column), applied with the unscaled x: with g = tau / (alpha - beta)
+//      = -1 / beta, d = tau W[k, c] + g x^T W[k+1:m, c] and W[k+1:m, c] -=
+//      (d / (alpha - beta)) x; then its squared norm is downdated,
+//      ||W[k+1:m, c]||^2 = ||W[k:m, c]||^2 - W[k, c]^2, and recomputed exactly
+//      when cancellation has eaten more than half the digits since the last
+//      exact value (the downdated value's relative error grows like
+//      eps (squared norm at last recompute / current squared norm)).
 // FP64 throughput is the bound: per element of the trailing matrix one FMA
-// for the dot product and one for the update.
+// for the dot product and one for the update.  GB300 issues an FP64 warp
+// instruction at a small fraction of the FP32 rate, so the per-step scalars
+// are formed once, by one warp, and comparisons avoid the FP64 pipe.
 #include <cooperative_groups.h>
 
+#include <climits>
 #include <mutex>
 #include <vector>
 
@@ -26,12 +33,39 @@
 
 namespace rfm {
 
-struct ArgMax {
-    double v;
-    int p, c;
-};
+constexpr unsigned kFull = 0xffffffffu;
 
-__device__ inline bool better(double v1, int p1, double v2, int p2) { return v1 > v2 || (v1 == v2 && p1 < p2); }
+// Pivot order: larger squared norm first, then lower original column index.
+__device__ inline long long norm_key(double c2) { return __double_as_longlong(c2); }   // c2 >= 0
+__device__ inline bool key_better(long long k1, int o1, long long k2, int o2) {
+    return k1 > k2 || (k1 == k2 && o1 < o2);
+}
+
+// Householder scalars of a pivot column with first entry alpha and norm
+// nx > 0: beta = -sign(alpha) nx, sc = 1 / (alpha - beta) (the scaling of v),
+// tau = (beta - alpha) / beta and g = tau sc = -1 / beta, from one division
+// (|alpha - beta| = |alpha| + nx, so nothing cancels).
+__device__ inline void house_scalars(double alpha, double nx, double *h) {
+    const double beta = alpha >= 0.0 ? -nx : nx;
+    const double amb = alpha - beta;
+    const double inv = 1.0 / (amb * beta);
+    const double g = -amb * inv;
+    h[1] = beta;
+    h[2] = beta * inv;   // sc
+    h[3] = amb * g;      // tau
+    h[4] = g;
+}
+
+// Squared-norm downdate of a trailing column after step k (rk = R(k, c)).
+// Returns true when the column's norm must be recomputed exactly.
+__device__ inline bool downdate(double c2, double thr, double rk, double *c2_new) {
+    if (c2 == 0.0) {
+        *c2_new = 0.0;
+        return false;
+    }
+    *c2_new = fma(-rk, rk, c2);
+    return !(*c2_new > thr);
+}
 
 template <typename TM>
 __global__ void __launch_bounds__(256) k_qrcp(const BlkRec *__restrict__ blks, const TM *__restrict__ M,
@@ -41,16 +75,18 @@ __global__ void __launch_bounds__(256) k_qrcp(const BlkRec *__restrict__ blks, c
     extern __shared__ double smem[];
     const BlkRec B = blks[blockIdx.x];
     const int m = B.m, K = B.K, ld = B.ldm;
-    double *cn = smem;             // K current trailing norms
-    double *cn0 = smem + K;        // K norms at the last exact recompute
+    double *cn2 = smem;            // K squared trailing norms
+    double *thr = smem + K;        // K recompute thresholds: tol3z * last exact squared norm
     int *perm = (int *)(smem + 2 * K);
-    __shared__ double red_v[8];
-    __shared__ int red_p[8], red_c[8];
-    __shared__ double s_nx;
+    __shared__ long long red_k[8];
+    __shared__ int red_o[8], red_c[8];
+    __shared__ double s_red[8];
+    __shared__ double s_h[5];
     __shared__ int s_piv;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double *Wb = W + B.moff;
     const TM *Mb = M + B.moff;
+    const double tol3z = sqrt(2.220446049250313e-16);
 
     // working copy in FP64
     for (int c = warp; c < K; c += 8)
@@ -62,38 +98,38 @@ __global__ void __launch_bounds__(256) k_qrcp(const BlkRec *__restrict__ blks, c
             double a = Wb[(int64_t)c * ld + i];
             s = fma(a, a, s);
         }
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
         if (lane == 0) {
-            cn[c] = sqrt(s);
-            cn0[c] = cn[c];
+            cn2[c] = s;
+            thr[c] = tol3z * s;
             perm[c] = c;
         }
     }
     __syncthreads();
 
     const int steps = m < K ? m : K;
-    const double tol3z = sqrt(2.220446049250313e-16);
     double R11 = 0.0;
     int rank = steps;
     for (int k = 0; k < steps; ++k) {
         // 1. pivot
-        double bv = -1.0;
-        int bp = 0x7fffffff, bc = k;
-        for (int c = k + tid; c < K; c += 256)
-            if (better(cn[c], perm[c], bv, bp)) { bv = cn[c]; bp = perm[c]; bc = c; }
-        for (int o = 16; o; o >>= 1) {
-            double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
-            int p2 = __shfl_xor_sync(0xffffffffu, bp, o);
-            int c2 = __shfl_xor_sync(0xffffffffu, bc, o);
-            if (better(v2, p2, bv, bp)) { bv = v2; bp = p2; bc = c2; }
+        long long bk = -1;
+        int bo = INT_MAX, bc = k;
+        for (int c = k + tid; c < K; c += 256) {
+            const long long kc = norm_key(cn2[c]);
+            if (key_better(kc, perm[c], bk, bo)) { bk = kc; bo = perm[c]; bc = c; }
         }
-        if (lane == 0) { red_v[warp] = bv; red_p[warp] = bp; red_c[warp] = bc; }
+        for (int o = 16; o; o >>= 1) {
+            const long long k2 = __shfl_xor_sync(kFull, bk, o);
+            const int o2 = __shfl_xor_sync(kFull, bo, o), c2 = __shfl_xor_sync(kFull, bc, o);
+            if (key_better(k2, o2, bk, bo)) { bk = k2; bo = o2; bc = c2; }
+        }
+        if (lane == 0) { red_k[warp] = bk; red_o[warp] = bo; red_c[warp] = bc; }
         __syncthreads();
         if (tid == 0) {
-            double v = red_v[0];
-            int p = red_p[0], c = red_c[0];
+            long long v = red_k[0];
+            int o = red_o[0], c = red_c[0];
             for (int w = 1; w < 8; ++w)
-                if (better(red_v[w], red_p[w], v, p)) { v = red_v[w]; p = red_p[w]; c = red_c[w]; }
+                if (key_better(red_k[w], red_o[w], v, o)) { v = red_k[w]; o = red_o[w]; c = red_c[w]; }
             s_piv = c;
         }
         __syncthreads();
@@ -105,74 +141,69 @@ __global__ void __launch_bounds__(256) k_qrcp(const BlkRec *__restrict__ blks, c
                 Wb[(int64_t)piv * ld + i] = a;
             }
             if (tid == 0) {
-                double t = cn[k]; cn[k] = cn[piv]; cn[piv] = t;
-                t = cn0[k]; cn0[k] = cn0[piv]; cn0[piv] = t;
+                double t = cn2[k]; cn2[k] = cn2[piv]; cn2[piv] = t;
+                t = thr[k]; thr[k] = thr[piv]; thr[piv] = t;
                 int q = perm[k]; perm[k] = perm[piv]; perm[piv] = q;
             }
         }
         __syncthreads();
-        // 2. exact norm of the pivot column below the diagonal
+        // 2. exact norm of the pivot column below the diagonal, reflector scalars
         double s = 0.0;
         for (int i = k + tid; i < m; i += 256) {
             double a = Wb[(int64_t)k * ld + i];
             s = fma(a, a, s);
         }
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) red_v[warp] = s;
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+        if (lane == 0) s_red[warp] = s;
         __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int w = 0; w < 8; ++w) t += red_v[w];
-            s_nx = sqrt(t);
+        if (warp == 0) {
+            double t = lane < 8 ? s_red[lane] : 0.0;
+            for (int o = 4; o; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+            if (lane == 0) {
+                const double nx = sqrt(t);
+                s_h[0] = nx;
+                if (nx > 0.0) house_scalars(Wb[(int64_t)k * ld + k], nx, s_h);
+            }
         }
         __syncthreads();
-        const double nx = s_nx;
+        const double nx = s_h[0];
         if (k == 0) R11 = nx;
         if (nx == 0.0 || nx < tol * R11) { rank = k; break; }
-        // 3. reflector
-        const double alpha = Wb[(int64_t)k * ld + k];
-        const double beta = alpha >= 0.0 ? -nx : nx;
-        const double scale = 1.0 / (alpha - beta);
-        const double tk = (beta - alpha) / beta;
-        for (int i = k + 1 + tid; i < m; i += 256) Wb[(int64_t)k * ld + i] *= scale;
-        __syncthreads();
-        if (tid == 0) {
-            Wb[(int64_t)k * ld + k] = beta;
-            tau[B.coff + k] = tk;
-        }
-        // 4. trailing update and norm downdate, one warp per column
-        const double *v = Wb + (int64_t)k * ld;
+        const double sc = s_h[2], tk = s_h[3], g = s_h[4];
+        // 3./4. trailing update with the unscaled pivot column, norm downdate
+        const double *x = Wb + (int64_t)k * ld;
         for (int c = k + 1 + warp; c < K; c += 8) {
             double *a = Wb + (int64_t)c * ld;
-            double d = 0.0;
-            for (int i = k + 1 + lane; i < m; i += 32) d = fma(v[i], a[i], d);
-            for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            double dot = 0.0;
+            for (int i = k + 1 + lane; i < m; i += 32) dot = fma(x[i], a[i], dot);
+            for (int o = 16; o; o >>= 1) dot += __shfl_xor_sync(kFull, dot, o);
             const double akc = a[k];
-            d = tk * (akc + d);
-            for (int i = k + 1 + lane; i < m; i += 32) a[i] = fma(-d, v[i], a[i]);
+            const double d = fma(g, dot, tk * akc);
+            const double e = d * sc;
+            for (int i = k + 1 + lane; i < m; i += 32) a[i] = fma(-e, x[i], a[i]);
             const double rkc = akc - d;
             __syncwarp();
-            if (lane == 0) a[k] = rkc;
-            double cc = cn[c];
-            int recompute = 0;
-            if (cc != 0.0) {
-                double t = fabs(rkc) / cc;
-                t = (1.0 + t) * (1.0 - t);
-                t = t < 0.0 ? 0.0 : t;
-                double r = cc / cn0[c];
-                if (t * r * r <= tol3z) recompute = 1;
-                else cc = cc * sqrt(t);
+            double c2;
+            const bool again = downdate(cn2[c], thr[c], rkc, &c2);
+            if (again) {
+                double q = 0.0;
+                for (int i = k + 1 + lane; i < m; i += 32) q = fma(a[i], a[i], q);
+                for (int o = 16; o; o >>= 1) q += __shfl_xor_sync(kFull, q, o);
+                c2 = q;
             }
-            if (recompute) {
-                double e = 0.0;
-                for (int i = k + 1 + lane; i < m; i += 32) e = fma(a[i], a[i], e);
-                for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-                cc = sqrt(e);
-                if (lane == 0) cn0[c] = cc;
+            if (lane == 0) {
+                a[k] = rkc;
+                cn2[c] = c2;
+                if (again) thr[c] = tol3z * c2;
             }
-            if (lane == 0) cn[c] = cc;
         }
         __syncthreads();
+        // v = x / (alpha - beta) below the diagonal, beta on it
+        for (int i = k + 1 + tid; i < m; i += 256) Wb[(int64_t)k * ld + i] *= sc;
+        if (tid == 0) {
+            Wb[(int64_t)k * ld + k] = s_h[1];
+            tau[B.coff + k] = tk;
+        }
     }
     if (tid == 0) {
         rank_out[blockIdx.x] = rank;
@@ -241,25 +272,30 @@ namespace rfm {
 // CTAs (thread-block cluster, distributed shared memory), distributed by
 // columns: original column c belongs to CTA c mod C, slot c / C, and never
 // moves.  Pivoting retires the chosen column in place and records its
-// position.  One cluster barrier per step:
-//   - each CTA publishes its best non-retired column (trailing norm, original
-//     index), double-buffered by step parity;
-//   - after the barrier one warp reads the C candidates through DSMEM and
-//     every CTA takes the same winner;
-//   - every CTA copies the winner's column (rows k..m) through DSMEM, forms
-//     the same reflector from it (same data, same order: bit-identical), and
-//     updates its own non-retired columns;
-//   - the owner writes beta and v into the retired column after the next
-//     barrier, when no CTA can still be reading it.
-// No global memory traffic inside the factorisation.  Q_hat (when wanted) is
-// then accumulated backwards in the same shared memory, each CTA on its own
-// columns, prefetching the next reflector from global memory.
+// position.  One cluster barrier and two CTA barriers per step:
+//   - every warp, right after updating its trailing columns, pushes its best
+//     one (squared norm as an integer key, original index) into a slot of
+//     every CTA of the cluster (double-buffered by step parity);
+//   - after the cluster barrier every warp reduces the C x 8 candidates in
+//     its own shared memory and takes the same winner;
+//   - every CTA copies the winner's column (rows k..m) through DSMEM and sums
+//     its squares; one warp forms the reflector scalars (same data, same
+//     order in every CTA: bit-identical), and every warp updates its own
+//     trailing columns, two at a time (the two dot products reduce-scattered
+//     in one shuffle tree), with the unscaled pivot column, downdating each
+//     column's squared norm on the spot;
+//   - the owner writes beta and the scaled v into the retired column after
+//     the next cluster barrier, when no CTA can still be reading it.
+// The arithmetic is that of k_qrcp step for step, so both kernels return the
+// same factors.  No global memory traffic inside the factorisation.  Q_hat
+// (when wanted) is then accumulated backwards in the same shared memory,
+// each CTA on its own columns, prefetching the next reflector from global
+// memory.
 // ---------------------------------------------------------------------------
 namespace cg = cooperative_groups;
 
-struct Cand {
-    double v;
-    int p, slot;
+struct __align__(16) Cand {
+    long long key, orig;
 };
 
 constexpr int kQT = 256;          // threads of a cluster-QR CTA (measured: 512 was slower on the 2D workload)
@@ -278,25 +314,34 @@ __global__ void __launch_bounds__(kQT) k_qrcp_cluster(const BlkRec *__restrict__
     const int m = B.m, K = B.K, ld = B.ldm;
     extern __shared__ __align__(16) double sm[];
     double *A = sm;                                  // nloc_max x ld_loc
-    double *vbuf = A + (size_t)nloc_max * ld_loc;     // ld_loc
-    double *vbuf2 = vbuf + ld_loc;                   // ld_loc (Q prefetch)
-    double *cn = vbuf2 + ld_loc;                     // nloc_max
-    double *cn0 = cn + nloc_max;                     // nloc_max
-    double *rk = cn0 + nloc_max;                     // nloc_max: R(k, c) of the step, for the norm downdate
-    int *pos = (int *)(rk + nloc_max);               // nloc_max: position of the column, -1 while trailing
-    int *redo = pos + nloc_max;                      // nloc_max: exact norm needed
-    int *lives = redo + nloc_max;                    // nloc_max: slots of the trailing columns (any order)
+    double *vbuf = A + (size_t)nloc_max * ld_loc;     // ld_loc: pivot column of even steps (later: Q prefetch)
+    double *vbuf2 = vbuf + ld_loc;                   // ld_loc: pivot column of odd steps
+    double *cn2 = vbuf2 + ld_loc;                    // nloc_max: squared trailing norms
+    double *thr = cn2 + nloc_max;                    // nloc_max: tol3z * last exact squared norm
+    int *pos = (int *)(thr + nloc_max);              // nloc_max: position of the column, -1 while trailing
+    int *lives = pos + nloc_max;                     // nloc_max: slots of the trailing columns (any order)
     int *where = lives + nloc_max;                   // nloc_max: index of a slot in lives
-    __shared__ Cand cand[2];
-    __shared__ Cand red[kQW];
-    __shared__ Cand s_win;
+    __shared__ Cand cands[2][C * kQW];
     __shared__ double s_red[kQW];
+    __shared__ double s_h[5];    // nx, beta, sc, tau, g of the step
     __shared__ int s_ndrop;
     __shared__ int s_nlive;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nloc = (K - cr + C - 1) / C;   // columns owned by this CTA
     double *Wb = W + B.moff;
+    const double tol3z = sqrt(2.220446049250313e-16);
 
+    // lanes 0..C-1 store the warp's candidate into the same slot of every CTA
+    auto push = [&](int par, long long key, int orig) {
+        if (lane < C) {
+            Cand *dst = cl.map_shared_rank(&cands[par][cr * kQW + warp], lane);
+            *reinterpret_cast<longlong2 *>(dst) = make_longlong2(key, (long long)orig);
+        }
+    };
+    cl.sync();   // every CTA of the cluster runs before any DSMEM access
+
+    long long bk = -1;
+    int bo = INT_MAX;
     for (int l = warp; l < nloc; l += kQW) {
         const int c = cr + C * l;
         const TM *src = M + B.moff + (int64_t)c * ld;
@@ -306,95 +351,50 @@ __global__ void __launch_bounds__(kQT) k_qrcp_cluster(const BlkRec *__restrict__
             A[(size_t)l * ld_loc + i] = a;
             s = fma(a, a, s);
         }
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
         if (lane == 0) {
-            cn[l] = sqrt(s);
-            cn0[l] = cn[l];
+            cn2[l] = s;
+            thr[l] = tol3z * s;
             pos[l] = -1;
             lives[l] = l;
             where[l] = l;
         }
+        if (key_better(norm_key(s), c, bk, bo)) { bk = norm_key(s); bo = c; }
     }
     if (tid == 0) s_nlive = nloc;
-    __syncthreads();
+    push(0, bk, bo);
     const int steps = m < K ? m : K;
-    const double tol3z = sqrt(2.220446049250313e-16);
     double R11 = 0.0;
     int rank = steps;
     int pend_slot = -1, pend_k = 0;   // owner's deferred write of the last reflector
-    double pend_beta = 0.0;
+    double pend_beta = 0.0, pend_sc = 0.0;
     for (int k = 0; k < steps; ++k) {
-        // 1. best non-retired column of this CTA
-        double bv = -1.0;
-        int bp = 0x7fffffff, bl = -1;
-        const int nlive = s_nlive;
-        for (int t = tid; t < nlive; t += kQT) {
-            const int l = lives[t];
-            if (better(cn[l], cr + C * l, bv, bp)) { bv = cn[l]; bp = cr + C * l; bl = l; }
-        }
-        for (int o = 16; o; o >>= 1) {
-            double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
-            int p2 = __shfl_xor_sync(0xffffffffu, bp, o);
-            int l2 = __shfl_xor_sync(0xffffffffu, bl, o);
-            if (better(v2, p2, bv, bp)) { bv = v2; bp = p2; bl = l2; }
-        }
-        if (lane == 0) red[warp] = Cand{bv, bp, bl};
-        __syncthreads();
-        if (tid == 0) {
-            Cand t = red[0];
-            for (int w = 1; w < kQW; ++w)
-                if (better(red[w].v, red[w].p, t.v, t.p)) t = red[w];
-            cand[k & 1] = t;
-        }
+        const int par = k & 1;
+        double *vb = par ? vbuf2 : vbuf;
         cl.sync();
-        // deferred write of the previous reflector into its (retired) column
+        // 1. winner over the cluster, in every warp
+        {
+            bk = -1;
+            bo = INT_MAX;
+            for (int t = lane; t < C * kQW; t += 32) {
+                const longlong2 cd = *reinterpret_cast<const longlong2 *>(&cands[par][t]);
+                if (key_better(cd.x, (int)cd.y, bk, bo)) { bk = cd.x; bo = (int)cd.y; }
+            }
+            for (int o = 16; o; o >>= 1) {
+                const long long k2 = __shfl_xor_sync(kFull, bk, o);
+                const int o2 = __shfl_xor_sync(kFull, bo, o);
+                if (key_better(k2, o2, bk, bo)) { bk = k2; bo = o2; }
+            }
+        }
+        const int own = bo % C, wsl = bo / C;   // owner CTA and its slot
+        // 2. deferred write of the previous reflector into its retired column
         if (pend_slot >= 0) {
+            const double *vp = par ? vbuf : vbuf2;
             double *x = A + (size_t)pend_slot * ld_loc;
-            for (int i = pend_k + 1 + tid; i < m; i += kQT) x[i] = vbuf[i];
+            for (int i = pend_k + 1 + tid; i < m; i += kQT) x[i] = vp[i] * pend_sc;
             if (tid == 0) x[pend_k] = pend_beta;
             pend_slot = -1;
         }
-        // 2. winner over the cluster
-        if (warp == 0) {
-            Cand t = Cand{-1.0, 0x7fffffff, -1};
-            int owner = 0;
-            if (lane < C) t = cl.map_shared_rank(&cand[k & 1], lane)[0];
-            int o = lane;
-            for (int sh = 16; sh; sh >>= 1) {
-                double v2 = __shfl_xor_sync(0xffffffffu, t.v, sh);
-                int p2 = __shfl_xor_sync(0xffffffffu, t.p, sh);
-                int l2 = __shfl_xor_sync(0xffffffffu, t.slot, sh);
-                int o2 = __shfl_xor_sync(0xffffffffu, o, sh);
-                if (better(v2, p2, t.v, t.p)) { t.v = v2; t.p = p2; t.slot = l2; o = o2; }
-            }
-            owner = o;
-            if (lane == 0) s_win = Cand{t.v, owner, t.slot};
-        }
-        __syncthreads();
-        const int own = s_win.p, wsl = s_win.slot;   // owner CTA and its slot
-        // 3. copy the pivot column (rows k..m) from its owner
-        {
-            const double *rx = cl.map_shared_rank(A, own) + (size_t)wsl * ld_loc;
-            for (int i = k + tid; i < m; i += kQT) vbuf[i] = rx[i];
-        }
-        __syncthreads();
-        // 4. exact norm and reflector (computed identically in every CTA)
-        double s = 0.0;
-        for (int i = k + tid; i < m; i += kQT) s = fma(vbuf[i], vbuf[i], s);
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) s_red[warp] = s;
-        __syncthreads();
-        double t2 = 0.0;
-        for (int w = 0; w < kQW; ++w) t2 += s_red[w];
-        const double nx = sqrt(t2);
-        if (k == 0) R11 = nx;
-        if (nx == 0.0 || nx < tol * R11) { rank = k; break; }
-        const double alpha = vbuf[k];
-        const double beta = alpha >= 0.0 ? -nx : nx;
-        const double scale = 1.0 / (alpha - beta);
-        const double tk = (beta - alpha) / beta;
-        __syncthreads();
-        for (int i = k + 1 + tid; i < m; i += kQT) vbuf[i] *= scale;
         if (cr == own && tid == 0) {
             pos[wsl] = k;
             // retire the pivot slot from the trailing list (swap with the last)
@@ -403,87 +403,108 @@ __global__ void __launch_bounds__(kQT) k_qrcp_cluster(const BlkRec *__restrict__
             where[last] = at;
             s_nlive -= 1;
         }
+        // 3. copy the pivot column (rows k..m) from its owner, sum of squares
+        {
+            const double *rx = cl.map_shared_rank(A, own) + (size_t)wsl * ld_loc;
+            double s = 0.0;
+            for (int i = k + tid; i < m; i += kQT) {
+                const double x = rx[i];
+                vb[i] = x;
+                s = fma(x, x, s);
+            }
+            for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+            if (lane == 0) s_red[warp] = s;
+        }
+        __syncthreads();
+        // 4. exact norm and reflector scalars (one warp)
+        if (warp == 0) {
+            double t = lane < kQW ? s_red[lane] : 0.0;
+            for (int o = kQW / 2; o; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+            if (lane == 0) {
+                const double nx = sqrt(t);
+                s_h[0] = nx;
+                if (nx > 0.0) house_scalars(vb[k], nx, s_h);
+            }
+        }
+        __syncthreads();
+        const double nx = s_h[0];
+        if (k == 0) R11 = nx;
+        if (nx == 0.0 || nx < tol * R11) {
+            rank = k;
+            if (cr == own && tid == 0) pos[wsl] = -1;   // not kept after all
+            break;
+        }
+        const double sc = s_h[2], tk = s_h[3], g = s_h[4];
         if (cr == 0 && tid == 0) tau[B.coff + k] = tk;
-        __syncthreads();
-        if (cr == own) { pend_slot = wsl; pend_k = k; pend_beta = beta; }
-        // 5. update own trailing columns, two per warp at a time (independent
-        //    reductions overlap); R(k, c) is kept for the downdate
+        if (cr == own) { pend_slot = wsl; pend_k = k; pend_beta = s_h[1]; pend_sc = sc; }
+        // 5. update own trailing columns, two per warp at a time; squared-norm
+        //    downdate (exact recompute when flagged); the warp's best candidate
         const int nl = s_nlive;
+        const bool hi = lane >= 16;
+        bk = -1;
+        bo = INT_MAX;
         for (int t = 2 * warp; t < nl; t += 2 * kQW) {
-            const int l = lives[t];
+            const int l1 = lives[t];
             const bool h2 = t + 1 < nl;
-            const int l2 = h2 ? lives[t + 1] : l;
-            const bool h1 = true;
-            double *a1 = A + (size_t)l * ld_loc;
+            const int l2 = h2 ? lives[t + 1] : l1;
+            double *a1 = A + (size_t)l1 * ld_loc;
             double *a2 = A + (size_t)l2 * ld_loc;
-            double d1 = 0.0, d2 = 0.0;
-            if (h2) {
+            double p1 = 0.0, p2 = 0.0;
+            for (int i = k + 1 + lane; i < m; i += 32) {
+                const double x = vb[i];
+                p1 = fma(x, a1[i], p1);
+                p2 = fma(x, a2[i], p2);
+            }
+            // lanes 0-15 end with column 1's dot product, lanes 16-31 with column 2's
+            double dot = (hi ? p2 : p1) + __shfl_xor_sync(kFull, hi ? p1 : p2, 16);
+            for (int o = 8; o; o >>= 1) dot += __shfl_xor_sync(kFull, dot, o);
+            const int lo = hi ? l2 : l1;
+            double *ao = hi ? a2 : a1;
+            const double akc = ao[k];
+            const double d = fma(g, dot, tk * akc);
+            const double e = d * sc;
+            const double rkc = akc - d;
+            const double e1 = __shfl_sync(kFull, e, 0), e2 = __shfl_sync(kFull, e, 16);
+            for (int i = k + 1 + lane; i < m; i += 32) {
+                const double x = vb[i];
+                a1[i] = fma(-e1, x, a1[i]);
+                if (h2) a2[i] = fma(-e2, x, a2[i]);
+            }
+            double c2;
+            const bool again = downdate(cn2[lo], thr[lo], rkc, &c2);
+            const bool ag1 = __shfl_sync(kFull, again, 0), ag2 = h2 && __shfl_sync(kFull, again, 16);
+            if (ag1 || ag2) {
+                double q1 = 0.0, q2 = 0.0;
                 for (int i = k + 1 + lane; i < m; i += 32) {
-                    const double v = vbuf[i];
-                    d1 = fma(v, a1[i], d1);
-                    d2 = fma(v, a2[i], d2);
+                    q1 = fma(a1[i], a1[i], q1);
+                    q2 = fma(a2[i], a2[i], q2);
                 }
-                for (int o = 16; o; o >>= 1) {
-                    d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-                    d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-                }
-            } else {
-                for (int i = k + 1 + lane; i < m; i += 32) d1 = fma(vbuf[i], a1[i], d1);
-                for (int o = 16; o; o >>= 1) d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+                double q = (hi ? q2 : q1) + __shfl_xor_sync(kFull, hi ? q1 : q2, 16);
+                for (int o = 8; o; o >>= 1) q += __shfl_xor_sync(kFull, q, o);
+                if (again) c2 = q;
             }
-            const double ak1 = a1[k], ak2 = a2[k];
-            d1 = tk * (ak1 + d1);
-            d2 = tk * (ak2 + d2);
-            if (h1)
-                for (int i = k + 1 + lane; i < m; i += 32) a1[i] = fma(-d1, vbuf[i], a1[i]);
-            if (h2)
-                for (int i = k + 1 + lane; i < m; i += 32) a2[i] = fma(-d2, vbuf[i], a2[i]);
             __syncwarp();
-            if (lane == 0) {
-                if (h1) { a1[k] = ak1 - d1; rk[l] = ak1 - d1; }
-                if (h2) { a2[k] = ak2 - d2; rk[l2] = ak2 - d2; }
+            if ((lane & 15) == 0 && (!hi || h2)) {
+                ao[k] = rkc;
+                cn2[lo] = c2;
+                if (again) thr[lo] = tol3z * c2;
             }
+            const double c21 = __shfl_sync(kFull, c2, 0), c22 = __shfl_sync(kFull, c2, 16);
+            const int o1 = cr + C * l1, o2 = cr + C * l2;
+            if (key_better(norm_key(c21), o1, bk, bo)) { bk = norm_key(c21); bo = o1; }
+            if (h2 && key_better(norm_key(c22), o2, bk, bo)) { bk = norm_key(c22); bo = o2; }
         }
-        __syncthreads();
-        // 6. norm downdate, one thread per column; columns whose downdate has
-        //    lost half the digits are marked for an exact recompute
-        for (int t = tid; t < nl; t += kQT) {
-            const int l = lives[t];
-            double cc = cn[l];
-            int again = 0;
-            if (cc != 0.0) {
-                double t = fabs(rk[l]) / cc;
-                t = (1.0 + t) * (1.0 - t);
-                t = t < 0.0 ? 0.0 : t;
-                const double rr = cc / cn0[l];
-                if (t * rr * rr <= tol3z) again = 1;
-                else cc = cc * sqrt(t);
-            }
-            cn[l] = cc;
-            redo[l] = again;
-        }
-        __syncthreads();
-        for (int t = warp; t < nl; t += kQW) {
-            const int l = lives[t];
-            if (!redo[l]) continue;
-            const double *a = A + (size_t)l * ld_loc;
-            double e = 0.0;
-            for (int i = k + 1 + lane; i < m; i += 32) e = fma(a[i], a[i], e);
-            for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-            if (lane == 0) {
-                cn[l] = sqrt(e);
-                cn0[l] = cn[l];
-            }
-        }
-        __syncthreads();
+        push(par ^ 1, bk, bo);
     }
     // every CTA has finished reading pivot columns; finish the last deferred write
     cl.sync();
     if (pend_slot >= 0) {
+        const double *vp = (pend_k & 1) ? vbuf2 : vbuf;
         double *x = A + (size_t)pend_slot * ld_loc;
-        for (int i = pend_k + 1 + tid; i < m; i += kQT) x[i] = vbuf[i];
+        for (int i = pend_k + 1 + tid; i < m; i += kQT) x[i] = vp[i] * pend_sc;
         if (tid == 0) x[pend_k] = pend_beta;
     }
+    __syncthreads();
     // positions of the dropped columns: rank + (dropped columns of lower CTAs) + local order
     if (tid == 0) {
         int nd = 0;
@@ -594,7 +615,7 @@ static rfm_status launch_cluster(const FilterBufs &F, double tol, int nloc, int 
 static size_t cluster_smem(int64_t max_m, int64_t max_K, int C, int *nloc, int *ldl) {
     *ldl = (int)((max_m + 1) / 2 * 2);
     *nloc = (int)((max_K + C - 1) / C);
-    return ((size_t)(*nloc) * (*ldl) + 2 * (size_t)(*ldl)) * 8 + (size_t)(*nloc) * 40 + 64;
+    return ((size_t)(*nloc) * (*ldl) + 2 * (size_t)(*ldl)) * 8 + (size_t)(*nloc) * 32 + 64;
 }
 
 template <typename TM>
