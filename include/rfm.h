@@ -182,7 +182,7 @@ typedef struct rfm_lsqr_report {
  * with zeros at dropped columns (Algorithm 2).
  *  d_y0     nullable warm start (n_cols doubles, per block the first r_j of
  *           each K-slot used); the iteration runs on the residual system.
- *  d_y      nullable output y (n_cols doubles, same layout).
+ *  d_y      nullable output y (n_cols doubles, same layout; 0 at dropped slots).
  *  d_a      output coefficients (n_cols doubles).
  *  d_report n_inst rfm_lsqr_report.
  * Stopping (per instance): ||r|| <= btol ||h|| + atol ||A||_F ||y||, or
@@ -352,8 +352,14 @@ int rfm_profile_read(const char **names, int64_t *launches, double *ms, int max)
  *    precision, block count) time every cluster size the blocks fit and keep
  *    the fastest for later calls in the process; that first call waits for
  *    its own timing runs (it synchronises the stream).  0 (default) takes the
- *    smallest cluster that holds the largest block. */
-enum { RFM_OPT_FILTER_KERNEL = 0, RFM_OPT_AUTOTUNE = 1 };
+ *    smallest cluster that holds the largest block.
+ *  RFM_OPT_QR_DOUBLE_FLOAT: 1 (default) factors FP32-assembled blocks in the
+ *    cluster kernel with double-float arithmetic (pairs of FP32 numbers, about
+ *    48 significant bits, on the FP32 pipe; the reflector scalars, norms fed
+ *    to the threshold test and R are formed in FP64) unless Q_hat is wanted in
+ *    FP64; 0 uses FP64 arithmetic for them too.  FP64-assembled blocks always
+ *    use FP64 arithmetic. */
+enum { RFM_OPT_FILTER_KERNEL = 0, RFM_OPT_AUTOTUNE = 1, RFM_OPT_QR_DOUBLE_FLOAT = 2 };
 rfm_status rfm_set_option(int option, int value);
 
 const char *rfm_last_error(void);

@@ -169,3 +169,9 @@ def set_autotune(on: bool):
     """Time every feasible QR cluster size on the first filter call of a block
     shape and keep the fastest (RFM_OPT_AUTOTUNE)."""
     check("rfm_set_option", load().rfm_set_option(1, 1 if on else 0))
+
+
+def set_qr_double_float(on: bool):
+    """Factor FP32-assembled blocks with double-float arithmetic (True, the
+    default) or with FP64 arithmetic (False) (RFM_OPT_QR_DOUBLE_FLOAT)."""
+    check("rfm_set_option", load().rfm_set_option(2, 1 if on else 0))

@@ -237,6 +237,33 @@ __device__ void reduce_partials(const double *part, int n_inst, double *out) {
     __syncthreads();
 }
 
+// Two reductions of per-CTA partials at once: warps 0-3 take the first
+// array's instances, warps 4-7 the second's (each sum in the order of
+// reduce_partials).
+__device__ void reduce_partials2(const double *pa, double *oa, const double *pb, double *ob, int n_inst) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, G = gridDim.x;
+    constexpr int half = kThreads / 64;
+    const double *part = warp < half ? pa : pb;
+    double *out = warp < half ? oa : ob;
+    for (int s = warp % half; s < n_inst; s += half) {
+        const double *p = part + (int64_t)s * G;
+        double x = 0.0;
+        for (int c0 = 0; c0 < G; c0 += 32 * 8) {
+            double v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int c = c0 + 32 * k + lane;
+                v[k] = c < G ? p[c] : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) x += v[k];
+        }
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) out[s] = x;
+    }
+    __syncthreads();
+}
+
 template <typename TA>
 struct Smem {
     double x[kMaxK];           // block column vector (v, p or z)
@@ -741,6 +768,7 @@ struct TileSmem {
     // per-instance factors formed once per phase (no division or square root
     // in per-element code: GB300's FP64 pipe is narrow)
     double inv_alpha[64], ab[64], bn[64], inv_bn[64];
+    int64_t wt0[65];              // first 32-row warp tile of each instance (row phase)
 };
 
 // Four rows of a column owned by one lane: FP32 one 16-byte load of rows
@@ -1011,9 +1039,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
     // block (chunks in block order, spread over every warp of the grid).  Each
     // lane keeps 2 x 8 sixteen-byte loads of the operator in flight, the 8
     // column sums are reduce-scattered in 9 shuffles so that lane 4t holds
-    // column t, and those lanes apply the FP64 update of vt at once (it
-    // overlaps the other warps' loads).  Per-instance sums ||vt||^2, ||y||^2
-    // stay lane-private until the instance changes.
+    // column t; the sums of 4 consecutive chunks of the warp are gathered one
+    // column per lane, and the FP64 update of vt runs on all 32 lanes at once
+    // (an FP64 warp instruction costs the same with 8 lanes or 32).  Per-
+    // instance sums ||vt||^2, ||y||^2 stay lane-private until the instance
+    // changes.
     const int64_t n_tu = *n_titems_p;
     auto tphase = [&](auto take, auto epi) {
         constexpr int VW = sizeof(TA) == 4 ? 4 : 2, STRIP = 32 * VW;
@@ -1031,81 +1061,175 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
             }
             pa = py = 0.0;
         };
-        const int mycol = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);   // for lane % 4 == 0
+        // the lane's batched column: sum, slot (-1: none), instance
+        TA zb = (TA)0;
+        int64_t ob = -1;
+        int ib = -1, nbat = 0;
+        auto run_batch = [&]() {
+            const bool valid = ob >= 0;
+            double ca = 0.0, cy = 0.0;
+            if (valid) epi(ib, ob, (double)zb, &ca, &cy);
+            const unsigned vm = __ballot_sync(0xffffffffu, valid);
+            if (vm) {
+                const int x = __shfl_sync(0xffffffffu, ib, __ffs(vm) - 1);
+                if (__all_sync(0xffffffffu, !valid || ib == x)) {
+                    if (x != cur_inst) {
+                        flush_lane();
+                        cur_inst = x;
+                    }
+                    pa += ca;
+                    py += cy;
+                } else {
+                    // columns of several instances: one warp sum per instance
+                    unsigned pend = vm;
+                    while (pend) {
+                        const int xi = __shfl_sync(0xffffffffu, ib, __ffs(pend) - 1);
+                        const bool mine = valid && ib == xi;
+                        double a2 = mine ? ca : 0.0, y2 = mine ? cy : 0.0;
+                        for (int o = 16; o; o >>= 1) {
+                            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+                            y2 += __shfl_xor_sync(0xffffffffu, y2, o);
+                        }
+                        if (lane == 0) {
+                            S.wacc[0][warp][xi] += a2;
+                            S.wacc[1][warp][xi] += y2;
+                        }
+                        pend &= ~__ballot_sync(0xffffffffu, mine);
+                    }
+                }
+            }
+            ob = -1;
+            nbat = 0;
+        };
         for (int64_t k = gwarp; k < n_tu; k += twarps) {
             const ColItem it = titems[k];
             if (!take(it.inst)) continue;
-            if (it.inst != cur_inst) {
-                flush_lane();
-                cur_inst = it.inst;
-            }
             const TA *ub = tu + it.roff;
-            for (int g0 = 0; g0 < it.nc; g0 += 8) {
-                const TA *base = Aop + it.moff + (int64_t)(it.c0 + g0) * it.ldm;
-                const int ng = min(8, it.nc - g0);
-                TA acc[8];
+            const TA *base = Aop + it.moff + (int64_t)it.c0 * it.ldm;
+            const int ng = min(8, it.nc);
+            TA acc[8];
 #pragma unroll
-                for (int c = 0; c < 8; ++c) acc[c] = (TA)0;
-                for (int i0 = 0; i0 < it.ldm; i0 += 2 * STRIP) {
-                    TA w[2][VW], q[8][2][VW];
+            for (int c = 0; c < 8; ++c) acc[c] = (TA)0;
+            for (int i0 = 0; i0 < it.ldm; i0 += 2 * STRIP) {
+                TA w[2][VW], q[8][2][VW];
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int i = i0 + STRIP * h + VW * lane;
-                        const bool in = i < it.ldm;
-                        if (sizeof(TA) == 4) {
-                            const float4 t = in ? *reinterpret_cast<const float4 *>(ub + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-                            w[h][0] = (TA)t.x; w[h][1 % VW] = (TA)t.y; w[h][2 % VW] = (TA)t.z; w[h][3 % VW] = (TA)t.w;
-                        } else {
-                            const double2 t = in ? *reinterpret_cast<const double2 *>(ub + i) : make_double2(0.0, 0.0);
-                            w[h][0] = (TA)t.x; w[h][1] = (TA)t.y;
-                        }
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            const bool ok = in && c < ng;
-                            const TA *src = base + (int64_t)c * it.ldm + (ok ? i : 0);
-                            if (sizeof(TA) == 4) {
-                                const float4 t = ok ? __ldg(reinterpret_cast<const float4 *>(src)) : make_float4(0.f, 0.f, 0.f, 0.f);
-                                q[c][h][0] = (TA)t.x; q[c][h][1 % VW] = (TA)t.y; q[c][h][2 % VW] = (TA)t.z; q[c][h][3 % VW] = (TA)t.w;
-                            } else {
-                                const double2 t = ok ? __ldg(reinterpret_cast<const double2 *>(src)) : make_double2(0.0, 0.0);
-                                q[c][h][0] = (TA)t.x; q[c][h][1] = (TA)t.y;
-                            }
-                        }
+                for (int h = 0; h < 2; ++h) {
+                    const int i = i0 + STRIP * h + VW * lane;
+                    const bool in = i < it.ldm;
+                    if (sizeof(TA) == 4) {
+                        const float4 t = in ? *reinterpret_cast<const float4 *>(ub + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        w[h][0] = (TA)t.x; w[h][1 % VW] = (TA)t.y; w[h][2 % VW] = (TA)t.z; w[h][3 % VW] = (TA)t.w;
+                    } else {
+                        const double2 t = in ? *reinterpret_cast<const double2 *>(ub + i) : make_double2(0.0, 0.0);
+                        w[h][0] = (TA)t.x; w[h][1] = (TA)t.y;
                     }
 #pragma unroll
-                    for (int h = 0; h < 2; ++h)
+                    for (int c = 0; c < 8; ++c) {
+                        const bool ok = in && c < ng;
+                        const TA *src = base + (int64_t)c * it.ldm + (ok ? i : 0);
+                        if (sizeof(TA) == 4) {
+                            const float4 t = ok ? __ldg(reinterpret_cast<const float4 *>(src)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                            q[c][h][0] = (TA)t.x; q[c][h][1 % VW] = (TA)t.y; q[c][h][2 % VW] = (TA)t.z; q[c][h][3 % VW] = (TA)t.w;
+                        } else {
+                            const double2 t = ok ? __ldg(reinterpret_cast<const double2 *>(src)) : make_double2(0.0, 0.0);
+                            q[c][h][0] = (TA)t.x; q[c][h][1] = (TA)t.y;
+                        }
+                    }
+                }
 #pragma unroll
-                        for (int c = 0; c < 8; ++c)
+                for (int h = 0; h < 2; ++h)
 #pragma unroll
-                            for (int v = 0; v < VW; ++v) acc[c] += q[c][h][v] * w[h][v];
-                }
-                // reduce-scatter: lane 4t ends with the full sum of column t
+                    for (int c = 0; c < 8; ++c)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const bool hi = lane & 16;
-                    const TA send = hi ? acc[j] : acc[j + 4], keep = hi ? acc[j + 4] : acc[j];
-                    acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-                }
+                        for (int v = 0; v < VW; ++v) acc[c] += q[c][h][v] * w[h][v];
+            }
+            // reduce-scatter: lane 4t ends with the full sum of column t
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const bool hi = lane & 8;
-                    const TA send = hi ? acc[j] : acc[j + 2], keep = hi ? acc[j + 2] : acc[j];
-                    acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+            for (int j = 0; j < 4; ++j) {
+                const bool hi = lane & 16;
+                const TA send = hi ? acc[j] : acc[j + 4], keep = hi ? acc[j + 4] : acc[j];
+                acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const bool hi = lane & 8;
+                const TA send = hi ? acc[j] : acc[j + 2], keep = hi ? acc[j + 2] : acc[j];
+                acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+            }
+            {
+                const bool hi = lane & 4;
+                const TA send = hi ? acc[0] : acc[1], keep = hi ? acc[1] : acc[0];
+                acc[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+            }
+            acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 2);
+            acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+            // column t (lane 4t) -> lane 8 nbat + t
+            const TA zt = __shfl_sync(0xffffffffu, acc[0], 4 * (lane & 7));
+            if ((lane >> 3) == nbat) {
+                zb = zt;
+                ob = (lane & 7) < ng ? it.coff + it.c0 + (lane & 7) : -1;
+                ib = it.inst;
+            }
+            if (++nbat == 4) run_batch();
+        }
+        run_batch();
+        flush_lane();
+    };
+
+    // rows (R): 32-row warp tiles (a tile never spans two instances), two
+    // tiles per warp per pass with their loads issued together; u~ of a row
+    // = fn(inst, sum of its block partials, old u~), stored to u and to the
+    // row's block-row copies; per-warp, per-instance sums of u~^2 in wacc[0]
+    auto row_phase = [&](auto take, auto fn) {
+        const int64_t n_wt = S.wt0[ni];
+        for (int64_t T0 = gwarp; T0 < n_wt; T0 += 2 * twarps) {
+            int si[2], Ci[2];
+            bool tv[2], rv[2];
+            int64_t gr[2];
+            const int32_t *lst[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int64_t T = T0 + (int64_t)j * twarps;
+                int sx = 0;
+                if (T < n_wt)
+                    while (S.wt0[sx + 1] <= T) ++sx;
+                si[j] = sx;
+                tv[j] = T < n_wt && take(sx);
+                const InstRec &I = a.insts[sx];
+                const int64_t r = (T - S.wt0[sx]) * 32 + lane;
+                rv[j] = tv[j] && r < I.N;
+                Ci[j] = I.C;
+                gr[j] = I.row0 + (rv[j] ? r : 0);
+                lst[j] = a.rowlist + I.rl_off + (rv[j] ? r : 0) * I.C;
+            }
+            double acc[2] = {0.0, 0.0}, uo[2];
+            const int Cm = Ci[0] > Ci[1] ? Ci[0] : Ci[1];
+            for (int e = 0; e < Cm; ++e) {
+                const int q0 = rv[0] && e < Ci[0] ? lst[0][e] : -1;
+                const int q1 = rv[1] && e < Ci[1] ? lst[1][e] : -1;
+                if (q0 >= 0) acc[0] += row_partials(q0);
+                if (q1 >= 0) acc[1] += row_partials(q1);
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) uo[j] = rv[j] ? a.u[gr[j]] : 0.0;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                if (!tv[j]) continue;    // warp-uniform
+                double uu = 0.0;
+                if (rv[j]) {
+                    const double uv = fn(si[j], acc[j], uo[j]);
+                    a.u[gr[j]] = uv;
+                    const TA ut = (TA)uv;
+                    for (int e = 0; e < Ci[j]; ++e) {
+                        const int q = lst[j][e];
+                        if (q >= 0) tu[q] = ut;
+                    }
+                    uu = uv * uv;
                 }
-                {
-                    const bool hi = lane & 4;
-                    const TA send = hi ? acc[0] : acc[1], keep = hi ? acc[1] : acc[0];
-                    acc[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-                }
-                acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 2);
-                acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
-                if ((lane & 3) == 0 && mycol < ng) {
-                    const int64_t o = it.coff + it.c0 + g0 + mycol;
-                    epi(it.inst, o, (double)acc[0], &pa, &py);
-                }
+                for (int o = 16; o; o >>= 1) uu += __shfl_xor_sync(0xffffffffu, uu, o);
+                if (lane == 0) S.wacc[0][warp][si[j]] += uu;
             }
         }
-        flush_lane();
     };
 
     // elementwise over the kept column slots
@@ -1137,6 +1261,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
         LsqrScal z;
         memset(&z, 0, sizeof(z));
         sc[s] = z;
+    }
+    if (tid == 0) {
+        int64_t t0 = 0;
+        for (int s = 0; s < ni; ++s) {
+            S.wt0[s] = t0;
+            t0 += (a.insts[s].N + 31) / 32;
+        }
+        S.wt0[ni] = t0;
     }
     __syncthreads();
     each_column(all_inst, [&](int inst, int64_t o) {
@@ -1258,37 +1390,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
         mark(0);
         if (!ok) break;
         // R: u~ = sum of the block partials - (alpha/beta) u~
-        clear(S.acc_b);
+        clear_w();
         __syncthreads();
-        for (int64_t T = cta; T < a.n_row_tiles; T += G) {
-            int64_t tc;
-            const int s = row_tile_inst(T, &tc);
-            const LsqrScal &q = sc[s];
-            if (q.done) continue;
-            const InstRec &I = a.insts[s];
-            const int64_t r = (T - tc) * kRowTile + tid;
-            double uu = 0.0;
-            if (r < I.N) {
-                const int64_t gr = I.row0 + r;
-                const int32_t *lst = a.rowlist + I.rl_off + r * I.C;
-                double acc = 0.0;
-                for (int e = 0; e < I.C; ++e) {
-                    int qq = lst[e];
-                    if (qq >= 0) acc += row_partials(qq);
-                }
-                const double uv = fma(-S.ab[s], a.u[gr], acc);
-                a.u[gr] = uv;
-                for (int e = 0; e < I.C; ++e) {
-                    int qq = lst[e];
-                    if (qq >= 0) tu[qq] = (TA)uv;
-                }
-                uu = uv * uv;
-            }
-            double s1 = cta_sum(uu, S.wred[0]);
-            if (tid == 0) S.acc_b[s] += s1;
-        }
+        row_phase(live, [&](int s, double acc, double uo) { return fma(-S.ab[s], uo, acc); });
         __syncthreads();
-        flush(S.acc_b, 1);
+        flush_w(0, 1);
         ok = grid_sync(a.bar, a.timeout_ns);
         mark(1);
         if (!ok) break;
@@ -1317,8 +1423,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
         ok = grid_sync(a.bar, a.timeout_ns);
         mark(2);
         if (!ok) break;
-        reduce_partials(a.part + (int64_t)2 * ni * G, ni, S.tmp2);   // alpha_{n+1}^2
-        reduce_partials(a.part, ni, S.yy);                           // ||y_{n-1}||^2
+        reduce_partials2(a.part + (int64_t)2 * ni * G, S.tmp2, a.part, S.yy, ni);   // alpha_{n+1}^2, ||y_{n-1}||^2
         __shared__ int s_all_done;
         if (tid == 0) s_all_done = 1;
         __syncthreads();
@@ -1326,9 +1431,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
             LsqrScal &q = sc[s];
             if (q.done) continue;
             if (!first) {
+                // (two square roots and two divisions per iteration: GB300's
+                // FP64 pipe makes each one a long serial latency)
                 q.ynorm = sqrt(S.yy[s]);
-                if (q.rnorm <= a.btol * q.bnorm + a.atol * sqrt(q.anorm2) * q.ynorm) { q.done = 1; q.istop = 1; }
-                else if (q.arnorm <= a.atol * sqrt(q.anorm2) * q.rnorm) { q.done = 1; q.istop = 2; }
+                const double anorm = sqrt(q.anorm2);
+                if (q.rnorm <= a.btol * q.bnorm + a.atol * anorm * q.ynorm) { q.done = 1; q.istop = 1; }
+                else if (q.arnorm <= a.atol * anorm * q.rnorm) { q.done = 1; q.istop = 2; }
                 else if (n - 1 >= a.max_iter) { q.done = 1; q.istop = 7; }
             } else if (a.max_iter == 0) {
                 q.done = 1;
@@ -1336,25 +1444,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
             }
             if (q.done) continue;
             q.itn = n;
-            const double beta = sqrt(S.tmp[s]);
+            const double beta = S.bn[s];
             const double alpha = sqrt(S.tmp2[s]);
             q.anorm2 += q.alpha * q.alpha + beta * beta;
             const double rho = sqrt(q.rhobar * q.rhobar + beta * beta);
-            const double c = rho > 0.0 ? q.rhobar / rho : 1.0;
-            const double sn = rho > 0.0 ? beta / rho : 0.0;
+            const double rinv = rho > 0.0 ? 1.0 / rho : 0.0;
+            const double c = rho > 0.0 ? q.rhobar * rinv : 1.0;
+            const double sn = beta * rinv;
             const double theta = sn * alpha;
             q.rhobar = -c * alpha;
             const double phi = c * q.phibar;
             q.phibar = sn * q.phibar;
-            q.phi_rho = rho > 0.0 ? phi / rho : 0.0;
-            q.theta_rho = rho > 0.0 ? theta / rho : 0.0;
+            q.phi_rho = phi * rinv;
+            q.theta_rho = theta * rinv;
             q.rnorm = q.phibar;
             q.arnorm = q.phibar * alpha * fabs(c);
             q.c = c;
             q.alpha = alpha;
             q.beta = beta;
             S.inv_alpha[s] = alpha > 0.0 ? 1.0 / alpha : 0.0;
-            S.ab[s] = beta > 0.0 ? alpha / beta : 0.0;
+            S.ab[s] = alpha * S.inv_bn[s];
             if (!isfinite(q.phibar) || !isfinite(q.rhobar) || !isfinite(q.phi_rho) || !isfinite(q.anorm2)) {
                 q.done = 1;
                 q.status = RFM_ENUMERIC;
@@ -1499,6 +1608,7 @@ rfm_status launch_lsqr(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, c
     LsqrArgs A;
     fill_args(P, ws, opts, y0, A);
     RFM_CUDA_CHECK(cudaMemsetAsync(A.bar, 0, 256, st));
+    RFM_CUDA_CHECK(cudaMemsetAsync(A.y, 0, sizeof(double) * L.n_cols, st));   // dropped slots of y read back as 0
     rfm_status rc;
     if (L.op == RFM_OP_Q32) {
         A.A = ws_ptr<float>(ws, L.off_q32);

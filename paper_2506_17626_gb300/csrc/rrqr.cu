@@ -28,6 +28,7 @@
 #include <mutex>
 #include <vector>
 
+#include "df.cuh"
 #include "device.cuh"
 #include "prof.cuh"
 
@@ -589,6 +590,359 @@ __global__ void __launch_bounds__(kQT) k_qrcp_cluster(const BlkRec *__restrict__
     }
 }
 
+// ---------------------------------------------------------------------------
+// Double-float variant of the cluster kernel, for blocks assembled in FP32
+// (their entries are exact double-floats with a zero low word).  Same
+// algorithm, data distribution and step structure; the block, the pivot
+// column and the trailing squared norms are double-float pairs in shared
+// memory, and every per-element operation (dot products, column updates,
+// squared norms) and the per-column scalars run on the FP32 pipe.  The
+// reflector scalars of a step (norm, beta, tau) are formed once in FP64 from
+// the double-float sums.  Pivots compare the high words of the squared
+// norms.  The factorisation leaves R and the reflectors in W (FP64) and, for
+// Q_hat, double-float copies of the reflectors in the scratch arena Vdf, from
+// which Q_hat = H_0 ... H_{r-1} [I_r; 0] is accumulated backwards in
+// double-float and rounded to FP32.
+// ---------------------------------------------------------------------------
+constexpr int kDT = 512;          // threads of a double-float cluster-QR CTA (its FP32 dependency chains want more warps)
+constexpr int kDW = kDT / 32;
+
+template <int C>
+__global__ void __launch_bounds__(kDT) k_qrcp_cluster_df(const BlkRec *__restrict__ blks, const float *__restrict__ M,
+                                                         double *__restrict__ W, double *__restrict__ tau,
+                                                         int32_t *__restrict__ perm_out, int32_t *__restrict__ rank_out,
+                                                         double *__restrict__ r11_out, double tol, int nloc_max,
+                                                         int ld_loc, int k_max, float2 *__restrict__ Vdf,
+                                                         float *__restrict__ Q32) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int cr = (int)cl.block_rank();
+    const int b = blockIdx.x / C;
+    const BlkRec B = blks[b];
+    const int m = B.m, K = B.K, ld = B.ldm;
+    extern __shared__ __align__(16) float2 smf[];
+    float2 *A = smf;                                        // nloc_max x ld_loc
+    float2 *vbuf = A + (size_t)nloc_max * ld_loc;           // ld_loc: pivot column of even steps (later: Q prefetch)
+    float2 *vbuf2 = vbuf + ld_loc;                          // ld_loc: pivot column of odd steps
+    float2 *taud = vbuf2 + ld_loc;                          // k_max: tau of every step
+    float2 *cn2 = taud + k_max;                             // nloc_max: squared trailing norms
+    float *thr = reinterpret_cast<float *>(cn2 + nloc_max);  // nloc_max: tol3z * last exact squared norm
+    int *pos = reinterpret_cast<int *>(thr + nloc_max);     // nloc_max: position, -1 while trailing
+    int *lives = pos + nloc_max;                            // nloc_max: slots of the trailing columns
+    int *where = lives + nloc_max;                          // nloc_max: index of a slot in lives
+    __shared__ Cand cands[2][C * kDW];
+    __shared__ float2 s_red[kDW];
+    __shared__ double s_nx, s_tau;
+    __shared__ float2 s_h[3];    // beta, sc, g of the step (tau goes to taud)
+    __shared__ int s_ndrop;
+    __shared__ int s_nlive;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nloc = (K - cr + C - 1) / C;
+    double *Wb = W + B.moff;
+    const float tol3z = 1.4901161193847656e-08f;   // sqrt of the FP64 epsilon, as in the FP64 kernels
+    // pivot key of a normalised squared norm (h >= 0): the high word's bits,
+    // then the low word's bits mapped to an order-preserving unsigned
+    auto fkey = [](float2 c2) {
+        unsigned lo = __float_as_uint(c2.y);
+        lo = (lo & 0x80000000u) ? ~lo : (lo | 0x80000000u);
+        return ((long long)__float_as_int(c2.x) << 32) | (long long)lo;
+    };
+
+    auto push = [&](int par, long long key, int orig) {
+        if (lane < C) {
+            Cand *dst = cl.map_shared_rank(&cands[par][cr * kDW + warp], lane);
+            *reinterpret_cast<longlong2 *>(dst) = make_longlong2(key, (long long)orig);
+        }
+    };
+    cl.sync();
+
+    long long bk = -1;
+    int bo = INT_MAX;
+    for (int l = warp; l < nloc; l += kDW) {
+        const int c = cr + C * l;
+        const float *src = M + B.moff + (int64_t)c * ld;
+        float sh = 0.f, sl = 0.f;
+        for (int i = lane; i < m; i += 32) {
+            const float2 a = make_float2(src[i], 0.f);
+            A[(size_t)l * ld_loc + i] = a;
+            df_acc(a, a, sh, sl);
+        }
+        float2 s2 = make_float2(sh, sl);
+        for (int o = 16; o; o >>= 1) s2 = df_xor_add(s2, o);
+        if (lane == 0) {
+            cn2[l] = s2;
+            thr[l] = tol3z * s2.x;
+            pos[l] = -1;
+            lives[l] = l;
+            where[l] = l;
+        }
+        if (key_better(fkey(s2), c, bk, bo)) { bk = fkey(s2); bo = c; }
+    }
+    if (tid == 0) s_nlive = nloc;
+    push(0, bk, bo);
+    const int steps = m < K ? m : K;
+    double R11 = 0.0;
+    int rank = steps;
+    int pend_slot = -1, pend_k = 0;
+    float2 pend_beta = make_float2(0.f, 0.f), pend_sc = make_float2(0.f, 0.f);
+    for (int k = 0; k < steps; ++k) {
+        const int par = k & 1;
+        float2 *vb = par ? vbuf2 : vbuf;
+        cl.sync();
+        // 1. winner over the cluster, in every warp
+        {
+            bk = -1;
+            bo = INT_MAX;
+            for (int t = lane; t < C * kDW; t += 32) {
+                const longlong2 cd = *reinterpret_cast<const longlong2 *>(&cands[par][t]);
+                if (key_better(cd.x, (int)cd.y, bk, bo)) { bk = cd.x; bo = (int)cd.y; }
+            }
+            for (int o = 16; o; o >>= 1) {
+                const long long k2 = __shfl_xor_sync(kFull, bk, o);
+                const int o2 = __shfl_xor_sync(kFull, bo, o);
+                if (key_better(k2, o2, bk, bo)) { bk = k2; bo = o2; }
+            }
+        }
+        const int own = bo % C, wsl = bo / C;
+        // 2. deferred write of the previous reflector (v = x sc, beta on the diagonal)
+        if (pend_slot >= 0) {
+            const float2 *vp = par ? vbuf : vbuf2;
+            float2 *x = A + (size_t)pend_slot * ld_loc;
+            for (int i = pend_k + 1 + tid; i < m; i += kDT) x[i] = df_mul(vp[i], pend_sc);
+            if (tid == 0) x[pend_k] = pend_beta;
+            pend_slot = -1;
+        }
+        if (cr == own && tid == 0) {
+            pos[wsl] = k;
+            const int at = where[wsl], last = lives[s_nlive - 1];
+            lives[at] = last;
+            where[last] = at;
+            s_nlive -= 1;
+        }
+        // 3. copy the pivot column (rows k..m) from its owner, sum of squares
+        {
+            const float2 *rx = cl.map_shared_rank(A, own) + (size_t)wsl * ld_loc;
+            float sh = 0.f, sl = 0.f;
+            for (int i = k + tid; i < m; i += kDT) {
+                const float2 x = rx[i];
+                vb[i] = x;
+                df_acc(x, x, sh, sl);
+            }
+            float2 s2 = make_float2(sh, sl);
+            for (int o = 16; o; o >>= 1) s2 = df_xor_add(s2, o);
+            if (lane == 0) s_red[warp] = s2;
+        }
+        __syncthreads();
+        // 4. exact norm and reflector scalars (one warp), in double-float:
+        //    beta = -sign(alpha) nx, sc = 1 / (alpha - beta), g = -1 / beta,
+        //    tau = (alpha - beta) g, from one reciprocal (as house_scalars)
+        if (warp == 0) {
+            float2 t = lane < kDW ? s_red[lane] : make_float2(0.f, 0.f);
+            for (int o = kDW / 2; o; o >>= 1) t = df_xor_add(t, o);
+            if (lane == 0) {
+                const float2 nxd = t.x > 0.f ? df_sqrt(t) : make_float2(0.f, 0.f);
+                s_nx = df_to_double(nxd);
+                if (nxd.x > 0.f) {
+                    const float2 alpha = vb[k];
+                    const float2 beta = alpha.x >= 0.f ? df_neg(nxd) : nxd;
+                    const float2 amb = df_sub(alpha, beta);
+                    const float2 inv = df_rcp(df_mul(amb, beta));
+                    const float2 g = df_neg(df_mul(amb, inv));
+                    const float2 tk = df_mul(amb, g);
+                    s_h[0] = beta;
+                    s_h[1] = df_mul(beta, inv);
+                    s_h[2] = g;
+                    taud[k] = tk;
+                    s_tau = df_to_double(tk);
+                }
+            }
+        }
+        __syncthreads();
+        const double nx = s_nx;
+        if (k == 0) R11 = nx;
+        if (nx == 0.0 || nx < tol * R11) {
+            rank = k;
+            if (cr == own && tid == 0) pos[wsl] = -1;
+            break;
+        }
+        const float2 sc = s_h[1], tk = taud[k], g = s_h[2];
+        if (cr == 0 && tid == 0) tau[B.coff + k] = s_tau;
+        if (cr == own) { pend_slot = wsl; pend_k = k; pend_beta = s_h[0]; pend_sc = sc; }
+        // 5. update own trailing columns, two per warp at a time
+        const int nl = s_nlive;
+        const bool hi = lane >= 16;
+        bk = -1;
+        bo = INT_MAX;
+        for (int t = 2 * warp; t < nl; t += 2 * kDW) {
+            const int l1 = lives[t];
+            const bool h2 = t + 1 < nl;
+            const int l2 = h2 ? lives[t + 1] : l1;
+            float2 *a1 = A + (size_t)l1 * ld_loc;
+            float2 *a2 = A + (size_t)l2 * ld_loc;
+            float p1h = 0.f, p1l = 0.f, p2h = 0.f, p2l = 0.f;
+            for (int i = k + 1 + lane; i < m; i += 32) {
+                const float2 x = vb[i];
+                df_acc(x, a1[i], p1h, p1l);
+                df_acc(x, a2[i], p2h, p2l);
+            }
+            // lanes 0-15 end with column 1's dot product, lanes 16-31 with column 2's
+            const float2 keep = hi ? make_float2(p2h, p2l) : make_float2(p1h, p1l);
+            const float2 send = hi ? make_float2(p1h, p1l) : make_float2(p2h, p2l);
+            float2 dot = df_add(keep, make_float2(__shfl_xor_sync(kFull, send.x, 16), __shfl_xor_sync(kFull, send.y, 16)));
+            for (int o = 8; o; o >>= 1) dot = df_xor_add(dot, o);
+            const int lo = hi ? l2 : l1;
+            float2 *ao = hi ? a2 : a1;
+            const float2 akc = ao[k];
+            const float2 d = df_add(df_mul(g, dot), df_mul(tk, akc));
+            const float2 e = df_mul(d, sc);
+            const float2 rkc = df_sub(akc, d);
+            const float2 e1 = make_float2(__shfl_sync(kFull, e.x, 0), __shfl_sync(kFull, e.y, 0));
+            const float2 e2 = make_float2(__shfl_sync(kFull, e.x, 16), __shfl_sync(kFull, e.y, 16));
+            for (int i = k + 1 + lane; i < m; i += 32) {
+                const float2 x = vb[i];
+                a1[i] = df_axmy(a1[i], e1, x);
+                if (h2) a2[i] = df_axmy(a2[i], e2, x);
+            }
+            const float2 c2o = cn2[lo];
+            float2 c2 = make_float2(0.f, 0.f);
+            bool again = false;
+            if (c2o.x != 0.f) {
+                c2 = df_sub(c2o, df_mul(rkc, rkc));
+                again = !(c2.x > thr[lo]);
+            }
+            const bool ag1 = __shfl_sync(kFull, again, 0), ag2 = h2 && __shfl_sync(kFull, again, 16);
+            if (ag1 || ag2) {
+                float q1h = 0.f, q1l = 0.f, q2h = 0.f, q2l = 0.f;
+                for (int i = k + 1 + lane; i < m; i += 32) {
+                    const float2 u1 = a1[i], u2 = a2[i];
+                    df_acc(u1, u1, q1h, q1l);
+                    df_acc(u2, u2, q2h, q2l);
+                }
+                const float2 qk = hi ? make_float2(q2h, q2l) : make_float2(q1h, q1l);
+                const float2 qs = hi ? make_float2(q1h, q1l) : make_float2(q2h, q2l);
+                float2 q = df_add(qk, make_float2(__shfl_xor_sync(kFull, qs.x, 16), __shfl_xor_sync(kFull, qs.y, 16)));
+                for (int o = 8; o; o >>= 1) q = df_xor_add(q, o);
+                if (again) c2 = q;
+            }
+            __syncwarp();
+            if ((lane & 15) == 0 && (!hi || h2)) {
+                ao[k] = rkc;
+                cn2[lo] = c2;
+                if (again) thr[lo] = tol3z * c2.x;
+            }
+            const long long k1 = fkey(make_float2(__shfl_sync(kFull, c2.x, 0), __shfl_sync(kFull, c2.y, 0)));
+            const long long k2 = fkey(make_float2(__shfl_sync(kFull, c2.x, 16), __shfl_sync(kFull, c2.y, 16)));
+            const int o1 = cr + C * l1, o2 = cr + C * l2;
+            if (key_better(k1, o1, bk, bo)) { bk = k1; bo = o1; }
+            if (h2 && key_better(k2, o2, bk, bo)) { bk = k2; bo = o2; }
+        }
+        push(par ^ 1, bk, bo);
+    }
+    cl.sync();
+    if (pend_slot >= 0) {
+        const float2 *vp = (pend_k & 1) ? vbuf2 : vbuf;
+        float2 *x = A + (size_t)pend_slot * ld_loc;
+        for (int i = pend_k + 1 + tid; i < m; i += kDT) x[i] = df_mul(vp[i], pend_sc);
+        if (tid == 0) x[pend_k] = pend_beta;
+    }
+    __syncthreads();
+    // positions of the dropped columns: rank + (dropped columns of lower CTAs) + local order
+    if (tid == 0) {
+        int nd = 0;
+        for (int l = 0; l < nloc; ++l) nd += pos[l] < 0;
+        s_ndrop = nd;
+    }
+    cl.sync();
+    if (tid == 0) {
+        int base = rank;
+        for (int r = 0; r < cr; ++r) base += *cl.map_shared_rank(&s_ndrop, r);
+        for (int l = 0; l < nloc; ++l)
+            if (pos[l] < 0) pos[l] = base++;
+    }
+    __syncthreads();
+    for (int l = warp; l < nloc; l += kDW) {
+        const int p = pos[l];
+        const float2 *src = A + (size_t)l * ld_loc;
+        for (int i = lane; i < m; i += 32) Wb[(int64_t)p * ld + i] = df_to_double(src[i]);
+        if (Vdf && p < rank)
+            for (int i = lane; i < m; i += 32) Vdf[B.moff + (int64_t)p * ld + i] = src[i];
+    }
+    for (int l = tid; l < nloc; l += kDT) perm_out[B.coff + pos[l]] = cr + C * l;
+    if (cr == 0 && tid == 0) {
+        rank_out[b] = rank;
+        r11_out[b] = R11;
+    }
+    cl.sync();   // reflectors in global memory; no DSMEM access after this point
+    if (!Q32 || !Vdf) return;
+    // Q_hat = H_0 ... H_{r-1} [I_r; 0], owned columns c < r (c mod C == cr),
+    // two columns per warp at a time
+    const int r = rank;
+    const int nq = (r - cr + C - 1) / C > 0 ? (r - cr + C - 1) / C : 0;
+    for (int l = warp; l < nq; l += kDW) {
+        const int c = cr + C * l;
+        for (int i = lane; i < m; i += 32) A[(size_t)l * ld_loc + i] = make_float2(i == c ? 1.f : 0.f, 0.f);
+    }
+    const float2 *Vb = Vdf + B.moff;
+    float2 *cur = vbuf, *nxt = vbuf2;
+    if (r > 0)
+        for (int i = r + tid; i < m; i += kDT) cur[i] = Vb[(int64_t)(r - 1) * ld + i];
+    __syncthreads();
+    const bool hi = lane >= 16;
+    for (int k = r - 1; k >= 0; --k) {
+        float2 pre[4];
+        if (k > 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = k + tid + kDT * j;
+                pre[j] = i < m ? Vb[(int64_t)(k - 1) * ld + i] : make_float2(0.f, 0.f);
+            }
+        }
+        const float2 tk = taud[k];
+        const int lq = (k - cr + C - 1) / C > 0 ? (k - cr + C - 1) / C : 0;
+        for (int t = lq + 2 * warp; t < nq; t += 2 * kDW) {
+            const bool h2 = t + 1 < nq;
+            float2 *q1 = A + (size_t)t * ld_loc;
+            float2 *q2 = A + (size_t)(h2 ? t + 1 : t) * ld_loc;
+            float p1h = 0.f, p1l = 0.f, p2h = 0.f, p2l = 0.f;
+            for (int i = k + 1 + lane; i < m; i += 32) {
+                const float2 v = cur[i];
+                df_acc(v, q1[i], p1h, p1l);
+                df_acc(v, q2[i], p2h, p2l);
+            }
+            const float2 keep = hi ? make_float2(p2h, p2l) : make_float2(p1h, p1l);
+            const float2 send = hi ? make_float2(p1h, p1l) : make_float2(p2h, p2l);
+            float2 dot = df_add(keep, make_float2(__shfl_xor_sync(kFull, send.x, 16), __shfl_xor_sync(kFull, send.y, 16)));
+            for (int o = 8; o; o >>= 1) dot = df_xor_add(dot, o);
+            float2 *qo = hi ? q2 : q1;
+            const float2 qk = qo[k];
+            const float2 d = df_mul(tk, df_add(qk, dot));
+            const float2 d1 = make_float2(__shfl_sync(kFull, d.x, 0), __shfl_sync(kFull, d.y, 0));
+            const float2 d2 = make_float2(__shfl_sync(kFull, d.x, 16), __shfl_sync(kFull, d.y, 16));
+            for (int i = k + 1 + lane; i < m; i += 32) {
+                const float2 v = cur[i];
+                q1[i] = df_axmy(q1[i], d1, v);
+                if (h2) q2[i] = df_axmy(q2[i], d2, v);
+            }
+            __syncwarp();
+            if ((lane & 15) == 0 && (!hi || h2)) qo[k] = df_sub(qk, d);
+        }
+        if (k > 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = k + tid + kDT * j;
+                if (i < m) nxt[i] = pre[j];
+            }
+            for (int i = k + tid + 4 * kDT; i < m; i += kDT) nxt[i] = Vb[(int64_t)(k - 1) * ld + i];
+        }
+        __syncthreads();
+        float2 *tt = cur; cur = nxt; nxt = tt;
+    }
+    for (int l = warp; l < nq; l += kDW) {
+        const int c = cr + C * l;
+        for (int i = lane; i < ld; i += 32)
+            Q32[B.moff + (int64_t)c * ld + i] = i < m ? df_to_float(A[(size_t)l * ld_loc + i]) : 0.f;
+    }
+}
+
 template <typename TM, int C>
 static rfm_status launch_cluster(const FilterBufs &F, double tol, int nloc, int ldl, size_t smem, cudaStream_t st) {
     auto kern = k_qrcp_cluster<TM, C>;
@@ -611,16 +965,60 @@ static rfm_status launch_cluster(const FilterBufs &F, double tol, int nloc, int 
     return RFM_OK;
 }
 
-// Shared-memory bytes of the cluster kernel for cluster size C.
-static size_t cluster_smem(int64_t max_m, int64_t max_K, int C, int *nloc, int *ldl) {
+// Shared-memory bytes of the cluster kernel for cluster size C (the
+// double-float kernel adds the tau of every step).
+static size_t cluster_smem(int64_t max_m, int64_t max_K, int C, int *nloc, int *ldl, bool df = false) {
     *ldl = (int)((max_m + 1) / 2 * 2);
     *nloc = (int)((max_K + C - 1) / C);
-    return ((size_t)(*nloc) * (*ldl) + 2 * (size_t)(*ldl)) * 8 + (size_t)(*nloc) * 32 + 64;
+    return ((size_t)(*nloc) * (*ldl) + 2 * (size_t)(*ldl) + (df ? (size_t)max_K : 0)) * 8 + (size_t)(*nloc) * 32 + 64;
+}
+
+// FP32-assembled blocks go to the double-float kernel unless Q_hat is wanted
+// in FP64 (RFM_OPT_QR_DOUBLE_FLOAT = 0 keeps them on the FP64 kernel).  Its
+// Q_hat path keeps double-float copies of the reflectors in the FP64
+// operator arena, which the FP32 operator leaves free.
+static int g_qr_df = 1;
+static bool use_df(const FilterBufs &F, int elem) {
+    return elem == 4 && g_qr_df && F.Q64 == nullptr && (F.Q32 == nullptr || F.Op != nullptr);
+}
+
+template <int C>
+static rfm_status launch_cluster_df(const FilterBufs &F, double tol, int nloc, int ldl, size_t smem,
+                                    cudaStream_t st) {
+    auto kern = k_qrcp_cluster_df<C>;
+    RFM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (C > 8) RFM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(F.n_blocks * C));
+    cfg.blockDim = dim3(kDT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    float2 *vdf = F.Q32 ? reinterpret_cast<float2 *>(F.Op) : nullptr;
+    RFM_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, F.blk, (const float *)F.M, F.W, F.tau, F.perm, F.rank, F.r11, tol,
+                                      nloc, ldl, (int)F.max_K, vdf, F.Q32));
+    return RFM_OK;
 }
 
 template <typename TM>
 static rfm_status launch_cluster_c(int C, const FilterBufs &F, double tol, cudaStream_t st) {
     int nloc = 0, ldl = 0;
+    if (use_df(F, (int)sizeof(TM))) {
+        const size_t smem = cluster_smem(F.max_m, F.max_K, C, &nloc, &ldl, true);
+        switch (C) {
+            case 1: return launch_cluster_df<1>(F, tol, nloc, ldl, smem, st);
+            case 2: return launch_cluster_df<2>(F, tol, nloc, ldl, smem, st);
+            case 4: return launch_cluster_df<4>(F, tol, nloc, ldl, smem, st);
+            case 8: return launch_cluster_df<8>(F, tol, nloc, ldl, smem, st);
+            default: return launch_cluster_df<16>(F, tol, nloc, ldl, smem, st);
+        }
+    }
     const size_t smem = cluster_smem(F.max_m, F.max_K, C, &nloc, &ldl);
     switch (C) {
         case 1: return launch_cluster<TM, 1>(F, tol, nloc, ldl, smem, st);
@@ -645,10 +1043,14 @@ struct TuneEntry {
 static std::mutex g_tune_mu;
 static std::vector<TuneEntry> g_tune;
 
+// kernel family of a launch: 2 = double-float, 4 / 8 = FP64 arithmetic on FP32 / FP64 blocks
+static int tune_kind(const FilterBufs &F, int elem) { return use_df(F, elem) ? 2 : elem; }
+
 static int cached_cluster(const FilterBufs &F, int elem) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (const TuneEntry &e : g_tune)
-        if (e.max_m == F.max_m && e.max_K == F.max_K && e.n_blocks == F.n_blocks && e.elem == elem) return e.C;
+        if (e.max_m == F.max_m && e.max_K == F.max_K && e.n_blocks == F.n_blocks && e.elem == tune_kind(F, elem))
+            return e.C;
     return 0;
 }
 
@@ -666,8 +1068,9 @@ static rfm_status autotune_cluster(const FilterBufs &F, double tol, int C_min, c
         if (C > 8) {
             int nclusters = 0;
             int nloc = 0, ldl = 0;
-            const size_t smem = cluster_smem(F.max_m, F.max_K, C, &nloc, &ldl);
-            auto kern = k_qrcp_cluster<TM, 16>;
+            const bool dfk = use_df(F, (int)sizeof(TM));
+            const size_t smem = cluster_smem(F.max_m, F.max_K, C, &nloc, &ldl, dfk);
+            const void *kern = dfk ? (const void *)k_qrcp_cluster_df<16> : (const void *)k_qrcp_cluster<TM, 16>;
             if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
                 cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
                 cudaGetLastError();
@@ -675,7 +1078,7 @@ static rfm_status autotune_cluster(const FilterBufs &F, double tol, int C_min, c
             }
             cudaLaunchConfig_t q = {};
             q.gridDim = dim3(16);
-            q.blockDim = dim3(kQT);
+            q.blockDim = dim3(dfk ? kDT : kQT);
             q.dynamicSmemBytes = smem;
             cudaLaunchAttribute at[1];
             at[0].id = cudaLaunchAttributeClusterDimension;
@@ -715,7 +1118,7 @@ static rfm_status autotune_cluster(const FilterBufs &F, double tol, int C_min, c
     cudaEventDestroy(e1);
     if (rc != RFM_OK) return rc;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune.push_back(TuneEntry{F.max_m, F.max_K, F.n_blocks, (int)sizeof(TM), *best});
+    g_tune.push_back(TuneEntry{F.max_m, F.max_K, F.n_blocks, tune_kind(F, (int)sizeof(TM)), *best});
     return RFM_OK;
 }
 
@@ -725,8 +1128,9 @@ static rfm_status launch_filter_t(const FilterBufs &F, double tol, cudaStream_t 
     const size_t kSmemCap = 220 * 1024;
     int C = 0, nloc = 0, ldl = 0;
     size_t smem = 0;
+    const bool dfk = use_df(F, (int)sizeof(TM));
     for (int c : {1, 2, 4, 8}) {
-        smem = cluster_smem(F.max_m, F.max_K, c, &nloc, &ldl);
+        smem = cluster_smem(F.max_m, F.max_K, c, &nloc, &ldl, dfk);
         if (smem <= kSmemCap) { C = c; break; }
     }
     if (C > 0) {
@@ -798,5 +1202,6 @@ rfm_status launch_filter(const HostPlan &P, void *ws, double tol, cudaStream_t s
 
 void set_force_global_filter(int on) { g_force_global = on; }
 void set_autotune(int on) { g_autotune = on; }
+void set_qr_double_float(int on) { g_qr_df = on; }
 
 }  // namespace rfm
