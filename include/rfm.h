@@ -165,9 +165,10 @@ typedef struct rfm_lsqr_opts {
                             row s-1 (kept slots only; the caller clears the buffer) */
     int32_t snap_every, snap_cap;
     double *d_phase_ms;  /* nullable, 4 doubles: milliseconds the first CTA spent in each
-                            part of the iterations (products A x and row updates, row sums,
-                            products A^T u, scalar updates), each up to the exit of the
-                            grid barrier that closes it; for profiling */
+                            part of the iterations (fused products A^T u and A x with the
+                            column updates, row sums, 0, scalar updates), each up to the exit
+                            of the grid barrier that closes it; for profiling; not written
+                            with RFM_OP_AR64 */
 } rfm_lsqr_opts;
 
 /* Report per instance (written to device memory):

@@ -82,8 +82,9 @@ struct Layout {
     size_t off_tu;                                      // u~ on the block rows in operator precision
     size_t off_fitems, off_nfitems;                     // live forward items (128-row tiles)
     int64_t n_slots;                                    // column items per block at most (ceil(max_K / 8))
-    int64_t n_t_items;                                  // column chunks of the staged transposed product (bound)
+    int64_t n_t_items;                                  // fused product items: column chunks + 32-row tiles (bound)
     size_t off_titems, off_ntitems;
+    size_t off_bcnt;                                    // per block: chunks of the transposed product finished (64-bit, monotone)
     size_t total;
     int asm_prec, op;
 };

@@ -50,6 +50,8 @@ struct LsqrArgs {
     int64_t n_cols;
     double *phase_ms;        // per-phase times of CTA 0 (nullable)
     int64_t n_block_rows;
+    unsigned long long *bcnt;  // per block: chunks of the transposed product finished (fused products)
+    int x_cap;               // staging row length of the forward tiles (>= every rank)
 };
 
 constexpr int kThreads = 256;
@@ -738,25 +740,60 @@ __global__ void k_report(const LsqrScal *__restrict__ sc, int n, rfm_lsqr_report
 // ---------------------------------------------------------------------------
 // Tile variant for the explicit operators (Q_hat in FP32 or FP64, or the
 // unfiltered M): the work of every phase is spread over all CTAs, so all SMs
-// stream the operator at once.
-//   forward (F): one warp per 128 rows of a block, t[rows] = Op_b[rows, :] v_b;
-//     each lane owns four rows (16-byte loads in FP32), the input vector is
-//     read in the operator's precision (a copy of vt kept beside it) and the
-//     1/alpha scaling is applied once per row;
-//   rows (R): u~ = sum of the block partials of each row - (alpha/beta) u~,
-//     copied onto the block rows in the operator's precision;
-//   transposed (T): each CTA owns a contiguous range of column chunks (block
-//     order); a chunk is contiguous in memory (column-major blocks), so it is
-//     copied whole by one bulk asynchronous copy into a ring of shared-memory
-//     stages; one warp reduces one column against the block's u~; the FP64
-//     update vt = z / beta - beta v and the sums ||vt||^2, ||y||^2 then run
-//     over the range with lane-private per-instance accumulators;
-//   scalars (S): the Givens recurrences, redundantly in every CTA.
-// The column updates of the Givens step (y, w) are elementwise and ride in
-// the forward phase; ||y||^2 rides in the transposed phase, so the stopping
-// test of iteration i is taken at the third barrier of round i+1 (with
-// iteration i's estimates).
+// stream the operator at once.  One iteration = two phases separated by grid
+// barriers:
+//   rows (R): u~ = (sum of the block partials of each row) / alpha
+//     - (alpha/beta) u~, copied onto the block rows in the operator's
+//     precision;
+//   fused products: one list of warp items holds, per block, its chunks of 8
+//     columns (transposed product: z = Op_b^T u~_b, then the FP64 update of
+//     vt, y and w per column) and, about 1.2 rounds of the grid's warps
+//     later, its 32-row tiles (forward product of the next iteration,
+//     t = Op_b vt_b, unscaled); a tile waits on a per-block counter of
+//     finished chunks, and re-reads the block while it is still in L2, so
+//     the operator comes from DRAM about once per iteration instead of twice.
+// After the second barrier every CTA forms the Givens recurrences redundantly
+// (scalars, S).  ||y||^2 rides in the fused phase, so the stopping test of
+// iteration i is taken at the fused barrier of round i+1 (with iteration i's
+// estimates).
 // ---------------------------------------------------------------------------
+
+// Operator loads with an L2 eviction priority (PTX createpolicy + cache_hint):
+// a chunk of the transposed product marks its block evict-last, so it is
+// still in L2 when the block's forward tiles re-read it; the tiles' loads
+// are its last use and mark the lines evict-first.
+__device__ __forceinline__ uint64_t l2_policy_keep() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_drop() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ float4 ld_hint(const float4 *p, uint64_t pol) {
+    float4 r;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ double2 ld_hint(const double2 *p, uint64_t pol) {
+    double2 r;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;" : "=d"(r.x), "=d"(r.y) : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ float ld_hint(const float *p, uint64_t pol) {
+    float r;
+    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ double ld_hint(const double *p, uint64_t pol) {
+    double r;
+    asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r) : "l"(p), "l"(pol));
+    return r;
+}
 
 template <typename TA>
 struct TileSmem {
@@ -822,11 +859,13 @@ struct Rows4<double> {
 
 // Live column items in block order: block b contributes ceil(r_b / 8) items.
 // One CTA, deterministic prefix sum.
-__global__ void __launch_bounds__(1024) k_build_items(const BlkRec *__restrict__ blks, int n_blocks,
+__global__ void __launch_bounds__(1024) k_build_items(const InstRec *__restrict__ insts, int n_inst,
+                                                      const BlkRec *__restrict__ blks, int n_blocks,
                                                       const int32_t *__restrict__ rank, ColItem *__restrict__ items,
                                                       int *__restrict__ n_items, ColItem *__restrict__ fitems,
                                                       int *__restrict__ n_fitems, ColItem *__restrict__ titems,
-                                                      int *__restrict__ n_titems, int elem_bytes, int64_t t_cap) {
+                                                      int *__restrict__ n_titems, int elem_bytes, int64_t t_cap,
+                                                      int twarps) {
     __shared__ int scan[1024];
     __shared__ int carry;
     const int tid = threadIdx.x;
@@ -911,18 +950,43 @@ __global__ void __launch_bounds__(1024) k_build_items(const BlkRec *__restrict__
         __syncthreads();
     }
     if (tid == 0) *n_fitems = carry;
-    // staged column chunks of the transposed product: ceil(r / cc) per block
+    // items of the fused products (transposed product of one round, forward
+    // product of the next): block b's column chunks (ceil(r / cc), kind T:
+    // nc = columns) and its 32-row tiles (kind F: c0 = first row, nc = -r).
+    // A block's tiles need the vector its chunks produce, so they follow its
+    // chunks with a lag of L blocks, chosen so that about 1.2 items per warp
+    // of the grid pass in between: the tiles rarely wait, and the block
+    // (re-read by its tiles, kept by an evict-last hint) is still in L2.
+    // Slot s holds the chunks of block s and the tiles of block s - L.
+    __shared__ int s_tot;
     __syncthreads();
+    if (tid == 0) s_tot = 0;
+    __syncthreads();
+    for (int b = tid; b < n_blocks; b += 1024) {
+        const int r = rank ? rank[b] : blks[b].K;
+        const int cc = tchunk_cols(blks[b].ldm, elem_bytes);
+        atomicAdd(&s_tot, (r + cc - 1) / cc + (blks[b].ldm + 31) / 32);
+    }
+    __syncthreads();
+    const int tot = s_tot;
+    const int lag = n_blocks > 0 && tot > 0 ? (int)min((int64_t)n_blocks, ((int64_t)twarps * 6 / 5 * n_blocks + tot - 1) / tot) : 0;
     if (tid == 0) carry = 0;
     __syncthreads();
-    for (int base = 0; base < n_blocks; base += 1024) {
-        const int b = base + tid;
-        int cnt = 0, r = 0, cc = 1;
-        if (b < n_blocks) {
-            r = rank ? rank[b] : blks[b].K;
-            cc = tchunk_cols(blks[b].ldm, elem_bytes);
-            cnt = (r + cc - 1) / cc;
+    const int n_slots = n_blocks + lag;
+    for (int base = 0; base < n_slots; base += 1024) {
+        const int sl = base + tid;
+        int nT = 0, nF = 0, rT = 0, ccT = 1, rF = 0;
+        if (sl < n_blocks) {
+            rT = rank ? rank[sl] : blks[sl].K;
+            ccT = tchunk_cols(blks[sl].ldm, elem_bytes);
+            nT = (rT + ccT - 1) / ccT;
         }
+        const int bF = sl - lag;
+        if (sl < n_slots && bF >= 0) {
+            rF = rank ? rank[bF] : blks[bF].K;
+            nF = (blks[bF].ldm + 31) / 32;
+        }
+        const int cnt = nT + nF;
         scan[tid] = cnt;
         __syncthreads();
         for (int off = 1; off < 1024; off <<= 1) {
@@ -932,21 +996,33 @@ __global__ void __launch_bounds__(1024) k_build_items(const BlkRec *__restrict__
             __syncthreads();
         }
         const int start = carry + scan[tid] - cnt;
-        if (b < n_blocks) {
-            const BlkRec &B = blks[b];
-            for (int k = 0; k < cnt; ++k) {
-                ColItem it;
-                it.b = b;
-                it.c0 = k * cc;
-                it.nc = min(cc, r - it.c0);
-                it.m = B.m;
-                it.ldm = B.ldm;
-                it.inst = B.inst;
-                it.moff = B.moff;
-                it.coff = B.coff;
-                it.roff = B.roff;
-                if (start + k < t_cap) titems[start + k] = it;   // the host sizes t_cap for every case
-            }
+        for (int k = 0; k < nT; ++k) {
+            const BlkRec &B = blks[sl];
+            ColItem it;
+            it.b = sl;
+            it.c0 = k * ccT;
+            it.nc = min(ccT, rT - it.c0);
+            it.m = B.m;
+            it.ldm = B.ldm;
+            it.inst = B.inst;
+            it.moff = B.moff;
+            it.coff = B.coff;
+            it.roff = B.roff;
+            if (start + k < t_cap) titems[start + k] = it;   // the host sizes t_cap for every case
+        }
+        for (int k = 0; k < nF; ++k) {
+            const BlkRec &B = blks[bF];
+            ColItem it;
+            it.b = bF;
+            it.c0 = k * 32;
+            it.nc = -rF;
+            it.m = B.m;
+            it.ldm = B.ldm;
+            it.inst = B.inst;
+            it.moff = B.moff;
+            it.coff = B.coff;
+            it.roff = B.roff;
+            if (start + nT + k < t_cap) titems[start + nT + k] = it;
         }
         __syncthreads();
         if (tid == 0) carry += scan[1023];
@@ -1035,17 +1111,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
     };
     // forward product of block row q
     auto row_partials = [&](int64_t q) { return a.t[q]; };
-    // ---- transposed product: one warp per chunk of up to 8 columns of a
-    // block (chunks in block order, spread over every warp of the grid).  Each
-    // lane keeps 2 x 8 sixteen-byte loads of the operator in flight, the 8
-    // column sums are reduce-scattered in 9 shuffles so that lane 4t holds
-    // column t; the sums of 4 consecutive chunks of the warp are gathered one
-    // column per lane, and the FP64 update of vt runs on all 32 lanes at once
-    // (an FP64 warp instruction costs the same with 8 lanes or 32).  Per-
-    // instance sums ||vt||^2, ||y||^2 stay lane-private until the instance
-    // changes.
+    // ---- fused products: the transposed product of a round and the forward
+    // product of the next, over one list of warp items (block b's column
+    // chunks, then, about 1.2 rounds of the grid later, its 32-row tiles).
+    //  chunk (kind T): up to 8 columns of a block; each lane keeps 2 x 8
+    //    sixteen-byte operator loads in flight; the 8 column sums are
+    //    reduce-scattered in 9 shuffles so that lane 4t holds column t, and
+    //    those lanes apply the FP64 epilogue epi (the new vt and its FP32 copy
+    //    vx; its FP64 operands were loaded when the chunk started); then the
+    //    block's counter of finished chunks is raised (fence, atomic).
+    //  tile (kind F): 32 rows of a block times its r kept columns, t = Op vx
+    //    (unscaled: the row phase applies 1/alpha); it waits until every chunk
+    //    of the block has finished this phase (bounded wait), stages
+    //    the block's vx in shared memory and re-reads the block, which its
+    //    chunks have just brought into L2.
+    // Per-instance sums ||vt||^2, ||y||^2 stay lane-private until the
+    // instance changes.
     const int64_t n_tu = *n_titems_p;
-    auto tphase = [&](auto take, auto epi) {
+    TA *xs = reinterpret_cast<TA *>(smem_raw + sizeof(TileSmem<TA>)) + (size_t)warp * a.x_cap;
+    auto fused = [&](auto take, auto epi, unsigned long long phase) {
+        const uint64_t pol_keep = l2_policy_keep(), pol_drop = l2_policy_drop();
         constexpr int VW = sizeof(TA) == 4 ? 4 : 2, STRIP = 32 * VW;
         double pa = 0.0, py = 0.0;
         int cur_inst = -1;
@@ -1061,55 +1146,86 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
             }
             pa = py = 0.0;
         };
-        // the lane's batched column: sum, slot (-1: none), instance
-        TA zb = (TA)0;
-        int64_t ob = -1;
-        int ib = -1, nbat = 0;
-        auto run_batch = [&]() {
-            const bool valid = ob >= 0;
-            double ca = 0.0, cy = 0.0;
-            if (valid) epi(ib, ob, (double)zb, &ca, &cy);
-            const unsigned vm = __ballot_sync(0xffffffffu, valid);
-            if (vm) {
-                const int x = __shfl_sync(0xffffffffu, ib, __ffs(vm) - 1);
-                if (__all_sync(0xffffffffu, !valid || ib == x)) {
-                    if (x != cur_inst) {
-                        flush_lane();
-                        cur_inst = x;
-                    }
-                    pa += ca;
-                    py += cy;
-                } else {
-                    // columns of several instances: one warp sum per instance
-                    unsigned pend = vm;
-                    while (pend) {
-                        const int xi = __shfl_sync(0xffffffffu, ib, __ffs(pend) - 1);
-                        const bool mine = valid && ib == xi;
-                        double a2 = mine ? ca : 0.0, y2 = mine ? cy : 0.0;
-                        for (int o = 16; o; o >>= 1) {
-                            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-                            y2 += __shfl_xor_sync(0xffffffffu, y2, o);
-                        }
-                        if (lane == 0) {
-                            S.wacc[0][warp][xi] += a2;
-                            S.wacc[1][warp][xi] += y2;
-                        }
-                        pend &= ~__ballot_sync(0xffffffffu, mine);
-                    }
-                }
-            }
-            ob = -1;
-            nbat = 0;
-        };
+        const int mycol = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);   // for lane % 4 == 0
+        // static round-robin over the list (the per-warp sums are then the
+        // same in every run); the next item's record is fetched while the
+        // current one runs.  A tile waits only on chunks earlier in the list,
+        // which every warp reaches first, so the earliest waiting tile always
+        // finds its chunks running.
+        ColItem nxt;
+        if (gwarp < n_tu) nxt = titems[gwarp];
         for (int64_t k = gwarp; k < n_tu; k += twarps) {
-            const ColItem it = titems[k];
+            const ColItem it = nxt;
+            if (k + twarps < n_tu) nxt = titems[k + twarps];
             if (!take(it.inst)) continue;
+            if (it.nc <= 0) {
+                // ---- forward tile
+                const int r = -it.nc;
+                if (r > 0) {
+                    // every chunk of the block is released once per phase
+                    if (lane == 0) {
+                        const unsigned long long target = phase * (unsigned long long)((r + kColTile - 1) / kColTile);
+                        volatile unsigned long long *cp = a.bcnt + it.b;
+                        const uint64_t t0 = global_ns();
+                        unsigned spins = 0;
+                        while (*cp < target) {
+                            if (*(volatile unsigned *)(a.bar + 2)) break;
+                            if ((++spins & 63u) == 0 && global_ns() - t0 > a.timeout_ns) {
+                                atomicCAS(a.bar + 2, 0u, (unsigned)RFM_ETIMEOUT);
+                                break;
+                            }
+                        }
+                        __threadfence();
+                    }
+                    __syncwarp();
+                    for (int c = lane; c < r; c += 32) xs[c] = __ldcg(vx + it.coff + c);
+                    __syncwarp();
+                }
+                // 8 KB of the block in flight per warp: 64 (FP32) or 32 (FP64)
+                // columns of the lane's row per round trip
+                constexpr int UF = sizeof(TA) == 4 ? 64 : 32;
+                const TA *base = Aop + it.moff + it.c0 + lane;   // row c0 + lane of column 0
+                TA acc = (TA)0;
+                int c = 0;
+                for (; c + UF <= r; c += UF) {
+                    TA q[UF];
+#pragma unroll
+                    for (int j = 0; j < UF; ++j) q[j] = ld_hint(base + (int64_t)(c + j) * it.ldm, pol_drop);
+#pragma unroll
+                    for (int j = 0; j < UF; ++j) acc += q[j] * xs[c + j];
+                }
+                for (; c + 8 <= r; c += 8) {
+                    TA q[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) q[j] = ld_hint(base + (int64_t)(c + j) * it.ldm, pol_drop);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc += q[j] * xs[c + j];
+                }
+                for (; c < r; ++c) acc += ld_hint(base + (int64_t)c * it.ldm, pol_drop) * xs[c];
+                a.t[it.roff + it.c0 + lane] = (double)acc;   // rows beyond m are zero padding
+                __syncwarp();
+                continue;
+            }
+            // ---- transposed chunk
+            if (it.inst != cur_inst) {
+                flush_lane();
+                cur_inst = it.inst;
+            }
             const TA *ub = tu + it.roff;
             const TA *base = Aop + it.moff + (int64_t)it.c0 * it.ldm;
-            const int ng = min(8, it.nc);
+            const int ng = it.nc;
+            // the epilogue's lane starts loading its column's FP64 entries now
+            const bool elane = (lane & 3) == 0 && mycol < ng;
+            const int64_t eo = it.coff + it.c0 + mycol;
+            double pre[3] = {0.0, 0.0, 0.0};
+            if (elane) {
+                pre[0] = __ldcg(a.vt + eo);
+                pre[1] = __ldcg(a.w + eo);
+                pre[2] = __ldcg(a.y + eo);
+            }
             TA acc[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) acc[c] = (TA)0;
+            for (int cq = 0; cq < 8; ++cq) acc[cq] = (TA)0;
             for (int i0 = 0; i0 < it.ldm; i0 += 2 * STRIP) {
                 TA w[2][VW], q[8][2][VW];
 #pragma unroll
@@ -1124,24 +1240,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
                         w[h][0] = (TA)t.x; w[h][1] = (TA)t.y;
                     }
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const bool ok = in && c < ng;
-                        const TA *src = base + (int64_t)c * it.ldm + (ok ? i : 0);
+                    for (int cq = 0; cq < 8; ++cq) {
+                        const bool ok = in && cq < ng;
+                        const TA *src = base + (int64_t)cq * it.ldm + (ok ? i : 0);
                         if (sizeof(TA) == 4) {
-                            const float4 t = ok ? __ldg(reinterpret_cast<const float4 *>(src)) : make_float4(0.f, 0.f, 0.f, 0.f);
-                            q[c][h][0] = (TA)t.x; q[c][h][1 % VW] = (TA)t.y; q[c][h][2 % VW] = (TA)t.z; q[c][h][3 % VW] = (TA)t.w;
+                            const float4 t = ok ? ld_hint(reinterpret_cast<const float4 *>(src), pol_keep) : make_float4(0.f, 0.f, 0.f, 0.f);
+                            q[cq][h][0] = (TA)t.x; q[cq][h][1 % VW] = (TA)t.y; q[cq][h][2 % VW] = (TA)t.z; q[cq][h][3 % VW] = (TA)t.w;
                         } else {
-                            const double2 t = ok ? __ldg(reinterpret_cast<const double2 *>(src)) : make_double2(0.0, 0.0);
-                            q[c][h][0] = (TA)t.x; q[c][h][1] = (TA)t.y;
+                            const double2 t = ok ? ld_hint(reinterpret_cast<const double2 *>(src), pol_keep) : make_double2(0.0, 0.0);
+                            q[cq][h][0] = (TA)t.x; q[cq][h][1] = (TA)t.y;
                         }
                     }
                 }
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
 #pragma unroll
-                    for (int c = 0; c < 8; ++c)
+                    for (int cq = 0; cq < 8; ++cq)
 #pragma unroll
-                        for (int v = 0; v < VW; ++v) acc[c] += q[c][h][v] * w[h][v];
+                        for (int v = 0; v < VW; ++v) acc[cq] += q[cq][h][v] * w[h][v];
             }
             // reduce-scatter: lane 4t ends with the full sum of column t
 #pragma unroll
@@ -1163,16 +1279,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
             }
             acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 2);
             acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
-            // column t (lane 4t) -> lane 8 nbat + t
-            const TA zt = __shfl_sync(0xffffffffu, acc[0], 4 * (lane & 7));
-            if ((lane >> 3) == nbat) {
-                zb = zt;
-                ob = (lane & 7) < ng ? it.coff + it.c0 + (lane & 7) : -1;
-                ib = it.inst;
-            }
-            if (++nbat == 4) run_batch();
+            if (elane) epi(it.inst, eo, (double)acc[0], pre, &pa, &py);
+            // the chunk's columns are written: release them to the block's tiles
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) atomicAdd(a.bcnt + it.b, 1ull);
         }
-        run_batch();
         flush_lane();
     };
 
@@ -1327,15 +1439,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
         S.inv_bn[s] = sc[s].beta > 0.0 ? 1.0 / sc[s].beta : 0.0;
     }
     __syncthreads();
-    // vt = Op^T u~ / beta, ||vt||^2
+    // vt = Op^T u~ / beta, ||vt||^2, fused with t = Op vt (round 1's forward product)
     clear_w();
     __syncthreads();
-    tphase(all_inst, [&](int inst, int64_t o, double z, double *pa, double *py) {
+    unsigned long long fphase = 1;
+    fused(all_inst, [&](int inst, int64_t o, double z, const double *pre, double *pa, double *py) {
         const double x = z * S.inv_bn[inst];
         a.vt[o] = x;
         if (sizeof(TA) != sizeof(double)) vx[o] = (TA)x;
         *pa += x * x;
-    });
+    }, fphase);
     __syncthreads();
     flush_w(0, 2);
     ok = grid_sync(a.bar, a.timeout_ns);
@@ -1358,9 +1471,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
     __syncthreads();
 
     // ------------------------------------------------------------ rounds
-    // Round n: F applies iteration n-1's update of y, w (n = 1: w = v_1) and
-    // forms Op v_n; R and T continue the bidiagonalisation; at the third
-    // barrier iteration n-1 is tested, then iteration n's rotation is formed.
+    // Round n: R forms u~_{n+1} = (Op vt_n) / alpha_n - (alpha_n / beta_n) u~_n
+    // from the forward partials of the previous fused phase; the fused phase
+    // forms Op^T u~_{n+1}, applies iteration n-1's update of y, w (n = 1:
+    // w = v_1), vt_{n+1} = Op^T u~_{n+1} / beta_{n+1} - beta_{n+1} v_n, and the
+    // forward partials Op vt_{n+1} of round n+1; at its barrier iteration n-1
+    // is tested and iteration n's rotation is formed.
     uint64_t tph = global_ns();
     double ph[4] = {0.0, 0.0, 0.0, 0.0};
     auto mark = [&](int k) {
@@ -1370,29 +1486,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
     };
     for (int n = 1;; ++n) {
         const bool first = n == 1;
-        // F
-        each_column(live, [&](int inst, int64_t o) {
-            const LsqrScal &q = sc[inst];
-            const double vn = a.vt[o] * S.inv_alpha[inst];
-            if (first) {
-                a.w[o] = vn;
-            } else {
-                const double wo = a.w[o];
-                const double yv = fma(q.phi_rho, wo, a.y[o]);
-                a.y[o] = yv;
-                a.w[o] = fma(-q.theta_rho, wo, vn);
-                if (a.snap && q.itn % a.snap_every == 0 && q.itn / a.snap_every <= a.snap_cap)
-                    a.snap[(int64_t)(q.itn / a.snap_every - 1) * a.n_cols + o] = yv;
-            }
-        });
-        forward(live, vx, [&](int inst) { return S.inv_alpha[inst]; });
-        ok = grid_sync(a.bar, a.timeout_ns);
-        mark(0);
-        if (!ok) break;
-        // R: u~ = sum of the block partials - (alpha/beta) u~
+        // R: u~ = (sum of the block partials) / alpha - (alpha / beta) u~
         clear_w();
         __syncthreads();
-        row_phase(live, [&](int s, double acc, double uo) { return fma(-S.ab[s], uo, acc); });
+        row_phase(live, [&](int s, double acc, double uo) { return fma(-S.ab[s], uo, acc * S.inv_alpha[s]); });
         __syncthreads();
         flush_w(0, 1);
         ok = grid_sync(a.bar, a.timeout_ns);
@@ -1405,23 +1502,36 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
             S.inv_bn[s] = bn > 0.0 ? 1.0 / bn : 0.0;
         }
         __syncthreads();
-        // T: vt = Op^T u~ / beta_new - beta_new v_n ; ||vt||^2 ; ||y_{n-1}||^2
+        // fused products: vt = Op^T u~ / beta_new - beta_new v_n (after
+        // iteration n-1's update of y, w); ||vt||^2; ||y_{n-1}||^2; Op vt
         clear_w();
         __syncthreads();
-        tphase(live, [&](int inst, int64_t o, double z, double *pa, double *py) {
-            const double vn = a.vt[o] * S.inv_alpha[inst];
+        ++fphase;
+        fused(live, [&](int inst, int64_t o, double z, const double *pre, double *pa, double *py) {
+            const LsqrScal &q = sc[inst];
+            const double vn = pre[0] * S.inv_alpha[inst];
+            double yv = pre[2];
+            if (first) {
+                a.w[o] = vn;
+            } else {
+                const double wo = pre[1];
+                yv = fma(q.phi_rho, wo, yv);
+                a.y[o] = yv;
+                a.w[o] = fma(-q.theta_rho, wo, vn);
+                if (a.snap && q.itn % a.snap_every == 0 && q.itn / a.snap_every <= a.snap_cap)
+                    a.snap[(int64_t)(q.itn / a.snap_every - 1) * a.n_cols + o] = yv;
+            }
             const double x = fma(z, S.inv_bn[inst], -S.bn[inst] * vn);
             a.vt[o] = x;
             if (sizeof(TA) != sizeof(double)) vx[o] = (TA)x;
             *pa += x * x;
-            const double yv = a.y[o];
             *py += yv * yv;
-        });
+        }, fphase);
         __syncthreads();
         flush_w(0, 2);
         flush_w(1, 0);
         ok = grid_sync(a.bar, a.timeout_ns);
-        mark(2);
+        mark(0);
         if (!ok) break;
         reduce_partials2(a.part + (int64_t)2 * ni * G, S.tmp2, a.part, S.yy, ni);   // alpha_{n+1}^2, ||y_{n-1}||^2
         __shared__ int s_all_done;
@@ -1499,18 +1609,9 @@ static rfm_status run_lsqr_tiles(const HostPlan &P, void *ws, LsqrArgs &args, cu
     RFM_CUDA_CHECK(cudaGetDevice(&dev));
     RFM_CUDA_CHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const Layout &L = P.L;
-    ColItem *items = ws_ptr<ColItem>(ws, L.off_items);
-    int *nitems = ws_ptr<int>(ws, L.off_nitems);
-    ColItem *titems = ws_ptr<ColItem>(ws, L.off_titems);
-    int *ntitems = ws_ptr<int>(ws, L.off_ntitems);
-    {
-        ProfScope ps("k_build_items", st);
-        k_build_items<<<1, 1024, 0, st>>>(args.blks, args.n_blocks, args.rank, items, nitems,
-                                          ws_ptr<ColItem>(ws, L.off_fitems), ws_ptr<int>(ws, L.off_nfitems), titems,
-                                          ntitems, (int)sizeof(TA), L.n_t_items);
-        RFM_CUDA_CHECK(cudaGetLastError());
-    }
-    const size_t sm = sizeof(TileSmem<TA>);
+    // per warp a staging row of the block vector for the forward tiles
+    args.x_cap = (int)(L.n_slots * kColTile);
+    const size_t sm = sizeof(TileSmem<TA>) + (size_t)(kThreads / 32) * args.x_cap * sizeof(TA);
     RFM_CUDA_CHECK(cudaFuncSetAttribute(k_lsqr_tiles<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     RFM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lsqr_tiles<TA>, kThreads, sm));
     if (per < 1) {
@@ -1519,9 +1620,22 @@ static rfm_status run_lsqr_tiles(const HostPlan &P, void *ws, LsqrArgs &args, cu
     }
     int G = nsm * per;
     if (G > kMaxPersistCtas) G = kMaxPersistCtas;
+    ColItem *items = ws_ptr<ColItem>(ws, L.off_items);
+    int *nitems = ws_ptr<int>(ws, L.off_nitems);
+    ColItem *titems = ws_ptr<ColItem>(ws, L.off_titems);
+    int *ntitems = ws_ptr<int>(ws, L.off_ntitems);
+    {
+        ProfScope ps("k_build_items", st);
+        k_build_items<<<1, 1024, 0, st>>>(args.insts, args.n_inst, args.blks, args.n_blocks, args.rank, items, nitems,
+                                          ws_ptr<ColItem>(ws, L.off_fitems), ws_ptr<int>(ws, L.off_nfitems), titems,
+                                          ntitems, (int)sizeof(TA), L.n_t_items, G * (kThreads / 32));
+        RFM_CUDA_CHECK(cudaGetLastError());
+    }
     TA *tu = ws_ptr<TA>(ws, L.off_tu);
     // padding block rows of u~ are never written by the row phase: keep them zero
     RFM_CUDA_CHECK(cudaMemsetAsync(tu, 0, sizeof(TA) * (size_t)L.block_rows, st));
+    args.bcnt = ws_ptr<unsigned long long>(ws, L.off_bcnt);
+    RFM_CUDA_CHECK(cudaMemsetAsync(args.bcnt, 0, sizeof(unsigned long long) * (size_t)L.n_blocks, st));
     const ColItem *citems = items, *cfitems = ws_ptr<ColItem>(ws, L.off_fitems), *ctitems = titems;
     const int *cn = nitems, *cfn = ws_ptr<int>(ws, L.off_nfitems), *ctn = ntitems;
     void *kargs[] = {&args, (void *)&citems, (void *)&cn, (void *)&cfitems, (void *)&cfn, (void *)&tu,

@@ -276,18 +276,20 @@ rfm_status build_plan(const rfm_problem *probs, int n_inst, const rfm_config *cf
     L.off_nitems = take(256);
     L.off_z = take(sizeof(double) * (col0 + 1));
     {
-        // chunks of the transposed product over every block's K columns (the
+        // items of the fused products: chunks of the transposed product over
+        // every block's K columns and 32-row tiles of the forward product (the
         // ranks are known only on the device; the fit of predicted values runs
         // an FP64 operator on any system)
         int64_t nt = 0;
         for (const BlkRec &B : blk) {
             const int cc = tchunk_cols(B.ldm, 8);
-            nt += (B.K + cc - 1) / cc;
+            nt += (B.K + cc - 1) / cc + (B.ldm + 31) / 32;
         }
         L.n_t_items = nt;
     }
     L.off_titems = take(sizeof(ColItem) * (L.n_t_items + 1));
     L.off_ntitems = take(256);
+    L.off_bcnt = take(sizeof(unsigned long long) * (blk.size() + 1));
     L.off_qblk = take(sizeof(int32_t) * (roff + 1));
     L.off_tu = take(sizeof(double) * (roff + 1));
     L.off_fitems = take(sizeof(ColItem) * (L.n_fwd_items + 1));
