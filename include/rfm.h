@@ -166,9 +166,9 @@ typedef struct rfm_lsqr_opts {
     int32_t snap_every, snap_cap;
     double *d_phase_ms;  /* nullable, 4 doubles: milliseconds the first CTA spent in each
                             part of the iterations (fused products A^T u and A x with the
-                            column updates, row sums, 0, scalar updates), each up to the exit
-                            of the grid barrier that closes it; for profiling; not written
-                            with RFM_OP_AR64 */
+                            column updates; row sums with the scalar updates overlapped; 0;
+                            0), each up to the exit of the grid barrier that closes it; for
+                            profiling; not written with RFM_OP_AR64 */
 } rfm_lsqr_opts;
 
 /* Report per instance (written to device memory):

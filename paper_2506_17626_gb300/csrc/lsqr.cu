@@ -752,16 +752,21 @@ __global__ void k_report(const LsqrScal *__restrict__ sc, int n, rfm_lsqr_report
 //     t = Op_b vt_b, unscaled); a tile waits on a per-block counter of
 //     finished chunks, and re-reads the block while it is still in L2, so
 //     the operator comes from DRAM about once per iteration instead of twice.
-// After the second barrier every CTA forms the Givens recurrences redundantly
-// (scalars, S).  ||y||^2 rides in the fused phase, so the stopping test of
-// iteration i is taken at the fused barrier of round i+1 (with iteration i's
-// estimates).
+// Every CTA forms the Givens recurrences redundantly (scalars), in warp 0
+// while its other warps issue the row phase's loads.  ||y||^2 rides in the
+// fused phase, so the stopping test of iteration i is taken after the fused
+// barrier of round i+1 (with iteration i's estimates).
 // ---------------------------------------------------------------------------
 
 // Operator loads with an L2 eviction priority (PTX createpolicy + cache_hint):
 // a chunk of the transposed product marks its block evict-last, so it is
 // still in L2 when the block's forward tiles re-read it; the tiles' loads
 // are its last use and mark the lines evict-first.
+// Release increment of a completion counter (no returned value to wait for).
+__device__ __forceinline__ void red_release_add(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 __device__ __forceinline__ uint64_t l2_policy_keep() {
     uint64_t p;
     asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
@@ -954,7 +959,7 @@ __global__ void __launch_bounds__(1024) k_build_items(const InstRec *__restrict_
     // product of the next): block b's column chunks (ceil(r / cc), kind T:
     // nc = columns) and its 32-row tiles (kind F: c0 = first row, nc = -r).
     // A block's tiles need the vector its chunks produce, so they follow its
-    // chunks with a lag of L blocks, chosen so that about 1.2 items per warp
+    // chunks with a lag of L blocks, chosen so that about 1.6 items per warp
     // of the grid pass in between: the tiles rarely wait, and the block
     // (re-read by its tiles, kept by an evict-last hint) is still in L2.
     // Slot s holds the chunks of block s and the tiles of block s - L.
@@ -969,7 +974,7 @@ __global__ void __launch_bounds__(1024) k_build_items(const InstRec *__restrict_
     }
     __syncthreads();
     const int tot = s_tot;
-    const int lag = n_blocks > 0 && tot > 0 ? (int)min((int64_t)n_blocks, ((int64_t)twarps * 6 / 5 * n_blocks + tot - 1) / tot) : 0;
+    const int lag = n_blocks > 0 && tot > 0 ? (int)min((int64_t)n_blocks, ((int64_t)twarps * 8 / 5 * n_blocks + tot - 1) / tot) : 0;
     if (tid == 0) carry = 0;
     __syncthreads();
     const int n_slots = n_blocks + lag;
@@ -1119,7 +1124,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
     //    reduce-scattered in 9 shuffles so that lane 4t holds column t, and
     //    those lanes apply the FP64 epilogue epi (the new vt and its FP32 copy
     //    vx; its FP64 operands were loaded when the chunk started); then the
-    //    block's counter of finished chunks is raised (fence, atomic).
+    //    block's counter of finished chunks is raised (release reduction).
     //  tile (kind F): 32 rows of a block times its r kept columns, t = Op vx
     //    (unscaled: the row phase applies 1/alpha); it waits until every chunk
     //    of the block has finished this phase (bounded wait), stages
@@ -1281,9 +1286,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
             acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
             if (elane) epi(it.inst, eo, (double)acc[0], pre, &pa, &py);
             // the chunk's columns are written: release them to the block's tiles
-            __threadfence();
+            // (__syncwarp orders the lanes' stores before lane 0's release)
             __syncwarp();
-            if (lane == 0) atomicAdd(a.bcnt + it.b, 1ull);
+            if (lane == 0) red_release_add(a.bcnt + it.b, 1ull);
         }
         flush_lane();
     };
@@ -1291,56 +1296,75 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
     // rows (R): 32-row warp tiles (a tile never spans two instances), two
     // tiles per warp per pass with their loads issued together; u~ of a row
     // = fn(inst, sum of its block partials, old u~), stored to u and to the
-    // row's block-row copies; per-warp, per-instance sums of u~^2 in wacc[0]
-    auto row_phase = [&](auto take, auto fn) {
+    // row's block-row copies; per-warp, per-instance sums of u~^2 in wacc[0].
+    // The loads need no scalars: the first pass's loads are issued before
+    // mid() (every thread of the CTA calls it once), where the previous
+    // phase's scalars can be formed.
+    struct RowPass {
+        int si[2], Ci[2];
+        bool tv[2], rv[2];
+        int64_t gr[2];
+        const int32_t *lst[2];
+        double acc[2], uo[2];
+    };
+    auto row_load = [&](RowPass &P, int64_t T0, int64_t tw) {
         const int64_t n_wt = S.wt0[ni];
-        for (int64_t T0 = gwarp; T0 < n_wt; T0 += 2 * twarps) {
-            int si[2], Ci[2];
-            bool tv[2], rv[2];
-            int64_t gr[2];
-            const int32_t *lst[2];
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int64_t T = T0 + (int64_t)j * twarps;
-                int sx = 0;
-                if (T < n_wt)
-                    while (S.wt0[sx + 1] <= T) ++sx;
-                si[j] = sx;
-                tv[j] = T < n_wt && take(sx);
-                const InstRec &I = a.insts[sx];
-                const int64_t r = (T - S.wt0[sx]) * 32 + lane;
-                rv[j] = tv[j] && r < I.N;
-                Ci[j] = I.C;
-                gr[j] = I.row0 + (rv[j] ? r : 0);
-                lst[j] = a.rowlist + I.rl_off + (rv[j] ? r : 0) * I.C;
-            }
-            double acc[2] = {0.0, 0.0}, uo[2];
-            const int Cm = Ci[0] > Ci[1] ? Ci[0] : Ci[1];
-            for (int e = 0; e < Cm; ++e) {
-                const int q0 = rv[0] && e < Ci[0] ? lst[0][e] : -1;
-                const int q1 = rv[1] && e < Ci[1] ? lst[1][e] : -1;
-                if (q0 >= 0) acc[0] += row_partials(q0);
-                if (q1 >= 0) acc[1] += row_partials(q1);
-            }
+        for (int j = 0; j < 2; ++j) {
+            const int64_t T = T0 + (int64_t)j * tw;
+            int sx = 0;
+            if (T < n_wt)
+                while (S.wt0[sx + 1] <= T) ++sx;
+            P.si[j] = sx;
+            P.tv[j] = T < n_wt;
+            const InstRec &I = a.insts[sx];
+            const int64_t r = (T - S.wt0[sx]) * 32 + lane;
+            P.rv[j] = P.tv[j] && r < I.N;
+            P.Ci[j] = I.C;
+            P.gr[j] = I.row0 + (P.rv[j] ? r : 0);
+            P.lst[j] = a.rowlist + I.rl_off + (P.rv[j] ? r : 0) * I.C;
+        }
+        P.acc[0] = P.acc[1] = 0.0;
+        const int Cm = P.Ci[0] > P.Ci[1] ? P.Ci[0] : P.Ci[1];
+        for (int e = 0; e < Cm; ++e) {
+            const int q0 = P.rv[0] && e < P.Ci[0] ? P.lst[0][e] : -1;
+            const int q1 = P.rv[1] && e < P.Ci[1] ? P.lst[1][e] : -1;
+            if (q0 >= 0) P.acc[0] += row_partials(q0);
+            if (q1 >= 0) P.acc[1] += row_partials(q1);
+        }
 #pragma unroll
-            for (int j = 0; j < 2; ++j) uo[j] = rv[j] ? a.u[gr[j]] : 0.0;
+        for (int j = 0; j < 2; ++j) P.uo[j] = P.rv[j] ? a.u[P.gr[j]] : 0.0;
+    };
+    auto row_finish = [&](RowPass &P, auto take, auto fn) {
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                if (!tv[j]) continue;    // warp-uniform
-                double uu = 0.0;
-                if (rv[j]) {
-                    const double uv = fn(si[j], acc[j], uo[j]);
-                    a.u[gr[j]] = uv;
-                    const TA ut = (TA)uv;
-                    for (int e = 0; e < Ci[j]; ++e) {
-                        const int q = lst[j][e];
-                        if (q >= 0) tu[q] = ut;
-                    }
-                    uu = uv * uv;
+        for (int j = 0; j < 2; ++j) {
+            if (!P.tv[j] || !take(P.si[j])) continue;    // warp-uniform
+            double uu = 0.0;
+            if (P.rv[j]) {
+                const double uv = fn(P.si[j], P.acc[j], P.uo[j]);
+                a.u[P.gr[j]] = uv;
+                const TA ut = (TA)uv;
+                for (int e = 0; e < P.Ci[j]; ++e) {
+                    const int q = P.lst[j][e];
+                    if (q >= 0) tu[q] = ut;
                 }
-                for (int o = 16; o; o >>= 1) uu += __shfl_xor_sync(0xffffffffu, uu, o);
-                if (lane == 0) S.wacc[0][warp][si[j]] += uu;
+                uu = uv * uv;
             }
+            for (int o = 16; o; o >>= 1) uu += __shfl_xor_sync(0xffffffffu, uu, o);
+            if (lane == 0) S.wacc[0][warp][P.si[j]] += uu;
+        }
+    };
+    // part: this warp takes tiles w0, w0 + tw, ...
+    auto row_phase = [&](bool part, int64_t w0, int64_t tw, auto take, auto fn, auto mid) {
+        const int64_t n_wt = S.wt0[ni];
+        RowPass P;
+        row_load(P, part ? w0 : n_wt, tw);
+        mid();
+        if (!part) return;
+        row_finish(P, take, fn);
+        for (int64_t T0 = w0 + 2 * tw; T0 < n_wt; T0 += 2 * tw) {
+            row_load(P, T0, tw);
+            row_finish(P, take, fn);
         }
     };
 
@@ -1475,8 +1499,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
     // from the forward partials of the previous fused phase; the fused phase
     // forms Op^T u~_{n+1}, applies iteration n-1's update of y, w (n = 1:
     // w = v_1), vt_{n+1} = Op^T u~_{n+1} / beta_{n+1} - beta_{n+1} v_n, and the
-    // forward partials Op vt_{n+1} of round n+1; at its barrier iteration n-1
-    // is tested and iteration n's rotation is formed.
+    // forward partials Op vt_{n+1} of round n+1.  The scalars of round n
+    // (test of iteration n-1, rotation of iteration n) are formed by warp 0 of
+    // every CTA at the start of round n+1, while warps 1-7 issue the loads of
+    // that round's row phase, which only its final combine needs them for.
     uint64_t tph = global_ns();
     double ph[4] = {0.0, 0.0, 0.0, 0.0};
     auto mark = [&](int k) {
@@ -1484,12 +1510,96 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
         ph[k] += (double)(t - tph) * 1e-6;
         tph = t;
     };
+    __shared__ int s_all_done;
+    // scalars after the fused phase of round m (warp 0): alpha_{m+1}^2 and
+    // ||y_{m-1}||^2 from the CTAs' partials, the test of iteration m-1 and the
+    // rotation of iteration m
+    auto scalars = [&](int m) {
+        for (int s = 0; s < ni; ++s) {
+            const double *pa = a.part + ((int64_t)2 * ni + s) * G, *py = a.part + (int64_t)s * G;
+            double xa = 0.0, xy = 0.0;
+            for (int c0 = 0; c0 < G; c0 += 32 * 8) {
+                double va[8], vy[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {   // both arrays' loads in flight before the adds
+                    const int c = c0 + 32 * k + lane;
+                    va[k] = c < G ? pa[c] : 0.0;
+                    vy[k] = c < G ? py[c] : 0.0;
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    xa += va[k];
+                    xy += vy[k];
+                }
+            }
+            for (int o = 16; o; o >>= 1) {
+                xa += __shfl_xor_sync(0xffffffffu, xa, o);
+                xy += __shfl_xor_sync(0xffffffffu, xy, o);
+            }
+            if (lane == 0) {
+                S.tmp2[s] = xa;
+                S.yy[s] = xy;
+            }
+        }
+        if (lane == 0) s_all_done = 1;
+        __syncwarp();
+        const bool firstm = m == 1;
+        for (int s = lane; s < ni; s += 32) {
+            LsqrScal &q = sc[s];
+            if (q.done) continue;
+            if (!firstm) {
+                // (two square roots and two divisions per iteration: GB300's
+                // FP64 pipe makes each one a long serial latency)
+                q.ynorm = sqrt(S.yy[s]);
+                const double anorm = sqrt(q.anorm2);
+                if (q.rnorm <= a.btol * q.bnorm + a.atol * anorm * q.ynorm) { q.done = 1; q.istop = 1; }
+                else if (q.arnorm <= a.atol * anorm * q.rnorm) { q.done = 1; q.istop = 2; }
+                else if (m - 1 >= a.max_iter) { q.done = 1; q.istop = 7; }
+            } else if (a.max_iter == 0) {
+                q.done = 1;
+                q.istop = 7;
+            }
+            if (q.done) continue;
+            q.itn = m;
+            const double beta = S.bn[s];
+            const double alpha = sqrt(S.tmp2[s]);
+            q.anorm2 += q.alpha * q.alpha + beta * beta;
+            const double rho = sqrt(q.rhobar * q.rhobar + beta * beta);
+            const double rinv = rho > 0.0 ? 1.0 / rho : 0.0;
+            const double c = rho > 0.0 ? q.rhobar * rinv : 1.0;
+            const double sn = beta * rinv;
+            const double theta = sn * alpha;
+            q.rhobar = -c * alpha;
+            const double phi = c * q.phibar;
+            q.phibar = sn * q.phibar;
+            q.phi_rho = phi * rinv;
+            q.theta_rho = theta * rinv;
+            q.rnorm = q.phibar;
+            q.arnorm = q.phibar * alpha * fabs(c);
+            q.c = c;
+            q.alpha = alpha;
+            q.beta = beta;
+            S.inv_alpha[s] = alpha > 0.0 ? 1.0 / alpha : 0.0;
+            S.ab[s] = alpha * S.inv_bn[s];
+            if (!isfinite(q.phibar) || !isfinite(q.rhobar) || !isfinite(q.phi_rho) || !isfinite(q.anorm2)) {
+                q.done = 1;
+                q.status = RFM_ENUMERIC;
+            }
+            atomicAnd(&s_all_done, 0);
+        }
+    };
+    const int64_t w7 = (int64_t)(warp - 1) * G + cta, tw7 = (int64_t)(nwarps - 1) * G;
     for (int n = 1;; ++n) {
         const bool first = n == 1;
         // R: u~ = (sum of the block partials) / alpha - (alpha / beta) u~
         clear_w();
         __syncthreads();
-        row_phase(live, [&](int s, double acc, double uo) { return fma(-S.ab[s], uo, acc * S.inv_alpha[s]); });
+        row_phase(warp > 0, w7, tw7, live, [&](int s, double acc, double uo) { return fma(-S.ab[s], uo, acc * S.inv_alpha[s]); },
+                  [&]() {
+                      if (!first && warp == 0) scalars(n - 1);
+                      __syncthreads();
+                  });
+        if (!first && s_all_done) break;
         __syncthreads();
         flush_w(0, 1);
         ok = grid_sync(a.bar, a.timeout_ns);
@@ -1533,56 +1643,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
         ok = grid_sync(a.bar, a.timeout_ns);
         mark(0);
         if (!ok) break;
-        reduce_partials2(a.part + (int64_t)2 * ni * G, S.tmp2, a.part, S.yy, ni);   // alpha_{n+1}^2, ||y_{n-1}||^2
-        __shared__ int s_all_done;
-        if (tid == 0) s_all_done = 1;
-        __syncthreads();
-        for (int s = tid; s < ni; s += kThreads) {
-            LsqrScal &q = sc[s];
-            if (q.done) continue;
-            if (!first) {
-                // (two square roots and two divisions per iteration: GB300's
-                // FP64 pipe makes each one a long serial latency)
-                q.ynorm = sqrt(S.yy[s]);
-                const double anorm = sqrt(q.anorm2);
-                if (q.rnorm <= a.btol * q.bnorm + a.atol * anorm * q.ynorm) { q.done = 1; q.istop = 1; }
-                else if (q.arnorm <= a.atol * anorm * q.rnorm) { q.done = 1; q.istop = 2; }
-                else if (n - 1 >= a.max_iter) { q.done = 1; q.istop = 7; }
-            } else if (a.max_iter == 0) {
-                q.done = 1;
-                q.istop = 7;
-            }
-            if (q.done) continue;
-            q.itn = n;
-            const double beta = S.bn[s];
-            const double alpha = sqrt(S.tmp2[s]);
-            q.anorm2 += q.alpha * q.alpha + beta * beta;
-            const double rho = sqrt(q.rhobar * q.rhobar + beta * beta);
-            const double rinv = rho > 0.0 ? 1.0 / rho : 0.0;
-            const double c = rho > 0.0 ? q.rhobar * rinv : 1.0;
-            const double sn = beta * rinv;
-            const double theta = sn * alpha;
-            q.rhobar = -c * alpha;
-            const double phi = c * q.phibar;
-            q.phibar = sn * q.phibar;
-            q.phi_rho = phi * rinv;
-            q.theta_rho = theta * rinv;
-            q.rnorm = q.phibar;
-            q.arnorm = q.phibar * alpha * fabs(c);
-            q.c = c;
-            q.alpha = alpha;
-            q.beta = beta;
-            S.inv_alpha[s] = alpha > 0.0 ? 1.0 / alpha : 0.0;
-            S.ab[s] = alpha * S.inv_bn[s];
-            if (!isfinite(q.phibar) || !isfinite(q.rhobar) || !isfinite(q.phi_rho) || !isfinite(q.anorm2)) {
-                q.done = 1;
-                q.status = RFM_ENUMERIC;
-            }
-            atomicAnd(&s_all_done, 0);
-        }
-        __syncthreads();
-        mark(3);
-        if (s_all_done) break;
     }
     if (cta == 0) {
         for (int s = tid; s < ni; s += kThreads) a.scal[s] = sc[s];
