@@ -76,6 +76,8 @@ struct Layout {
     size_t off_W, off_tau, off_perm, off_rank, off_r11, off_op, off_q32;  // filter
     size_t off_u, off_v, off_vt, off_w, off_y, off_t, off_part, off_scal, off_bar;  // lsqr
     size_t off_evpart;                                  // eval scratch
+    size_t off_evdf;                                    // eval: double-float parameters and coefficients
+    int64_t n_prm;                                      // feature parameters over all instances (doubles)
     int64_t n_fwd_items, n_col_items;                   // LSQR tile work items
     size_t off_fwd_items, off_col_items;
     size_t off_items, off_nitems, off_z, off_qblk;      // live column items, transposed-product scratch, block of each block row

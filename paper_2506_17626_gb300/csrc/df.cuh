@@ -118,6 +118,56 @@ __device__ __forceinline__ float2 df_rcp(float2 a) {
     return make_float2(h, l);
 }
 
+// a * 2^k for integer k (both words scaled exactly, no overflow in range)
+__device__ __forceinline__ float2 df_ldexp(float2 a, int k) { return make_float2(ldexpf(a.x, k), ldexpf(a.y, k)); }
+
+// Double-float constant from a double known at compile time.
+struct DfConst {
+    float h, l;
+    constexpr DfConst(double x) : h((float)x), l((float)(x - (double)(float)x)) {}
+};
+
+// expm1(r) = sum_{n >= 1} r^n / n! for |r| <= ln2 / 2, by Horner's rule
+// on the Taylor series cut after n = 13 (the next term is below 2^-52 of
+// the sum there).
+__device__ __forceinline__ float2 df_expm1_reduced(float2 r) {
+    constexpr double f[14] = {1.0, 1.0, 1.0 / 2, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720, 1.0 / 5040,
+                              1.0 / 40320, 1.0 / 362880, 1.0 / 3628800, 1.0 / 39916800, 1.0 / 479001600,
+                              1.0 / 6227020800.0};
+    float2 p = make_float2(DfConst(f[13]).h, DfConst(f[13]).l);
+#pragma unroll
+    for (int n = 12; n >= 1; --n) p = df_add(df_mul(p, r), make_float2(DfConst(f[n]).h, DfConst(f[n]).l));
+    return df_mul(p, r);
+}
+
+// tanh(z) in double-float.  With x = 2|z|: for x <= ln2/2, tanh = e / (e + 2)
+// with e = expm1(x) (no cancellation near 0); otherwise x = k ln2 + r with
+// |r| <= ln2/2, E = 2^k (1 + expm1(r)) = exp(x) and tanh = 1 - 2 / (E + 1);
+// |z| > 20 gives 1 (tanh(20) = 1 - 8.5e-18).  The sign follows z.
+__device__ __forceinline__ float2 df_tanh(float2 z) {
+    const bool neg = z.x < 0.f;
+    const float2 az = neg ? df_neg(z) : z;
+    float2 t;
+    if (az.x > 20.f) {
+        t = make_float2(1.f, 0.f);
+    } else {
+        const float2 x = make_float2(2.f * az.x, 2.f * az.y);
+        constexpr double kLn2 = 0.693147180559945309417232121458;
+        if (x.x <= 0.34657359f) {
+            const float2 e = df_expm1_reduced(x);
+            t = df_mul(e, df_rcp(df_add(e, make_float2(2.f, 0.f))));
+        } else {
+            const float k = rintf(x.x * 1.44269504f);
+            const float rh = __fmaf_rn(-k, DfConst(kLn2).h, x.x);   // exact: x.x and k ln2_hi agree in their leading bits
+            const float2 r = df_add(make_float2(rh, 0.f), make_float2(__fmaf_rn(-k, DfConst(kLn2).l, x.y), 0.f));
+            const float2 E = df_ldexp(df_add(df_expm1_reduced(r), make_float2(1.f, 0.f)), (int)k);
+            const float2 q = df_rcp(df_add(E, make_float2(1.f, 0.f)));
+            t = df_sub(make_float2(1.f, 0.f), make_float2(2.f * q.x, 2.f * q.y));
+        }
+    }
+    return neg ? df_neg(t) : t;
+}
+
 // sum over the 2^k lanes of an aligned group (xor butterfly); every lane of
 // the group ends with the same pair (two_sum is symmetric in its arguments)
 __device__ __forceinline__ float2 df_xor_add(float2 v, int o) {

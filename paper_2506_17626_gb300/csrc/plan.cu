@@ -267,6 +267,8 @@ rfm_status build_plan(const rfm_problem *probs, int n_inst, const rfm_config *cf
     L.off_scal = take(sizeof(LsqrScal) * n_inst);
     L.off_bar = take(256);
     L.off_evpart = take(sizeof(double) * 4 * 1024 * n_inst);
+    L.n_prm = prm0;
+    L.off_evdf = take(8 * (size_t)(prm0 + col0 + 2));   // double-float copies of the parameters and coefficients
     L.n_fwd_items = (int64_t)fwd_items.size() / 2;
     L.n_col_items = (int64_t)col_items.size() / 2;
     L.off_fwd_items = take(sizeof(int32_t) * (fwd_items.size() + 2));
