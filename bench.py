@@ -49,7 +49,7 @@ FP64_PEAK_GFLOPS = 152 * 4 * 2.07
 # iteration for k_lsqr ((10.690 + 0.283) GB over a 50-iteration capture, scaled
 # by the launch's iteration count), per launch otherwise; a kernel without an
 # entry reports None.
-NCU_TRAFFIC_PER_ITER = {"k_lsqr": (10.833e9 + 0.314e9) / 50}
+NCU_TRAFFIC_PER_ITER = {"k_lsqr": (7.072e9 + 0.222e9) / 50}
 NCU_TRAFFIC = {"k_qrcp_cluster": 0.264e9 + 0.868e9}
 
 
