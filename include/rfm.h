@@ -189,9 +189,10 @@ typedef struct rfm_lsqr_report {
  * Stopping (per instance): ||r|| <= btol ||h|| + atol ||A||_F ||y||, or
  * ||A^T r|| <= atol ||A||_F ||r||, or max_iter, with the norm estimates of
  * the 1982 paper and ||y|| computed exactly.
- * Returns RFM_ETIMEOUT if a device-side grid barrier waited longer than
- * timeout_ms (the kernel then stops at that barrier; results are invalid),
- * RFM_ENUMERIC is reported through report.status. */
+ * The call is asynchronous: a device-side wait (grid barrier or the wait of
+ * a forward tile on its block) that runs longer than timeout_ms ends the
+ * kernel at that wait, and every report's status is then RFM_ETIMEOUT
+ * (results invalid); a non-finite recurrence gives RFM_ENUMERIC there. */
 rfm_status rfm_lsqr_solve(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const rfm_lsqr_opts *opts,
                           const double *d_y0, double *d_y, double *d_a, rfm_lsqr_report *d_report,
                           void *d_ws, size_t ws_bytes, void *stream);
@@ -359,8 +360,13 @@ int rfm_profile_read(const char **names, int64_t *launches, double *ms, int max)
  *    48 significant bits, on the FP32 pipe; the reflector scalars, norms fed
  *    to the threshold test and R are formed in FP64) unless Q_hat is wanted in
  *    FP64; 0 uses FP64 arithmetic for them too.  FP64-assembled blocks always
- *    use FP64 arithmetic. */
-enum { RFM_OPT_FILTER_KERNEL = 0, RFM_OPT_AUTOTUNE = 1, RFM_OPT_QR_DOUBLE_FLOAT = 2 };
+ *    use FP64 arithmetic.
+ *  RFM_OPT_LSQR_STALL (test hook for failure detection): 1 makes the first
+ *    grid barrier of the next explicit-operator solves wait for an arrival
+ *    that never comes, 2 makes their forward tiles wait for a chunk that never
+ *    finishes; the bounded waits then run out after timeout_ms, the kernel
+ *    leaves and the report's status is RFM_ETIMEOUT.  0 (default) is off. */
+enum { RFM_OPT_FILTER_KERNEL = 0, RFM_OPT_AUTOTUNE = 1, RFM_OPT_QR_DOUBLE_FLOAT = 2, RFM_OPT_LSQR_STALL = 3 };
 rfm_status rfm_set_option(int option, int value);
 
 const char *rfm_last_error(void);

@@ -171,6 +171,12 @@ def set_autotune(on: bool):
     check("rfm_set_option", load().rfm_set_option(1, 1 if on else 0))
 
 
+def set_lsqr_stall(mode: int):
+    """Test hook (RFM_OPT_LSQR_STALL): 1 or 2 make the next solves' bounded
+    waits run out (first grid barrier, or the forward tiles' waits); 0 is off."""
+    check("rfm_set_option", load().rfm_set_option(3, int(mode)))
+
+
 def set_qr_double_float(on: bool):
     """Factor FP32-assembled blocks with double-float arithmetic (True, the
     default) or with FP64 arithmetic (False) (RFM_OPT_QR_DOUBLE_FLOAT)."""

@@ -51,6 +51,7 @@ struct LsqrArgs {
     double *phase_ms;        // per-phase times of CTA 0 (nullable)
     int64_t n_block_rows;
     unsigned long long *bcnt;  // per block: chunks of the transposed product finished (fused products)
+    int stall;               // test hook: 1 = the first grid barrier, 2 = the forward tiles' waits never release
     int x_cap;               // staging row length of the forward tiles (>= every rank)
 };
 
@@ -105,7 +106,9 @@ struct Ring {
 };
 
 // Bounded grid barrier.  Returns false when any CTA has reported an error.
-__device__ bool grid_sync(unsigned *bar, uint64_t timeout_ns) {
+// extra > 0 raises the arrival count that releases it beyond the grid (a
+// barrier nothing releases: the test hook of RFM_OPT_LSQR_STALL).
+__device__ bool grid_sync(unsigned *bar, uint64_t timeout_ns, unsigned extra = 0) {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned *vgen = bar + 1;
@@ -113,7 +116,7 @@ __device__ bool grid_sync(unsigned *bar, uint64_t timeout_ns) {
         unsigned g = *vgen;
         __threadfence();
         unsigned arrived = atomicAdd(bar, 1u);
-        if (arrived == gridDim.x - 1) {
+        if (arrived == gridDim.x - 1 + extra) {
             atomicExch(bar, 0u);
             __threadfence();
             atomicAdd(bar + 1, 1u);
@@ -800,6 +803,9 @@ __device__ __forceinline__ double ld_hint(const double *p, uint64_t pol) {
     return r;
 }
 
+static int g_lsqr_stall = 0;
+void set_lsqr_stall(int v) { g_lsqr_stall = v; }
+
 template <typename TA>
 struct TileSmem {
     double wacc[2][kThreads / 32][64];          // per-warp partials per instance (alpha^2, ||y||^2)
@@ -1169,7 +1175,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
                 if (r > 0) {
                     // every chunk of the block is released once per phase
                     if (lane == 0) {
-                        const unsigned long long target = phase * (unsigned long long)((r + kColTile - 1) / kColTile);
+                        const unsigned long long target =
+                            phase * (unsigned long long)((r + kColTile - 1) / kColTile) + (a.stall == 2 ? 1ull : 0ull);
                         volatile unsigned long long *cp = a.bcnt + it.b;
                         const uint64_t t0 = global_ns();
                         unsigned spins = 0;
@@ -1417,7 +1424,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
         if (!ok) return;
         forward(all_inst, vx, [](int) { return 1.0; });
     }
-    ok = grid_sync(a.bar, a.timeout_ns);
+    ok = grid_sync(a.bar, a.timeout_ns, a.stall == 1 ? 1u : 0u);
     // u~ = h - (Op y0), ||u~||^2, ||h||^2; u~ copied onto the block rows
     clear(S.acc_b);
     clear(S.hacc);
@@ -1759,6 +1766,7 @@ static void fill_args(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, co
     A.btol = opts->btol;
     A.max_iter = opts->max_iter;
     A.timeout_ns = (uint64_t)(opts->timeout_ms > 0 ? opts->timeout_ms : 10000) * 1000000ull;
+    A.stall = g_lsqr_stall;
     int64_t nt = 0;
     for (int s = 0; s < L.n_inst; ++s) nt += (P.inst[s].N + kRowTile - 1) / kRowTile;
     A.n_row_tiles = nt;
