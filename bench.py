@@ -402,6 +402,19 @@ def run_learned(args, dev):
     W.theta[-129:] *= scale
     n_samples = int(X.shape[0])
     del X, T, Xs, Ts
+    # forward throughput of the network (the tensor-core kernel for this shape), 2^22 samples
+    Xf = torch.empty((1 << 22, 9), device=dev).uniform_(-1, 1)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    W.net.forward(W.theta, Xf)
+    ev0.record()
+    for _ in range(5):
+        W.net.forward(W.theta, Xf)
+    ev1.record()
+    torch.cuda.synchronize()
+    fwd_s = ev0.elapsed_time(ev1) / 5e3
+    fwd = {"samples_per_s": Xf.shape[0] / fwd_s, "tflops": 2.0 * W.net.n_params * Xf.shape[0] / fwd_s / 1e12,
+           "kernel": "k_mlp_fwd_tc (tcgen05, BF16 operands, FP32 accumulation)"}
+    del Xf
 
     held = fam(range(10000, 10008))
     d = params(held)
@@ -426,7 +439,6 @@ def run_learned(args, dev):
     pl = (pred.double() * scale_rows).index_select(0, live)
     tl = torch.cat(ub).index_select(0, live)
     pred_err = float(torch.linalg.norm(pl - tl) / torch.linalg.norm(tl))
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
     y0 = W.warm_start(S, ctx(held), fit_iters=300, inst_scale=inv)
     ev1.record()
@@ -454,7 +466,9 @@ def run_learned(args, dev):
         "workload": f"2D Poisson, f = sin(a pi x) sin(b pi y) + c sin(d pi x + e pi y), {S_}x{S_} subdomains, "
                     f"overlap ratio {D_}, K={K_}, {n}^2 interior + boundary rows, filter tol {TOL:g}, "
                     f"mixed path; 8 held-out instances (seeds 10000-10007)",
-        "network": "9 -> 128 x4 (tanh) -> 1, FP32, Adam lr 2e-3 -> 1e-4, batch 4096, targets x pi^2 (a^2+b^2)",
+        "network": "9 -> 128 x4 (tanh) -> 1, trained in FP32 (Adam lr 2e-3 -> 1e-4, batch 4096, targets x pi^2 "
+                   "(a^2+b^2)), prediction on the tensor cores",
+        "forward": fwd,
         "training_solves": ntr, "training_lsqr_iterations": train_iters, "training_samples": n_samples,
         "epochs": epochs, "data_s": t_data, "train_s": t_train, "train_samples_per_s": n_samples * epochs / t_train,
         "loss_first_last": [hist[0], hist[-1]],

@@ -365,8 +365,17 @@ int rfm_profile_read(const char **names, int64_t *launches, double *ms, int max)
  *    grid barrier of the next explicit-operator solves wait for an arrival
  *    that never comes, 2 makes their forward tiles wait for a chunk that never
  *    finishes; the bounded waits then run out after timeout_ms, the kernel
- *    leaves and the report's status is RFM_ETIMEOUT.  0 (default) is off. */
-enum { RFM_OPT_FILTER_KERNEL = 0, RFM_OPT_AUTOTUNE = 1, RFM_OPT_QR_DOUBLE_FLOAT = 2, RFM_OPT_LSQR_STALL = 3 };
+ *    leaves and the report's status is RFM_ETIMEOUT.  0 (default) is off.
+ *  RFM_OPT_MLP_TENSOR_CORES: 1 (default) runs rfm_mlp_forward on the tensor
+ *    cores (tcgen05, BF16 operands, FP32 accumulation) when every hidden
+ *    layer is 128 wide; 0 keeps the FP32 kernel for every network. */
+enum {
+    RFM_OPT_FILTER_KERNEL = 0,
+    RFM_OPT_AUTOTUNE = 1,
+    RFM_OPT_QR_DOUBLE_FLOAT = 2,
+    RFM_OPT_LSQR_STALL = 3,
+    RFM_OPT_MLP_TENSOR_CORES = 4
+};
 rfm_status rfm_set_option(int option, int value);
 
 const char *rfm_last_error(void);

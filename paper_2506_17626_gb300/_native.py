@@ -177,6 +177,12 @@ def set_lsqr_stall(mode: int):
     check("rfm_set_option", load().rfm_set_option(3, int(mode)))
 
 
+def set_mlp_tensor_cores(on: bool):
+    """Network forward on the tensor cores when every hidden layer is 128 wide
+    (True, the default) or always in FP32 (False) (RFM_OPT_MLP_TENSOR_CORES)."""
+    check("rfm_set_option", load().rfm_set_option(4, 1 if on else 0))
+
+
 def set_qr_double_float(on: bool):
     """Factor FP32-assembled blocks with double-float arithmetic (True, the
     default) or with FP64 arithmetic (False) (RFM_OPT_QR_DOUBLE_FLOAT)."""

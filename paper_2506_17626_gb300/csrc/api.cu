@@ -18,6 +18,7 @@ void set_force_global_filter(int on);
 void set_autotune(int on);
 void set_qr_double_float(int on);
 void set_lsqr_stall(int v);
+void set_mlp_tensor_cores(int on);
 rfm_status launch_eval_noalloc(const HostPlan &P, const double *params, const double *a, const double *X,
                                const int64_t *pt_off, double *u, double *err, cudaStream_t st);
 rfm_status launch_eval(const HostPlan &P, void *ws, const double *params, const double *a, const double *X,
@@ -226,6 +227,10 @@ rfm_status rfm_set_option(int option, int value) {
     }
     if (option == RFM_OPT_LSQR_STALL && value >= 0 && value <= 2) {
         set_lsqr_stall(value);
+        return RFM_OK;
+    }
+    if (option == RFM_OPT_MLP_TENSOR_CORES && (value == 0 || value == 1)) {
+        set_mlp_tensor_cores(value);
         return RFM_OK;
     }
     set_error("rfm_set_option: unknown option %d or value %d", option, value);

@@ -13,6 +13,8 @@
 // sums the slices in a fixed order (the result does not depend on timing).
 #include <math.h>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "prof.cuh"
 
@@ -328,6 +330,196 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     (void)red;
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core forward pass (tcgen05) for networks whose hidden layers are all
+// 128 wide: 128 samples per tile (one per TMEM lane), 128 threads.  The
+// 128 x 128 hidden layers run as BF16 x BF16 -> FP32 MMAs: the activations of
+// the tile (A, 128 samples x 128 features) and W_l (B, 128 outputs x 128
+// inputs) sit in shared memory in the canonical K-major layout without
+// swizzle -- 8 x 8 BF16 core matrices of 128 contiguous bytes, the next core
+// matrix along K 128 bytes on, along the rows 16 core matrices on -- and the
+// product lands in tensor memory; each warp reads back its 32 rows, adds the
+// bias, applies tanh and writes the next layer's BF16 operand.  The first
+// layer (input width <= 32) and the scalar output layer run on the FP32 pipe.
+// One thread issues the MMAs; their completion is awaited on an mbarrier
+// with a bounded wait (on expiry the kernel writes NaN outputs).
+// ---------------------------------------------------------------------------
+constexpr int kTcM = 128;        // samples per tile = TMEM lanes
+constexpr int kTcW = 128;        // hidden width of the tensor-core path
+constexpr int kTcMaxMma = kMlpMaxLayers - 2;
+
+__device__ inline unsigned tc_su32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// byte offset of element (r, k) of a 128-column K-major operand
+__device__ inline int tc_off(int r, int k) { return ((r >> 3) * (kTcW / 8) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+
+__device__ inline uint64_t tc_desc(const void *base) {
+    uint64_t d = (uint64_t)((tc_su32(base) >> 4) & 0x3FFF);
+    d |= (uint64_t)(128 >> 4) << 16;                 // leading byte offset: next core matrix along K
+    d |= (uint64_t)((kTcW / 8 * 128) >> 4) << 32;    // stride byte offset: next 8 rows
+    d |= (uint64_t)1 << 46;                          // descriptor version
+    return d;                                        // base offset 0, no swizzle
+}
+
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, K-major, M x N
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcW >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+
+__device__ inline bool tc_wait(uint64_t *mbar, unsigned parity) {
+    for (long it = 0; it < (1l << 26); ++it) {
+        unsigned d;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(d) : "r"(tc_su32(mbar)), "r"(parity) : "memory");
+        if (d) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kTcM, 1) k_mlp_fwd_tc(MlpDesc D, const float *__restrict__ theta,
+                                                        const float *__restrict__ X, int64_t n, float *__restrict__ Y) {
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    const int L = D.L, n_mma = L - 2, w0 = D.w[0];
+    unsigned char *sWm = tsm;                                  // n_mma x 32 KB: W_2 .. W_{L-1} (BF16)
+    unsigned char *sAct = sWm + (size_t)n_mma * kTcW * kTcW * 2;   // 2 x 32 KB: activations (BF16)
+    float *sW1 = reinterpret_cast<float *>(sAct + 2 * kTcM * kTcW * 2);   // kTcW x w0
+    float *sB = sW1 + kTcW * w0;                               // biases of layers 1 .. L-1 (kTcW each)
+    float *sWL = sB + (L - 1) * kTcW;                          // output weights (kTcW) and bias
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // weights once per CTA
+    for (int l = 2; l < L; ++l) {
+        const float *W = theta + D.off[l];
+        unsigned char *dst = sWm + (size_t)(l - 2) * kTcW * kTcW * 2;
+        for (int e = tid; e < kTcW * kTcW; e += kTcM) {
+            const int o = e / kTcW, i = e % kTcW;
+            *reinterpret_cast<__nv_bfloat16 *>(dst + tc_off(o, i)) = __float2bfloat16_rn(__ldg(W + e));
+        }
+    }
+    for (int e = tid; e < kTcW * w0; e += kTcM) sW1[e] = __ldg(theta + D.off[1] + e);
+    for (int l = 1; l < L; ++l)
+        for (int o = tid; o < kTcW; o += kTcM) sB[(l - 1) * kTcW + o] = __ldg(theta + D.off[l] + (int64_t)kTcW * D.w[l - 1] + o);
+    for (int i = tid; i <= kTcW; i += kTcM) sWL[i] = __ldg(theta + D.off[L] + i);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_su32(&mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_su32(&tmem_base)), "r"(kTcW) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    unsigned parity = 0;
+    bool ok = true;
+    const int64_t n_tiles = (n + kTcM - 1) / kTcM;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t s = tile * kTcM + tid;   // this thread's sample (row)
+        // layer 1 on the FP32 pipe: h_1 = tanh(W_1 x + b_1), written as BF16 operand
+        {
+            float x[kMlpMaxIn];
+#pragma unroll
+            for (int i = 0; i < kMlpMaxIn; ++i) x[i] = (i < w0 && s < n) ? __ldg(X + s * w0 + i) : 0.f;
+            unsigned char *A0 = sAct;
+            for (int o0 = 0; o0 < kTcW; o0 += 8) {
+                __align__(16) __nv_bfloat16 hv[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int o = o0 + j;
+                    float t = sB[o];
+                    for (int i = 0; i < w0; ++i) t = fmaf(sW1[o * w0 + i], x[i], t);
+                    hv[j] = __float2bfloat16_rn(tanhf(t));
+                }
+                *reinterpret_cast<uint4 *>(A0 + tc_off(tid, o0)) = *reinterpret_cast<const uint4 *>(hv);
+            }
+        }
+        float yv = 0.f;
+        for (int l = 2; l < L; ++l) {
+            const unsigned char *Ain = sAct + (size_t)((l - 2) & 1) * kTcM * kTcW * 2;
+            unsigned char *Aout = sAct + (size_t)((l - 1) & 1) * kTcM * kTcW * 2;
+            // operands written by the generic proxy -> visible to the MMA
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (tid == 0) {
+                const unsigned char *Bw = sWm + (size_t)(l - 2) * kTcW * kTcW * 2;
+                for (int kk = 0; kk < kTcW / 16; ++kk) {
+                    const uint64_t da = tc_desc(Ain + kk * 256), db = tc_desc(Bw + kk * 256);
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                        ::"r"(tmem), "l"(da), "l"(db), "r"(kTcIdesc), "r"(kk > 0 ? 1u : 0u) : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(tc_su32(&mbar)) : "memory");
+            }
+            const bool got = __syncthreads_and(tc_wait(&mbar, parity));   // the same decision in every thread
+            if (!got) {
+                tc_wait(&mbar, parity);   // a second bounded wait for MMAs still in flight before TMEM is freed
+                ok = false;
+                break;
+            }
+            parity ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const float *bl = sB + (l - 1) * kTcW;
+            const bool last = l == L - 1;
+            for (int c0 = 0; c0 < kTcW; c0 += 32) {
+                uint32_t r[32];
+                const uint32_t addr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                      "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                      "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(addr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    __align__(16) __nv_bfloat16 hv[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int o = c0 + 8 * g + j;
+                        const float h = tanhf(__uint_as_float(r[8 * g + j]) + bl[o]);
+                        if (last) yv = fmaf(h, sWL[o], yv);
+                        else hv[j] = __float2bfloat16_rn(h);
+                    }
+                    if (!last) *reinterpret_cast<uint4 *>(Aout + tc_off(tid, c0 + 8 * g)) = *reinterpret_cast<const uint4 *>(hv);
+                }
+            }
+        }
+        if (!ok) break;
+        if (s < n) Y[s] = yv + sWL[kTcW];
+    }
+    if (!ok) {
+        for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+            const int64_t s = tile * kTcM + tid;
+            if (s < n) Y[s] = __int_as_float(0x7fc00000);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcW) : "memory");
+}
+
+static bool mlp_tc_shape(const MlpDesc &D) {
+    if (D.L < 3) return false;
+    for (int l = 1; l < D.L; ++l)
+        if (D.w[l] != kTcW) return false;
+    return D.w[0] <= kMlpMaxIn;
+}
+
+static size_t mlp_tc_smem(const MlpDesc &D) {
+    return (size_t)(D.L - 2) * kTcW * kTcW * 2 + 2 * (size_t)kTcM * kTcW * 2 +
+           4 * ((size_t)kTcW * D.w[0] + (size_t)(D.L - 1) * kTcW + kTcW + 1) + 64;
+}
+
+static int g_mlp_tc = 1;
+void set_mlp_tensor_cores(int on) { g_mlp_tc = on; }
+
 // grad[p] = sum over CTA slices (fixed order); loss = sum of partials / n.
 __global__ void k_mlp_reduce(const float *__restrict__ gpart, int nslices, int64_t np, float *__restrict__ grad,
                              const double *__restrict__ lpart, float *__restrict__ loss, double inv_n) {
@@ -390,6 +582,19 @@ rfm_status launch_mlp_forward(const rfm_mlp *net, const float *theta, const floa
     rfm_status rc = mlp_desc(net, &D);
     if (rc != RFM_OK) return rc;
     if (n <= 0) return RFM_OK;
+    if (g_mlp_tc && mlp_tc_shape(D) && mlp_tc_smem(D) <= 200 * 1024) {
+        const size_t smem = mlp_tc_smem(D);
+        RFM_CUDA_CHECK(cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int dev = 0, nsm = 0;
+        RFM_CUDA_CHECK(cudaGetDevice(&dev));
+        RFM_CUDA_CHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        const int64_t tiles = (n + kTcM - 1) / kTcM;
+        const int grid = (int)(tiles < nsm ? tiles : nsm);
+        ProfScope ps("k_mlp_fwd_tc", st);
+        k_mlp_fwd_tc<<<grid, kTcM, smem, st>>>(D, theta, X, n, Y);
+        RFM_CUDA_CHECK(cudaGetLastError());
+        return RFM_OK;
+    }
     const size_t smem = (size_t)D.smem_floats * 4;
     RFM_CUDA_CHECK(cudaFuncSetAttribute(k_mlp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, nsm = 0;

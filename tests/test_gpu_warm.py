@@ -1,7 +1,9 @@
 """Learned warm start on the GPU against the oracle, through the C ABI.
 
 Network (FP32 kernels vs the FP64 oracle on the same FP32 parameters and
-inputs, upcast exactly): outputs within 2e-5 of the largest output; the
+inputs, upcast exactly): outputs within 2e-5 of the largest output (the
+tensor-core forward: the same BF16 arithmetic emulated in numpy to 1e-5 in
+the median and 5e-3 at worst, the oracle to 3e-2); the
 gradient within 2e-4 of its largest entry (FP32 sums over 64-sample tiles and
 per-CTA slices); Adam within 1e-6 relative.  Ragged batches, batches spanning
 several tiles per CTA, and widths from 16 to 128 are covered.
@@ -43,13 +45,73 @@ NETS = [[9, 128, 128, 128, 128, 1], [3, 16, 1], [5, 48, 32, 1], [32, 1], [1, 64,
 @pytest.mark.parametrize("widths", NETS)
 @pytest.mark.parametrize("n", [1, 63, 200])
 def test_forward_matches_oracle(rfm, widths, n):
+    from paper_2506_17626_gb300 import _native as N
     M = rfm.Mlp(widths)
     assert M.n_params == oracle.mlp_nparams(widths)
     th = _net(widths, len(widths) + n, scale=0.3)
     X = np.random.default_rng(n).uniform(-1, 1, (n, widths[0])).astype(np.float32)
-    y = M.forward(torch.from_numpy(th).cuda(), torch.from_numpy(X).cuda()).cpu().numpy()
+    N.set_mlp_tensor_cores(False)   # the FP32 kernel
+    try:
+        y = M.forward(torch.from_numpy(th).cuda(), torch.from_numpy(X).cuda()).cpu().numpy()
+    finally:
+        N.set_mlp_tensor_cores(True)
     ref = oracle.mlp_forward(widths, th.astype(np.float64), X.astype(np.float64))
     assert np.abs(y - ref).max() <= 2e-5 * max(1.0, np.abs(ref).max())
+
+
+def _bf16(a):
+    """Round FP32 values to BF16 (nearest, ties to even), returned as float64."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _forward_bf16(widths, th, X):
+    """The tensor-core path's arithmetic: layer 1 and the output layer in
+    FP32-like precision, the 128-wide hidden layers with BF16 weights and BF16
+    activations, sums in high precision."""
+    L = len(widths) - 1
+    o = 0
+    layers = []
+    for l in range(1, L + 1):
+        no, ni = widths[l], widths[l - 1]
+        W = th[o:o + no * ni].astype(np.float64).reshape(no, ni)
+        b = th[o + no * ni:o + no * ni + no].astype(np.float64)
+        layers.append((W, b))
+        o += no * ni + no
+    h = np.tanh(X.astype(np.float64) @ layers[0][0].T + layers[0][1])
+    for l in range(1, L - 1):
+        W, b = layers[l]
+        h = np.tanh(_bf16(h) @ _bf16(W).T + b)
+    W, b = layers[L - 1]
+    return h @ W[0] + b[0]
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 1000, 20011])
+def test_tensor_core_forward(rfm, n):
+    """tcgen05 forward of the 9-128x4-1 network: against the same arithmetic
+    with BF16 operands emulated in numpy -- the median error within 1e-5 of
+    the largest output and all but 1 + 1% of the samples within 1e-4 (FP32
+    accumulation and tanhf against FP64), the largest within 5e-3 (a BF16
+    rounding of an activation that tips the other way between tanhf and the
+    FP64 tanh moves it by 2^-8, amplified by the later layers; measured up to
+    1.7e-3) -- and against the
+    FP64 oracle within 3e-2 (BF16 keeps 8 bits, 2^-8 relative per operand
+    through three layers; measured up to 8.7e-3)."""
+    widths = [9, 128, 128, 128, 128, 1]
+    M = rfm.Mlp(widths)
+    th = _net(widths, 5 + n, scale=0.3)
+    X = np.random.default_rng(100 + n).uniform(-1, 1, (n, 9)).astype(np.float32)
+    y = M.forward(torch.from_numpy(th).cuda(), torch.from_numpy(X).cuda()).cpu().numpy()
+    assert np.all(np.isfinite(y))
+    emu = _forward_bf16(widths, th, X)
+    ref = oracle.mlp_forward(widths, th.astype(np.float64), X.astype(np.float64))
+    scale = max(1.0, np.abs(ref).max())
+    err = np.abs(y - emu)
+    assert np.median(err) <= 1e-5 * scale
+    assert np.count_nonzero(err > 1e-4 * scale) <= 1 + n // 100
+    assert err.max() <= 5e-3 * scale
+    assert np.abs(y - ref).max() <= 3e-2 * scale
 
 
 @pytest.mark.parametrize("widths,n", [([9, 128, 128, 128, 128, 1], 130), ([9, 128, 128, 128, 128, 1], 1000),
