@@ -297,14 +297,17 @@ typedef struct {
 /* Parameter count and the workspace bytes of rfm_mlp_grad (any batch size). */
 rfm_status rfm_mlp_size(const rfm_mlp *net, int64_t *n_params, size_t *ws_bytes);
 
-/* d_y[i] = network(d_x[i, :]) for n samples (d_x row-major n x width[0]). */
+/* d_y[i] = network(d_x[i, :]) for n samples (d_x row-major n x width[0]).
+ * On the tensor-core path (RFM_OPT_MLP_TENSOR_CORES) a wait for the MMAs
+ * that runs out (about a second) leaves NaN in the CTA's outputs. */
 rfm_status rfm_mlp_forward(const rfm_mlp *net, const float *d_theta, const float *d_x, int64_t n, float *d_y,
                            void *stream);
 
 /* Mean squared error (1/n) sum_i (network(x_i) - t_i)^2 over the batch and its
  * gradient (n_params floats) by backpropagation; d_loss (1 float, may be
  * NULL).  The per-CTA partial gradients are summed in a fixed order, so the
- * result is reproducible on a given GPU. */
+ * result is reproducible on a given GPU.  On the tensor-core path a wait for
+ * the MMAs that runs out leaves NaN in the gradient and the loss. */
 rfm_status rfm_mlp_grad(const rfm_mlp *net, const float *d_theta, const float *d_x, const float *d_t, int64_t n,
                         float *d_grad, float *d_loss, void *d_ws, size_t ws_bytes, void *stream);
 
@@ -366,9 +369,12 @@ int rfm_profile_read(const char **names, int64_t *launches, double *ms, int max)
  *    that never comes, 2 makes their forward tiles wait for a chunk that never
  *    finishes; the bounded waits then run out after timeout_ms, the kernel
  *    leaves and the report's status is RFM_ETIMEOUT.  0 (default) is off.
- *  RFM_OPT_MLP_TENSOR_CORES: 1 (default) runs rfm_mlp_forward on the tensor
- *    cores (tcgen05, BF16 operands, FP32 accumulation) when every hidden
- *    layer is 128 wide; 0 keeps the FP32 kernel for every network. */
+ *  RFM_OPT_MLP_TENSOR_CORES: 1 (default) runs rfm_mlp_forward and
+ *    rfm_mlp_grad on the tensor cores (tcgen05, BF16 operands, FP32
+ *    accumulation) when every hidden layer is 128 wide (rfm_mlp_grad: one to
+ *    three 128 x 128 layers and fewer than 32 inputs); results then carry
+ *    BF16 rounding (about 1e-2 relative).  0 keeps the FP32 kernels for every
+ *    network. */
 enum {
     RFM_OPT_FILTER_KERNEL = 0,
     RFM_OPT_AUTOTUNE = 1,

@@ -332,21 +332,21 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
 
 // ---------------------------------------------------------------------------
 // Tensor-core forward pass (tcgen05) for networks whose hidden layers are all
-// 128 wide: 128 samples per tile (one per TMEM lane), 128 threads.  The
+// 128 wide: 128 samples per tile (one per TMEM lane), 256 threads (warps w
+// and w + 4 read the same 32 TMEM lanes and split the 128 columns).  The
 // 128 x 128 hidden layers run as BF16 x BF16 -> FP32 MMAs: the activations of
 // the tile (A, 128 samples x 128 features) and W_l (B, 128 outputs x 128
 // inputs) sit in shared memory in the canonical K-major layout without
 // swizzle -- 8 x 8 BF16 core matrices of 128 contiguous bytes, the next core
 // matrix along K 128 bytes on, along the rows 16 core matrices on -- and the
-// product lands in tensor memory; each warp reads back its 32 rows, adds the
-// bias, applies tanh and writes the next layer's BF16 operand.  The first
+// product lands in tensor memory; each thread reads back half a row, adds
+// the bias, applies tanh and writes the next layer's BF16 operand.  The first
 // layer (input width <= 32) and the scalar output layer run on the FP32 pipe.
 // One thread issues the MMAs; their completion is awaited on an mbarrier
 // with a bounded wait (on expiry the kernel writes NaN outputs).
 // ---------------------------------------------------------------------------
 constexpr int kTcM = 128;        // samples per tile = TMEM lanes
 constexpr int kTcW = 128;        // hidden width of the tensor-core path
-constexpr int kTcMaxMma = kMlpMaxLayers - 2;
 
 __device__ inline unsigned tc_su32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -361,9 +361,6 @@ __device__ inline uint64_t tc_desc(const void *base) {
     return d;                                        // base offset 0, no swizzle
 }
 
-// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, K-major, M x N
-constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcW >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
-
 __device__ inline bool tc_wait(uint64_t *mbar, unsigned parity) {
     for (long it = 0; it < (1l << 26); ++it) {
         unsigned d;
@@ -374,31 +371,142 @@ __device__ inline bool tc_wait(uint64_t *mbar, unsigned parity) {
     return false;
 }
 
-__global__ void __launch_bounds__(kTcM, 1) k_mlp_fwd_tc(MlpDesc D, const float *__restrict__ theta,
-                                                        const float *__restrict__ X, int64_t n, float *__restrict__ Y) {
+constexpr int kTgThreads = 256;
+constexpr int kTgMaxMma = 3;
+constexpr int kTgN1 = 32;        // first-layer product columns: inputs, a ones row, zero padding
+constexpr int kTgTile = kTcM * kTcW * 2;   // bytes of one 128 x 128 BF16 operand
+
+__device__ inline uint64_t tc_desc_mn(const void *base) {
+    uint64_t d = (uint64_t)((tc_su32(base) >> 4) & 0x3FFF);
+    d |= (uint64_t)((kTcW / 8 * 128) >> 4) << 16;   // leading byte offset: next 8 along K (the stored rows)
+    d |= (uint64_t)(128 >> 4) << 32;                 // stride byte offset: next 8 along M / N (the stored columns)
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// kind::f16 instruction descriptor with N columns; a_mn / b_mn select MN-major operands
+__host__ __device__ constexpr uint32_t tc_idesc(int n, int a_mn, int b_mn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+}
+
+__device__ inline void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+
+__device__ inline void tc_commit(uint64_t *mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(tc_su32(mbar)) : "memory");
+}
+
+// operands written through the generic proxy become visible to the MMAs, and
+// every earlier TMEM read of the CTA is ordered before them
+__device__ inline void tc_sync_for_mma() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// bounded wait for the round's commit, the same decision in every thread; on
+// expiry a second bounded wait for MMAs still in flight
+__device__ inline bool tc_round_wait(uint64_t *mbar, unsigned &parity) {
+    const bool got = __syncthreads_and(tc_wait(mbar, parity));
+    if (!got) {
+        tc_wait(mbar, parity);
+        return false;
+    }
+    parity ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return true;
+}
+
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes
+__device__ inline void tc_ld32(uint32_t addr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// v[j] summed over the warp's 32 lanes for every j; lane j returns column j
+// (five halving exchanges: at each the lanes keep one half and add the
+// partner's copy of it)
+__device__ inline float warp_transpose_sum(float (&v)[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) {
+        const bool up = (lane & k) != 0;
+#pragma unroll
+        for (int j = 0; j < k; ++j) {
+            const float send = up ? v[j] : v[j + k];
+            const float keep = up ? v[j + k] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, k);
+        }
+    }
+    return v[0];
+}
+
+__device__ inline void bf16x8_load(const unsigned char *p, float (&h)[8]) {
+    const uint4 u = *reinterpret_cast<const uint4 *>(p);
+    const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float2 f = __bfloat1622float2(b[j]);
+        h[2 * j] = f.x;
+        h[2 * j + 1] = f.y;
+    }
+}
+
+__device__ inline void bf16x8_store(unsigned char *p, const float (&h)[8]) {
+    __align__(16) __nv_bfloat162 b[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = __floats2bfloat162_rn(h[2 * j], h[2 * j + 1]);
+    *reinterpret_cast<uint4 *>(p) = *reinterpret_cast<const uint4 *>(b);
+}
+
+constexpr int kTcThreads = 256;
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(MlpDesc D, const float *__restrict__ theta,
+                                                              const float *__restrict__ X, int64_t n,
+                                                              float *__restrict__ Y) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     const int L = D.L, n_mma = L - 2, w0 = D.w[0];
     unsigned char *sWm = tsm;                                  // n_mma x 32 KB: W_2 .. W_{L-1} (BF16)
-    unsigned char *sAct = sWm + (size_t)n_mma * kTcW * kTcW * 2;   // 2 x 32 KB: activations (BF16)
-    float *sW1 = reinterpret_cast<float *>(sAct + 2 * kTcM * kTcW * 2);   // kTcW x w0
+    unsigned char *sAct = sWm + (size_t)n_mma * kTgTile;       // 2 x 32 KB: activations (BF16)
+    float *sW1 = reinterpret_cast<float *>(sAct + 2 * kTgTile);   // kTcW x w0
     float *sB = sW1 + kTcW * w0;                               // biases of layers 1 .. L-1 (kTcW each)
     float *sWL = sB + (L - 1) * kTcW;                          // output weights (kTcW) and bias
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
+    __shared__ float sY[2][kTcM];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = 32 * (warp & 3) + lane, cb = 64 * (warp >> 2);
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
     // weights once per CTA
     for (int l = 2; l < L; ++l) {
         const float *W = theta + D.off[l];
-        unsigned char *dst = sWm + (size_t)(l - 2) * kTcW * kTcW * 2;
-        for (int e = tid; e < kTcW * kTcW; e += kTcM) {
+        unsigned char *dst = sWm + (size_t)(l - 2) * kTgTile;
+        for (int e = tid; e < kTcW * kTcW; e += kTcThreads) {
             const int o = e / kTcW, i = e % kTcW;
             *reinterpret_cast<__nv_bfloat16 *>(dst + tc_off(o, i)) = __float2bfloat16_rn(__ldg(W + e));
         }
     }
-    for (int e = tid; e < kTcW * w0; e += kTcM) sW1[e] = __ldg(theta + D.off[1] + e);
+    for (int e = tid; e < kTcW * w0; e += kTcThreads) sW1[e] = __ldg(theta + D.off[1] + e);
     for (int l = 1; l < L; ++l)
-        for (int o = tid; o < kTcW; o += kTcM) sB[(l - 1) * kTcW + o] = __ldg(theta + D.off[l] + (int64_t)kTcW * D.w[l - 1] + o);
-    for (int i = tid; i <= kTcW; i += kTcM) sWL[i] = __ldg(theta + D.off[L] + i);
+        for (int o = tid; o < kTcW; o += kTcThreads) sB[(l - 1) * kTcW + o] = __ldg(theta + D.off[l] + (int64_t)kTcW * D.w[l - 1] + o);
+    for (int i = tid; i <= kTcW; i += kTcThreads) sWL[i] = __ldg(theta + D.off[L] + i);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_su32(&mbar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -414,90 +522,69 @@ __global__ void __launch_bounds__(kTcM, 1) k_mlp_fwd_tc(MlpDesc D, const float *
     unsigned parity = 0;
     bool ok = true;
     const int64_t n_tiles = (n + kTcM - 1) / kTcM;
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int64_t s = tile * kTcM + tid;   // this thread's sample (row)
-        // layer 1 on the FP32 pipe: h_1 = tanh(W_1 x + b_1), written as BF16 operand
+    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        const int64_t s = tile * kTcM + row;   // this thread's sample
+        // layer 1 on the FP32 pipe: h_1 = tanh(W_1 x + b_1) over this thread's 64 columns
         {
             float x[kMlpMaxIn];
 #pragma unroll
             for (int i = 0; i < kMlpMaxIn; ++i) x[i] = (i < w0 && s < n) ? __ldg(X + s * w0 + i) : 0.f;
-            unsigned char *A0 = sAct;
-            for (int o0 = 0; o0 < kTcW; o0 += 8) {
-                __align__(16) __nv_bfloat16 hv[8];
+            for (int o0 = cb; o0 < cb + 64; o0 += 8) {
+                float hv[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int o = o0 + j;
                     float t = sB[o];
-                    for (int i = 0; i < w0; ++i) t = fmaf(sW1[o * w0 + i], x[i], t);
-                    hv[j] = __float2bfloat16_rn(tanhf(t));
+#pragma unroll
+                    for (int i = 0; i < kMlpMaxIn; ++i)
+                        if (i < w0) t = fmaf(sW1[o * w0 + i], x[i], t);
+                    hv[j] = tanhf(t);
                 }
-                *reinterpret_cast<uint4 *>(A0 + tc_off(tid, o0)) = *reinterpret_cast<const uint4 *>(hv);
+                bf16x8_store(sAct + tc_off(row, o0), hv);
             }
         }
         float yv = 0.f;
         for (int l = 2; l < L; ++l) {
-            const unsigned char *Ain = sAct + (size_t)((l - 2) & 1) * kTcM * kTcW * 2;
-            unsigned char *Aout = sAct + (size_t)((l - 1) & 1) * kTcM * kTcW * 2;
-            // operands written by the generic proxy -> visible to the MMA
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned char *Ain = sAct + (size_t)((l - 2) & 1) * kTgTile;
+            unsigned char *Aout = sAct + (size_t)((l - 1) & 1) * kTgTile;
+            tc_sync_for_mma();
             if (tid == 0) {
-                const unsigned char *Bw = sWm + (size_t)(l - 2) * kTcW * kTcW * 2;
-                for (int kk = 0; kk < kTcW / 16; ++kk) {
-                    const uint64_t da = tc_desc(Ain + kk * 256), db = tc_desc(Bw + kk * 256);
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                        ::"r"(tmem), "l"(da), "l"(db), "r"(kTcIdesc), "r"(kk > 0 ? 1u : 0u) : "memory");
-                }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                             ::"r"(tc_su32(&mbar)) : "memory");
+                const unsigned char *Bw = sWm + (size_t)(l - 2) * kTgTile;
+                for (int kk = 0; kk < kTcW / 16; ++kk)
+                    tc_mma(tmem, tc_desc(Ain + kk * 256), tc_desc(Bw + kk * 256), tc_idesc(kTcW, 0, 0), kk > 0);
+                tc_commit(&mbar);
             }
-            const bool got = __syncthreads_and(tc_wait(&mbar, parity));   // the same decision in every thread
-            if (!got) {
-                tc_wait(&mbar, parity);   // a second bounded wait for MMAs still in flight before TMEM is freed
+            if (!tc_round_wait(&mbar, parity)) {
                 ok = false;
                 break;
             }
-            parity ^= 1u;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const float *bl = sB + (l - 1) * kTcW;
             const bool last = l == L - 1;
-            for (int c0 = 0; c0 < kTcW; c0 += 32) {
-                uint32_t r[32];
-                const uint32_t addr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-                      "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-                      "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                    : "r"(addr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            for (int c0 = cb; c0 < cb + 64; c0 += 32) {
+                float v[32];
+                tc_ld32(tmem + lane_off + (uint32_t)c0, v);
 #pragma unroll
                 for (int g = 0; g < 4; ++g) {
-                    __align__(16) __nv_bfloat16 hv[8];
+                    float hv[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int o = c0 + 8 * g + j;
-                        const float h = tanhf(__uint_as_float(r[8 * g + j]) + bl[o]);
-                        if (last) yv = fmaf(h, sWL[o], yv);
-                        else hv[j] = __float2bfloat16_rn(h);
+                        hv[j] = tanhf(v[8 * g + j] + bl[o]);
+                        if (last) yv = fmaf(hv[j], sWL[o], yv);
                     }
-                    if (!last) *reinterpret_cast<uint4 *>(Aout + tc_off(tid, c0 + 8 * g)) = *reinterpret_cast<const uint4 *>(hv);
+                    if (!last) bf16x8_store(Aout + tc_off(row, c0 + 8 * g), hv);
                 }
             }
         }
         if (!ok) break;
-        if (s < n) Y[s] = yv + sWL[kTcW];
+        sY[warp >> 2][row] = yv;
+        __syncthreads();
+        if (warp < 4 && s < n) Y[s] = sY[0][row] + sY[1][row] + sWL[kTcW];
     }
     if (!ok) {
         for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-            const int64_t s = tile * kTcM + tid;
-            if (s < n) Y[s] = __int_as_float(0x7fc00000);
+            const int64_t s = tile * kTcM + row;
+            if (warp < 4 && s < n) Y[s] = __int_as_float(0x7fc00000);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -515,6 +602,340 @@ static bool mlp_tc_shape(const MlpDesc &D) {
 static size_t mlp_tc_smem(const MlpDesc &D) {
     return (size_t)(D.L - 2) * kTcW * kTcW * 2 + 2 * (size_t)kTcM * kTcW * 2 +
            4 * ((size_t)kTcW * D.w[0] + (size_t)(D.L - 1) * kTcW + kTcW + 1) + 64;
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core loss gradient (tcgen05) for networks whose hidden layers are
+// all 128 wide, with one to three 128 x 128 layers (L = 3 .. 5).  128
+// samples per tile, 256 threads: the two threads of a sample (warps w and
+// w + 4 share TMEM lanes 32 (w % 4) ..) split the 128 columns of every
+// epilogue.  Every operand stays in the layout the forward pass writes --
+// activations and errors as (sample, feature) and W_l as (output, input),
+// K-major without swizzle -- and the backward pass reads the transposes it
+// needs through MN-major descriptors (the same bytes with the two strides
+// swapped).  Per tile:
+//   forward   layer 1 on the FP32 pipe, the hidden layers as BF16 MMAs into
+//             a 128-column TMEM working region, the scalar output in FP32;
+//   output    e = 2 (y - t) / n; dW_L and db_L; e_{L-1} = e w_L (1 - h^2);
+//   layer l   one round of two MMAs: working = e_l W_l (propagation) and
+//             dW_l += e_l^T h_{l-1} (a 128-column TMEM accumulator that
+//             persists over the CTA's tiles); e_{l-1} = working (1 - h^2);
+//   layer 1   dW_1 and db_1 = e_1^T [x, 1] by one N = 32 MMA, summed over
+//             tiles in registers (thread = output row).
+// Bias gradients of the hidden layers and dW_L are column sums over the
+// tile's samples, formed by transposing warp sums in the epilogues.  h_1 is
+// recomputed in the backward pass, so max(2, L - 2) activation buffers of
+// 32 KB suffice.  The product of 1 - h^2 uses h as the BF16 operand holds
+// it.  Waits are bounded; on expiry the CTA's gradient slice is NaN.
+// ---------------------------------------------------------------------------
+struct TgLayout {
+    int nm, nb;
+    size_t w, buf, x, w1, b, wl, acc, total;
+};
+
+__host__ __device__ inline TgLayout tg_layout(const MlpDesc &D) {
+    TgLayout t;
+    t.nm = D.L - 2;
+    t.nb = t.nm > 2 ? t.nm : 2;
+    t.w = 0;
+    t.buf = t.w + (size_t)t.nm * kTgTile;
+    t.x = t.buf + (size_t)t.nb * kTgTile;
+    t.w1 = t.x + (size_t)kTgN1 * kTcM * 2;
+    t.b = t.w1 + (size_t)kTcW * D.w[0] * 4;
+    t.wl = t.b + (size_t)(D.L - 1) * kTcW * 4;
+    t.acc = t.wl + 132 * 4;
+    t.total = t.acc + (size_t)4 * (t.nm + 1) * kTcW * 4;
+    return t;
+}
+
+__global__ void __launch_bounds__(kTgThreads, 1)
+    k_mlp_grad_tc(MlpDesc D, const float *__restrict__ theta, const float *__restrict__ X,
+                  const float *__restrict__ T, int64_t n, float *__restrict__ gpart, double *__restrict__ lpart,
+                  float inv_n) {
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    const TgLayout Ly = tg_layout(D);
+    const int L = D.L, nm = Ly.nm, w0 = D.w[0];
+    unsigned char *sW = tsm + Ly.w;                                  // W_2 .. W_{L-1}, BF16 (output, input)
+    unsigned char *sBuf = tsm + Ly.buf;                              // activation / error buffers
+    unsigned char *sX = tsm + Ly.x;                                  // [x, 1, 0] as (input, sample), BF16
+    float *sW1 = reinterpret_cast<float *>(tsm + Ly.w1);             // W_1, FP32 (output, input)
+    float *sB = reinterpret_cast<float *>(tsm + Ly.b);               // b_1 .. b_{L-1}
+    float *sWL = reinterpret_cast<float *>(tsm + Ly.wl);             // w_L and b_L
+    float *sAcc = reinterpret_cast<float *>(tsm + Ly.acc);           // per lane group: db_2 .. db_{L-1}, dW_L
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ float sY[2][kTcM];
+    __shared__ double sL[kTgThreads / 32];
+    __shared__ float sE[kTgThreads / 32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = 32 * (warp & 3) + lane;       // sample of the tile (and TMEM lane)
+    const int half = warp >> 2;                   // columns 64 half .. 64 half + 63
+    const int cb = 64 * half;
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+    auto buf = [&](int i) { return sBuf + (size_t)i * kTgTile; };
+    // buffer of h_l: h_1 and h_{L-1} in buffer 0, h_l (2 <= l <= L-2) in buffer l-1;
+    // h_1 is recomputed for the backward pass into buffer 0 (L > 3) or 1 (L = 3)
+    auto hbuf = [&](int l) { return (l == 1 || l == L - 1) ? buf(0) : buf(l - 1); };
+    unsigned char *sR = nm >= 2 ? buf(0) : buf(1);
+
+    for (int l = 2; l < L; ++l) {
+        const float *W = theta + D.off[l];
+        unsigned char *dst = sW + (size_t)(l - 2) * kTgTile;
+        for (int e = tid; e < kTcW * kTcW; e += kTgThreads) {
+            const int o = e / kTcW, i = e % kTcW;
+            *reinterpret_cast<__nv_bfloat16 *>(dst + tc_off(o, i)) = __float2bfloat16_rn(__ldg(W + e));
+        }
+    }
+    for (int e = tid; e < kTcW * w0; e += kTgThreads) sW1[e] = __ldg(theta + D.off[1] + e);
+    for (int l = 1; l < L; ++l)
+        for (int o = tid; o < kTcW; o += kTgThreads)
+            sB[(l - 1) * kTcW + o] = __ldg(theta + D.off[l] + (int64_t)kTcW * D.w[l - 1] + o);
+    for (int i = tid; i <= kTcW; i += kTgThreads) sWL[i] = __ldg(theta + D.off[L] + i);
+    for (int e = tid; e < 4 * (nm + 1) * kTcW; e += kTgThreads) sAcc[e] = 0.f;
+    for (int e = tid; e < kTgN1 * kTcM / 8; e += kTgThreads) reinterpret_cast<uint4 *>(sX)[e] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_su32(&mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_su32(&tmem_base)), "r"(512) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint32_t twork = tmem + lane_off;
+    unsigned parity = 0;
+    bool ok = true, first = true;
+    double lsum = 0.0;
+    float gb_out = 0.f;            // db_L share of this thread (half 0 only)
+    float gW1[kTgN1 / 2];          // dW_1 row `row`, columns 16 half .. 16 half + 15 of [x, 1, 0]
+#pragma unroll
+    for (int j = 0; j < kTgN1 / 2; ++j) gW1[j] = 0.f;
+    float xr[kMlpMaxIn];
+
+    // h_1 of this thread's sample over its 64 columns, rounded to BF16 into dst
+    auto layer1 = [&](unsigned char *dst) {
+        for (int o0 = cb; o0 < cb + 64; o0 += 8) {
+            float hv[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int o = o0 + j;
+                float t = sB[o];
+#pragma unroll
+                for (int i = 0; i < kMlpMaxIn; ++i)
+                    if (i < w0) t = fmaf(sW1[o * w0 + i], xr[i], t);
+                hv[j] = tanhf(t);
+            }
+            bf16x8_store(dst + tc_off(row, o0), hv);
+        }
+    };
+
+    const int64_t n_tiles = (n + kTcM - 1) / kTcM;
+    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        const int64_t s = tile * kTcM + row;
+        const bool valid = s < n;
+#pragma unroll
+        for (int i = 0; i < kMlpMaxIn; ++i) xr[i] = (i < w0 && valid) ? __ldg(X + s * w0 + i) : 0.f;
+        // [x, 1] of the sample as column `row` of the first-layer operand (half 0 writes it)
+        if (half == 0) {
+#pragma unroll
+            for (int i = 0; i < kMlpMaxIn; ++i)
+                if (i <= w0)
+                    *reinterpret_cast<__nv_bfloat16 *>(sX + tc_off(i, row)) =
+                        __float2bfloat16_rn(i < w0 ? xr[i] : (valid ? 1.f : 0.f));
+        }
+        layer1(buf(0));
+        // ---- forward through the hidden 128 x 128 layers
+        float yp = 0.f;
+        for (int l = 2; l < L && ok; ++l) {
+            tc_sync_for_mma();
+            if (tid == 0) {
+                const unsigned char *A = hbuf(l - 1), *Bw = sW + (size_t)(l - 2) * kTgTile;
+                for (int kk = 0; kk < kTcW / 16; ++kk)
+                    tc_mma(tmem, tc_desc(A + kk * 256), tc_desc(Bw + kk * 256), tc_idesc(kTcW, 0, 0), kk > 0);
+                tc_commit(&mbar);
+            }
+            if (!tc_round_wait(&mbar, parity)) {
+                ok = false;
+                break;
+            }
+            const float *bl = sB + (l - 1) * kTcW;
+            unsigned char *out = hbuf(l);
+            const bool last = l == L - 1;
+            for (int c0 = cb; c0 < cb + 64; c0 += 32) {
+                float v[32];
+                tc_ld32(twork + (uint32_t)c0, v);
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    float hv[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int o = c0 + 8 * g + j;
+                        hv[j] = tanhf(v[8 * g + j] + bl[o]);
+                        if (last) yp = fmaf(hv[j], sWL[o], yp);
+                    }
+                    bf16x8_store(out + tc_off(row, c0 + 8 * g), hv);
+                }
+            }
+        }
+        if (!ok) break;
+        // ---- output layer: y, e = 2 (y - t) / n, dW_L, db_L, e_{L-1}
+        sY[half][row] = yp;
+        __syncthreads();
+        const float y = sY[0][row] + sY[1][row] + sWL[kTcW];
+        const float dlt = valid ? y - __ldg(T + s) : 0.f;
+        if (half == 0) {
+            lsum += (double)dlt * (double)dlt;
+            gb_out += 2.f * dlt * inv_n;
+        }
+        const float ey = 2.f * dlt * inv_n;
+        {
+            unsigned char *H = hbuf(L - 1);
+            for (int c0 = cb; c0 < cb + 64; c0 += 32) {
+                float d[32], g[32];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float hb[8];
+                    bf16x8_load(H + tc_off(row, c0 + 8 * q), hb);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int o = c0 + 8 * q + j;
+                        g[8 * q + j] = ey * hb[j];
+                        d[8 * q + j] = ey * sWL[o] * (1.f - hb[j] * hb[j]);
+                    }
+                    float dq[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) dq[j] = d[8 * q + j];
+                    bf16x8_store(H + tc_off(row, c0 + 8 * q), dq);
+                }
+                const float sg = warp_transpose_sum(g);
+                sAcc[((warp & 3) * (nm + 1) + nm) * kTcW + c0 + lane] += sg;
+                const float sd = warp_transpose_sum(d);
+                sAcc[((warp & 3) * (nm + 1) + (L - 1 - 2)) * kTcW + c0 + lane] += sd;
+            }
+        }
+        // ---- backward through the hidden layers: e_l W_l and dW_l += e_l^T h_{l-1}
+        for (int l = L - 1; l >= 2 && ok; --l) {
+            if (l == 2) layer1(sR);
+            unsigned char *E = hbuf(l);
+            unsigned char *H = l - 1 == 1 ? sR : hbuf(l - 1);
+            tc_sync_for_mma();
+            if (tid == 0) {
+                const unsigned char *Bw = sW + (size_t)(l - 2) * kTgTile;
+                const uint32_t tacc = tmem + (uint32_t)(kTcW * (l - 1));
+                for (int kk = 0; kk < kTcW / 16; ++kk)
+                    tc_mma(tmem, tc_desc(E + kk * 256), tc_desc_mn(Bw + kk * 4096), tc_idesc(kTcW, 0, 1), kk > 0);
+                for (int kk = 0; kk < kTcM / 16; ++kk)
+                    tc_mma(tacc, tc_desc_mn(E + kk * 4096), tc_desc_mn(H + kk * 4096), tc_idesc(kTcW, 1, 1),
+                           (kk > 0 || !first) ? 1u : 0u);
+                tc_commit(&mbar);
+            }
+            if (!tc_round_wait(&mbar, parity)) {
+                ok = false;
+                break;
+            }
+            for (int c0 = cb; c0 < cb + 64; c0 += 32) {
+                float d[32];
+                tc_ld32(twork + (uint32_t)c0, d);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float hb[8], dq[8];
+                    bf16x8_load(H + tc_off(row, c0 + 8 * q), hb);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        d[8 * q + j] *= 1.f - hb[j] * hb[j];
+                        dq[j] = d[8 * q + j];
+                    }
+                    bf16x8_store(H + tc_off(row, c0 + 8 * q), dq);
+                }
+                if (l - 1 >= 2) {
+                    const float sd = warp_transpose_sum(d);
+                    sAcc[((warp & 3) * (nm + 1) + (l - 1 - 2)) * kTcW + c0 + lane] += sd;
+                }
+            }
+        }
+        if (!ok) break;
+        // ---- dW_1 and db_1 = e_1^T [x, 1]
+        tc_sync_for_mma();
+        if (tid == 0) {
+            for (int kk = 0; kk < kTcM / 16; ++kk)
+                tc_mma(tmem, tc_desc_mn(sR + kk * 4096), tc_desc(sX + kk * 256), tc_idesc(kTgN1, 1, 0), kk > 0);
+            tc_commit(&mbar);
+        }
+        if (!tc_round_wait(&mbar, parity)) {
+            ok = false;
+            break;
+        }
+        {
+            float v[32];
+            tc_ld32(twork, v);
+#pragma unroll
+            for (int j = 0; j < kTgN1 / 2; ++j) gW1[j] += half ? v[kTgN1 / 2 + j] : v[j];
+        }
+        first = false;
+    }
+
+    // ---- the CTA's gradient slice
+    float *g = gpart + (int64_t)blockIdx.x * D.np;
+    tc_sync_for_mma();
+    if (ok) {
+        for (int l = 2; l < L; ++l) {
+            const uint32_t tacc = tmem + (uint32_t)(kTcW * (l - 1)) + lane_off;
+            for (int c0 = cb; c0 < cb + 64; c0 += 32) {
+                float v[32];
+                tc_ld32(tacc + (uint32_t)c0, v);
+                float *p = g + D.off[l] + (int64_t)row * kTcW + c0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) p[j] = first ? 0.f : v[j];
+            }
+        }
+        for (int o = tid; o < kTcW; o += kTgThreads) {
+            for (int v = 0; v <= nm; ++v) {
+                float t = 0.f;
+                for (int w = 0; w < 4; ++w) t += sAcc[(w * (nm + 1) + v) * kTcW + o];
+                if (v < nm) g[D.off[v + 2] + (int64_t)kTcW * kTcW + o] = t;
+                else g[D.off[L] + o] = t;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kTgN1 / 2; ++j) {
+            const int i = (kTgN1 / 2) * half + j;
+            if (i < w0) g[D.off[1] + (int64_t)row * w0 + i] = gW1[j];
+            else if (i == w0) g[D.off[1] + (int64_t)kTcW * w0 + row] = gW1[j];
+        }
+    }
+    float t = gb_out;
+    double ls = lsum;
+    for (int o = 16; o; o >>= 1) {
+        t += __shfl_xor_sync(0xffffffffu, t, o);
+        ls += __shfl_xor_sync(0xffffffffu, ls, o);
+    }
+    if (lane == 0) {
+        sE[warp] = t;
+        sL[warp] = ls;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float te = 0.f;
+        double tl = 0.0;
+        for (int w = 0; w < kTgThreads / 32; ++w) {
+            te += sE[w];
+            tl += sL[w];
+        }
+        if (ok) g[D.off[L] + kTcW] = te;
+        lpart[blockIdx.x] = ok ? tl : (double)__int_as_float(0x7fc00000);
+    }
+    if (!ok)
+        for (int64_t p = tid; p < D.np; p += kTgThreads) g[p] = __int_as_float(0x7fc00000);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
+static bool mlp_tg_shape(const MlpDesc &D) {
+    return mlp_tc_shape(D) && D.L - 2 <= kTgMaxMma && D.w[0] < kTgN1 && tg_layout(D).total <= 224 * 1024;
 }
 
 static int g_mlp_tc = 1;
@@ -591,7 +1012,7 @@ rfm_status launch_mlp_forward(const rfm_mlp *net, const float *theta, const floa
         const int64_t tiles = (n + kTcM - 1) / kTcM;
         const int grid = (int)(tiles < nsm ? tiles : nsm);
         ProfScope ps("k_mlp_fwd_tc", st);
-        k_mlp_fwd_tc<<<grid, kTcM, smem, st>>>(D, theta, X, n, Y);
+        k_mlp_fwd_tc<<<grid, kTcThreads, smem, st>>>(D, theta, X, n, Y);
         RFM_CUDA_CHECK(cudaGetLastError());
         return RFM_OK;
     }
@@ -623,10 +1044,23 @@ rfm_status launch_mlp_grad(const rfm_mlp *net, const float *theta, const float *
     }
     float *gpart = ws_ptr<float>(ws, 0);
     double *lpart = ws_ptr<double>(ws, ((size_t)kMlpMaxCtas * D.np * 4 + 255) / 256 * 256);
-    const size_t smem = (size_t)D.smem_floats * 4;
-    RFM_CUDA_CHECK(cudaFuncSetAttribute(k_mlp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = mlp_grid(n);
-    {
+    int grid;
+    if (g_mlp_tc && mlp_tg_shape(D)) {
+        const size_t smem = tg_layout(D).total;
+        RFM_CUDA_CHECK(cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int dev = 0, nsm = 0;
+        RFM_CUDA_CHECK(cudaGetDevice(&dev));
+        RFM_CUDA_CHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        const int64_t tiles = (n + kTcM - 1) / kTcM;
+        grid = (int)(tiles < nsm ? tiles : nsm);
+        if (grid > kMlpMaxCtas) grid = kMlpMaxCtas;
+        ProfScope ps("k_mlp_grad_tc", st);
+        k_mlp_grad_tc<<<grid, kTgThreads, smem, st>>>(D, theta, X, T, n, gpart, lpart, (float)(1.0 / n));
+        RFM_CUDA_CHECK(cudaGetLastError());
+    } else {
+        const size_t smem = (size_t)D.smem_floats * 4;
+        RFM_CUDA_CHECK(cudaFuncSetAttribute(k_mlp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        grid = mlp_grid(n);
         ProfScope ps("k_mlp_grad", st);
         k_mlp<true><<<grid, kMlpThreads, smem, st>>>(D, theta, X, T, n, nullptr, gpart, lpart, (float)(1.0 / n));
         RFM_CUDA_CHECK(cudaGetLastError());
