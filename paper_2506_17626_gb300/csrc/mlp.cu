@@ -371,6 +371,36 @@ __device__ inline bool tc_wait(uint64_t *mbar, unsigned parity) {
     return false;
 }
 
+// tanh(x) = 1 - 2 / (1 + e^{2x}), e^{2x} = 2^{(2 / ln 2) x} by the SFU's base-2
+// exponential and its reciprocal: absolute error about 1e-7, +-1 for large
+// |x|.  The tensor-core paths round the result to BF16 (8 significant bits).
+__device__ __forceinline__ float tanh_sfu(float x) {
+    float e, r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(x * 2.88539008f));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.f + e));
+    return fmaf(-2.f, r, 1.f);
+}
+
+// first-layer weights in shared memory with the row stride padded to 4 floats
+__host__ __device__ inline int w1_ld(int w0) { return (w0 + 3) & ~3; }
+
+// pre-activation of first-layer output o: b + W_1[o, :] x with 16-byte loads
+__device__ __forceinline__ float layer1_dot(const float *sW1, int ld, int w0, int o, float b, const float (&x)[kMlpMaxIn]) {
+    float t = b;
+    const float4 *w = reinterpret_cast<const float4 *>(sW1 + o * ld);
+#pragma unroll
+    for (int q = 0; q < kMlpMaxIn / 4; ++q) {
+        if (4 * q < w0) {
+            const float4 v = w[q];
+            t = fmaf(v.x, x[4 * q], t);
+            t = fmaf(v.y, x[4 * q + 1], t);
+            t = fmaf(v.z, x[4 * q + 2], t);
+            t = fmaf(v.w, x[4 * q + 3], t);
+        }
+    }
+    return t;
+}
+
 constexpr int kTgThreads = 256;
 constexpr int kTgMaxMma = 3;
 constexpr int kTgN1 = 32;        // first-layer product columns: inputs, a ones row, zero padding
@@ -485,8 +515,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(MlpDesc D, const f
     const int L = D.L, n_mma = L - 2, w0 = D.w[0];
     unsigned char *sWm = tsm;                                  // n_mma x 32 KB: W_2 .. W_{L-1} (BF16)
     unsigned char *sAct = sWm + (size_t)n_mma * kTgTile;       // 2 x 32 KB: activations (BF16)
-    float *sW1 = reinterpret_cast<float *>(sAct + 2 * kTgTile);   // kTcW x w0
-    float *sB = sW1 + kTcW * w0;                               // biases of layers 1 .. L-1 (kTcW each)
+    float *sW1 = reinterpret_cast<float *>(sAct + 2 * kTgTile);   // kTcW x w1_ld(w0)
+    float *sB = sW1 + kTcW * w1_ld(w0);                        // biases of layers 1 .. L-1 (kTcW each)
     float *sWL = sB + (L - 1) * kTcW;                          // output weights (kTcW) and bias
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
@@ -503,7 +533,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(MlpDesc D, const f
             *reinterpret_cast<__nv_bfloat16 *>(dst + tc_off(o, i)) = __float2bfloat16_rn(__ldg(W + e));
         }
     }
-    for (int e = tid; e < kTcW * w0; e += kTcThreads) sW1[e] = __ldg(theta + D.off[1] + e);
+    for (int e = tid; e < kTcW * w1_ld(w0); e += kTcThreads) {
+        const int o = e / w1_ld(w0), i = e % w1_ld(w0);
+        sW1[e] = i < w0 ? __ldg(theta + D.off[1] + o * w0 + i) : 0.f;
+    }
     for (int l = 1; l < L; ++l)
         for (int o = tid; o < kTcW; o += kTcThreads) sB[(l - 1) * kTcW + o] = __ldg(theta + D.off[l] + (int64_t)kTcW * D.w[l - 1] + o);
     for (int i = tid; i <= kTcW; i += kTcThreads) sWL[i] = __ldg(theta + D.off[L] + i);
@@ -534,11 +567,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(MlpDesc D, const f
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int o = o0 + j;
-                    float t = sB[o];
-#pragma unroll
-                    for (int i = 0; i < kMlpMaxIn; ++i)
-                        if (i < w0) t = fmaf(sW1[o * w0 + i], x[i], t);
-                    hv[j] = tanhf(t);
+                    hv[j] = tanh_sfu(layer1_dot(sW1, w1_ld(w0), w0, o, sB[o], x));
                 }
                 bf16x8_store(sAct + tc_off(row, o0), hv);
             }
@@ -569,7 +598,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(MlpDesc D, const f
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int o = c0 + 8 * g + j;
-                        hv[j] = tanhf(v[8 * g + j] + bl[o]);
+                        hv[j] = tanh_sfu(v[8 * g + j] + bl[o]);
                         if (last) yv = fmaf(hv[j], sWL[o], yv);
                     }
                     if (!last) bf16x8_store(Aout + tc_off(row, c0 + 8 * g), hv);
@@ -601,7 +630,7 @@ static bool mlp_tc_shape(const MlpDesc &D) {
 
 static size_t mlp_tc_smem(const MlpDesc &D) {
     return (size_t)(D.L - 2) * kTcW * kTcW * 2 + 2 * (size_t)kTcM * kTcW * 2 +
-           4 * ((size_t)kTcW * D.w[0] + (size_t)(D.L - 1) * kTcW + kTcW + 1) + 64;
+           4 * ((size_t)kTcW * w1_ld(D.w[0]) + (size_t)(D.L - 1) * kTcW + kTcW + 1) + 64;
 }
 
 // ---------------------------------------------------------------------------
@@ -641,7 +670,7 @@ __host__ __device__ inline TgLayout tg_layout(const MlpDesc &D) {
     t.buf = t.w + (size_t)t.nm * kTgTile;
     t.x = t.buf + (size_t)t.nb * kTgTile;
     t.w1 = t.x + (size_t)kTgN1 * kTcM * 2;
-    t.b = t.w1 + (size_t)kTcW * D.w[0] * 4;
+    t.b = t.w1 + (size_t)kTcW * w1_ld(D.w[0]) * 4;
     t.wl = t.b + (size_t)(D.L - 1) * kTcW * 4;
     t.acc = t.wl + 132 * 4;
     t.total = t.acc + (size_t)4 * (t.nm + 1) * kTcW * 4;
@@ -658,7 +687,7 @@ __global__ void __launch_bounds__(kTgThreads, 1)
     unsigned char *sW = tsm + Ly.w;                                  // W_2 .. W_{L-1}, BF16 (output, input)
     unsigned char *sBuf = tsm + Ly.buf;                              // activation / error buffers
     unsigned char *sX = tsm + Ly.x;                                  // [x, 1, 0] as (input, sample), BF16
-    float *sW1 = reinterpret_cast<float *>(tsm + Ly.w1);             // W_1, FP32 (output, input)
+    float *sW1 = reinterpret_cast<float *>(tsm + Ly.w1);             // W_1, FP32 (output, input), padded rows
     float *sB = reinterpret_cast<float *>(tsm + Ly.b);               // b_1 .. b_{L-1}
     float *sWL = reinterpret_cast<float *>(tsm + Ly.wl);             // w_L and b_L
     float *sAcc = reinterpret_cast<float *>(tsm + Ly.acc);           // per lane group: db_2 .. db_{L-1}, dW_L
@@ -686,7 +715,10 @@ __global__ void __launch_bounds__(kTgThreads, 1)
             *reinterpret_cast<__nv_bfloat16 *>(dst + tc_off(o, i)) = __float2bfloat16_rn(__ldg(W + e));
         }
     }
-    for (int e = tid; e < kTcW * w0; e += kTgThreads) sW1[e] = __ldg(theta + D.off[1] + e);
+    for (int e = tid; e < kTcW * w1_ld(w0); e += kTgThreads) {
+        const int o = e / w1_ld(w0), i = e % w1_ld(w0);
+        sW1[e] = i < w0 ? __ldg(theta + D.off[1] + o * w0 + i) : 0.f;
+    }
     for (int l = 1; l < L; ++l)
         for (int o = tid; o < kTcW; o += kTgThreads)
             sB[(l - 1) * kTcW + o] = __ldg(theta + D.off[l] + (int64_t)kTcW * D.w[l - 1] + o);
@@ -722,11 +754,7 @@ __global__ void __launch_bounds__(kTgThreads, 1)
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int o = o0 + j;
-                float t = sB[o];
-#pragma unroll
-                for (int i = 0; i < kMlpMaxIn; ++i)
-                    if (i < w0) t = fmaf(sW1[o * w0 + i], xr[i], t);
-                hv[j] = tanhf(t);
+                hv[j] = tanh_sfu(layer1_dot(sW1, w1_ld(w0), w0, o, sB[o], xr));
             }
             bf16x8_store(dst + tc_off(row, o0), hv);
         }
@@ -773,7 +801,7 @@ __global__ void __launch_bounds__(kTgThreads, 1)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int o = c0 + 8 * g + j;
-                        hv[j] = tanhf(v[8 * g + j] + bl[o]);
+                        hv[j] = tanh_sfu(v[8 * g + j] + bl[o]);
                         if (last) yp = fmaf(hv[j], sWL[o], yp);
                     }
                     bf16x8_store(out + tc_off(row, c0 + 8 * g), hv);
