@@ -466,8 +466,8 @@ def run_learned(args, dev):
         "workload": f"2D Poisson, f = sin(a pi x) sin(b pi y) + c sin(d pi x + e pi y), {S_}x{S_} subdomains, "
                     f"overlap ratio {D_}, K={K_}, {n}^2 interior + boundary rows, filter tol {TOL:g}, "
                     f"mixed path; 8 held-out instances (seeds 10000-10007)",
-        "network": "9 -> 128 x4 (tanh) -> 1, trained in FP32 (Adam lr 2e-3 -> 1e-4, batch 4096, targets x pi^2 "
-                   "(a^2+b^2)), prediction on the tensor cores",
+        "network": "9 -> 128 x4 (tanh) -> 1 on the tensor cores (BF16 operands, FP32 accumulation and master "
+                   "weights), Adam lr 2e-3 -> 1e-4, batch 4096, targets x pi^2 (a^2+b^2)",
         "forward": fwd,
         "training_solves": ntr, "training_lsqr_iterations": train_iters, "training_samples": n_samples,
         "epochs": epochs, "data_s": t_data, "train_s": t_train, "train_samples_per_s": n_samples * epochs / t_train,
