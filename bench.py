@@ -342,12 +342,92 @@ def run_gpu(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(p, prm, kstar["fp64"], budget_s=args.cpu_budget)
+    if rank == 0 and world == 1 and args.batched > 0:
+        out["batched"] = run_batched(args, dev)
     if rank == 0 and world == 1 and args.learned_train > 0:
         out["learned"] = run_learned(args, dev)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_batched(args, dev):
+    """The batched family in one launch per call: 64 instances of uneven size
+    (per instance seeded S in [8, 24]^2 subdomains, K in [100, 400] features,
+    four separable sine modes), p_lo..p_hi points per subdomain edge (the
+    family's 40..200 would need about 450 GB for the FP32 blocks alone), mixed
+    path, a fixed number of LSQR iterations.  Phase times by CUDA events after
+    one untimed pass; the filter also in block order (RFM_OPT_QR_ORDER = 0)."""
+    import copy
+    import torch
+    import paper_2506_17626_gb300 as R
+    from paper_2506_17626_gb300 import _native as N
+    n_inst, (p_lo, p_hi), iters = args.batched, (8, 16), args.batched_iters
+    probs = [synth.batched_instance(i, p_range=(p_lo, p_hi)) for i in range(n_inst)]
+    d = torch.from_numpy(np.concatenate([synth.feature_params(p).ravel() for p in probs])).to(dev)
+    grids = []
+    for p in probs:
+        q = copy.copy(p)
+        q.n_test = [100, 100]
+        grids.append(torch.from_numpy(oracle_free_test_grid(q)).to(dev))
+    S = R.System(probs, asm="fp32", op="q32", tol=TOL, device=str(dev))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+
+    def step(timed):
+        if timed:
+            ev[0].record()
+        S.assemble(d)
+        if timed:
+            ev[1].record()
+        rank = S.filter()
+        if timed:
+            ev[2].record()
+        a, rep = S.solve(atol=0, btol=0, max_iter=iters)
+        if timed:
+            ev[3].record()
+        _, err = S.evaluate(d, a, grids)
+        if timed:
+            ev[4].record()
+        return rank, err
+
+    step(False)
+    rank, err = step(True)
+    N.set_qr_order(False)
+    try:
+        ev[5].record()
+        S.filter()
+        ev[6].record()
+    finally:
+        N.set_qr_order(True)
+    torch.cuda.synchronize()
+    e = err.cpu().numpy().reshape(n_inst, 4)
+    rel = np.sqrt(e[:, 0] / e[:, 1])
+    nblk = [p.J for p in probs]
+    m_blk = S.block_table()[0]
+    r_blk = rank.cpu().numpy().astype(np.int64)
+    K_blk = np.repeat([p.K for p in probs], nblk)
+    nnz = int((m_blk * r_blk).sum())
+    ms_it = ev[2].elapsed_time(ev[3]) / iters
+    lsqr_gbs = lsqr_bytes_per_iter(m_blk, r_blk, S.sizes["n_rows"], 4) / (ms_it * 1e-3) / 1e9
+    qr_fl = 0.0
+    for mj, Kj, rj in zip(m_blk, K_blk, r_blk):
+        i = np.arange(int(rj), dtype=np.float64)
+        qr_fl += float(np.sum(4.0 * (mj - i) * (Kj - i) + 4.0 * (mj - i) * (rj - i)))
+    return {
+        "workload": f"batched 2D Poisson: {n_inst} instances, S in [8, 24]^2, K in [100, 400], "
+                    f"{p_lo}-{p_hi} points per subdomain edge, 4 separable sine modes; mixed path, filter tol {TOL:g}, "
+                    f"{iters} LSQR iterations, error on a 100^2 grid per instance",
+        "blocks": int(sum(nblk)), "blocks_per_instance": [int(min(nblk)), int(max(nblk))],
+        "rows": int(S.sizes["n_rows"]), "columns": int(S.sizes["n_cols"]), "kept_columns": int(rank.sum().item()),
+        "ms": {"assemble": ev[0].elapsed_time(ev[1]), "filter": ev[1].elapsed_time(ev[2]),
+               "lsqr": ev[2].elapsed_time(ev[3]), "eval": ev[3].elapsed_time(ev[4]),
+               "step": ev[0].elapsed_time(ev[4]), "filter_block_order": ev[5].elapsed_time(ev[6])},
+        "ms_per_lsqr_iteration": ms_it, "nnz_q_hat": nnz,
+        "lsqr_gbs_algorithmic": lsqr_gbs,
+        "qr_gflops_algorithmic": qr_fl / (ev[1].elapsed_time(ev[2]) * 1e-3) / 1e9,
+        "rel_l2": {"median": float(np.median(rel)), "max": float(rel.max())},
+    }
 
 
 def run_learned(args, dev):
@@ -575,6 +655,8 @@ def main():
     ap.add_argument("--learned-train", type=int, default=384,
                     help="training solves of the learned warm start section (0 skips it)")
     ap.add_argument("--learned-epochs", type=int, default=6)
+    ap.add_argument("--batched", type=int, default=64, help="instances of the batched section (0 skips it)")
+    ap.add_argument("--batched-iters", type=int, default=2000)
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: 10x10 subdomains with the same block shapes (profiler captures)")
     args = ap.parse_args()

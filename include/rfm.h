@@ -374,13 +374,18 @@ int rfm_profile_read(const char **names, int64_t *launches, double *ms, int max)
  *    accumulation) when every hidden layer is 128 wide (rfm_mlp_grad: one to
  *    three 128 x 128 layers and fewer than 32 inputs); results then carry
  *    BF16 rounding (about 1e-2 relative).  0 keeps the FP32 kernels for every
- *    network. */
+ *    network.
+ *  RFM_OPT_QR_ORDER: 1 (default) starts the QR of the blocks with the most
+ *    work (m K min(m, K), largest first), so that a batch of uneven blocks
+ *    does not end on a few large ones; 0 takes them in block order.  The
+ *    factors are the same either way. */
 enum {
     RFM_OPT_FILTER_KERNEL = 0,
     RFM_OPT_AUTOTUNE = 1,
     RFM_OPT_QR_DOUBLE_FLOAT = 2,
     RFM_OPT_LSQR_STALL = 3,
-    RFM_OPT_MLP_TENSOR_CORES = 4
+    RFM_OPT_MLP_TENSOR_CORES = 4,
+    RFM_OPT_QR_ORDER = 5
 };
 rfm_status rfm_set_option(int option, int value);
 

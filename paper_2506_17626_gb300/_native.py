@@ -178,9 +178,16 @@ def set_lsqr_stall(mode: int):
 
 
 def set_mlp_tensor_cores(on: bool):
-    """Network forward on the tensor cores when every hidden layer is 128 wide
-    (True, the default) or always in FP32 (False) (RFM_OPT_MLP_TENSOR_CORES)."""
+    """Network forward pass and gradient on the tensor cores when every hidden
+    layer is 128 wide (True, the default) or always in FP32 (False)
+    (RFM_OPT_MLP_TENSOR_CORES)."""
     check("rfm_set_option", load().rfm_set_option(4, 1 if on else 0))
+
+
+def set_qr_order(largest_first: bool):
+    """Launch the QR clusters on the blocks by decreasing work (True, the
+    default) or in block order (False) (RFM_OPT_QR_ORDER)."""
+    check("rfm_set_option", load().rfm_set_option(5, 1 if largest_first else 0))
 
 
 def set_qr_double_float(on: bool):

@@ -19,6 +19,7 @@ void set_autotune(int on);
 void set_qr_double_float(int on);
 void set_lsqr_stall(int v);
 void set_mlp_tensor_cores(int on);
+void set_qr_order(int on);
 rfm_status launch_eval_noalloc(const HostPlan &P, const double *params, const double *a, const double *X,
                                const int64_t *pt_off, double *u, double *err, cudaStream_t st);
 rfm_status launch_eval(const HostPlan &P, void *ws, const double *params, const double *a, const double *X,
@@ -130,9 +131,12 @@ rfm_status rfm_assemble(const rfm_problem *probs, int n_inst, const rfm_config *
     cudaStream_t st = (cudaStream_t)stream;
     RFM_CUDA_CHECK(cudaMemcpyAsync(ws_ptr<void>(d_ws, L.off_inst), P.p.inst, sizeof(InstRec) * L.n_inst,
                                    cudaMemcpyHostToDevice, st));
-    if (L.n_blocks)
+    if (L.n_blocks) {
         RFM_CUDA_CHECK(cudaMemcpyAsync(ws_ptr<void>(d_ws, L.off_blk), P.p.blk, sizeof(BlkRec) * L.n_blocks,
                                        cudaMemcpyHostToDevice, st));
+        RFM_CUDA_CHECK(cudaMemcpyAsync(ws_ptr<void>(d_ws, L.off_qord), P.p.qr_order, sizeof(int32_t) * L.n_blocks,
+                                       cudaMemcpyHostToDevice, st));
+    }
     if (L.n_tiles) {
         RFM_CUDA_CHECK(cudaMemcpyAsync(ws_ptr<void>(d_ws, L.off_tile), P.p.tile_blk, sizeof(int32_t) * L.n_tiles,
                                        cudaMemcpyHostToDevice, st));
@@ -231,6 +235,10 @@ rfm_status rfm_set_option(int option, int value) {
     }
     if (option == RFM_OPT_MLP_TENSOR_CORES && (value == 0 || value == 1)) {
         set_mlp_tensor_cores(value);
+        return RFM_OK;
+    }
+    if (option == RFM_OPT_QR_ORDER && (value == 0 || value == 1)) {
+        set_qr_order(value);
         return RFM_OK;
     }
     set_error("rfm_set_option: unknown option %d or value %d", option, value);

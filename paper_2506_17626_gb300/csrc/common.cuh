@@ -87,6 +87,7 @@ struct Layout {
     int64_t n_t_items;                                  // fused product items: column chunks + 32-row tiles (bound)
     size_t off_titems, off_ntitems;
     size_t off_bcnt;                                    // per block: chunks of the transposed product finished (64-bit, monotone)
+    size_t off_qord;                                    // QR launch order of the blocks (largest first)
     size_t total;
     int asm_prec, op;
 };
@@ -103,6 +104,7 @@ struct HostPlan {
     int32_t *cov;        // per-dimension cover tables: first covering subdomain, count (pairs)
     int32_t *fwd_items;  // (block, first row) of every 128-row tile
     int32_t *col_items;  // (block, first column) of every 8-column tile
+    int32_t *qr_order;   // n_blocks: blocks by decreasing QR work (m K min(m, K)), ties by index
 };
 
 constexpr int kFwdRows = 128;  // rows of a forward (A x) work item (one warp)
@@ -126,6 +128,7 @@ void set_error(const char *fmt, ...);
 // filter, or the fit of predicted values through the kept features.
 struct FilterBufs {
     const BlkRec *blk;
+    const int32_t *order;   // launch order of the blocks in the cluster kernels (null: natural)
     const void *M;          // input blocks (FP32 or FP64), ldm x K each
     double *W, *tau, *r11;  // QR work (R above the diagonal, reflectors below)
     int32_t *perm, *rank;
@@ -137,6 +140,8 @@ struct FilterBufs {
     int64_t n_blocks, max_m, max_K;
 };
 rfm_status launch_filter_bufs(const FilterBufs &F, bool fp32, double tol, cudaStream_t st);
+// The plan's QR launch order in the workspace, or null when RFM_OPT_QR_ORDER = 0.
+const int32_t *qr_order_ptr(void *ws, const Layout &L);
 
 template <typename T>
 __host__ __device__ inline T *ws_ptr(void *ws, size_t off) {

@@ -222,6 +222,7 @@ rfm_status launch_fit_prepare(const HostPlan &P, void *ws, const double *params,
     }
     FilterBufs B;
     B.blk = ws_ptr<BlkRec>(ws, L.off_blk);
+    B.order = qr_order_ptr(ws, L);
     B.M = Phi;
     B.W = ws_ptr<double>(fws, F.off_w);
     B.tau = ws_ptr<double>(fws, F.off_tau);

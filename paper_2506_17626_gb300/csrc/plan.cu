@@ -14,6 +14,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -292,6 +293,7 @@ rfm_status build_plan(const rfm_problem *probs, int n_inst, const rfm_config *cf
     L.off_titems = take(sizeof(ColItem) * (L.n_t_items + 1));
     L.off_ntitems = take(256);
     L.off_bcnt = take(sizeof(unsigned long long) * (blk.size() + 1));
+    L.off_qord = take(sizeof(int32_t) * (blk.size() + 1));
     L.off_qblk = take(sizeof(int32_t) * (roff + 1));
     L.off_tu = take(sizeof(double) * (roff + 1));
     L.off_fitems = take(sizeof(ColItem) * (L.n_fwd_items + 1));
@@ -314,6 +316,20 @@ rfm_status build_plan(const rfm_problem *probs, int n_inst, const rfm_config *cf
         memcpy(out->tile_row, tile_row.data(), sizeof(int32_t) * tile_row.size());
     }
     if (!cov.empty()) memcpy(out->cov, cov.data(), sizeof(int32_t) * cov.size());
+    // QR launch order: the longest factorizations start first, so that an
+    // uneven batch does not end on a few large blocks (longest processing time
+    // first); the estimate is the leading term m K min(m, K) of the flops
+    out->qr_order = (int32_t *)malloc(sizeof(int32_t) * (blk.size() + 1));
+    {
+        std::vector<int32_t> ord(blk.size());
+        for (size_t b = 0; b < blk.size(); ++b) ord[b] = (int32_t)b;
+        auto work = [&](int32_t b) {
+            const double m = blk[b].m, k = blk[b].K;
+            return m * k * (m < k ? m : k);
+        };
+        std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return work(a) > work(b); });
+        if (!ord.empty()) memcpy(out->qr_order, ord.data(), sizeof(int32_t) * ord.size());
+    }
     return RFM_OK;
 }
 
@@ -324,6 +340,7 @@ void free_plan(HostPlan *p) {
     free(p->cov);
     free(p->fwd_items);
     free(p->col_items);
+    free(p->qr_order);
     memset(p, 0, sizeof(*p));
 }
 

@@ -303,14 +303,15 @@ constexpr int kQT = 256;          // threads of a cluster-QR CTA (measured: 512 
 constexpr int kQW = kQT / 32;
 
 template <typename TM, int C>
-__global__ void __launch_bounds__(kQT) k_qrcp_cluster(const BlkRec *__restrict__ blks, const TM *__restrict__ M,
+__global__ void __launch_bounds__(kQT) k_qrcp_cluster(const BlkRec *__restrict__ blks,
+                                                      const int32_t *__restrict__ order, const TM *__restrict__ M,
                                                       double *__restrict__ W, double *__restrict__ tau,
                                                       int32_t *__restrict__ perm_out, int32_t *__restrict__ rank_out,
                                                       double *__restrict__ r11_out, double tol, int nloc_max,
                                                       int ld_loc, double *__restrict__ Qout, float *__restrict__ Q32) {
     cg::cluster_group cl = cg::this_cluster();
     const int cr = (int)cl.block_rank();
-    const int b = blockIdx.x / C;
+    const int b = order ? order[blockIdx.x / C] : (int)(blockIdx.x / C);
     const BlkRec B = blks[b];
     const int m = B.m, K = B.K, ld = B.ldm;
     extern __shared__ __align__(16) double sm[];
@@ -608,7 +609,8 @@ constexpr int kDT = 512;          // threads of a double-float cluster-QR CTA (i
 constexpr int kDW = kDT / 32;
 
 template <int C>
-__global__ void __launch_bounds__(kDT) k_qrcp_cluster_df(const BlkRec *__restrict__ blks, const float *__restrict__ M,
+__global__ void __launch_bounds__(kDT) k_qrcp_cluster_df(const BlkRec *__restrict__ blks,
+                                                         const int32_t *__restrict__ order, const float *__restrict__ M,
                                                          double *__restrict__ W, double *__restrict__ tau,
                                                          int32_t *__restrict__ perm_out, int32_t *__restrict__ rank_out,
                                                          double *__restrict__ r11_out, double tol, int nloc_max,
@@ -616,7 +618,7 @@ __global__ void __launch_bounds__(kDT) k_qrcp_cluster_df(const BlkRec *__restric
                                                          float *__restrict__ Q32) {
     cg::cluster_group cl = cg::this_cluster();
     const int cr = (int)cl.block_rank();
-    const int b = blockIdx.x / C;
+    const int b = order ? order[blockIdx.x / C] : (int)(blockIdx.x / C);
     const BlkRec B = blks[b];
     const int m = B.m, K = B.K, ld = B.ldm;
     extern __shared__ __align__(16) float2 smf[];
@@ -960,8 +962,8 @@ static rfm_status launch_cluster(const FilterBufs &F, double tol, int nloc, int 
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    RFM_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, F.blk, (const TM *)F.M, F.W, F.tau, F.perm, F.rank, F.r11, tol, nloc,
-                                      ldl, F.Q64, F.Q32));
+    RFM_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, F.blk, F.order, (const TM *)F.M, F.W, F.tau, F.perm, F.rank, F.r11, tol,
+                                      nloc, ldl, F.Q64, F.Q32));
     return RFM_OK;
 }
 
@@ -1001,8 +1003,8 @@ static rfm_status launch_cluster_df(const FilterBufs &F, double tol, int nloc, i
     cfg.attrs = at;
     cfg.numAttrs = 1;
     float2 *vdf = F.Q32 ? reinterpret_cast<float2 *>(F.Op) : nullptr;
-    RFM_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, F.blk, (const float *)F.M, F.W, F.tau, F.perm, F.rank, F.r11, tol,
-                                      nloc, ldl, (int)F.max_K, vdf, F.Q32));
+    RFM_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, F.blk, F.order, (const float *)F.M, F.W, F.tau, F.perm, F.rank, F.r11,
+                                      tol, nloc, ldl, (int)F.max_K, vdf, F.Q32));
     return RFM_OK;
 }
 
@@ -1169,10 +1171,19 @@ static rfm_status launch_filter_t(const FilterBufs &F, double tol, cudaStream_t 
     return RFM_OK;
 }
 
+// Cluster kernels visit the blocks largest first (the plan's order) unless
+// RFM_OPT_QR_ORDER = 0; the factors do not depend on the order.
+static int g_qr_order = 1;
+
+const int32_t *qr_order_ptr(void *ws, const Layout &L) {
+    return g_qr_order ? ws_ptr<int32_t>(ws, L.off_qord) : nullptr;
+}
+
 static FilterBufs system_bufs(const HostPlan &P, void *ws) {
     const Layout &L = P.L;
     FilterBufs F;
     F.blk = ws_ptr<BlkRec>(ws, L.off_blk);
+    F.order = qr_order_ptr(ws, L);
     F.M = ws_ptr<char>(ws, L.off_M);
     F.W = ws_ptr<double>(ws, L.off_W);
     F.tau = ws_ptr<double>(ws, L.off_tau);
@@ -1207,5 +1218,6 @@ rfm_status launch_filter(const HostPlan &P, void *ws, double tol, cudaStream_t s
 void set_force_global_filter(int on) { g_force_global = on; }
 void set_autotune(int on) { g_autotune = on; }
 void set_qr_double_float(int on) { g_qr_df = on; }
+void set_qr_order(int on) { g_qr_order = on; }
 
 }  // namespace rfm
