@@ -328,6 +328,13 @@ rfm_status rfm_block_info(const rfm_problem *probs, int n_inst, const rfm_config
 rfm_status rfm_block_table(const rfm_problem *probs, int n_inst, const rfm_config *cfg, int64_t *m, int64_t *ld,
                            int64_t *moff, int64_t *roff);
 
+/* The order in which the filter's QR clusters take the blocks (n_blocks
+ * indices, host array): decreasing m K min(m, K), the leading term of the
+ * block's factorization flops, ties by block index.  A scheduling choice of
+ * this implementation (row a7 of the batched workload); the paper has no
+ * counterpart.  Host only. */
+rfm_status rfm_qr_order(const rfm_problem *probs, int n_inst, const rfm_config *cfg, int32_t *order);
+
 /* Device pointers into the workspace (views for tests and for the warm
  * start): which = 0 M arena (FP64 or FP32 by asm_prec), 1 h (FP64, n_rows),
  * 2 grow (int32, block_rows; global row index across instances),

@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH):
         "rfm_block_info": [P, C.c_int, CF, i64, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)],
         "rfm_workspace_view": [P, C.c_int, CF, vp, C.c_int, C.POINTER(vp)],
         "rfm_block_table": [P, C.c_int, CF, vp, vp, vp, vp],
+        "rfm_qr_order": [P, C.c_int, CF, vp],
         "rfm_block_inputs": [P, C.c_int, CF, vp, C.c_int, vp, vp, vp, C.c_size_t, vp],
         "rfm_fit_size": [P, C.c_int, CF, C.POINTER(C.c_size_t)],
         "rfm_fit_prepare": [P, C.c_int, CF, vp, C.c_double, vp, C.c_size_t, vp, C.c_size_t, vp],

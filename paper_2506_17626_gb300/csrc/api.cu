@@ -328,6 +328,19 @@ rfm_status rfm_block_table(const rfm_problem *probs, int n_inst, const rfm_confi
     RFM_GUARD_END
 }
 
+rfm_status rfm_qr_order(const rfm_problem *probs, int n_inst, const rfm_config *cfg, int32_t *order) {
+    RFM_GUARD_BEGIN
+    Plan P(probs, n_inst, cfg);
+    if (!P.ok) return P.rc;
+    if (!order) {
+        set_error("rfm_qr_order: order is NULL");
+        return RFM_EINVAL;
+    }
+    if (P.p.L.n_blocks) memcpy(order, P.p.qr_order, sizeof(int32_t) * P.p.L.n_blocks);
+    return RFM_OK;
+    RFM_GUARD_END
+}
+
 rfm_status rfm_workspace_view(const rfm_problem *probs, int n_inst, const rfm_config *cfg, void *d_ws, int which,
                               void **ptr) {
     RFM_GUARD_BEGIN

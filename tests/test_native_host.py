@@ -91,3 +91,24 @@ def test_subdomain_without_points_is_rejected(native):
     p = synth.poisson1d(S=20, K=4, n=3)
     rc, *_ = _sizes(native, [p])
     assert rc == native.RFM_EINVAL
+
+
+def test_qr_launch_order_is_largest_first(native):
+    """The filter's QR launch order over an uneven batch: a permutation of the
+    blocks, by decreasing m K min(m, K) with ties in block order, where m are
+    the oracle's block row counts."""
+    ps = [synth.batched_instance(i, p_range=(3, 5)) for i in range(3)] + [synth.poisson1d(S=5, K=7, n=50)]
+    rc, sz, arr, cfg = _sizes(native, ps)
+    assert rc == 0
+    order = np.zeros(sz.n_blocks, dtype=np.int32)
+    assert native.load().rfm_qr_order(arr, len(ps), C.byref(cfg), order.ctypes.data_as(C.c_void_p)) == 0
+    assert np.array_equal(np.sort(order), np.arange(sz.n_blocks))
+    work = []
+    for p in ps:
+        for j in range(p.J):
+            m = len(oracle.block_rows(p, j))
+            work.append(m * p.K * min(m, p.K))
+    work = np.array(work, dtype=np.float64)
+    expect = sorted(range(len(work)), key=lambda b: (-work[b], b))
+    assert order.tolist() == expect
+    assert len(set(work.tolist())) > 3           # the batch is uneven
