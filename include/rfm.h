@@ -385,14 +385,18 @@ int rfm_profile_read(const char **names, int64_t *launches, double *ms, int max)
  *  RFM_OPT_QR_ORDER: 1 (default) starts the QR of the blocks with the most
  *    work (m K min(m, K), largest first), so that a batch of uneven blocks
  *    does not end on a few large ones; 0 takes them in block order.  The
- *    factors are the same either way. */
+ *    factors are the same either way.
+ *  RFM_OPT_MLP_TC_THREADS: threads per CTA of the tensor-core network
+ *    kernels, 512 (default: four threads per sample, each with 32 of the 128
+ *    columns) or 256 (two per sample).  The results are the same. */
 enum {
     RFM_OPT_FILTER_KERNEL = 0,
     RFM_OPT_AUTOTUNE = 1,
     RFM_OPT_QR_DOUBLE_FLOAT = 2,
     RFM_OPT_LSQR_STALL = 3,
     RFM_OPT_MLP_TENSOR_CORES = 4,
-    RFM_OPT_QR_ORDER = 5
+    RFM_OPT_QR_ORDER = 5,
+    RFM_OPT_MLP_TC_THREADS = 6
 };
 rfm_status rfm_set_option(int option, int value);
 

@@ -185,6 +185,12 @@ def set_mlp_tensor_cores(on: bool):
     check("rfm_set_option", load().rfm_set_option(4, 1 if on else 0))
 
 
+def set_mlp_tc_threads(threads: int):
+    """Threads per CTA of the tensor-core network kernels: 512 (default, four
+    per sample) or 256 (two per sample) (RFM_OPT_MLP_TC_THREADS)."""
+    check("rfm_set_option", load().rfm_set_option(6, int(threads)))
+
+
 def set_qr_order(largest_first: bool):
     """Launch the QR clusters on the blocks by decreasing work (True, the
     default) or in block order (False) (RFM_OPT_QR_ORDER)."""

@@ -20,6 +20,7 @@ void set_qr_double_float(int on);
 void set_lsqr_stall(int v);
 void set_mlp_tensor_cores(int on);
 void set_qr_order(int on);
+void set_mlp_tc_threads(int threads);
 rfm_status launch_eval_noalloc(const HostPlan &P, const double *params, const double *a, const double *X,
                                const int64_t *pt_off, double *u, double *err, cudaStream_t st);
 rfm_status launch_eval(const HostPlan &P, void *ws, const double *params, const double *a, const double *X,
@@ -239,6 +240,10 @@ rfm_status rfm_set_option(int option, int value) {
     }
     if (option == RFM_OPT_QR_ORDER && (value == 0 || value == 1)) {
         set_qr_order(value);
+        return RFM_OK;
+    }
+    if (option == RFM_OPT_MLP_TC_THREADS && (value == 256 || value == 512)) {
+        set_mlp_tc_threads(value);
         return RFM_OK;
     }
     set_error("rfm_set_option: unknown option %d or value %d", option, value);

@@ -401,7 +401,6 @@ __device__ __forceinline__ float layer1_dot(const float *sW1, int ld, int w0, in
     return t;
 }
 
-constexpr int kTgThreads = 256;
 constexpr int kTgMaxMma = 3;
 constexpr int kTgN1 = 32;        // first-layer product columns: inputs, a ones row, zero padding
 constexpr int kTgTile = kTcM * kTcW * 2;   // bytes of one 128 x 128 BF16 operand
@@ -506,11 +505,12 @@ __device__ inline void bf16x8_store(unsigned char *p, const float (&h)[8]) {
     *reinterpret_cast<uint4 *>(p) = *reinterpret_cast<const uint4 *>(b);
 }
 
-constexpr int kTcThreads = 256;
-
-__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(MlpDesc D, const float *__restrict__ theta,
-                                                              const float *__restrict__ X, int64_t n,
-                                                              float *__restrict__ Y) {
+// P threads per sample (128 P per CTA), each with 128 / P columns of its row
+template <int P>
+__global__ void __launch_bounds__(128 * P, 1) k_mlp_fwd_tc(MlpDesc D, const float *__restrict__ theta,
+                                                           const float *__restrict__ X, int64_t n,
+                                                           float *__restrict__ Y) {
+    constexpr int NT = 128 * P, CW = 128 / P;
     extern __shared__ __align__(1024) unsigned char tsm[];
     const int L = D.L, n_mma = L - 2, w0 = D.w[0];
     unsigned char *sWm = tsm;                                  // n_mma x 32 KB: W_2 .. W_{L-1} (BF16)
@@ -520,26 +520,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(MlpDesc D, const f
     float *sWL = sB + (L - 1) * kTcW;                          // output weights (kTcW) and bias
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
-    __shared__ float sY[2][kTcM];
+    __shared__ float sY[P][kTcM];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int row = 32 * (warp & 3) + lane, cb = 64 * (warp >> 2);
+    const int row = 32 * (warp & 3) + lane, cb = CW * (warp >> 2);
     const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
     // weights once per CTA
     for (int l = 2; l < L; ++l) {
         const float *W = theta + D.off[l];
         unsigned char *dst = sWm + (size_t)(l - 2) * kTgTile;
-        for (int e = tid; e < kTcW * kTcW; e += kTcThreads) {
+        for (int e = tid; e < kTcW * kTcW; e += NT) {
             const int o = e / kTcW, i = e % kTcW;
             *reinterpret_cast<__nv_bfloat16 *>(dst + tc_off(o, i)) = __float2bfloat16_rn(__ldg(W + e));
         }
     }
-    for (int e = tid; e < kTcW * w1_ld(w0); e += kTcThreads) {
+    for (int e = tid; e < kTcW * w1_ld(w0); e += NT) {
         const int o = e / w1_ld(w0), i = e % w1_ld(w0);
         sW1[e] = i < w0 ? __ldg(theta + D.off[1] + o * w0 + i) : 0.f;
     }
     for (int l = 1; l < L; ++l)
-        for (int o = tid; o < kTcW; o += kTcThreads) sB[(l - 1) * kTcW + o] = __ldg(theta + D.off[l] + (int64_t)kTcW * D.w[l - 1] + o);
-    for (int i = tid; i <= kTcW; i += kTcThreads) sWL[i] = __ldg(theta + D.off[L] + i);
+        for (int o = tid; o < kTcW; o += NT) sB[(l - 1) * kTcW + o] = __ldg(theta + D.off[l] + (int64_t)kTcW * D.w[l - 1] + o);
+    for (int i = tid; i <= kTcW; i += NT) sWL[i] = __ldg(theta + D.off[L] + i);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_su32(&mbar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(MlpDesc D, const f
             float x[kMlpMaxIn];
 #pragma unroll
             for (int i = 0; i < kMlpMaxIn; ++i) x[i] = (i < w0 && s < n) ? __ldg(X + s * w0 + i) : 0.f;
-            for (int o0 = cb; o0 < cb + 64; o0 += 8) {
+            for (int o0 = cb; o0 < cb + CW; o0 += 8) {
                 float hv[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
@@ -589,7 +589,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(MlpDesc D, const f
             }
             const float *bl = sB + (l - 1) * kTcW;
             const bool last = l == L - 1;
-            for (int c0 = cb; c0 < cb + 64; c0 += 32) {
+            for (int c0 = cb; c0 < cb + CW; c0 += 32) {
                 float v[32];
                 tc_ld32(tmem + lane_off + (uint32_t)c0, v);
 #pragma unroll
@@ -608,7 +608,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(MlpDesc D, const f
         if (!ok) break;
         sY[warp >> 2][row] = yv;
         __syncthreads();
-        if (warp < 4 && s < n) Y[s] = sY[0][row] + sY[1][row] + sWL[kTcW];
+        if (warp < 4 && s < n) {
+            float t = sY[0][row];
+#pragma unroll
+            for (int q = 1; q < P; ++q) t += sY[q][row];
+            Y[s] = t + sWL[kTcW];
+        }
     }
     if (!ok) {
         for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -677,10 +682,12 @@ __host__ __device__ inline TgLayout tg_layout(const MlpDesc &D) {
     return t;
 }
 
-__global__ void __launch_bounds__(kTgThreads, 1)
+template <int P>
+__global__ void __launch_bounds__(128 * P, 1)
     k_mlp_grad_tc(MlpDesc D, const float *__restrict__ theta, const float *__restrict__ X,
                   const float *__restrict__ T, int64_t n, float *__restrict__ gpart, double *__restrict__ lpart,
                   float inv_n) {
+    constexpr int NT = 128 * P, CW = 128 / P, NG = kTgN1 / P;
     extern __shared__ __align__(1024) unsigned char tsm[];
     const TgLayout Ly = tg_layout(D);
     const int L = D.L, nm = Ly.nm, w0 = D.w[0];
@@ -693,13 +700,13 @@ __global__ void __launch_bounds__(kTgThreads, 1)
     float *sAcc = reinterpret_cast<float *>(tsm + Ly.acc);           // per lane group: db_2 .. db_{L-1}, dW_L
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
-    __shared__ float sY[2][kTcM];
-    __shared__ double sL[kTgThreads / 32];
-    __shared__ float sE[kTgThreads / 32];
+    __shared__ float sY[P][kTcM];
+    __shared__ double sL[NT / 32];
+    __shared__ float sE[NT / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row = 32 * (warp & 3) + lane;       // sample of the tile (and TMEM lane)
-    const int half = warp >> 2;                   // columns 64 half .. 64 half + 63
-    const int cb = 64 * half;
+    const int part = warp >> 2;                   // columns CW part .. CW part + CW - 1
+    const int cb = CW * part;
     const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
     auto buf = [&](int i) { return sBuf + (size_t)i * kTgTile; };
     // buffer of h_l: h_1 and h_{L-1} in buffer 0, h_l (2 <= l <= L-2) in buffer l-1;
@@ -710,21 +717,21 @@ __global__ void __launch_bounds__(kTgThreads, 1)
     for (int l = 2; l < L; ++l) {
         const float *W = theta + D.off[l];
         unsigned char *dst = sW + (size_t)(l - 2) * kTgTile;
-        for (int e = tid; e < kTcW * kTcW; e += kTgThreads) {
+        for (int e = tid; e < kTcW * kTcW; e += NT) {
             const int o = e / kTcW, i = e % kTcW;
             *reinterpret_cast<__nv_bfloat16 *>(dst + tc_off(o, i)) = __float2bfloat16_rn(__ldg(W + e));
         }
     }
-    for (int e = tid; e < kTcW * w1_ld(w0); e += kTgThreads) {
+    for (int e = tid; e < kTcW * w1_ld(w0); e += NT) {
         const int o = e / w1_ld(w0), i = e % w1_ld(w0);
         sW1[e] = i < w0 ? __ldg(theta + D.off[1] + o * w0 + i) : 0.f;
     }
     for (int l = 1; l < L; ++l)
-        for (int o = tid; o < kTcW; o += kTgThreads)
+        for (int o = tid; o < kTcW; o += NT)
             sB[(l - 1) * kTcW + o] = __ldg(theta + D.off[l] + (int64_t)kTcW * D.w[l - 1] + o);
-    for (int i = tid; i <= kTcW; i += kTgThreads) sWL[i] = __ldg(theta + D.off[L] + i);
-    for (int e = tid; e < 4 * (nm + 1) * kTcW; e += kTgThreads) sAcc[e] = 0.f;
-    for (int e = tid; e < kTgN1 * kTcM / 8; e += kTgThreads) reinterpret_cast<uint4 *>(sX)[e] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i <= kTcW; i += NT) sWL[i] = __ldg(theta + D.off[L] + i);
+    for (int e = tid; e < 4 * (nm + 1) * kTcW; e += NT) sAcc[e] = 0.f;
+    for (int e = tid; e < kTgN1 * kTcM / 8; e += NT) reinterpret_cast<uint4 *>(sX)[e] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_su32(&mbar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -741,15 +748,15 @@ __global__ void __launch_bounds__(kTgThreads, 1)
     unsigned parity = 0;
     bool ok = true, first = true;
     double lsum = 0.0;
-    float gb_out = 0.f;            // db_L share of this thread (half 0 only)
-    float gW1[kTgN1 / 2];          // dW_1 row `row`, columns 16 half .. 16 half + 15 of [x, 1, 0]
+    float gb_out = 0.f;            // db_L share of this thread (part 0 only)
+    float gW1[NG];                 // dW_1 row `row`, columns NG part .. NG part + NG - 1 of [x, 1, 0]
 #pragma unroll
-    for (int j = 0; j < kTgN1 / 2; ++j) gW1[j] = 0.f;
+    for (int j = 0; j < NG; ++j) gW1[j] = 0.f;
     float xr[kMlpMaxIn];
 
     // h_1 of this thread's sample over its 64 columns, rounded to BF16 into dst
     auto layer1 = [&](unsigned char *dst) {
-        for (int o0 = cb; o0 < cb + 64; o0 += 8) {
+        for (int o0 = cb; o0 < cb + CW; o0 += 8) {
             float hv[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -766,8 +773,8 @@ __global__ void __launch_bounds__(kTgThreads, 1)
         const bool valid = s < n;
 #pragma unroll
         for (int i = 0; i < kMlpMaxIn; ++i) xr[i] = (i < w0 && valid) ? __ldg(X + s * w0 + i) : 0.f;
-        // [x, 1] of the sample as column `row` of the first-layer operand (half 0 writes it)
-        if (half == 0) {
+        // [x, 1] of the sample as column `row` of the first-layer operand (part 0 writes it)
+        if (part == 0) {
 #pragma unroll
             for (int i = 0; i < kMlpMaxIn; ++i)
                 if (i <= w0)
@@ -792,7 +799,7 @@ __global__ void __launch_bounds__(kTgThreads, 1)
             const float *bl = sB + (l - 1) * kTcW;
             unsigned char *out = hbuf(l);
             const bool last = l == L - 1;
-            for (int c0 = cb; c0 < cb + 64; c0 += 32) {
+            for (int c0 = cb; c0 < cb + CW; c0 += 32) {
                 float v[32];
                 tc_ld32(twork + (uint32_t)c0, v);
 #pragma unroll
@@ -810,18 +817,21 @@ __global__ void __launch_bounds__(kTgThreads, 1)
         }
         if (!ok) break;
         // ---- output layer: y, e = 2 (y - t) / n, dW_L, db_L, e_{L-1}
-        sY[half][row] = yp;
+        sY[part][row] = yp;
         __syncthreads();
-        const float y = sY[0][row] + sY[1][row] + sWL[kTcW];
+        float ysum = sY[0][row];
+#pragma unroll
+        for (int q = 1; q < P; ++q) ysum += sY[q][row];
+        const float y = ysum + sWL[kTcW];
         const float dlt = valid ? y - __ldg(T + s) : 0.f;
-        if (half == 0) {
+        if (part == 0) {
             lsum += (double)dlt * (double)dlt;
             gb_out += 2.f * dlt * inv_n;
         }
         const float ey = 2.f * dlt * inv_n;
         {
             unsigned char *H = hbuf(L - 1);
-            for (int c0 = cb; c0 < cb + 64; c0 += 32) {
+            for (int c0 = cb; c0 < cb + CW; c0 += 32) {
                 float d[32], g[32];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -864,7 +874,7 @@ __global__ void __launch_bounds__(kTgThreads, 1)
                 ok = false;
                 break;
             }
-            for (int c0 = cb; c0 < cb + 64; c0 += 32) {
+            for (int c0 = cb; c0 < cb + CW; c0 += 32) {
                 float d[32];
                 tc_ld32(twork + (uint32_t)c0, d);
 #pragma unroll
@@ -900,7 +910,11 @@ __global__ void __launch_bounds__(kTgThreads, 1)
             float v[32];
             tc_ld32(twork, v);
 #pragma unroll
-            for (int j = 0; j < kTgN1 / 2; ++j) gW1[j] += half ? v[kTgN1 / 2 + j] : v[j];
+            for (int j = 0; j < NG; ++j) {
+#pragma unroll
+                for (int q = 0; q < P; ++q)
+                    if (q == part) gW1[j] += v[NG * q + j];
+            }
         }
         first = false;
     }
@@ -911,7 +925,7 @@ __global__ void __launch_bounds__(kTgThreads, 1)
     if (ok) {
         for (int l = 2; l < L; ++l) {
             const uint32_t tacc = tmem + (uint32_t)(kTcW * (l - 1)) + lane_off;
-            for (int c0 = cb; c0 < cb + 64; c0 += 32) {
+            for (int c0 = cb; c0 < cb + CW; c0 += 32) {
                 float v[32];
                 tc_ld32(tacc + (uint32_t)c0, v);
                 float *p = g + D.off[l] + (int64_t)row * kTcW + c0;
@@ -919,7 +933,7 @@ __global__ void __launch_bounds__(kTgThreads, 1)
                 for (int j = 0; j < 32; ++j) p[j] = first ? 0.f : v[j];
             }
         }
-        for (int o = tid; o < kTcW; o += kTgThreads) {
+        for (int o = tid; o < kTcW; o += NT) {
             for (int v = 0; v <= nm; ++v) {
                 float t = 0.f;
                 for (int w = 0; w < 4; ++w) t += sAcc[(w * (nm + 1) + v) * kTcW + o];
@@ -928,8 +942,8 @@ __global__ void __launch_bounds__(kTgThreads, 1)
             }
         }
 #pragma unroll
-        for (int j = 0; j < kTgN1 / 2; ++j) {
-            const int i = (kTgN1 / 2) * half + j;
+        for (int j = 0; j < NG; ++j) {
+            const int i = NG * part + j;
             if (i < w0) g[D.off[1] + (int64_t)row * w0 + i] = gW1[j];
             else if (i == w0) g[D.off[1] + (int64_t)kTcW * w0 + row] = gW1[j];
         }
@@ -948,7 +962,7 @@ __global__ void __launch_bounds__(kTgThreads, 1)
     if (tid == 0) {
         float te = 0.f;
         double tl = 0.0;
-        for (int w = 0; w < kTgThreads / 32; ++w) {
+        for (int w = 0; w < NT / 32; ++w) {
             te += sE[w];
             tl += sL[w];
         }
@@ -956,7 +970,7 @@ __global__ void __launch_bounds__(kTgThreads, 1)
         lpart[blockIdx.x] = ok ? tl : (double)__int_as_float(0x7fc00000);
     }
     if (!ok)
-        for (int64_t p = tid; p < D.np; p += kTgThreads) g[p] = __int_as_float(0x7fc00000);
+        for (int64_t p = tid; p < D.np; p += NT) g[p] = __int_as_float(0x7fc00000);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
@@ -968,6 +982,9 @@ static bool mlp_tg_shape(const MlpDesc &D) {
 
 static int g_mlp_tc = 1;
 void set_mlp_tensor_cores(int on) { g_mlp_tc = on; }
+// threads per sample of the tensor-core kernels: 2 (256 per CTA) or 4 (512)
+static int g_mlp_tc_parts = 4;
+void set_mlp_tc_threads(int threads) { g_mlp_tc_parts = threads / 128; }
 
 // grad[p] = sum over CTA slices (fixed order); loss = sum of partials / n.
 __global__ void k_mlp_reduce(const float *__restrict__ gpart, int nslices, int64_t np, float *__restrict__ grad,
@@ -1033,14 +1050,16 @@ rfm_status launch_mlp_forward(const rfm_mlp *net, const float *theta, const floa
     if (n <= 0) return RFM_OK;
     if (g_mlp_tc && mlp_tc_shape(D) && mlp_tc_smem(D) <= 200 * 1024) {
         const size_t smem = mlp_tc_smem(D);
-        RFM_CUDA_CHECK(cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RFM_CUDA_CHECK(cudaFuncSetAttribute(k_mlp_fwd_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RFM_CUDA_CHECK(cudaFuncSetAttribute(k_mlp_fwd_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int dev = 0, nsm = 0;
         RFM_CUDA_CHECK(cudaGetDevice(&dev));
         RFM_CUDA_CHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         const int64_t tiles = (n + kTcM - 1) / kTcM;
         const int grid = (int)(tiles < nsm ? tiles : nsm);
         ProfScope ps("k_mlp_fwd_tc", st);
-        k_mlp_fwd_tc<<<grid, kTcThreads, smem, st>>>(D, theta, X, n, Y);
+        if (g_mlp_tc_parts == 4) k_mlp_fwd_tc<4><<<grid, 512, smem, st>>>(D, theta, X, n, Y);
+        else k_mlp_fwd_tc<2><<<grid, 256, smem, st>>>(D, theta, X, n, Y);
         RFM_CUDA_CHECK(cudaGetLastError());
         return RFM_OK;
     }
@@ -1075,7 +1094,8 @@ rfm_status launch_mlp_grad(const rfm_mlp *net, const float *theta, const float *
     int grid;
     if (g_mlp_tc && mlp_tg_shape(D)) {
         const size_t smem = tg_layout(D).total;
-        RFM_CUDA_CHECK(cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RFM_CUDA_CHECK(cudaFuncSetAttribute(k_mlp_grad_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RFM_CUDA_CHECK(cudaFuncSetAttribute(k_mlp_grad_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int dev = 0, nsm = 0;
         RFM_CUDA_CHECK(cudaGetDevice(&dev));
         RFM_CUDA_CHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -1083,7 +1103,10 @@ rfm_status launch_mlp_grad(const rfm_mlp *net, const float *theta, const float *
         grid = (int)(tiles < nsm ? tiles : nsm);
         if (grid > kMlpMaxCtas) grid = kMlpMaxCtas;
         ProfScope ps("k_mlp_grad_tc", st);
-        k_mlp_grad_tc<<<grid, kTgThreads, smem, st>>>(D, theta, X, T, n, gpart, lpart, (float)(1.0 / n));
+        if (g_mlp_tc_parts == 4)
+            k_mlp_grad_tc<4><<<grid, 512, smem, st>>>(D, theta, X, T, n, gpart, lpart, (float)(1.0 / n));
+        else
+            k_mlp_grad_tc<2><<<grid, 256, smem, st>>>(D, theta, X, T, n, gpart, lpart, (float)(1.0 / n));
         RFM_CUDA_CHECK(cudaGetLastError());
     } else {
         const size_t smem = (size_t)D.smem_floats * 4;

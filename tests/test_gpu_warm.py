@@ -268,6 +268,32 @@ def test_training_on_the_gpu_fits_a_teacher(rfm):
 
 
 
+
+def test_tensor_core_thread_counts_agree(rfm):
+    """256 and 512 threads per CTA (two or four threads per sample): the same
+    MMAs and per-element epilogues; only the output layer's dot product is
+    summed in another order, so outputs and gradients agree to FP32 rounding."""
+    from paper_2506_17626_gb300 import _native as N
+    w = [9, 128, 128, 128, 128, 1]
+    M = rfm.Mlp(w)
+    th = torch.from_numpy(_net(w, 21, scale=0.3)).cuda()
+    rng = np.random.default_rng(21)
+    X = torch.from_numpy(rng.uniform(-1, 1, (3001, 9)).astype(np.float32)).cuda()
+    T = torch.from_numpy(rng.standard_normal(3001).astype(np.float32)).cuda()
+    out = {}
+    for threads in (256, 512):
+        N.set_mlp_tc_threads(threads)
+        try:
+            y = M.forward(th, X).cpu().numpy()
+            g, lo = M.grad(th, X, T)
+            out[threads] = (y, g.cpu().numpy(), float(lo.item()))
+        finally:
+            N.set_mlp_tc_threads(512)
+    (y2, g2, l2), (y4, g4, l4) = out[256], out[512]
+    assert np.abs(y2 - y4).max() <= 1e-5 * max(1.0, np.abs(y2).max())
+    assert np.abs(g2 - g4).max() <= 1e-4 * np.abs(g2).max()
+    assert l2 == pytest.approx(l4, rel=1e-5)
+
 def test_tensor_core_training_tracks_fp32_training(rfm):
     """Adam on a 4-128x3-1 teacher with the tcgen05 gradient and with the FP32
     one from the same start: both reduce the loss below a fifth of its first
