@@ -371,14 +371,24 @@ __device__ inline bool tc_wait(uint64_t *mbar, unsigned parity) {
     return false;
 }
 
-// tanh(x) = 1 - 2 / (1 + e^{2x}), e^{2x} = 2^{(2 / ln 2) x} by the SFU's base-2
-// exponential and its reciprocal: absolute error about 1e-7, +-1 for large
-// |x|.  The tensor-core paths round the result to BF16 (8 significant bits).
-__device__ __forceinline__ float tanh_sfu(float x) {
+// tanh(x) = 1 - 2 / (1 + e^{2x}) with e^{2x} = 2^{xk}, xk = (2 / ln 2) x, by the
+// SFU's base-2 exponential and its reciprocal: absolute error about 1e-7, +-1
+// for large |x|; the tensor-core paths round the result to BF16 (8
+// significant bits).  The kernels keep the biases and the first layer's
+// weights scaled by kTanhK, so that a pre-activation v + b enters as
+// fma(v, kTanhK, b kTanhK).
+constexpr float kTanhK = 2.88539008f;
+__device__ __forceinline__ float tanh_sfu_k(float xk) {
     float e, r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(x * 2.88539008f));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(xk));
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.f + e));
     return fmaf(-2.f, r, 1.f);
+}
+
+// 8 consecutive floats of shared memory (16-byte aligned)
+__device__ __forceinline__ void lds8(const float *p, float (&v)[8]) {
+    const float4 a = reinterpret_cast<const float4 *>(p)[0], b = reinterpret_cast<const float4 *>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
 }
 
 // first-layer weights in shared memory with the row stride padded to 4 floats
@@ -535,10 +545,11 @@ __global__ void __launch_bounds__(128 * P, 1) k_mlp_fwd_tc(MlpDesc D, const floa
     }
     for (int e = tid; e < kTcW * w1_ld(w0); e += NT) {
         const int o = e / w1_ld(w0), i = e % w1_ld(w0);
-        sW1[e] = i < w0 ? __ldg(theta + D.off[1] + o * w0 + i) : 0.f;
+        sW1[e] = i < w0 ? kTanhK * __ldg(theta + D.off[1] + o * w0 + i) : 0.f;
     }
     for (int l = 1; l < L; ++l)
-        for (int o = tid; o < kTcW; o += NT) sB[(l - 1) * kTcW + o] = __ldg(theta + D.off[l] + (int64_t)kTcW * D.w[l - 1] + o);
+        for (int o = tid; o < kTcW; o += NT)
+            sB[(l - 1) * kTcW + o] = kTanhK * __ldg(theta + D.off[l] + (int64_t)kTcW * D.w[l - 1] + o);
     for (int i = tid; i <= kTcW; i += NT) sWL[i] = __ldg(theta + D.off[L] + i);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_su32(&mbar)) : "memory");
@@ -567,7 +578,7 @@ __global__ void __launch_bounds__(128 * P, 1) k_mlp_fwd_tc(MlpDesc D, const floa
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int o = o0 + j;
-                    hv[j] = tanh_sfu(layer1_dot(sW1, w1_ld(w0), w0, o, sB[o], x));
+                    hv[j] = tanh_sfu_k(layer1_dot(sW1, w1_ld(w0), w0, o, sB[o], x));
                 }
                 bf16x8_store(sAct + tc_off(row, o0), hv);
             }
@@ -594,14 +605,18 @@ __global__ void __launch_bounds__(128 * P, 1) k_mlp_fwd_tc(MlpDesc D, const floa
                 tc_ld32(tmem + lane_off + (uint32_t)c0, v);
 #pragma unroll
                 for (int g = 0; g < 4; ++g) {
-                    float hv[8];
+                    float hv[8], bk[8];
+                    lds8(bl + c0 + 8 * g, bk);
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int o = c0 + 8 * g + j;
-                        hv[j] = tanh_sfu(v[8 * g + j] + bl[o]);
-                        if (last) yv = fmaf(hv[j], sWL[o], yv);
+                    for (int j = 0; j < 8; ++j) hv[j] = tanh_sfu_k(fmaf(v[8 * g + j], kTanhK, bk[j]));
+                    if (last) {
+                        float wl[8];
+                        lds8(sWL + c0 + 8 * g, wl);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) yv = fmaf(hv[j], wl[j], yv);
+                    } else {
+                        bf16x8_store(Aout + tc_off(row, c0 + 8 * g), hv);
                     }
-                    if (!last) bf16x8_store(Aout + tc_off(row, c0 + 8 * g), hv);
                 }
             }
         }
@@ -724,11 +739,11 @@ __global__ void __launch_bounds__(128 * P, 1)
     }
     for (int e = tid; e < kTcW * w1_ld(w0); e += NT) {
         const int o = e / w1_ld(w0), i = e % w1_ld(w0);
-        sW1[e] = i < w0 ? __ldg(theta + D.off[1] + o * w0 + i) : 0.f;
+        sW1[e] = i < w0 ? kTanhK * __ldg(theta + D.off[1] + o * w0 + i) : 0.f;
     }
     for (int l = 1; l < L; ++l)
         for (int o = tid; o < kTcW; o += NT)
-            sB[(l - 1) * kTcW + o] = __ldg(theta + D.off[l] + (int64_t)kTcW * D.w[l - 1] + o);
+            sB[(l - 1) * kTcW + o] = kTanhK * __ldg(theta + D.off[l] + (int64_t)kTcW * D.w[l - 1] + o);
     for (int i = tid; i <= kTcW; i += NT) sWL[i] = __ldg(theta + D.off[L] + i);
     for (int e = tid; e < 4 * (nm + 1) * kTcW; e += NT) sAcc[e] = 0.f;
     for (int e = tid; e < kTgN1 * kTcM / 8; e += NT) reinterpret_cast<uint4 *>(sX)[e] = make_uint4(0, 0, 0, 0);
@@ -761,7 +776,7 @@ __global__ void __launch_bounds__(128 * P, 1)
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int o = o0 + j;
-                hv[j] = tanh_sfu(layer1_dot(sW1, w1_ld(w0), w0, o, sB[o], xr));
+                hv[j] = tanh_sfu_k(layer1_dot(sW1, w1_ld(w0), w0, o, sB[o], xr));
             }
             bf16x8_store(dst + tc_off(row, o0), hv);
         }
@@ -804,12 +819,15 @@ __global__ void __launch_bounds__(128 * P, 1)
                 tc_ld32(twork + (uint32_t)c0, v);
 #pragma unroll
                 for (int g = 0; g < 4; ++g) {
-                    float hv[8];
+                    float hv[8], bk[8];
+                    lds8(bl + c0 + 8 * g, bk);
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int o = c0 + 8 * g + j;
-                        hv[j] = tanh_sfu(v[8 * g + j] + bl[o]);
-                        if (last) yp = fmaf(hv[j], sWL[o], yp);
+                    for (int j = 0; j < 8; ++j) hv[j] = tanh_sfu_k(fmaf(v[8 * g + j], kTanhK, bk[j]));
+                    if (last) {
+                        float wl[8];
+                        lds8(sWL + c0 + 8 * g, wl);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) yp = fmaf(hv[j], wl[j], yp);
                     }
                     bf16x8_store(out + tc_off(row, c0 + 8 * g), hv);
                 }
@@ -835,13 +853,13 @@ __global__ void __launch_bounds__(128 * P, 1)
                 float d[32], g[32];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    float hb[8];
+                    float hb[8], wl[8];
                     bf16x8_load(H + tc_off(row, c0 + 8 * q), hb);
+                    lds8(sWL + c0 + 8 * q, wl);
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
-                        const int o = c0 + 8 * q + j;
                         g[8 * q + j] = ey * hb[j];
-                        d[8 * q + j] = ey * sWL[o] * (1.f - hb[j] * hb[j]);
+                        d[8 * q + j] = ey * wl[j] * (1.f - hb[j] * hb[j]);
                     }
                     float dq[8];
 #pragma unroll
