@@ -316,6 +316,22 @@ rfm_status rfm_mlp_grad(const rfm_mlp *net, const float *d_theta, const float *d
 rfm_status rfm_adam_step(int64_t n, float *d_theta, float *d_m, float *d_v, const float *d_g, int t, float lr,
                          float beta1, float beta2, float eps, void *stream);
 
+/* Minibatch training loop on the host side of the library: n_steps steps,
+ * step k gathering the batch d_x[d_order[k batch + s], :], d_t[...] (s <
+ * batch; d_order: device int64, n_steps * batch sample indices, each < the
+ * caller's sample count), then rfm_mlp_grad on it and rfm_adam_step with step
+ * number t0 + k and learning rate lr[k] (host array of n_steps floats).
+ * d_loss (device, n_steps floats, may be NULL) receives each step's batch
+ * loss.  Parameters and moments are updated in place, exactly as the
+ * separate calls would, without a host round trip between the steps'
+ * launches.  d_ws: 256-byte aligned, rfm_mlp_train_size bytes for this batch
+ * size.  Not in the paper: the training of the warm-start network. */
+rfm_status rfm_mlp_train_size(const rfm_mlp *net, int batch, size_t *ws_bytes);
+rfm_status rfm_mlp_train(const rfm_mlp *net, float *d_theta, float *d_m, float *d_v, const float *d_x,
+                         const float *d_t, const int64_t *d_order, int batch, int n_steps, int t0, const float *lr,
+                         float beta1, float beta2, float eps, float *d_loss, void *d_ws, size_t ws_bytes,
+                         void *stream);
+
 /* Device-side copies of the assembled blocks for inspection and tests:
  * block b's M_j (|I_j| x K, column-major with leading dimension *ld) starts at
  * element offset *moff of the M arena, and its rows are the global rows

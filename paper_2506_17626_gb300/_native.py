@@ -91,6 +91,9 @@ def load(path: str = LIB_PATH):
         "rfm_mlp_forward": [C.POINTER(RfmMlp), vp, vp, i64, vp, vp],
         "rfm_mlp_grad": [C.POINTER(RfmMlp), vp, vp, vp, i64, vp, vp, vp, C.c_size_t, vp],
         "rfm_adam_step": [i64, vp, vp, vp, vp, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, vp],
+        "rfm_mlp_train_size": [C.POINTER(RfmMlp), C.c_int, C.POINTER(C.c_size_t)],
+        "rfm_mlp_train": [C.POINTER(RfmMlp), vp, vp, vp, vp, vp, vp, C.c_int, C.c_int, C.c_int, vp, C.c_float,
+                          C.c_float, C.c_float, vp, vp, C.c_size_t, vp],
     }
     for name, args in sigs.items():
         f = getattr(L, name)

@@ -255,6 +255,26 @@ class Mlp:
                                                       _stream()))
         return g, lo
 
+    def train_steps(self, theta, m, v, X: torch.Tensor, T: torch.Tensor, order: torch.Tensor, batch: int,
+                    t0: int, lrs, b1=0.9, b2=0.999, eps=1e-8, loss: Optional[torch.Tensor] = None):
+        """len(lrs) minibatch steps in one library call: step k takes the samples
+        order[k batch:(k+1) batch] (int64, on the device), the loss gradient
+        and an Adam step with number t0 + k and rate lrs[k]."""
+        n_steps = len(lrs)
+        assert order.dtype == torch.int64 and order.is_contiguous() and order.numel() >= n_steps * batch
+        assert X.dtype == torch.float32 and T.dtype == torch.float32 and X.is_contiguous() and T.is_contiguous()
+        wsb = C.c_size_t()
+        N.check("rfm_mlp_train_size", self.lib.rfm_mlp_train_size(C.byref(self._net), int(batch), C.byref(wsb)))
+        if getattr(self, "_tws_bytes", 0) < wsb.value:
+            self._tws = torch.empty(wsb.value + 256, dtype=torch.uint8, device=self.device)
+            self._tws_bytes = wsb.value
+        ptr = self._tws.data_ptr() + (-self._tws.data_ptr()) % 256
+        lr_arr = (C.c_float * max(1, n_steps))(*[float(r) for r in lrs])
+        N.check("rfm_mlp_train", self.lib.rfm_mlp_train(C.byref(self._net), _ptr(theta), _ptr(m), _ptr(v), _ptr(X),
+                                                        _ptr(T), _ptr(order), int(batch), int(n_steps), int(t0),
+                                                        lr_arr, float(b1), float(b2), float(eps), _ptr(loss),
+                                                        C.c_void_p(ptr), self._tws_bytes, _stream()))
+
     def adam_step(self, theta, m, v, g, t: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         N.check("rfm_adam_step", self.lib.rfm_adam_step(theta.numel(), _ptr(theta), _ptr(m), _ptr(v), _ptr(g), int(t),
                                                         float(lr), float(b1), float(b2), float(eps), _stream()))

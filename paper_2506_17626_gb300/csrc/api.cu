@@ -36,6 +36,10 @@ rfm_status mlp_nparams(const rfm_mlp *net, int64_t *np);
 rfm_status mlp_workspace(const rfm_mlp *net, size_t *bytes);
 rfm_status launch_mlp_forward(const rfm_mlp *net, const float *theta, const float *X, int64_t n, float *Y,
                               cudaStream_t st);
+rfm_status mlp_train_size(const rfm_mlp *net, int batch, size_t *bytes);
+rfm_status launch_mlp_train(const rfm_mlp *net, float *theta, float *m, float *v, const float *X, const float *T,
+                            const int64_t *order, int batch, int n_steps, int t0, const float *lr, float b1, float b2,
+                            float eps, float *loss, void *ws, size_t ws_bytes, cudaStream_t st);
 rfm_status launch_mlp_grad(const rfm_mlp *net, const float *theta, const float *X, const float *T, int64_t n,
                            float *grad, float *loss, void *ws, size_t ws_bytes, cudaStream_t st);
 rfm_status launch_adam(int64_t n, float *theta, float *m, float *v, const float *g, int t, float lr, float b1,
@@ -484,6 +488,30 @@ rfm_status rfm_mlp_grad(const rfm_mlp *net, const float *d_theta, const float *d
         return RFM_EINVAL;
     }
     return launch_mlp_grad(net, d_theta, d_x, d_t, n, d_grad, d_loss, d_ws, ws_bytes, (cudaStream_t)stream);
+    RFM_GUARD_END
+}
+
+rfm_status rfm_mlp_train_size(const rfm_mlp *net, int batch, size_t *ws_bytes) {
+    RFM_GUARD_BEGIN
+    if (!ws_bytes) {
+        set_error("rfm_mlp_train_size: ws_bytes is NULL");
+        return RFM_EINVAL;
+    }
+    return mlp_train_size(net, batch, ws_bytes);
+    RFM_GUARD_END
+}
+
+rfm_status rfm_mlp_train(const rfm_mlp *net, float *d_theta, float *d_m, float *d_v, const float *d_x,
+                         const float *d_t, const int64_t *d_order, int batch, int n_steps, int t0, const float *lr,
+                         float beta1, float beta2, float eps, float *d_loss, void *d_ws, size_t ws_bytes,
+                         void *stream) {
+    RFM_GUARD_BEGIN
+    if (!d_theta || !d_m || !d_v || !d_x || !d_t || !d_order || (n_steps > 0 && !lr)) {
+        set_error("rfm_mlp_train: null argument");
+        return RFM_EINVAL;
+    }
+    return launch_mlp_train(net, d_theta, d_m, d_v, d_x, d_t, d_order, batch, n_steps, t0, lr, beta1, beta2, eps,
+                            d_loss, d_ws, ws_bytes, (cudaStream_t)stream);
     RFM_GUARD_END
 }
 

@@ -1143,6 +1143,80 @@ rfm_status launch_mlp_grad(const rfm_mlp *net, const float *theta, const float *
     return RFM_OK;
 }
 
+// Minibatch gather: xb[s, :] = X[order[s], :], tb[s] = T[order[s]].
+__global__ void k_gather_batch(const float *__restrict__ X, const float *__restrict__ T,
+                               const int64_t *__restrict__ order, int batch, int w0, float *__restrict__ xb,
+                               float *__restrict__ tb) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)batch * (w0 + 1);
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = e / (w0 + 1);
+        const int i = (int)(e - s * (w0 + 1));
+        const int64_t src = order[s];
+        if (i < w0) xb[s * w0 + i] = X[src * w0 + i];
+        else tb[s] = T[src];
+    }
+}
+
+// Workspace of the training loop: the gradient's workspace, the gradient,
+// and the gathered batch.
+static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+size_t mlp_train_bytes(const MlpDesc &D, int batch) {
+    return align256(mlp_workspace_bytes(D)) + align256((size_t)D.np * 4) + align256((size_t)batch * D.w[0] * 4) +
+           align256((size_t)batch * 4);
+}
+
+rfm_status mlp_train_size(const rfm_mlp *net, int batch, size_t *bytes) {
+    MlpDesc D;
+    rfm_status rc = mlp_desc(net, &D);
+    if (rc != RFM_OK) return rc;
+    if (batch < 1) {
+        set_error("rfm_mlp_train_size: batch must be >= 1");
+        return RFM_EINVAL;
+    }
+    *bytes = mlp_train_bytes(D, batch);
+    return RFM_OK;
+}
+
+rfm_status launch_adam(int64_t n, float *theta, float *m, float *v, const float *g, int t, float lr, float b1,
+                       float b2, float eps, cudaStream_t st);
+
+rfm_status launch_mlp_train(const rfm_mlp *net, float *theta, float *m, float *v, const float *X, const float *T,
+                            const int64_t *order, int batch, int n_steps, int t0, const float *lr, float b1, float b2,
+                            float eps, float *loss, void *ws, size_t ws_bytes, cudaStream_t st) {
+    MlpDesc D;
+    rfm_status rc = mlp_desc(net, &D);
+    if (rc != RFM_OK) return rc;
+    if (batch < 1 || n_steps < 0 || t0 < 1) {
+        set_error("rfm_mlp_train: need batch >= 1, n_steps >= 0, t0 >= 1");
+        return RFM_EINVAL;
+    }
+    const size_t need = mlp_train_bytes(D, batch);
+    if (!ws || ws_bytes < need || ((uintptr_t)ws & 255)) {
+        set_error("rfm_mlp_train: workspace must be 256-byte aligned with at least %zu bytes", need);
+        return RFM_ENOSPACE;
+    }
+    char *w = static_cast<char *>(ws);
+    const size_t gws = align256(mlp_workspace_bytes(D));
+    float *g = reinterpret_cast<float *>(w + gws);
+    float *xb = reinterpret_cast<float *>(w + gws + align256((size_t)D.np * 4));
+    float *tb = reinterpret_cast<float *>(w + gws + align256((size_t)D.np * 4) + align256((size_t)batch * D.w[0] * 4));
+    const int64_t work = (int64_t)batch * (D.w[0] + 1);
+    const unsigned gblocks = (unsigned)((work + 255) / 256 < 1024 ? (work + 255) / 256 : 1024);
+    for (int k = 0; k < n_steps; ++k) {
+        {
+            ProfScope ps("k_gather_batch", st);
+            k_gather_batch<<<gblocks, 256, 0, st>>>(X, T, order + (int64_t)k * batch, batch, D.w[0], xb, tb);
+            RFM_CUDA_CHECK(cudaGetLastError());
+        }
+        rc = launch_mlp_grad(net, theta, xb, tb, batch, g, loss ? loss + k : nullptr, ws, gws, st);
+        if (rc != RFM_OK) return rc;
+        rc = launch_adam(D.np, theta, m, v, g, t0 + k, lr[k], b1, b2, eps, st);
+        if (rc != RFM_OK) return rc;
+    }
+    return RFM_OK;
+}
+
 rfm_status launch_adam(int64_t n, float *theta, float *m, float *v, const float *g, int t, float lr, float b1,
                        float b2, float eps, cudaStream_t st) {
     if (n <= 0 || t < 1 || !(lr >= 0.f) || !(b1 >= 0.f && b1 < 1.f) || !(b2 >= 0.f && b2 < 1.f) || !(eps > 0.f)) {

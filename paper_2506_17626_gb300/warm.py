@@ -83,27 +83,21 @@ class LearnedWarmStart:
         """Adam on minibatches (reshuffled every epoch); returns the mean loss
         of every epoch.  With lr_final the rate decays geometrically to it."""
         n = X.shape[0]
+        batch = min(batch, n)
         gen = torch.Generator(device=self.device)
         gen.manual_seed(seed)
-        g = torch.empty_like(self.theta)
-        loss = torch.zeros(1, dtype=torch.float32, device=self.device)
         hist = []
         nb = max(1, n // batch)
         total = epochs * nb
+        losses = torch.zeros(nb, dtype=torch.float32, device=self.device)
         for e in range(epochs):
             perm = torch.randperm(n, generator=gen, device=self.device)
-            acc = torch.zeros(1, dtype=torch.float32, device=self.device)
-            for b in range(nb):
-                sel = perm[b * batch:(b + 1) * batch]
-                xb = X.index_select(0, sel).contiguous()
-                tb = T.index_select(0, sel).contiguous()
-                self.net.grad(self.theta, xb, tb, out=g, loss=loss)
-                self.step += 1
-                k = e * nb + b
-                rate = lr if lr_final is None else lr * (lr_final / lr) ** (k / max(1, total - 1))
-                self.net.adam_step(self.theta, self.m, self.v, g, self.step, lr=rate)
-                acc += loss
-            hist.append(float(acc.item()) / nb)
+            rates = [lr if lr_final is None else lr * (lr_final / lr) ** ((e * nb + b) / max(1, total - 1))
+                     for b in range(nb)]
+            # one library call per epoch: gather, gradient and Adam for every batch
+            self.net.train_steps(self.theta, self.m, self.v, X, T, perm, batch, self.step + 1, rates, loss=losses)
+            self.step += nb
+            hist.append(float(losses.sum().item()) / nb)
         return hist
 
     # -- use -----------------------------------------------------------------------------

@@ -294,6 +294,40 @@ def test_tensor_core_thread_counts_agree(rfm):
     assert np.abs(g2 - g4).max() <= 1e-4 * np.abs(g2).max()
     assert l2 == pytest.approx(l4, rel=1e-5)
 
+
+@pytest.mark.parametrize("tc", [True, False])
+def test_training_loop_equals_separate_calls(rfm, tc):
+    """rfm_mlp_train (gather, gradient and Adam per step inside the library)
+    leaves the parameters, the moments and the per-step losses bitwise where
+    the separate calls (index_select, rfm_mlp_grad, rfm_adam_step) leave them."""
+    from paper_2506_17626_gb300 import _native as N
+    w = [9, 128, 128, 128, 128, 1]
+    M = rfm.Mlp(w)
+    rng = np.random.default_rng(31)
+    X = torch.from_numpy(rng.uniform(-1, 1, (5000, 9)).astype(np.float32)).cuda()
+    T = torch.from_numpy(rng.standard_normal(5000).astype(np.float32)).cuda()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(3)
+    order = torch.randperm(5000, generator=gen, device="cuda")
+    batch, lrs = 1200, [2e-3 * 0.8 ** k for k in range(4)]
+    th0 = torch.from_numpy(_net(w, 31, scale=0.2)).cuda()
+    N.set_mlp_tensor_cores(tc)
+    try:
+        th1, m1, v1 = th0.clone(), torch.zeros_like(th0), torch.zeros_like(th0)
+        l1 = []
+        for k, r in enumerate(lrs):
+            sel = order[k * batch:(k + 1) * batch]
+            g, lo = M.grad(th1, X.index_select(0, sel).contiguous(), T.index_select(0, sel).contiguous())
+            l1.append(lo.clone())
+            M.adam_step(th1, m1, v1, g, 7 + k, lr=r)
+        th2, m2, v2 = th0.clone(), torch.zeros_like(th0), torch.zeros_like(th0)
+        l2 = torch.zeros(len(lrs), dtype=torch.float32, device="cuda")
+        M.train_steps(th2, m2, v2, X, T, order, batch, 7, lrs, loss=l2)
+    finally:
+        N.set_mlp_tensor_cores(True)
+    assert torch.equal(th1, th2) and torch.equal(m1, m2) and torch.equal(v1, v2)
+    assert torch.equal(torch.cat(l1), l2)
+
 def test_tensor_core_training_tracks_fp32_training(rfm):
     """Adam on a 4-128x3-1 teacher with the tcgen05 gradient and with the FP32
     one from the same start: both reduce the loss below a fifth of its first
