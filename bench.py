@@ -27,6 +27,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -258,8 +259,7 @@ def run_gpu(args):
         per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
         return per, outs, prof_data
 
-    with Clocks(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp",
-                             "bench_clocks.csv")) as clk:
+    with Clocks(args.clocks_log) as clk:
         per_mixed, outs, prof = timed(paths["mixed"], kstar["mixed"], args.steps, args.warmup, prof=True)
     per_fp64, outs64, prof64 = timed(paths["fp64"], kstar["fp64"], args.steps, args.warmup, prof=True)
     per_e2e, outs_e2e, _ = timed(paths["mixed"], kstar["mixed"], args.steps, max(1, args.warmup // 2), e2e=True)
@@ -655,6 +655,8 @@ def main():
     ap.add_argument("--learned-train", type=int, default=384,
                     help="training solves of the learned warm start section (0 skips it)")
     ap.add_argument("--learned-epochs", type=int, default=6)
+    ap.add_argument("--clocks-log", default=os.path.join(tempfile.gettempdir(), "bench_clocks.csv"),
+                    help="CSV of the nvidia-smi clock samples taken during the timed region")
     ap.add_argument("--batched", type=int, default=64, help="instances of the batched section (0 skips it)")
     ap.add_argument("--batched-iters", type=int, default=2000)
     ap.add_argument("--case", default="full", choices=["full", "small"],
