@@ -243,7 +243,7 @@ rfm_status rfm_eval_noalloc(const rfm_problem *probs, int n_inst, const double *
  * the block's kept features, and the fitted coefficients c_j become the LSQR
  * starting point y0_j = R_j c_j of Algorithm 2's preconditioned unknowns
  * (pass it as y0 to rfm_lsqr_solve).  The stopping rule of the solve is
- * unchanged, so a zero start remains the fallback and the judge of the gain.
+ * unchanged, so a zero start remains the fallback and the yardstick for the gain.
  * ------------------------------------------------------------------------ */
 
 /* Network inputs at every block row (rows in the block-row layout of

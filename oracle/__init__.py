@@ -6,8 +6,10 @@ does.  The numerics live in ``rfm_oracle.c`` (plain FP64 loops written from the
 paper); this module only marshals numpy arrays through ctypes and strings the
 steps of Algorithm 2 together.
 
-Parity status of each function (what pins it) is listed in the design doc; every
-function here is pinned by a ``-m "not gpu"`` test in tests/test_oracle_*.py.
+Every function here is pinned by a ``-m "not gpu"`` test in
+tests/test_oracle_*.py against something other than itself (closed forms,
+invariants, numpy/scipy routines on tiny inputs, finite differences); the
+docstring of each test names its pin.
 """
 from __future__ import annotations
 

@@ -23,8 +23,8 @@
  *     and Proposition 3.1 (explicit Q_j, used only as a check);
  *   - solver: Algorithm 2 with LSQR (Paige and Saunders 1982), output a with
  *     zeros at dropped columns.
- * Readings of points where the paper is silent are listed in the design doc; the
- * ones that change arithmetic are restated at the function that uses them.
+ * Where the paper is silent, ambiguous or garbled, the reading taken is stated
+ * at the function whose arithmetic it decides.
  */
 #include <math.h>
 #include <stdint.h>

@@ -1470,7 +1470,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
         S.inv_bn[s] = sc[s].beta > 0.0 ? 1.0 / sc[s].beta : 0.0;
     }
     __syncthreads();
-    // vt = Op^T u~ / beta, ||vt||^2, fused with t = Op vt (round 1's forward product)
+    // vt = Op^T u~ / beta, ||vt||^2, fused with t = Op vt (the first loop pass's forward product)
     clear_w();
     __syncthreads();
     unsigned long long fphase = 1;

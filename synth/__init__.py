@@ -127,9 +127,11 @@ def feature_params(p: Problem, seed: Optional[int] = None) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
-# Workloads.  Sizes follow the published workload descriptions; the readings of
-# ambiguous items (overlap ratio = 1 + stated overlap fraction, collocation
-# counts, boundary point sets) are the ones listed in the design doc.
+# Workloads.  Sizes follow the published workload descriptions.  Readings of
+# ambiguous items: the overlap ratio (subdomain width over centre spacing) is
+# 1 + the stated overlap fraction; collocation points are cell-centred uniform
+# grids; boundary points lie on each face at the interior grid's cell-centred
+# coordinates in the other dimensions (so no point sits on a corner).
 # ---------------------------------------------------------------------------
 
 def poisson1d(S=20, K=100, n=1600, delta=1.3, R=5.0, seed=0, n_test=1000) -> Problem:
