@@ -66,6 +66,26 @@ def workload(case: str = "full"):
     return synth.poisson2d()
 
 
+def instance_seed(base_seed: int, rank: int) -> int:
+    """Seed of the instance rank `rank` solves: with N ranks every rank takes
+    its own independent instance (weak scaling, no collective in the data
+    path), seeds base_seed .. base_seed + N - 1."""
+    return base_seed + rank
+
+
+def max_over_ranks(v: float, world: int, device) -> float:
+    """Largest value of `v` over the ranks (the job's time is its slowest
+    rank's); a tensor on `device` (the rank's GPU under NCCL, the CPU under
+    gloo) carries it through one all-reduce."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -166,7 +186,7 @@ def run_gpu(args):
 
     p = workload(args.case)
     if world > 1:           # independent instances, one per rank (weak scaling)
-        p.seed = p.seed + rank
+        p.seed = instance_seed(p.seed, rank)
     prm = synth.feature_params(p)
     h_prm = torch.from_numpy(prm.ravel()).pin_memory()
     d_prm = h_prm.to(dev)
@@ -265,11 +285,7 @@ def run_gpu(args):
     per_e2e, outs_e2e, _ = timed(paths["mixed"], kstar["mixed"], args.steps, max(1, args.warmup // 2), e2e=True)
 
     def mx(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(v, world, dev)
 
     ms_mixed = mx(float(np.mean(per_mixed)))
     ms_fp64 = mx(float(np.mean(per_fp64)))
