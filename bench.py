@@ -362,6 +362,8 @@ def run_gpu(args):
         out["batched"] = run_batched(args, dev)
     if rank == 0 and world == 1 and args.learned_train > 0:
         out["learned"] = run_learned(args, dev)
+    if rank == 0 and world == 1 and not args.no_poisson1d:
+        out["poisson1d"] = guarded(run_poisson1d, args, dev)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -444,6 +446,66 @@ def run_batched(args, dev):
         "qr_gflops_algorithmic": qr_fl / (ev[1].elapsed_time(ev[2]) * 1e-3) / 1e9,
         "rel_l2": {"median": float(np.median(rel)), "max": float(rel.max())},
     }
+
+
+def run_poisson1d(args, dev):
+    """Time to 1e-6 relative L2 error on the 1D Poisson workload (-u'' = f on
+    [0,1], u = sin 2 pi x + 0.1 sin 50 pi x, 20 subdomains, overlap ratio
+    1.3, K = 100, 1600 interior points, FP64), which, unlike the 2D workload,
+    reaches it.  Calibration (untimed): zero-start LSQR for 10,000 iterations
+    with the iterate evaluated every 100, plain LSQR on the unfiltered M and
+    the filtered, preconditioned solver (R_hat^-1 operator) at thresholds 1e-6
+    and 1e-8.  Timed (CUDA events, after warm-up): assemble -> filter -> LSQR
+    for the first recorded iteration count at 1e-6 -> a = S^-1 y -> u_hat and
+    its error, for each threshold that reaches 1e-6; plain LSQR does not reach
+    it, and its best error and the time of its 10,000 iterations are
+    reported."""
+    import torch
+    import paper_2506_17626_gb300 as R
+    from paper_2506_17626_gb300 import sweep as SW
+    p = synth.poisson1d()
+    prm = torch.from_numpy(synth.feature_params(p).ravel()).to(dev)
+    X = torch.from_numpy(SW.grid_points(p)).to(dev)
+    runs = SW.sweep(p, prm, X, asm="fp64", op="ar64", sigmas=(1e-6, 1e-8), iters=10000, every=100, device=dev)
+    st = torch.cuda.current_stream()
+    out = {"workload": "1D Poisson, 20 subdomains, delta 1.3, K=100, 1600 interior + 2 boundary rows, FP64, "
+                       "error on 1000 test points", "target_rel_l2": 1e-6, "runs": []}
+    for r in runs:
+        row = {k: r[k] for k in ("op", "sigma", "dropped_pct", "min_rel_l2", "min_rel_l2_at", "min_e_l1",
+                                 "iterations_to", "lsqr_ms")}
+        k = r["iterations_to"]["1e-06"]
+        if k is not None:
+            S = R.System([p], asm="fp64", op=r["op"], tol=r["sigma"] or 0.0, device=str(dev))
+
+            def step():
+                S.assemble(prm)
+                S.filter()
+                a, _ = S.solve(atol=0.0, btol=0.0, max_iter=k)
+                return S.evaluate(prm, a, [X])[1]
+
+            for _ in range(max(3, args.warmup)):
+                step()
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(st)
+            for _ in range(args.steps):
+                err = step()
+            ev[1].record(st)
+            torch.cuda.synchronize()
+            e = SW.errors_from_sums(err.cpu().numpy(), X.shape[0])
+            row.update({"iterations": k, "time_to_target_ms": ev[0].elapsed_time(ev[1]) / args.steps,
+                        "rel_l2_reached": e["rel_l2"]})
+        out["runs"].append(row)
+    return out
+
+
+def guarded(fn, *a):
+    """A section of the JSON line that reports its failure instead of
+    aborting the benchmark."""
+    try:
+        return fn(*a)
+    except Exception as exc:           # noqa: BLE001
+        return {"error": f"{type(exc).__name__}: {exc}"}
 
 
 def run_learned(args, dev):
@@ -674,6 +736,7 @@ def main():
     ap.add_argument("--clocks-log", default=os.path.join(tempfile.gettempdir(), "bench_clocks.csv"),
                     help="CSV of the nvidia-smi clock samples taken during the timed region")
     ap.add_argument("--batched", type=int, default=64, help="instances of the batched section (0 skips it)")
+    ap.add_argument("--no-poisson1d", action="store_true", help="skip the 1D time-to-1e-6 section")
     ap.add_argument("--batched-iters", type=int, default=2000)
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: 10x10 subdomains with the same block shapes (profiler captures)")
