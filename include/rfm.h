@@ -24,9 +24,15 @@
  *    rfm_config must be passed to every call on a workspace.
  *  - Calls are asynchronous on the given CUDA stream (NULL = legacy default
  *    stream): results are valid once the stream has reached the call.  No
- *    call synchronises the host, allocates device memory, or runs numerics on
- *    the host.  Host-side work is limited to O(J + grid size) layout
- *    bookkeeping and one small upload in rfm_assemble.
+ *    call allocates device memory or runs numerics on the host.  Host-side
+ *    work is limited to O(J + grid size) layout bookkeeping.  Two calls
+ *    upload small host tables with cudaMemcpyAsync from pageable host memory:
+ *    rfm_assemble (instance and block records, work lists) and
+ *    rfm_eval_noalloc (instance records).  CUDA may wait for the stream's
+ *    earlier work before it stages such a copy, so these two calls can block
+ *    the host until the stream reaches them; no other call of the path
+ *    waits on the device (the QR autotuner and rfm_profile_read, which do,
+ *    say so below).
  *  - Every call returns an rfm_status; on failure rfm_last_error() (per host
  *    thread) describes it.  No C++ exception crosses the ABI.
  *  - Device pointers must be aligned to 16 bytes and the workspace to 256.
