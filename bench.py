@@ -46,6 +46,11 @@ CAL_ITERS = 10000
 # flop/clk/SM (2 DFMA lanes) x 2.07 GHz = 1258 GFLOP/s (a DFMA probe measured
 # 1194 GFLOP/s on this part).
 FP64_PEAK_GFLOPS = 152 * 4 * 2.07
+# Ceiling of the cluster QR on FP32-assembled blocks, which runs in double-float
+# arithmetic on the FP32 pipe: the issue rate (152 SMs x 4 schedulers x 32 lanes
+# x 2.07 GHz = 40.3 T lane-instructions/s) over the 27 instructions of one
+# column-update element (4 FP64-equivalent flops) = 5967 GFLOP/s.
+DF_PEAK_GFLOPS = 152 * 4 * 32 * 2.07 * 4 / 27
 # DRAM traffic from ncu captures of the current kernels (profiles/): per LSQR
 # iteration for k_lsqr ((10.690 + 0.283) GB over a 50-iteration capture, scaled
 # by the launch's iteration count), per launch otherwise; a kernel without an
@@ -310,11 +315,17 @@ def run_gpu(args):
     fused_q = qr_name == "k_qrcp_cluster"     # Q_hat accumulated in the same kernel
     qr_alg = qrcp_flops(m, K, ranks) + (formq_flops(m, ranks) if fused_q else 0.0)
     if dom == qr_name:
+        # the mixed path's blocks are FP32-assembled: the cluster kernel factors
+        # them in double-float, the global-memory fallback in FP64
         fl = qr_alg
         ach = fl / (per_launch_ms[dom] * 1e-3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
-                "frac": ach / (FP64_PEAK_GFLOPS / 1e3), "peak_source": "derived FP64: 152 SMs x 4 flop/clk x 2.07 GHz",
-                "algorithmic_per_launch": fl}
+        if fused_q:
+            pk, src = DF_PEAK_GFLOPS / 1e3, ("derived double-float: FP32 issue 152 SMs x 4 x 32 lanes x 2.07 GHz / "
+                                             "27 instructions per 4-flop update element")
+        else:
+            pk, src = FP64_PEAK_GFLOPS / 1e3, "derived FP64: 152 SMs x 4 flop/clk x 2.07 GHz"
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                "frac": ach / pk, "peak_source": src, "algorithmic_per_launch": fl}
     elif dom == "k_form_q":
         fl = formq_flops(m, ranks)
         ach = fl / (per_launch_ms[dom] * 1e-3) / 1e12
