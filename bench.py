@@ -121,6 +121,16 @@ def lsqr_bytes_per_iter(m, r, N, val_bytes):
     return 2.0 * nnz * val_bytes + 2.0 * (N + float(np.sum(r))) * 8.0
 
 
+def smi_device_id(env=None) -> str:
+    """nvidia-smi id of this rank's GPU: entry LOCAL_RANK of
+    CUDA_VISIBLE_DEVICES when it is set (an index or a UUID), else the index
+    LOCAL_RANK."""
+    env = os.environ if env is None else env
+    local = int(env.get("LOCAL_RANK", "0"))
+    ids = [x.strip() for x in env.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
+    return ids[local] if local < len(ids) else str(local)
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -134,7 +144,7 @@ class Clocks:
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             self.f = open(self.path, "w")
-            dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+            dev = smi_device_id()
             self.p = subprocess.Popen(["nvidia-smi", f"--id={dev}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
                                        "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
             time.sleep(0.3)

@@ -117,3 +117,11 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
         r = bench.run_reference(argparse.Namespace(steps=1, warmup=3, ref_iters=10))
     assert r is None
     assert buf.getvalue() == ""
+
+
+def test_clock_sampler_watches_the_ranks_own_gpu():
+    import bench
+    assert bench.smi_device_id({}) == "0"
+    assert bench.smi_device_id({"LOCAL_RANK": "3"}) == "3"
+    assert bench.smi_device_id({"LOCAL_RANK": "1", "CUDA_VISIBLE_DEVICES": "4,5,6"}) == "5"
+    assert bench.smi_device_id({"CUDA_VISIBLE_DEVICES": "GPU-abc, GPU-def", "LOCAL_RANK": "1"}) == "GPU-def"
