@@ -19,6 +19,12 @@ that records LSQR iterates every 100 iterations up to the paper's budget of
 a fixed ladder that both the mixed path and the plain FP64 path (FP64
 assembly, FP64 QRCP, explicit FP64 Q_hat of Proposition 3.1, zero start)
 reach.  Both paths are timed; "value" is the mixed path.
+
+At N = 1 the line also carries, each measured in the same run: the oracle
+timed on a sample of the workload ("cpu_baseline"), 64 uneven instances in one
+launch per call ("batched"), the learned warm start ("learned"), and the time
+to 1e-6 relative L2 error on the 1D Poisson workload against plain LSQR
+("poisson1d").  --impl reference times the oracle alone.
 """
 from __future__ import annotations
 
