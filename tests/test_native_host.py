@@ -112,3 +112,17 @@ def test_qr_launch_order_is_largest_first(native):
     expect = sorted(range(len(work)), key=lambda b: (-work[b], b))
     assert order.tolist() == expect
     assert len(set(work.tolist())) > 3           # the batch is uneven
+
+
+def test_full_size_heat_workload_plans_on_the_host(native):
+    """The (2+1)D heat workload at its full size (10^3 subdomains, K = 500,
+    100^3 interior points plus the lateral and initial faces): the plan builds
+    and its sizes agree with the oracle's row count."""
+    p = synth.heat3d()
+    rc, sz, _, _ = _sizes(native, [p], asm="fp32", op="q32", tol=1e-6)
+    assert rc == 0, native.load().rfm_last_error()
+    z = oracle.sizes(p)
+    assert sz.n_rows == z["N"] == 100 ** 3 + 5 * 100 ** 2
+    assert sz.n_blocks == 1000 and sz.n_cols == 1000 * 500 and sz.max_K == 500
+    assert sz.max_block_rows == 2744
+    assert sz.workspace_bytes < 32 * 2 ** 30
