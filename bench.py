@@ -386,9 +386,9 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(p, prm, kstar["fp64"], stride=args.cpu_stride)
     if rank == 0 and world == 1 and args.batched > 0:
-        out["batched"] = run_batched(args, dev)
+        out["batched"] = guarded(run_batched, args, dev)
     if rank == 0 and world == 1 and args.learned_train > 0:
-        out["learned"] = run_learned(args, dev)
+        out["learned"] = guarded(run_learned, args, dev)
     if rank == 0 and world == 1 and not args.no_poisson1d:
         out["poisson1d"] = guarded(run_poisson1d, args, dev)
     if rank == 0:
