@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define RFM_ABI_VERSION 1
+#define RFM_ABI_VERSION 2
 
 typedef enum {
     RFM_OK = 0,
@@ -175,13 +175,27 @@ typedef struct rfm_lsqr_opts {
                             column updates; row sums with the scalar updates overlapped; 0;
                             0), each up to the exit of the grid barrier that closes it; for
                             profiling; not written with RFM_OP_AR64 */
+    int32_t refine_steps;  /* iterative refinement: correction solves after the first solve
+                              (0..64; 0 = none), see rfm_lsqr_solve */
+    int32_t refine_iters;  /* iteration limit of each correction solve (0 = max_iter) */
+    double *d_rnorm64;     /* nullable: n_inst x (refine_steps + 1) doubles (row-major), the
+                              residual ||h - M a_s|| of the assembled system evaluated in FP64
+                              after solve s = 0 .. refine_steps */
 } rfm_lsqr_opts;
 
 /* Report per instance (written to device memory):
  *   itn, istop (0 exact start, 1 residual test, 2 normal-equation test,
- *   7 iteration limit), rnorm, arnorm, anorm, ynorm, bnorm estimates. */
+ *   7 iteration limit), rnorm, arnorm, anorm, ynorm, bnorm estimates,
+ *   status (an rfm_status of the device-side run),
+ *   start: 1 when the warm start y0 was used, 0 for a zero start (no y0, or
+ *   a y0 whose residual ||h - A S^-1 y0|| was not below ||h||, the fallback),
+ *   r0norm: ||h - A S^-1 y0|| of the given y0 (||h|| without y0).
+ * With refinement, itn counts the iterations of every solve and the other
+ * estimates are those of the last correction solve (on its own right-hand
+ * side); d_rnorm64 carries the residuals of the assembled system. */
 typedef struct rfm_lsqr_report {
     double itn, istop, rnorm, arnorm, anorm, ynorm, bnorm, status;
+    double start, r0norm;
 } rfm_lsqr_report;
 
 /* LSQR on min ||M_hat S^-1 y - h|| for every instance at once (each with its
@@ -189,16 +203,31 @@ typedef struct rfm_lsqr_report {
  * with zeros at dropped columns (Algorithm 2).
  *  d_y0     nullable warm start (n_cols doubles, per block the first r_j of
  *           each K-slot used); the iteration runs on the residual system.
+ *           Per instance, a y0 whose residual ||h - A S^-1 y0|| is not below
+ *           ||h|| is dropped for a zero start (report field start = 0).
  *  d_y      nullable output y (n_cols doubles, same layout; 0 at dropped slots).
  *  d_a      output coefficients (n_cols doubles).
  *  d_report n_inst rfm_lsqr_report.
  * Stopping (per instance): ||r|| <= btol ||h|| + atol ||A||_F ||y||, or
  * ||A^T r|| <= atol ||A||_F ||r||, or max_iter, with the norm estimates of
  * the 1982 paper and ||y|| computed exactly.
+ * Iterative refinement (opts->refine_steps = R > 0; the paper solves once,
+ * this is the mixed-precision refinement of Carson and Higham, "Accelerating
+ * the solution of linear systems by iterative refinement in three
+ * precisions", SISC 2018, applied to the least-squares problem of
+ * Algorithm 2): after the first solve, R times: a = S^-1 y, the residual
+ * r = h - M a of the assembled system in FP64 (FP64 blocks, or the FP32
+ * blocks' values taken exactly), a correction solve min ||M_hat S^-1 d - r||
+ * from zero with the configured operator (at most refine_iters iterations,
+ * same atol and btol), y += d.  With an FP32 operator this brings the mixed
+ * path to the FP64 least-squares solution of the kept columns.  The h and M
+ * arenas are read, not changed.
  * The call is asynchronous: a device-side wait (grid barrier or the wait of
  * a forward tile on its block) that runs longer than timeout_ms ends the
  * kernel at that wait, and every report's status is then RFM_ETIMEOUT
- * (results invalid); a non-finite recurrence gives RFM_ENUMERIC there. */
+ * (results invalid); a non-finite recurrence gives RFM_ENUMERIC there.
+ * Errors: RFM_EINVAL for more than 64 instances, refine_steps outside 0..64
+ * or a negative refine_iters. */
 rfm_status rfm_lsqr_solve(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const rfm_lsqr_opts *opts,
                           const double *d_y0, double *d_y, double *d_a, rfm_lsqr_report *d_report,
                           void *d_ws, size_t ws_bytes, void *stream);
@@ -391,8 +420,11 @@ int rfm_profile_read(const char **names, int64_t *launches, double *ms, int max)
  *    cluster kernel with double-float arithmetic (pairs of FP32 numbers, about
  *    48 significant bits, on the FP32 pipe; the reflector scalars, norms fed
  *    to the threshold test and R are formed in FP64) unless Q_hat is wanted in
- *    FP64; 0 uses FP64 arithmetic for them too.  FP64-assembled blocks always
- *    use FP64 arithmetic.
+ *    FP64; 0 uses FP64 arithmetic for them too.  2 also factors FP64-assembled
+ *    blocks in double-float when the operator is RFM_OP_Q32 (each FP64 entry
+ *    split into two FP32 numbers on load, relative error 2^-48; the mixed
+ *    path with refinement); with 0 or 1 FP64-assembled blocks use FP64
+ *    arithmetic.
  *  RFM_OPT_LSQR_STALL (test hook for failure detection): 1 makes the first
  *    grid barrier of the next explicit-operator solves wait for an arrival
  *    that never comes, 2 makes their forward tiles wait for a chunk that never

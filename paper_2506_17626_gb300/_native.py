@@ -36,7 +36,8 @@ class RfmSizes(C.Structure):
 class RfmLsqrOpts(C.Structure):
     _fields_ = [("atol", C.c_double), ("btol", C.c_double), ("max_iter", C.c_int32), ("timeout_ms", C.c_int32),
                 ("d_snap", C.c_void_p), ("snap_every", C.c_int32), ("snap_cap", C.c_int32),
-                ("d_phase_ms", C.c_void_p)]
+                ("d_phase_ms", C.c_void_p), ("refine_steps", C.c_int32), ("refine_iters", C.c_int32),
+                ("d_rnorm64", C.c_void_p)]
 
 
 class RfmMlp(C.Structure):
@@ -51,7 +52,8 @@ def mlp_struct(widths) -> RfmMlp:
     return m
 
 
-REPORT_FIELDS = ("itn", "istop", "rnorm", "arnorm", "anorm", "ynorm", "bnorm", "status")
+REPORT_FIELDS = ("itn", "istop", "rnorm", "arnorm", "anorm", "ynorm", "bnorm", "status", "start", "r0norm")
+REPORT_LEN = len(REPORT_FIELDS)
 
 EXPORTS = ["rfm_problem_size", "rfm_assemble", "rfm_rrqr_filter", "rfm_lsqr_solve", "rfm_coefficients",
            "rfm_eval", "rfm_block_info", "rfm_workspace_view", "rfm_profile_enable", "rfm_profile_reset",
@@ -200,7 +202,10 @@ def set_qr_order(largest_first: bool):
     check("rfm_set_option", load().rfm_set_option(5, 1 if largest_first else 0))
 
 
-def set_qr_double_float(on: bool):
-    """Factor FP32-assembled blocks with double-float arithmetic (True, the
-    default) or with FP64 arithmetic (False) (RFM_OPT_QR_DOUBLE_FLOAT)."""
-    check("rfm_set_option", load().rfm_set_option(2, 1 if on else 0))
+def set_qr_double_float(on):
+    """Factor FP32-assembled blocks with double-float arithmetic (True or 1,
+    the default) or with FP64 arithmetic (False or 0); 2 also puts
+    FP64-assembled blocks with the FP32 Q_hat operator on the double-float
+    kernel (RFM_OPT_QR_DOUBLE_FLOAT)."""
+    v = int(on) if not isinstance(on, bool) else (1 if on else 0)
+    check("rfm_set_option", load().rfm_set_option(2, v))

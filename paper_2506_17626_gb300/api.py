@@ -67,18 +67,26 @@ class System:
 
     def solve(self, atol=1e-10, btol=1e-10, max_iter=10000, y0: Optional[torch.Tensor] = None,
               timeout_ms: int = 10000, want_y: bool = False, snap: Optional[torch.Tensor] = None,
-              snap_every: int = 0, phase_ms: Optional[torch.Tensor] = None):
+              snap_every: int = 0, phase_ms: Optional[torch.Tensor] = None, refine_steps: int = 0,
+              refine_iters: int = 0, rnorm64: Optional[torch.Tensor] = None):
         """LSQR of Algorithm 2.  snap: optional (cap, n_cols) FP64 tensor that
-        receives y after every snap_every-th iteration."""
+        receives y after every snap_every-th iteration.  refine_steps > 0 adds
+        that many correction solves (at most refine_iters iterations each) on
+        the FP64 residual of the assembled system; rnorm64: optional FP64
+        tensor of n x (refine_steps + 1) that receives those residual norms."""
         nc = self.sizes["n_cols"]
         a = torch.empty(nc, dtype=torch.float64, device=self.device)
         y = torch.empty(nc, dtype=torch.float64, device=self.device) if want_y else None
-        rep = torch.empty(self.n * 8, dtype=torch.float64, device=self.device)
+        rep = torch.empty(self.n * N.REPORT_LEN, dtype=torch.float64, device=self.device)
         cap = 0 if snap is None else snap.shape[0]
         if snap is not None:
             assert snap.is_cuda and snap.dtype == torch.float64 and snap.shape[1] == nc and snap.is_contiguous()
+        if rnorm64 is not None:
+            assert rnorm64.is_cuda and rnorm64.dtype == torch.float64 and rnorm64.is_contiguous()
+            assert rnorm64.numel() >= self.n * (refine_steps + 1)
         opts = N.RfmLsqrOpts(float(atol), float(btol), int(max_iter), int(timeout_ms),
-                             _ptr(snap), int(snap_every if snap is not None else 0), int(cap), _ptr(phase_ms))
+                             _ptr(snap), int(snap_every if snap is not None else 0), int(cap), _ptr(phase_ms),
+                             int(refine_steps), int(refine_iters), _ptr(rnorm64))
         if y0 is not None:
             assert y0.is_cuda and y0.dtype == torch.float64 and y0.numel() == nc
         N.check("rfm_lsqr_solve", self.lib.rfm_lsqr_solve(self._probs, self.n, C.byref(self._cfg), C.byref(opts),
@@ -217,8 +225,8 @@ class System:
 
 
 def report_dict(rep: torch.Tensor, i: int = 0) -> dict:
-    r = rep.view(-1, 8)[i].tolist()
-    return {k: (int(v) if k in ("itn", "istop", "status") else v) for k, v in zip(N.REPORT_FIELDS, r)}
+    r = rep.view(-1, N.REPORT_LEN)[i].tolist()
+    return {k: (int(v) if k in ("itn", "istop", "status", "start") else v) for k, v in zip(N.REPORT_FIELDS, r)}
 
 
 class Mlp:

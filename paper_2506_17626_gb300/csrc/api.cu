@@ -230,7 +230,7 @@ rfm_status rfm_set_option(int option, int value) {
         set_autotune(value);
         return RFM_OK;
     }
-    if (option == RFM_OPT_QR_DOUBLE_FLOAT && (value == 0 || value == 1)) {
+    if (option == RFM_OPT_QR_DOUBLE_FLOAT && value >= 0 && value <= 2) {
         set_qr_double_float(value);
         return RFM_OK;
     }

@@ -64,7 +64,9 @@ struct ColItem {
 struct LsqrScal {
     double alpha, beta, rhobar, phibar, anorm2, bnorm;
     double rnorm, arnorm, ynorm, phi_rho, theta_rho, c;
+    double r0norm;              // ||h - Op y0|| of the given start (||h|| without one)
     int32_t itn, istop, done, status;
+    int32_t start, pad;         // 1: the warm start is used, 0: zero start
 };
 
 // Offsets (bytes) of every array of a system inside the workspace.
@@ -88,6 +90,8 @@ struct Layout {
     size_t off_titems, off_ntitems;
     size_t off_bcnt;                                    // per block: chunks of the transposed product finished (64-bit, monotone)
     size_t off_qord;                                    // QR launch order of the blocks (largest first)
+    size_t off_yacc, off_rres, off_itn, off_scal0;      // refinement: accumulated y, FP64 residual, iterations,
+                                                        // the first solve's scalars
     size_t total;
     int asm_prec, op;
 };

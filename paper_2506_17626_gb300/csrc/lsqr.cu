@@ -505,6 +505,41 @@ __global__ void __launch_bounds__(kThreads) k_lsqr(LsqrArgs a) {
     reduce_partials(a.part + (int64_t)ni * G, ni, S.tmp);
     for (int s = tid; s < ni; s += kThreads) sc[s].bnorm = sqrt(S.tmp[s]);
     __syncthreads();
+    // a warm start whose residual is not below ||h|| is dropped for a zero
+    // start (every CTA takes the same decision from the same sums)
+    int back = 0;
+    for (int s = tid; s < ni; s += kThreads) {
+        sc[s].r0norm = sc[s].beta;
+        sc[s].start = a.y0 ? 1 : 0;
+        if (a.y0 && !(sc[s].beta < sc[s].bnorm)) {
+            sc[s].start = 0;
+            sc[s].beta = sc[s].bnorm;
+            back = 1;
+        }
+    }
+    back = __syncthreads_or(back);
+    if (back) {
+        for (int b = cta; b < a.n_blocks; b += G) {
+            const BlkRec &B = a.blks[b];
+            if (sc[B.inst].start) continue;
+            for (int c = tid; c < B.K; c += kThreads) a.y[B.coff + c] = 0.0;
+        }
+        for (int64_t T = cta; T < a.n_row_tiles; T += G) {
+            int s = 0;
+            int64_t tcount = 0;
+            for (; s < ni; ++s) {
+                int64_t nt = (a.insts[s].N + kRowTile - 1) / kRowTile;
+                if (T < tcount + nt) break;
+                tcount += nt;
+            }
+            if (sc[s].start) continue;
+            const InstRec &I = a.insts[s];
+            const int64_t r = (T - tcount) * kRowTile + tid;
+            if (r < I.N) a.u[I.row0 + r] = a.h[I.row0 + r];
+        }
+        ok = grid_sync(a.bar, a.timeout_ns);
+        if (!ok) return;
+    }
     // I3: vt = Op^T (u~/beta), ||vt||^2
     clear_acc();
     transpose_all(
@@ -725,18 +760,24 @@ __global__ void __launch_bounds__(kThreads) k_coefficients(const BlkRec *__restr
     }
 }
 
-__global__ void k_report(const LsqrScal *__restrict__ sc, int n, rfm_lsqr_report *__restrict__ rep, const unsigned *bar) {
+// itn_add (nullable): iterations of earlier solves of a refinement, per instance.
+__global__ void k_report(const LsqrScal *__restrict__ sc, int n, rfm_lsqr_report *__restrict__ rep, const unsigned *bar,
+                         const double *__restrict__ itn_add, const LsqrScal *__restrict__ sc_first) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const LsqrScal &q = sc[s];
-    rep[s].itn = q.itn;
+    rep[s].itn = q.itn + (itn_add ? itn_add[s] : 0.0);
+    rep[s].start = sc_first ? sc_first[s].start : q.start;
+    rep[s].r0norm = sc_first ? sc_first[s].r0norm : q.r0norm;
+    const double st_now = bar[2] ? (double)bar[2] : (double)q.status;
+    const double st_before = itn_add ? itn_add[n + s] : 0.0;
+    rep[s].status = st_before != 0.0 ? st_before : st_now;
     rep[s].istop = q.istop;
     rep[s].rnorm = q.rnorm;
     rep[s].arnorm = q.arnorm;
     rep[s].anorm = sqrt(q.anorm2);
     rep[s].ynorm = q.ynorm;
     rep[s].bnorm = q.bnorm;
-    rep[s].status = bar[2] ? (double)bar[2] : (double)q.status;
 }
 
 
@@ -1464,10 +1505,46 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
     if (!ok) return;
     reduce_partials(a.part + (int64_t)ni * G, ni, S.tmp);
     reduce_partials(a.part, ni, S.tmp2);
+    // a warm start whose residual is not below ||h|| is dropped for a zero
+    // start (every CTA takes the same decision from the same sums)
+    int back = 0;
     for (int s = tid; s < ni; s += kThreads) {
-        sc[s].beta = sqrt(S.tmp[s]);
-        sc[s].bnorm = sqrt(S.tmp2[s]);
+        const double r0 = sqrt(S.tmp[s]), hn = sqrt(S.tmp2[s]);
+        sc[s].r0norm = r0;
+        sc[s].bnorm = hn;
+        sc[s].start = a.y0 ? 1 : 0;
+        if (a.y0 && !(r0 < hn)) {
+            sc[s].start = 0;
+            back = 1;
+        }
+        sc[s].beta = sc[s].start ? r0 : hn;
         S.inv_bn[s] = sc[s].beta > 0.0 ? 1.0 / sc[s].beta : 0.0;
+    }
+    back = __syncthreads_or(back);
+    if (back) {
+        // those instances restart from zero: y = 0 on their columns, u~ = h on
+        // their rows and block rows
+        auto fell = [&](int s) { return sc[s].start == 0; };
+        each_column(fell, [&](int, int64_t o) { a.y[o] = 0.0; });
+        for (int64_t T = cta; T < a.n_row_tiles; T += G) {
+            int64_t tc;
+            const int s = row_tile_inst(T, &tc);
+            if (!fell(s)) continue;
+            const InstRec &I = a.insts[s];
+            const int64_t r = (T - tc) * kRowTile + tid;
+            if (r < I.N) {
+                const int64_t gr = I.row0 + r;
+                const double hv = a.h[gr];
+                a.u[gr] = hv;
+                const int32_t *lst = a.rowlist + I.rl_off + r * I.C;
+                for (int e = 0; e < I.C; ++e) {
+                    const int q = lst[e];
+                    if (q >= 0) tu[q] = (TA)hv;
+                }
+            }
+        }
+        ok = grid_sync(a.bar, a.timeout_ns);
+        if (!ok) return;
     }
     __syncthreads();
     // vt = Op^T u~ / beta, ||vt||^2, fused with t = Op vt (the first loop pass's forward product)
@@ -1658,6 +1735,125 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
     }
 }
 
+// ---------------------------------------------------------------------------
+// Iterative refinement (Carson and Higham 2018, for the least-squares problem
+// of Algorithm 2): the residual r = h - M a of the assembled system in FP64,
+// from the stored blocks (FP64, or the FP32 values taken exactly).
+// ---------------------------------------------------------------------------
+
+// t[q] = (M_b a_b)(q) for the 32 block rows of one tile, all K columns, FP64
+// accumulation: warp w takes columns w, w + 8, ..., lane = row; the eight
+// partial sums are added in warp order.
+template <typename TM>
+__global__ void __launch_bounds__(256) k_block_apply(const BlkRec *__restrict__ blks,
+                                                     const int32_t *__restrict__ tile_blk,
+                                                     const int32_t *__restrict__ tile_row, const TM *__restrict__ M,
+                                                     const double *__restrict__ a, double *__restrict__ t) {
+    __shared__ double part[8][33];
+    const BlkRec &B = blks[tile_blk[blockIdx.x]];
+    const int r0 = tile_row[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const TM *col = M + B.moff + r0 + lane;   // rows r0 + lane < ldm (tiles lie inside the padded block)
+    const double *ab = a + B.coff;
+    double acc = 0.0;
+    for (int c = warp; c < B.K; c += 8) acc = fma((double)__ldg(col + (int64_t)c * B.ldm), __ldg(ab + c), acc);
+    part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0) {
+        double s = part[0][lane];
+        for (int w = 1; w < 8; ++w) s += part[w][lane];
+        if (r0 + lane < B.m) t[B.roff + r0 + lane] = s;
+    }
+}
+
+// r[g] = h[g] - sum over the block rows holding global row g (fixed order).
+__global__ void k_residual(const InstRec *__restrict__ insts, int n_inst, const int32_t *__restrict__ rowlist,
+                           const double *__restrict__ h, const double *__restrict__ t, double *__restrict__ r,
+                           int64_t n_rows) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_rows; g += (int64_t)gridDim.x * blockDim.x) {
+        int s = 0;
+        while (s + 1 < n_inst && insts[s + 1].row0 <= g) ++s;
+        const InstRec &I = insts[s];
+        const int32_t *lst = rowlist + I.rl_off + (g - I.row0) * I.C;
+        double acc = 0.0;
+        for (int e = 0; e < I.C; ++e) {
+            const int q = lst[e];
+            if (q >= 0) acc += t[q];
+        }
+        r[g] = h[g] - acc;
+    }
+}
+
+// out[s * stride] = ||r over the rows of instance s||, one CTA per instance,
+// fixed summation order.
+__global__ void __launch_bounds__(256) k_inst_norm(const InstRec *__restrict__ insts, const double *__restrict__ r,
+                                                   double *__restrict__ out, int stride) {
+    __shared__ double red[8];
+    const InstRec &I = insts[blockIdx.x];
+    double s2 = 0.0;
+    for (int64_t i = threadIdx.x; i < I.N; i += 256) s2 = fma(r[I.row0 + i], r[I.row0 + i], s2);
+    for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        out[(int64_t)blockIdx.x * stride] = sqrt(t);
+    }
+}
+
+__global__ void k_add(double *__restrict__ y, const double *__restrict__ d, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += d[i];
+}
+
+// acc[s] (+)= itn of the solve just finished; acc[n + s] keeps the first
+// nonzero status of the solves so far (a later solve resets the barrier words)
+__global__ void k_itn_acc(const LsqrScal *__restrict__ sc, int n, double *__restrict__ acc, int first,
+                          const unsigned *__restrict__ bar) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    acc[s] = (first ? 0.0 : acc[s]) + (double)sc[s].itn;
+    const double st = bar[2] ? (double)bar[2] : (double)sc[s].status;
+    acc[n + s] = (first || acc[n + s] == 0.0) ? st : acc[n + s];
+}
+
+static unsigned grid_for(int64_t n, int threads) {
+    int64_t g = (n + threads - 1) / threads;
+    return (unsigned)(g < 1 ? 1 : (g > 8192 ? 8192 : g));
+}
+
+// r = h - M a over every instance; ||r|| per instance to out (nullable) with stride.
+static rfm_status residual64(const HostPlan &P, void *ws, const double *a, double *r, double *norm_out, int stride,
+                             cudaStream_t st) {
+    const Layout &L = P.L;
+    double *t = ws_ptr<double>(ws, L.off_t);
+    if (L.n_tiles > 0) {
+        ProfScope ps("k_block_apply", st);
+        const int32_t *tb = ws_ptr<int32_t>(ws, L.off_tile);
+        if (L.asm_prec == RFM_ASM_FP32)
+            k_block_apply<float><<<(unsigned)L.n_tiles, 256, 0, st>>>(ws_ptr<BlkRec>(ws, L.off_blk), tb,
+                                                                       tb + L.n_tiles, ws_ptr<float>(ws, L.off_M), a, t);
+        else
+            k_block_apply<double><<<(unsigned)L.n_tiles, 256, 0, st>>>(ws_ptr<BlkRec>(ws, L.off_blk), tb,
+                                                                        tb + L.n_tiles, ws_ptr<double>(ws, L.off_M), a, t);
+        RFM_CUDA_CHECK(cudaGetLastError());
+    }
+    {
+        ProfScope ps("k_residual", st);
+        k_residual<<<grid_for(L.n_rows, 256), 256, 0, st>>>(ws_ptr<InstRec>(ws, L.off_inst), L.n_inst,
+                                                            ws_ptr<int32_t>(ws, L.off_rowlist),
+                                                            ws_ptr<double>(ws, L.off_h), t, r, L.n_rows);
+        RFM_CUDA_CHECK(cudaGetLastError());
+    }
+    if (norm_out) {
+        ProfScope ps("k_inst_norm", st);
+        k_inst_norm<<<(unsigned)L.n_inst, 256, 0, st>>>(ws_ptr<InstRec>(ws, L.off_inst), r, norm_out, stride);
+        RFM_CUDA_CHECK(cudaGetLastError());
+    }
+    return RFM_OK;
+}
+
 rfm_status launch_coefficients(const HostPlan &P, void *ws, const double *y, double *a_out, cudaStream_t st) {
     const Layout &L = P.L;
     if (L.n_blocks == 0) return RFM_OK;
@@ -1780,6 +1976,28 @@ static void fill_args(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, co
     }
 }
 
+// One LSQR run of the configured operator with the arguments in A.
+static rfm_status run_op(const HostPlan &P, void *ws, LsqrArgs &A, cudaStream_t st) {
+    const Layout &L = P.L;
+    RFM_CUDA_CHECK(cudaMemsetAsync(A.bar, 0, 256, st));
+    RFM_CUDA_CHECK(cudaMemsetAsync(A.y, 0, sizeof(double) * L.n_cols, st));   // dropped slots of y read back as 0
+    if (L.op == RFM_OP_Q32) {
+        A.A = ws_ptr<float>(ws, L.off_q32);
+        return run_lsqr_tiles<float>(P, ws, A, st);
+    } else if (L.op == RFM_OP_Q64) {
+        A.A = ws_ptr<double>(ws, L.off_op);
+        return run_lsqr_tiles<double>(P, ws, A, st);
+    } else if (L.op == RFM_OP_AR64) {
+        A.A = ws_ptr<double>(ws, L.off_op);
+        return run_lsqr<double, true>(P, ws, A, st);
+    } else if (L.asm_prec == RFM_ASM_FP32) {
+        A.A = ws_ptr<float>(ws, L.off_M);
+        return run_lsqr_tiles<float>(P, ws, A, st);
+    }
+    A.A = ws_ptr<double>(ws, L.off_M);
+    return run_lsqr_tiles<double>(P, ws, A, st);
+}
+
 rfm_status launch_lsqr(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, const double *y0, double *y_out,
                        double *a_out, rfm_lsqr_report *rep, cudaStream_t st) {
     const Layout &L = P.L;
@@ -1787,34 +2005,59 @@ rfm_status launch_lsqr(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, c
         set_error("rfm_lsqr_solve: at most 64 instances per system");
         return RFM_EINVAL;
     }
+    const int R = opts->refine_steps;
+    if (R < 0 || R > 64 || opts->refine_iters < 0) {
+        set_error("rfm_lsqr_solve: refine_steps must be 0..64 and refine_iters >= 0");
+        return RFM_EINVAL;
+    }
     LsqrArgs A;
     fill_args(P, ws, opts, y0, A);
-    RFM_CUDA_CHECK(cudaMemsetAsync(A.bar, 0, 256, st));
-    RFM_CUDA_CHECK(cudaMemsetAsync(A.y, 0, sizeof(double) * L.n_cols, st));   // dropped slots of y read back as 0
-    rfm_status rc;
-    if (L.op == RFM_OP_Q32) {
-        A.A = ws_ptr<float>(ws, L.off_q32);
-        rc = run_lsqr_tiles<float>(P, ws, A, st);
-    } else if (L.op == RFM_OP_Q64) {
-        A.A = ws_ptr<double>(ws, L.off_op);
-        rc = run_lsqr_tiles<double>(P, ws, A, st);
-    } else if (L.op == RFM_OP_AR64) {
-        A.A = ws_ptr<double>(ws, L.off_op);
-        rc = run_lsqr<double, true>(P, ws, A, st);
-    } else if (L.asm_prec == RFM_ASM_FP32) {
-        A.A = ws_ptr<float>(ws, L.off_M);
-        rc = run_lsqr_tiles<float>(P, ws, A, st);
-    } else {
-        A.A = ws_ptr<double>(ws, L.off_M);
-        rc = run_lsqr_tiles<double>(P, ws, A, st);
-    }
+    rfm_status rc = run_op(P, ws, A, st);
     if (rc != RFM_OK) return rc;
-    if (y_out) RFM_CUDA_CHECK(cudaMemcpyAsync(y_out, A.y, sizeof(double) * L.n_cols, cudaMemcpyDeviceToDevice, st));
-    rc = launch_coefficients(P, ws, A.y, a_out, st);
+    const double *y_fin = A.y;
+    double *itn_acc = nullptr;
+    const LsqrScal *sc0 = nullptr;
+    if (R > 0 || opts->d_rnorm64) {
+        double *yacc = ws_ptr<double>(ws, L.off_yacc);
+        double *r = ws_ptr<double>(ws, L.off_rres);
+        double *acc = ws_ptr<double>(ws, L.off_itn);
+        LsqrScal *s0 = ws_ptr<LsqrScal>(ws, L.off_scal0);
+        RFM_CUDA_CHECK(cudaMemcpyAsync(yacc, A.y, sizeof(double) * L.n_cols, cudaMemcpyDeviceToDevice, st));
+        RFM_CUDA_CHECK(cudaMemcpyAsync(s0, A.scal, sizeof(LsqrScal) * L.n_inst, cudaMemcpyDeviceToDevice, st));
+        sc0 = s0;
+        if (R > 0) itn_acc = acc;
+        const unsigned gi = (unsigned)((L.n_inst + 63) / 64);
+        for (int s = 0; s <= R; ++s) {
+            // after solve s: a = S^-1 y (a_out as scratch), r = h - M a, ||r||
+            if (s == R && !opts->d_rnorm64) break;
+            rc = launch_coefficients(P, ws, yacc, a_out, st);
+            if (rc != RFM_OK) return rc;
+            rc = residual64(P, ws, a_out, r, opts->d_rnorm64 ? opts->d_rnorm64 + s : nullptr, R + 1, st);
+            if (rc != RFM_OK) return rc;
+            if (s == R) break;
+            // iterations of solve s, then the correction solve s + 1 from zero on r; y += d
+            k_itn_acc<<<gi, 64, 0, st>>>(A.scal, L.n_inst, acc, s == 0, A.bar);
+            RFM_CUDA_CHECK(cudaGetLastError());
+            rfm_lsqr_opts o = *opts;
+            o.max_iter = opts->refine_iters > 0 ? opts->refine_iters : opts->max_iter;
+            o.d_snap = nullptr;
+            o.d_phase_ms = nullptr;
+            fill_args(P, ws, &o, nullptr, A);
+            A.h = r;
+            rc = run_op(P, ws, A, st);
+            if (rc != RFM_OK) return rc;
+            ProfScope ps("k_add", st);
+            k_add<<<grid_for(L.n_cols, 256), 256, 0, st>>>(yacc, A.y, L.n_cols);
+            RFM_CUDA_CHECK(cudaGetLastError());
+        }
+        y_fin = yacc;
+    }
+    if (y_out) RFM_CUDA_CHECK(cudaMemcpyAsync(y_out, y_fin, sizeof(double) * L.n_cols, cudaMemcpyDeviceToDevice, st));
+    rc = launch_coefficients(P, ws, y_fin, a_out, st);
     if (rc != RFM_OK) return rc;
     if (rep) {
         ProfScope ps("k_report", st);
-        k_report<<<(L.n_inst + 63) / 64, 64, 0, st>>>(A.scal, L.n_inst, rep, A.bar);
+        k_report<<<(L.n_inst + 63) / 64, 64, 0, st>>>(A.scal, L.n_inst, rep, A.bar, itn_acc, sc0);
         RFM_CUDA_CHECK(cudaGetLastError());
     }
     return RFM_OK;
@@ -1845,7 +2088,7 @@ rfm_status launch_lsqr_on(const HostPlan &P, void *ws, const double *Op, const i
     RFM_CUDA_CHECK(cudaMemcpyAsync(z_out, A.y, sizeof(double) * L.n_cols, cudaMemcpyDeviceToDevice, st));
     if (rep) {
         ProfScope ps("k_report", st);
-        k_report<<<(L.n_inst + 63) / 64, 64, 0, st>>>(A.scal, L.n_inst, rep, A.bar);
+        k_report<<<(L.n_inst + 63) / 64, 64, 0, st>>>(A.scal, L.n_inst, rep, A.bar, nullptr, nullptr);
         RFM_CUDA_CHECK(cudaGetLastError());
     }
     return RFM_OK;

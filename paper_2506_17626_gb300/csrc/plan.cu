@@ -294,6 +294,10 @@ rfm_status build_plan(const rfm_problem *probs, int n_inst, const rfm_config *cf
     L.off_ntitems = take(256);
     L.off_bcnt = take(sizeof(unsigned long long) * (blk.size() + 1));
     L.off_qord = take(sizeof(int32_t) * (blk.size() + 1));
+    L.off_yacc = take(sizeof(double) * (col0 + 1));
+    L.off_rres = take(sizeof(double) * (row0 + 1));
+    L.off_itn = take(sizeof(double) * 2 * n_inst);
+    L.off_scal0 = take(sizeof(LsqrScal) * n_inst);
     L.off_qblk = take(sizeof(int32_t) * (roff + 1));
     L.off_tu = take(sizeof(double) * (roff + 1));
     L.off_fitems = take(sizeof(ColItem) * (L.n_fwd_items + 1));

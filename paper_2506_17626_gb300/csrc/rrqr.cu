@@ -608,9 +608,14 @@ __global__ void __launch_bounds__(kQT) k_qrcp_cluster(const BlkRec *__restrict__
 constexpr int kDT = 512;          // threads of a double-float cluster-QR CTA (its FP32 dependency chains want more warps)
 constexpr int kDW = kDT / 32;
 
-template <int C>
+// An input entry as a double-float: FP32 entries exactly, FP64 entries split
+// into their nearest FP32 number and the FP32 rounding of the remainder.
+__device__ inline float2 df_in(float x) { return make_float2(x, 0.f); }
+__device__ inline float2 df_in(double x) { return df_from_double(x); }
+
+template <typename TM, int C>
 __global__ void __launch_bounds__(kDT) k_qrcp_cluster_df(const BlkRec *__restrict__ blks,
-                                                         const int32_t *__restrict__ order, const float *__restrict__ M,
+                                                         const int32_t *__restrict__ order, const TM *__restrict__ M,
                                                          double *__restrict__ W, double *__restrict__ tau,
                                                          int32_t *__restrict__ perm_out, int32_t *__restrict__ rank_out,
                                                          double *__restrict__ r11_out, double tol, int nloc_max,
@@ -661,10 +666,10 @@ __global__ void __launch_bounds__(kDT) k_qrcp_cluster_df(const BlkRec *__restric
     int bo = INT_MAX;
     for (int l = warp; l < nloc; l += kDW) {
         const int c = cr + C * l;
-        const float *src = M + B.moff + (int64_t)c * ld;
+        const TM *src = M + B.moff + (int64_t)c * ld;
         float sh = 0.f, sl = 0.f;
         for (int i = lane; i < m; i += 32) {
-            const float2 a = make_float2(src[i], 0.f);
+            const float2 a = df_in(src[i]);
             A[(size_t)l * ld_loc + i] = a;
             df_acc(a, a, sh, sl);
         }
@@ -979,15 +984,18 @@ static size_t cluster_smem(int64_t max_m, int64_t max_K, int C, int *nloc, int *
 // in FP64 (RFM_OPT_QR_DOUBLE_FLOAT = 0 keeps them on the FP64 kernel).  Its
 // Q_hat path keeps double-float copies of the reflectors in the FP64
 // operator arena, which the FP32 operator leaves free.
+// With RFM_OPT_QR_DOUBLE_FLOAT = 2, FP64 blocks whose Q_hat is wanted in FP32
+// take it too (their entries split into double-floats on load).
 static int g_qr_df = 1;
 static bool use_df(const FilterBufs &F, int elem) {
-    return elem == 4 && g_qr_df && F.Q64 == nullptr && (F.Q32 == nullptr || F.Op != nullptr);
+    const bool kind = (elem == 4 && g_qr_df) || (elem == 8 && g_qr_df == 2 && F.Q32 != nullptr);
+    return kind && F.Q64 == nullptr && (F.Q32 == nullptr || F.Op != nullptr);
 }
 
-template <int C>
+template <typename TM, int C>
 static rfm_status launch_cluster_df(const FilterBufs &F, double tol, int nloc, int ldl, size_t smem,
                                     cudaStream_t st) {
-    auto kern = k_qrcp_cluster_df<C>;
+    auto kern = k_qrcp_cluster_df<TM, C>;
     RFM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (C > 8) RFM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchConfig_t cfg = {};
@@ -1003,7 +1011,7 @@ static rfm_status launch_cluster_df(const FilterBufs &F, double tol, int nloc, i
     cfg.attrs = at;
     cfg.numAttrs = 1;
     float2 *vdf = F.Q32 ? reinterpret_cast<float2 *>(F.Op) : nullptr;
-    RFM_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, F.blk, F.order, (const float *)F.M, F.W, F.tau, F.perm, F.rank, F.r11,
+    RFM_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, F.blk, F.order, (const TM *)F.M, F.W, F.tau, F.perm, F.rank, F.r11,
                                       tol, nloc, ldl, (int)F.max_K, vdf, F.Q32));
     return RFM_OK;
 }
@@ -1014,11 +1022,11 @@ static rfm_status launch_cluster_c(int C, const FilterBufs &F, double tol, cudaS
     if (use_df(F, (int)sizeof(TM))) {
         const size_t smem = cluster_smem(F.max_m, F.max_K, C, &nloc, &ldl, true);
         switch (C) {
-            case 1: return launch_cluster_df<1>(F, tol, nloc, ldl, smem, st);
-            case 2: return launch_cluster_df<2>(F, tol, nloc, ldl, smem, st);
-            case 4: return launch_cluster_df<4>(F, tol, nloc, ldl, smem, st);
-            case 8: return launch_cluster_df<8>(F, tol, nloc, ldl, smem, st);
-            default: return launch_cluster_df<16>(F, tol, nloc, ldl, smem, st);
+            case 1: return launch_cluster_df<TM, 1>(F, tol, nloc, ldl, smem, st);
+            case 2: return launch_cluster_df<TM, 2>(F, tol, nloc, ldl, smem, st);
+            case 4: return launch_cluster_df<TM, 4>(F, tol, nloc, ldl, smem, st);
+            case 8: return launch_cluster_df<TM, 8>(F, tol, nloc, ldl, smem, st);
+            default: return launch_cluster_df<TM, 16>(F, tol, nloc, ldl, smem, st);
         }
     }
     const size_t smem = cluster_smem(F.max_m, F.max_K, C, &nloc, &ldl);
@@ -1073,7 +1081,7 @@ static rfm_status autotune_cluster(const FilterBufs &F, double tol, int C_min, c
             int nloc = 0, ldl = 0;
             const bool dfk = use_df(F, (int)sizeof(TM));
             const size_t smem = cluster_smem(F.max_m, F.max_K, C, &nloc, &ldl, dfk);
-            const void *kern = dfk ? (const void *)k_qrcp_cluster_df<16> : (const void *)k_qrcp_cluster<TM, 16>;
+            const void *kern = dfk ? (const void *)k_qrcp_cluster_df<TM, 16> : (const void *)k_qrcp_cluster<TM, 16>;
             if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
                 cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
                 cudaGetLastError();

@@ -30,7 +30,7 @@ def test_library_exports_every_declared_symbol(native):
     for name in declared:
         assert hasattr(lib, name), name
     L = native.load()
-    assert L.rfm_abi_version() == 1
+    assert L.rfm_abi_version() == 2
 
 
 def _sizes(native, probs, asm="fp64", op="ar64", tol=1e-10):
