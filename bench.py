@@ -1,35 +1,44 @@
 """Benchmark: solve time to a fixed error for the RRQR-filtered, preconditioned
 ELM-FBPINN solver on one GB300 (and N independent instances on N GPUs).
 
-Workload (N = 1): 2D Poisson on [0,1]^2, u = sin2pix sin2piy + 0.05
-sin30pix sin30piy, 20 x 20 subdomains (overlap ratio 1.25), 300 tanh features
-each, 360 x 360 cell-centred interior grid (the paper's S*ceil(K^(1/d)) rule)
-plus 1440 boundary points, filter threshold 1e-6 on both paths (a threshold
-below the FP32 rounding level of the assembled matrix would keep rounding-noise
-columns on the mixed path).
+Workload (N = 1, the largest single-GPU configuration): (2+1)D heat
+u_t = kappa Lap u on [0,1]^2 x [0,1], kappa = 0.01, u = exp(-2 kappa pi^2 k^2
+t) sin(k pi x) sin(k pi y) with k = 6, 10 x 10 x 10 space-time subdomains
+(overlap ratio 1.2), 500 tanh features each, 100^3 interior collocation points
+plus 50,000 boundary and initial rows, filter threshold 1e-6, error on the
+50^3 test grid.  --case p2d takes the 2D Poisson workload (20 x 20 subdomains,
+300 features, 360^2 + 1440 rows, 400^2 test grid) instead; --case small a
+heat instance with the same block shapes on 4 x 4 x 4 subdomains (profiler
+captures).
 
 A step is one pass of the whole path over one instance:
-  assemble (FP32) -> RRQR filter (FP64 QRCP, Q_hat rounded to FP32) ->
-  LSQR on Q_hat (FP32 products, FP64 vectors and scalars) for the iteration
-  count that reaches the target error -> a = S^-1 y -> u_hat and its error on
-  the 400 x 400 test grid.
+  assemble (FP32) -> RRQR filter (QR with column pivoting, Q_hat rounded to
+  FP32) -> LSQR on Q_hat (FP32 products, FP64 vectors and scalars) for the
+  iteration count that reaches the target error -> a = S^-1 y -> u_hat and
+  its error on the test grid.
 The target error and the iteration counts come from an untimed calibration
-that records LSQR iterates every 100 iterations up to the paper's budget of
+that records LSQR iterates every SNAP iterations up to the paper's budget of
 10,000 iterations and evaluates each one; the target is the tightest value of
 a fixed ladder that both the mixed path and the plain FP64 path (FP64
-assembly, FP64 QRCP, explicit FP64 Q_hat of Proposition 3.1, zero start)
-reach.  Both paths are timed; "value" is the mixed path.
+assembly, FP64 QR, explicit FP64 Q_hat of Proposition 3.1, zero start)
+reach.  "solved" in the line says whether that target is at or below 1e-2;
+above it the time is that of a solve that has not converged, and the line
+says so.  Both paths are timed; "value" is the mixed path.
 
-At N = 1 the line also carries, each measured in the same run: the oracle
-timed on a sample of the workload ("cpu_baseline"), 64 uneven instances in one
-launch per call ("batched"), the learned warm start ("learned"), and the time
-to 1e-6 relative L2 error on the 1D Poisson workload against plain LSQR
-("poisson1d").  --impl reference times the oracle alone.
+At N = 1 the line also carries, each measured in the same run: the 2D
+Poisson workload's time to its target ("poisson2d"), the time to 1e-6
+relative L2 error on the 1D Poisson workload, which converges, for the FP64
+operators and the mixed path with refinement ("poisson1d"), 64 uneven
+instances in one launch per call ("batched"), the learned warm start
+("learned"), and the oracle timed on a sample of the workload on one core and
+on all cores ("cpu_baseline", "cpu_baseline_all_cores").  --impl reference
+times the oracle alone.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -44,9 +53,9 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 TARGET_LADDER = [1e-6, 2e-6, 5e-6, 1e-5, 2e-5, 5e-5, 1e-4, 2e-4, 5e-4, 1e-3, 2e-3, 5e-3, 1e-2, 2e-2, 5e-2,
-                 0.1, 0.2, 0.3, 0.5, 0.7, 0.8, 0.9, 0.95, 0.99]
+                 0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 0.95, 0.99]
+SOLVED_AT = 1e-2
 TOL = 1e-6
-SNAP_EVERY = 100
 CAL_ITERS = 10000
 # Nominal FP64 rate derived from the unit count and clock: 152 SMs x 4 FP64
 # flop/clk/SM (2 DFMA lanes) x 2.07 GHz = 1258 GFLOP/s (a DFMA probe measured
@@ -57,24 +66,44 @@ FP64_PEAK_GFLOPS = 152 * 4 * 2.07
 # x 2.07 GHz = 40.3 T lane-instructions/s) over the 27 instructions of one
 # column-update element (4 FP64-equivalent flops) = 5967 GFLOP/s.
 DF_PEAK_GFLOPS = 152 * 4 * 32 * 2.07 * 4 / 27
-# DRAM traffic from ncu captures of the current kernels (profiles/): per LSQR
-# iteration for k_lsqr ((10.690 + 0.283) GB over a 50-iteration capture, scaled
-# by the launch's iteration count), per launch otherwise; a kernel without an
-# entry reports None.
-NCU_TRAFFIC_PER_ITER = {"k_lsqr": (7.072e9 + 0.222e9) / 50}
-NCU_TRAFFIC = {"k_qrcp_cluster": 0.264e9 + 0.868e9}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of ncu captures,
+# per workload and kernel: a profile constant, not measured in this run.  Each
+# entry names its capture (profiles/) and the SHA-256 prefix of the kernel's
+# source file when it was taken; the line reports the traffic only while the
+# source is unchanged (else null).  "per": iteration (scaled by the launch's
+# iteration count) or launch.
+NCU_TRAFFIC = {}
 
 
-def workload(case: str = "full"):
-    """The 20x20x300 workload; "small" keeps its block shapes (same spacing,
-    same points per block) on 10 x 10 subdomains of the box [0, 9/19]^2, for
-    profiler captures."""
+def source_sha16(rel: str) -> str:
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2506_17626_gb300", rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def workload(case: str = "heat"):
+    """The benchmark's workload.  "small" keeps the heat blocks' shapes (same
+    centre spacing and points per block) on 4 x 4 x 4 subdomains of the box
+    [0, 1/3]^3, for profiler captures."""
     if case == "small":
-        p = synth.poisson2d(S=10, n=180)
-        p.hi = (9.0 / 19.0, 9.0 / 19.0, 1.0)
-        p.n_test = [180, 180]
+        p = synth.heat3d(S=4, n=33)
+        p.hi = (1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0)
+        p.n_test = [20, 20, 20]
         return p
-    return synth.poisson2d()
+    if case == "p2d":
+        return synth.poisson2d()
+    return synth.heat3d()
+
+
+def workload_name(p) -> str:
+    if p.dim == 3:
+        return (f"(2+1)D heat, {p.S[0]}x{p.S[1]}x{p.S[2]} space-time subdomains, delta {p.delta:g}, K={p.K}, "
+                f"{p.n[0]}^3 interior + boundary/initial rows, kappa {p.kappa:g}, k=6, filter tol {TOL:g}, "
+                f"error on {p.n_test[0]}^3 test grid")
+    if p.dim == 2:
+        return (f"2D Poisson {p.S[0]}x{p.S[1]} subdomains, delta {p.delta:g}, K={p.K}, {p.n[0]}^2 interior + "
+                f"{4 * p.n[0]} boundary rows, filter tol {TOL:g}, error on {p.n_test[0]}^2 test grid")
+    return f"1D Poisson, {p.S[0]} subdomains, delta {p.delta:g}, K={p.K}, {p.n[0]} interior + 2 boundary rows"
 
 
 def instance_seed(base_seed: int, rank: int) -> int:
@@ -189,73 +218,67 @@ class Clocks:
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def run_gpu(args):
+def calibrate(S, d_prm, Xt, cal_iters, every, dev):
+    """Zero-start LSQR for cal_iters iterations, the iterate every `every`
+    iterations evaluated (relative L2 on the test grid) and the residual of
+    the assembled system at it (FP64); returns (errors, residuals, kept)."""
+    import torch
+    S.assemble(d_prm)
+    rank = S.filter()
+    cap = cal_iters // every
+    snap = torch.zeros((cap, S.sizes["n_cols"]), dtype=torch.float64, device=dev)
+    S.solve(atol=0, btol=0, max_iter=cal_iters, snap=snap, snap_every=every)
+    errs, res = [], []
+    for k in range(cap):
+        a_k = S.coefficients(snap[k])
+        _, err = S.evaluate(d_prm, a_k, [Xt])
+        e = err.cpu().numpy()
+        errs.append(float(np.sqrt(e[0] / e[1])))
+        res.append(float(S.residual(a_k)[0].item()))
+    del snap
+    return np.array(errs), np.array(res), int(rank.sum().item())
+
+
+def time_to_error(p, args, dev, world, rank_id, headline):
+    """Both paths (mixed: FP32 assembly and Q_hat; FP64: FP64 assembly, QR
+    and Q_hat) on workload p: calibration, target, timed steps, kernel
+    profile.  `headline` adds the end-to-end run through host buffers."""
     import torch
     import torch.distributed as dist
-    from paper_2506_17626_gb300 import build as B
-    B.build()
     import paper_2506_17626_gb300 as R
     from paper_2506_17626_gb300 import _native as N
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    dev = torch.device("cuda", local)
-
-    p = workload(args.case)
-    if world > 1:           # independent instances, one per rank (weak scaling)
-        p.seed = instance_seed(p.seed, rank)
     prm = synth.feature_params(p)
     h_prm = torch.from_numpy(prm.ravel()).pin_memory()
     d_prm = h_prm.to(dev)
     Xt = torch.from_numpy(oracle_free_test_grid(p)).to(dev)
-
-    def make(asm, op):
-        S = R.System([p], asm=asm, op=op, tol=TOL, device=str(dev))
-        return S
-
-    paths = {"mixed": make("fp32", "q32"), "fp64": make("fp64", "q64")}
-    # the QR cluster size is autotuned on the first filter call of each path
-    # (untimed: calibration or warm-up) unless --no-autotune
-    N.set_autotune(not args.no_autotune)
-
-    # ---- calibration (untimed): error after every SNAP_EVERY iterations
-    curves, conv = {}, {}
-    for name, S in (paths.items() if args.iters_mixed is None else []):
-        S.assemble(d_prm)
-        S.filter()
-        cap = CAL_ITERS // SNAP_EVERY
-        snap = torch.zeros((cap, S.sizes["n_cols"]), dtype=torch.float64, device=dev)
-        a, rep = S.solve(atol=0, btol=0, max_iter=CAL_ITERS, snap=snap, snap_every=SNAP_EVERY)
-        errs = []
-        for s in range(cap):
-            a_s = S.coefficients(snap[s])
-            _, err = S.evaluate(d_prm, a_s, [Xt])
-            e = err.cpu().numpy()
-            errs.append(float(np.sqrt(e[0] / e[1])))
-        curves[name] = np.array(errs)
-        conv[name] = {"min_rel_l2": float(curves[name].min()),
-                      "at_iteration": SNAP_EVERY * (1 + int(curves[name].argmin())),
-                      "rel_l2_at_10000": float(curves[name][-1]), "kept_columns": int(S.filter().sum().item())}
-        log(f"[cal] {name}: min rel L2 {curves[name].min():.3e} at it {SNAP_EVERY * (1 + int(curves[name].argmin()))}")
-    target = None
-    if args.iters_mixed is not None:
-        kstar = {"mixed": args.iters_mixed, "fp64": args.iters_fp64 or args.iters_mixed}
-        target = args.target
-    else:
+    paths = {"mixed": R.System([p], asm="fp32", op="q32", tol=TOL, device=str(dev)),
+             "fp64": R.System([p], asm="fp64", op="q64", tol=TOL, device=str(dev))}
+    every = args.snap_every
+    curves, resid, conv = {}, {}, {}
+    if args.iters_mixed is None:
+        for name, S in paths.items():
+            e, r, kept = calibrate(S, d_prm, Xt, args.cal_iters, every, dev)
+            curves[name], resid[name] = e, r
+            conv[name] = {"min_rel_l2": float(e.min()), "at_iteration": every * (1 + int(e.argmin())),
+                          "rel_l2_at_end": float(e[-1]), "kept_columns": kept,
+                          "rel_l2_history": [float(v) for v in e[:: max(1, len(e) // 20)]],
+                          "residual_history": [float(v) for v in r[:: max(1, len(r) // 20)]],
+                          "history_every": every * max(1, len(e) // 20)}
+            log(f"[cal] {p.name} {name}: min rel L2 {e.min():.3e} at it {every * (1 + int(e.argmin()))}")
+        target = None
         for t in TARGET_LADDER:
             if all((c <= t).any() for c in curves.values()):
                 target = t
                 break
         if target is None:
             target = float(max(c.min() for c in curves.values())) * 1.01
-        kstar = {n: SNAP_EVERY * (1 + int(np.argmax(c <= target))) for n, c in curves.items()}
-    log(f"[cal] target {target}, iterations {kstar}")
+        kstar = {n: every * (1 + int(np.argmax(c <= target))) for n, c in curves.items()}
+    else:
+        kstar = {"mixed": args.iters_mixed, "fp64": args.iters_fp64 or args.iters_mixed}
+        target = args.target
+    log(f"[cal] {p.name}: target {target}, iterations {kstar}")
 
-    # ---- timed steps
     st = torch.cuda.current_stream()
 
     def step(S, k, e2e=False):
@@ -300,97 +323,148 @@ def run_gpu(args):
         per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
         return per, outs, prof_data
 
-    with Clocks(args.clocks_log) as clk:
-        per_mixed, outs, prof = timed(paths["mixed"], kstar["mixed"], args.steps, args.warmup, prof=True)
-    per_fp64, outs64, prof64 = timed(paths["fp64"], kstar["fp64"], args.steps, args.warmup, prof=True)
-    per_e2e, outs_e2e, _ = timed(paths["mixed"], kstar["mixed"], args.steps, max(1, args.warmup // 2), e2e=True)
+    steps_m = args.steps if headline else min(args.steps, 3)
+    warm_m = args.warmup if headline else max(1, min(args.warmup, 2))
+    steps_f = min(args.steps, 5) if headline else min(args.steps, 2)
+    clk = None
+    if headline:
+        with Clocks(args.clocks_log) as clk:
+            per_mixed, outs, prof = timed(paths["mixed"], kstar["mixed"], steps_m, warm_m, prof=True)
+    else:
+        per_mixed, outs, prof = timed(paths["mixed"], kstar["mixed"], steps_m, warm_m, prof=True)
+    per_fp64, outs64, _ = timed(paths["fp64"], kstar["fp64"], steps_f, 1)
+    out = {"workload": workload_name(p), "target_rel_l2": target, "solved": bool(target <= SOLVED_AT),
+           "iterations": kstar}
+    if target > SOLVED_AT:
+        out["note"] = (f"no path reaches {SOLVED_AT:g} relative L2 within {args.cal_iters} LSQR iterations: the "
+                       f"times are those of solves that have not converged (tightest common error {target:g})")
+    err_m, err_f = outs[1].cpu().numpy(), outs64[1].cpu().numpy()
+    out["rel_l2_reached"] = {"mixed": float(np.sqrt(err_m[0] / err_m[1])), "fp64": float(np.sqrt(err_f[0] / err_f[1]))}
+    out["convergence"] = conv
+    ms_mixed = max_over_ranks(float(np.mean(per_mixed)), world, dev)
+    ms_fp64 = max_over_ranks(float(np.mean(per_fp64)), world, dev)
+    out.update({"ms_mixed": ms_mixed, "ms_fp64": ms_fp64, "steps_mixed": steps_m, "steps_fp64": steps_f})
+    if headline:
+        per_e2e, _, _ = timed(paths["mixed"], kstar["mixed"], steps_f, 1, e2e=True)
+        out["e2e"] = {"value": max_over_ranks(float(np.mean(per_e2e)), world, dev), "unit": "ms",
+                      "h2d_bytes_per_step": int(h_prm.numel() * 8),
+                      "d2h_bytes_per_step": int(paths["mixed"].sizes["n_cols"] * 8 + 4 * 8),
+                      "steps": steps_f}
+        out["clocks"] = clk.summary() if clk else None
 
-    def mx(v):
-        return max_over_ranks(v, world, dev)
-
-    ms_mixed = mx(float(np.mean(per_mixed)))
-    ms_fp64 = mx(float(np.mean(per_fp64)))
-    ms_e2e = mx(float(np.mean(per_e2e)))
-    err_m = outs[1].cpu().numpy()
-    err_f = outs64[1].cpu().numpy()
-    rel_m = float(np.sqrt(err_m[0] / err_m[1]))
-    rel_f = float(np.sqrt(err_f[0] / err_f[1]))
-
-    # ---- roofline of the dominant kernel (mixed path)
+    # ---- rates and the roofline of the dominant kernel (mixed path)
     S = paths["mixed"]
     ranks = S.filter().cpu().numpy()
-    m = np.array([S.block_info(j)[0] for j in range(S.sizes["n_blocks"])])
+    m = S.block_table()[0]
     K = p.K
-    steps = args.steps
-    tot = {k: v for k, v in prof.items()}
-    dom = max(tot, key=lambda k: tot[k][1])
-    launches = sum(v[0] for v in tot.values())
+    tot = dict(prof)
     per_launch_ms = {k: v[1] / v[0] for k, v in tot.items()}
-    roof = None
-    qr_name = "k_qrcp_cluster" if "k_qrcp_cluster" in per_launch_ms else "k_qrcp"
-    fused_q = qr_name == "k_qrcp_cluster"     # Q_hat accumulated in the same kernel
-    qr_alg = qrcp_flops(m, K, ranks) + (formq_flops(m, ranks) if fused_q else 0.0)
-    if dom == qr_name:
-        # the mixed path's blocks are FP32-assembled: the cluster kernel factors
-        # them in double-float, the global-memory fallback in FP64
-        fl = qr_alg
-        ach = fl / (per_launch_ms[dom] * 1e-3) / 1e12
+    out["kernels_ms_per_step"] = {k: v[1] / steps_m for k, v in tot.items()}
+    out["gpu_launches"] = int(sum(v[0] for v in tot.values()))
+    dom = max(tot, key=lambda k: tot[k][1])
+    qr_names = [k for k in ("k_qrcp_cluster", "k_qrcp", "k_form_q") if k in per_launch_ms]
+    qr_ms = sum(per_launch_ms[k] for k in qr_names)
+    fused_q = "k_qrcp_cluster" in per_launch_ms
+    qr_alg = qrcp_flops(m, K, ranks) + formq_flops(m, ranks)
+    out["qr_gflops"] = qr_alg / (qr_ms * 1e-3) / 1e9
+    lsqr_by = lsqr_bytes_per_iter(m, ranks, S.sizes["n_rows"], 4) * kstar["mixed"]
+    out["spmv_gbs"] = lsqr_by / (per_launch_ms["k_lsqr"] * 1e-3) / 1e9
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    if dom in ("k_qrcp_cluster", "k_qrcp", "k_form_q"):
+        # the QR and the formation of Q_hat: algorithmic flops over their time
+        ach = qr_alg / (qr_ms * 1e-3) / 1e12
         if fused_q:
             pk, src = DF_PEAK_GFLOPS / 1e3, ("derived double-float: FP32 issue 152 SMs x 4 x 32 lanes x 2.07 GHz / "
                                              "27 instructions per 4-flop update element")
         else:
-            pk, src = FP64_PEAK_GFLOPS / 1e3, "derived FP64: 152 SMs x 4 flop/clk x 2.07 GHz"
-        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                "frac": ach / pk, "peak_source": src, "algorithmic_per_launch": fl}
-    elif dom == "k_form_q":
-        fl = formq_flops(m, ranks)
-        ach = fl / (per_launch_ms[dom] * 1e-3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
-                "frac": ach / (FP64_PEAK_GFLOPS / 1e3), "peak_source": "derived FP64: 152 SMs x 4 flop/clk x 2.07 GHz",
-                "algorithmic_per_launch": fl}
+            pk, src = FP64_PEAK_GFLOPS / 1e3, "derived FP64: 152 SMs x 4 flop/clk x 2.07 GHz (DFMA probe 1.19)"
+        roof = {"kernel": "+".join(qr_names), "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                "frac": ach / pk, "peak_source": src, "algorithmic_per_launch": qr_alg,
+                "algorithmic": "sum over blocks and QR steps i < r_j of 4 (m_j - i)(K - i), plus 4 (m_j - i)(r_j - i) "
+                               "for Q_hat"}
     else:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        by = lsqr_bytes_per_iter(m, ranks, S.sizes["n_rows"], 4) * kstar["mixed"]
-        ach = by / (per_launch_ms[dom] * 1e-3) / 1e9
+        ach = lsqr_by / (per_launch_ms[dom] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-                "algorithmic_per_launch": by}
-    roof["traffic"] = (NCU_TRAFFIC_PER_ITER[dom] * kstar["mixed"] if dom in NCU_TRAFFIC_PER_ITER
-                       else NCU_TRAFFIC.get(dom))
-    qr_gflops = qr_alg / (per_launch_ms[qr_name] * 1e-3) / 1e9
-    lsqr_ms = per_launch_ms["k_lsqr"]
-    spmv_gbs = lsqr_bytes_per_iter(m, ranks, S.sizes["n_rows"], 4) * kstar["mixed"] / (lsqr_ms * 1e-3) / 1e9
+                "algorithmic_per_launch": lsqr_by,
+                "algorithmic": "2 nnz(Q_hat) x 4 B + 2 (N + sum r_j) x 8 B per iteration x iterations"}
+    case = "heat" if p.dim == 3 else ("p2d" if p.dim == 2 else "p1d")
+    tr = NCU_TRAFFIC.get((case, dom))
+    roof["traffic"] = None
+    if tr is not None and source_sha16(tr["source"]) == tr["sha16"]:
+        per = kstar["mixed"] if tr["per"] == "iteration" else 1
+        roof["traffic"] = tr["bytes"] * per
+        roof["traffic_source"] = (f"profile constant: ncu capture {tr['profile']} of the same kernel source "
+                                  f"(sha256 {tr['sha16']}), scaled per {tr['per']}")
+        if roof["bound"] == "hbm":
+            dram = roof["traffic"] / (per_launch_ms[dom] * 1e-3) / 1e9
+            roof["dram_achieved"] = dram
+            roof["dram_frac"] = dram / peaks["hbm_gbs"]
+    out["roofline"] = roof
+    return out, paths
 
-    clocks = clk.summary()
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2506_17626_gb300 import build as B
+    B.build()
+    from paper_2506_17626_gb300 import _native as N
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    # the QR cluster size is autotuned on the first filter call of each block
+    # shape (untimed: calibration or warm-up) unless --no-autotune
+    N.set_autotune(not args.no_autotune)
+
+    p = workload(args.case)
+    if world > 1:           # independent instances, one per rank (weak scaling)
+        p.seed = instance_seed(p.seed, rank)
+    head, paths = time_to_error(p, args, dev, world, rank, headline=True)
     out = {
         "metric": "solve time to fixed error (mixed FP32/FP64, zero start)",
-        "value": ms_mixed, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_mixed, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": "2D Poisson 20x20 subdomains, delta 1.25, K=300, 360^2 interior + 1440 boundary "
-                               "rows, filter tol 1e-6, error on 400^2 test grid",
-                   "target_rel_l2": target, "iterations": kstar, "rel_l2_reached": {"mixed": rel_m, "fp64": rel_f},
-                   "convergence_10000_iterations": conv,
-                   "l2_flush": "none: working set (M, QR work, Q_hat > 1.5 GB) exceeds L2 every step",
+        "value": head["ms_mixed"], "unit": "ms", "n_gpus": world, "steps": head["steps_mixed"],
+        "warmup": args.warmup, "ms_per_step": head["ms_mixed"], "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": head["workload"], "target_rel_l2": head["target_rel_l2"], "solved": head["solved"],
+                   "iterations": head["iterations"], "rel_l2_reached": head["rel_l2_reached"],
+                   "convergence_10000_iterations": head["convergence"],
+                   "l2_flush": "none: the working set (M, QR work, Q_hat: > 1.5 GB) exceeds L2 every step",
                    "parallelism": f"independent instances x{world}" if world > 1 else "1 instance",
                    "qr_cluster_autotune": not args.no_autotune},
-        "fp64_zero_start_ms": ms_fp64,
-        "qr_gflops": qr_gflops, "spmv_gbs": spmv_gbs,
-        "kernels_ms_per_step": {k: v[1] / steps for k, v in tot.items()},
-        "roofline": roof,
-        "e2e": {"value": ms_e2e, "unit": "ms", "h2d_bytes_per_step": int(h_prm.numel() * 8),
-                "d2h_bytes_per_step": int(S.sizes["n_cols"] * 8 + 4 * 8)},
-        "gpu_launches": int(launches),
-        "clocks": clocks,
+        "fp64_zero_start_ms": head["ms_fp64"],
+        "qr_gflops": head["qr_gflops"], "spmv_gbs": head["spmv_gbs"],
+        "kernels_ms_per_step": head["kernels_ms_per_step"],
+        "roofline": head["roofline"],
+        "e2e": head["e2e"],
+        "gpu_launches": head["gpu_launches"],
+        "clocks": head["clocks"],
     }
+    if "note" in head:
+        out["config"]["note"] = head["note"]
+    del paths
+    torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(p, prm, kstar["fp64"], stride=args.cpu_stride)
-    if rank == 0 and world == 1 and args.batched > 0:
-        out["batched"] = guarded(run_batched, args, dev)
-    if rank == 0 and world == 1 and args.learned_train > 0:
-        out["learned"] = guarded(run_learned, args, dev)
+        prm = synth.feature_params(p)
+        out["cpu_baseline"] = cpu_baseline(p, prm, head["iterations"]["fp64"], stride=args.cpu_stride)
+        out["cpu_baseline_all_cores"] = guarded(cpu_baseline_pool, p, prm, head["iterations"]["fp64"],
+                                                args.cpu_stride_pool)
+    if rank == 0 and world == 1 and args.case != "p2d" and not args.no_p2d:
+        sec = guarded(lambda: time_to_error(synth.poisson2d(), args, dev, 1, 0, headline=False)[0])
+        out["poisson2d"] = sec
+        torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_poisson1d:
         out["poisson1d"] = guarded(run_poisson1d, args, dev)
+    if rank == 0 and world == 1 and args.batched > 0:
+        out["batched"] = guarded(run_batched, args, dev)
+        torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and args.learned_train > 0:
+        out["learned"] = guarded(run_learned, args, dev)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -478,50 +552,68 @@ def run_batched(args, dev):
 def run_poisson1d(args, dev):
     """Time to 1e-6 relative L2 error on the 1D Poisson workload (-u'' = f on
     [0,1], u = sin 2 pi x + 0.1 sin 50 pi x, 20 subdomains, overlap ratio
-    1.3, K = 100, 1600 interior points, FP64), which, unlike the 2D workload,
-    reaches it.  Calibration (untimed): zero-start LSQR for 10,000 iterations
-    with the iterate evaluated every 100, plain LSQR on the unfiltered M and
-    the filtered, preconditioned solver (R_hat^-1 operator) at thresholds 1e-6
-    and 1e-8.  Timed (CUDA events, after warm-up): assemble -> filter -> LSQR
-    for the first recorded iteration count at 1e-6 -> a = S^-1 y -> u_hat and
-    its error, for each threshold that reaches 1e-6; plain LSQR does not reach
-    it, and its best error and the time of its 10,000 iterations are
-    reported."""
+    1.3, K = 100, 1600 interior points), which, unlike the 2D and heat
+    workloads, reaches it.  Calibration (untimed): zero-start LSQR for 10,000
+    iterations, the iterate evaluated every 100, for plain LSQR on the
+    unfiltered M and for the filtered, preconditioned solver at threshold
+    1e-8 with three operators: the paper's form (FP64 kept columns and
+    R_hat^-1 substitution, ar64), the explicit FP64 Q_hat (q64, FP64 path),
+    and the mixed path's FP32 Q_hat (FP64 blocks factored in double-float;
+    also with three refinement steps on the FP64 residual).  Timed (CUDA
+    events, after warm-up): assemble -> filter -> LSQR for the first
+    recorded iteration count at 1e-6 -> a = S^-1 y -> u_hat and its error,
+    for each run that reaches 1e-6."""
     import torch
     import paper_2506_17626_gb300 as R
+    from paper_2506_17626_gb300 import _native as N
     from paper_2506_17626_gb300 import sweep as SW
     p = synth.poisson1d()
     prm = torch.from_numpy(synth.feature_params(p).ravel()).to(dev)
     X = torch.from_numpy(SW.grid_points(p)).to(dev)
-    runs = SW.sweep(p, prm, X, asm="fp64", op="ar64", sigmas=(1e-6, 1e-8), iters=10000, every=100, device=dev)
+    sig = 1e-8
     st = torch.cuda.current_stream()
-    out = {"workload": "1D Poisson, 20 subdomains, delta 1.3, K=100, 1600 interior + 2 boundary rows, FP64, "
-                       "error on 1000 test points", "target_rel_l2": 1e-6, "runs": []}
-    for r in runs:
-        row = {k: r[k] for k in ("op", "sigma", "dropped_pct", "min_rel_l2", "min_rel_l2_at", "min_e_l1",
-                                 "iterations_to", "lsqr_ms")}
-        k = r["iterations_to"]["1e-06"]
-        if k is not None:
-            S = R.System([p], asm="fp64", op=r["op"], tol=r["sigma"] or 0.0, device=str(dev))
+    out = {"workload": "1D Poisson, 20 subdomains, delta 1.3, K=100, 1600 interior + 2 boundary rows, "
+                       "error on 1000 test points", "target_rel_l2": 1e-6, "sigma": sig, "runs": []}
+    specs = [("plain", "fp64", "plain", 1), ("paper operator (ar64), FP64", "fp64", "ar64", 1),
+             ("explicit Q_hat (q64), FP64", "fp64", "q64", 1),
+             ("mixed: FP32 Q_hat (q32), FP64 blocks, double-float QR", "fp64", "q32", 2)]
 
-            def step():
-                S.assemble(prm)
-                S.filter()
-                a, _ = S.solve(atol=0.0, btol=0.0, max_iter=k)
-                return S.evaluate(prm, a, [X])[1]
+    def timed_step(S, k, refine=0, refine_iters=0):
+        def step():
+            S.assemble(prm)
+            S.filter()
+            a, _ = S.solve(atol=0.0, btol=0.0, max_iter=k, refine_steps=refine, refine_iters=refine_iters)
+            return S.evaluate(prm, a, [X])[1]
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        n = max(1, min(args.steps, 10))
+        ev[0].record(st)
+        for _ in range(n):
+            err = step()
+        ev[1].record(st)
+        torch.cuda.synchronize()
+        e = SW.errors_from_sums(err.cpu().numpy(), X.shape[0])
+        return ev[0].elapsed_time(ev[1]) / n, e["rel_l2"]
 
-            for _ in range(max(3, args.warmup)):
-                step()
-            torch.cuda.synchronize()
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-            ev[0].record(st)
-            for _ in range(args.steps):
-                err = step()
-            ev[1].record(st)
-            torch.cuda.synchronize()
-            e = SW.errors_from_sums(err.cpu().numpy(), X.shape[0])
-            row.update({"iterations": k, "time_to_target_ms": ev[0].elapsed_time(ev[1]) / args.steps,
-                        "rel_l2_reached": e["rel_l2"]})
+    for label, asm, op, qdf in specs:
+        N.set_qr_double_float(qdf)
+        try:
+            r = SW.run_one(p, prm, X, asm, op, 0.0 if op == "plain" else sig, 10000, 100, dev)
+            row = {"run": label, **{k: r[k] for k in ("op", "sigma", "dropped_pct", "min_rel_l2", "min_rel_l2_at",
+                                                       "min_e_l1", "iterations_to", "lsqr_ms")}}
+            k = r["iterations_to"]["1e-06"]
+            S = R.System([p], asm=asm, op=op, tol=0.0 if op == "plain" else sig, device=str(dev))
+            if k is not None:
+                t, e = timed_step(S, k)
+                row.update({"iterations": k, "time_to_target_ms": t, "rel_l2_reached": e})
+            if op == "q32":
+                t, e = timed_step(S, 3000, refine=3, refine_iters=1000)
+                row["refined"] = {"iterations": "3000 + 3 x 1000", "ms": t, "rel_l2": e, "reaches_target": e <= 1e-6}
+            del S
+        finally:
+            N.set_qr_double_float(1)
         out["runs"].append(row)
     return out
 
@@ -680,15 +772,24 @@ def oracle_free_test_grid(p):
 # CPU oracle leg (bounded sample)
 # ---------------------------------------------------------------------------
 
-def cpu_baseline(p, prm, iters, stride=2):
-    """The oracle (single-threaded FP64 C, as it stands) on every stride-th
-    block of the workload: assembly, QRCP and 10 LSQR iterations of the
-    sampled-block subsystem, plus evaluation at every 10th test point; each
-    part scaled to the full workload (blocks x J/sample, iterations x the FP64
-    path's iteration count, points x 10)."""
+def _oracle_block(args):
+    """One block through the oracle (assembly and QR with column pivoting);
+    returns its wall times.  Top-level so that a spawned worker can run it."""
+    p, prm, j = args
+    import oracle
+    t0 = time.perf_counter()
+    Bk = oracle.assemble(p, prm, blocks=[j])
+    t1 = time.perf_counter()
+    oracle.filter_blocks(Bk, TOL)
+    return t1 - t0, time.perf_counter() - t1
+
+
+def _oracle_sample(p, prm, blocks, iters, pt_stride):
+    """The oracle on the sampled blocks: assembly and QR timed per block, 10
+    LSQR iterations of the sampled-block subsystem, evaluation at every
+    pt_stride-th test point; each part scaled to the whole workload."""
     import oracle
     J = p.J
-    blocks = list(range(0, J, stride))
     t0 = time.perf_counter()
     Bk = oracle.assemble(p, prm, blocks=blocks)
     t_asm = time.perf_counter() - t0
@@ -699,44 +800,94 @@ def cpu_baseline(p, prm, iters, stride=2):
     t0 = time.perf_counter()
     Ssub.lsqr(Bk.h, atol=0, btol=0, max_iter=10)
     t_it = (time.perf_counter() - t0) / 10
-    X = oracle_free_test_grid(p)[::10]
-    a = np.zeros(J * p.K)
+    X = oracle_free_test_grid(p)[::pt_stride]
     t0 = time.perf_counter()
-    oracle.evaluate(p, prm, a, X)
-    t_ev = (time.perf_counter() - t0) * 10
+    oracle.evaluate(p, prm, np.zeros(J * p.K), X)
+    t_ev = (time.perf_counter() - t0) * pt_stride
     scale = J / len(blocks)
-    total_s = (t_asm + t_qr) * scale + t_it * scale * iters + t_ev
-    return {"value": total_s * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": f"{len(blocks)} of {J} blocks (one in {stride}): assembly + QRCP + 10 LSQR iterations on "
-                      f"the sampled subsystem scaled x{scale:g} and to {iters} iterations; evaluation at every "
-                      f"10th of the 400^2 test points scaled x10",
-            "parts_s": {"assembly": t_asm * scale, "qrcp": t_qr * scale, "lsqr": t_it * scale * iters,
-                        "eval": t_ev}}
+    parts = {"assembly": t_asm * scale, "qrcp": t_qr * scale, "lsqr": t_it * scale * iters, "eval": t_ev}
+    return parts, sum(parts.values())
+
+
+def sample_blocks(p, stride: int, offset: int = 0):
+    return list(range(offset % stride, p.J, stride))
+
+
+def cpu_baseline(p, prm, iters, stride=100):
+    """The oracle (single-threaded FP64 C, as it stands) on every stride-th
+    block of the workload: assembly, QRCP and 10 LSQR iterations of the
+    sampled-block subsystem, evaluation at every 10th test point; each part
+    scaled to the full workload (blocks x J / sample, iterations x the FP64
+    path's iteration count, points x 10).  Extrapolated, not a full run."""
+    blocks = sample_blocks(p, stride)
+    parts, total_s = _oracle_sample(p, prm, blocks, iters, 10)
+    return {"value": total_s * 1e3, "unit": "ms", "cores": 1, "kind": "oracle", "extrapolated": True,
+            "sample": f"{len(blocks)} of {p.J} blocks (one in {stride}): assembly + QRCP + 10 LSQR iterations on "
+                      f"the sampled subsystem scaled x{p.J / len(blocks):g} and to {iters} iterations; evaluation at "
+                      f"every 10th test point scaled x10",
+            "parts_s": parts}
+
+
+def cpu_baseline_pool(p, prm, iters, stride=25):
+    """The oracle's assembly and QR of every stride-th block on all of this
+    host's cores (a process pool over blocks, started with spawn; core count
+    from sched_getaffinity), scaled to the workload; the LSQR and evaluation
+    parts are those of the single-threaded oracle (its LSQR products and
+    evaluation are sequential code), measured here on the same sample."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0))
+    blocks = sample_blocks(p, stride)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_block, [(p, prm, blocks[0])] * min(cores, len(blocks)))   # warm: workers load the oracle
+        t0 = time.perf_counter()
+        pool.map(_oracle_block, [(p, prm, j) for j in blocks], chunksize=1)
+        t_blocks = time.perf_counter() - t0
+    parts, _ = _oracle_sample(p, prm, blocks[:: max(1, len(blocks) // 4)], iters, 10)
+    scale = p.J / len(blocks)
+    total = t_blocks * scale + parts["lsqr"] + parts["eval"]
+    return {"value": total * 1e3, "unit": "ms", "cores": cores, "kind": "oracle", "extrapolated": True,
+            "sample": f"assembly + QRCP of {len(blocks)} of {p.J} blocks (one in {stride}) over {cores} processes, "
+                      f"scaled x{scale:g}; LSQR and evaluation single-threaded as in cpu_baseline",
+            "parts_s": {"assembly_qrcp": t_blocks * scale, "lsqr": parts["lsqr"], "eval": parts["eval"]}}
 
 
 def run_reference(args):
-    """Reference arm: the CPU oracle as it stands, one bounded sample per step."""
+    """Reference arm: the CPU oracle as it stands on the headline workload,
+    one bounded sample per step: step i runs block sample[i mod len] of the
+    same one-in-stride sample as cpu_baseline (assembly, QRCP, 10 LSQR
+    iterations of that block's subsystem) and evaluation at every 100th test
+    point, scaled to the workload; the mean over the steps estimates the
+    same extrapolated time as cpu_baseline."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
     oracle.build()
-    p = workload()
+    p = workload(args.case)
     prm = synth.feature_params(p)
     iters = args.ref_iters
+    blocks = sample_blocks(p, args.cpu_stride)
     vals = []
+    t_start = time.perf_counter()
     for s in range(args.warmup + args.steps):
-        r = cpu_baseline(p, prm, iters, stride=8)
+        j = blocks[s % len(blocks)]
+        parts, total = _oracle_sample(p, prm, [j], iters, 100)
         if s >= args.warmup:
-            vals.append(r["value"])
+            vals.append(total * 1e3)
+    wall = time.perf_counter() - t_start
     v = float(np.mean(vals))
+    smp = (f"per step one of the {len(blocks)} blocks of the one-in-{args.cpu_stride} sample (cycled): assembly + "
+           f"QRCP + 10 LSQR iterations of its subsystem scaled x{p.J} and to {iters} iterations; evaluation at every "
+           f"100th test point scaled x100")
     out = {"impl": "reference", "metric": "solve time to fixed error (mixed FP32/FP64, zero start)",
            "value": v, "unit": "ms", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "2D Poisson 20x20 subdomains, delta 1.25, K=300, 360^2 interior + 1440 boundary "
-                                  "rows, filter tol 1e-6, error on 400^2 test grid", "lsqr_iterations": iters},
-           "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": r["sample"]},
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "extrapolated": True,
+           "config": {"workload": workload_name(p), "lsqr_iterations": iters,
+                      "wall_s_of_this_run": wall},
+           "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": smp,
+                            "extrapolated": True},
            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -748,11 +899,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-stride", type=int, default=2,
-                    help="the CPU baseline runs the oracle on every n-th block (about 10-30 s at 2)")
-    ap.add_argument("--ref-iters", type=int, default=2600,
-                    help="LSQR iteration count the reference arm extrapolates to (the calibrated count of the "
-                         "GPU arm on this workload)")
+    ap.add_argument("--cpu-stride", type=int, default=100,
+                    help="the CPU baseline runs the oracle on every n-th block (one core); the reference arm "
+                         "cycles through the same sample, one block per step")
+    ap.add_argument("--cpu-stride-pool", type=int, default=25,
+                    help="block sample of the all-cores oracle leg")
+    ap.add_argument("--ref-iters", type=int, default=100,
+                    help="LSQR iteration count the reference arm extrapolates to (the FP64 path's calibrated count "
+                         "on the headline workload)")
+    ap.add_argument("--cal-iters", type=int, default=CAL_ITERS, help="calibration budget (LSQR iterations)")
+    ap.add_argument("--snap-every", type=int, default=100, help="calibration: iterate recorded every n iterations")
     ap.add_argument("--iters-mixed", type=int, default=None, help="skip calibration: LSQR iterations (mixed)")
     ap.add_argument("--iters-fp64", type=int, default=None, help="skip calibration: LSQR iterations (FP64)")
     ap.add_argument("--target", type=float, default=None, help="target recorded when calibration is skipped")
@@ -765,8 +921,10 @@ def main():
     ap.add_argument("--batched", type=int, default=64, help="instances of the batched section (0 skips it)")
     ap.add_argument("--no-poisson1d", action="store_true", help="skip the 1D time-to-1e-6 section")
     ap.add_argument("--batched-iters", type=int, default=2000)
-    ap.add_argument("--case", default="full", choices=["full", "small"],
-                    help="small: 10x10 subdomains with the same block shapes (profiler captures)")
+    ap.add_argument("--no-p2d", action="store_true", help="skip the 2D Poisson section")
+    ap.add_argument("--case", default="heat", choices=["heat", "p2d", "small"],
+                    help="heat: the (2+1)D heat workload (default); p2d: the 2D Poisson workload; small: heat "
+                         "blocks on 4x4x4 subdomains (profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -232,6 +232,16 @@ rfm_status rfm_lsqr_solve(const rfm_problem *probs, int n_inst, const rfm_config
                           const double *d_y0, double *d_y, double *d_a, rfm_lsqr_report *d_report,
                           void *d_ws, size_t ws_bytes, void *stream);
 
+/* Residual of the assembled least-squares system (Eqs. (4)-(5)) at
+ * coefficients d_a (n_cols doubles, the J*K layout of rfm_lsqr_solve):
+ * r = h - M a in FP64 from the stored blocks (FP64, or the FP32 blocks'
+ * values taken exactly), each row summed over its blocks in a fixed order.
+ * d_r (nullable, n_rows doubles) receives r; d_rnorm (nullable, n_inst
+ * doubles) ||r|| per instance.  Uses the workspace's row scratch (do not
+ * overlap with rfm_lsqr_solve on the same workspace).  Requires rfm_assemble. */
+rfm_status rfm_residual(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const double *d_a, double *d_r,
+                        double *d_rnorm, void *d_ws, size_t ws_bytes, void *stream);
+
 /* a = S^-1 y (Algorithm 2's last step) for an arbitrary y in the n_cols
  * layout: per block a_j[perm[c]] = (R_hat_j^-1 y_j)[c] for kept c, 0 at
  * dropped columns (RFM_OP_PLAIN: a = y).  Requires a filtered workspace. */

@@ -94,6 +94,16 @@ class System:
                                                           C.c_void_p(self.ws_ptr), self.ws_bytes, _stream()))
         return (a, rep, y) if want_y else (a, rep)
 
+    def residual(self, a: torch.Tensor, want_r: bool = False):
+        """||h - M a|| per instance (FP64, from the assembled blocks), and r
+        itself when want_r."""
+        assert a.is_cuda and a.dtype == torch.float64 and a.numel() == self.sizes["n_cols"]
+        r = torch.empty(self.sizes["n_rows"], dtype=torch.float64, device=self.device) if want_r else None
+        rn = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        N.check("rfm_residual", self.lib.rfm_residual(self._probs, self.n, C.byref(self._cfg), _ptr(a), _ptr(r),
+                                                      _ptr(rn), C.c_void_p(self.ws_ptr), self.ws_bytes, _stream()))
+        return (rn, r) if want_r else rn
+
     def coefficients(self, y: torch.Tensor) -> torch.Tensor:
         """a = S^-1 y with zeros at dropped columns (Algorithm 2, last step)."""
         a = torch.empty(self.sizes["n_cols"], dtype=torch.float64, device=self.device)

@@ -14,6 +14,8 @@ rfm_status launch_filter(const HostPlan &P, void *ws, double tol, cudaStream_t s
 rfm_status launch_lsqr(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, const double *y0, double *y_out,
                        double *a_out, rfm_lsqr_report *rep, cudaStream_t st);
 rfm_status launch_coefficients(const HostPlan &P, void *ws, const double *y, double *a_out, cudaStream_t st);
+rfm_status launch_residual(const HostPlan &P, void *ws, const double *a, double *r_out, double *rnorm,
+                           cudaStream_t st);
 void set_force_global_filter(int on);
 void set_autotune(int on);
 void set_qr_double_float(int on);
@@ -218,6 +220,21 @@ rfm_status rfm_coefficients(const rfm_problem *probs, int n_inst, const rfm_conf
         return RFM_EINVAL;
     }
     return launch_coefficients(P.p, d_ws, d_y, d_a, (cudaStream_t)stream);
+    RFM_GUARD_END
+}
+
+rfm_status rfm_residual(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const double *d_a, double *d_r,
+                        double *d_rnorm, void *d_ws, size_t ws_bytes, void *stream) {
+    RFM_GUARD_BEGIN
+    Plan P(probs, n_inst, cfg);
+    if (!P.ok) return P.rc;
+    rfm_status rc = check_ws(P.p.L, d_ws, ws_bytes);
+    if (rc != RFM_OK) return rc;
+    if (!d_a) {
+        set_error("rfm_residual: d_a is NULL");
+        return RFM_EINVAL;
+    }
+    return launch_residual(P.p, d_ws, d_a, d_r, d_rnorm, (cudaStream_t)stream);
     RFM_GUARD_END
 }
 

@@ -1854,6 +1854,12 @@ static rfm_status residual64(const HostPlan &P, void *ws, const double *a, doubl
     return RFM_OK;
 }
 
+rfm_status launch_residual(const HostPlan &P, void *ws, const double *a, double *r_out, double *rnorm,
+                           cudaStream_t st) {
+    double *r = r_out ? r_out : ws_ptr<double>(ws, P.L.off_rres);
+    return residual64(P, ws, a, r, rnorm, 1, st);
+}
+
 rfm_status launch_coefficients(const HostPlan &P, void *ws, const double *y, double *a_out, cudaStream_t st) {
     const Layout &L = P.L;
     if (L.n_blocks == 0) return RFM_OK;
