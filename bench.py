@@ -453,7 +453,7 @@ def run_gpu(args):
         prm = synth.feature_params(p)
         out["cpu_baseline"] = cpu_baseline(p, prm, head["iterations"]["fp64"], stride=args.cpu_stride)
         out["cpu_baseline_all_cores"] = guarded(cpu_baseline_pool, p, prm, head["iterations"]["fp64"],
-                                                args.cpu_stride_pool)
+                                                args.cpu_stride_pool, out["cpu_baseline"])
     if rank == 0 and world == 1 and args.case != "p2d" and not args.no_p2d:
         sec = guarded(lambda: time_to_error(synth.poisson2d(), args, dev, 1, 0, headline=False)[0])
         out["poisson2d"] = sec
@@ -828,12 +828,12 @@ def cpu_baseline(p, prm, iters, stride=100):
             "parts_s": parts}
 
 
-def cpu_baseline_pool(p, prm, iters, stride=25):
+def cpu_baseline_pool(p, prm, iters, stride=25, single=None):
     """The oracle's assembly and QR of every stride-th block on all of this
     host's cores (a process pool over blocks, started with spawn; core count
     from sched_getaffinity), scaled to the workload; the LSQR and evaluation
     parts are those of the single-threaded oracle (its LSQR products and
-    evaluation are sequential code), measured here on the same sample."""
+    evaluation are sequential code), taken from the single-core leg."""
     import multiprocessing as mp
     cores = len(os.sched_getaffinity(0))
     blocks = sample_blocks(p, stride)
@@ -843,7 +843,7 @@ def cpu_baseline_pool(p, prm, iters, stride=25):
         t0 = time.perf_counter()
         pool.map(_oracle_block, [(p, prm, j) for j in blocks], chunksize=1)
         t_blocks = time.perf_counter() - t0
-    parts, _ = _oracle_sample(p, prm, blocks[:: max(1, len(blocks) // 4)], iters, 10)
+    parts = single["parts_s"] if single else _oracle_sample(p, prm, blocks[:: max(1, len(blocks) // 4)], iters, 10)[0]
     scale = p.J / len(blocks)
     total = t_blocks * scale + parts["lsqr"] + parts["eval"]
     return {"value": total * 1e3, "unit": "ms", "cores": cores, "kind": "oracle", "extrapolated": True,
@@ -904,7 +904,7 @@ def main():
                          "cycles through the same sample, one block per step")
     ap.add_argument("--cpu-stride-pool", type=int, default=25,
                     help="block sample of the all-cores oracle leg")
-    ap.add_argument("--ref-iters", type=int, default=100,
+    ap.add_argument("--ref-iters", type=int, default=8300,
                     help="LSQR iteration count the reference arm extrapolates to (the FP64 path's calibrated count "
                          "on the headline workload)")
     ap.add_argument("--cal-iters", type=int, default=CAL_ITERS, help="calibration budget (LSQR iterations)")
