@@ -41,7 +41,8 @@ class Problem(C.Structure):
     _fields_ = [("dim", C.c_int32), ("pde", C.c_int32), ("family", C.c_int32), ("n_modes", C.c_int32),
                 ("S", C.c_int32 * 3), ("n", C.c_int32 * 3), ("K", C.c_int32), ("pad0", C.c_int32),
                 ("delta", C.c_double), ("kappa", C.c_double), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
-                ("lam", C.c_double * 2), ("fam", C.c_double * 64)]
+                ("lam", C.c_double * 2), ("fam", C.c_double * 64), ("depth", C.c_int32), ("act", C.c_int32),
+                ("hard_bc", C.c_double)]
 
 
 class System(C.Structure):
@@ -65,6 +66,7 @@ def lib():
             "orc_subdomain": (None, [P, i64, vp, vp]), "orc_window_hat": (dbl, [P, i64, vp, vp, vp]),
             "orc_window": (dbl, [P, i64, vp, vp, vp]), "orc_exact": (dbl, [P, vp]),
             "orc_source": (dbl, [P, vp]), "orc_bdata": (dbl, [P, vp]),
+            "orc_bdata_set": (dbl, [P, vp, C.c_int]), "orc_params_per_subdomain": (i64, [P]),
             "orc_block_rows": (i64, [P, i64, vp]), "orc_assemble_block": (None, [P, vp, i64, vp, i64, vp]),
             "orc_rhs": (None, [P, vp]), "orc_assemble_dense": (None, [P, vp, vp]),
             "orc_qrcp": (C.c_int, [C.c_int, C.c_int, vp, C.c_int, dbl, vp, vp, vp]),
@@ -110,6 +112,11 @@ def problem_struct(p) -> Problem:
     fv = p.fam_vector()
     for i in range(64):
         s.fam[i] = fv[i]
+    s.depth = int(getattr(p, "depth", 1))
+    s.act = int(getattr(p, "act", 0))
+    s.hard_bc = float(getattr(p, "hard_bc", 0.0))
+    if s.depth > 1 and p.K > 128:
+        raise ValueError("the oracle's deep networks are at most 128 wide")
     return s
 
 

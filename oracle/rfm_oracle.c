@@ -35,9 +35,14 @@
 #define M_PI 3.14159265358979323846
 #endif
 
-enum { PDE_POISSON = 0, PDE_HEAT = 1 };
-enum { FAM_SINPROD = 0, FAM_HEAT_SINPROD = 1, FAM_PARAM5 = 2 };
+enum { PDE_POISSON = 0, PDE_HEAT = 1, PDE_OSC = 2 };
+enum { FAM_SINPROD = 0, FAM_HEAT_SINPROD = 1, FAM_PARAM5 = 2, FAM_OSC = 3 };
+enum { ACT_TANH = 0, ACT_SIGMOID = 1, ACT_SIN = 2 };
 
+/* One problem instance.  depth is h of Eq. (2) (0 is read as 1), act the
+ * activation Xi, hard_bc > 0 the factor c of the hard-constraint ansatz of the
+ * Laplace problem (Sec. 4.1).  The damped oscillator (PDE_OSC, Sec. 4.1) takes
+ * its coefficients m, mu, k from fam[0], fam[1], fam[2]. */
 typedef struct {
     int32_t dim, pde, family, n_modes;
     int32_t S[3], n[3];
@@ -46,6 +51,8 @@ typedef struct {
     double lo[3], hi[3];
     double lam[2];
     double fam[64];
+    int32_t depth, act;
+    double hard_bc;
 } orc_problem;
 
 /* ------------------------------------------------------------------------ */
@@ -62,10 +69,17 @@ static int64_t n_interior(const orc_problem *P) {
  * heat equation the last coordinate is time and only its lo face (the initial
  * condition) carries data. */
 static int n_faces(const orc_problem *P) {
+    if (P->hard_bc > 0.0) return 0;   /* the ansatz satisfies the boundary condition: no boundary rows */
+    if (P->pde == PDE_OSC) return 2;  /* u(t0) and du/dt(t0): two rows at the initial time */
     return P->pde == PDE_HEAT ? 2 * (P->dim - 1) + 1 : 2 * P->dim;
 }
 
 static void face_info(const orc_problem *P, int f, int *normal, int *side) {
+    if (P->pde == PDE_OSC) {
+        *normal = 0;
+        *side = 0;
+        return;
+    }
     *normal = f / 2;
     *side = f % 2;
 }
@@ -84,6 +98,7 @@ static int64_t face_points(const orc_problem *P, int f) {
 static int face_set(const orc_problem *P, int f) {
     int nd, sd;
     face_info(P, f, &nd, &sd);
+    if (P->pde == PDE_OSC) return f;   /* 0: value, 1: first derivative */
     if (P->pde == PDE_HEAT && nd == P->dim - 1) return 1;
     return 0;
 }
@@ -253,7 +268,23 @@ double orc_exact(const orc_problem *P, const double *x) {
         }
         return u;
     }
+    if (P->family == FAM_OSC) {
+        /* under-damped oscillator m u'' + mu u' + k u = 0 with u(t0) = 1,
+         * u'(t0) = 0: u = e^{-d s}(cos(w s) + (d/w) sin(w s)), s = t - t0,
+         * d = mu/(2m), w = sqrt(k/m - d^2) (Sec. 4.1) */
+        double m = P->fam[0], mu = P->fam[1], k = P->fam[2];
+        double d = mu / (2.0 * m), w = sqrt(k / m - d * d), t = x[0] - P->lo[0];
+        return exp(-d * t) * (cos(w * t) + d / w * sin(w * t));
+    }
     return NAN;
+}
+
+/* du/dt of the oscillator's exact solution (the data of its derivative row) */
+static double osc_exact_dt(const orc_problem *P, const double *x) {
+    double m = P->fam[0], mu = P->fam[1], k = P->fam[2];
+    double d = mu / (2.0 * m), w = sqrt(k / m - d * d), t = x[0] - P->lo[0];
+    /* d/dt of e^{-dt}(cos wt + (d/w) sin wt) = -(d^2/w + w) e^{-dt} sin wt */
+    return -(d * d / w + w) * exp(-d * t) * sin(w * t);
 }
 
 /* right-hand side f of the PDE at an interior point */
@@ -272,7 +303,7 @@ double orc_source(const orc_problem *P, const double *x) {
         }
         return f;
     }
-    if (P->family == FAM_HEAT_SINPROD) return 0.0; /* u_t - kappa Lap u = 0 */
+    if (P->family == FAM_HEAT_SINPROD || P->family == FAM_OSC) return 0.0; /* homogeneous equations */
     if (P->family == FAM_PARAM5) {
         const double *p = P->fam;
         return sin(p[0] * M_PI * x[0]) * sin(p[1] * M_PI * x[1])
@@ -281,11 +312,15 @@ double orc_source(const orc_problem *P, const double *x) {
     return NAN;
 }
 
-/* boundary / initial data g at a boundary point */
-double orc_bdata(const orc_problem *P, const double *x) {
+/* boundary / initial data g_l of boundary set `kind` at a boundary point */
+static double bdata_set(const orc_problem *P, const double *x, int kind) {
     if (P->family == FAM_PARAM5) return 0.0;
+    if (P->pde == PDE_OSC && kind == 1) return osc_exact_dt(P, x);
     return orc_exact(P, x);
 }
+
+double orc_bdata(const orc_problem *P, const double *x) { return bdata_set(P, x, 0); }
+double orc_bdata_set(const orc_problem *P, const double *x, int kind) { return bdata_set(P, x, kind); }
 
 /* ------------------------------------------------------------------------ */
 /* assembly (Sec. 2.1, entry formulas after Eq. (5); Eq. (6))                 */
@@ -314,31 +349,185 @@ int64_t orc_block_rows(const orc_problem *P, int64_t j, int64_t *grow) {
     return c;
 }
 
-/* Feature phi_jk = tanh(sum_i w_i (x_i - mu_i)/sig_i + b): the one-hidden-layer
- * network of Eq. (2) with inputs normalised to [-1, 1] over the subdomain
- * (Sec. 4.2) and a bias.  Gives value, gradient and pure second partials. */
-static void feature(const orc_problem *P, const double *prm, const double *mu, const double *sig,
-                    const double *x, double *phi, double *dphi, double *d2phi) {
-    double z = prm[P->dim];
-    for (int i = 0; i < P->dim; ++i) z += prm[i] * (x[i] - mu[i]) / sig[i];
-    double t = tanh(z);
-    *phi = t;
-    for (int i = 0; i < P->dim; ++i) {
-        double a = prm[i] / sig[i];
-        dphi[i] = a * (1.0 - t * t);
-        d2phi[i] = a * a * (-2.0 * t * (1.0 - t * t));
+/* ---- the subdomain networks of Eq. (2) ---------------------------------- */
+
+static int depth_of(const orc_problem *P) { return P->depth > 1 ? P->depth : 1; }
+
+/* Inputs of the output layer: d for a one-layer network (the normalised
+ * coordinates), else K (the last hidden layer's width; hidden layers are K
+ * wide). */
+static int n_last(const orc_problem *P) { return depth_of(P) > 1 ? P->K : P->dim; }
+
+/* Parameters of one subdomain network, laid out as: the output layer, one row
+ * (w_1 .. w_nlast, b) per feature k; then hidden layers l = 1 .. h-1, each its
+ * weights W^(l) (K x n_{l-1}, row-major) followed by its biases b^(l) (K),
+ * with n_0 = dim.  For h = 1 this is (k, [w_1..w_d, b]). */
+int64_t orc_params_per_subdomain(const orc_problem *P) {
+    int64_t c = (int64_t)P->K * (n_last(P) + 1);
+    int nin = P->dim;
+    for (int l = 1; l < depth_of(P); ++l) {
+        c += (int64_t)P->K * (nin + 1);
+        nin = P->K;
+    }
+    return c;
+}
+
+/* Activation Xi and its first two derivatives. */
+static void activation(const orc_problem *P, double s, double *f, double *f1, double *f2) {
+    if (P->act == ACT_SIGMOID) {
+        double g = 1.0 / (1.0 + exp(-s));
+        *f = g;
+        *f1 = g * (1.0 - g);
+        *f2 = g * (1.0 - g) * (1.0 - 2.0 * g);
+    } else if (P->act == ACT_SIN) {
+        *f = sin(s);
+        *f1 = cos(s);
+        *f2 = -sin(s);
+    } else {
+        double t = tanh(s);
+        *f = t;
+        *f1 = 1.0 - t * t;
+        *f2 = -2.0 * t * (1.0 - t * t);
     }
 }
 
-/* One entry of M: interior rows carry N[w_j phi_jk](x)/sqrt(N_I); boundary
- * rows carry sqrt(lambda_l/N_B^(l)) B_l[w_j phi_jk](x) with B_l the trace. */
+#define ORC_MAXH 128   /* widest layer input the oracle handles */
+
+/* Input of the output layer of subdomain j's network at x, with its partial
+ * derivatives dz[i][m] = d z_m / d x_i and pure second partials d2z[i][m]
+ * (forward propagation of value, gradient and second partials through the
+ * hidden layers of Eq. (2); the network input is (x - mu)/sig, the subdomain
+ * normalisation of Sec. 4.2).  Returns the input width. */
+static int last_hidden(const orc_problem *P, const double *prm_j, const double *mu, const double *sig,
+                       const double *x, double *z, double dz[3][ORC_MAXH], double d2z[3][ORC_MAXH]) {
+    int nin = P->dim;
+    for (int m = 0; m < nin; ++m) {
+        z[m] = (x[m] - mu[m]) / sig[m];
+        for (int i = 0; i < 3; ++i) {
+            dz[i][m] = (i == m) ? 1.0 / sig[m] : 0.0;
+            d2z[i][m] = 0.0;
+        }
+    }
+    const double *q = prm_j + (int64_t)P->K * (n_last(P) + 1);
+    for (int l = 1; l < depth_of(P); ++l) {
+        double nz[ORC_MAXH], ndz[3][ORC_MAXH], nd2z[3][ORC_MAXH];
+        const double *W = q, *b = q + (int64_t)P->K * nin;
+        for (int u = 0; u < P->K; ++u) {
+            double p = b[u], dp[3] = {0, 0, 0}, d2p[3] = {0, 0, 0};
+            for (int m = 0; m < nin; ++m) {
+                double wum = W[(int64_t)u * nin + m];
+                p += wum * z[m];
+                for (int i = 0; i < P->dim; ++i) {
+                    dp[i] += wum * dz[i][m];
+                    d2p[i] += wum * d2z[i][m];
+                }
+            }
+            double f, f1, f2;
+            activation(P, p, &f, &f1, &f2);
+            nz[u] = f;
+            for (int i = 0; i < 3; ++i) {
+                ndz[i][u] = i < P->dim ? f1 * dp[i] : 0.0;
+                nd2z[i][u] = i < P->dim ? f2 * dp[i] * dp[i] + f1 * d2p[i] : 0.0;
+            }
+        }
+        q += (int64_t)P->K * (nin + 1);
+        nin = P->K;
+        for (int u = 0; u < nin; ++u) {
+            z[u] = nz[u];
+            for (int i = 0; i < 3; ++i) {
+                dz[i][u] = ndz[i][u];
+                d2z[i][u] = nd2z[i][u];
+            }
+        }
+    }
+    return nin;
+}
+
+/* Feature phi_jk = Xi(w_k . z + b_k) on the output layer's input z (for a
+ * one-layer network z = (x - mu)/sig, the normalised coordinates of Sec. 4.2,
+ * with a bias), with gradient and pure second partials by the chain rule. */
+static void feature_from(const orc_problem *P, const double *prm_k, int nin, const double *z,
+                         double dz[3][ORC_MAXH], double d2z[3][ORC_MAXH], double *phi, double *dphi,
+                         double *d2phi) {
+    double s = prm_k[nin], ds[3] = {0, 0, 0}, d2s[3] = {0, 0, 0};
+    for (int m = 0; m < nin; ++m) {
+        s += prm_k[m] * z[m];
+        for (int i = 0; i < P->dim; ++i) {
+            ds[i] += prm_k[m] * dz[i][m];
+            d2s[i] += prm_k[m] * d2z[i][m];
+        }
+    }
+    double f, f1, f2;
+    activation(P, s, &f, &f1, &f2);
+    *phi = f;
+    for (int i = 0; i < 3; ++i) {
+        dphi[i] = i < P->dim ? f1 * ds[i] : 0.0;
+        d2phi[i] = i < P->dim ? f2 * ds[i] * ds[i] + f1 * d2s[i] : 0.0;
+    }
+}
+
+/* The hard-constraint factor of the Laplace ansatz (Sec. 4.1),
+ * g(x) = prod_i tanh(c (x_i - a_i)) tanh(c (b_i - x_i)), with gradient and pure
+ * second partials; g = 1 when hard_bc is 0. */
+static double hard_factor(const orc_problem *P, const double *x, double *dg, double *d2g) {
+    double gi[3], g1[3], g2[3];
+    for (int i = 0; i < 3; ++i) { gi[i] = 1.0; g1[i] = 0.0; g2[i] = 0.0; }
+    if (P->hard_bc > 0.0) {
+        double c = P->hard_bc;
+        for (int i = 0; i < P->dim; ++i) {
+            double A = tanh(c * (x[i] - P->lo[i])), B = tanh(c * (P->hi[i] - x[i]));
+            double A1 = c * (1.0 - A * A), B1 = -c * (1.0 - B * B);
+            double A2 = -2.0 * c * c * A * (1.0 - A * A), B2 = -2.0 * c * c * B * (1.0 - B * B);
+            gi[i] = A * B;
+            g1[i] = A1 * B + A * B1;
+            g2[i] = A2 * B + 2.0 * A1 * B1 + A * B2;
+        }
+    }
+    double g = 1.0;
+    for (int i = 0; i < P->dim; ++i) g *= gi[i];
+    for (int i = 0; i < 3; ++i) {
+        double o = 1.0;
+        for (int k = 0; k < P->dim; ++k)
+            if (k != i) o *= gi[k];
+        dg[i] = i < P->dim ? g1[i] * o : 0.0;
+        d2g[i] = i < P->dim ? g2[i] * o : 0.0;
+    }
+    return g;
+}
+
+/* The function multiplying each feature of subdomain j: the window w_j, times
+ * the hard-constraint factor g when the ansatz has one (product rule). */
+static double window_ansatz(const orc_problem *P, int64_t j, const double *x, double *dw, double *d2w) {
+    double wd[3] = {0, 0, 0}, wd2[3] = {0, 0, 0}, gd[3], gd2[3];
+    double w = orc_window(P, j, x, wd, wd2);
+    double g = hard_factor(P, x, gd, gd2);
+    for (int i = 0; i < 3; ++i) {
+        dw[i] = gd[i] * w + g * wd[i];
+        d2w[i] = gd2[i] * w + 2.0 * gd[i] * wd[i] + g * wd2[i];
+    }
+    return g * w;
+}
+
+/* One entry of M for the function v = w phi (w the window, times g with the
+ * hard constraint): interior rows carry N[v](x)/sqrt(N_I); boundary rows carry
+ * sqrt(lambda_l/N_B^(l)) B_l[v](x), with B_l the trace, or for the
+ * oscillator's second initial condition the first derivative. */
 static double entry(const orc_problem *P, const double *x, int kind, double w, const double *dw,
                     const double *d2w, double phi, const double *dphi, const double *d2phi) {
     if (kind >= 0) {
         double NB = (double)orc_num_set(P, kind);
-        return sqrt(P->lam[kind] / NB) * w * phi;
+        double b = w * phi;
+        if (P->pde == PDE_OSC && kind == 1) b = dw[0] * phi + w * dphi[0];
+        return sqrt(P->lam[kind] / NB) * b;
     }
     double NI = (double)n_interior(P);
+    if (P->pde == PDE_OSC) {
+        /* m v'' + mu v' + k v */
+        double v0 = w * phi;
+        double v1 = dw[0] * phi + w * dphi[0];
+        double v2 = d2w[0] * phi + 2.0 * dw[0] * dphi[0] + w * d2phi[0];
+        return (P->fam[0] * v2 + P->fam[1] * v1 + P->fam[2] * v0) / sqrt(NI);
+    }
     double lap = 0.0;
     int nsp = P->pde == PDE_HEAT ? P->dim - 1 : P->dim;
     for (int i = 0; i < nsp; ++i)
@@ -355,20 +544,25 @@ static double entry(const orc_problem *P, const double *x, int kind, double w, c
 }
 
 /* Block M_j = M restricted to I_j x K_j, column-major m x K with ld = m.
- * params holds (w_1..w_d, b) per feature, (J, K, dim+1) row-major. */
+ * params holds orc_params_per_subdomain doubles per subdomain, subdomains in
+ * order (for one-layer networks (J, K, dim+1) row-major). */
 void orc_assemble_block(const orc_problem *P, const double *params, int64_t j, const int64_t *grow,
                         int64_t m, double *Mj) {
     double mu[3], sig[3];
     orc_subdomain(P, j, mu, sig);
+    const int64_t np = orc_params_per_subdomain(P);
+    const double *pj = params + j * np;
+    const int nl = n_last(P);
     for (int64_t lr = 0; lr < m; ++lr) {
         double x[3], dw[3], d2w[3];
         int kind;
         orc_row_point(P, grow[lr], x, &kind);
-        double w = orc_window(P, j, x, dw, d2w);
+        double w = window_ansatz(P, j, x, dw, d2w);
+        double z[ORC_MAXH], dz[3][ORC_MAXH], d2z[3][ORC_MAXH];
+        int nin = last_hidden(P, pj, mu, sig, x, z, dz, d2z);
         for (int k = 0; k < P->K; ++k) {
-            const double *prm = params + ((size_t)j * P->K + k) * (P->dim + 1);
             double phi, dphi[3], d2phi[3];
-            feature(P, prm, mu, sig, x, &phi, dphi, d2phi);
+            feature_from(P, pj + (int64_t)k * (nl + 1), nin, z, dz, d2z, &phi, dphi, d2phi);
             Mj[(size_t)k * m + lr] = entry(P, x, kind, w, dw, d2w, phi, dphi, d2phi);
         }
     }
@@ -384,7 +578,7 @@ void orc_rhs(const orc_problem *P, double *h) {
         if (kind < 0)
             h[r] = orc_source(P, x) / sqrt((double)NI);
         else
-            h[r] = sqrt(P->lam[kind] / (double)orc_num_set(P, kind)) * orc_bdata(P, x);
+            h[r] = sqrt(P->lam[kind] / (double)orc_num_set(P, kind)) * bdata_set(P, x, kind);
     }
 }
 
@@ -393,6 +587,8 @@ void orc_rhs(const orc_problem *P, double *h) {
 void orc_assemble_dense(const orc_problem *P, const double *params, double *M) {
     int64_t N = n_interior(P) + orc_num_boundary(P);
     int64_t J = orc_num_subdomains(P);
+    const int64_t np = orc_params_per_subdomain(P);
+    const int nl = n_last(P);
     for (int64_t j = 0; j < J; ++j) {
         double mu[3], sig[3];
         orc_subdomain(P, j, mu, sig);
@@ -400,11 +596,12 @@ void orc_assemble_dense(const orc_problem *P, const double *params, double *M) {
             double x[3], dw[3], d2w[3];
             int kind;
             orc_row_point(P, r, x, &kind);
-            double w = orc_window(P, j, x, dw, d2w);
+            double w = window_ansatz(P, j, x, dw, d2w);
+            double z[ORC_MAXH], dz[3][ORC_MAXH], d2z[3][ORC_MAXH];
+            int nin = last_hidden(P, params + j * np, mu, sig, x, z, dz, d2z);
             for (int k = 0; k < P->K; ++k) {
-                const double *prm = params + ((size_t)j * P->K + k) * (P->dim + 1);
                 double phi, dphi[3], d2phi[3];
-                feature(P, prm, mu, sig, x, &phi, dphi, d2phi);
+                feature_from(P, params + j * np + (int64_t)k * (nl + 1), nin, z, dz, d2z, &phi, dphi, d2phi);
                 M[(size_t)(j * P->K + k) * N + r] = entry(P, x, kind, w, dw, d2w, phi, dphi, d2phi);
             }
         }
@@ -701,13 +898,16 @@ void orc_coefficients(int64_t J, int K, const int32_t *r, const int32_t *perm, c
 /* evaluation (Eq. (1)) and errors (Sec. 4.2)                                */
 /* ------------------------------------------------------------------------ */
 
-/* u_hat(x) = sum_j w_j(x) sum_k a_jk phi_jk(x) at npts points X (npts x dim).
- * The normalising sum W(x) = sum_l hat_w_l(x) is the same for every j at a
- * point, so it is formed once per point (same terms, same order as in
- * orc_window) and w_j = hat_w_j / W. */
+/* u_hat(x) = g(x) sum_j w_j(x) sum_k a_jk phi_jk(x) at npts points X
+ * (npts x dim), g the hard-constraint factor (1 without one).  The
+ * normalising sum W(x) = sum_l hat_w_l(x) is the same for every j at a point,
+ * so it is formed once per point (same terms, same order as in orc_window)
+ * and w_j = hat_w_j / W. */
 void orc_eval(const orc_problem *P, const double *params, const double *a, int64_t npts,
               const double *X, double *u) {
     int64_t J = orc_num_subdomains(P);
+    const int64_t np = orc_params_per_subdomain(P);
+    const int nl = n_last(P);
     for (int64_t p = 0; p < npts; ++p) {
         double x[3] = {0, 0, 0};
         for (int i = 0; i < P->dim; ++i) x[i] = X[p * P->dim + i];
@@ -724,16 +924,18 @@ void orc_eval(const orc_problem *P, const double *params, const double *a, int64
             double w = h / W;
             double mu[3], sig[3];
             orc_subdomain(P, j, mu, sig);
+            double z[ORC_MAXH], dz[3][ORC_MAXH], d2z[3][ORC_MAXH];
+            int nin = last_hidden(P, params + j * np, mu, sig, x, z, dz, d2z);
             double sj = 0.0;
             for (int k = 0; k < P->K; ++k) {
-                const double *prm = params + ((size_t)j * P->K + k) * (P->dim + 1);
                 double phi, dphi[3], d2phi[3];
-                feature(P, prm, mu, sig, x, &phi, dphi, d2phi);
+                feature_from(P, params + j * np + (int64_t)k * (nl + 1), nin, z, dz, d2z, &phi, dphi, d2phi);
                 sj += a[j * P->K + k] * phi;
             }
             s += w * sj;
         }
-        u[p] = s;
+        double gd[3], gd2[3];
+        u[p] = hard_factor(P, x, gd, gd2) * s;
     }
 }
 
@@ -755,13 +957,16 @@ void orc_feature_values(const orc_problem *P, const double *params, int64_t j, i
                         double *Phi) {
     double mu[3], sig[3];
     orc_subdomain(P, j, mu, sig);
+    const int64_t np = orc_params_per_subdomain(P);
+    const int nl = n_last(P);
     for (int64_t p = 0; p < npts; ++p) {
         double x[3] = {0, 0, 0};
         for (int i = 0; i < P->dim; ++i) x[i] = X[p * P->dim + i];
+        double z[ORC_MAXH], dz[3][ORC_MAXH], d2z[3][ORC_MAXH];
+        int nin = last_hidden(P, params + j * np, mu, sig, x, z, dz, d2z);
         for (int k = 0; k < P->K; ++k) {
-            const double *prm = params + ((size_t)j * P->K + k) * (P->dim + 1);
             double phi, dphi[3], d2phi[3];
-            feature(P, prm, mu, sig, x, &phi, dphi, d2phi);
+            feature_from(P, params + j * np + (int64_t)k * (nl + 1), nin, z, dz, d2z, &phi, dphi, d2phi);
             Phi[(size_t)k * npts + p] = phi;
         }
     }

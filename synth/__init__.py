@@ -26,11 +26,16 @@ _MASK = (1 << 64) - 1
 PDE_POISSON = 0   # -Laplace(u) = f, Dirichlet data on every face
 PDE_HEAT = 1      # u_t - kappa * Laplace_x(u) = f, last coordinate is time;
                   # Dirichlet data on spatial faces, initial data on t = lo
+PDE_OSC = 2       # m u'' + mu u' + k u = f in 1D (time), u and u' given at t = lo
+
+# activations of the subdomain networks
+ACT_TANH, ACT_SIGMOID, ACT_SIN = 0, 1, 2
 
 # manufactured-solution families
 FAM_SINPROD = 0       # u = sum_m c_m prod_i sin(k_mi pi x_i)         (Poisson)
 FAM_HEAT_SINPROD = 1  # u = sum_m c_m exp(-kappa pi^2 |k_m|^2 t) prod_i sin(k_mi pi x_i)  (heat)
 FAM_PARAM5 = 2        # f = sin(a pi x) sin(b pi y) + c sin(d pi x + e pi y), g = 0, no closed form
+FAM_OSC = 3           # damped oscillator with u(lo) = 1, u'(lo) = 0; fparams = (m, mu, k)
 
 MAX_MODES = 8
 
@@ -79,6 +84,23 @@ class Problem:
     seed: int = 0
     n_test: Sequence[int] = ()   # test grid (cell-centred) per dimension
     name: str = ""
+    depth: int = 1          # h of Eq. (2): h - 1 hidden layers of K units before the features
+    act: int = ACT_TANH     # activation of every layer
+    hard_bc: float = 0.0    # > 0: the hard-constraint ansatz of the Laplace problem with this factor
+    init: str = "range"     # "range": weights U(-R/2, R/2), biases U(-R, R); "lecun": uniform LeCun
+
+    @property
+    def params_per_subdomain(self) -> int:
+        """Doubles of one subdomain network: the output layer (K rows of
+        w_1..w_n, b, n = dim for h = 1, else K), then each hidden layer's
+        weights (K x n_in, row-major) and biases (K)."""
+        n_last = self.dim if self.depth <= 1 else self.K
+        c = self.K * (n_last + 1)
+        nin = self.dim
+        for _ in range(1, max(1, self.depth)):
+            c += self.K * (nin + 1)
+            nin = self.K
+        return c
 
     @property
     def J(self) -> int:
@@ -108,7 +130,9 @@ class Problem:
 
 
 def feature_params(p: Problem, seed: Optional[int] = None) -> np.ndarray:
-    """Random feature parameters, shape (J, K, dim+1): (w_1..w_d, b) per feature.
+    """Random network parameters: shape (J, K, dim+1), (w_1..w_d, b) per
+    feature, for one-layer networks with the "range" draw; else (J, P) with P
+    = p.params_per_subdomain in the layout described there.
 
     The features act on the input normalised to [-1, 1] over the subdomain
     (x - mu) / sig (sig the half-width).  Workloads state "weights U(-R, R)
@@ -117,12 +141,30 @@ def feature_params(p: Problem, seed: Optional[int] = None) -> np.ndarray:
     biases are U(-R, R).
     Draw order: subdomain j (lexicographic, dimension 0 fastest), then feature k,
     then w_1..w_d, then b; each value is R * (2u - 1) with u from SplitMix64.
+    "lecun": every weight and bias of a layer with n inputs is drawn from
+    U(-sqrt(3/n), sqrt(3/n)) (uniform LeCun initialisation, Sec. 4.2, read as
+    applying to the biases too), in the layout order.
     """
     s = p.seed if seed is None else seed
-    n = p.J * p.K * (p.dim + 1)
-    u = splitmix64_unit(s, n)
-    v = (p.R * (2.0 * u - 1.0)).reshape(p.J, p.K, p.dim + 1)
-    v[:, :, : p.dim] *= 0.5
+    if p.depth <= 1 and p.init == "range":
+        n = p.J * p.K * (p.dim + 1)
+        u = splitmix64_unit(s, n)
+        v = (p.R * (2.0 * u - 1.0)).reshape(p.J, p.K, p.dim + 1)
+        v[:, :, : p.dim] *= 0.5
+        return v
+    P = p.params_per_subdomain
+    u = splitmix64_unit(s, p.J * P).reshape(p.J, P)
+    lim = np.empty(P)
+    n_last = p.dim if p.depth <= 1 else p.K
+    lim[: p.K * (n_last + 1)] = math.sqrt(3.0 / n_last)
+    o, nin = p.K * (n_last + 1), p.dim
+    for _ in range(1, max(1, p.depth)):
+        lim[o: o + p.K * (nin + 1)] = math.sqrt(3.0 / nin)
+        o += p.K * (nin + 1)
+        nin = p.K
+    v = lim * (2.0 * u - 1.0)
+    if p.depth <= 1:
+        return v.reshape(p.J, p.K, p.dim + 1)
     return v
 
 
@@ -160,6 +202,33 @@ def heat3d(S=10, K=500, n=100, delta=1.2, R=5.0, kappa=0.01, k=6.0, seed=0, n_te
     return Problem(dim=3, pde=PDE_HEAT, S=[S, S, S], delta=delta, K=K, n=[n, n, n],
                    family=FAM_HEAT_SINPROD, coef=[1.0], waves=[[k, k]], kappa=kappa,
                    R=R, seed=seed, n_test=[n_test] * 3, name=f"heat3d_S{S}_K{K}_n{n}")
+
+
+def oscillator(S=20, K=8, delta=2.9, omega0=60.0, mu=4.0, m=1.0, seed=0, act=ACT_TANH, depth=1) -> Problem:
+    """The damped harmonic oscillator of Sec. 4.1: m u'' + mu u' + k u = 0 on
+    [0, 1], u(0) = 1, u'(0) = 0, k = m omega0^2 (m = 1, mu = 4, omega0 = 60 in
+    the paper's baseline), S subdomains at overlap ratio delta, K features,
+    S ceil(K) interior collocation points (Sec. 4.2), uniform LeCun features,
+    test points 50 S (Sec. 4.3)."""
+    return Problem(dim=1, pde=PDE_OSC, S=[S], delta=delta, K=K, n=[S * K], family=FAM_OSC,
+                   fparams=[m, mu, m * omega0 * omega0], seed=seed, n_test=[50 * S], init="lecun", act=act,
+                   depth=depth, name=f"oscillator_w{omega0:g}_S{S}_K{K}")
+
+
+def laplace_multiscale(n_scales=3, S=16, K=16, delta=2.9, seed=0, act=ACT_TANH, depth=1) -> Problem:
+    """The multi-scale Laplace problem of Sec. 4.1: -Lap u = f on [0,1]^2,
+    u = 0 on the boundary, u = (1/n) sum_i sin(w_i pi x) sin(w_i pi y) with
+    w_i = 2^i (i = 1..n), by the hard-constraint ansatz with factor w_n (no
+    boundary rows); S x S subdomains, overlap ratio delta, K features, S
+    ceil(sqrt K) collocation points per dimension, 6 S test points per
+    dimension (Sec. 4.4)."""
+    import math as _m
+    n = S * int(_m.ceil(K ** 0.5 - 1e-12))
+    coef = [1.0 / n_scales] * n_scales
+    waves = [[2.0 ** i, 2.0 ** i] for i in range(1, n_scales + 1)]
+    return Problem(dim=2, pde=PDE_POISSON, S=[S, S], delta=delta, K=K, n=[n, n], family=FAM_SINPROD, coef=coef,
+                   waves=waves, seed=seed, n_test=[6 * S, 6 * S], init="lecun", act=act, depth=depth,
+                   hard_bc=2.0 ** n_scales, name=f"laplace_n{n_scales}_S{S}_K{K}")
 
 
 def batched_instance(i: int, S_range=(8, 24), K_range=(100, 400), p_range=(40, 200),
