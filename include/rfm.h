@@ -61,8 +61,15 @@ typedef enum {
 /* PDE kinds: RFM_PDE_POISSON is -Laplace(u) = f with Dirichlet data on every
  * face; RFM_PDE_HEAT is u_t - kappa Laplace_x(u) = f where the last coordinate
  * is time, with Dirichlet data on the spatial faces (boundary set 0) and
- * initial data on t = lo (boundary set 1). */
-enum { RFM_PDE_POISSON = 0, RFM_PDE_HEAT = 1 };
+ * initial data on t = lo (boundary set 1); RFM_PDE_OSC is the damped
+ * oscillator of Sec. 4.1, m u'' + mu u' + k u = f in one dimension (time),
+ * with (m, mu, k) = fam[0..2], the value u(lo) (boundary set 0) and the first
+ * derivative u'(lo) (boundary set 1) given at the initial time, one row each. */
+enum { RFM_PDE_POISSON = 0, RFM_PDE_HEAT = 1, RFM_PDE_OSC = 2 };
+
+/* Activation Xi of every layer of the subdomain networks (Eq. (2); Tables 1
+ * and 2 compare tanh with sigmoid and sine). */
+enum { RFM_ACT_TANH = 0, RFM_ACT_SIGMOID = 1, RFM_ACT_SIN = 2 };
 
 /* Manufactured data families (fam[] layout):
  *  RFM_FAM_SINPROD       u = sum_m fam[4m] prod_i sin(fam[4m+1+i] pi x_i);
@@ -70,8 +77,12 @@ enum { RFM_PDE_POISSON = 0, RFM_PDE_HEAT = 1 };
  *  RFM_FAM_HEAT_SINPROD  u = sum_m fam[4m] exp(-kappa pi^2 |k_m|^2 t)
  *                        prod_{spatial i} sin(fam[4m+1+i] pi x_i); f = 0, g = u.
  *  RFM_FAM_PARAM5        f = sin(a pi x) sin(b pi y) + c sin(d pi x + e pi y),
- *                        g = 0 with (a,b,c,d,e) = fam[0..4]; no closed form. */
-enum { RFM_FAM_SINPROD = 0, RFM_FAM_HEAT_SINPROD = 1, RFM_FAM_PARAM5 = 2 };
+ *                        g = 0 with (a,b,c,d,e) = fam[0..4]; no closed form.
+ *  RFM_FAM_OSC           the under-damped oscillator (RFM_PDE_OSC) with
+ *                        u(lo) = 1, u'(lo) = 0, f = 0: u = e^{-d s} (cos(w s)
+ *                        + (d/w) sin(w s)), s = t - lo, d = mu/(2m),
+ *                        w = sqrt(k/m - d^2). */
+enum { RFM_FAM_SINPROD = 0, RFM_FAM_HEAT_SINPROD = 1, RFM_FAM_PARAM5 = 2, RFM_FAM_OSC = 3 };
 
 /* One problem instance (Sec. 2.1 and the common settings of Sec. 4.2).
  *  dim            1..3; the box is prod_i [lo[i], hi[i]].
@@ -86,7 +97,20 @@ enum { RFM_FAM_SINPROD = 0, RFM_FAM_HEAT_SINPROD = 1, RFM_FAM_PARAM5 = 2 };
  *                 other dimensions.  Row order: interior (dimension 0
  *                 fastest), then faces (dim 0 lo, dim 0 hi, dim 1 lo, ...).
  *  lam[l]         loss weight of boundary set l (Eq. (3)).
- *  family, n_modes, fam[]: the data, see above. */
+ *  family, n_modes, fam[]: the data, see above.
+ *  depth          h of Eq. (2), 1..8 (0 reads as 1): h - 1 hidden layers of
+ *                 K units (K <= 32 when h > 1) before the K features.
+ *  act            RFM_ACT_*, the activation of every layer.
+ *  hard_bc        0, or c > 0: the hard-constraint ansatz of the Laplace
+ *                 problem (Sec. 4.1), u = g(x) u_hat(x) with g = prod_i
+ *                 tanh(c (x_i - lo_i)) tanh(c (hi_i - x_i)); the instance then
+ *                 has no boundary rows (Poisson only).
+ * Network parameters of one subdomain (the d_params layout): the output
+ * layer first, one row (w_1 .. w_n, b) per feature with n = dim for h = 1 and
+ * n = K otherwise, then every hidden layer l = 1 .. h-1 as its weights (K x
+ * n_{l-1}, row-major, n_0 = dim) followed by its biases (K).  A feature is
+ * Xi(w . z + b) with z the normalised coordinates (x - mu)/sig for h = 1, or
+ * the last hidden layer's output. */
 typedef struct rfm_problem {
     int32_t dim, pde, family, n_modes;
     int32_t S[3], n[3];
@@ -95,6 +119,8 @@ typedef struct rfm_problem {
     double lo[3], hi[3];
     double lam[2];
     double fam[64];
+    int32_t depth, act;
+    double hard_bc;
 } rfm_problem;
 
 /* Arithmetic of the assembly. */
@@ -135,18 +161,23 @@ typedef struct rfm_sizes {
 
 /* Host only.  Validates the instances and computes the system's sizes.
  * Errors: RFM_EINVAL for an invalid instance (dim outside 1..3, S < 2, K < 1
- * or > 1024, n < 1, delta <= 0, a subdomain with no collocation point, or a
- * block taller than 4194304 rows). */
+ * or > 1024, n < 1, delta <= 0, a subdomain with no collocation point, a
+ * block taller than 4194304 rows, depth outside 0..8, depth > 1 with K > 32,
+ * an unknown activation, a negative hard_bc or one on a non-Poisson instance,
+ * or RFM_PDE_OSC other than in one dimension with RFM_FAM_OSC). */
 rfm_status rfm_problem_size(const rfm_problem *probs, int n_inst, const rfm_config *cfg, rfm_sizes *out);
 
 /* Assembly (Sec. 2.1, Eqs. (1)-(6)).  For every block j the dense local
  * matrix M_j = M restricted to I_j x K_j, with I_j = {r : w_j(x_r) != 0}:
  * interior rows N[w_j phi_jk](x)/sqrt(N_I), boundary rows
  * sqrt(lam_l/N_B^(l)) w_j phi_jk(x), and h = [f/sqrt(N_I); sqrt(lam_l/N_B^(l)) g].
- * Features phi_jk = tanh(sum_i w_i (x_i - mu_i)/sig_i + b) with (w, b) read
- * from d_params: per instance J*K*(dim+1) doubles, (j, k, [w_1..w_d, b])
- * row-major, instances concatenated in order.  Windows: the normalised
- * cosine window of Sec. 4.2.  Writes the workspace only. */
+ * Features phi_jk of Eq. (2) (for h = 1, phi_jk = Xi(sum_i w_i (x_i -
+ * mu_i)/sig_i + b)) with the parameters read from d_params: per instance J
+ * subdomain networks in the layout described at rfm_problem (for h = 1:
+ * J*K*(dim+1) doubles, (j, k, [w_1..w_d, b]) row-major), instances
+ * concatenated in order.  Windows: the normalised cosine window of Sec. 4.2,
+ * times the hard-constraint factor g when hard_bc > 0 (the operator then acts
+ * on g w_j phi_jk).  Writes the workspace only. */
 rfm_status rfm_assemble(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const double *d_params,
                         void *d_ws, size_t ws_bytes, void *stream);
 
@@ -310,6 +341,7 @@ rfm_status rfm_fit_size(const rfm_problem *probs, int n_inst, const rfm_config *
  * truncated at tol_fit |R_11| (the same kernels as Algorithm 1), with explicit
  * Q_hat.
  * Needs rfm_assemble and rfm_rrqr_filter on d_ws (any operator but PLAIN).
+ * Instances with one-layer tanh networks only (RFM_EINVAL otherwise).
  * d_fit_ws: 256-byte aligned, rfm_fit_size bytes, owned by the caller. */
 rfm_status rfm_fit_prepare(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const double *d_params,
                            double tol_fit, void *d_ws, size_t ws_bytes, void *d_fit_ws, size_t fit_bytes,

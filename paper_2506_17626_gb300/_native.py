@@ -21,7 +21,8 @@ class RfmProblem(C.Structure):
     _fields_ = [("dim", C.c_int32), ("pde", C.c_int32), ("family", C.c_int32), ("n_modes", C.c_int32),
                 ("S", C.c_int32 * 3), ("n", C.c_int32 * 3), ("K", C.c_int32), ("reserved0", C.c_int32),
                 ("delta", C.c_double), ("kappa", C.c_double), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
-                ("lam", C.c_double * 2), ("fam", C.c_double * 64)]
+                ("lam", C.c_double * 2), ("fam", C.c_double * 64), ("depth", C.c_int32), ("act", C.c_int32),
+                ("hard_bc", C.c_double)]
 
 
 class RfmConfig(C.Structure):
@@ -145,6 +146,9 @@ def problem_struct(p) -> RfmProblem:
     fv = p.fam_vector()
     for i in range(64):
         s.fam[i] = float(fv[i])
+    s.depth = int(getattr(p, "depth", 1))
+    s.act = int(getattr(p, "act", 0))
+    s.hard_bc = float(getattr(p, "hard_bc", 0.0))
     return s
 
 

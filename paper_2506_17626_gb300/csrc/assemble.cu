@@ -70,22 +70,122 @@ __global__ void __launch_bounds__(256) k_assemble(const InstRec *__restrict__ in
         sx[i] = s_s[lane][i];
         isg[i] = (T)(1.0 / B.sig[i]);
     }
-    const double *prm = params + I.prm_off + (int64_t)B.j * B.K * (d + 1);
+    const double *prm = params + I.prm_off + (int64_t)B.j * I.n_prm_sub;
     T *Mb = M + B.moff + lr;
+    if (I.act == RFM_ACT_TANH) {
+        for (int k = wy; k < B.K; k += 8) {
+            const double *pk = prm + (int64_t)k * (d + 1);
+            T z = (T)pk[d];
+            T wv[3], a[3];
+            for (int i = 0; i < 3; ++i) {
+                wv[i] = i < d ? (T)pk[i] : (T)0;
+                z += wv[i] * sx[i];
+                a[i] = wv[i] * isg[i];
+            }
+            T t = tanh_t(z);
+            T q = (T)1 - t * t;
+            T acc = (T)0;
+            for (int i = 0; i < 3; ++i) acc += a[i] * (c1[i] - (T)2 * a[i] * t * c2[i]);
+            Mb[(int64_t)k * B.ldm] = c0 * t + q * acc;
+        }
+        return;
+    }
+    // other activations: phi = Xi(z), dphi/dx_i = Xi'(z) a_i, d2phi/dx_i^2 = Xi''(z) a_i^2
     for (int k = wy; k < B.K; k += 8) {
         const double *pk = prm + (int64_t)k * (d + 1);
         T z = (T)pk[d];
-        T wv[3], a[3];
+        T a[3];
         for (int i = 0; i < 3; ++i) {
-            wv[i] = i < d ? (T)pk[i] : (T)0;
-            z += wv[i] * sx[i];
-            a[i] = wv[i] * isg[i];
+            const T wv = i < d ? (T)pk[i] : (T)0;
+            z += wv * sx[i];
+            a[i] = wv * isg[i];
         }
-        T t = tanh_t(z);
-        T q = (T)1 - t * t;
+        T f, f1, f2;
+        act_eval(I.act, z, &f, &f1, &f2);
         T acc = (T)0;
-        for (int i = 0; i < 3; ++i) acc += a[i] * (c1[i] - (T)2 * a[i] * t * c2[i]);
-        Mb[(int64_t)k * B.ldm] = c0 * t + q * acc;
+        for (int i = 0; i < 3; ++i) acc += a[i] * (c1[i] * f1 + c2[i] * a[i] * f2);
+        Mb[(int64_t)k * B.ldm] = c0 * f + acc;
+    }
+}
+
+// Networks with hidden layers (Eq. (2), depth h > 1, K <= kMaxDeepK): one CTA
+// per 32-row tile as above; warp 0 forms, per row, the row coefficients and
+// the output layer's input z with its partial derivatives (FP64 forward
+// propagation through the hidden layers, net_hidden) into shared memory;
+// then every warp takes features k = warp, warp + 8, ...: s = w_k . z + b_k,
+// ds_i = w_k . dz_i, d2s_i = w_k . d2z_i, and
+//   M[r, k] = c0 Xi(s) + sum_i c1_i Xi'(s) ds_i + c2_i (Xi''(s) ds_i^2 + Xi'(s) d2s_i).
+// FP64 throughout (the assembly precision only at the store).
+template <typename T>
+__global__ void __launch_bounds__(256) k_assemble_deep(const InstRec *__restrict__ insts,
+                                                       const BlkRec *__restrict__ blks,
+                                                       const int32_t *__restrict__ tile_blk,
+                                                       const int32_t *__restrict__ tile_row,
+                                                       const double *__restrict__ params, T *__restrict__ M) {
+    extern __shared__ double s_deep[];   // per row: z, dz (3 x kMaxDeepK), d2z (3 x kMaxDeepK)
+    double(*s_z)[kMaxDeepK] = reinterpret_cast<double(*)[kMaxDeepK]>(s_deep);
+    double(*s_dz)[3 * kMaxDeepK] = reinterpret_cast<double(*)[3 * kMaxDeepK]>(s_deep + 32 * kMaxDeepK);
+    double(*s_d2z)[3 * kMaxDeepK] = reinterpret_cast<double(*)[3 * kMaxDeepK]>(s_deep + 32 * 4 * kMaxDeepK);
+    __shared__ double s_c0[32], s_c1[32][3], s_c2[32][3];
+    __shared__ BlkRec sB;
+    __shared__ InstRec sI;
+    const int tile = blockIdx.x;
+    if (threadIdx.x == 0) {
+        sB = blks[tile_blk[tile]];
+        sI = insts[sB.inst];
+    }
+    __syncthreads();
+    const BlkRec &B = sB;
+    const InstRec &I = sI;
+    const int r0 = tile_row[tile];
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const double *prm = params + I.prm_off + (int64_t)B.j * I.n_prm_sub;
+    if (wy == 0) {
+        const int lr = r0 + lane;
+        double c0 = 0.0, c1[3] = {0, 0, 0}, c2[3] = {0, 0, 0}, x[3] = {0, 0, 0};
+        if (lr < B.m) {
+            int kind, gcov[3];
+            block_row_point(I, B, lr, x, &kind, gcov);
+            double w, dw[3], d2w[3];
+            window_nd(I, B.jd, x, &w, dw, d2w);
+            row_coefficients(I, kind, w, dw, d2w, &c0, c1, c2);
+            double xn[3], isg[3];
+            for (int i = 0; i < 3; ++i) {
+                xn[i] = i < I.dim ? (x[i] - B.mu[i]) / B.sig[i] : 0.0;
+                isg[i] = 1.0 / B.sig[i];
+            }
+            net_hidden(I, prm, xn, isg, s_z[lane], s_dz[lane], s_d2z[lane]);
+        }
+        s_c0[lane] = c0;
+        for (int i = 0; i < 3; ++i) {
+            s_c1[lane][i] = c1[i];
+            s_c2[lane][i] = c2[i];
+        }
+    }
+    __syncthreads();
+    const int lr = r0 + lane;
+    if (lr >= B.m) {
+        if (lr < B.ldm)
+            for (int k = wy; k < B.K; k += 8) M[B.moff + lr + (int64_t)k * B.ldm] = (T)0;
+        return;
+    }
+    const int d = I.dim, nin = I.n_last;
+    T *Mb = M + B.moff + lr;
+    for (int k = wy; k < B.K; k += 8) {
+        const double *pk = prm + (int64_t)k * (nin + 1);
+        double sv = pk[nin], ds[3] = {0, 0, 0}, d2s[3] = {0, 0, 0};
+        for (int m = 0; m < nin; ++m) {
+            sv = fma(pk[m], s_z[lane][m], sv);
+            for (int i = 0; i < d; ++i) {
+                ds[i] = fma(pk[m], s_dz[lane][i * kMaxDeepK + m], ds[i]);
+                d2s[i] = fma(pk[m], s_d2z[lane][i * kMaxDeepK + m], d2s[i]);
+            }
+        }
+        double f, f1, f2;
+        act_eval(I.act, sv, &f, &f1, &f2);
+        double v = s_c0[lane] * f;
+        for (int i = 0; i < d; ++i) v += s_c1[lane][i] * f1 * ds[i] + s_c2[lane][i] * (f2 * ds[i] * ds[i] + f1 * d2s[i]);
+        Mb[(int64_t)k * B.ldm] = (T)v;
     }
 }
 
@@ -125,7 +225,7 @@ __global__ void k_rhs(const InstRec *__restrict__ insts, int s, double *__restri
         double x[3];
         int kind;
         row_point(I, r, x, &kind);
-        h[I.row0 + r] = kind < 0 ? I.scale_int * fam_source(I, x) : I.scale_set[kind] * fam_bdata(I, x);
+        h[I.row0 + r] = kind < 0 ? I.scale_int * fam_source(I, x) : I.scale_set[kind] * fam_bdata(I, x, kind);
     }
 }
 
@@ -144,10 +244,29 @@ rfm_status launch_assemble(const HostPlan &P, void *ws, const double *params, cu
                                                       ws_ptr<int32_t>(ws, L.off_qblk)); }
         RFM_CUDA_CHECK(cudaGetLastError());
         ProfScope ps("k_assemble", st);
-        if (L.asm_prec == RFM_ASM_FP32)
+        bool deep = false;
+        for (int s = 0; s < L.n_inst; ++s) deep = deep || P.inst[s].depth > 1;
+        // one launch over every tile; a system with any deep network takes the
+        // deep kernel for all its tiles (it also computes one-layer networks:
+        // their output-layer input is the normalised point)
+        if (deep) {
+            const int sm = (int)(sizeof(double) * 32 * 7 * kMaxDeepK);
+            if (L.asm_prec == RFM_ASM_FP32) {
+                RFM_CUDA_CHECK(cudaFuncSetAttribute(k_assemble_deep<float>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+                k_assemble_deep<float><<<(unsigned)L.n_tiles, 256, sm, st>>>(dI, dB, dTB, dTR, params,
+                                                                              ws_ptr<float>(ws, L.off_M));
+            } else {
+                RFM_CUDA_CHECK(cudaFuncSetAttribute(k_assemble_deep<double>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+                k_assemble_deep<double><<<(unsigned)L.n_tiles, 256, sm, st>>>(dI, dB, dTB, dTR, params,
+                                                                               ws_ptr<double>(ws, L.off_M));
+            }
+        } else if (L.asm_prec == RFM_ASM_FP32) {
             k_assemble<float><<<(unsigned)L.n_tiles, 256, 0, st>>>(dI, dB, dTB, dTR, params, ws_ptr<float>(ws, L.off_M));
-        else
+        } else {
             k_assemble<double><<<(unsigned)L.n_tiles, 256, 0, st>>>(dI, dB, dTB, dTR, params, ws_ptr<double>(ws, L.off_M));
+        }
         RFM_CUDA_CHECK(cudaGetLastError());
     }
     for (int s = 0; s < L.n_inst; ++s) {

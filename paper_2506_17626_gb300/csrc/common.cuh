@@ -38,7 +38,32 @@ struct InstRec {
     int64_t prm_off;            // offset (doubles) of the instance's feature parameters
     int32_t cov_off[3];         // offset of per-dimension cover tables (n[i] + 2 entries)
     int32_t pad3;
+    int32_t depth, act;         // subdomain networks (Eq. (2)): depth h >= 1, activation
+    double hard_bc;             // factor of the hard-constraint ansatz (0: none)
+    int64_t n_prm_sub;          // parameters of one subdomain network (doubles)
+    int32_t n_last, pad4;       // inputs of the output layer: dim (h = 1) or K
 };
+
+constexpr int kMaxDeepK = 32;   // width limit of networks with hidden layers
+
+// Normal dimension and side of face f (the oscillator's two initial rows both
+// sit at the lower end of its one dimension).
+__host__ __device__ inline void face_dims(int pde, int f, int *nd, int *side) {
+    if (pde == RFM_PDE_OSC) {
+        *nd = 0;
+        *side = 0;
+        return;
+    }
+    *nd = f / 2;
+    *side = f % 2;
+}
+
+// Boundary set of face f: heat's initial face is set 1; the oscillator's
+// value row set 0 and derivative row set 1; every other face set 0.
+__host__ __device__ inline int face_set_of(int pde, int dim, int f) {
+    if (pde == RFM_PDE_OSC) return f;
+    return (pde == RFM_PDE_HEAT && f / 2 == dim - 1) ? 1 : 0;
+}
 
 // Per-block record: block b is subdomain j of instance inst.
 struct BlkRec {

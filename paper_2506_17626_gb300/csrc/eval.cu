@@ -62,14 +62,37 @@ __global__ void __launch_bounds__(256) k_eval(const InstRec *__restrict__ insts,
             }
             double mu[3] = {0, 0, 0}, sig[3] = {1, 1, 1};
             for (int i = 0; i < d; ++i) sub_geom(I.lo[i], I.hi[i], I.S[i], I.delta, jd[i], &mu[i], &sig[i]);
-            const double *prm = params + I.prm_off + j * I.K * (d + 1);
+            const double *prm = params + I.prm_off + j * I.n_prm_sub;
             const double *aj = a + I.col0 + j * I.K;
             double sj = 0.0;
-            for (int k = lane; k < I.K; k += 32) {
-                const double *pk = prm + (int64_t)k * (d + 1);
-                double z = pk[d];
-                for (int i = 0; i < d; ++i) z += pk[i] * ((x[i] - mu[i]) / sig[i]);
-                sj = fma(aj[k], tanh(z), sj);
+            if (I.depth > 1) {
+                // the output layer's input: the last hidden layer at the point (Eq. (2))
+                double xn[3] = {0, 0, 0}, isg[3] = {1, 1, 1}, z[kMaxDeepK];
+                for (int i = 0; i < d; ++i) xn[i] = (x[i] - mu[i]) / sig[i];
+                net_hidden(I, prm, xn, isg, z, nullptr, nullptr);
+                const int nin = I.n_last;
+                for (int k = lane; k < I.K; k += 32) {
+                    const double *pk = prm + (int64_t)k * (nin + 1);
+                    double sv = pk[nin];
+                    for (int m = 0; m < nin; ++m) sv = fma(pk[m], z[m], sv);
+                    double f, f1, f2;
+                    act_eval(I.act, sv, &f, &f1, &f2);
+                    sj = fma(aj[k], f, sj);
+                }
+            } else {
+                for (int k = lane; k < I.K; k += 32) {
+                    const double *pk = prm + (int64_t)k * (d + 1);
+                    double z = pk[d];
+                    for (int i = 0; i < d; ++i) z += pk[i] * ((x[i] - mu[i]) / sig[i]);
+                    double f = 0.0;
+                    if (I.act == RFM_ACT_TANH) {
+                        f = tanh(z);
+                    } else {
+                        double f1, f2;
+                        act_eval(I.act, z, &f, &f1, &f2);
+                    }
+                    sj = fma(aj[k], f, sj);
+                }
             }
             for (int o = 16; o; o >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o);
             double w, dw[3], d2w[3];
@@ -236,8 +259,15 @@ rfm_status launch_eval(const HostPlan &P, void *ws, const double *params, const 
         }
         int g = (int)((n + 7) / 8);
         g = g < 1 ? 1 : (g > kEvalCtas ? kEvalCtas : g);
-        { ProfScope ps("k_eval", st);
-        k_eval_df<<<g, 256, 0, st>>>(dI, s, evdf, evdf + n_prm, X + 3 * pt_off[s], n, u + pt_off[s], part); }
+        const InstRec &I = P.inst[s];
+        if (I.depth == 1 && I.act == RFM_ACT_TANH && I.hard_bc == 0.0) {
+            ProfScope ps("k_eval", st);
+            k_eval_df<<<g, 256, 0, st>>>(dI, s, evdf, evdf + n_prm, X + 3 * pt_off[s], n, u + pt_off[s], part);
+        } else {
+            // other networks and the hard-constraint ansatz: the FP64 kernel
+            ProfScope ps("k_eval", st);
+            k_eval<<<g, 256, 0, st>>>(dI, s, params, a, X + 3 * pt_off[s], n, u + pt_off[s], part);
+        }
         RFM_CUDA_CHECK(cudaGetLastError());
         if (err) {
             ProfScope ps("k_eval_finish", st);

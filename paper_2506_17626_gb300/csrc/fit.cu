@@ -209,6 +209,11 @@ rfm_status launch_fit_prepare(const HostPlan &P, void *ws, const double *params,
         set_error("rfm_fit_prepare: the system has no filter factors (plain operator)");
         return RFM_EINVAL;
     }
+    for (int s = 0; s < L.n_inst; ++s)
+        if (P.inst[s].depth != 1 || P.inst[s].act != RFM_ACT_TANH || P.inst[s].hard_bc != 0.0) {
+            set_error("rfm_fit_prepare: the fit takes one-layer tanh networks without hard constraint");
+            return RFM_EINVAL;
+        }
     if (L.n_blocks == 0) return RFM_OK;
     const FitLayout F = fit_layout(P);
     double *Phi = ws_ptr<double>(fws, F.off_phi);

@@ -34,7 +34,25 @@ const char *last_error() { return g_err; }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static int nfaces_of(const rfm_problem &p) { return p.pde == RFM_PDE_HEAT ? 2 * (p.dim - 1) + 1 : 2 * p.dim; }
+static int nfaces_of(const rfm_problem &p) {
+    if (p.hard_bc > 0.0) return 0;   // the ansatz satisfies the boundary condition: no boundary rows
+    if (p.pde == RFM_PDE_OSC) return 2;
+    return p.pde == RFM_PDE_HEAT ? 2 * (p.dim - 1) + 1 : 2 * p.dim;
+}
+
+static int depth_of(const rfm_problem &p) { return p.depth > 1 ? p.depth : 1; }
+
+// Parameters of one subdomain network (the layout of rfm_problem in rfm.h).
+static int64_t params_per_subdomain(const rfm_problem &p) {
+    const int nl = depth_of(p) > 1 ? p.K : p.dim;
+    int64_t c = (int64_t)p.K * (nl + 1);
+    int nin = p.dim;
+    for (int l = 1; l < depth_of(p); ++l) {
+        c += (int64_t)p.K * (nin + 1);
+        nin = p.K;
+    }
+    return c;
+}
 
 rfm_status build_plan(const rfm_problem *probs, int n_inst, const rfm_config *cfg, HostPlan *out, char *err,
                       size_t errlen) {
@@ -65,11 +83,17 @@ rfm_status build_plan(const rfm_problem *probs, int n_inst, const rfm_config *cf
         InstRec &I = inst[s];
         memset(&I, 0, sizeof(I));
         if (p.dim < 1 || p.dim > 3) { snprintf(err, errlen, "instance %d: dim must be 1..3", s); return RFM_EINVAL; }
-        if (p.pde != RFM_PDE_POISSON && p.pde != RFM_PDE_HEAT) { snprintf(err, errlen, "instance %d: unknown pde", s); return RFM_EINVAL; }
+        if (p.pde != RFM_PDE_POISSON && p.pde != RFM_PDE_HEAT && p.pde != RFM_PDE_OSC) { snprintf(err, errlen, "instance %d: unknown pde", s); return RFM_EINVAL; }
+        if (p.pde == RFM_PDE_OSC && (p.dim != 1 || p.family != RFM_FAM_OSC)) { snprintf(err, errlen, "instance %d: the oscillator is one-dimensional with RFM_FAM_OSC", s); return RFM_EINVAL; }
+        if (p.family == RFM_FAM_OSC && p.pde != RFM_PDE_OSC) { snprintf(err, errlen, "instance %d: RFM_FAM_OSC needs RFM_PDE_OSC", s); return RFM_EINVAL; }
+        if (p.depth < 0 || p.depth > 8) { snprintf(err, errlen, "instance %d: depth must be 0..8", s); return RFM_EINVAL; }
+        if (p.depth > 1 && p.K > kMaxDeepK) { snprintf(err, errlen, "instance %d: networks with hidden layers are at most %d wide", s, kMaxDeepK); return RFM_EINVAL; }
+        if (p.act < RFM_ACT_TANH || p.act > RFM_ACT_SIN) { snprintf(err, errlen, "instance %d: unknown activation", s); return RFM_EINVAL; }
+        if (!(p.hard_bc >= 0.0) || (p.hard_bc > 0.0 && p.pde != RFM_PDE_POISSON)) { snprintf(err, errlen, "instance %d: hard_bc must be >= 0 and is for Poisson problems", s); return RFM_EINVAL; }
         if (p.pde == RFM_PDE_HEAT && p.dim < 2) { snprintf(err, errlen, "instance %d: heat needs dim >= 2", s); return RFM_EINVAL; }
         if (p.K < 1 || p.K > kMaxK) { snprintf(err, errlen, "instance %d: K must be 1..%d", s, kMaxK); return RFM_EINVAL; }
         if (!(p.delta > 0.0)) { snprintf(err, errlen, "instance %d: delta must be > 0", s); return RFM_EINVAL; }
-        if (p.family < RFM_FAM_SINPROD || p.family > RFM_FAM_PARAM5) { snprintf(err, errlen, "instance %d: unknown family", s); return RFM_EINVAL; }
+        if (p.family < RFM_FAM_SINPROD || p.family > RFM_FAM_OSC) { snprintf(err, errlen, "instance %d: unknown family", s); return RFM_EINVAL; }
         if (p.family == RFM_FAM_PARAM5 && (p.dim != 2 || p.pde != RFM_PDE_POISSON)) { snprintf(err, errlen, "instance %d: PARAM5 is a 2D Poisson family", s); return RFM_EINVAL; }
         if (p.n_modes < 0 || p.n_modes > 16) { snprintf(err, errlen, "instance %d: n_modes must be 0..16", s); return RFM_EINVAL; }
         int64_t J = 1, NI = 1;
@@ -82,6 +106,11 @@ rfm_status build_plan(const rfm_problem *probs, int n_inst, const rfm_config *cf
         }
         I.dim = p.dim; I.pde = p.pde; I.family = p.family; I.n_modes = p.n_modes;
         I.K = p.K; I.kappa = p.kappa; I.delta = p.delta;
+        I.depth = depth_of(p);
+        I.act = p.act;
+        I.hard_bc = p.hard_bc;
+        I.n_prm_sub = params_per_subdomain(p);
+        I.n_last = I.depth > 1 ? p.K : p.dim;
         for (int i = 0; i < 3; ++i) {
             I.n[i] = i < p.dim ? p.n[i] : 1;
             I.S[i] = i < p.dim ? p.S[i] : 1;
@@ -94,14 +123,14 @@ rfm_status build_plan(const rfm_problem *probs, int n_inst, const rfm_config *cf
         I.NI = NI;
         int64_t fr = NI, nb_set[2] = {0, 0};
         for (int f = 0; f < nf; ++f) {
-            int nd = f / 2;
+            int nd, side;
+            face_dims(p.pde, f, &nd, &side);
             int64_t c = 1;
             for (int i = 0; i < p.dim; ++i)
                 if (i != nd) c *= p.n[i];
             I.face_row0[f] = fr;
             fr += c;
-            int set = (p.pde == RFM_PDE_HEAT && nd == p.dim - 1) ? 1 : 0;
-            nb_set[set] += c;
+            nb_set[face_set_of(p.pde, p.dim, f)] += c;
         }
         I.N = fr;
         I.scale_int = 1.0 / sqrt((double)NI);
@@ -184,7 +213,8 @@ rfm_status build_plan(const rfm_problem *probs, int n_inst, const rfm_config *cf
             int64_t m = nint;
             for (int f = 0; f < kMaxFaces; ++f) B.face_off[f] = -1;
             for (int f = 0; f < nf; ++f) {
-                int nd = f / 2, side = f % 2;
+                int nd, side;
+                face_dims(p.pde, f, &nd, &side);
                 int touch = side ? thi[nd][B.jd[nd]] : tlo[nd][B.jd[nd]];
                 int64_t c = 1;
                 for (int i = 0; i < p.dim; ++i)
@@ -223,7 +253,7 @@ rfm_status build_plan(const rfm_problem *probs, int n_inst, const rfm_config *cf
         max_K = p.K > max_K ? p.K : max_K;
         row0 += I.N;
         col0 += J * p.K;
-        prm0 += J * p.K * (p.dim + 1);
+        prm0 += J * params_per_subdomain(p);
     }
 
     Layout &L = out->L;

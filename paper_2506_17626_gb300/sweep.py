@@ -20,7 +20,12 @@ Workloads: p1d is 1D Poisson -u'' = f on [0,1], u = sin 2 pi x + 0.1 sin 50 pi
 x, 20 subdomains, overlap ratio 1.3, 100 features, 1600 interior points,
 FP64 throughout; p2d is the 2D Poisson workload of the benchmark (20 x 20
 subdomains, overlap ratio 1.25, 300 features, 360^2 interior points), FP64
-assembly with the explicit FP64 Q_hat operator.
+assembly with the explicit FP64 Q_hat operator; osc and laplace are the
+paper's own baselines (Sec. 4.3 and 4.4: the damped oscillator with omega0 =
+60, J = 20, overlap ratio 2.9, K = 8; the multi-scale Laplace problem with
+n = 3, 16 x 16 subdomains, overlap ratio 2.9, K = 16 and the hard-constraint
+ansatz), FP64 with the paper's operator form (R_hat^-1 substitution), with
+--depth and --act for the network ablations of Tables 1 and 2.
 """
 from __future__ import annotations
 
@@ -106,7 +111,10 @@ def sweep(p, params: torch.Tensor, X: torch.Tensor, asm: str = "fp64", op: str =
 
 def main(argv: Optional[Sequence[str]] = None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="p1d", choices=["p1d", "p2d"])
+    ap.add_argument("--case", default="p1d", choices=["p1d", "p2d", "osc", "laplace"])
+    ap.add_argument("--depth", type=int, default=1, help="osc, laplace: depth h of the subdomain networks")
+    ap.add_argument("--act", default="tanh", choices=["tanh", "sigmoid", "sin"],
+                    help="osc, laplace: activation of the subdomain networks")
     ap.add_argument("--iters", type=int, default=10000)
     ap.add_argument("--every", type=int, default=100)
     ap.add_argument("--op", default=None, choices=["ar64", "q64"],
@@ -117,8 +125,15 @@ def main(argv: Optional[Sequence[str]] = None):
         sys.path.insert(0, root)
     import synth
     dev = torch.device("cuda:0")
+    act = {"tanh": synth.ACT_TANH, "sigmoid": synth.ACT_SIGMOID, "sin": synth.ACT_SIN}[args.act]
     if args.case == "p1d":
         p = synth.poisson1d()
+        op = args.op or "ar64"
+    elif args.case == "osc":
+        p = synth.oscillator(act=act, depth=args.depth)
+        op = args.op or "ar64"
+    elif args.case == "laplace":
+        p = synth.laplace_multiscale(act=act, depth=args.depth)
         op = args.op or "ar64"
     else:
         p = synth.poisson2d()

@@ -172,3 +172,32 @@ def test_network_calls_reject_null_arguments(native):
 
 def test_unknown_option_is_rejected(native):
     _expect(native, native.load().rfm_set_option(12345, 1), native.RFM_EINVAL)
+
+
+@pytest.mark.parametrize("case", ["depth", "deep_width", "act", "hard_bc_negative", "hard_bc_heat", "osc_2d",
+                                  "osc_family"])
+def test_invalid_networks_and_problem_kinds_are_rejected(native, case):
+    """The size call rejects networks and problem kinds the path does not
+    define, with a message, before anything else."""
+    p = synth.poisson2d(S=3, K=8, n=12)
+    if case == "depth":
+        p.depth = 9
+    elif case == "deep_width":
+        p.depth, p.K = 3, 40
+    elif case == "act":
+        p.act = 3
+    elif case == "hard_bc_negative":
+        p.hard_bc = -1.0
+    elif case == "hard_bc_heat":
+        p = synth.heat3d(S=2, K=4, n=5)
+        p.hard_bc = 2.0
+    elif case == "osc_2d":
+        p.pde = synth.PDE_OSC
+    else:
+        p = synth.oscillator(S=3, K=4)
+        p.family = synth.FAM_SINPROD
+    arr = (native.RfmProblem * 1)(native.problem_struct(p))
+    cfg = native.RfmConfig(native.ASM["fp64"], native.OPS["ar64"], 1e-6)
+    sz = native.RfmSizes()
+    assert native.load().rfm_problem_size(arr, 1, C.byref(cfg), C.byref(sz)) == native.RFM_EINVAL
+    assert native.load().rfm_last_error()

@@ -42,7 +42,9 @@ def _sizes(native, probs, asm="fp64", op="ar64", tol=1e-10):
 
 
 @pytest.mark.parametrize("p", [synth.poisson1d(S=5, K=7, n=50), synth.poisson2d(S=4, K=5, n=13),
-                               synth.heat3d(S=3, K=4, n=7), synth.poisson2d(S=5, K=3, n=11, delta=2.9)])
+                               synth.heat3d(S=3, K=4, n=7), synth.poisson2d(S=5, K=3, n=11, delta=2.9),
+                               synth.oscillator(S=5, K=4), synth.laplace_multiscale(S=3, K=4),
+                               synth.laplace_multiscale(S=3, K=9, depth=3, act=synth.ACT_SIN)])
 def test_block_row_counts_match_oracle(native, p):
     rc, sz, arr, cfg = _sizes(native, [p])
     assert rc == 0
