@@ -325,7 +325,7 @@ def time_to_error(p, args, dev, world, rank_id, headline):
 
     steps_m = args.steps if headline else min(args.steps, 3)
     warm_m = args.warmup if headline else max(1, min(args.warmup, 2))
-    steps_f = min(args.steps, 5) if headline else min(args.steps, 2)
+    steps_f = min(args.steps, 3) if headline else min(args.steps, 2)
     clk = None
     if headline:
         with Clocks(args.clocks_log) as clk:

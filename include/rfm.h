@@ -273,6 +273,45 @@ rfm_status rfm_lsqr_solve(const rfm_problem *probs, int n_inst, const rfm_config
 rfm_status rfm_residual(const rfm_problem *probs, int n_inst, const rfm_config *cfg, const double *d_a, double *d_r,
                         double *d_rnorm, void *d_ws, size_t ws_bytes, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Many right-hand sides on one operator.  Data sets of one family that share
+ * the decomposition, the features and the collocation (every field of
+ * rfm_problem but family, n_modes and fam; the oscillator's coefficients
+ * fam[0..2] included) share M, so Algorithm 1's factors and Proposition 3.1's
+ * Q_hat_j are those of one system; only h differs.  LSQR then runs for every
+ * data set at once, each with its own scalars, estimates and stopping test,
+ * and the block products of an iteration read Q_hat_j once for all of them:
+ * dense (m_j x r_j) x (r_j x nrhs) products.  The paper solves one data set
+ * at a time; this is an implementation choice.
+ * ------------------------------------------------------------------------ */
+
+/* Bytes of the multi-right-hand-side workspace for nrhs data sets (1..256)
+ * of the system described by prob (one instance). */
+rfm_status rfm_lsqr_multi_size(const rfm_problem *prob, const rfm_config *cfg, int nrhs, size_t *bytes);
+
+/* h (Eq. (5)) of data sets probs[0..nrhs) into d_H (nrhs x n_rows doubles,
+ * set j at d_H + j n_rows).  Every probs[j] must equal probs[0] except in its
+ * data (RFM_EINVAL otherwise).  d_mws: the multi-right-hand-side workspace
+ * (rfm_lsqr_multi_size bytes, 256-byte aligned); its first bytes receive the
+ * sets' records, uploaded with cudaMemcpyAsync from pageable host memory. */
+rfm_status rfm_rhs_many(const rfm_problem *probs, int nrhs, const rfm_config *cfg, double *d_H, void *d_mws,
+                        size_t mws_bytes, void *stream);
+
+/* LSQR of Algorithm 2 from zero for nrhs right-hand sides d_H (layout of
+ * rfm_rhs_many) on the filtered system in d_ws (assembled and filtered with
+ * RFM_OP_Q32 or RFM_OP_Q64, one instance), then a_j = S^-1 y_j into d_A
+ * (nrhs x n_cols doubles, set j at d_A + j n_cols, zeros at dropped
+ * columns), d_report[j] per set.  opts: atol, btol, max_iter (the other
+ * fields unused).  Every set stops on the tests of rfm_lsqr_solve, with
+ * ||y|| of the previous iteration.  The call issues a fixed sequence of
+ * launches per iteration (max_iter of them; sets that have stopped keep their
+ * iterate) and uploads its tile lists from pageable host memory.
+ * Errors: RFM_EINVAL for another operator, more than one instance, nrhs
+ * outside 1..256 or bad options; RFM_ENOSPACE for a short workspace. */
+rfm_status rfm_lsqr_multi(const rfm_problem *prob, const rfm_config *cfg, const rfm_lsqr_opts *opts, int nrhs,
+                          const double *d_H, double *d_A, rfm_lsqr_report *d_report, void *d_ws, size_t ws_bytes,
+                          void *d_mws, size_t mws_bytes, void *stream);
+
 /* a = S^-1 y (Algorithm 2's last step) for an arbitrary y in the n_cols
  * layout: per block a_j[perm[c]] = (R_hat_j^-1 y_j)[c] for kept c, 0 at
  * dropped columns (RFM_OP_PLAIN: a = y).  Requires a filtered workspace. */

@@ -57,7 +57,7 @@ REPORT_FIELDS = ("itn", "istop", "rnorm", "arnorm", "anorm", "ynorm", "bnorm", "
 REPORT_LEN = len(REPORT_FIELDS)
 
 EXPORTS = ["rfm_problem_size", "rfm_assemble", "rfm_rrqr_filter", "rfm_lsqr_solve", "rfm_coefficients",
-           "rfm_eval", "rfm_residual", "rfm_block_info", "rfm_workspace_view", "rfm_profile_enable", "rfm_profile_reset",
+           "rfm_eval", "rfm_residual", "rfm_lsqr_multi_size", "rfm_rhs_many", "rfm_lsqr_multi", "rfm_block_info", "rfm_workspace_view", "rfm_profile_enable", "rfm_profile_reset",
            "rfm_profile_read", "rfm_set_option", "rfm_last_error", "rfm_abi_version"]
 
 _lib = None
@@ -82,6 +82,9 @@ def load(path: str = LIB_PATH):
         "rfm_lsqr_solve": [P, C.c_int, CF, C.POINTER(RfmLsqrOpts), vp, vp, vp, vp, vp, C.c_size_t, vp],
         "rfm_eval": [P, C.c_int, CF, vp, vp, vp, vp, vp, vp, vp, C.c_size_t, vp],
         "rfm_residual": [P, C.c_int, CF, vp, vp, vp, vp, C.c_size_t, vp],
+        "rfm_lsqr_multi_size": [P, CF, C.c_int, C.POINTER(C.c_size_t)],
+        "rfm_rhs_many": [P, C.c_int, CF, vp, vp, C.c_size_t, vp],
+        "rfm_lsqr_multi": [P, CF, C.POINTER(RfmLsqrOpts), C.c_int, vp, vp, vp, vp, C.c_size_t, vp, C.c_size_t, vp],
         "rfm_coefficients": [P, C.c_int, CF, vp, vp, vp, C.c_size_t, vp],
         "rfm_block_info": [P, C.c_int, CF, i64, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)],
         "rfm_workspace_view": [P, C.c_int, CF, vp, C.c_int, C.POINTER(vp)],

@@ -104,6 +104,43 @@ class System:
                                                       _ptr(rn), C.c_void_p(self.ws_ptr), self.ws_bytes, _stream()))
         return (rn, r) if want_r else rn
 
+    # -- many right-hand sides on one operator ------------------------------------
+    def _multi_ws(self, nrhs: int):
+        nb = C.c_size_t()
+        N.check("rfm_lsqr_multi_size", self.lib.rfm_lsqr_multi_size(self._probs, C.byref(self._cfg), int(nrhs),
+                                                                    C.byref(nb)))
+        ws = torch.empty(nb.value + 256, dtype=torch.uint8, device=self.device)
+        return ws, ws.data_ptr() + (-ws.data_ptr()) % 256, nb.value
+
+    def rhs_many(self, problems) -> torch.Tensor:
+        """h of data sets `problems` (same decomposition, features and rows as
+        this one-instance system, other data), nrhs x n_rows FP64."""
+        assert self.n == 1
+        n = len(problems)
+        arr = (N.RfmProblem * n)(*[N.problem_struct(p) for p in problems])
+        H = torch.empty((n, self.sizes["n_rows"]), dtype=torch.float64, device=self.device)
+        ws, ptr, nb = self._multi_ws(n)
+        N.check("rfm_rhs_many", self.lib.rfm_rhs_many(arr, n, C.byref(self._cfg), _ptr(H), C.c_void_p(ptr), nb,
+                                                      _stream()))
+        self._mws_keep = ws
+        return H
+
+    def solve_multi(self, H: torch.Tensor, atol=1e-10, btol=1e-10, max_iter=10000):
+        """LSQR from zero for every row of H (nrhs x n_rows) on this system's
+        operator (one instance, explicit Q_hat); returns the coefficients
+        (nrhs x n_cols) and the reports (nrhs x report fields)."""
+        assert H.is_cuda and H.dtype == torch.float64 and H.is_contiguous() and H.shape[1] == self.sizes["n_rows"]
+        n = H.shape[0]
+        A = torch.empty((n, self.sizes["n_cols"]), dtype=torch.float64, device=self.device)
+        rep = torch.empty(n * N.REPORT_LEN, dtype=torch.float64, device=self.device)
+        ws, ptr, nb = self._multi_ws(n)
+        opts = N.RfmLsqrOpts(float(atol), float(btol), int(max_iter), 10000, None, 0, 0, None, 0, 0, None)
+        N.check("rfm_lsqr_multi", self.lib.rfm_lsqr_multi(self._probs, C.byref(self._cfg), C.byref(opts), n, _ptr(H),
+                                                          _ptr(A), _ptr(rep), C.c_void_p(self.ws_ptr), self.ws_bytes,
+                                                          C.c_void_p(ptr), nb, _stream()))
+        self._mws_keep = ws
+        return A, rep
+
     def coefficients(self, y: torch.Tensor) -> torch.Tensor:
         """a = S^-1 y with zeros at dropped columns (Algorithm 2, last step)."""
         a = torch.empty(self.sizes["n_cols"], dtype=torch.float64, device=self.device)

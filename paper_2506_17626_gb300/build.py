@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librfm.so")
-SOURCES = ["plan.cu", "assemble.cu", "rrqr.cu", "lsqr.cu", "eval.cu", "fit.cu", "mlp.cu", "api.cu", "prof.cu"]
+SOURCES = ["plan.cu", "assemble.cu", "rrqr.cu", "lsqr.cu", "lsqr_multi.cu", "eval.cu", "fit.cu", "mlp.cu", "api.cu",
+           "prof.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "--expt-relaxed-constexpr",
               "-I", os.path.join(os.path.dirname(HERE), "include")]

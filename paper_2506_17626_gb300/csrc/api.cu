@@ -3,6 +3,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 #include "prof.cuh"
@@ -16,6 +17,10 @@ rfm_status launch_lsqr(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, c
 rfm_status launch_coefficients(const HostPlan &P, void *ws, const double *y, double *a_out, cudaStream_t st);
 rfm_status launch_residual(const HostPlan &P, void *ws, const double *a, double *r_out, double *rnorm,
                            cudaStream_t st);
+size_t multi_workspace_bytes(const HostPlan &P, int R);
+rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, int R, const double *H,
+                             double *A, rfm_lsqr_report *rep, void *mws, cudaStream_t st);
+rfm_status launch_rhs_many(const InstRec *recs, int R, int64_t N, double *H, void *scratch, cudaStream_t st);
 void set_force_global_filter(int on);
 void set_autotune(int on);
 void set_qr_double_float(int on);
@@ -235,6 +240,89 @@ rfm_status rfm_residual(const rfm_problem *probs, int n_inst, const rfm_config *
         return RFM_EINVAL;
     }
     return launch_residual(P.p, d_ws, d_a, d_r, d_rnorm, (cudaStream_t)stream);
+    RFM_GUARD_END
+}
+
+rfm_status rfm_lsqr_multi_size(const rfm_problem *prob, const rfm_config *cfg, int nrhs, size_t *bytes) {
+    RFM_GUARD_BEGIN
+    Plan P(prob, 1, cfg);
+    if (!P.ok) return P.rc;
+    if (!bytes || nrhs < 1 || nrhs > 256) {
+        set_error("rfm_lsqr_multi_size: need bytes and 1 <= nrhs <= 256");
+        return RFM_EINVAL;
+    }
+    *bytes = multi_workspace_bytes(P.p, nrhs);
+    return RFM_OK;
+    RFM_GUARD_END
+}
+
+static rfm_status check_mws(const HostPlan &P, int nrhs, const void *mws, size_t bytes) {
+    if (!mws || ((uintptr_t)mws & 255)) {
+        set_error("multi-right-hand-side workspace must be a 256-byte aligned device pointer");
+        return RFM_EINVAL;
+    }
+    if (bytes < multi_workspace_bytes(P, nrhs)) {
+        set_error("multi-right-hand-side workspace has %zu bytes, %zu needed", bytes, multi_workspace_bytes(P, nrhs));
+        return RFM_ENOSPACE;
+    }
+    return RFM_OK;
+}
+
+// Data sets of one family: everything but the data (family, n_modes, fam) equal.
+static bool same_layout(const rfm_problem &a, const rfm_problem &b) {
+    rfm_problem x = a, y = b;
+    x.family = y.family = 0;
+    x.n_modes = y.n_modes = 0;
+    memset(x.fam, 0, sizeof(x.fam));
+    memset(y.fam, 0, sizeof(y.fam));
+    if (a.pde == RFM_PDE_OSC) {   // the oscillator's coefficients are part of the operator
+        memcpy(x.fam, a.fam, 3 * sizeof(double));
+        memcpy(y.fam, b.fam, 3 * sizeof(double));
+    }
+    return memcmp(&x, &y, sizeof(rfm_problem)) == 0;
+}
+
+rfm_status rfm_rhs_many(const rfm_problem *probs, int nrhs, const rfm_config *cfg, double *d_H, void *d_mws,
+                        size_t mws_bytes, void *stream) {
+    RFM_GUARD_BEGIN
+    if (!probs || nrhs < 1 || nrhs > 256 || !d_H) {
+        set_error("rfm_rhs_many: need probs, 1 <= nrhs <= 256 and d_H");
+        return RFM_EINVAL;
+    }
+    Plan P0(probs, 1, cfg);
+    if (!P0.ok) return P0.rc;
+    rfm_status rc = check_mws(P0.p, nrhs, d_mws, mws_bytes);
+    if (rc != RFM_OK) return rc;
+    std::vector<InstRec> recs((size_t)nrhs);
+    for (int j = 0; j < nrhs; ++j) {
+        if (!same_layout(probs[0], probs[j])) {
+            set_error("rfm_rhs_many: data set %d differs from set 0 in more than its data", j);
+            return RFM_EINVAL;
+        }
+        Plan Pj(probs + j, 1, cfg);
+        if (!Pj.ok) return Pj.rc;
+        recs[(size_t)j] = Pj.p.inst[0];
+    }
+    return launch_rhs_many(recs.data(), nrhs, P0.p.L.n_rows, d_H, d_mws, (cudaStream_t)stream);
+    RFM_GUARD_END
+}
+
+rfm_status rfm_lsqr_multi(const rfm_problem *prob, const rfm_config *cfg, const rfm_lsqr_opts *opts, int nrhs,
+                          const double *d_H, double *d_A, rfm_lsqr_report *d_report, void *d_ws, size_t ws_bytes,
+                          void *d_mws, size_t mws_bytes, void *stream) {
+    RFM_GUARD_BEGIN
+    Plan P(prob, 1, cfg);
+    if (!P.ok) return P.rc;
+    rfm_status rc = check_ws(P.p.L, d_ws, ws_bytes);
+    if (rc != RFM_OK) return rc;
+    if (nrhs < 1 || nrhs > 256 || !d_H || !d_A || !opts || opts->max_iter < 0 || !(opts->atol >= 0.0) ||
+        !(opts->btol >= 0.0)) {
+        set_error("rfm_lsqr_multi: need 1 <= nrhs <= 256, d_H, d_A and opts (max_iter >= 0, atol, btol >= 0)");
+        return RFM_EINVAL;
+    }
+    rc = check_mws(P.p, nrhs, d_mws, mws_bytes);
+    if (rc != RFM_OK) return rc;
+    return launch_lsqr_multi(P.p, d_ws, opts, nrhs, d_H, d_A, d_report, d_mws, (cudaStream_t)stream);
     RFM_GUARD_END
 }
 

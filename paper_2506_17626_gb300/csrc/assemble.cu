@@ -229,6 +229,22 @@ __global__ void k_rhs(const InstRec *__restrict__ insts, int s, double *__restri
     }
 }
 
+// h of every data set of a family sharing one row layout: recs[j] is the
+// record of set j (rows from 0), uploaded into the first bytes of scratch
+// (room for R records); H[j * N + r].
+rfm_status launch_rhs_many(const InstRec *recs, int R, int64_t N, double *H, void *scratch, cudaStream_t st) {
+    InstRec *d = reinterpret_cast<InstRec *>(scratch);
+    RFM_CUDA_CHECK(cudaMemcpyAsync(d, recs, sizeof(InstRec) * R, cudaMemcpyHostToDevice, st));
+    unsigned g = (unsigned)((N + 255) / 256);
+    g = g > 4096 ? 4096 : (g < 1 ? 1 : g);
+    for (int j = 0; j < R; ++j) {
+        ProfScope ps("k_rhs", st);
+        k_rhs<<<g, 256, 0, st>>>(d, j, H + (int64_t)j * N);
+        RFM_CUDA_CHECK(cudaGetLastError());
+    }
+    return RFM_OK;
+}
+
 rfm_status launch_assemble(const HostPlan &P, void *ws, const double *params, cudaStream_t st) {
     const Layout &L = P.L;
     InstRec *dI = ws_ptr<InstRec>(ws, L.off_inst);

@@ -1,0 +1,532 @@
+// lsqr_multi.cu -- LSQR (Paige and Saunders 1982) for many right-hand sides
+// on one operator: the instances of a parametric family that share the
+// decomposition and the features (only the data f, g differ) share M_hat,
+// R_hat and Q_hat (Algorithm 1 and Proposition 3.1 depend on M alone), so
+// the products of every right-hand side's iteration read the operator once:
+//
+//   forward     T_b = Q_hat_b V_b          (m_b x r_b) x (r_b x R) per block
+//   transposed  Z_b = Q_hat_b^T U_b        (r_b x m_b) x (m_b x R) per block
+//
+// dense block products (CUDA-core register tiles of 64 x 64 outputs, 4 x 4 per
+// thread, FP32 with FP32 accumulation for the FP32 Q_hat, FP64 for the FP64
+// one).  Each right-hand side keeps its own LSQR scalars, estimates and
+// stopping test; vectors are FP64, stored with the right-hand sides fastest
+// ([row][R], [slot][R]).  One iteration is a fixed sequence of launches:
+//   fwd -> rows (u~, ||u~||^2 partials) -> beta -> trans -> cols (v~,
+//   ||v~||^2 partials) -> alpha (rotation, estimates, stopping) -> update
+//   (y, w, ||y||^2 partials).
+// Reductions are per-CTA partials summed in a fixed order: bitwise
+// reproducible.
+#include <string.h>
+
+#include <vector>
+
+#include "device.cuh"
+#include "prof.cuh"
+
+namespace rfm {
+
+rfm_status launch_coefficients(const HostPlan &P, void *ws, const double *y, double *a_out, cudaStream_t st);
+
+constexpr int kMT = 64;     // rows (forward) or columns (transposed) of a CTA tile
+constexpr int kMR = 64;     // right-hand sides of a CTA tile
+constexpr int kMK = 16;     // reduction depth of one shared-memory stage
+constexpr int kMaxRhs = 256;
+constexpr int kRedCtas = 512;   // CTAs of the row / column phases (partial sums)
+
+struct MScal {
+    double alpha, beta, rhobar, phibar, anorm2, bnorm, rnorm, arnorm, ynorm;
+    double phi_rho, theta_rho, c, inv_alpha, inv_beta, inv_alpha_old, beta_old;
+    int32_t itn, istop, done, pad;
+};
+
+struct MLayout {
+    int R;
+    int64_t n_fitems, n_titems;
+    size_t off_inst, off_fitems, off_titems, off_vt, off_w, off_y, off_z, off_u, off_t, off_out, off_part, off_scal;
+    size_t total;
+};
+
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static MLayout multi_layout(const HostPlan &P, int R) {
+    const Layout &L = P.L;
+    MLayout M;
+    memset(&M, 0, sizeof(M));
+    M.R = R;
+    int64_t nf = 0, nt = 0;
+    for (int64_t b = 0; b < L.n_blocks; ++b) {
+        nf += (P.blk[b].m + kMT - 1) / kMT;
+        nt += (P.blk[b].K + kMT - 1) / kMT;
+    }
+    M.n_fitems = nf;
+    M.n_titems = nt;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = al256(o + bytes); return r; };
+    M.off_inst = take(sizeof(InstRec) * kMaxRhs);
+    M.off_fitems = take(sizeof(int32_t) * 2 * (nf + 1));
+    M.off_titems = take(sizeof(int32_t) * 2 * (nt + 1));
+    const size_t cols = (size_t)L.n_cols * R * sizeof(double);
+    M.off_vt = take(cols);
+    M.off_w = take(cols);
+    M.off_y = take(cols);
+    M.off_z = take(cols);
+    M.off_u = take((size_t)L.n_rows * R * sizeof(double));
+    M.off_t = take((size_t)L.block_rows * R * sizeof(double));
+    M.off_out = take(cols);
+    M.off_part = take(sizeof(double) * 2 * kRedCtas * R);
+    M.off_scal = take(sizeof(MScal) * R);
+    M.total = o;
+    return M;
+}
+
+size_t multi_workspace_bytes(const HostPlan &P, int R) { return multi_layout(P, R).total; }
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+// U[g][j] = H[j][g] (right-hand sides fastest), ||b_j||^2 partials
+__global__ void __launch_bounds__(256) k_m_load(const double *__restrict__ H, int64_t n_rows, int R,
+                                                double *__restrict__ U, double *__restrict__ part) {
+    __shared__ double red[256];
+    const int Rp = R <= 1 ? 1 : (R <= 2 ? 2 : (R <= 4 ? 4 : (R <= 8 ? 8 : (R <= 16 ? 16 : (R <= 32 ? 32 : (R <= 64 ? 64 : (R <= 128 ? 128 : 256)))))));
+    const int j = threadIdx.x % Rp, sub = threadIdx.x / Rp, nsub = 256 / Rp;
+    double ss = 0.0;
+    if (j < R)
+        for (int64_t g = (int64_t)blockIdx.x * nsub + sub; g < n_rows; g += (int64_t)gridDim.x * nsub) {
+            const double v = H[(int64_t)j * n_rows + g];
+            U[g * R + j] = v;
+            ss = fma(v, v, ss);
+        }
+    red[threadIdx.x] = ss;
+    __syncthreads();
+    if (threadIdx.x < Rp && j < R) {
+        double t = 0.0;
+        for (int s = 0; s < nsub; ++s) t += red[s * Rp + threadIdx.x];
+        part[(int64_t)blockIdx.x * R + threadIdx.x] = t;
+    }
+}
+
+// T = Q_hat_b (V / alpha) for one 64-row tile of one block and 64 right-hand
+// sides (blockIdx.y); rows past the block and slots past its rank read 0.
+template <typename TA>
+__global__ void __launch_bounds__(256) k_m_fwd(const BlkRec *__restrict__ blks, const int32_t *__restrict__ items,
+                                               const int32_t *__restrict__ rank, const TA *__restrict__ Q,
+                                               const double *__restrict__ VT, const MScal *__restrict__ sc, int R,
+                                               double *__restrict__ T) {
+    __shared__ TA As[kMK][kMT], Bs[kMK][kMR];
+    const int b = items[2 * blockIdx.x], r0 = items[2 * blockIdx.x + 1];
+    const BlkRec &B = blks[b];
+    const int rb = rank[b], m = B.m, j0 = blockIdx.y * kMR;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    TA acc[4][4];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) acc[i][j] = (TA)0;
+    for (int c0 = 0; c0 < rb; c0 += kMK) {
+        for (int e = tid; e < kMK * kMT; e += 256) {
+            const int col = e / kMT, row = e % kMT;
+            As[col][row] = (c0 + col < rb && r0 + row < m) ? Q[B.moff + (int64_t)(c0 + col) * B.ldm + r0 + row] : (TA)0;
+            const int jj = e % kMR, cc = e / kMR;
+            Bs[cc][jj] = (c0 + cc < rb && j0 + jj < R)
+                             ? (TA)(VT[(B.coff + c0 + cc) * R + j0 + jj] * sc[j0 + jj].inv_alpha)
+                             : (TA)0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kMK; ++kk) {
+            TA a[4], v[4];
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+            for (int j = 0; j < 4; ++j) v[j] = Bs[kk][tx * 4 + j];
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * v[j];
+        }
+        __syncthreads();
+    }
+    for (int i = 0; i < 4; ++i) {
+        const int row = r0 + ty * 4 + i;
+        if (row >= m) continue;
+        for (int j = 0; j < 4; ++j) {
+            const int jj = j0 + tx * 4 + j;
+            if (jj < R) T[(B.roff + row) * R + jj] = (double)acc[i][j];
+        }
+    }
+}
+
+// Z = Q_hat_b^T (U_b / beta) for one 64-column tile of one block (columns
+// below its rank) and 64 right-hand sides; U_b gathered by the block's rows.
+template <typename TA>
+__global__ void __launch_bounds__(256) k_m_trans(const BlkRec *__restrict__ blks, const int32_t *__restrict__ items,
+                                                 const int32_t *__restrict__ rank, const int32_t *__restrict__ grow,
+                                                 const TA *__restrict__ Q, const double *__restrict__ U,
+                                                 const MScal *__restrict__ sc, int R, int64_t row_base,
+                                                 double *__restrict__ Z) {
+    __shared__ TA As[kMK][kMT], Bs[kMK][kMR];
+    __shared__ int64_t s_g[kMK];
+    const int b = items[2 * blockIdx.x], c0 = items[2 * blockIdx.x + 1];
+    const BlkRec &B = blks[b];
+    const int rb = rank[b], m = B.m, j0 = blockIdx.y * kMR;
+    if (c0 >= rb) return;   // uniform over the CTA
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    TA acc[4][4];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) acc[i][j] = (TA)0;
+    for (int i0 = 0; i0 < m; i0 += kMK) {
+        if (tid < kMK) s_g[tid] = i0 + tid < m ? (int64_t)grow[B.roff + i0 + tid] - row_base : -1;
+        __syncthreads();
+        for (int e = tid; e < kMK * kMT; e += 256) {
+            const int col = e / kMK, row = e % kMK;
+            As[row][col] = (c0 + col < rb && i0 + row < m) ? Q[B.moff + (int64_t)(c0 + col) * B.ldm + i0 + row] : (TA)0;
+            const int rr = e / kMR, jj = e % kMR;
+            const int64_t g = s_g[rr];
+            Bs[rr][jj] = (g >= 0 && j0 + jj < R) ? (TA)(U[g * R + j0 + jj] * sc[j0 + jj].inv_beta) : (TA)0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kMK; ++kk) {
+            TA a[4], v[4];
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+            for (int j = 0; j < 4; ++j) v[j] = Bs[kk][tx * 4 + j];
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * v[j];
+        }
+        __syncthreads();
+    }
+    for (int i = 0; i < 4; ++i) {
+        const int col = c0 + ty * 4 + i;
+        if (col >= rb) continue;
+        for (int j = 0; j < 4; ++j) {
+            const int jj = j0 + tx * 4 + j;
+            if (jj < R) Z[(B.coff + col) * R + jj] = (double)acc[i][j];
+        }
+    }
+}
+
+__device__ inline int pow2_at_least(int R) {
+    int p = 1;
+    while (p < R) p <<= 1;
+    return p;
+}
+
+// per-CTA partial sums of one value per right-hand side (threads (sub, j))
+__device__ inline void m_partials(double v, int R, double *red, double *part) {
+    const int Rp = pow2_at_least(R), nsub = 256 / Rp;
+    red[threadIdx.x] = v;
+    __syncthreads();
+    if (threadIdx.x < R) {
+        double t = 0.0;
+        for (int s = 0; s < nsub; ++s) t += red[s * Rp + threadIdx.x];
+        part[(int64_t)blockIdx.x * R + threadIdx.x] = t;
+    }
+}
+
+// rows: u~ = sum over the row's block rows of T - alpha (u~ / beta), ||u~||^2
+__global__ void __launch_bounds__(256) k_m_rows(const InstRec *__restrict__ insts, const int32_t *__restrict__ rowlist,
+                                                const double *__restrict__ T, double *__restrict__ U,
+                                                const MScal *__restrict__ sc, int R, double *__restrict__ part) {
+    __shared__ double red[256];
+    const InstRec &I = insts[0];
+    const int Rp = pow2_at_least(R), j = threadIdx.x % Rp, sub = threadIdx.x / Rp, nsub = 256 / Rp;
+    double ss = 0.0;
+    if (j < R) {
+        const double al = sc[j].alpha, ib = sc[j].inv_beta;
+        for (int64_t g = (int64_t)blockIdx.x * nsub + sub; g < I.N; g += (int64_t)gridDim.x * nsub) {
+            const int32_t *lst = rowlist + I.rl_off + g * I.C;
+            double s = 0.0;
+            for (int e = 0; e < I.C; ++e) {
+                const int q = lst[e];
+                if (q >= 0) s += T[(int64_t)q * R + j];
+            }
+            const double u = s - al * (U[g * R + j] * ib);
+            U[g * R + j] = u;
+            ss = fma(u, u, ss);
+        }
+    }
+    m_partials(ss, R, red, part);
+}
+
+// columns: v~ = Z (first pass) or Z - beta (v~_old / alpha_old), ||v~||^2
+__global__ void __launch_bounds__(256) k_m_cols(const int32_t *__restrict__ rank,
+                                                int64_t n_cols, int K, const double *__restrict__ Z,
+                                                double *__restrict__ VT, const MScal *__restrict__ sc, int R,
+                                                int first, double *__restrict__ part) {
+    __shared__ double red[256];
+    const int Rp = pow2_at_least(R), j = threadIdx.x % Rp, sub = threadIdx.x / Rp, nsub = 256 / Rp;
+    double ss = 0.0;
+    if (j < R) {
+        const double be = sc[j].beta, ia = sc[j].inv_alpha;
+        for (int64_t s = (int64_t)blockIdx.x * nsub + sub; s < n_cols; s += (int64_t)gridDim.x * nsub) {
+            if ((int)(s % K) >= rank[s / K]) continue;
+            const double z = Z[s * R + j];
+            const double v = first ? z : z - be * (VT[s * R + j] * ia);
+            VT[s * R + j] = v;
+            ss = fma(v, v, ss);
+        }
+    }
+    m_partials(ss, R, red, part);
+}
+
+// the first nctas partial rows of part, summed in CTA order, per right-hand side
+__device__ inline double m_sum(const double *part, int nctas, int R, int j) {
+    double t = 0.0;
+    for (int c = 0; c < nctas; ++c) t += part[(int64_t)c * R + j];
+    return t;
+}
+
+// beta = ||u~|| and the stop flag of the previous update; ||y||^2 of it
+__global__ void k_m_beta(MScal *__restrict__ sc, const double *__restrict__ part, int nctas,
+                         const double *__restrict__ ypart, int ynctas, int R, int first) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= R) return;
+    MScal &q = sc[j];
+    const double b2 = m_sum(part, nctas, R, j);
+    if (!first && ypart) q.ynorm = sqrt(m_sum(ypart, ynctas, R, j));
+    if (q.done == 2) q.done = 1;
+    q.beta_old = q.beta;
+    q.beta = sqrt(b2);
+    q.inv_beta = q.beta > 0.0 ? 1.0 / q.beta : 0.0;
+    if (first) {
+        q.bnorm = q.beta;
+        q.phibar = q.beta;
+        q.rnorm = q.beta;
+        q.istop = 7;
+        q.itn = 0;
+        q.done = 0;
+    }
+}
+
+// alpha = ||v~||, then the plane rotation of the iteration, the estimates of
+// the 1982 paper and the stopping test (done = 2: this iteration's update is
+// applied, then the right-hand side stops)
+__global__ void k_m_alpha(MScal *__restrict__ sc, const double *__restrict__ part, int nctas, int R, int first,
+                          double atol, double btol, int max_iter) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= R) return;
+    MScal &q = sc[j];
+    const double al = sqrt(m_sum(part, nctas, R, j));
+    q.inv_alpha_old = q.inv_alpha;
+    q.alpha = al;
+    q.inv_alpha = al > 0.0 ? 1.0 / al : 0.0;
+    if (first) {
+        q.rhobar = al;
+        q.arnorm = al * q.beta;
+        q.anorm2 = al * al;
+        if (q.beta == 0.0 || al == 0.0) {
+            q.done = 1;
+            q.istop = 0;
+        }
+        return;
+    }
+    if (q.done) return;
+    q.anorm2 += al * al + q.beta * q.beta;
+    const double rho = sqrt(q.rhobar * q.rhobar + q.beta * q.beta);
+    const double ir = 1.0 / rho;
+    const double c = q.rhobar * ir, s = q.beta * ir;
+    const double theta = s * al;
+    q.rhobar = -c * al;
+    const double phi = c * q.phibar;
+    q.phibar = s * q.phibar;
+    q.phi_rho = phi * ir;
+    q.theta_rho = theta * ir;
+    q.c = c;
+    q.rnorm = q.phibar;
+    q.arnorm = q.phibar * al * fabs(c);
+    q.itn += 1;
+    const double anorm = sqrt(q.anorm2);
+    if (!isfinite(rho) || !isfinite(q.phibar)) {
+        q.done = 2;
+        q.istop = -1;
+    } else if (al == 0.0 || q.beta == 0.0) {
+        q.done = 2;
+        q.istop = 0;
+    } else if (q.rnorm <= btol * q.bnorm + atol * anorm * q.ynorm && (atol > 0.0 || btol > 0.0)) {
+        q.done = 2;
+        q.istop = 1;
+    } else if (q.arnorm <= atol * anorm * q.rnorm && atol > 0.0) {
+        q.done = 2;
+        q.istop = 2;
+    } else if (q.itn >= max_iter) {
+        q.done = 2;
+        q.istop = 7;
+    }
+}
+
+// v = v~ / alpha; first pass: w = v; then y += (phi/rho) w, w = v - (theta/rho) w; ||y||^2
+__global__ void __launch_bounds__(256) k_m_update(const int32_t *__restrict__ rank, int64_t n_cols, int K,
+                                                  const double *__restrict__ VT, double *__restrict__ W,
+                                                  double *__restrict__ Y, const MScal *__restrict__ sc, int R,
+                                                  int first, double *__restrict__ part) {
+    __shared__ double red[256];
+    const int Rp = pow2_at_least(R), j = threadIdx.x % Rp, sub = threadIdx.x / Rp, nsub = 256 / Rp;
+    double ss = 0.0;
+    if (j < R) {
+        const MScal &q = sc[j];
+        const bool live = first || q.done != 1;
+        for (int64_t s = (int64_t)blockIdx.x * nsub + sub; s < n_cols; s += (int64_t)gridDim.x * nsub) {
+            if ((int)(s % K) >= rank[s / K]) continue;
+            const int64_t o = s * R + j;
+            double yv = Y[o];
+            if (live) {
+                const double v = VT[o] * q.inv_alpha;
+                if (first) {
+                    W[o] = v;
+                } else {
+                    const double wo = W[o];
+                    yv = fma(q.phi_rho, wo, yv);
+                    Y[o] = yv;
+                    W[o] = fma(-q.theta_rho, wo, v);
+                }
+            }
+            ss = fma(yv, yv, ss);
+        }
+    }
+    m_partials(ss, R, red, part);
+}
+
+// out[j][s] = Y[s][j] (right-hand sides contiguous), and the reports
+__global__ void k_m_out(const double *__restrict__ Y, int64_t n_cols, int R, double *__restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_cols * R; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = e / R;
+        const int j = (int)(e % R);
+        out[(int64_t)j * n_cols + s] = Y[e];
+    }
+}
+
+__global__ void k_m_report(const MScal *__restrict__ sc, int R, rfm_lsqr_report *__restrict__ rep) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= R) return;
+    const MScal &q = sc[j];
+    rep[j].itn = q.itn;
+    rep[j].istop = q.istop;
+    rep[j].rnorm = q.rnorm;
+    rep[j].arnorm = q.arnorm;
+    rep[j].anorm = sqrt(q.anorm2);
+    rep[j].ynorm = q.ynorm;
+    rep[j].bnorm = q.bnorm;
+    rep[j].status = q.istop < 0 ? (double)RFM_ENUMERIC : 0.0;
+    rep[j].start = 0.0;
+    rep[j].r0norm = q.bnorm;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+static unsigned red_grid(int64_t n, int R) {
+    int Rp = 1;
+    while (Rp < R) Rp <<= 1;
+    const int64_t per = 256 / Rp;
+    int64_t g = (n + per - 1) / per;
+    return (unsigned)(g < 1 ? 1 : (g > kRedCtas ? kRedCtas : g));
+}
+
+rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, int R, const double *H,
+                             double *A, rfm_lsqr_report *rep, void *mws, cudaStream_t st) {
+    const Layout &L = P.L;
+    if (L.n_inst != 1 || (L.op != RFM_OP_Q32 && L.op != RFM_OP_Q64)) {
+        set_error("rfm_lsqr_multi: one instance with an explicit Q_hat operator (RFM_OP_Q32 or RFM_OP_Q64)");
+        return RFM_EINVAL;
+    }
+    if (R < 1 || R > kMaxRhs) {
+        set_error("rfm_lsqr_multi: 1..%d right-hand sides", kMaxRhs);
+        return RFM_EINVAL;
+    }
+    const MLayout M = multi_layout(P, R);
+    // work lists: (block, first row) of every 64-row tile, (block, first column) of every 64-column tile
+    std::vector<int32_t> fi, ti;
+    for (int64_t b = 0; b < L.n_blocks; ++b) {
+        for (int r = 0; r < P.blk[b].m; r += kMT) { fi.push_back((int32_t)b); fi.push_back(r); }
+        for (int c = 0; c < P.blk[b].K; c += kMT) { ti.push_back((int32_t)b); ti.push_back(c); }
+    }
+    int32_t *d_fi = ws_ptr<int32_t>(mws, M.off_fitems), *d_ti = ws_ptr<int32_t>(mws, M.off_titems);
+    if (!fi.empty())
+        RFM_CUDA_CHECK(cudaMemcpyAsync(d_fi, fi.data(), sizeof(int32_t) * fi.size(), cudaMemcpyHostToDevice, st));
+    if (!ti.empty())
+        RFM_CUDA_CHECK(cudaMemcpyAsync(d_ti, ti.data(), sizeof(int32_t) * ti.size(), cudaMemcpyHostToDevice, st));
+    // (copies from pageable host memory are staged before cudaMemcpyAsync returns)
+    double *VT = ws_ptr<double>(mws, M.off_vt), *W = ws_ptr<double>(mws, M.off_w), *Y = ws_ptr<double>(mws, M.off_y);
+    double *Z = ws_ptr<double>(mws, M.off_z), *U = ws_ptr<double>(mws, M.off_u), *T = ws_ptr<double>(mws, M.off_t);
+    double *part = ws_ptr<double>(mws, M.off_part), *ypart = part + (size_t)kRedCtas * R;
+    MScal *sc = ws_ptr<MScal>(mws, M.off_scal);
+    const size_t cols = (size_t)L.n_cols * R * sizeof(double);
+    RFM_CUDA_CHECK(cudaMemsetAsync(sc, 0, sizeof(MScal) * R, st));
+    RFM_CUDA_CHECK(cudaMemsetAsync(Y, 0, cols, st));
+    RFM_CUDA_CHECK(cudaMemsetAsync(VT, 0, cols, st));
+    RFM_CUDA_CHECK(cudaMemsetAsync(W, 0, cols, st));
+    const BlkRec *blks = ws_ptr<BlkRec>(ws, L.off_blk);
+    const int32_t *rank = ws_ptr<int32_t>(ws, L.off_rank), *grow = ws_ptr<int32_t>(ws, L.off_grow);
+    const InstRec *insts = ws_ptr<InstRec>(ws, L.off_inst);
+    const int32_t *rowlist = ws_ptr<int32_t>(ws, L.off_rowlist);
+    const int K = (int)P.inst[0].K;
+    const unsigned gr = red_grid(L.n_rows, R), gc = red_grid(L.n_cols, R), gs = (unsigned)((R + 63) / 64);
+    const dim3 gf((unsigned)M.n_fitems, (unsigned)((R + kMR - 1) / kMR)), gt((unsigned)M.n_titems, (unsigned)((R + kMR - 1) / kMR));
+    const bool q32 = L.op == RFM_OP_Q32;
+    const void *Q = q32 ? (const void *)ws_ptr<float>(ws, L.off_q32) : (const void *)ws_ptr<double>(ws, L.off_op);
+
+    auto fwd = [&]() -> rfm_status {
+        ProfScope ps("k_m_fwd", st);
+        if (q32)
+            k_m_fwd<float><<<gf, 256, 0, st>>>(blks, d_fi, rank, (const float *)Q, VT, sc, R, T);
+        else
+            k_m_fwd<double><<<gf, 256, 0, st>>>(blks, d_fi, rank, (const double *)Q, VT, sc, R, T);
+        RFM_CUDA_CHECK(cudaGetLastError());
+        return RFM_OK;
+    };
+    auto trans = [&]() -> rfm_status {
+        ProfScope ps("k_m_trans", st);
+        if (q32)
+            k_m_trans<float><<<gt, 256, 0, st>>>(blks, d_ti, rank, grow, (const float *)Q, U, sc, R, 0, Z);
+        else
+            k_m_trans<double><<<gt, 256, 0, st>>>(blks, d_ti, rank, grow, (const double *)Q, U, sc, R, 0, Z);
+        RFM_CUDA_CHECK(cudaGetLastError());
+        return RFM_OK;
+    };
+    rfm_status rc;
+    // initialisation: beta_1 u_1 = h, alpha_1 v_1 = A^T u_1, w_1 = v_1
+    {
+        ProfScope ps("k_m_load", st);
+        k_m_load<<<gr, 256, 0, st>>>(H, L.n_rows, R, U, part);
+        RFM_CUDA_CHECK(cudaGetLastError());
+    }
+    k_m_beta<<<gs, 64, 0, st>>>(sc, part, (int)gr, nullptr, 0, R, 1);
+    if ((rc = trans()) != RFM_OK) return rc;
+    k_m_cols<<<gc, 256, 0, st>>>(rank, L.n_cols, K, Z, VT, sc, R, 1, part);
+    k_m_alpha<<<gs, 64, 0, st>>>(sc, part, (int)gc, R, 1, opts->atol, opts->btol, opts->max_iter);
+    k_m_update<<<gc, 256, 0, st>>>(rank, L.n_cols, K, VT, W, Y, sc, R, 1, ypart);
+    RFM_CUDA_CHECK(cudaGetLastError());
+    for (int it = 0; it < opts->max_iter; ++it) {
+        if ((rc = fwd()) != RFM_OK) return rc;
+        {
+            ProfScope ps("k_m_rows", st);
+            k_m_rows<<<gr, 256, 0, st>>>(insts, rowlist, T, U, sc, R, part);
+        }
+        k_m_beta<<<gs, 64, 0, st>>>(sc, part, (int)gr, ypart, (int)gc, R, 0);
+        if ((rc = trans()) != RFM_OK) return rc;
+        {
+            ProfScope ps("k_m_cols", st);
+            k_m_cols<<<gc, 256, 0, st>>>(rank, L.n_cols, K, Z, VT, sc, R, 0, part);
+        }
+        k_m_alpha<<<gs, 64, 0, st>>>(sc, part, (int)gc, R, 0, opts->atol, opts->btol, opts->max_iter);
+        {
+            ProfScope ps("k_m_update", st);
+            k_m_update<<<gc, 256, 0, st>>>(rank, L.n_cols, K, VT, W, Y, sc, R, 0, ypart);
+        }
+        RFM_CUDA_CHECK(cudaGetLastError());
+    }
+    if (rep) {
+        k_m_report<<<gs, 64, 0, st>>>(sc, R, rep);
+        RFM_CUDA_CHECK(cudaGetLastError());
+    }
+    // a_j = S^-1 y_j per right-hand side
+    double *out = ws_ptr<double>(mws, M.off_out);
+    k_m_out<<<2048, 256, 0, st>>>(Y, L.n_cols, R, out);
+    RFM_CUDA_CHECK(cudaGetLastError());
+    for (int j = 0; j < R; ++j) {
+        rc = launch_coefficients(P, ws, out + (size_t)j * L.n_cols, A + (size_t)j * L.n_cols, st);
+        if (rc != RFM_OK) return rc;
+    }
+    return RFM_OK;
+}
+
+
+}  // namespace rfm

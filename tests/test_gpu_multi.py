@@ -1,0 +1,101 @@
+"""Many right-hand sides on one operator (rfm_rhs_many, rfm_lsqr_multi): the
+data sets of the parametric source family share M, R_hat and Q_hat, and one
+call runs LSQR for all of them.  Checks per data set:
+  * h against the oracle's (1e-13 of its largest entry);
+  * the FP64 path (explicit FP64 Q_hat): the iterate after k steps against
+    the oracle's LSQR on that data set alone (1e-8 relative), and against the
+    single-data-set solver on the same workspace (1e-10);
+  * the FP32 path (FP32 Q_hat): against the single-data-set FP32 solver at
+    the same iteration count: the residual estimate and the FP64 residual of
+    the assembled system at the coefficients (1e-5, the mixed path's
+    tolerance);
+  * the stopping test per data set (a data set with h = 0 stops at once).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rfm():
+    from paper_2506_17626_gb300 import build
+    build.build()
+    import paper_2506_17626_gb300 as R
+    return R
+
+
+def _family(n, S=4, K=20, grid=24):
+    return [synth.param5(*synth.param5_draw(s), S=S, K=K, n=grid, delta=2.0) for s in range(n)]
+
+
+@pytest.mark.parametrize("op,nrhs", [("q64", 5), ("q64", 70), ("q32", 9)])
+def test_multi_rhs_matches_single_solves_and_oracle(rfm, op, nrhs):
+    probs = _family(nrhs)
+    prm = synth.feature_params(probs[0])
+    d = torch.from_numpy(prm.ravel()).cuda()
+    asm = "fp64" if op == "q64" else "fp32"
+    S = rfm.System([probs[0]], asm=asm, op=op, tol=1e-6)
+    S.assemble(d)
+    rank = S.filter().cpu().numpy()
+    H = S.rhs_many(probs)
+    k = 25
+    A, rep = S.solve_multi(H, atol=0, btol=0, max_iter=k)
+    torch.cuda.synchronize()
+    A = A.cpu().numpy()
+    B0 = oracle.assemble(probs[0], prm)
+    F = oracle.filter_blocks(B0, 1e-6)
+    for j in sorted({0, 1, nrhs // 2, nrhs - 1}):
+        p = probs[j]
+        S1 = rfm.System([p], asm=asm, op=op, tol=1e-6)
+        S1.assemble(d)
+        S1.filter()
+        a1, rep1 = S1.solve(atol=0, btol=0, max_iter=k)
+        a1 = a1.cpu().numpy()
+        r, r1 = rfm.report_dict(rep, j), rfm.report_dict(rep1)
+        assert r["itn"] == k and r["istop"] == 7
+        h1 = S1.rhs().cpu().numpy()
+        assert np.abs(H[j].cpu().numpy() - h1).max() <= 1e-13 * np.abs(h1).max()
+        if op == "q64":
+            assert np.linalg.norm(A[j] - a1) <= 1e-10 * np.linalg.norm(a1)
+            Bj = oracle.assemble(p, prm)
+            assert np.abs(H[j].cpu().numpy() - Bj.h).max() <= 1e-13 * np.abs(Bj.h).max()
+            So = oracle.build_system(Bj, F, mode=0)
+            ref = So.lsqr(Bj.h, atol=0, btol=0, max_iter=k)
+            a_o = So.coefficients(ref["y"])
+            assert np.linalg.norm(A[j] - a_o) <= 1e-8 * np.linalg.norm(a_o), j
+            assert r["rnorm"] == pytest.approx(ref["rnorm"], rel=1e-8)
+        else:
+            # FP32 products: the two solvers round in different orders; compare
+            # what does not amplify that rounding by kappa(R_hat): the residual
+            # estimate and the residual of the assembled system at a (FP64)
+            assert r["rnorm"] == pytest.approx(r1["rnorm"], rel=1e-5)
+            res_m = float(S1.residual(torch.from_numpy(A[j]).cuda())[0])
+            res_1 = float(S1.residual(torch.from_numpy(a1).cuda())[0])
+            assert res_m == pytest.approx(res_1, rel=1e-5), j
+
+
+def test_multi_rhs_stopping_per_data_set(rfm):
+    probs = _family(3)
+    prm = synth.feature_params(probs[0])
+    d = torch.from_numpy(prm.ravel()).cuda()
+    S = rfm.System([probs[0]], asm="fp64", op="q64", tol=1e-6)
+    S.assemble(d)
+    S.filter()
+    H = S.rhs_many(probs)
+    H[1].zero_()
+    A, rep = S.solve_multi(H, atol=1e-6, btol=1e-6, max_iter=2000)
+    r0, r1, r2 = (rfm.report_dict(rep, j) for j in range(3))
+    assert r1["istop"] == 0 and r1["itn"] == 0 and torch.count_nonzero(A[1]) == 0
+    for r in (r0, r2):
+        assert r["istop"] in (1, 2) and 0 < r["itn"] < 2000
+    # the same stopping point as the single solver
+    S1 = rfm.System([probs[2]], asm="fp64", op="q64", tol=1e-6)
+    S1.assemble(d)
+    S1.filter()
+    _, rep1 = S1.solve(atol=1e-6, btol=1e-6, max_iter=2000)
+    assert abs(rfm.report_dict(rep1)["itn"] - r2["itn"]) <= 1
