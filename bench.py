@@ -28,8 +28,9 @@ says so.  Both paths are timed; "value" is the mixed path.
 At N = 1 the line also carries, each measured in the same run: the 2D
 Poisson workload's time to its target ("poisson2d"), the time to 1e-6
 relative L2 error on the 1D Poisson workload, which converges, for the FP64
-operators and the mixed path with refinement ("poisson1d"), 64 uneven
-instances in one launch per call ("batched"), the learned warm start
+operators and the mixed path with refinement ("poisson1d"), many data sets
+of a source family on one operator ("multi_rhs"), 64 uneven instances in
+memory-budgeted waves ("batched"), the learned warm start
 ("learned"), and the oracle timed on a sample of the workload on one core and
 on all cores ("cpu_baseline", "cpu_baseline_all_cores").  --impl reference
 times the oracle alone.
@@ -460,6 +461,9 @@ def run_gpu(args):
         torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_poisson1d:
         out["poisson1d"] = guarded(run_poisson1d, args, dev)
+    if rank == 0 and world == 1 and args.multi_rhs > 0:
+        out["multi_rhs"] = guarded(run_multi_rhs, args, dev)
+        torch.cuda.empty_cache()
     if rank == 0 and world == 1 and args.batched > 0:
         out["batched"] = guarded(run_batched, args, dev)
         torch.cuda.empty_cache()
@@ -576,6 +580,53 @@ def run_batched(args, dev):
         "qr_gflops_algorithmic": qr_fl / (totals["filter"] * 1e-3) / 1e9,
         "rel_l2": {"median": float(np.median(rel)), "max": float(rel.max())},
     }
+
+
+def run_multi_rhs(args, dev):
+    """Many right-hand sides on one operator: the parametric source family on
+    the 20 x 20 x 300 decomposition (overlap ratio 1.25, 360^2 interior +
+    1440 boundary rows, mixed path, filter tol 1e-6), nrhs data sets solved
+    at once (rfm_lsqr_multi) against one data set at a time (rfm_lsqr_solve),
+    a fixed number of LSQR iterations each; CUDA events after one untimed
+    call of each."""
+    import torch
+    import paper_2506_17626_gb300 as R
+    nrhs, iters = args.multi_rhs, args.multi_iters
+    probs = [synth.param5(*synth.param5_draw(s), S=20, K=300, n=360, delta=1.25) for s in range(nrhs)]
+    prm = torch.from_numpy(synth.feature_params(probs[0]).ravel()).to(dev)
+    out = {"workload": f"2D Poisson source family f = sin(a pi x) sin(b pi y) + c sin(d pi x + e pi y) on 20x20 "
+                       f"subdomains, delta 1.25, K=300, 360^2 + 1440 rows, filter tol {TOL:g}; {nrhs} data sets, "
+                       f"{iters} LSQR iterations", "nrhs": nrhs, "iterations": iters}
+    for asm, op in (("fp32", "q32"), ("fp64", "q64")):
+        S = R.System([probs[0]], asm=asm, op=op, tol=TOL, device=str(dev))
+        S.assemble(prm)
+        rank = S.filter()
+        H = S.rhs_many(probs)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        S.solve_multi(H, atol=0, btol=0, max_iter=2)
+        ev[0].record()
+        A, rep = S.solve_multi(H, atol=0, btol=0, max_iter=iters)
+        ev[1].record()
+        S.solve(atol=0, btol=0, max_iter=2)
+        ev[2].record()
+        S.solve(atol=0, btol=0, max_iter=iters)
+        ev[3].record()
+        torch.cuda.synchronize()
+        m = S.block_table()[0]
+        r = rank.cpu().numpy()
+        nnz = float(np.sum(m * r))
+        t_multi = ev[0].elapsed_time(ev[1])
+        t_single = ev[2].elapsed_time(ev[3])
+        flops = 4.0 * nnz * nrhs * iters
+        out[op] = {"ms_multi": t_multi, "ms_single_one_data_set": t_single,
+                   "rhs_iterations_per_s_multi": nrhs * iters / (t_multi * 1e-3),
+                   "rhs_iterations_per_s_single": iters / (t_single * 1e-3),
+                   "speedup_per_data_set": nrhs * t_single / t_multi,
+                   "block_product_tflops": flops / (t_multi * 1e-3) / 1e12,
+                   "nnz_q_hat": nnz}
+        del S, H, A
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_poisson1d(args, dev):
@@ -950,6 +1001,8 @@ def main():
     ap.add_argument("--batched", type=int, default=64, help="instances of the batched section (0 skips it)")
     ap.add_argument("--no-poisson1d", action="store_true", help="skip the 1D time-to-1e-6 section")
     ap.add_argument("--batched-iters", type=int, default=500)
+    ap.add_argument("--multi-rhs", type=int, default=64, help="data sets of the multi-right-hand-side section (0 skips)")
+    ap.add_argument("--multi-iters", type=int, default=200)
     ap.add_argument("--batched-points", default="40,60", help="points per subdomain edge of the batched family")
     ap.add_argument("--batched-budget", type=float, default=0.6,
                     help="device memory budget of one wave of the batched section (fraction of 288 GB)")
