@@ -210,6 +210,12 @@ def set_qr_order(largest_first: bool):
     check("rfm_set_option", load().rfm_set_option(5, 1 if largest_first else 0))
 
 
+def set_lsqr_lag(tenths: int):
+    """Lag of the explicit-operator LSQR kernel's row tiles behind their
+    block's column chunks, in tenths of a grid pass (RFM_OPT_LSQR_LAG)."""
+    check("rfm_set_option", load().rfm_set_option(7, int(tenths)))
+
+
 def set_qr_double_float(on):
     """Factor FP32-assembled blocks with double-float arithmetic (True or 1,
     the default) or with FP64 arithmetic (False or 0); 2 also puts

@@ -28,6 +28,7 @@ void set_lsqr_stall(int v);
 void set_mlp_tensor_cores(int on);
 void set_qr_order(int on);
 void set_mlp_tc_threads(int threads);
+void set_lsqr_lag(int tenths);
 rfm_status launch_eval_noalloc(const HostPlan &P, const double *params, const double *a, const double *X,
                                const int64_t *pt_off, double *u, double *err, cudaStream_t st);
 rfm_status launch_eval(const HostPlan &P, void *ws, const double *params, const double *a, const double *X,
@@ -349,6 +350,10 @@ rfm_status rfm_set_option(int option, int value) {
     }
     if (option == RFM_OPT_QR_ORDER && (value == 0 || value == 1)) {
         set_qr_order(value);
+        return RFM_OK;
+    }
+    if (option == RFM_OPT_LSQR_LAG && value >= 1 && value <= 100) {
+        set_lsqr_lag(value);
         return RFM_OK;
     }
     if (option == RFM_OPT_MLP_TC_THREADS && (value == 256 || value == 512)) {

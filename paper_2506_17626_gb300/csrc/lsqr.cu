@@ -846,6 +846,8 @@ __device__ __forceinline__ double ld_hint(const double *p, uint64_t pol) {
 
 static int g_lsqr_stall = 0;
 void set_lsqr_stall(int v) { g_lsqr_stall = v; }
+static int g_lsqr_lag = 16;   // lag of the fused products' tiles, tenths of a grid round of items
+void set_lsqr_lag(int v) { g_lsqr_lag = v; }
 
 template <typename TA>
 struct TileSmem {
@@ -917,7 +919,7 @@ __global__ void __launch_bounds__(1024) k_build_items(const InstRec *__restrict_
                                                       int *__restrict__ n_items, ColItem *__restrict__ fitems,
                                                       int *__restrict__ n_fitems, ColItem *__restrict__ titems,
                                                       int *__restrict__ n_titems, int elem_bytes, int64_t t_cap,
-                                                      int twarps) {
+                                                      int twarps, int lag_tenths) {
     __shared__ int scan[1024];
     __shared__ int carry;
     const int tid = threadIdx.x;
@@ -1006,9 +1008,10 @@ __global__ void __launch_bounds__(1024) k_build_items(const InstRec *__restrict_
     // product of the next): block b's column chunks (ceil(r / cc), kind T:
     // nc = columns) and its 32-row tiles (kind F: c0 = first row, nc = -r).
     // A block's tiles need the vector its chunks produce, so they follow its
-    // chunks with a lag of L blocks, chosen so that about 1.6 items per warp
-    // of the grid pass in between: the tiles rarely wait, and the block
-    // (re-read by its tiles, kept by an evict-last hint) is still in L2.
+    // chunks with a lag of L blocks, chosen so that about lag_tenths / 10
+    // items per warp of the grid pass in between (1.6 by default): the tiles
+    // rarely wait, and the block (re-read by its tiles, kept by an
+    // evict-last hint) is still in L2 when the blocks are small enough.
     // Slot s holds the chunks of block s and the tiles of block s - L.
     __shared__ int s_tot;
     __syncthreads();
@@ -1021,7 +1024,10 @@ __global__ void __launch_bounds__(1024) k_build_items(const InstRec *__restrict_
     }
     __syncthreads();
     const int tot = s_tot;
-    const int lag = n_blocks > 0 && tot > 0 ? (int)min((int64_t)n_blocks, ((int64_t)twarps * 8 / 5 * n_blocks + tot - 1) / tot) : 0;
+    const int lag = n_blocks > 0 && tot > 0
+                        ? (int)min((int64_t)n_blocks,
+                                   ((int64_t)twarps * lag_tenths / 10 * n_blocks + tot - 1) / tot)
+                        : 0;
     if (tid == 0) carry = 0;
     __syncthreads();
     const int n_slots = n_blocks + lag;
@@ -1897,7 +1903,7 @@ static rfm_status run_lsqr_tiles(const HostPlan &P, void *ws, LsqrArgs &args, cu
         ProfScope ps("k_build_items", st);
         k_build_items<<<1, 1024, 0, st>>>(args.insts, args.n_inst, args.blks, args.n_blocks, args.rank, items, nitems,
                                           ws_ptr<ColItem>(ws, L.off_fitems), ws_ptr<int>(ws, L.off_nfitems), titems,
-                                          ntitems, (int)sizeof(TA), L.n_t_items, G * (kThreads / 32));
+                                          ntitems, (int)sizeof(TA), L.n_t_items, G * (kThreads / 32), g_lsqr_lag);
         RFM_CUDA_CHECK(cudaGetLastError());
     }
     TA *tu = ws_ptr<TA>(ws, L.off_tu);
