@@ -525,11 +525,12 @@ int rfm_profile_read(const char **names, int64_t *launches, double *ms, int max)
  *    kernels, 512 (default: four threads per sample, each with 32 of the 128
  *    columns) or 256 (two per sample).  The results are the same.
  *  RFM_OPT_LSQR_LAG: how far (in tenths of one pass of the grid's warps over
- *    the work list, 1..100, default 16) a block's row tiles of the forward
- *    product follow its column chunks of the transposed product in the
- *    explicit-operator LSQR kernel.  Shorter lags keep the block in L2 for
- *    its second read, longer ones keep the tiles from waiting on the chunks;
- *    the iterates agree to rounding (the per-warp partial sums change). */
+ *    the work list, 1..100) a block's row tiles of the forward product follow
+ *    its column chunks of the transposed product in the explicit-operator
+ *    LSQR kernel; 0 (default) takes 1.6 passes, capped so that about 120 MB
+ *    of operator lie in between.  Shorter lags keep the block in L2 for its
+ *    second read, longer ones keep the tiles from waiting on the chunks; the
+ *    iterates agree to rounding (the per-warp partial sums change). */
 enum {
     RFM_OPT_FILTER_KERNEL = 0,
     RFM_OPT_AUTOTUNE = 1,

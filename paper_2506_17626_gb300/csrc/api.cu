@@ -352,7 +352,7 @@ rfm_status rfm_set_option(int option, int value) {
         set_qr_order(value);
         return RFM_OK;
     }
-    if (option == RFM_OPT_LSQR_LAG && value >= 1 && value <= 100) {
+    if (option == RFM_OPT_LSQR_LAG && value >= 0 && value <= 100) {
         set_lsqr_lag(value);
         return RFM_OK;
     }

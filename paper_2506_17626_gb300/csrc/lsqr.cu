@@ -846,7 +846,7 @@ __device__ __forceinline__ double ld_hint(const double *p, uint64_t pol) {
 
 static int g_lsqr_stall = 0;
 void set_lsqr_stall(int v) { g_lsqr_stall = v; }
-static int g_lsqr_lag = 16;   // lag of the fused products' tiles, tenths of a grid round of items
+static int g_lsqr_lag = 0;   // lag of the fused products' tiles, tenths of a grid round of items (0: automatic)
 void set_lsqr_lag(int v) { g_lsqr_lag = v; }
 
 template <typename TA>
@@ -1014,19 +1014,33 @@ __global__ void __launch_bounds__(1024) k_build_items(const InstRec *__restrict_
     // evict-last hint) is still in L2 when the blocks are small enough.
     // Slot s holds the chunks of block s and the tiles of block s - L.
     __shared__ int s_tot;
+    __shared__ unsigned long long s_bytes;
     __syncthreads();
-    if (tid == 0) s_tot = 0;
+    if (tid == 0) {
+        s_tot = 0;
+        s_bytes = 0ull;
+    }
     __syncthreads();
     for (int b = tid; b < n_blocks; b += 1024) {
         const int r = rank ? rank[b] : blks[b].K;
         const int cc = tchunk_cols(blks[b].ldm, elem_bytes);
         atomicAdd(&s_tot, (r + cc - 1) / cc + (blks[b].ldm + 31) / 32);
+        atomicAdd(&s_bytes, 2ull * (unsigned long long)blks[b].ldm * (unsigned long long)r * elem_bytes);
     }
     __syncthreads();
     const int tot = s_tot;
+    // lag in items: lag_tenths / 10 passes of the grid's warps, or (lag_tenths
+    // = 0) that of 1.6 passes capped so that about 120 MB of operator pass
+    // between a block's chunks and its tiles (blocks of a few MB need the
+    // cap to be re-read from L2; small blocks keep the 1.6 passes)
+    int64_t lag_items = (int64_t)twarps * (lag_tenths > 0 ? lag_tenths : 16) / 10;
+    if (lag_tenths == 0 && tot > 0 && s_bytes > 0) {
+        const double per_item = (double)s_bytes / (double)tot;
+        const int64_t cap = (int64_t)(120.0e6 / per_item);
+        lag_items = lag_items < cap ? lag_items : (cap > 1 ? cap : 1);
+    }
     const int lag = n_blocks > 0 && tot > 0
-                        ? (int)min((int64_t)n_blocks,
-                                   ((int64_t)twarps * lag_tenths / 10 * n_blocks + tot - 1) / tot)
+                        ? (int)min((int64_t)n_blocks, (lag_items * n_blocks + tot - 1) / tot)
                         : 0;
     if (tid == 0) carry = 0;
     __syncthreads();

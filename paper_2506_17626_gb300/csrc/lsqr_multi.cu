@@ -273,15 +273,27 @@ __device__ inline double m_sum(const double *part, int nctas, int R, int j) {
     return t;
 }
 
-// beta = ||u~|| and the stop flag of the previous update; ||y||^2 of it
+// The stopping test of the previous iteration k (its estimates, ||y_k|| from
+// its update's partials; the tests of rfm_lsqr_solve), then beta = ||u~||.
 __global__ void k_m_beta(MScal *__restrict__ sc, const double *__restrict__ part, int nctas,
-                         const double *__restrict__ ypart, int ynctas, int R, int first) {
+                         const double *__restrict__ ypart, int ynctas, int R, int first, double atol, double btol) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= R) return;
     MScal &q = sc[j];
     const double b2 = m_sum(part, nctas, R, j);
     if (!first && ypart) q.ynorm = sqrt(m_sum(ypart, ynctas, R, j));
     if (q.done == 2) q.done = 1;
+    if (!first && !q.done && q.itn > 0) {
+        const double anorm = sqrt(q.anorm2);
+        if (q.rnorm <= btol * q.bnorm + atol * anorm * q.ynorm) {
+            q.done = 1;
+            q.istop = 1;
+        } else if (q.arnorm <= atol * anorm * q.rnorm) {
+            q.done = 1;
+            q.istop = 2;
+        }
+    }
+    if (q.done) return;
     q.beta_old = q.beta;
     q.beta = sqrt(b2);
     q.inv_beta = q.beta > 0.0 ? 1.0 / q.beta : 0.0;
@@ -295,30 +307,32 @@ __global__ void k_m_beta(MScal *__restrict__ sc, const double *__restrict__ part
     }
 }
 
-// alpha = ||v~||, then the plane rotation of the iteration, the estimates of
-// the 1982 paper and the stopping test (done = 2: this iteration's update is
-// applied, then the right-hand side stops)
+// alpha = ||v~||, then the plane rotation of the iteration and the estimates
+// of the 1982 paper (||B_k||_F^2 gains alpha_k^2 + beta_{k+1}^2); an exact
+// stop (alpha or beta zero) or a non-finite scalar ends the right-hand side
+// after this iteration's update (done = 2)
 __global__ void k_m_alpha(MScal *__restrict__ sc, const double *__restrict__ part, int nctas, int R, int first,
                           double atol, double btol, int max_iter) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= R) return;
     MScal &q = sc[j];
+    if (!first && q.done) return;
     const double al = sqrt(m_sum(part, nctas, R, j));
+    const double al_old = q.alpha;
     q.inv_alpha_old = q.inv_alpha;
     q.alpha = al;
     q.inv_alpha = al > 0.0 ? 1.0 / al : 0.0;
     if (first) {
         q.rhobar = al;
         q.arnorm = al * q.beta;
-        q.anorm2 = al * al;
+        q.anorm2 = 0.0;
         if (q.beta == 0.0 || al == 0.0) {
             q.done = 1;
             q.istop = 0;
         }
         return;
     }
-    if (q.done) return;
-    q.anorm2 += al * al + q.beta * q.beta;
+    q.anorm2 += al_old * al_old + q.beta * q.beta;
     const double rho = sqrt(q.rhobar * q.rhobar + q.beta * q.beta);
     const double ir = 1.0 / rho;
     const double c = q.rhobar * ir, s = q.beta * ir;
@@ -339,16 +353,11 @@ __global__ void k_m_alpha(MScal *__restrict__ sc, const double *__restrict__ par
     } else if (al == 0.0 || q.beta == 0.0) {
         q.done = 2;
         q.istop = 0;
-    } else if (q.rnorm <= btol * q.bnorm + atol * anorm * q.ynorm && (atol > 0.0 || btol > 0.0)) {
-        q.done = 2;
-        q.istop = 1;
-    } else if (q.arnorm <= atol * anorm * q.rnorm && atol > 0.0) {
-        q.done = 2;
-        q.istop = 2;
-    } else if (q.itn >= max_iter) {
-        q.done = 2;
-        q.istop = 7;
     }
+    (void)anorm;
+    (void)atol;
+    (void)btol;
+    (void)max_iter;
 }
 
 // v = v~ / alpha; first pass: w = v; then y += (phi/rho) w, w = v - (theta/rho) w; ||y||^2
@@ -488,7 +497,7 @@ rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *o
         k_m_load<<<gr, 256, 0, st>>>(H, L.n_rows, R, U, part);
         RFM_CUDA_CHECK(cudaGetLastError());
     }
-    k_m_beta<<<gs, 64, 0, st>>>(sc, part, (int)gr, nullptr, 0, R, 1);
+    k_m_beta<<<gs, 64, 0, st>>>(sc, part, (int)gr, nullptr, 0, R, 1, opts->atol, opts->btol);
     if ((rc = trans()) != RFM_OK) return rc;
     k_m_cols<<<gc, 256, 0, st>>>(rank, L.n_cols, K, Z, VT, sc, R, 1, part);
     k_m_alpha<<<gs, 64, 0, st>>>(sc, part, (int)gc, R, 1, opts->atol, opts->btol, opts->max_iter);
@@ -500,7 +509,7 @@ rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *o
             ProfScope ps("k_m_rows", st);
             k_m_rows<<<gr, 256, 0, st>>>(insts, rowlist, T, U, sc, R, part);
         }
-        k_m_beta<<<gs, 64, 0, st>>>(sc, part, (int)gr, ypart, (int)gc, R, 0);
+        k_m_beta<<<gs, 64, 0, st>>>(sc, part, (int)gr, ypart, (int)gc, R, 0, opts->atol, opts->btol);
         if ((rc = trans()) != RFM_OK) return rc;
         {
             ProfScope ps("k_m_cols", st);
