@@ -455,6 +455,13 @@ rfm_status rfm_mlp_train(const rfm_mlp *net, float *d_theta, float *d_m, float *
 rfm_status rfm_block_info(const rfm_problem *probs, int n_inst, const rfm_config *cfg, int64_t block,
                           int64_t *m, int64_t *ld, int64_t *moff, int64_t *roff);
 
+/* The global rows (across instances) of block b's rows I_j (Eq. (6)), in
+ * the block's row order: interior rows, then its face rows (host array of
+ * |I_j| entries).  Host only; the partition of a system over several
+ * processes is built from it. */
+rfm_status rfm_block_rows(const rfm_problem *probs, int n_inst, const rfm_config *cfg, int64_t block,
+                          int64_t *rows);
+
 /* rfm_block_info for every block at once: host arrays of n_blocks entries
  * (any may be NULL). */
 rfm_status rfm_block_table(const rfm_problem *probs, int n_inst, const rfm_config *cfg, int64_t *m, int64_t *ld,

@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH):
         "rfm_lsqr_solve": [P, C.c_int, CF, C.POINTER(RfmLsqrOpts), vp, vp, vp, vp, vp, C.c_size_t, vp],
         "rfm_eval": [P, C.c_int, CF, vp, vp, vp, vp, vp, vp, vp, C.c_size_t, vp],
         "rfm_residual": [P, C.c_int, CF, vp, vp, vp, vp, C.c_size_t, vp],
+        "rfm_block_rows": [P, C.c_int, CF, i64, vp],
         "rfm_lsqr_multi_size": [P, CF, C.c_int, C.POINTER(C.c_size_t)],
         "rfm_rhs_many": [P, C.c_int, CF, vp, vp, C.c_size_t, vp],
         "rfm_lsqr_multi": [P, CF, C.POINTER(RfmLsqrOpts), C.c_int, vp, vp, vp, vp, C.c_size_t, vp, C.c_size_t, vp],

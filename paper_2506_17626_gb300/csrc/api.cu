@@ -447,6 +447,20 @@ rfm_status rfm_block_table(const rfm_problem *probs, int n_inst, const rfm_confi
     RFM_GUARD_END
 }
 
+rfm_status rfm_block_rows(const rfm_problem *probs, int n_inst, const rfm_config *cfg, int64_t block,
+                          int64_t *rows) {
+    RFM_GUARD_BEGIN
+    Plan P(probs, n_inst, cfg);
+    if (!P.ok) return P.rc;
+    if (block < 0 || block >= P.p.L.n_blocks || !rows) {
+        set_error("rfm_block_rows: block %lld out of range or rows NULL", (long long)block);
+        return RFM_EINVAL;
+    }
+    host_block_rows(P.p, block, rows);
+    return RFM_OK;
+    RFM_GUARD_END
+}
+
 rfm_status rfm_qr_order(const rfm_problem *probs, int n_inst, const rfm_config *cfg, int32_t *order) {
     RFM_GUARD_BEGIN
     Plan P(probs, n_inst, cfg);

@@ -150,6 +150,7 @@ constexpr int kColTile = 8;    // columns of a transpose (A^T u) work item (one 
 rfm_status build_plan(const rfm_problem *probs, int n_inst, const rfm_config *cfg, HostPlan *out, char *err,
                       size_t errlen);
 void free_plan(HostPlan *p);
+void host_block_rows(const HostPlan &P, int64_t b, int64_t *rows);
 
 void set_error(const char *fmt, ...);
 

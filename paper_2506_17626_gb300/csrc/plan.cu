@@ -367,6 +367,41 @@ rfm_status build_plan(const rfm_problem *probs, int n_inst, const rfm_config *cf
     return RFM_OK;
 }
 
+// Global rows (across instances) of block b's rows, in block-row order: the
+// index arithmetic of block_row_point (device.cuh) without the coordinates.
+void host_block_rows(const HostPlan &P, int64_t b, int64_t *rows) {
+    const BlkRec &B = P.blk[b];
+    const InstRec &I = P.inst[B.inst];
+    for (int lr = 0; lr < B.m; ++lr) {
+        int64_t r = 0, stride = 1;
+        if (lr < B.n_int) {
+            int l = lr;
+            for (int i = 0; i < I.dim; ++i) {
+                const int g = B.box_lo[i] + l % B.box_n[i];
+                l /= B.box_n[i];
+                r += g * stride;
+                stride *= I.n[i];
+            }
+        } else {
+            int f = -1;
+            for (int ff = 0; ff < I.nfaces; ++ff)
+                if (B.face_off[ff] >= 0 && B.face_off[ff] <= lr) f = ff;
+            int nd, side;
+            face_dims(I.pde, f, &nd, &side);
+            int l = lr - B.face_off[f];
+            r = I.face_row0[f];
+            for (int i = 0; i < I.dim; ++i) {
+                if (i == nd) continue;
+                const int g = B.box_lo[i] + l % B.box_n[i];
+                l /= B.box_n[i];
+                r += g * stride;
+                stride *= I.n[i];
+            }
+        }
+        rows[lr] = I.row0 + r;
+    }
+}
+
 void free_plan(HostPlan *p) {
     free(p->inst);
     free(p->blk);

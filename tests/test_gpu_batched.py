@@ -113,9 +113,11 @@ def test_batch_matches_oracle_per_instance(rfm):
         ref = So.lsqr(B.h, atol=0, btol=0, max_iter=k)
         yg = np.concatenate([y[c0 + j * p.K: c0 + j * p.K + f.rank] for j, f in enumerate(F)])
         assert np.linalg.norm(yg - ref["y"]) <= 1e-8 * np.linalg.norm(ref["y"]), i
-        # the residual estimate (these blocks have fewer rows than features, so
-        # the systems are consistent and the residual falls to rounding level)
-        assert abs(rfm.report_dict(rep, i)["rnorm"] - ref["rnorm"]) <= 1e-8 * ref["rnorm"] + 1e-12 * np.linalg.norm(B.h)
+        # the residual estimate phibar ~ ||h - A y_k||: a 1e-8 relative change
+        # of the recurrence moves it by at most about 1e-8 ||h|| (it ranges from
+        # rounding level, on instances whose blocks have fewer rows than
+        # features, to 2e-7 ||h||)
+        assert abs(rfm.report_dict(rep, i)["rnorm"] - ref["rnorm"]) <= 1e-8 * np.linalg.norm(B.h)
         # the ansatz of the oracle's coefficients, instance by instance in one call
         a_o = So.coefficients(ref["y"])
         X = oracle.test_grid(p, [13, 13])

@@ -80,6 +80,14 @@ def test_multi_rhs_matches_single_solves_and_oracle(rfm, op, nrhs):
 
 
 def test_multi_rhs_stopping_per_data_set(rfm):
+    """Each data set stops on its own test: a zero right-hand side at once,
+    the others when the reported estimates meet the 1982 paper's tests
+    (||A^T r|| <= atol ||A|| ||r|| here).  Where that test is met depends on
+    rounding: the ratio flattens near 1e-6 for tens of iterations, and the
+    oracle itself stops at 628 iterations with the explicit Q_hat and at 695
+    with R_hat^-1 substitution (the same operator on paper) for data set 2.
+    So the single and the many-data-set solvers are held to the oracle's
+    stopping count within 10%, not to each other's iteration."""
     probs = _family(3)
     prm = synth.feature_params(probs[0])
     d = torch.from_numpy(prm.ravel()).cuda()
@@ -88,14 +96,21 @@ def test_multi_rhs_stopping_per_data_set(rfm):
     S.filter()
     H = S.rhs_many(probs)
     H[1].zero_()
-    A, rep = S.solve_multi(H, atol=1e-6, btol=1e-6, max_iter=2000)
+    atol = btol = 1e-6
+    A, rep = S.solve_multi(H, atol=atol, btol=btol, max_iter=2000)
     r0, r1, r2 = (rfm.report_dict(rep, j) for j in range(3))
     assert r1["istop"] == 0 and r1["itn"] == 0 and torch.count_nonzero(A[1]) == 0
     for r in (r0, r2):
         assert r["istop"] in (1, 2) and 0 < r["itn"] < 2000
-    # the same stopping point as the single solver
+        met1 = r["rnorm"] <= btol * r["bnorm"] + atol * r["anorm"] * r["ynorm"]
+        met2 = r["arnorm"] <= atol * r["anorm"] * r["rnorm"]
+        assert met1 if r["istop"] == 1 else met2, r
     S1 = rfm.System([probs[2]], asm="fp64", op="q64", tol=1e-6)
     S1.assemble(d)
     S1.filter()
-    _, rep1 = S1.solve(atol=1e-6, btol=1e-6, max_iter=2000)
-    assert abs(rfm.report_dict(rep1)["itn"] - r2["itn"]) <= 1
+    _, rep1 = S1.solve(atol=atol, btol=btol, max_iter=2000)
+    B = oracle.assemble(probs[2], prm)
+    ref = oracle.build_system(B, oracle.filter_blocks(B, 1e-6), mode=1).lsqr(B.h, atol=atol, btol=btol,
+                                                                            max_iter=2000)
+    for itn in (r2["itn"], rfm.report_dict(rep1)["itn"]):
+        assert abs(itn - ref["itn"]) <= 0.1 * ref["itn"], (itn, ref["itn"])
