@@ -5,7 +5,8 @@ amplitude pi^2 (a^2 + b^2)), and LSQR started from the fitted prediction.
 
 What the test asserts: the training lowers the loss; the fitted prediction
 for solved instances starts far inside the zero start's error (which is 1 by
-definition); and LSQR from it runs.  What it reports: the error trajectories
+definition); the solver keeps that start (its residual is below ||h||, the
+rule that otherwise falls back to zero) and LSQR from it runs.  What it reports: the error trajectories
 from both starts.  On these 2D systems the measured gain does not survive
 the first LSQR iterations (the preconditioned unknowns map to function values
 through a badly conditioned evaluation, so the residual-driven iterations
@@ -102,13 +103,18 @@ def test_learned_warm_start_end_to_end(rfm):
 
     def errs(y0=None, every=100, iters=1000):
         snap = torch.zeros((iters // every, S.sizes["n_cols"]), dtype=torch.float64, device="cuda")
-        S.solve(atol=0, btol=0, max_iter=iters, snap=snap, snap_every=every, y0=y0)
-        return np.array([_rel(S.evaluate(d, S.coefficients(snap[k]), Xt, with_error=False)[0], u_ref)
-                         for k in range(snap.shape[0])])
+        _, rep = S.solve(atol=0, btol=0, max_iter=iters, snap=snap, snap_every=every, y0=y0)
+        e = np.array([_rel(S.evaluate(d, S.coefficients(snap[k]), Xt, with_error=False)[0], u_ref)
+                      for k in range(snap.shape[0])])
+        return e, [rfm.report_dict(rep, i) for i in range(len(ps))]
 
-    cold, warm = errs(None), errs(y0)
+    (cold, rc), (warm, rw) = errs(None), errs(y0)
     print(f"\nlearned warm start: error at the start {e0:.3e} (zero start 1); after 100/500/1000 LSQR "
           f"iterations: zero start {cold[0]:.2e}/{cold[4]:.2e}/{cold[-1]:.2e}, "
           f"learned start {warm[0]:.2e}/{warm[4]:.2e}/{warm[-1]:.2e}")
     assert e0 < 0.5
     assert np.all(np.isfinite(warm))
+    # the solver keeps the fitted start (its residual is below ||h||) and
+    # reports it; the zero start reports no start
+    assert all(r["start"] == 1 and r["r0norm"] < r["bnorm"] for r in rw)
+    assert all(r["start"] == 0 and r["r0norm"] == r["bnorm"] for r in rc)
