@@ -837,6 +837,71 @@ def run_learned(args, dev):
         k = np.nonzero(c <= th)[0]
         return int(every * (1 + k[0])) if len(k) else None
 
+    # many held-out instances: the family shares its operator, so the fitted
+    # starts (32 instances per fitting system) and LSQR for all of them run
+    # as one many-data-set solve, from zero and from the fitted starts
+    # (rfm_lsqr_multi with its warm starts), errors at checkpoints against a
+    # 10,000-iteration mixed-path solve of the same data sets
+    many = {}
+    nh = args.learned_heldout_many
+    if nh > 0:
+        held2 = fam(range(20000, 20000 + nh))
+        d1 = params(held2[:1])
+        Sm = R.System([held2[0]], asm="fp32", op="q32", tol=TOL, device=str(dev))
+        Sm.assemble(d1)
+        Sm.filter()
+        Hm = Sm.rhs_many(held2)
+        ev0.record()
+        Aref, _ = Sm.solve_multi(Hm, atol=0, btol=0, max_iter=10000)
+        ev1.record()
+        torch.cuda.synchronize()
+        t_ref = ev0.elapsed_time(ev1)
+        uref = [Sm.evaluate(d1, Aref[j].contiguous(), [grid], with_error=False)[0][0] for j in range(nh)]
+        del Aref
+        ncols = Sm.sizes["n_cols"]
+        Y0 = torch.zeros((nh, ncols), dtype=torch.float64, device=dev)
+        ev0.record()
+        for c0 in range(0, nh, 32):
+            ps = held2[c0:c0 + 32]
+            dc = params(ps)
+            Sc = R.System(ps, asm="fp32", op="q32", tol=TOL, device=str(dev))
+            Sc.assemble(dc)
+            Sc.filter()
+            Sc.fit_prepare(dc, tol_fit=1e-8)
+            invc = torch.tensor([1.0 / v for v in scl(ps)], dtype=torch.float32, device=dev)
+            Y0[c0:c0 + len(ps)] = W.warm_start(Sc, ctx(ps), fit_iters=300, inst_scale=invc).view(len(ps), ncols)
+            del Sc
+        ev1.record()
+        torch.cuda.synchronize()
+        t_fit = ev0.elapsed_time(ev1)
+        cps = (100, 300, 1000, 3000)
+        res, kept, ms_multi = {}, 0, {}
+        for name, yy in (("zero_start", None), ("learned_start", Y0)):
+            res[name] = {}
+            for it in cps:
+                ev0.record()
+                A, rep = Sm.solve_multi(Hm, atol=0, btol=0, max_iter=it, Y0=yy)
+                ev1.record()
+                torch.cuda.synchronize()
+                ms_multi[f"{name}_{it}"] = ev0.elapsed_time(ev1)
+                if yy is not None and it == cps[0]:
+                    kept = sum(int(R.report_dict(rep, j)["start"]) for j in range(nh))
+                e = np.array([float(torch.linalg.norm(Sm.evaluate(d1, A[j].contiguous(), [grid],
+                                                                  with_error=False)[0][0] - uref[j]) /
+                                    torch.linalg.norm(uref[j])) for j in range(nh)])
+                res[name][str(it)] = {"median": float(np.median(e)), "max": float(e.max()),
+                                      "p90": float(np.percentile(e, 90))}
+            if yy is not None:
+                e0m = np.array([float(torch.linalg.norm(Sm.evaluate(d1, Sm.coefficients(Y0[j].contiguous()), [grid],
+                                                                    with_error=False)[0][0] - uref[j]) /
+                                      torch.linalg.norm(uref[j])) for j in range(nh)])
+        many = {"instances": nh, "seeds": f"20000-{20000 + nh - 1}",
+                "solver": "rfm_lsqr_multi, all instances in one call per checkpoint (Y0 = the fitted starts)",
+                "reference": "mixed path, 10000 iterations, the same many-data-set solver",
+                "reference_ms": t_ref, "fit_ms": t_fit, "fit_systems": "32 instances per fitting system",
+                "start_error": {"median": float(np.median(e0m)), "max": float(e0m.max())},
+                "learned_starts_kept": kept, "rel_l2_after_iterations": res, "solve_ms": ms_multi}
+
     return {
         "workload": f"2D Poisson, f = sin(a pi x) sin(b pi y) + c sin(d pi x + e pi y), {S_}x{S_} subdomains, "
                     f"overlap ratio {D_}, K={K_}, {n}^2 interior + boundary rows, filter tol {TOL:g}, "
@@ -865,6 +930,7 @@ def run_learned(args, dev):
         "iterations_to_0.1_median": {name: first(c, 0.1) for name, c in med.items()},
         "ms_per_lsqr_iteration": ms_it,
         "reference": "FP64 explicit-Q LSQR, 10000 iterations, same discretisation",
+        "many_heldout": many,
     }
 
 
@@ -1025,6 +1091,8 @@ def main():
                     help="training solves of the learned warm start section (0 skips it)")
     ap.add_argument("--learned-epochs", type=int, default=2)
     ap.add_argument("--learned-heldout", type=int, default=32, help="held-out instances of the learned section")
+    ap.add_argument("--learned-heldout-many", type=int, default=256,
+                    help="held-out instances solved together in the learned section (0 skips)")
     ap.add_argument("--clocks-log", default=os.path.join(tempfile.gettempdir(), "bench_clocks.csv"),
                     help="CSV of the nvidia-smi clock samples taken during the timed region")
     ap.add_argument("--batched", type=int, default=64, help="instances of the batched section (0 skips it)")

@@ -297,20 +297,24 @@ rfm_status rfm_lsqr_multi_size(const rfm_problem *prob, const rfm_config *cfg, i
 rfm_status rfm_rhs_many(const rfm_problem *probs, int nrhs, const rfm_config *cfg, double *d_H, void *d_mws,
                         size_t mws_bytes, void *stream);
 
-/* LSQR of Algorithm 2 from zero for nrhs right-hand sides d_H (layout of
+/* LSQR of Algorithm 2 for nrhs right-hand sides d_H (layout of
  * rfm_rhs_many) on the filtered system in d_ws (assembled and filtered with
  * RFM_OP_Q32 or RFM_OP_Q64, one instance), then a_j = S^-1 y_j into d_A
  * (nrhs x n_cols doubles, set j at d_A + j n_cols, zeros at dropped
  * columns), d_report[j] per set.  opts: atol, btol, max_iter (the other
- * fields unused).  Every set stops on the tests of rfm_lsqr_solve, with
+ * fields unused).  d_Y0: nullable warm starts, nrhs x n_cols doubles in the
+ * y layout of rfm_lsqr_solve's d_y0 (set j at d_Y0 + j n_cols); as there, a
+ * set keeps its start only when ||h_j - A S^-1 y0_j|| < ||h_j|| and falls
+ * back to zero otherwise (report fields start, r0norm).  Without d_Y0 every
+ * set starts from zero.  Every set stops on the tests of rfm_lsqr_solve, with
  * ||y|| of the previous iteration.  The call issues a fixed sequence of
  * launches per iteration (max_iter of them; sets that have stopped keep their
  * iterate) and uploads its tile lists from pageable host memory.
  * Errors: RFM_EINVAL for another operator, more than one instance, nrhs
  * outside 1..256 or bad options; RFM_ENOSPACE for a short workspace. */
 rfm_status rfm_lsqr_multi(const rfm_problem *prob, const rfm_config *cfg, const rfm_lsqr_opts *opts, int nrhs,
-                          const double *d_H, double *d_A, rfm_lsqr_report *d_report, void *d_ws, size_t ws_bytes,
-                          void *d_mws, size_t mws_bytes, void *stream);
+                          const double *d_H, const double *d_Y0, double *d_A, rfm_lsqr_report *d_report, void *d_ws,
+                          size_t ws_bytes, void *d_mws, size_t mws_bytes, void *stream);
 
 /* a = S^-1 y (Algorithm 2's last step) for an arbitrary y in the n_cols
  * layout: per block a_j[perm[c]] = (R_hat_j^-1 y_j)[c] for kept c, 0 at
@@ -341,7 +345,10 @@ rfm_status rfm_eval(const rfm_problem *probs, int n_inst, const rfm_config *cfg,
  *  - At most 16 instances per call (more: RFM_EINVAL with a message).
  *  - The first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    before any stream capture.  Later calls may be captured into a CUDA
+ *    graph: the instance records travel as kernel parameters (no copy from
+ *    host memory), so a replay evaluates the captured problems at the
+ *    current contents of the captured device buffers.
  *  - The call allocates no device memory and calls no allocating library
  *    routine.  Every call shares the array, which keeps the last call's
  *    contents; each call overwrites what it reads, so nothing needs clearing,

@@ -85,7 +85,7 @@ def load(path: str = LIB_PATH):
         "rfm_block_rows": [P, C.c_int, CF, i64, vp],
         "rfm_lsqr_multi_size": [P, CF, C.c_int, C.POINTER(C.c_size_t)],
         "rfm_rhs_many": [P, C.c_int, CF, vp, vp, C.c_size_t, vp],
-        "rfm_lsqr_multi": [P, CF, C.POINTER(RfmLsqrOpts), C.c_int, vp, vp, vp, vp, C.c_size_t, vp, C.c_size_t, vp],
+        "rfm_lsqr_multi": [P, CF, C.POINTER(RfmLsqrOpts), C.c_int, vp, vp, vp, vp, vp, C.c_size_t, vp, C.c_size_t, vp],
         "rfm_coefficients": [P, C.c_int, CF, vp, vp, vp, C.c_size_t, vp],
         "rfm_block_info": [P, C.c_int, CF, i64, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)],
         "rfm_workspace_view": [P, C.c_int, CF, vp, C.c_int, C.POINTER(vp)],

@@ -125,17 +125,23 @@ class System:
         self._mws_keep = ws
         return H
 
-    def solve_multi(self, H: torch.Tensor, atol=1e-10, btol=1e-10, max_iter=10000):
-        """LSQR from zero for every row of H (nrhs x n_rows) on this system's
-        operator (one instance, explicit Q_hat); returns the coefficients
-        (nrhs x n_cols) and the reports (nrhs x report fields)."""
+    def solve_multi(self, H: torch.Tensor, atol=1e-10, btol=1e-10, max_iter=10000, Y0: Optional[torch.Tensor] = None):
+        """LSQR for every row of H (nrhs x n_rows) on this system's operator
+        (one instance, explicit Q_hat), from zero or from the rows of Y0
+        (nrhs x n_cols, the y layout of solve's y0; a set falls back to zero
+        when its start's residual is not below ||h||); returns the
+        coefficients (nrhs x n_cols) and the reports (nrhs x report fields)."""
         assert H.is_cuda and H.dtype == torch.float64 and H.is_contiguous() and H.shape[1] == self.sizes["n_rows"]
         n = H.shape[0]
+        if Y0 is not None:
+            assert Y0.is_cuda and Y0.dtype == torch.float64 and Y0.is_contiguous()
+            assert tuple(Y0.shape) == (n, self.sizes["n_cols"])
         A = torch.empty((n, self.sizes["n_cols"]), dtype=torch.float64, device=self.device)
         rep = torch.empty(n * N.REPORT_LEN, dtype=torch.float64, device=self.device)
         ws, ptr, nb = self._multi_ws(n)
         opts = N.RfmLsqrOpts(float(atol), float(btol), int(max_iter), 10000, None, 0, 0, None, 0, 0, None)
         N.check("rfm_lsqr_multi", self.lib.rfm_lsqr_multi(self._probs, C.byref(self._cfg), C.byref(opts), n, _ptr(H),
+                                                          _ptr(Y0),
                                                           _ptr(A), _ptr(rep), C.c_void_p(self.ws_ptr), self.ws_bytes,
                                                           C.c_void_p(ptr), nb, _stream()))
         self._mws_keep = ws

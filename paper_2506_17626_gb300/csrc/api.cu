@@ -19,7 +19,7 @@ rfm_status launch_residual(const HostPlan &P, void *ws, const double *a, double 
                            cudaStream_t st);
 size_t multi_workspace_bytes(const HostPlan &P, int R);
 rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, int R, const double *H,
-                             double *A, rfm_lsqr_report *rep, void *mws, cudaStream_t st);
+                             const double *Y0, double *A, rfm_lsqr_report *rep, void *mws, cudaStream_t st);
 rfm_status launch_rhs_many(const InstRec *recs, int R, int64_t N, double *H, void *scratch, cudaStream_t st);
 void set_force_global_filter(int on);
 void set_autotune(int on);
@@ -309,8 +309,8 @@ rfm_status rfm_rhs_many(const rfm_problem *probs, int nrhs, const rfm_config *cf
 }
 
 rfm_status rfm_lsqr_multi(const rfm_problem *prob, const rfm_config *cfg, const rfm_lsqr_opts *opts, int nrhs,
-                          const double *d_H, double *d_A, rfm_lsqr_report *d_report, void *d_ws, size_t ws_bytes,
-                          void *d_mws, size_t mws_bytes, void *stream) {
+                          const double *d_H, const double *d_Y0, double *d_A, rfm_lsqr_report *d_report, void *d_ws,
+                          size_t ws_bytes, void *d_mws, size_t mws_bytes, void *stream) {
     RFM_GUARD_BEGIN
     Plan P(prob, 1, cfg);
     if (!P.ok) return P.rc;
@@ -323,7 +323,7 @@ rfm_status rfm_lsqr_multi(const rfm_problem *prob, const rfm_config *cfg, const 
     }
     rc = check_mws(P.p, nrhs, d_mws, mws_bytes);
     if (rc != RFM_OK) return rc;
-    return launch_lsqr_multi(P.p, d_ws, opts, nrhs, d_H, d_A, d_report, d_mws, (cudaStream_t)stream);
+    return launch_lsqr_multi(P.p, d_ws, opts, nrhs, d_H, d_Y0, d_A, d_report, d_mws, (cudaStream_t)stream);
     RFM_GUARD_END
 }
 

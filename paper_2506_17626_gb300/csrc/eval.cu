@@ -326,6 +326,17 @@ static rfm_status noalloc_scratch(NoallocScratch **out) {
     return RFM_OK;
 }
 
+// One instance record, passed by value (as a kernel parameter), into device
+// memory: unlike a copy from host memory that the plan frees on return, a
+// parameter is recorded with the launch, so the call can be captured into a
+// CUDA graph and replayed.
+__global__ void k_put_rec(InstRec *__restrict__ dst, const InstRec rec) {
+    const uint64_t *s = reinterpret_cast<const uint64_t *>(&rec);
+    uint64_t *d = reinterpret_cast<uint64_t *>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(InstRec) / 8); i += blockDim.x) d[i] = s[i];
+}
+static_assert(sizeof(InstRec) % 8 == 0 && sizeof(InstRec) <= 4000, "InstRec travels as one kernel parameter");
+
 rfm_status launch_eval_noalloc(const HostPlan &P, const double *params, const double *a, const double *X,
                                const int64_t *pt_off, double *u, double *err, cudaStream_t st) {
     const Layout &L = P.L;
@@ -337,7 +348,10 @@ rfm_status launch_eval_noalloc(const HostPlan &P, const double *params, const do
     NoallocScratch *S = nullptr;
     rfm_status rc = noalloc_scratch(&S);
     if (rc != RFM_OK) return rc;
-    RFM_CUDA_CHECK(cudaMemcpyAsync(S->inst, P.inst, sizeof(InstRec) * L.n_inst, cudaMemcpyHostToDevice, st));
+    for (int s = 0; s < L.n_inst; ++s) {
+        k_put_rec<<<1, 32, 0, st>>>(S->inst + s, P.inst[s]);
+        RFM_CUDA_CHECK(cudaGetLastError());
+    }
     for (int s = 0; s < L.n_inst; ++s) {
         const int64_t n = pt_off[s + 1] - pt_off[s];
         if (n < 0) {

@@ -37,7 +37,8 @@ constexpr int kRedCtas = 512;   // CTAs of the row / column phases (partial sums
 struct MScal {
     double alpha, beta, rhobar, phibar, anorm2, bnorm, rnorm, arnorm, ynorm;
     double phi_rho, theta_rho, c, inv_alpha, inv_beta, inv_alpha_old, beta_old;
-    int32_t itn, istop, done, pad;
+    double r0norm, hnorm, r0w;  // reported start residual; ||h||, ||h - Op y0|| of a given start
+    int32_t itn, istop, done, start;   // start: 1 when the set keeps its warm start
 };
 
 struct MLayout {
@@ -220,6 +221,106 @@ __device__ inline void m_partials(double v, int R, double *red, double *part) {
     }
 }
 
+__device__ inline double m_sum(const double *part, int nctas, int R, int j) {
+    double t = 0.0;
+    for (int c = 0; c < nctas; ++c) t += part[(int64_t)c * R + j];
+    return t;
+}
+
+// Warm starts.  VT and Y = Y0 (sets contiguous in Y0) on the kept slots, 0
+// elsewhere; inv_alpha = 1 so that the forward kernel forms T = Op Y0.
+__global__ void __launch_bounds__(256) k_m_in(const double *__restrict__ Y0, const int32_t *__restrict__ rank,
+                                              int64_t n_cols, int K, int R, double *__restrict__ VT,
+                                              double *__restrict__ Y, MScal *__restrict__ sc) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_cols * R;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t slot = e / R;
+        const int j = (int)(e % R);
+        const double v = (int)(slot % K) < rank[slot / K] ? Y0[(int64_t)j * n_cols + slot] : 0.0;
+        VT[e] = v;
+        Y[e] = v;
+    }
+    if (blockIdx.x == 0)
+        for (int j = threadIdx.x; j < R; j += blockDim.x) sc[j].inv_alpha = 1.0;
+}
+
+// u = h - (sum over the row's block rows of T); partials of ||u||^2 (part)
+// and of ||h||^2 (part + gridDim.x R)
+__global__ void __launch_bounds__(256) k_m_load_warm(const InstRec *__restrict__ insts,
+                                                     const int32_t *__restrict__ rowlist, const double *__restrict__ H,
+                                                     const double *__restrict__ T, int R, double *__restrict__ U,
+                                                     double *__restrict__ part) {
+    __shared__ double red[256];
+    const InstRec &I = insts[0];
+    const int Rp = pow2_at_least(R), j = threadIdx.x % Rp, sub = threadIdx.x / Rp, nsub = 256 / Rp;
+    double su = 0.0, sh = 0.0;
+    if (j < R)
+        for (int64_t g = (int64_t)blockIdx.x * nsub + sub; g < I.N; g += (int64_t)gridDim.x * nsub) {
+            const int32_t *lst = rowlist + I.rl_off + g * I.C;
+            double s = 0.0;
+            for (int e = 0; e < I.C; ++e) {
+                const int q = lst[e];
+                if (q >= 0) s += T[(int64_t)q * R + j];
+            }
+            const double h = H[(int64_t)j * I.N + g], u = h - s;
+            U[g * R + j] = u;
+            su = fma(u, u, su);
+            sh = fma(h, h, sh);
+        }
+    m_partials(su, R, red, part);
+    __syncthreads();
+    m_partials(sh, R, red, part + (int64_t)gridDim.x * R);
+}
+
+// per set: keep the warm start when ||h - Op y0|| < ||h||, else fall back to
+// the zero start (the rule of rfm_lsqr_solve)
+__global__ void k_m_start(MScal *__restrict__ sc, const double *__restrict__ part, int nctas, int R) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= R) return;
+    const double r0 = sqrt(m_sum(part, nctas, R, j)), hn = sqrt(m_sum(part + (int64_t)nctas * R, nctas, R, j));
+    sc[j].r0w = r0;
+    sc[j].hnorm = hn;
+    sc[j].start = r0 < hn ? 1 : 0;
+}
+
+// the sets that fall back: u = h, y = 0
+__global__ void __launch_bounds__(256) k_m_fallback(const MScal *__restrict__ sc, const double *__restrict__ H,
+                                                    int64_t n_rows, int64_t n_cols, int R, double *__restrict__ U,
+                                                    double *__restrict__ Y) {
+    const int64_t nr = n_rows * R, nt = nr + n_cols * R;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
+        if (e < nr) {
+            const int64_t g = e / R;
+            const int j = (int)(e % R);
+            if (!sc[j].start) U[e] = H[(int64_t)j * n_rows + g];
+        } else {
+            const int j = (int)((e - nr) % R);
+            if (!sc[j].start) Y[e - nr] = 0.0;
+        }
+    }
+}
+
+// partials of ||u||^2 (after the fallback)
+__global__ void __launch_bounds__(256) k_m_unorm(const double *__restrict__ U, int64_t n_rows, int R,
+                                                 double *__restrict__ part) {
+    __shared__ double red[256];
+    const int Rp = pow2_at_least(R), j = threadIdx.x % Rp, sub = threadIdx.x / Rp, nsub = 256 / Rp;
+    double ss = 0.0;
+    if (j < R)
+        for (int64_t g = (int64_t)blockIdx.x * nsub + sub; g < n_rows; g += (int64_t)gridDim.x * nsub)
+            ss = fma(U[g * R + j], U[g * R + j], ss);
+    m_partials(ss, R, red, part);
+}
+
+// after the first beta: the stopping test's ||b|| is ||h||, and the given
+// start's residual is reported (also when it was not kept, as rfm_lsqr_solve)
+__global__ void k_m_fixb(MScal *__restrict__ sc, int R) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= R) return;
+    sc[j].bnorm = sc[j].hnorm;
+    sc[j].r0norm = sc[j].r0w;
+}
+
 // rows: u~ = sum over the row's block rows of T - alpha (u~ / beta), ||u~||^2
 __global__ void __launch_bounds__(256) k_m_rows(const InstRec *__restrict__ insts, const int32_t *__restrict__ rowlist,
                                                 const double *__restrict__ T, double *__restrict__ U,
@@ -267,11 +368,6 @@ __global__ void __launch_bounds__(256) k_m_cols(const int32_t *__restrict__ rank
 }
 
 // the first nctas partial rows of part, summed in CTA order, per right-hand side
-__device__ inline double m_sum(const double *part, int nctas, int R, int j) {
-    double t = 0.0;
-    for (int c = 0; c < nctas; ++c) t += part[(int64_t)c * R + j];
-    return t;
-}
 
 // The stopping test of the previous iteration k (its estimates, ||y_k|| from
 // its update's partials; the tests of rfm_lsqr_solve), then beta = ||u~||.
@@ -299,6 +395,7 @@ __global__ void k_m_beta(MScal *__restrict__ sc, const double *__restrict__ part
     q.inv_beta = q.beta > 0.0 ? 1.0 / q.beta : 0.0;
     if (first) {
         q.bnorm = q.beta;
+        q.r0norm = q.beta;
         q.phibar = q.beta;
         q.rnorm = q.beta;
         q.istop = 7;
@@ -413,8 +510,8 @@ __global__ void k_m_report(const MScal *__restrict__ sc, int R, rfm_lsqr_report 
     rep[j].ynorm = q.ynorm;
     rep[j].bnorm = q.bnorm;
     rep[j].status = q.istop < 0 ? (double)RFM_ENUMERIC : 0.0;
-    rep[j].start = 0.0;
-    rep[j].r0norm = q.bnorm;
+    rep[j].start = (double)q.start;
+    rep[j].r0norm = q.r0norm;
 }
 
 // ---------------------------------------------------------------------------
@@ -430,7 +527,7 @@ static unsigned red_grid(int64_t n, int R) {
 }
 
 rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, int R, const double *H,
-                             double *A, rfm_lsqr_report *rep, void *mws, cudaStream_t st) {
+                             const double *Y0, double *A, rfm_lsqr_report *rep, void *mws, cudaStream_t st) {
     const Layout &L = P.L;
     if (L.n_inst != 1 || (L.op != RFM_OP_Q32 && L.op != RFM_OP_Q64)) {
         set_error("rfm_lsqr_multi: one instance with an explicit Q_hat operator (RFM_OP_Q32 or RFM_OP_Q64)");
@@ -491,13 +588,25 @@ rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *o
         return RFM_OK;
     };
     rfm_status rc;
-    // initialisation: beta_1 u_1 = h, alpha_1 v_1 = A^T u_1, w_1 = v_1
-    {
+    // initialisation: beta_1 u_1 = h (or h - Op y0 for a kept warm start),
+    // alpha_1 v_1 = A^T u_1, w_1 = v_1
+    if (Y0) {
+        ProfScope ps("k_m_warm", st);
+        k_m_in<<<2048, 256, 0, st>>>(Y0, rank, L.n_cols, K, R, VT, Y, sc);
+        RFM_CUDA_CHECK(cudaGetLastError());
+        if ((rc = fwd()) != RFM_OK) return rc;
+        k_m_load_warm<<<gr, 256, 0, st>>>(insts, rowlist, H, T, R, U, part);
+        k_m_start<<<gs, 64, 0, st>>>(sc, part, (int)gr, R);
+        k_m_fallback<<<2048, 256, 0, st>>>(sc, H, L.n_rows, L.n_cols, R, U, Y);
+        k_m_unorm<<<gr, 256, 0, st>>>(U, L.n_rows, R, part);
+        RFM_CUDA_CHECK(cudaGetLastError());
+    } else {
         ProfScope ps("k_m_load", st);
         k_m_load<<<gr, 256, 0, st>>>(H, L.n_rows, R, U, part);
         RFM_CUDA_CHECK(cudaGetLastError());
     }
     k_m_beta<<<gs, 64, 0, st>>>(sc, part, (int)gr, nullptr, 0, R, 1, opts->atol, opts->btol);
+    if (Y0) k_m_fixb<<<gs, 64, 0, st>>>(sc, R);
     if ((rc = trans()) != RFM_OK) return rc;
     k_m_cols<<<gc, 256, 0, st>>>(rank, L.n_cols, K, Z, VT, sc, R, 1, part);
     k_m_alpha<<<gs, 64, 0, st>>>(sc, part, (int)gc, R, 1, opts->atol, opts->btol, opts->max_iter);

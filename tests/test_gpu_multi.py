@@ -114,3 +114,53 @@ def test_multi_rhs_stopping_per_data_set(rfm):
                                                                             max_iter=2000)
     for itn in (r2["itn"], rfm.report_dict(rep1)["itn"]):
         assert abs(itn - ref["itn"]) <= 0.1 * ref["itn"], (itn, ref["itn"])
+
+
+@pytest.mark.parametrize("op", ["q64", "q32"])
+def test_multi_rhs_warm_starts(rfm, op):
+    """Warm starts per data set (the rule of rfm_lsqr_solve: a start is kept
+    when its residual is below ||h||): set 0 from a good start (the oracle's
+    iterate after 5 steps), set 1 from a start whose residual exceeds ||h||
+    (falls back to zero), set 2 from zero.  Each against the single-data-set
+    solver from the same start after k steps: the iterate (1e-10 relative on
+    the FP64 operator, 1e-5 on the FP32 one, the mixed path's tolerance),
+    the reported start and its residual."""
+    probs = _family(3)
+    prm = synth.feature_params(probs[0])
+    d = torch.from_numpy(prm.ravel()).cuda()
+    asm = "fp64" if op == "q64" else "fp32"
+    S = rfm.System([probs[0]], asm=asm, op=op, tol=1e-6)
+    S.assemble(d)
+    rank = S.filter().cpu().numpy()
+    H = S.rhs_many(probs)
+    nc = S.sizes["n_cols"]
+    K = probs[0].K
+    B = oracle.assemble(probs[0], prm)
+    F = oracle.filter_blocks(B, 1e-6)
+    if op == "q64":
+        assert [int(x) for x in rank] == [f.rank for f in F]
+    # starts in the y layout: a good one from the single solver's 5-step iterate
+    S0 = rfm.System([probs[0]], asm=asm, op=op, tol=1e-6)
+    S0.assemble(d)
+    S0.filter()
+    _, _, y5 = S0.solve(atol=0, btol=0, max_iter=5, want_y=True)
+    Y0 = torch.zeros((3, nc), dtype=torch.float64, device="cuda")
+    Y0[0] = y5
+    Y0[1] = 1e3 * y5          # residual far above ||h||
+    k = 20
+    A, rep = S.solve_multi(H, atol=0, btol=0, max_iter=k, Y0=Y0)
+    torch.cuda.synchronize()
+    rtol = 1e-10 if op == "q64" else 1e-5
+    starts = [1, 0, 0]
+    for j, p in enumerate(probs):
+        r = rfm.report_dict(rep, j)
+        assert r["start"] == starts[j] and r["itn"] == k, (j, r)
+        S1 = rfm.System([p], asm=asm, op=op, tol=1e-6)
+        S1.assemble(d)
+        S1.filter()
+        a1, rep1 = S1.solve(atol=0, btol=0, max_iter=k, y0=Y0[j].clone())
+        r1 = rfm.report_dict(rep1)
+        assert r1["start"] == starts[j]
+        assert r["r0norm"] == pytest.approx(r1["r0norm"], rel=1e-8)
+        assert r["bnorm"] == pytest.approx(r1["bnorm"], rel=1e-12)
+        assert torch.linalg.norm(A[j] - a1) <= rtol * torch.linalg.norm(a1), j
