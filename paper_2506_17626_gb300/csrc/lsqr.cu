@@ -23,6 +23,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "device.cuh"
 #include "prof.cuh"
@@ -1181,8 +1182,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
             }
         }
     };
-    // forward product of block row q
-    auto row_partials = [&](int64_t q) { return a.t[q]; };
+    // forward product of block row q (written in this kernel: coherent loads)
+    auto row_partials = [&](int64_t q) { return __ldcg(a.t + q); };
     // ---- fused products: the transposed product of a round and the forward
     // product of the next, over one list of warp items (block b's column
     // chunks, then, about 1.2 rounds of the grid later, its 32-row tiles).
@@ -1394,12 +1395,40 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_tiles(LsqrArgs a, const Co
         }
         P.acc[0] = P.acc[1] = 0.0;
         const int Cm = P.Ci[0] > P.Ci[1] ? P.Ci[0] : P.Ci[1];
-        for (int e = 0; e < Cm; ++e) {
-            const int q0 = P.rv[0] && e < P.Ci[0] ? P.lst[0][e] : -1;
-            const int q1 = P.rv[1] && e < P.Ci[1] ? P.lst[1][e] : -1;
-            if (q0 >= 0) P.acc[0] += row_partials(q0);
-            if (q1 >= 0) P.acc[1] += row_partials(q1);
-        }
+        // up to 8 covering blocks: every row-list entry loaded first, then
+        // every partial, then the sums in entry order (two round trips
+        // instead of two per entry); more: entry by entry
+        auto gather = [&](auto cmc) {
+            constexpr int CM = decltype(cmc)::value;
+            int q0[CM], q1[CM];
+            double t0[CM], t1[CM];
+#pragma unroll
+            for (int e = 0; e < CM; ++e) {
+                q0[e] = P.rv[0] && e < P.Ci[0] ? __ldg(P.lst[0] + e) : -1;
+                q1[e] = P.rv[1] && e < P.Ci[1] ? __ldg(P.lst[1] + e) : -1;
+            }
+#pragma unroll
+            for (int e = 0; e < CM; ++e) {
+                t0[e] = q0[e] >= 0 ? row_partials(q0[e]) : 0.0;
+                t1[e] = q1[e] >= 0 ? row_partials(q1[e]) : 0.0;
+            }
+#pragma unroll
+            for (int e = 0; e < CM; ++e) {
+                if (q0[e] >= 0) P.acc[0] += t0[e];
+                if (q1[e] >= 0) P.acc[1] += t1[e];
+            }
+        };
+        if (Cm <= 1) gather(std::integral_constant<int, 1>{});
+        else if (Cm <= 2) gather(std::integral_constant<int, 2>{});
+        else if (Cm <= 4) gather(std::integral_constant<int, 4>{});
+        else if (Cm <= 8) gather(std::integral_constant<int, 8>{});
+        else
+            for (int e = 0; e < Cm; ++e) {
+                const int q0 = P.rv[0] && e < P.Ci[0] ? P.lst[0][e] : -1;
+                const int q1 = P.rv[1] && e < P.Ci[1] ? P.lst[1][e] : -1;
+                if (q0 >= 0) P.acc[0] += row_partials(q0);
+                if (q1 >= 0) P.acc[1] += row_partials(q1);
+            }
 #pragma unroll
         for (int j = 0; j < 2; ++j) P.uo[j] = P.rv[j] ? a.u[P.gr[j]] : 0.0;
     };
