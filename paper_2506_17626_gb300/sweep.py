@@ -2,7 +2,7 @@
 the C ABI (the comparison of Sec. 4.3 and Table 1: share of columns dropped,
 error, convergence of LSQR with and without the filter and preconditioner).
 
-    python -m paper_2506_17626_gb300.sweep [--case p1d|p2d] [--iters 10000] [--every 100]
+    python -m paper_2506_17626_gb300.sweep [--case p1d|p2d|osc|laplace] [--iters 10000] [--every 100]
 
 Runs, on one problem instance, zero-start LSQR for a fixed number of
 iterations with no stopping rule (as the paper runs its solvers), once on the
