@@ -544,7 +544,12 @@ int rfm_profile_read(const char **names, int64_t *launches, double *ms, int max)
  *    LSQR kernel; 0 (default) takes 1.6 passes, capped so that about 120 MB
  *    of operator lie in between.  Shorter lags keep the block in L2 for its
  *    second read, longer ones keep the tiles from waiting on the chunks; the
- *    iterates agree to rounding (the per-warp partial sums change). */
+ *    iterates agree to rounding (the per-warp partial sums change).
+ *  RFM_OPT_MULTI_TENSOR_CORES: 1 (default) forms rfm_lsqr_multi's block
+ *    products of the FP32 operator on the tensor cores (tcgen05, every FP32
+ *    operand split into three BF16 terms, six products accumulated in FP32:
+ *    FP32-grade products); 0 on the CUDA cores in FP32.  The FP64 operator's
+ *    products always run on the CUDA cores.  The iterates agree to rounding. */
 enum {
     RFM_OPT_FILTER_KERNEL = 0,
     RFM_OPT_AUTOTUNE = 1,
@@ -553,7 +558,8 @@ enum {
     RFM_OPT_MLP_TENSOR_CORES = 4,
     RFM_OPT_QR_ORDER = 5,
     RFM_OPT_MLP_TC_THREADS = 6,
-    RFM_OPT_LSQR_LAG = 7
+    RFM_OPT_LSQR_LAG = 7,
+    RFM_OPT_MULTI_TENSOR_CORES = 8
 };
 rfm_status rfm_set_option(int option, int value);
 

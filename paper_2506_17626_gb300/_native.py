@@ -217,6 +217,13 @@ def set_lsqr_lag(tenths: int):
     check("rfm_set_option", load().rfm_set_option(7, int(tenths)))
 
 
+def set_multi_tensor_cores(on: bool):
+    """Many-right-hand-side LSQR on the FP32 operator: block products on the
+    tensor cores (True, the default) or the CUDA cores
+    (RFM_OPT_MULTI_TENSOR_CORES)."""
+    check("rfm_set_option", load().rfm_set_option(8, 1 if on else 0))
+
+
 def set_qr_double_float(on):
     """Factor FP32-assembled blocks with double-float arithmetic (True or 1,
     the default) or with FP64 arithmetic (False or 0); 2 also puts

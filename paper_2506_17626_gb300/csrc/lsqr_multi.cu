@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "device.cuh"
+#include "tc.cuh"
 #include "prof.cuh"
 
 namespace rfm {
@@ -201,6 +202,202 @@ __global__ void __launch_bounds__(256) k_m_trans(const BlkRec *__restrict__ blks
             if (jj < R) Z[(B.coff + col) * R + jj] = (double)acc[i][j];
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core block products of the FP32 operator (tcgen05, kind::f16): a CTA
+// forms one 128 x 64 tile of T = Q_hat_b (V / alpha) (128 rows of a block, 64
+// right-hand sides) or of Z = Q_hat_b^T (U_b / beta) (128 kept columns, 64
+// right-hand sides) in tensor memory.  The FP32 operands are split into three
+// BF16 terms as they are staged (bf16_split3) and the six products of terms
+// whose orders add up to at most 2 are accumulated in FP32, which keeps the
+// products at FP32 accuracy.  Per 64-deep K chunk the 256 threads stage A
+// (128 x 64) and B (64 x 64) in the K-major layout, one thread issues the 4 x
+// 6 MMAs (K = 16 each) and commits them to an mbarrier, and every thread waits
+// (bounded) before the next chunk overwrites the operands; then every thread
+// adds its part of the chunk's product (warps w and w + 4: TMEM lanes 32 (w
+// mod 4) .. + 31, columns 32 (w / 4) .. + 31) to FP32 registers, so the
+// tensor memory sums only 64 products at a time (its accumulation truncates:
+// over whole blocks of thousands of rows it lost about a decade against the
+// CUDA cores' FP32 sums).  A wait that runs out gives NaN outputs.
+// ---------------------------------------------------------------------------
+constexpr int kTM = 128;                  // rows of D (block rows, or kept columns)
+constexpr int kTN = 64;                   // right-hand sides per CTA
+constexpr int kTK = 64;                   // K per staged chunk
+constexpr int kTA = kTM * kTK * 2;        // bytes of one BF16 split of A
+constexpr int kTB = kTN * kTK * 2;        // bytes of one BF16 split of B
+constexpr int kTSmem = 3 * kTA + 3 * kTB; // dynamic shared memory
+
+__device__ inline void tcm_round(unsigned char *sA, unsigned char *sB, uint32_t tmem, uint64_t *mbar,
+                                 unsigned &parity, bool &ok) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (threadIdx.x == 0) {
+        constexpr uint32_t idesc = tcm_idesc(kTM, kTN);
+        const int sa[6] = {0, 0, 1, 0, 1, 2}, sb[6] = {0, 1, 0, 2, 1, 0};
+#pragma unroll
+        for (int kk = 0; kk < kTK / 16; ++kk)
+#pragma unroll
+            for (int t = 5; t >= 0; --t)   // smallest terms first
+                tcm_mma(tmem, tcm_desc<kTK>(sA + sa[t] * kTA + kk * 256), tcm_desc<kTK>(sB + sb[t] * kTB + kk * 256),
+                        idesc, (kk > 0 || t < 5) ? 1u : 0u);
+        tcm_commit(mbar);
+    }
+    const bool got = __syncthreads_and(tcm_wait(mbar, parity));
+    if (!got) {
+        (void)tcm_wait(mbar, parity);   // MMAs still in flight: a second bounded wait
+        ok = false;
+    }
+    parity ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ inline uint32_t tcm_setup(uint64_t *mbar, uint32_t *tmem_slot) {
+    const int warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tcm_su32(tmem_slot)),
+                     "r"(kTN) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 32) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tcm_su32(mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return *tmem_slot;
+}
+
+__device__ inline void tcm_teardown(uint32_t tmem) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTN) : "memory");
+}
+
+// T = Q_hat_b (V / alpha) for 128 rows of one block (items: block, first row)
+__global__ void __launch_bounds__(256) k_m_fwd_tc(const BlkRec *__restrict__ blks, const int32_t *__restrict__ items,
+                                                  const int32_t *__restrict__ rank, const float *__restrict__ Q,
+                                                  const double *__restrict__ VT, const MScal *__restrict__ sc, int R,
+                                                  double *__restrict__ T) {
+    extern __shared__ __align__(128) unsigned char tsm[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    unsigned char *sA = tsm, *sB = tsm + 3 * kTA;
+    const int b = items[2 * blockIdx.x], r0 = items[2 * blockIdx.x + 1];
+    const BlkRec &B = blks[b];
+    const int rb = rank[b], m = B.m, ldm = B.ldm, j0 = blockIdx.y * kTN;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = r0 + 32 * (warp & 3) + lane, jc = j0 + 32 * (warp >> 2);
+    if (rb <= 0) {   // no kept columns: the rows' partials are zero (uniform over the CTA)
+        if (row < m)
+            for (int q = 0; q < 32; ++q)
+                if (jc + q < R) T[(B.roff + row) * R + jc + q] = 0.0;
+        return;
+    }
+    const uint32_t tmem = tcm_setup(&mbar, &tmem_slot);
+    unsigned parity = 0;
+    bool ok = true;
+    float acc[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) acc[q] = 0.f;
+    for (int c0 = 0; c0 < rb && ok; c0 += kTK) {
+        for (int e = tid; e < kTM * (kTK / 8); e += 256) {   // A: row r, columns c0 + 8 kg .. + 7
+            const int r = e % kTM, kg = e / kTM;
+            float x[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = c0 + 8 * kg + q;
+                x[q] = (k < rb && r0 + r < m) ? __ldg(Q + B.moff + (int64_t)k * ldm + r0 + r) : 0.f;
+            }
+            tcm_store8(sA, tcm_off<kTK>(r, 8 * kg), kTA, x);
+        }
+        for (int e = tid; e < kTN * (kTK / 8); e += 256) {   // B: right-hand side n, columns c0 + 8 kg .. + 7
+            const int n = e % kTN, kg = e / kTN, j = j0 + n;
+            const double ia = j < R ? sc[j].inv_alpha : 0.0;
+            float x[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = c0 + 8 * kg + q;
+                x[q] = (k < rb && j < R) ? (float)(VT[(B.coff + k) * R + j] * ia) : 0.f;
+            }
+            tcm_store8(sB, tcm_off<kTK>(n, 8 * kg), kTB, x);
+        }
+        tcm_round(sA, sB, tmem, &mbar, parity, ok);
+        float v[32];
+        tcm_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2)), v);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) acc[q] += v[q];
+    }
+    if (row < m)
+        for (int q = 0; q < 32; ++q)
+            if (jc + q < R) T[(B.roff + row) * R + jc + q] = ok ? (double)acc[q] : __longlong_as_double(0x7ff8000000000000ll);
+    tcm_teardown(tmem);
+}
+
+// Z = Q_hat_b^T (U_b / beta) for 128 kept columns of one block (items: block,
+// first column); U_b gathered by the block's rows
+__global__ void __launch_bounds__(256) k_m_trans_tc(const BlkRec *__restrict__ blks, const int32_t *__restrict__ items,
+                                                    const int32_t *__restrict__ rank, const int32_t *__restrict__ grow,
+                                                    const float *__restrict__ Q, const double *__restrict__ U,
+                                                    const MScal *__restrict__ sc, int R, double *__restrict__ Z) {
+    extern __shared__ __align__(128) unsigned char tsm[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    unsigned char *sA = tsm, *sB = tsm + 3 * kTA;
+    const int b = items[2 * blockIdx.x], c0 = items[2 * blockIdx.x + 1];
+    const BlkRec &B = blks[b];
+    const int rb = rank[b], m = B.m, ldm = B.ldm, j0 = blockIdx.y * kTN;
+    if (c0 >= rb || m <= 0) return;   // uniform over the CTA
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t tmem = tcm_setup(&mbar, &tmem_slot);
+    unsigned parity = 0;
+    bool ok = true;
+    float acc[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) acc[q] = 0.f;
+    for (int i0 = 0; i0 < m && ok; i0 += kTK) {
+        for (int e = tid; e < kTM * (kTK / 8); e += 256) {   // A: kept column c, rows i0 + 8 ig .. + 7
+            const int c = e % kTM, ig = e / kTM, i = i0 + 8 * ig;
+            float x[8];
+            if (c0 + c < rb && i < ldm) {   // ldm is a multiple of 32: the 8 rows lie inside the column
+                const float4 *src = reinterpret_cast<const float4 *>(Q + B.moff + (int64_t)(c0 + c) * ldm + i);
+                const float4 p = __ldg(src), q4 = __ldg(src + 1);
+                x[0] = p.x; x[1] = p.y; x[2] = p.z; x[3] = p.w; x[4] = q4.x; x[5] = q4.y; x[6] = q4.z; x[7] = q4.w;
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (i + q >= m) x[q] = 0.f;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) x[q] = 0.f;
+            }
+            tcm_store8(sA, tcm_off<kTK>(c, 8 * ig), kTA, x);
+        }
+        for (int e = tid; e < kTN * (kTK / 8); e += 256) {   // B: right-hand side n, rows i0 + 8 ig .. + 7
+            const int n = e % kTN, ig = e / kTN, j = j0 + n;
+            const double ib = j < R ? sc[j].inv_beta : 0.0;
+            float x[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int i = i0 + 8 * ig + q;
+                x[q] = (i < m && j < R) ? (float)(U[(int64_t)grow[B.roff + i] * R + j] * ib) : 0.f;
+            }
+            tcm_store8(sB, tcm_off<kTK>(n, 8 * ig), kTB, x);
+        }
+        tcm_round(sA, sB, tmem, &mbar, parity, ok);
+        float v[32];
+        tcm_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2)), v);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) acc[q] += v[q];
+    }
+    const int col = c0 + 32 * (warp & 3) + lane, jc = j0 + 32 * (warp >> 2);
+    if (col < rb)
+        for (int q = 0; q < 32; ++q)
+            if (jc + q < R) Z[(B.coff + col) * R + jc + q] = ok ? (double)acc[q] : __longlong_as_double(0x7ff8000000000000ll);
+    tcm_teardown(tmem);
 }
 
 __device__ inline int pow2_at_least(int R) {
@@ -526,6 +723,9 @@ static unsigned red_grid(int64_t n, int R) {
     return (unsigned)(g < 1 ? 1 : (g > kRedCtas ? kRedCtas : g));
 }
 
+static int g_multi_tc = 1;   // FP32 operator: block products on the tensor cores (1) or the CUDA cores (0)
+void set_multi_tc(int v) { g_multi_tc = v; }
+
 rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, int R, const double *H,
                              const double *Y0, double *A, rfm_lsqr_report *rep, void *mws, cudaStream_t st) {
     const Layout &L = P.L;
@@ -538,11 +738,15 @@ rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *o
         return RFM_EINVAL;
     }
     const MLayout M = multi_layout(P, R);
-    // work lists: (block, first row) of every 64-row tile, (block, first column) of every 64-column tile
+    // the FP32 operator's products on the tensor cores (128-row / 128-column
+    // tiles), the FP64 one's on the CUDA cores (64)
+    const bool tc = L.op == RFM_OP_Q32 && g_multi_tc;
+    const int tile = tc ? kTM : kMT;
+    // work lists: (block, first row) of every row tile, (block, first column) of every column tile
     std::vector<int32_t> fi, ti;
     for (int64_t b = 0; b < L.n_blocks; ++b) {
-        for (int r = 0; r < P.blk[b].m; r += kMT) { fi.push_back((int32_t)b); fi.push_back(r); }
-        for (int c = 0; c < P.blk[b].K; c += kMT) { ti.push_back((int32_t)b); ti.push_back(c); }
+        for (int r = 0; r < P.blk[b].m; r += tile) { fi.push_back((int32_t)b); fi.push_back(r); }
+        for (int c = 0; c < P.blk[b].K; c += tile) { ti.push_back((int32_t)b); ti.push_back(c); }
     }
     int32_t *d_fi = ws_ptr<int32_t>(mws, M.off_fitems), *d_ti = ws_ptr<int32_t>(mws, M.off_titems);
     if (!fi.empty())
@@ -565,13 +769,20 @@ rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *o
     const int32_t *rowlist = ws_ptr<int32_t>(ws, L.off_rowlist);
     const int K = (int)P.inst[0].K;
     const unsigned gr = red_grid(L.n_rows, R), gc = red_grid(L.n_cols, R), gs = (unsigned)((R + 63) / 64);
-    const dim3 gf((unsigned)M.n_fitems, (unsigned)((R + kMR - 1) / kMR)), gt((unsigned)M.n_titems, (unsigned)((R + kMR - 1) / kMR));
+    const dim3 gf((unsigned)(fi.size() / 2), (unsigned)((R + kMR - 1) / kMR)),
+        gt((unsigned)(ti.size() / 2), (unsigned)((R + kMR - 1) / kMR));
+    if (tc) {
+        RFM_CUDA_CHECK(cudaFuncSetAttribute(k_m_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTSmem));
+        RFM_CUDA_CHECK(cudaFuncSetAttribute(k_m_trans_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTSmem));
+    }
     const bool q32 = L.op == RFM_OP_Q32;
     const void *Q = q32 ? (const void *)ws_ptr<float>(ws, L.off_q32) : (const void *)ws_ptr<double>(ws, L.off_op);
 
     auto fwd = [&]() -> rfm_status {
         ProfScope ps("k_m_fwd", st);
-        if (q32)
+        if (tc)
+            k_m_fwd_tc<<<gf, 256, kTSmem, st>>>(blks, d_fi, rank, (const float *)Q, VT, sc, R, T);
+        else if (q32)
             k_m_fwd<float><<<gf, 256, 0, st>>>(blks, d_fi, rank, (const float *)Q, VT, sc, R, T);
         else
             k_m_fwd<double><<<gf, 256, 0, st>>>(blks, d_fi, rank, (const double *)Q, VT, sc, R, T);
@@ -580,7 +791,9 @@ rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *o
     };
     auto trans = [&]() -> rfm_status {
         ProfScope ps("k_m_trans", st);
-        if (q32)
+        if (tc)
+            k_m_trans_tc<<<gt, 256, kTSmem, st>>>(blks, d_ti, rank, grow, (const float *)Q, U, sc, R, Z);
+        else if (q32)
             k_m_trans<float><<<gt, 256, 0, st>>>(blks, d_ti, rank, grow, (const float *)Q, U, sc, R, 0, Z);
         else
             k_m_trans<double><<<gt, 256, 0, st>>>(blks, d_ti, rank, grow, (const double *)Q, U, sc, R, 0, Z);
