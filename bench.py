@@ -698,7 +698,38 @@ def run_poisson1d(args, dev):
         finally:
             N.set_qr_double_float(1)
         out["runs"].append(row)
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_p1d(p, out["runs"], sig)
     return out
+
+
+def cpu_baseline_p1d(p, runs, sig):
+    """The oracle as it stands on one host core, the whole 1D step (assembly,
+    QR with column pivoting, LSQR for the GPU run's iteration count to 1e-6,
+    coefficients, evaluation on the test points), for the two FP64 operator
+    forms that reach 1e-6.  Not sampled."""
+    import oracle
+    from paper_2506_17626_gb300 import sweep as SW
+    prm = synth.feature_params(p)
+    X = SW.grid_points(p)
+    ue = oracle.exact(p, X)
+    res = {"kind": "oracle", "cores": 1, "sample": "the whole step, not sampled", "runs": {}}
+    for r in runs:
+        k = r.get("iterations")
+        if r["op"] not in ("ar64", "q64") or not k:
+            continue
+        t0 = time.perf_counter()
+        B = oracle.assemble(p, prm)
+        F = oracle.filter_blocks(B, sig)
+        S0 = oracle.build_system(B, F, mode=0)
+        So = S0 if r["op"] == "ar64" else oracle.build_system(B, F, mode=1)
+        y = So.lsqr(B.h, atol=0, btol=0, max_iter=k)["y"]
+        u = oracle.evaluate(p, prm, S0.coefficients(y), X)
+        ms = (time.perf_counter() - t0) * 1e3
+        res["runs"][r["op"]] = {"ms": ms, "iterations": k,
+                                "rel_l2": float(np.linalg.norm(u - ue) / np.linalg.norm(ue)),
+                                "gpu_ms": r.get("time_to_target_ms")}
+    return res
 
 
 def guarded(fn, *a):

@@ -549,7 +549,11 @@ int rfm_profile_read(const char **names, int64_t *launches, double *ms, int max)
  *    products of the FP32 operator on the tensor cores (tcgen05, every FP32
  *    operand split into three BF16 terms, six products accumulated in FP32:
  *    FP32-grade products); 0 on the CUDA cores in FP32.  The FP64 operator's
- *    products always run on the CUDA cores.  The iterates agree to rounding. */
+ *    products always run on the CUDA cores.  The iterates agree to rounding.
+ *  RFM_OPT_QR_WARPS: warps per CTA (4, 8, 16 or 32 (default)) of the
+ *    global-memory QR kernels (blocks too large for a cluster: one CTA per
+ *    block, warps over the trailing columns).  The factors agree to rounding
+ *    (the pivot column's norm is summed in another order). */
 enum {
     RFM_OPT_FILTER_KERNEL = 0,
     RFM_OPT_AUTOTUNE = 1,
@@ -559,7 +563,8 @@ enum {
     RFM_OPT_QR_ORDER = 5,
     RFM_OPT_MLP_TC_THREADS = 6,
     RFM_OPT_LSQR_LAG = 7,
-    RFM_OPT_MULTI_TENSOR_CORES = 8
+    RFM_OPT_MULTI_TENSOR_CORES = 8,
+    RFM_OPT_QR_WARPS = 9
 };
 rfm_status rfm_set_option(int option, int value);
 

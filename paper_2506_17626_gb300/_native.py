@@ -224,6 +224,11 @@ def set_multi_tensor_cores(on: bool):
     check("rfm_set_option", load().rfm_set_option(8, 1 if on else 0))
 
 
+def set_qr_warps(n: int):
+    """Warps per CTA of the global-memory QR kernels (RFM_OPT_QR_WARPS)."""
+    check("rfm_set_option", load().rfm_set_option(9, int(n)))
+
+
 def set_qr_double_float(on):
     """Factor FP32-assembled blocks with double-float arithmetic (True or 1,
     the default) or with FP64 arithmetic (False or 0); 2 also puts
