@@ -74,8 +74,8 @@ DF_PEAK_GFLOPS = 152 * 4 * 32 * 2.07 * 4 / 27
 # source is unchanged (else null).  "per": iteration (scaled by the launch's
 # iteration count) or launch.
 NCU_TRAFFIC = {
-    ("heat", "k_lsqr"): {"bytes": (981200140800 + 8471601664) / 200, "per": "iteration", "source": "csrc/lsqr.cu",
-                         "sha16": "2352101015bebe1f", "profile": "profiles/heat3d_10x10x10_K500_launches.md"},
+    ("heat", "k_lsqr"): {"bytes": (987047687680 + 8470948096) / 200, "per": "iteration", "source": "csrc/lsqr.cu",
+                         "sha16": "f4f66c220bac6949", "profile": "profiles/heat3d_10x10x10_K500_launches.md"},
 }
 
 
