@@ -167,6 +167,7 @@ struct FilterBufs {
     float *Q32;             // Q_hat rounded to FP32
     bool gather;            // write the kept columns into Op instead of Q_hat
     bool fit;               // profiling label only
+    bool no_cluster;        // test hook: the global-memory kernels only
     int64_t n_blocks, max_m, max_K;
 };
 rfm_status launch_filter_bufs(const FilterBufs &F, bool fp32, double tol, cudaStream_t st);

@@ -225,7 +225,7 @@ rfm_status launch_fit_prepare(const HostPlan &P, void *ws, const double *params,
             ws_ptr<int32_t>(ws, L.off_rank), Phi, ws_ptr<double>(fws, F.off_wrow));
         RFM_CUDA_CHECK(cudaGetLastError());
     }
-    FilterBufs B;
+    FilterBufs B = {};
     B.blk = ws_ptr<BlkRec>(ws, L.off_blk);
     B.order = qr_order_ptr(ws, L);
     B.M = Phi;

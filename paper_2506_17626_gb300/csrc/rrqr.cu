@@ -215,6 +215,239 @@ __global__ void __launch_bounds__(NW * 32) k_qrcp(const BlkRec *__restrict__ blk
     for (int c = tid; c < K; c += NT) perm_out[B.coff + c] = perm[c];
 }
 
+// Double-float variant of k_qrcp for FP32-assembled blocks (the global-memory
+// counterpart of k_qrcp_cluster_df): the same steps in the same order, the
+// working copy, norms and reflector scalars as double-floats (pairs of FP32
+// numbers, 48 bits, on the FP32 pipe, `df.cuh`) held in the W arena (a
+// double-float takes the 8 bytes of a double), the pivot column staged in
+// shared memory.  At the end every element is converted to FP64 in place, so
+// W, tau, the permutation and R leave in the layout of k_qrcp.
+__device__ inline float2 dfg_in(float x) { return make_float2(x, 0.f); }
+__device__ inline float2 dfg_in(double x) { return df_from_double(x); }
+__device__ inline long long dfg_key(float2 c2) {   // order-preserving key of a normalised h >= 0
+    unsigned lo = __float_as_uint(c2.y);
+    lo = (lo & 0x80000000u) ? ~lo : (lo | 0x80000000u);
+    return ((long long)__float_as_int(c2.x) << 32) | (long long)lo;
+}
+
+template <typename TM, int NW>
+__global__ void __launch_bounds__(NW * 32) k_qrcp_gdf(const BlkRec *__restrict__ blks, const TM *__restrict__ M,
+                                                      double *__restrict__ W, double *__restrict__ tau,
+                                                      int32_t *__restrict__ perm_out, int32_t *__restrict__ rank_out,
+                                                      double *__restrict__ r11_out, double tol) {
+    constexpr int NT = NW * 32;
+    extern __shared__ __align__(16) unsigned char gsm[];
+    const BlkRec B = blks[blockIdx.x];
+    const int m = B.m, K = B.K, ld = B.ldm;
+    float2 *xs = reinterpret_cast<float2 *>(gsm);        // m: the pivot column of the step
+    float2 *cn2 = xs + m;                                // K squared trailing norms
+    float *thr = reinterpret_cast<float *>(cn2 + K);     // K recompute thresholds
+    int *perm = reinterpret_cast<int *>(thr + K);        // K
+    __shared__ long long red_k[NW];
+    __shared__ int red_o[NW], red_c[NW];
+    __shared__ float2 s_red[NW];
+    __shared__ float2 s_h[4];      // beta, sc, g, tau of the step
+    __shared__ double s_nx, s_tau;
+    __shared__ int s_piv;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float2 *Wb = reinterpret_cast<float2 *>(W + B.moff);
+    const TM *Mb = M + B.moff;
+    const float tol3z = 1.4901161193847656e-08f;   // sqrt of the FP64 epsilon, as in the FP64 kernels
+
+    for (int c = warp; c < K; c += NW) {
+        float sh = 0.f, sl = 0.f;
+        for (int i = lane; i < m; i += 32) {
+            const float2 a = dfg_in(Mb[(int64_t)c * ld + i]);
+            Wb[(int64_t)c * ld + i] = a;
+            df_acc(a, a, sh, sl);
+        }
+        float2 s2 = make_float2(sh, sl);
+        for (int o = 16; o; o >>= 1) s2 = df_xor_add(s2, o);
+        if (lane == 0) {
+            cn2[c] = s2;
+            thr[c] = tol3z * s2.x;
+            perm[c] = c;
+        }
+    }
+    __syncthreads();
+
+    const int steps = m < K ? m : K;
+    double R11 = 0.0;
+    int rank = steps;
+    for (int k = 0; k < steps; ++k) {
+        // 1. pivot: the trailing column of largest squared norm, ties to the lowest original index
+        long long bk = -1;
+        int bo = INT_MAX, bc = k;
+        for (int c = k + tid; c < K; c += NT) {
+            const long long kc = dfg_key(cn2[c]);
+            if (key_better(kc, perm[c], bk, bo)) { bk = kc; bo = perm[c]; bc = c; }
+        }
+        for (int o = 16; o; o >>= 1) {
+            const long long k2 = __shfl_xor_sync(kFull, bk, o);
+            const int o2 = __shfl_xor_sync(kFull, bo, o), c2 = __shfl_xor_sync(kFull, bc, o);
+            if (key_better(k2, o2, bk, bo)) { bk = k2; bo = o2; bc = c2; }
+        }
+        if (lane == 0) { red_k[warp] = bk; red_o[warp] = bo; red_c[warp] = bc; }
+        __syncthreads();
+        if (tid == 0) {
+            long long v = red_k[0];
+            int o = red_o[0], c = red_c[0];
+            for (int w = 1; w < NW; ++w)
+                if (key_better(red_k[w], red_o[w], v, o)) { v = red_k[w]; o = red_o[w]; c = red_c[w]; }
+            s_piv = c;
+        }
+        __syncthreads();
+        const int piv = s_piv;
+        if (piv != k) {
+            for (int i = tid; i < m; i += NT) {
+                const float2 a = Wb[(int64_t)k * ld + i];
+                Wb[(int64_t)k * ld + i] = Wb[(int64_t)piv * ld + i];
+                Wb[(int64_t)piv * ld + i] = a;
+            }
+            if (tid == 0) {
+                const float2 t = cn2[k]; cn2[k] = cn2[piv]; cn2[piv] = t;
+                const float u = thr[k]; thr[k] = thr[piv]; thr[piv] = u;
+                const int q = perm[k]; perm[k] = perm[piv]; perm[piv] = q;
+            }
+        }
+        __syncthreads();
+        // 2. the pivot column (rows k..m) to shared memory, its exact norm, reflector scalars
+        {
+            float sh = 0.f, sl = 0.f;
+            for (int i = k + tid; i < m; i += NT) {
+                const float2 x = Wb[(int64_t)k * ld + i];
+                xs[i] = x;
+                df_acc(x, x, sh, sl);
+            }
+            float2 s2 = make_float2(sh, sl);
+            for (int o = 16; o; o >>= 1) s2 = df_xor_add(s2, o);
+            if (lane == 0) s_red[warp] = s2;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            float2 t = lane < NW ? s_red[lane] : make_float2(0.f, 0.f);
+            for (int o = 16; o; o >>= 1) t = df_xor_add(t, o);
+            if (lane == 0) {
+                const float2 nxd = t.x > 0.f ? df_sqrt(t) : make_float2(0.f, 0.f);
+                s_nx = df_to_double(nxd);
+                if (nxd.x > 0.f) {
+                    const float2 alpha = xs[k];
+                    const float2 beta = alpha.x >= 0.f ? df_neg(nxd) : nxd;
+                    const float2 amb = df_sub(alpha, beta);
+                    const float2 inv = df_rcp(df_mul(amb, beta));
+                    const float2 g = df_neg(df_mul(amb, inv));
+                    const float2 tk = df_mul(amb, g);
+                    s_h[0] = beta;
+                    s_h[1] = df_mul(beta, inv);
+                    s_h[2] = g;
+                    s_h[3] = tk;
+                    s_tau = df_to_double(tk);
+                }
+            }
+        }
+        __syncthreads();
+        const double nx = s_nx;
+        if (k == 0) R11 = nx;
+        if (nx == 0.0 || nx < tol * R11) { rank = k; break; }
+        const float2 sc = s_h[1], g = s_h[2], tk = s_h[3];
+        // 3. trailing update with the unscaled pivot column, norm downdate
+        for (int c = k + 1 + warp; c < K; c += NW) {
+            float2 *a = Wb + (int64_t)c * ld;
+            float ph = 0.f, pl = 0.f;
+            for (int i = k + 1 + lane; i < m; i += 32) df_acc(xs[i], a[i], ph, pl);
+            float2 dot = make_float2(ph, pl);
+            for (int o = 16; o; o >>= 1) dot = df_xor_add(dot, o);
+            const float2 akc = a[k];
+            const float2 d = df_add(df_mul(g, dot), df_mul(tk, akc));
+            const float2 e = df_mul(d, sc);
+            for (int i = k + 1 + lane; i < m; i += 32) a[i] = df_axmy(a[i], e, xs[i]);
+            const float2 rkc = df_sub(akc, d);
+            __syncwarp();
+            const float2 c2o = cn2[c];
+            float2 c2 = make_float2(0.f, 0.f);
+            bool again = false;
+            if (c2o.x != 0.f) {
+                c2 = df_sub(c2o, df_mul(rkc, rkc));
+                again = !(c2.x > thr[c]);
+            }
+            if (again) {
+                float qh = 0.f, ql = 0.f;
+                for (int i = k + 1 + lane; i < m; i += 32) df_acc(a[i], a[i], qh, ql);
+                float2 q = make_float2(qh, ql);
+                for (int o = 16; o; o >>= 1) q = df_xor_add(q, o);
+                c2 = q;
+            }
+            if (lane == 0) {
+                a[k] = rkc;
+                cn2[c] = c2;
+                if (again) thr[c] = tol3z * c2.x;
+            }
+        }
+        __syncthreads();
+        // v = x sc below the diagonal, beta on it
+        for (int i = k + 1 + tid; i < m; i += NT) Wb[(int64_t)k * ld + i] = df_mul(xs[i], sc);
+        if (tid == 0) {
+            Wb[(int64_t)k * ld + k] = s_h[0];
+            tau[B.coff + k] = s_tau;
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    // the layout of k_qrcp: every element to FP64 in place (same 8 bytes, same thread)
+    for (int c = warp; c < K; c += NW)
+        for (int i = lane; i < m; i += 32) {
+            const float2 v = Wb[(int64_t)c * ld + i];
+            W[B.moff + (int64_t)c * ld + i] = df_to_double(v);
+        }
+    if (tid == 0) {
+        rank_out[blockIdx.x] = rank;
+        r11_out[blockIdx.x] = R11;
+    }
+    for (int c = tid; c < K; c += NT) perm_out[B.coff + c] = perm[c];
+}
+
+// Q_hat = H_0 ... H_{r-1} [I_r; 0] of k_form_q in double-float arithmetic,
+// for the FP32 operator (rounded to FP32 at the end): the working columns as
+// double-floats in the FP64 operator arena (which the FP32 operator leaves
+// free), the reflector of the step staged in shared memory.
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) k_form_q_gdf(const BlkRec *__restrict__ blks, const double *__restrict__ W,
+                                                        const double *__restrict__ tau, const int32_t *__restrict__ rank,
+                                                        double *__restrict__ Q, float *__restrict__ Q32) {
+    constexpr int NT = NW * 32;
+    extern __shared__ __align__(16) float2 vs[];   // m: the reflector of the step
+    const BlkRec &B = blks[blockIdx.x];
+    const int r = rank[blockIdx.x], m = B.m, ld = B.ldm;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float2 *Qb = reinterpret_cast<float2 *>(Q + B.moff);
+    const double *Wb = W + B.moff;
+    for (int c = warp; c < r; c += NW)
+        for (int i = lane; i < ld; i += 32) Qb[(int64_t)c * ld + i] = make_float2((i == c && i < m) ? 1.f : 0.f, 0.f);
+    __syncthreads();
+    for (int k = r - 1; k >= 0; --k) {
+        const float2 tk = df_from_double(tau[B.coff + k]);
+        for (int i = k + 1 + tid; i < m; i += NT) vs[i] = df_from_double(Wb[(int64_t)k * ld + i]);
+        __syncthreads();
+        for (int c = k + warp; c < r; c += NW) {
+            float2 *q = Qb + (int64_t)c * ld;
+            float ph = 0.f, pl = 0.f;
+            for (int i = k + 1 + lane; i < m; i += 32) df_acc(vs[i], q[i], ph, pl);
+            float2 dot = make_float2(ph, pl);
+            for (int o = 16; o; o >>= 1) dot = df_xor_add(dot, o);
+            const float2 qk = q[k];
+            const float2 d = df_mul(tk, df_add(qk, dot));
+            for (int i = k + 1 + lane; i < m; i += 32) q[i] = df_axmy(q[i], d, vs[i]);
+            __syncwarp();
+            if (lane == 0) q[k] = df_sub(qk, d);
+        }
+        __syncthreads();
+    }
+    float *q32 = Q32 + B.moff;
+    for (int c = warp; c < r; c += NW)
+        for (int i = lane; i < ld; i += 32)
+            q32[(int64_t)c * ld + i] = i < m ? df_to_float(Qb[(int64_t)c * ld + i]) : 0.f;
+}
+
 // Kept columns of the original block, compacted: Op[:, c] = M[:, perm[c]] (FP64).
 template <typename TM>
 __global__ void __launch_bounds__(256) k_gather_kept(const BlkRec *__restrict__ blks, const TM *__restrict__ M,
@@ -1149,6 +1382,7 @@ static rfm_status launch_filter_t(const FilterBufs &F, double tol, cudaStream_t 
     size_t smem = 0;
     const bool dfk = use_df(F, (int)sizeof(TM));
     for (int c : {1, 2, 4, 8}) {
+        if (F.no_cluster) break;
         smem = cluster_smem(F.max_m, F.max_K, c, &nloc, &ldl, dfk);
         if (smem <= kSmemCap) { C = c; break; }
     }
@@ -1164,15 +1398,31 @@ static rfm_status launch_filter_t(const FilterBufs &F, double tol, cudaStream_t 
         if (rc != RFM_OK) return rc;
     } else {
         const size_t sm = (size_t)F.max_K * (2 * sizeof(double) + sizeof(int));
+        // FP32-assembled blocks in double-float (RFM_OPT_QR_DOUBLE_FLOAT, as the cluster kernels)
+        const bool gdf = sizeof(TM) == 4 && g_qr_df != 0 && !F.fit &&
+                         sizeof(float2) * (size_t)F.max_m + (size_t)F.max_K * 16 <= 200 * 1024;
         auto global_qr = [&](auto nwc) -> rfm_status {
             constexpr int NW = decltype(nwc)::value;
-            {
+            if (gdf) {
+                // FP32-assembled blocks in double-float arithmetic (the pivot column in shared memory)
+                const size_t smd = sizeof(float2) * (size_t)F.max_m + (size_t)F.max_K * (sizeof(float2) + sizeof(float) + sizeof(int));
+                ProfScope ps(F.fit ? "k_qrcp_fit" : "k_qrcp", st);
+                RFM_CUDA_CHECK(cudaFuncSetAttribute(k_qrcp_gdf<TM, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd));
+                k_qrcp_gdf<TM, NW><<<nb, NW * 32, smd, st>>>(F.blk, (const TM *)F.M, F.W, F.tau, F.perm, F.rank, F.r11, tol);
+                RFM_CUDA_CHECK(cudaGetLastError());
+            } else {
                 ProfScope ps(F.fit ? "k_qrcp_fit" : "k_qrcp", st);
                 RFM_CUDA_CHECK(cudaFuncSetAttribute(k_qrcp<TM, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
                 k_qrcp<TM, NW><<<nb, NW * 32, sm, st>>>(F.blk, (const TM *)F.M, F.W, F.tau, F.perm, F.rank, F.r11, tol);
                 RFM_CUDA_CHECK(cudaGetLastError());
             }
-            if (F.Q64 || F.Q32) {
+            if (gdf && F.Q32 && !F.Q64) {
+                const size_t smq = sizeof(float2) * (size_t)F.max_m;
+                ProfScope ps(F.fit ? "k_form_q_fit" : "k_form_q", st);
+                RFM_CUDA_CHECK(cudaFuncSetAttribute(k_form_q_gdf<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq));
+                k_form_q_gdf<NW><<<nb, NW * 32, smq, st>>>(F.blk, F.W, F.tau, F.rank, F.Op, F.Q32);
+                RFM_CUDA_CHECK(cudaGetLastError());
+            } else if (F.Q64 || F.Q32) {
                 ProfScope ps(F.fit ? "k_form_q_fit" : "k_form_q", st);
                 k_form_q<NW><<<nb, NW * 32, 0, st>>>(F.blk, F.W, F.tau, F.rank, F.Op, F.Q32);
                 RFM_CUDA_CHECK(cudaGetLastError());
@@ -1208,7 +1458,7 @@ const int32_t *qr_order_ptr(void *ws, const Layout &L) {
 
 static FilterBufs system_bufs(const HostPlan &P, void *ws) {
     const Layout &L = P.L;
-    FilterBufs F;
+    FilterBufs F = {};
     F.blk = ws_ptr<BlkRec>(ws, L.off_blk);
     F.order = qr_order_ptr(ws, L);
     F.M = ws_ptr<char>(ws, L.off_M);
@@ -1234,7 +1484,7 @@ static int g_force_global = 0;
 rfm_status launch_filter_bufs(const FilterBufs &F0, bool fp32, double tol, cudaStream_t st) {
     if (F0.n_blocks == 0) return RFM_OK;
     FilterBufs F = F0;
-    if (g_force_global) F.max_m = 1 << 30;   // no cluster size fits
+    if (g_force_global) F.no_cluster = true;
     return fp32 ? launch_filter_t<float>(F, tol, st) : launch_filter_t<double>(F, tol, st);
 }
 

@@ -1,6 +1,7 @@
-"""The double-float QR kernel (FP32-assembled blocks; the FP32 Q_hat or the
-kept-column operator) against the oracle's QR with column pivoting of the
-same FP32-rounded blocks, and against the FP64-arithmetic kernel.
+"""The double-float QR kernels (FP32-assembled blocks; the FP32 Q_hat or the
+kept-column operator; the cluster kernel and the global-memory one) against
+the oracle's QR with column pivoting of the same FP32-rounded blocks, and
+against the FP64-arithmetic kernel.
 
 A normalised double-float pair carries about 48 bits (unit roundoff
 u = 2^-48), so a backward-stable Householder QR in it determines |R_kk| to
@@ -47,12 +48,20 @@ def rfm():
     return R
 
 
-def _system(rfm, p, prm, op, tol):
+def _system(rfm, p, prm, op, tol, kernel="cluster"):
+    """kernel: "cluster" (the block in a cluster's shared memory) or "global"
+    (the global-memory double-float kernel that takes blocks too tall for a
+    cluster, forced here on small blocks)."""
+    from paper_2506_17626_gb300 import _native as N
     S = rfm.System([p], asm="fp32", op=op, tol=tol)
     d = torch.from_numpy(np.ascontiguousarray(prm).ravel()).cuda()
     S.assemble(d)
-    rank, perm = S.filter(want_perm=True)
-    torch.cuda.synchronize()
+    N.set_filter_kernel(kernel == "global")
+    try:
+        rank, perm = S.filter(want_perm=True)
+        torch.cuda.synchronize()
+    finally:
+        N.set_filter_kernel(False)
     return S, rank.cpu().numpy(), perm.cpu().numpy().reshape(p.J, p.K)
 
 
@@ -71,12 +80,13 @@ def check_kept(Mg, tol, rank, kept):
     return f
 
 
+@pytest.mark.parametrize("kernel", ["cluster", "global"])
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("tol", [1e-10, 1e-6, 1e-2])
-def test_double_float_filter_matches_oracle(rfm, name, tol):
+def test_double_float_filter_matches_oracle(rfm, name, tol, kernel):
     p = CASES[name]()
     prm = synth.feature_params(p)
-    S, rank, perm = _system(rfm, p, prm, "q32", tol)
+    S, rank, perm = _system(rfm, p, prm, "q32", tol, kernel)
     r11 = S.r11().cpu().numpy()
     for j in range(p.J):
         Mg = np.asfortranarray(S.block_matrix(j).double().cpu().numpy())
