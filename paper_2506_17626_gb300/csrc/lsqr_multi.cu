@@ -46,6 +46,7 @@ struct MLayout {
     int R;
     int64_t n_fitems, n_titems;
     size_t off_inst, off_fitems, off_titems, off_vt, off_w, off_y, off_z, off_u, off_t, off_out, off_part, off_scal;
+    size_t off_v32, off_u32;   // FP32 copies of v~ and u~ for the tensor-core products
     size_t total;
 };
 
@@ -77,6 +78,8 @@ static MLayout multi_layout(const HostPlan &P, int R) {
     M.off_t = take((size_t)L.block_rows * R * sizeof(double));
     M.off_out = take(cols);
     M.off_part = take(sizeof(double) * 2 * kRedCtas * R);
+    M.off_v32 = take((size_t)L.n_cols * R * sizeof(float));
+    M.off_u32 = take((size_t)L.n_rows * R * sizeof(float));
     M.off_scal = take(sizeof(MScal) * R);
     M.total = o;
     return M;
@@ -90,7 +93,7 @@ size_t multi_workspace_bytes(const HostPlan &P, int R) { return multi_layout(P, 
 
 // U[g][j] = H[j][g] (right-hand sides fastest), ||b_j||^2 partials
 __global__ void __launch_bounds__(256) k_m_load(const double *__restrict__ H, int64_t n_rows, int R,
-                                                double *__restrict__ U, double *__restrict__ part) {
+                                                double *__restrict__ U, double *__restrict__ part, float *__restrict__ U32) {
     __shared__ double red[256];
     const int Rp = R <= 1 ? 1 : (R <= 2 ? 2 : (R <= 4 ? 4 : (R <= 8 ? 8 : (R <= 16 ? 16 : (R <= 32 ? 32 : (R <= 64 ? 64 : (R <= 128 ? 128 : 256)))))));
     const int j = threadIdx.x % Rp, sub = threadIdx.x / Rp, nsub = 256 / Rp;
@@ -99,6 +102,7 @@ __global__ void __launch_bounds__(256) k_m_load(const double *__restrict__ H, in
         for (int64_t g = (int64_t)blockIdx.x * nsub + sub; g < n_rows; g += (int64_t)gridDim.x * nsub) {
             const double v = H[(int64_t)j * n_rows + g];
             U[g * R + j] = v;
+            if (U32) U32[g * R + j] = (float)v;
             ss = fma(v, v, ss);
         }
     red[threadIdx.x] = ss;
@@ -211,7 +215,10 @@ __global__ void __launch_bounds__(256) k_m_trans(const BlkRec *__restrict__ blks
 // right-hand sides) in tensor memory.  The FP32 operands are split into three
 // BF16 terms as they are staged (bf16_split3) and the six products of terms
 // whose orders add up to at most 2 are accumulated in FP32, which keeps the
-// products at FP32 accuracy.  Per 64-deep K chunk the 256 threads stage A
+// products at FP32 accuracy.  The vectors come from FP32 copies that the
+// kernels producing v~ and u~ write (one conversion per element and
+// iteration, not one per tile that reads it); 1 / alpha and 1 / beta scale
+// the finished products.  Per 64-deep K chunk the 256 threads stage A
 // (128 x 64) and B (64 x 64) in the K-major layout, one thread issues the 4 x
 // 6 MMAs (K = 16 each) and commits them to an mbarrier, and every thread waits
 // (bounded) before the next chunk overwrites the operands; then every thread
@@ -281,7 +288,7 @@ __device__ inline void tcm_teardown(uint32_t tmem) {
 // T = Q_hat_b (V / alpha) for 128 rows of one block (items: block, first row)
 __global__ void __launch_bounds__(256) k_m_fwd_tc(const BlkRec *__restrict__ blks, const int32_t *__restrict__ items,
                                                   const int32_t *__restrict__ rank, const float *__restrict__ Q,
-                                                  const double *__restrict__ VT, const MScal *__restrict__ sc, int R,
+                                                  const float *__restrict__ V32, const MScal *__restrict__ sc, int R,
                                                   double *__restrict__ T) {
     extern __shared__ __align__(128) unsigned char tsm[];
     __shared__ __align__(8) uint64_t mbar;
@@ -317,12 +324,11 @@ __global__ void __launch_bounds__(256) k_m_fwd_tc(const BlkRec *__restrict__ blk
         }
         for (int e = tid; e < kTN * (kTK / 8); e += 256) {   // B: right-hand side n, columns c0 + 8 kg .. + 7
             const int n = e % kTN, kg = e / kTN, j = j0 + n;
-            const double ia = j < R ? sc[j].inv_alpha : 0.0;
             float x[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int k = c0 + 8 * kg + q;
-                x[q] = (k < rb && j < R) ? (float)(VT[(B.coff + k) * R + j] * ia) : 0.f;
+                x[q] = (k < rb && j < R) ? V32[(B.coff + k) * R + j] : 0.f;   // v~ (scaled by 1 / alpha below)
             }
             tcm_store8(sB, tcm_off<kTK>(n, 8 * kg), kTB, x);
         }
@@ -334,7 +340,9 @@ __global__ void __launch_bounds__(256) k_m_fwd_tc(const BlkRec *__restrict__ blk
     }
     if (row < m)
         for (int q = 0; q < 32; ++q)
-            if (jc + q < R) T[(B.roff + row) * R + jc + q] = ok ? (double)acc[q] : __longlong_as_double(0x7ff8000000000000ll);
+            if (jc + q < R)
+                T[(B.roff + row) * R + jc + q] =
+                    ok ? (double)acc[q] * sc[jc + q].inv_alpha : __longlong_as_double(0x7ff8000000000000ll);
     tcm_teardown(tmem);
 }
 
@@ -342,7 +350,7 @@ __global__ void __launch_bounds__(256) k_m_fwd_tc(const BlkRec *__restrict__ blk
 // first column); U_b gathered by the block's rows
 __global__ void __launch_bounds__(256) k_m_trans_tc(const BlkRec *__restrict__ blks, const int32_t *__restrict__ items,
                                                     const int32_t *__restrict__ rank, const int32_t *__restrict__ grow,
-                                                    const float *__restrict__ Q, const double *__restrict__ U,
+                                                    const float *__restrict__ Q, const float *__restrict__ U32,
                                                     const MScal *__restrict__ sc, int R, double *__restrict__ Z) {
     extern __shared__ __align__(128) unsigned char tsm[];
     __shared__ __align__(8) uint64_t mbar;
@@ -378,12 +386,11 @@ __global__ void __launch_bounds__(256) k_m_trans_tc(const BlkRec *__restrict__ b
         }
         for (int e = tid; e < kTN * (kTK / 8); e += 256) {   // B: right-hand side n, rows i0 + 8 ig .. + 7
             const int n = e % kTN, ig = e / kTN, j = j0 + n;
-            const double ib = j < R ? sc[j].inv_beta : 0.0;
             float x[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int i = i0 + 8 * ig + q;
-                x[q] = (i < m && j < R) ? (float)(U[(int64_t)grow[B.roff + i] * R + j] * ib) : 0.f;
+                x[q] = (i < m && j < R) ? U32[(int64_t)grow[B.roff + i] * R + j] : 0.f;   // u~ (scaled by 1 / beta below)
             }
             tcm_store8(sB, tcm_off<kTK>(n, 8 * ig), kTB, x);
         }
@@ -396,7 +403,9 @@ __global__ void __launch_bounds__(256) k_m_trans_tc(const BlkRec *__restrict__ b
     const int col = c0 + 32 * (warp & 3) + lane, jc = j0 + 32 * (warp >> 2);
     if (col < rb)
         for (int q = 0; q < 32; ++q)
-            if (jc + q < R) Z[(B.coff + col) * R + jc + q] = ok ? (double)acc[q] : __longlong_as_double(0x7ff8000000000000ll);
+            if (jc + q < R)
+                Z[(B.coff + col) * R + jc + q] =
+                    ok ? (double)acc[q] * sc[jc + q].inv_beta : __longlong_as_double(0x7ff8000000000000ll);
     tcm_teardown(tmem);
 }
 
@@ -428,13 +437,14 @@ __device__ inline double m_sum(const double *part, int nctas, int R, int j) {
 // elsewhere; inv_alpha = 1 so that the forward kernel forms T = Op Y0.
 __global__ void __launch_bounds__(256) k_m_in(const double *__restrict__ Y0, const int32_t *__restrict__ rank,
                                               int64_t n_cols, int K, int R, double *__restrict__ VT,
-                                              double *__restrict__ Y, MScal *__restrict__ sc) {
+                                              double *__restrict__ Y, MScal *__restrict__ sc, float *__restrict__ V32) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_cols * R;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t slot = e / R;
         const int j = (int)(e % R);
         const double v = (int)(slot % K) < rank[slot / K] ? Y0[(int64_t)j * n_cols + slot] : 0.0;
         VT[e] = v;
+        if (V32) V32[e] = (float)v;
         Y[e] = v;
     }
     if (blockIdx.x == 0)
@@ -446,7 +456,7 @@ __global__ void __launch_bounds__(256) k_m_in(const double *__restrict__ Y0, con
 __global__ void __launch_bounds__(256) k_m_load_warm(const InstRec *__restrict__ insts,
                                                      const int32_t *__restrict__ rowlist, const double *__restrict__ H,
                                                      const double *__restrict__ T, int R, double *__restrict__ U,
-                                                     double *__restrict__ part) {
+                                                     double *__restrict__ part, float *__restrict__ U32) {
     __shared__ double red[256];
     const InstRec &I = insts[0];
     const int Rp = pow2_at_least(R), j = threadIdx.x % Rp, sub = threadIdx.x / Rp, nsub = 256 / Rp;
@@ -461,6 +471,7 @@ __global__ void __launch_bounds__(256) k_m_load_warm(const InstRec *__restrict__
             }
             const double h = H[(int64_t)j * I.N + g], u = h - s;
             U[g * R + j] = u;
+            if (U32) U32[g * R + j] = (float)u;
             su = fma(u, u, su);
             sh = fma(h, h, sh);
         }
@@ -483,13 +494,16 @@ __global__ void k_m_start(MScal *__restrict__ sc, const double *__restrict__ par
 // the sets that fall back: u = h, y = 0
 __global__ void __launch_bounds__(256) k_m_fallback(const MScal *__restrict__ sc, const double *__restrict__ H,
                                                     int64_t n_rows, int64_t n_cols, int R, double *__restrict__ U,
-                                                    double *__restrict__ Y) {
+                                                    double *__restrict__ Y, float *__restrict__ U32) {
     const int64_t nr = n_rows * R, nt = nr + n_cols * R;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
         if (e < nr) {
             const int64_t g = e / R;
             const int j = (int)(e % R);
-            if (!sc[j].start) U[e] = H[(int64_t)j * n_rows + g];
+            if (!sc[j].start) {
+                U[e] = H[(int64_t)j * n_rows + g];
+                if (U32) U32[e] = (float)U[e];
+            }
         } else {
             const int j = (int)((e - nr) % R);
             if (!sc[j].start) Y[e - nr] = 0.0;
@@ -521,7 +535,8 @@ __global__ void k_m_fixb(MScal *__restrict__ sc, int R) {
 // rows: u~ = sum over the row's block rows of T - alpha (u~ / beta), ||u~||^2
 __global__ void __launch_bounds__(256) k_m_rows(const InstRec *__restrict__ insts, const int32_t *__restrict__ rowlist,
                                                 const double *__restrict__ T, double *__restrict__ U,
-                                                const MScal *__restrict__ sc, int R, double *__restrict__ part) {
+                                                const MScal *__restrict__ sc, int R, double *__restrict__ part,
+                                                float *__restrict__ U32) {
     __shared__ double red[256];
     const InstRec &I = insts[0];
     const int Rp = pow2_at_least(R), j = threadIdx.x % Rp, sub = threadIdx.x / Rp, nsub = 256 / Rp;
@@ -537,6 +552,7 @@ __global__ void __launch_bounds__(256) k_m_rows(const InstRec *__restrict__ inst
             }
             const double u = s - al * (U[g * R + j] * ib);
             U[g * R + j] = u;
+            if (U32) U32[g * R + j] = (float)u;
             ss = fma(u, u, ss);
         }
     }
@@ -547,7 +563,7 @@ __global__ void __launch_bounds__(256) k_m_rows(const InstRec *__restrict__ inst
 __global__ void __launch_bounds__(256) k_m_cols(const int32_t *__restrict__ rank,
                                                 int64_t n_cols, int K, const double *__restrict__ Z,
                                                 double *__restrict__ VT, const MScal *__restrict__ sc, int R,
-                                                int first, double *__restrict__ part) {
+                                                int first, double *__restrict__ part, float *__restrict__ V32) {
     __shared__ double red[256];
     const int Rp = pow2_at_least(R), j = threadIdx.x % Rp, sub = threadIdx.x / Rp, nsub = 256 / Rp;
     double ss = 0.0;
@@ -558,6 +574,7 @@ __global__ void __launch_bounds__(256) k_m_cols(const int32_t *__restrict__ rank
             const double z = Z[s * R + j];
             const double v = first ? z : z - be * (VT[s * R + j] * ia);
             VT[s * R + j] = v;
+            if (V32) V32[s * R + j] = (float)v;
             ss = fma(v, v, ss);
         }
     }
@@ -758,6 +775,7 @@ rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *o
     double *Z = ws_ptr<double>(mws, M.off_z), *U = ws_ptr<double>(mws, M.off_u), *T = ws_ptr<double>(mws, M.off_t);
     double *part = ws_ptr<double>(mws, M.off_part), *ypart = part + (size_t)kRedCtas * R;
     MScal *sc = ws_ptr<MScal>(mws, M.off_scal);
+    float *V32 = tc ? ws_ptr<float>(mws, M.off_v32) : nullptr, *U32 = tc ? ws_ptr<float>(mws, M.off_u32) : nullptr;
     const size_t cols = (size_t)L.n_cols * R * sizeof(double);
     RFM_CUDA_CHECK(cudaMemsetAsync(sc, 0, sizeof(MScal) * R, st));
     RFM_CUDA_CHECK(cudaMemsetAsync(Y, 0, cols, st));
@@ -781,7 +799,7 @@ rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *o
     auto fwd = [&]() -> rfm_status {
         ProfScope ps("k_m_fwd", st);
         if (tc)
-            k_m_fwd_tc<<<gf, 256, kTSmem, st>>>(blks, d_fi, rank, (const float *)Q, VT, sc, R, T);
+            k_m_fwd_tc<<<gf, 256, kTSmem, st>>>(blks, d_fi, rank, (const float *)Q, V32, sc, R, T);
         else if (q32)
             k_m_fwd<float><<<gf, 256, 0, st>>>(blks, d_fi, rank, (const float *)Q, VT, sc, R, T);
         else
@@ -792,7 +810,7 @@ rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *o
     auto trans = [&]() -> rfm_status {
         ProfScope ps("k_m_trans", st);
         if (tc)
-            k_m_trans_tc<<<gt, 256, kTSmem, st>>>(blks, d_ti, rank, grow, (const float *)Q, U, sc, R, Z);
+            k_m_trans_tc<<<gt, 256, kTSmem, st>>>(blks, d_ti, rank, grow, (const float *)Q, U32, sc, R, Z);
         else if (q32)
             k_m_trans<float><<<gt, 256, 0, st>>>(blks, d_ti, rank, grow, (const float *)Q, U, sc, R, 0, Z);
         else
@@ -805,23 +823,23 @@ rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *o
     // alpha_1 v_1 = A^T u_1, w_1 = v_1
     if (Y0) {
         ProfScope ps("k_m_warm", st);
-        k_m_in<<<2048, 256, 0, st>>>(Y0, rank, L.n_cols, K, R, VT, Y, sc);
+        k_m_in<<<2048, 256, 0, st>>>(Y0, rank, L.n_cols, K, R, VT, Y, sc, V32);
         RFM_CUDA_CHECK(cudaGetLastError());
         if ((rc = fwd()) != RFM_OK) return rc;
-        k_m_load_warm<<<gr, 256, 0, st>>>(insts, rowlist, H, T, R, U, part);
+        k_m_load_warm<<<gr, 256, 0, st>>>(insts, rowlist, H, T, R, U, part, U32);
         k_m_start<<<gs, 64, 0, st>>>(sc, part, (int)gr, R);
-        k_m_fallback<<<2048, 256, 0, st>>>(sc, H, L.n_rows, L.n_cols, R, U, Y);
+        k_m_fallback<<<2048, 256, 0, st>>>(sc, H, L.n_rows, L.n_cols, R, U, Y, U32);
         k_m_unorm<<<gr, 256, 0, st>>>(U, L.n_rows, R, part);
         RFM_CUDA_CHECK(cudaGetLastError());
     } else {
         ProfScope ps("k_m_load", st);
-        k_m_load<<<gr, 256, 0, st>>>(H, L.n_rows, R, U, part);
+        k_m_load<<<gr, 256, 0, st>>>(H, L.n_rows, R, U, part, U32);
         RFM_CUDA_CHECK(cudaGetLastError());
     }
     k_m_beta<<<gs, 64, 0, st>>>(sc, part, (int)gr, nullptr, 0, R, 1, opts->atol, opts->btol);
     if (Y0) k_m_fixb<<<gs, 64, 0, st>>>(sc, R);
     if ((rc = trans()) != RFM_OK) return rc;
-    k_m_cols<<<gc, 256, 0, st>>>(rank, L.n_cols, K, Z, VT, sc, R, 1, part);
+    k_m_cols<<<gc, 256, 0, st>>>(rank, L.n_cols, K, Z, VT, sc, R, 1, part, V32);
     k_m_alpha<<<gs, 64, 0, st>>>(sc, part, (int)gc, R, 1, opts->atol, opts->btol, opts->max_iter);
     k_m_update<<<gc, 256, 0, st>>>(rank, L.n_cols, K, VT, W, Y, sc, R, 1, ypart);
     RFM_CUDA_CHECK(cudaGetLastError());
@@ -829,13 +847,13 @@ rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *o
         if ((rc = fwd()) != RFM_OK) return rc;
         {
             ProfScope ps("k_m_rows", st);
-            k_m_rows<<<gr, 256, 0, st>>>(insts, rowlist, T, U, sc, R, part);
+            k_m_rows<<<gr, 256, 0, st>>>(insts, rowlist, T, U, sc, R, part, U32);
         }
         k_m_beta<<<gs, 64, 0, st>>>(sc, part, (int)gr, ypart, (int)gc, R, 0, opts->atol, opts->btol);
         if ((rc = trans()) != RFM_OK) return rc;
         {
             ProfScope ps("k_m_cols", st);
-            k_m_cols<<<gc, 256, 0, st>>>(rank, L.n_cols, K, Z, VT, sc, R, 0, part);
+            k_m_cols<<<gc, 256, 0, st>>>(rank, L.n_cols, K, Z, VT, sc, R, 0, part, V32);
         }
         k_m_alpha<<<gs, 64, 0, st>>>(sc, part, (int)gc, R, 0, opts->atol, opts->btol, opts->max_iter);
         {
