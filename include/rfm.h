@@ -507,10 +507,12 @@ int rfm_profile_read(const char **names, int64_t *launches, double *ms, int max)
  *    1 forces the global-memory kernel (for comparison and testing).
  *  RFM_OPT_AUTOTUNE: 1 makes the first rfm_rrqr_filter (and rfm_fit_prepare)
  *    call for a block shape (largest block rows and features, assembly
- *    precision, block count) time every cluster size the blocks fit and keep
- *    the fastest for later calls in the process; that first call waits for
- *    its own timing runs (it synchronises the stream).  0 (default) takes the
- *    smallest cluster that holds the largest block.
+ *    precision, block count) time every cluster size the blocks fit -- or,
+ *    for blocks too large for a cluster, 8, 16 and 32 warps per block of the
+ *    global-memory kernels -- and keep the fastest for later calls in the
+ *    process; that first call waits for its own timing runs (it synchronises
+ *    the stream).  0 (default) takes the smallest cluster that holds the
+ *    largest block, or RFM_OPT_QR_WARPS warps.
  *  RFM_OPT_QR_DOUBLE_FLOAT: 1 (default) factors FP32-assembled blocks in the
  *    cluster kernel with double-float arithmetic (pairs of FP32 numbers, about
  *    48 significant bits, on the FP32 pipe; the reflector scalars, norms fed

@@ -1374,6 +1374,50 @@ static rfm_status autotune_cluster(const FilterBufs &F, double tol, int C_min, c
     return RFM_OK;
 }
 
+// Warps-per-block tuner of the global-memory kernels (same shape key as the
+// cluster tuner, their own table); the candidates run in the order 8, 16, 32.
+static std::vector<TuneEntry> g_tune_global;
+
+static int cached_global(const FilterBufs &F, int kind) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const TuneEntry &e : g_tune_global)
+        if (e.max_m == F.max_m && e.max_K == F.max_K && e.n_blocks == F.n_blocks && e.elem == kind) return e.C;
+    return 0;
+}
+
+template <typename Run>
+static rfm_status autotune_global(const FilterBufs &F, int kind, cudaStream_t st, Run run, int *best) {
+    cudaEvent_t e0, e1;
+    RFM_CUDA_CHECK(cudaEventCreate(&e0));
+    RFM_CUDA_CHECK(cudaEventCreate(&e1));
+    float best_ms = 0.f;
+    *best = 32;
+    rfm_status rc = RFM_OK;
+    for (int nw : {8, 16, 32}) {
+        cudaEventRecord(e0, st);
+        rc = run(nw);
+        cudaEventRecord(e1, st);
+        if (rc != RFM_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            set_error("QR autotuner: timing run failed");
+            rc = RFM_ECUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (nw == 8 || ms < best_ms) {
+            best_ms = ms;
+            *best = nw;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != RFM_OK) return rc;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_global.push_back(TuneEntry{F.max_m, F.max_K, F.n_blocks, kind, *best});
+    return RFM_OK;
+}
+
 template <typename TM>
 static rfm_status launch_filter_t(const FilterBufs &F, double tol, cudaStream_t st) {
     const unsigned nb = (unsigned)F.n_blocks;
@@ -1429,14 +1473,27 @@ static rfm_status launch_filter_t(const FilterBufs &F, double tol, cudaStream_t 
             }
             return RFM_OK;
         };
-        rfm_status rc;
         // (32 warps, one 1024-thread CTA per block: the heat workload's filter
         // takes 1.87 s against 2.19 s with 8 warps and 2.86 s with 4)
-        switch (g_qr_warps) {
-        case 4: rc = global_qr(std::integral_constant<int, 4>{}); break;
-        case 8: rc = global_qr(std::integral_constant<int, 8>{}); break;
-        case 16: rc = global_qr(std::integral_constant<int, 16>{}); break;
-        default: rc = global_qr(std::integral_constant<int, 32>{}); break;
+        auto run_warps = [&](int nw) -> rfm_status {
+            switch (nw) {
+            case 4: return global_qr(std::integral_constant<int, 4>{});
+            case 8: return global_qr(std::integral_constant<int, 8>{});
+            case 16: return global_qr(std::integral_constant<int, 16>{});
+            default: return global_qr(std::integral_constant<int, 32>{});
+            }
+        };
+        const int kind = tune_kind(F, (int)sizeof(TM)) + (gdf ? 16 : 0);
+        int nw = g_autotune ? cached_global(F, kind) : g_qr_warps;
+        rfm_status rc;
+        if (nw == 0) {
+            // autotuner (RFM_OPT_AUTOTUNE): time 8, 16 and 32 warps per block
+            // once each for this block shape, keep the fastest for the
+            // process, and leave its factors (the variants agree to rounding)
+            rc = autotune_global(F, kind, st, run_warps, &nw);
+            if (rc == RFM_OK && nw != 32) rc = run_warps(nw);
+        } else {
+            rc = run_warps(nw);
         }
         if (rc != RFM_OK) return rc;
     }
