@@ -14,7 +14,8 @@ rfm_status launch_assemble(const HostPlan &P, void *ws, const double *params, cu
 rfm_status launch_filter(const HostPlan &P, void *ws, double tol, cudaStream_t st);
 rfm_status launch_lsqr(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, const double *y0, double *y_out,
                        double *a_out, rfm_lsqr_report *rep, cudaStream_t st);
-rfm_status launch_coefficients(const HostPlan &P, void *ws, const double *y, double *a_out, cudaStream_t st);
+rfm_status launch_coefficients(const HostPlan &P, void *ws, const double *y, double *a_out, cudaStream_t st,
+                               int nsets = 1);
 rfm_status launch_residual(const HostPlan &P, void *ws, const double *a, double *r_out, double *rnorm,
                            cudaStream_t st);
 size_t multi_workspace_bytes(const HostPlan &P, int R);

@@ -745,9 +745,11 @@ __global__ void __launch_bounds__(kThreads) k_coefficients(const BlkRec *__restr
                                                            const int32_t *__restrict__ rank,
                                                            const int32_t *__restrict__ perm,
                                                            const double *__restrict__ y, double *__restrict__ out,
-                                                           int tri) {
+                                                           int tri, int64_t set_stride) {
     __shared__ double x[kMaxK];
     const BlkRec &B = blks[blockIdx.x];
+    y += blockIdx.y * set_stride;     // data set blockIdx.y of a many-right-hand-side solve
+    out += blockIdx.y * set_stride;
     const int r = rank ? rank[blockIdx.x] : B.K;
     for (int c = threadIdx.x; c < B.K; c += kThreads) {
         out[B.coff + c] = 0.0;
@@ -1909,14 +1911,16 @@ rfm_status launch_residual(const HostPlan &P, void *ws, const double *a, double 
     return residual64(P, ws, a, r, rnorm, 1, st);
 }
 
-rfm_status launch_coefficients(const HostPlan &P, void *ws, const double *y, double *a_out, cudaStream_t st) {
+// a = S^-1 y for nsets vectors n_cols apart (one launch)
+rfm_status launch_coefficients(const HostPlan &P, void *ws, const double *y, double *a_out, cudaStream_t st,
+                               int nsets) {
     const Layout &L = P.L;
-    if (L.n_blocks == 0) return RFM_OK;
+    if (L.n_blocks == 0 || nsets < 1) return RFM_OK;
     const bool plain = L.op == RFM_OP_PLAIN;
     ProfScope ps("k_coefficients", st);
-    k_coefficients<<<(unsigned)L.n_blocks, kThreads, 0, st>>>(
+    k_coefficients<<<dim3((unsigned)L.n_blocks, (unsigned)nsets), kThreads, 0, st>>>(
         ws_ptr<BlkRec>(ws, L.off_blk), ws_ptr<double>(ws, L.off_W), plain ? nullptr : ws_ptr<int32_t>(ws, L.off_rank),
-        plain ? nullptr : ws_ptr<int32_t>(ws, L.off_perm), y, a_out, plain ? 0 : 1);
+        plain ? nullptr : ws_ptr<int32_t>(ws, L.off_perm), y, a_out, plain ? 0 : 1, (int64_t)L.n_cols);
     RFM_CUDA_CHECK(cudaGetLastError());
     return RFM_OK;
 }
@@ -2085,7 +2089,7 @@ rfm_status launch_lsqr(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, c
         for (int s = 0; s <= R; ++s) {
             // after solve s: a = S^-1 y (a_out as scratch), r = h - M a, ||r||
             if (s == R && !opts->d_rnorm64) break;
-            rc = launch_coefficients(P, ws, yacc, a_out, st);
+            rc = launch_coefficients(P, ws, yacc, a_out, st, 1);
             if (rc != RFM_OK) return rc;
             rc = residual64(P, ws, a_out, r, opts->d_rnorm64 ? opts->d_rnorm64 + s : nullptr, R + 1, st);
             if (rc != RFM_OK) return rc;
@@ -2108,7 +2112,7 @@ rfm_status launch_lsqr(const HostPlan &P, void *ws, const rfm_lsqr_opts *opts, c
         y_fin = yacc;
     }
     if (y_out) RFM_CUDA_CHECK(cudaMemcpyAsync(y_out, y_fin, sizeof(double) * L.n_cols, cudaMemcpyDeviceToDevice, st));
-    rc = launch_coefficients(P, ws, y_fin, a_out, st);
+    rc = launch_coefficients(P, ws, y_fin, a_out, st, 1);
     if (rc != RFM_OK) return rc;
     if (rep) {
         ProfScope ps("k_report", st);

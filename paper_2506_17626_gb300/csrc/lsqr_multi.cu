@@ -27,7 +27,8 @@
 
 namespace rfm {
 
-rfm_status launch_coefficients(const HostPlan &P, void *ws, const double *y, double *a_out, cudaStream_t st);
+rfm_status launch_coefficients(const HostPlan &P, void *ws, const double *y, double *a_out, cudaStream_t st,
+                               int nsets = 1);
 
 constexpr int kMT = 64;     // rows (forward) or columns (transposed) of a CTA tile
 constexpr int kMR = 64;     // right-hand sides of a CTA tile
@@ -218,15 +219,19 @@ __global__ void __launch_bounds__(256) k_m_trans(const BlkRec *__restrict__ blks
 // products at FP32 accuracy.  The vectors come from FP32 copies that the
 // kernels producing v~ and u~ write (one conversion per element and
 // iteration, not one per tile that reads it); 1 / alpha and 1 / beta scale
-// the finished products.  Per 64-deep K chunk the 256 threads stage A
-// (128 x 64) and B (64 x 64) in the K-major layout, one thread issues the 4 x
-// 6 MMAs (K = 16 each) and commits them to an mbarrier, and every thread waits
-// (bounded) before the next chunk overwrites the operands; then every thread
-// adds its part of the chunk's product (warps w and w + 4: TMEM lanes 32 (w
-// mod 4) .. + 31, columns 32 (w / 4) .. + 31) to FP32 registers, so the
-// tensor memory sums only 64 products at a time (its accumulation truncates:
-// over whole blocks of thousands of rows it lost about a decade against the
-// CUDA cores' FP32 sums).  A wait that runs out gives NaN outputs.
+// the finished products.  Per 64-deep K chunk the 256 threads store A
+// (128 x 64) and B (64 x 64) in the K-major layout from registers, one thread
+// issues the 4 x 6 MMAs (K = 16 each) and commits them to an mbarrier, and
+// while they run every thread loads its part of the next chunk into
+// registers (48 loads in flight per thread: the loads' latency, not the
+// MMAs, bounds the products); every thread then waits (bounded) and adds its
+// part of the chunk's product (warps w and w + 4: TMEM lanes 32 (w mod 4) ..
+// + 31, columns 32 (w / 4) .. + 31) to FP32 registers, so the tensor memory
+// sums only 64 products at a time (its accumulation truncates: over whole
+// blocks of thousands of rows it lost about a decade against the CUDA cores'
+// FP32 sums).  The finished tile goes out through shared memory, one warp
+// per output row of 64 consecutive doubles.  A wait that runs out gives NaN
+// outputs.
 // ---------------------------------------------------------------------------
 constexpr int kTM = 128;                  // rows of D (block rows, or kept columns)
 constexpr int kTN = 64;                   // right-hand sides per CTA
@@ -235,8 +240,9 @@ constexpr int kTA = kTM * kTK * 2;        // bytes of one BF16 split of A
 constexpr int kTB = kTN * kTK * 2;        // bytes of one BF16 split of B
 constexpr int kTSmem = 3 * kTA + 3 * kTB; // dynamic shared memory
 
-__device__ inline void tcm_round(unsigned char *sA, unsigned char *sB, uint32_t tmem, uint64_t *mbar,
-                                 unsigned &parity, bool &ok) {
+// every thread's staging of the chunk is in shared memory: one thread issues
+// the 4 x 6 MMAs of the chunk and commits them to the mbarrier
+__device__ inline void tcm_issue(unsigned char *sA, unsigned char *sB, uint32_t tmem, uint64_t *mbar) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -252,6 +258,11 @@ __device__ inline void tcm_round(unsigned char *sA, unsigned char *sB, uint32_t 
                         idesc, (kk > 0 || t < 5) ? 1u : 0u);
         tcm_commit(mbar);
     }
+}
+
+// bounded wait for the chunk's MMAs (ok = false when it runs out); the
+// operands in shared memory are free afterwards
+__device__ inline void tcm_finish(uint64_t *mbar, unsigned &parity, bool &ok) {
     const bool got = __syncthreads_and(tcm_wait(mbar, parity));
     if (!got) {
         (void)tcm_wait(mbar, parity);   // MMAs still in flight: a second bounded wait
@@ -259,6 +270,39 @@ __device__ inline void tcm_round(unsigned char *sA, unsigned char *sB, uint32_t 
     }
     parity ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// acc += this thread's 32 columns of the chunk's product (TMEM lanes 32 (w mod
+// 4) .. + 31 for warps w and w + 4, columns 32 (w / 4) .. + 31), 16 at a time
+__device__ inline void tcm_accumulate(uint32_t tmem, float (&acc)[32]) {
+    const int warp = threadIdx.x >> 5;
+    const uint32_t a = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2));
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float v[16];
+        tcm_ld16(a + 16 * h, v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[16 * h + q] += v[q];
+    }
+}
+
+// The finished 128 x 64 tile leaves through shared memory (the operand
+// buffers, free once the last MMAs completed), rows padded to 65 doubles, so
+// that each output row's 64 consecutive doubles are written by one warp.
+constexpr int kTLd = kTN + 1;
+static_assert(kTM * kTLd * 8 <= kTSmem, "output tile fits the operand buffers");
+
+__device__ inline void tcm_tile_to_smem(double *stile, const float (&acc)[32], const MScal *__restrict__ sc,
+                                        bool by_alpha, int j0, int R, bool ok) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lr = 32 * (warp & 3) + lane, lc = 32 * (warp >> 2);
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+        const int j = j0 + lc + q;
+        const double s = j < R ? (by_alpha ? sc[j].inv_alpha : sc[j].inv_beta) : 0.0;
+        stile[lr * kTLd + lc + q] = ok ? (double)acc[q] * s : __longlong_as_double(0x7ff8000000000000ll);
+    }
+    __syncthreads();
 }
 
 __device__ inline uint32_t tcm_setup(uint64_t *mbar, uint32_t *tmem_slot) {
@@ -285,11 +329,15 @@ __device__ inline void tcm_teardown(uint32_t tmem) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTN) : "memory");
 }
 
-// T = Q_hat_b (V / alpha) for 128 rows of one block (items: block, first row)
-__global__ void __launch_bounds__(256) k_m_fwd_tc(const BlkRec *__restrict__ blks, const int32_t *__restrict__ items,
-                                                  const int32_t *__restrict__ rank, const float *__restrict__ Q,
-                                                  const float *__restrict__ V32, const MScal *__restrict__ sc, int R,
-                                                  double *__restrict__ T) {
+// T = Q_hat_b (V / alpha) for 128 rows of one block (items: block, first row).
+// Each thread stages 4 core-matrix rows of A (row tid mod 128, column groups
+// tid / 128 + 2i) and 2 of B (data set tid mod 64, column groups tid / 64 +
+// 4i); the next chunk's 48 loads are issued while the current chunk's MMAs
+// run.
+__global__ void __launch_bounds__(256, 2) k_m_fwd_tc(const BlkRec *__restrict__ blks, const int32_t *__restrict__ items,
+                                                     const int32_t *__restrict__ rank, const float *__restrict__ Q,
+                                                     const float *__restrict__ V32, const MScal *__restrict__ sc, int R,
+                                                     double *__restrict__ T) {
     extern __shared__ __align__(128) unsigned char tsm[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
@@ -298,8 +346,8 @@ __global__ void __launch_bounds__(256) k_m_fwd_tc(const BlkRec *__restrict__ blk
     const BlkRec &B = blks[b];
     const int rb = rank[b], m = B.m, ldm = B.ldm, j0 = blockIdx.y * kTN;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int row = r0 + 32 * (warp & 3) + lane, jc = j0 + 32 * (warp >> 2);
     if (rb <= 0) {   // no kept columns: the rows' partials are zero (uniform over the CTA)
+        const int row = r0 + 32 * (warp & 3) + lane, jc = j0 + 32 * (warp >> 2);
         if (row < m)
             for (int q = 0; q < 32; ++q)
                 if (jc + q < R) T[(B.roff + row) * R + jc + q] = 0.0;
@@ -311,47 +359,56 @@ __global__ void __launch_bounds__(256) k_m_fwd_tc(const BlkRec *__restrict__ blk
     float acc[32];
 #pragma unroll
     for (int q = 0; q < 32; ++q) acc[q] = 0.f;
+    const int ra = tid & (kTM - 1), ga = tid >> 7;    // A: row, first column group
+    const int nb = tid & (kTN - 1), gb = tid >> 6;    // B: data set, first column group
+    const bool row_in = r0 + ra < m, set_in = j0 + nb < R;
+    const float *qa = Q + B.moff + r0 + ra;
+    const float *vb = V32 + (int64_t)B.coff * R + j0 + nb;
+    float xa[4][8], xb[2][8];
+    auto load = [&](int c0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = c0 + 8 * (ga + 2 * i) + q;
+                xa[i][q] = (k < rb && row_in) ? __ldg(qa + (int64_t)k * ldm) : 0.f;
+            }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = c0 + 8 * (gb + 4 * i) + q;
+                xb[i][q] = (k < rb && set_in) ? vb[(int64_t)k * R] : 0.f;   // v~ (scaled by 1 / alpha below)
+            }
+    };
+    load(0);
     for (int c0 = 0; c0 < rb && ok; c0 += kTK) {
-        for (int e = tid; e < kTM * (kTK / 8); e += 256) {   // A: row r, columns c0 + 8 kg .. + 7
-            const int r = e % kTM, kg = e / kTM;
-            float x[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int k = c0 + 8 * kg + q;
-                x[q] = (k < rb && r0 + r < m) ? __ldg(Q + B.moff + (int64_t)k * ldm + r0 + r) : 0.f;
-            }
-            tcm_store8(sA, tcm_off<kTK>(r, 8 * kg), kTA, x);
-        }
-        for (int e = tid; e < kTN * (kTK / 8); e += 256) {   // B: right-hand side n, columns c0 + 8 kg .. + 7
-            const int n = e % kTN, kg = e / kTN, j = j0 + n;
-            float x[8];
+        for (int i = 0; i < 4; ++i) tcm_store8(sA, tcm_off<kTK>(ra, 8 * (ga + 2 * i)), kTA, xa[i]);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int k = c0 + 8 * kg + q;
-                x[q] = (k < rb && j < R) ? V32[(B.coff + k) * R + j] : 0.f;   // v~ (scaled by 1 / alpha below)
-            }
-            tcm_store8(sB, tcm_off<kTK>(n, 8 * kg), kTB, x);
-        }
-        tcm_round(sA, sB, tmem, &mbar, parity, ok);
-        float v[32];
-        tcm_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2)), v);
-#pragma unroll
-        for (int q = 0; q < 32; ++q) acc[q] += v[q];
+        for (int i = 0; i < 2; ++i) tcm_store8(sB, tcm_off<kTK>(nb, 8 * (gb + 4 * i)), kTB, xb[i]);
+        tcm_issue(sA, sB, tmem, &mbar);
+        if (c0 + kTK < rb) load(c0 + kTK);
+        tcm_finish(&mbar, parity, ok);
+        tcm_accumulate(tmem, acc);
     }
-    if (row < m)
-        for (int q = 0; q < 32; ++q)
-            if (jc + q < R)
-                T[(B.roff + row) * R + jc + q] =
-                    ok ? (double)acc[q] * sc[jc + q].inv_alpha : __longlong_as_double(0x7ff8000000000000ll);
+    double *stile = reinterpret_cast<double *>(tsm);
+    tcm_tile_to_smem(stile, acc, sc, true, j0, R, ok);
+    const int nj = min(kTN, R - j0);
+    for (int lr = warp; lr < kTM && r0 + lr < m; lr += 8)
+        for (int jj = lane; jj < nj; jj += 32) T[(B.roff + r0 + lr) * R + j0 + jj] = stile[lr * kTLd + jj];
     tcm_teardown(tmem);
 }
 
 // Z = Q_hat_b^T (U_b / beta) for 128 kept columns of one block (items: block,
-// first column); U_b gathered by the block's rows
-__global__ void __launch_bounds__(256) k_m_trans_tc(const BlkRec *__restrict__ blks, const int32_t *__restrict__ items,
-                                                    const int32_t *__restrict__ rank, const int32_t *__restrict__ grow,
-                                                    const float *__restrict__ Q, const float *__restrict__ U32,
-                                                    const MScal *__restrict__ sc, int R, double *__restrict__ Z) {
+// first column); U_b gathered by the block's rows.  Staging as in k_m_fwd_tc:
+// 4 core-matrix rows of A (kept column tid mod 128, row groups tid / 128 +
+// 2i, two 16-byte loads each) and 2 of B (data set tid mod 64, row groups
+// tid / 64 + 4i), the next chunk's loads issued while the MMAs run.
+__global__ void __launch_bounds__(256, 2) k_m_trans_tc(const BlkRec *__restrict__ blks, const int32_t *__restrict__ items,
+                                                       const int32_t *__restrict__ rank, const int32_t *__restrict__ grow,
+                                                       const float *__restrict__ Q, const float *__restrict__ U32,
+                                                       const MScal *__restrict__ sc, int R, double *__restrict__ Z) {
     extern __shared__ __align__(128) unsigned char tsm[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
@@ -367,45 +424,60 @@ __global__ void __launch_bounds__(256) k_m_trans_tc(const BlkRec *__restrict__ b
     float acc[32];
 #pragma unroll
     for (int q = 0; q < 32; ++q) acc[q] = 0.f;
-    for (int i0 = 0; i0 < m && ok; i0 += kTK) {
-        for (int e = tid; e < kTM * (kTK / 8); e += 256) {   // A: kept column c, rows i0 + 8 ig .. + 7
-            const int c = e % kTM, ig = e / kTM, i = i0 + 8 * ig;
-            float x[8];
-            if (c0 + c < rb && i < ldm) {   // ldm is a multiple of 32: the 8 rows lie inside the column
-                const float4 *src = reinterpret_cast<const float4 *>(Q + B.moff + (int64_t)(c0 + c) * ldm + i);
+    const int ca = tid & (kTM - 1), ga = tid >> 7;    // A: kept column, first row group
+    const int nb = tid & (kTN - 1), gb = tid >> 6;    // B: data set, first row group
+    const bool col_in = c0 + ca < rb, set_in = j0 + nb < R;
+    const float *qa = Q + B.moff + (int64_t)(c0 + ca) * ldm;
+    const int32_t *gr = grow + B.roff;
+    const float *ub = U32 + j0 + nb;
+    float xa[4][8], xb[2][8];
+    auto load = [&](int i0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = i0 + 8 * (ga + 2 * i);
+            if (col_in && r < ldm) {   // ldm is a multiple of 32: the 8 rows lie inside the column
+                const float4 *src = reinterpret_cast<const float4 *>(qa + r);
                 const float4 p = __ldg(src), q4 = __ldg(src + 1);
-                x[0] = p.x; x[1] = p.y; x[2] = p.z; x[3] = p.w; x[4] = q4.x; x[5] = q4.y; x[6] = q4.z; x[7] = q4.w;
+                xa[i][0] = p.x; xa[i][1] = p.y; xa[i][2] = p.z; xa[i][3] = p.w;
+                xa[i][4] = q4.x; xa[i][5] = q4.y; xa[i][6] = q4.z; xa[i][7] = q4.w;
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
-                    if (i + q >= m) x[q] = 0.f;
+                    if (r + q >= m) xa[i][q] = 0.f;
             } else {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) x[q] = 0.f;
+                for (int q = 0; q < 8; ++q) xa[i][q] = 0.f;
             }
-            tcm_store8(sA, tcm_off<kTK>(c, 8 * ig), kTA, x);
         }
-        for (int e = tid; e < kTN * (kTK / 8); e += 256) {   // B: right-hand side n, rows i0 + 8 ig .. + 7
-            const int n = e % kTN, ig = e / kTN, j = j0 + n;
-            float x[8];
+        int g[2][8];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const int i = i0 + 8 * ig + q;
-                x[q] = (i < m && j < R) ? U32[(int64_t)grow[B.roff + i] * R + j] : 0.f;   // u~ (scaled by 1 / beta below)
+                const int r = i0 + 8 * (gb + 4 * i) + q;
+                g[i][q] = (r < m && set_in) ? __ldg(gr + r) : -1;
             }
-            tcm_store8(sB, tcm_off<kTK>(n, 8 * ig), kTB, x);
-        }
-        tcm_round(sA, sB, tmem, &mbar, parity, ok);
-        float v[32];
-        tcm_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2)), v);
 #pragma unroll
-        for (int q = 0; q < 32; ++q) acc[q] += v[q];
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                xb[i][q] = g[i][q] >= 0 ? ub[(int64_t)g[i][q] * R] : 0.f;   // u~ (scaled by 1 / beta below)
+    };
+    load(0);
+    for (int i0 = 0; i0 < m && ok; i0 += kTK) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) tcm_store8(sA, tcm_off<kTK>(ca, 8 * (ga + 2 * i)), kTA, xa[i]);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) tcm_store8(sB, tcm_off<kTK>(nb, 8 * (gb + 4 * i)), kTB, xb[i]);
+        tcm_issue(sA, sB, tmem, &mbar);
+        if (i0 + kTK < m) load(i0 + kTK);
+        tcm_finish(&mbar, parity, ok);
+        tcm_accumulate(tmem, acc);
     }
-    const int col = c0 + 32 * (warp & 3) + lane, jc = j0 + 32 * (warp >> 2);
-    if (col < rb)
-        for (int q = 0; q < 32; ++q)
-            if (jc + q < R)
-                Z[(B.coff + col) * R + jc + q] =
-                    ok ? (double)acc[q] * sc[jc + q].inv_beta : __longlong_as_double(0x7ff8000000000000ll);
+    double *stile = reinterpret_cast<double *>(tsm);
+    tcm_tile_to_smem(stile, acc, sc, false, j0, R, ok);
+    const int nj = min(kTN, R - j0);
+    for (int lc = warp; lc < kTM && c0 + lc < rb; lc += 8)
+        for (int jj = lane; jj < nj; jj += 32) Z[(B.coff + c0 + lc) * R + j0 + jj] = stile[lc * kTLd + jj];
     tcm_teardown(tmem);
 }
 
@@ -427,10 +499,25 @@ __device__ inline void m_partials(double v, int R, double *red, double *part) {
     }
 }
 
-__device__ inline double m_sum(const double *part, int nctas, int R, int j) {
+// The scalar kernels run kMSub threads per right-hand side (kMSets sets per
+// CTA): thread sub of set j sums the partials of CTAs sub, sub + kMSub, ...,
+// and the kMSub sums are combined in sub order, so the result is fixed for a
+// given partial count; valid in the sub = 0 threads.  Every thread of the CTA
+// calls it (it synchronises).
+constexpr int kMSets = 64, kMSub = 8;
+
+__device__ inline double m_sum(const double *part, int nctas, int R, int j, double (*red)[kMSets]) {
+    const int js = threadIdx.x % kMSets, sub = threadIdx.x / kMSets;
     double t = 0.0;
-    for (int c = 0; c < nctas; ++c) t += part[(int64_t)c * R + j];
-    return t;
+    if (j < R)
+        for (int c = sub; c < nctas; c += kMSub) t += part[(int64_t)c * R + j];
+    red[sub][js] = t;
+    __syncthreads();
+    double s = 0.0;
+    if (sub == 0)
+        for (int u = 0; u < kMSub; ++u) s += red[u][js];
+    __syncthreads();
+    return s;
 }
 
 // Warm starts.  VT and Y = Y0 (sets contiguous in Y0) on the kept slots, 0
@@ -482,10 +569,13 @@ __global__ void __launch_bounds__(256) k_m_load_warm(const InstRec *__restrict__
 
 // per set: keep the warm start when ||h - Op y0|| < ||h||, else fall back to
 // the zero start (the rule of rfm_lsqr_solve)
-__global__ void k_m_start(MScal *__restrict__ sc, const double *__restrict__ part, int nctas, int R) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= R) return;
-    const double r0 = sqrt(m_sum(part, nctas, R, j)), hn = sqrt(m_sum(part + (int64_t)nctas * R, nctas, R, j));
+__global__ void __launch_bounds__(kMSets * kMSub) k_m_start(MScal *__restrict__ sc, const double *__restrict__ part,
+                                                             int nctas, int R) {
+    __shared__ double red[kMSub][kMSets];
+    const int j = blockIdx.x * kMSets + threadIdx.x % kMSets;
+    const double r2 = m_sum(part, nctas, R, j, red), h2 = m_sum(part + (int64_t)nctas * R, nctas, R, j, red);
+    if (threadIdx.x >= kMSets || j >= R) return;
+    const double r0 = sqrt(r2), hn = sqrt(h2);
     sc[j].r0w = r0;
     sc[j].hnorm = hn;
     sc[j].start = r0 < hn ? 1 : 0;
@@ -585,13 +675,16 @@ __global__ void __launch_bounds__(256) k_m_cols(const int32_t *__restrict__ rank
 
 // The stopping test of the previous iteration k (its estimates, ||y_k|| from
 // its update's partials; the tests of rfm_lsqr_solve), then beta = ||u~||.
-__global__ void k_m_beta(MScal *__restrict__ sc, const double *__restrict__ part, int nctas,
-                         const double *__restrict__ ypart, int ynctas, int R, int first, double atol, double btol) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= R) return;
+__global__ void __launch_bounds__(kMSets * kMSub) k_m_beta(MScal *__restrict__ sc, const double *__restrict__ part,
+                                                            int nctas, const double *__restrict__ ypart, int ynctas,
+                                                            int R, int first, double atol, double btol) {
+    __shared__ double red[kMSub][kMSets];
+    const int j = blockIdx.x * kMSets + threadIdx.x % kMSets;
+    const double b2 = m_sum(part, nctas, R, j, red);
+    const double y2 = ypart ? m_sum(ypart, ynctas, R, j, red) : 0.0;
+    if (threadIdx.x >= kMSets || j >= R) return;
     MScal &q = sc[j];
-    const double b2 = m_sum(part, nctas, R, j);
-    if (!first && ypart) q.ynorm = sqrt(m_sum(ypart, ynctas, R, j));
+    if (!first && ypart) q.ynorm = sqrt(y2);
     if (q.done == 2) q.done = 1;
     if (!first && !q.done && q.itn > 0) {
         const double anorm = sqrt(q.anorm2);
@@ -622,13 +715,16 @@ __global__ void k_m_beta(MScal *__restrict__ sc, const double *__restrict__ part
 // of the 1982 paper (||B_k||_F^2 gains alpha_k^2 + beta_{k+1}^2); an exact
 // stop (alpha or beta zero) or a non-finite scalar ends the right-hand side
 // after this iteration's update (done = 2)
-__global__ void k_m_alpha(MScal *__restrict__ sc, const double *__restrict__ part, int nctas, int R, int first,
-                          double atol, double btol, int max_iter) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= R) return;
+__global__ void __launch_bounds__(kMSets * kMSub) k_m_alpha(MScal *__restrict__ sc, const double *__restrict__ part,
+                                                             int nctas, int R, int first, double atol, double btol,
+                                                             int max_iter) {
+    __shared__ double red[kMSub][kMSets];
+    const int j = blockIdx.x * kMSets + threadIdx.x % kMSets;
+    const double a2 = m_sum(part, nctas, R, j, red);
+    if (threadIdx.x >= kMSets || j >= R) return;
     MScal &q = sc[j];
     if (!first && q.done) return;
-    const double al = sqrt(m_sum(part, nctas, R, j));
+    const double al = sqrt(a2);
     const double al_old = q.alpha;
     q.inv_alpha_old = q.inv_alpha;
     q.alpha = al;
@@ -786,7 +882,7 @@ rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *o
     const InstRec *insts = ws_ptr<InstRec>(ws, L.off_inst);
     const int32_t *rowlist = ws_ptr<int32_t>(ws, L.off_rowlist);
     const int K = (int)P.inst[0].K;
-    const unsigned gr = red_grid(L.n_rows, R), gc = red_grid(L.n_cols, R), gs = (unsigned)((R + 63) / 64);
+    const unsigned gr = red_grid(L.n_rows, R), gc = red_grid(L.n_cols, R), gs = (unsigned)((R + kMSets - 1) / kMSets);
     const dim3 gf((unsigned)(fi.size() / 2), (unsigned)((R + kMR - 1) / kMR)),
         gt((unsigned)(ti.size() / 2), (unsigned)((R + kMR - 1) / kMR));
     if (tc) {
@@ -827,7 +923,7 @@ rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *o
         RFM_CUDA_CHECK(cudaGetLastError());
         if ((rc = fwd()) != RFM_OK) return rc;
         k_m_load_warm<<<gr, 256, 0, st>>>(insts, rowlist, H, T, R, U, part, U32);
-        k_m_start<<<gs, 64, 0, st>>>(sc, part, (int)gr, R);
+        k_m_start<<<gs, kMSets * kMSub, 0, st>>>(sc, part, (int)gr, R);
         k_m_fallback<<<2048, 256, 0, st>>>(sc, H, L.n_rows, L.n_cols, R, U, Y, U32);
         k_m_unorm<<<gr, 256, 0, st>>>(U, L.n_rows, R, part);
         RFM_CUDA_CHECK(cudaGetLastError());
@@ -836,11 +932,11 @@ rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *o
         k_m_load<<<gr, 256, 0, st>>>(H, L.n_rows, R, U, part, U32);
         RFM_CUDA_CHECK(cudaGetLastError());
     }
-    k_m_beta<<<gs, 64, 0, st>>>(sc, part, (int)gr, nullptr, 0, R, 1, opts->atol, opts->btol);
+    k_m_beta<<<gs, kMSets * kMSub, 0, st>>>(sc, part, (int)gr, nullptr, 0, R, 1, opts->atol, opts->btol);
     if (Y0) k_m_fixb<<<gs, 64, 0, st>>>(sc, R);
     if ((rc = trans()) != RFM_OK) return rc;
     k_m_cols<<<gc, 256, 0, st>>>(rank, L.n_cols, K, Z, VT, sc, R, 1, part, V32);
-    k_m_alpha<<<gs, 64, 0, st>>>(sc, part, (int)gc, R, 1, opts->atol, opts->btol, opts->max_iter);
+    k_m_alpha<<<gs, kMSets * kMSub, 0, st>>>(sc, part, (int)gc, R, 1, opts->atol, opts->btol, opts->max_iter);
     k_m_update<<<gc, 256, 0, st>>>(rank, L.n_cols, K, VT, W, Y, sc, R, 1, ypart);
     RFM_CUDA_CHECK(cudaGetLastError());
     for (int it = 0; it < opts->max_iter; ++it) {
@@ -849,13 +945,19 @@ rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *o
             ProfScope ps("k_m_rows", st);
             k_m_rows<<<gr, 256, 0, st>>>(insts, rowlist, T, U, sc, R, part, U32);
         }
-        k_m_beta<<<gs, 64, 0, st>>>(sc, part, (int)gr, ypart, (int)gc, R, 0, opts->atol, opts->btol);
+        {
+            ProfScope ps("k_m_beta", st);
+            k_m_beta<<<gs, kMSets * kMSub, 0, st>>>(sc, part, (int)gr, ypart, (int)gc, R, 0, opts->atol, opts->btol);
+        }
         if ((rc = trans()) != RFM_OK) return rc;
         {
             ProfScope ps("k_m_cols", st);
             k_m_cols<<<gc, 256, 0, st>>>(rank, L.n_cols, K, Z, VT, sc, R, 0, part, V32);
         }
-        k_m_alpha<<<gs, 64, 0, st>>>(sc, part, (int)gc, R, 0, opts->atol, opts->btol, opts->max_iter);
+        {
+            ProfScope ps("k_m_alpha", st);
+            k_m_alpha<<<gs, kMSets * kMSub, 0, st>>>(sc, part, (int)gc, R, 0, opts->atol, opts->btol, opts->max_iter);
+        }
         {
             ProfScope ps("k_m_update", st);
             k_m_update<<<gc, 256, 0, st>>>(rank, L.n_cols, K, VT, W, Y, sc, R, 0, ypart);
@@ -870,11 +972,7 @@ rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *o
     double *out = ws_ptr<double>(mws, M.off_out);
     k_m_out<<<2048, 256, 0, st>>>(Y, L.n_cols, R, out);
     RFM_CUDA_CHECK(cudaGetLastError());
-    for (int j = 0; j < R; ++j) {
-        rc = launch_coefficients(P, ws, out + (size_t)j * L.n_cols, A + (size_t)j * L.n_cols, st);
-        if (rc != RFM_OK) return rc;
-    }
-    return RFM_OK;
+    return launch_coefficients(P, ws, out, A, st, R);
 }
 
 

@@ -72,6 +72,19 @@ __device__ inline void tcm_ld32(uint32_t addr, float (&v)[32]) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes
+__device__ inline void tcm_ld16(uint32_t addr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 // x = h0 + h1 + h2 in BF16 (each the rounding of what the previous terms
 // leave), 24 significant bits in all: the FP32 value to within about
 // 2^-24 |x|.  Products of two split values keep the six terms whose orders
@@ -84,14 +97,30 @@ __device__ inline void bf16_split3(float x, __nv_bfloat16 &h0, __nv_bfloat16 &h1
     h2 = __float2bfloat16_rn(r2);
 }
 
+// bf16_split3 of two values at once (packed conversions, the same rounding):
+// the three terms as bf16x2 words, x[0] in the low half (the lower address)
+__device__ inline void bf16_split3x2(float a, float b, uint32_t &w0, uint32_t &w1, uint32_t &w2) {
+    const __nv_bfloat162 h0 = __floats2bfloat162_rn(a, b);
+    const float2 f0 = __bfloat1622float2(h0);
+    const float ra = a - f0.x, rb = b - f0.y;
+    const __nv_bfloat162 h1 = __floats2bfloat162_rn(ra, rb);
+    const float2 f1 = __bfloat1622float2(h1);
+    const __nv_bfloat162 h2 = __floats2bfloat162_rn(ra - f1.x, rb - f1.y);
+    w0 = *reinterpret_cast<const uint32_t *>(&h0);
+    w1 = *reinterpret_cast<const uint32_t *>(&h1);
+    w2 = *reinterpret_cast<const uint32_t *>(&h2);
+}
+
 // 8 consecutive-K values of one row, split, stored as 16-byte core-matrix
 // rows into the three split operands (byte offset off, split stride sz)
 __device__ inline void tcm_store8(unsigned char *base, int off, int sz, const float (&x)[8]) {
-    __align__(16) __nv_bfloat16 h[3][8];
+    uint4 w[3];
+    bf16_split3x2(x[0], x[1], w[0].x, w[1].x, w[2].x);
+    bf16_split3x2(x[2], x[3], w[0].y, w[1].y, w[2].y);
+    bf16_split3x2(x[4], x[5], w[0].z, w[1].z, w[2].z);
+    bf16_split3x2(x[6], x[7], w[0].w, w[1].w, w[2].w);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) bf16_split3(x[q], h[0][q], h[1][q], h[2][q]);
-#pragma unroll
-    for (int s = 0; s < 3; ++s) *reinterpret_cast<uint4 *>(base + s * sz + off) = *reinterpret_cast<const uint4 *>(h[s]);
+    for (int s = 0; s < 3; ++s) *reinterpret_cast<uint4 *>(base + s * sz + off) = w[s];
 }
 
 }  // namespace rfm
