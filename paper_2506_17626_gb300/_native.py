@@ -229,6 +229,12 @@ def set_qr_warps(n: int):
     check("rfm_set_option", load().rfm_set_option(9, int(n)))
 
 
+def set_qr_panel(n: int):
+    """Reflectors per pass of the global-memory double-float Q_hat formation
+    (RFM_OPT_QR_PANEL: 1, 2, 4 or 8)."""
+    check("rfm_set_option", load().rfm_set_option(10, int(n)))
+
+
 def set_qr_double_float(on):
     """Factor FP32-assembled blocks with double-float arithmetic (True or 1,
     the default) or with FP64 arithmetic (False or 0); 2 also puts

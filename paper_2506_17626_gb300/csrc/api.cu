@@ -32,6 +32,7 @@ void set_mlp_tc_threads(int threads);
 void set_lsqr_lag(int tenths);
 void set_multi_tc(int v);
 void set_qr_warps(int v);
+void set_qr_panel(int v);
 rfm_status launch_eval_noalloc(const HostPlan &P, const double *params, const double *a, const double *X,
                                const int64_t *pt_off, double *u, double *err, cudaStream_t st);
 rfm_status launch_eval(const HostPlan &P, void *ws, const double *params, const double *a, const double *X,
@@ -361,6 +362,10 @@ rfm_status rfm_set_option(int option, int value) {
     }
     if (option == RFM_OPT_QR_WARPS && (value == 4 || value == 8 || value == 16 || value == 32)) {
         set_qr_warps(value);
+        return RFM_OK;
+    }
+    if (option == RFM_OPT_QR_PANEL && (value == 1 || value == 2 || value == 4 || value == 8)) {
+        set_qr_panel(value);
         return RFM_OK;
     }
     if (option == RFM_OPT_MULTI_TENSOR_CORES && (value == 0 || value == 1)) {

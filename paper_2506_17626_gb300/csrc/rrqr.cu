@@ -448,6 +448,104 @@ __global__ void __launch_bounds__(NW * 32) k_form_q_gdf(const BlkRec *__restrict
             q32[(int64_t)c * ld + i] = i < m ? df_to_float(Qb[(int64_t)c * ld + i]) : 0.f;
 }
 
+// The same Q_hat with NB reflectors per pass over each column (compact WY
+// form, Schreiber and Van Loan 1989): H_k0 ... H_k0+nb-1 = I - V T V^T with
+// V the panel's reflectors (unit at row k0 + t, zeros above) and T upper
+// triangular, T[t][t] = tau_t, T[0:t, t] = -tau_t T[0:t, 0:t] (V[:, 0:t]^T
+// v_t).  Going backwards over the panels, every column c >= k0 takes
+// w = V^T q, z = T w, q -= V z: one read and one read-write of the column per
+// panel instead of per reflector, the same arithmetic per element.  All in
+// double-float; the panel (nb x (m - k0)) lives in shared memory.
+template <int NW, int NB>
+__global__ void __launch_bounds__(NW * 32) k_form_q_gdf_blk(const BlkRec *__restrict__ blks, const double *__restrict__ W,
+                                                            const double *__restrict__ tau, const int32_t *__restrict__ rank,
+                                                            double *__restrict__ Q, float *__restrict__ Q32) {
+    constexpr int NT = NW * 32;
+    extern __shared__ __align__(16) float2 vs[];   // NB x ld: v_t at vs[t * ld + i]
+    __shared__ float2 Gs[NB][NB], Ts[NB][NB];
+    const BlkRec &B = blks[blockIdx.x];
+    const int r = rank[blockIdx.x], m = B.m, ld = B.ldm;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float2 *Qb = reinterpret_cast<float2 *>(Q + B.moff);
+    const double *Wb = W + B.moff;
+    for (int c = warp; c < r; c += NW)
+        for (int i = lane; i < ld; i += 32) Qb[(int64_t)c * ld + i] = make_float2((i == c && i < m) ? 1.f : 0.f, 0.f);
+    for (int p = (r + NB - 1) / NB - 1; p >= 0; --p) {
+        const int k0 = p * NB, nb = min(NB, r - k0), mr = m - k0;
+        __syncthreads();   // the previous panel's columns and shared arrays are done with
+        for (int e = tid; e < nb * mr; e += NT) {
+            const int t = e / mr, i = k0 + e % mr;
+            vs[t * ld + i] = i < k0 + t ? make_float2(0.f, 0.f)
+                                        : (i == k0 + t ? make_float2(1.f, 0.f) : df_from_double(Wb[(int64_t)(k0 + t) * ld + i]));
+        }
+        __syncthreads();
+        // G[s][t] = v_s . v_t for s < t (v_t is zero above row k0 + t), one warp per pair
+        for (int pr = warp; pr < nb * nb; pr += NW) {
+            const int s2 = pr / nb, t = pr % nb;
+            if (s2 >= t) continue;
+            float h = 0.f, l = 0.f;
+            for (int i = k0 + t + lane; i < m; i += 32) df_acc(vs[s2 * ld + i], vs[t * ld + i], h, l);
+            float2 d = make_float2(h, l);
+            for (int o = 16; o; o >>= 1) d = df_xor_add(d, o);
+            if (lane == 0) Gs[s2][t] = d;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int t = 0; t < nb; ++t) {
+                const float2 tt = df_from_double(tau[B.coff + k0 + t]);
+                for (int s2 = 0; s2 < t; ++s2) {
+                    float h = 0.f, l = 0.f;
+                    for (int u = s2; u < t; ++u) df_acc(Ts[s2][u], Gs[u][t], h, l);
+                    Ts[s2][t] = df_neg(df_mul(tt, df_add(make_float2(h, 0.f), make_float2(l, 0.f))));
+                }
+                Ts[t][t] = tt;
+            }
+        }
+        __syncthreads();
+        for (int c = k0 + warp; c < r; c += NW) {
+            float2 *q = Qb + (int64_t)c * ld;
+            float wh[NB], wl[NB];
+#pragma unroll
+            for (int t = 0; t < NB; ++t) wh[t] = wl[t] = 0.f;
+            for (int i = k0 + lane; i < m; i += 32) {
+                const float2 qi = q[i];
+#pragma unroll
+                for (int t = 0; t < NB; ++t)
+                    if (t < nb) df_acc(vs[t * ld + i], qi, wh[t], wl[t]);
+            }
+            float2 z[NB];
+#pragma unroll
+            for (int t = 0; t < NB; ++t) {
+                float2 w = make_float2(wh[t], wl[t]);
+                for (int o = 16; o; o >>= 1) w = df_xor_add(w, o);
+                z[t] = w;   // w_t, every lane
+            }
+            // z = T w in place (upper triangular: z_s uses w_t for t >= s)
+#pragma unroll
+            for (int s2 = 0; s2 < NB; ++s2) {
+                if (s2 >= nb) break;
+                float h = 0.f, l = 0.f;
+#pragma unroll
+                for (int t = 0; t < NB; ++t)
+                    if (t >= s2 && t < nb) df_acc(Ts[s2][t], z[t], h, l);
+                z[s2] = df_add(make_float2(h, 0.f), make_float2(l, 0.f));
+            }
+            for (int i = k0 + lane; i < m; i += 32) {
+                float h = 0.f, l = 0.f;
+#pragma unroll
+                for (int t = 0; t < NB; ++t)
+                    if (t < nb) df_acc(vs[t * ld + i], z[t], h, l);
+                q[i] = df_sub(q[i], df_add(make_float2(h, 0.f), make_float2(l, 0.f)));
+            }
+        }
+    }
+    __syncthreads();
+    float *q32 = Q32 + B.moff;
+    for (int c = warp; c < r; c += NW)
+        for (int i = lane; i < ld; i += 32)
+            q32[(int64_t)c * ld + i] = i < m ? df_to_float(Qb[(int64_t)c * ld + i]) : 0.f;
+}
+
 // Kept columns of the original block, compacted: Op[:, c] = M[:, perm[c]] (FP64).
 template <typename TM>
 __global__ void __launch_bounds__(256) k_gather_kept(const BlkRec *__restrict__ blks, const TM *__restrict__ M,
@@ -1285,6 +1383,8 @@ static rfm_status launch_cluster_c(int C, const FilterBufs &F, double tol, cudaS
 static int g_autotune = 0;
 static int g_qr_warps = 32;  // warps per CTA of the global-memory QR kernels
 void set_qr_warps(int v) { g_qr_warps = v; }
+static int g_qr_panel = 8;   // reflectors per pass of the double-float Q_hat formation (1, 2, 4 or 8)
+void set_qr_panel(int v) { g_qr_panel = v; }
 struct TuneEntry {
     int64_t max_m, max_K, n_blocks;
     int elem, C;
@@ -1418,6 +1518,43 @@ static rfm_status autotune_global(const FilterBufs &F, int kind, cudaStream_t st
     return RFM_OK;
 }
 
+// Panel-width tuner of the double-float Q_hat formation: times each
+// candidate once, keeps the fastest for the process and leaves its Q_hat
+// (the candidate last timed is re-run when it is not the fastest).
+template <typename Run>
+static rfm_status autotune_panel(const FilterBufs &F, int kind, cudaStream_t st, Run run, const std::vector<int> &cands,
+                                 int *best) {
+    cudaEvent_t e0, e1;
+    RFM_CUDA_CHECK(cudaEventCreate(&e0));
+    RFM_CUDA_CHECK(cudaEventCreate(&e1));
+    float best_ms = 0.f;
+    rfm_status rc = RFM_OK;
+    for (size_t k = 0; k < cands.size(); ++k) {
+        cudaEventRecord(e0, st);
+        rc = run(cands[k]);
+        cudaEventRecord(e1, st);
+        if (rc != RFM_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            set_error("QR autotuner: timing run failed");
+            rc = RFM_ECUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (k == 0 || ms < best_ms) {
+            best_ms = ms;
+            *best = cands[k];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == RFM_OK && !cands.empty() && *best != cands.back()) rc = run(*best);
+    if (rc != RFM_OK) return rc;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_global.push_back(TuneEntry{F.max_m, F.max_K, F.n_blocks, kind, *best});
+    return RFM_OK;
+}
+
 template <typename TM>
 static rfm_status launch_filter_t(const FilterBufs &F, double tol, cudaStream_t st) {
     const unsigned nb = (unsigned)F.n_blocks;
@@ -1445,6 +1582,33 @@ static rfm_status launch_filter_t(const FilterBufs &F, double tol, cudaStream_t 
         // FP32-assembled blocks in double-float (RFM_OPT_QR_DOUBLE_FLOAT, as the cluster kernels)
         const bool gdf = sizeof(TM) == 4 && g_qr_df != 0 && !F.fit &&
                          sizeof(float2) * (size_t)F.max_m + (size_t)F.max_K * 16 <= 200 * 1024;
+        // Q_hat of the double-float path: panel width pw (1 = one reflector
+        // per pass; 2, 4, 8 = compact WY panels in shared memory)
+        const size_t ldmax = (size_t)((F.max_m + kLdAlign - 1) / kLdAlign * kLdAlign);
+        auto panel_fits = [&](int pw) { return pw == 1 || sizeof(float2) * (size_t)pw * ldmax <= 200 * 1024; };
+        auto form_gdf = [&](auto nwc, int pw) -> rfm_status {
+            constexpr int NW = decltype(nwc)::value;
+            ProfScope ps(F.fit ? "k_form_q_fit" : "k_form_q", st);
+            if (pw == 1) {
+                const size_t smq = sizeof(float2) * (size_t)F.max_m;
+                RFM_CUDA_CHECK(cudaFuncSetAttribute(k_form_q_gdf<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq));
+                k_form_q_gdf<NW><<<nb, NW * 32, smq, st>>>(F.blk, F.W, F.tau, F.rank, F.Op, F.Q32);
+            } else {
+                const size_t smq = sizeof(float2) * (size_t)pw * ldmax;
+                auto launch = [&](auto kern) {
+                    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
+                    kern<<<nb, NW * 32, smq, st>>>(F.blk, F.W, F.tau, F.rank, F.Op, F.Q32);
+                };
+                if (pw == 2) launch(k_form_q_gdf_blk<NW, 2>);
+                else if (pw == 4) launch(k_form_q_gdf_blk<NW, 4>);
+                else launch(k_form_q_gdf_blk<NW, 8>);
+            }
+            RFM_CUDA_CHECK(cudaGetLastError());
+            return RFM_OK;
+        };
+        int panel = 1;
+        for (int pw : {8, 4, 2})
+            if (pw <= g_qr_panel && panel_fits(pw)) { panel = pw; break; }
         auto global_qr = [&](auto nwc) -> rfm_status {
             constexpr int NW = decltype(nwc)::value;
             if (gdf) {
@@ -1461,11 +1625,7 @@ static rfm_status launch_filter_t(const FilterBufs &F, double tol, cudaStream_t 
                 RFM_CUDA_CHECK(cudaGetLastError());
             }
             if (gdf && F.Q32 && !F.Q64) {
-                const size_t smq = sizeof(float2) * (size_t)F.max_m;
-                ProfScope ps(F.fit ? "k_form_q_fit" : "k_form_q", st);
-                RFM_CUDA_CHECK(cudaFuncSetAttribute(k_form_q_gdf<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq));
-                k_form_q_gdf<NW><<<nb, NW * 32, smq, st>>>(F.blk, F.W, F.tau, F.rank, F.Op, F.Q32);
-                RFM_CUDA_CHECK(cudaGetLastError());
+                return form_gdf(nwc, panel);
             } else if (F.Q64 || F.Q32) {
                 ProfScope ps(F.fit ? "k_form_q_fit" : "k_form_q", st);
                 k_form_q<NW><<<nb, NW * 32, 0, st>>>(F.blk, F.W, F.tau, F.rank, F.Op, F.Q32);
@@ -1486,12 +1646,34 @@ static rfm_status launch_filter_t(const FilterBufs &F, double tol, cudaStream_t 
         const int kind = tune_kind(F, (int)sizeof(TM)) + (gdf ? 16 : 0);
         int nw = g_autotune ? cached_global(F, kind) : g_qr_warps;
         rfm_status rc;
+        const bool tune_panel = g_autotune && gdf && F.Q32 && !F.Q64;
+        const int pkind = kind + 32;
+        if (tune_panel) {
+            const int pc = cached_global(F, pkind);
+            if (pc > 0) panel = pc;
+        }
         if (nw == 0) {
             // autotuner (RFM_OPT_AUTOTUNE): time 8, 16 and 32 warps per block
             // once each for this block shape, keep the fastest for the
             // process, and leave its factors (the variants agree to rounding)
             rc = autotune_global(F, kind, st, run_warps, &nw);
             if (rc == RFM_OK && nw != 32) rc = run_warps(nw);
+            if (rc == RFM_OK && tune_panel) {
+                // then the Q_hat panel width with those warps (the formation
+                // alone, which starts from the reflectors every time)
+                auto run_form = [&](int pw) -> rfm_status {
+                    switch (nw) {
+                    case 4: return form_gdf(std::integral_constant<int, 4>{}, pw);
+                    case 8: return form_gdf(std::integral_constant<int, 8>{}, pw);
+                    case 16: return form_gdf(std::integral_constant<int, 16>{}, pw);
+                    default: return form_gdf(std::integral_constant<int, 32>{}, pw);
+                    }
+                };
+                std::vector<int> cands;
+                for (int pw : {1, 2, 4, 8})
+                    if (panel_fits(pw)) cands.push_back(pw);
+                rc = autotune_panel(F, pkind, st, run_form, cands, &panel);
+            }
         } else {
             rc = run_warps(nw);
         }
