@@ -509,8 +509,8 @@ int rfm_profile_read(const char **names, int64_t *launches, double *ms, int max)
  *    call for a block shape (largest block rows and features, assembly
  *    precision, block count) time every cluster size the blocks fit -- or,
  *    for blocks too large for a cluster, 8, 16 and 32 warps per block of the
- *    global-memory kernels, then the Q_hat panel widths of RFM_OPT_QR_PANEL
- *    that fit -- and keep the fastest for later calls in the
+ *    global-memory kernels, then the panel widths of RFM_OPT_QR_PANEL that
+ *    fit -- and keep the fastest for later calls in the
  *    process; that first call waits for its own timing runs (it synchronises
  *    the stream).  0 (default) takes the smallest cluster that holds the
  *    largest block, or RFM_OPT_QR_WARPS warps.
@@ -557,12 +557,17 @@ int rfm_profile_read(const char **names, int64_t *launches, double *ms, int max)
  *    global-memory QR kernels (blocks too large for a cluster: one CTA per
  *    block, warps over the trailing columns).  The factors agree to rounding
  *    (the pivot column's norm is summed in another order).
- *  RFM_OPT_QR_PANEL: reflectors applied per pass over each column when those
- *    kernels form the FP32 Q_hat of FP32-assembled blocks in double-float
- *    arithmetic: 1 (one reflector at a time), 2, 4 or 8 (default; compact WY
- *    panels I - V T V^T staged in shared memory, narrowed to what fits).  With
+ *  RFM_OPT_QR_PANEL: panel width of those kernels on FP32-assembled blocks in
+ *    double-float arithmetic: 1 (one step at a time), 2, 4 or 8 (default),
+ *    narrowed to what fits in shared memory.  The QR with column pivoting
+ *    defers the trailing update over panels of up to 4 of its steps
+ *    (Quintana-Orti, Sun and Bischof: per step one read of the trailing
+ *    columns, the pivot row and the norm downdates; one rank-nb update per
+ *    panel), and the FP32 Q_hat is formed from compact WY panels
+ *    I - V T V^T of the full width.  With
  *    RFM_OPT_AUTOTUNE the first call for a block shape times every width
- *    that fits and keeps the fastest.  Q_hat agrees to rounding. */
+ *    that fits and keeps the fastest.  R and Q_hat agree to rounding; the
+ *    kept columns agree except where two trailing norms tie to within it. */
 enum {
     RFM_OPT_FILTER_KERNEL = 0,
     RFM_OPT_AUTOTUNE = 1,

@@ -406,6 +406,283 @@ __global__ void __launch_bounds__(NW * 32) k_qrcp_gdf(const BlkRec *__restrict__
     for (int c = tid; c < K; c += NT) perm_out[B.coff + c] = perm[c];
 }
 
+// k_qrcp_gdf with the trailing update deferred over panels of NB steps (the
+// BLAS-3 QR with column pivoting of Quintana-Orti, Sun and Bischof 1998):
+// within a panel the trailing columns keep their values from the panel's
+// start, A0, and the updated matrix is A0 - V F^T, with V the panel's
+// reflectors (v_j: 1 at its step's row, v below) and F[c][j] = tau_j
+// (A_j^T v_j)[c], A_j the matrix after the panel's first j steps.  Step k =
+// k0 + j:
+//   pivot from the downdated squared norms (as k_qrcp_gdf); the pivot column
+//     updated, x = A0[k:, k] - V[k:, 0:j] F[k, 0:j]^T, and its reflector;
+//   y = V[k:, 0:j]^T v_j, then per trailing column c: one read pass for
+//     A0[k:, c]^T v_j, F[c][j] = tau_j (that - F[c, 0:j] y), the row-k entry
+//     r_kc = A0[k][c] - V[k, 0:j] F[c, 0:j]^T - F[c][j] (an entry of R, stored
+//     in place), and the norm downdate ||a_c||^2 -= r_kc^2 with the same
+//     recompute rule (the recomputed norm from the updated column);
+// after the panel, one pass A0[k0+nb:, c] -= V[k0+nb:, :] F[c, :]^T per
+// trailing column.  Per panel of nb steps each trailing column is read nb
+// times and read and written once, against nb times each in k_qrcp_gdf.
+// Shared memory: V (NB x ld double-floats), F (K x NB), the norms, the
+// recompute thresholds and the permutation.
+template <typename TM, int NW, int NB>
+__global__ void __launch_bounds__(NW * 32) k_qrcp_gdf_blk(const BlkRec *__restrict__ blks, const TM *__restrict__ M,
+                                                          double *__restrict__ W, double *__restrict__ tau,
+                                                          int32_t *__restrict__ perm_out, int32_t *__restrict__ rank_out,
+                                                          double *__restrict__ r11_out, double tol) {
+    constexpr int NT = NW * 32;
+    extern __shared__ __align__(16) unsigned char gsm[];
+    const BlkRec B = blks[blockIdx.x];
+    const int m = B.m, K = B.K, ld = B.ldm;
+    float2 *Vs = reinterpret_cast<float2 *>(gsm);        // NB x ld: v_j at Vs[j * ld + i], rows >= its step
+    float2 *Fs = Vs + (size_t)NB * ld;                   // K x NB: F[c][j] at Fs[c * NB + j]
+    float2 *cn2 = Fs + (size_t)K * NB;                   // K squared trailing norms
+    float *thr = reinterpret_cast<float *>(cn2 + K);     // K recompute thresholds
+    int *perm = reinterpret_cast<int *>(thr + K);        // K
+    __shared__ long long red_k[NW];
+    __shared__ int red_o[NW], red_c[NW];
+    __shared__ float2 s_red[NW];
+    __shared__ float2 s_h[4];      // beta, sc, g, tau of the step
+    __shared__ float2 s_y[NB];     // V[k:, 0:j]^T v_j
+    __shared__ double s_nx, s_tau;
+    __shared__ int s_piv;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float2 *Wb = reinterpret_cast<float2 *>(W + B.moff);
+    const TM *Mb = M + B.moff;
+    const float tol3z = 1.4901161193847656e-08f;   // sqrt of the FP64 epsilon, as in the FP64 kernels
+
+    for (int c = warp; c < K; c += NW) {
+        float sh = 0.f, sl = 0.f;
+        for (int i = lane; i < m; i += 32) {
+            const float2 a = dfg_in(Mb[(int64_t)c * ld + i]);
+            Wb[(int64_t)c * ld + i] = a;
+            df_acc(a, a, sh, sl);
+        }
+        float2 s2 = make_float2(sh, sl);
+        for (int o = 16; o; o >>= 1) s2 = df_xor_add(s2, o);
+        if (lane == 0) {
+            cn2[c] = s2;
+            thr[c] = tol3z * s2.x;
+            perm[c] = c;
+        }
+    }
+    for (int e = tid; e < K * NB; e += NT) Fs[e] = make_float2(0.f, 0.f);
+    __syncthreads();
+
+    const int steps = m < K ? m : K;
+    double R11 = 0.0;
+    int rank = steps;
+    bool stop = false;
+    for (int k0 = 0; k0 < steps && !stop; k0 += NB) {
+        const int nbp = min(NB, steps - k0);
+        int j = 0;
+        for (; j < nbp; ++j) {
+            const int k = k0 + j;
+            // 1. pivot: the trailing column of largest squared norm, ties to the lowest original index
+            long long bk = -1;
+            int bo = INT_MAX, bc = k;
+            for (int c = k + tid; c < K; c += NT) {
+                const long long kc = dfg_key(cn2[c]);
+                if (key_better(kc, perm[c], bk, bo)) { bk = kc; bo = perm[c]; bc = c; }
+            }
+            for (int o = 16; o; o >>= 1) {
+                const long long k2 = __shfl_xor_sync(kFull, bk, o);
+                const int o2 = __shfl_xor_sync(kFull, bo, o), c2 = __shfl_xor_sync(kFull, bc, o);
+                if (key_better(k2, o2, bk, bo)) { bk = k2; bo = o2; bc = c2; }
+            }
+            if (lane == 0) { red_k[warp] = bk; red_o[warp] = bo; red_c[warp] = bc; }
+            __syncthreads();
+            if (tid == 0) {
+                long long v = red_k[0];
+                int o = red_o[0], c = red_c[0];
+                for (int w = 1; w < NW; ++w)
+                    if (key_better(red_k[w], red_o[w], v, o)) { v = red_k[w]; o = red_o[w]; c = red_c[w]; }
+                s_piv = c;
+            }
+            __syncthreads();
+            const int piv = s_piv;
+            if (piv != k) {   // whole columns (R entries above, panel-start values below) with their F rows
+                for (int i = tid; i < m; i += NT) {
+                    const float2 a = Wb[(int64_t)k * ld + i];
+                    Wb[(int64_t)k * ld + i] = Wb[(int64_t)piv * ld + i];
+                    Wb[(int64_t)piv * ld + i] = a;
+                }
+                if (tid < NB) {
+                    const float2 f = Fs[k * NB + tid];
+                    Fs[k * NB + tid] = Fs[piv * NB + tid];
+                    Fs[piv * NB + tid] = f;
+                }
+                if (tid == 0) {
+                    const float2 t = cn2[k]; cn2[k] = cn2[piv]; cn2[piv] = t;
+                    const float u = thr[k]; thr[k] = thr[piv]; thr[piv] = u;
+                    const int q = perm[k]; perm[k] = perm[piv]; perm[piv] = q;
+                }
+            }
+            __syncthreads();
+            // 2. the updated pivot column (rows k..m) into V's slot j, its exact norm, reflector scalars
+            {
+                float2 fk[NB];
+#pragma unroll
+                for (int jj = 0; jj < NB; ++jj) fk[jj] = Fs[k * NB + jj];
+                float sh = 0.f, sl = 0.f;
+                for (int i = k + tid; i < m; i += NT) {
+                    float2 x = Wb[(int64_t)k * ld + i];
+                    if (j > 0) {
+                        float h = 0.f, l = 0.f;
+#pragma unroll
+                        for (int jj = 0; jj < NB; ++jj)
+                            if (jj < j) df_acc(Vs[jj * ld + i], fk[jj], h, l);
+                        x = df_sub(x, df_add(make_float2(h, 0.f), make_float2(l, 0.f)));
+                    }
+                    Vs[j * ld + i] = x;
+                    df_acc(x, x, sh, sl);
+                }
+                float2 s2 = make_float2(sh, sl);
+                for (int o = 16; o; o >>= 1) s2 = df_xor_add(s2, o);
+                if (lane == 0) s_red[warp] = s2;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                float2 t = lane < NW ? s_red[lane] : make_float2(0.f, 0.f);
+                for (int o = 16; o; o >>= 1) t = df_xor_add(t, o);
+                if (lane == 0) {
+                    const float2 nxd = t.x > 0.f ? df_sqrt(t) : make_float2(0.f, 0.f);
+                    s_nx = df_to_double(nxd);
+                    if (nxd.x > 0.f) {
+                        const float2 alpha = Vs[j * ld + k];
+                        const float2 beta = alpha.x >= 0.f ? df_neg(nxd) : nxd;
+                        const float2 amb = df_sub(alpha, beta);
+                        const float2 inv = df_rcp(df_mul(amb, beta));
+                        const float2 g = df_neg(df_mul(amb, inv));
+                        const float2 tk = df_mul(amb, g);
+                        s_h[0] = beta;
+                        s_h[1] = df_mul(beta, inv);
+                        s_h[2] = g;
+                        s_h[3] = tk;
+                        s_tau = df_to_double(tk);
+                    }
+                }
+            }
+            __syncthreads();
+            const double nx = s_nx;
+            if (k == 0) R11 = nx;
+            if (nx == 0.0 || nx < tol * R11) { rank = k; stop = true; break; }
+            const float2 sc = s_h[1], tk = s_h[3];
+            // 3. v_j = x sc below the diagonal (1 on it) in V and in the block, beta on the diagonal
+            for (int i = k + 1 + tid; i < m; i += NT) {
+                const float2 v = df_mul(Vs[j * ld + i], sc);
+                Vs[j * ld + i] = v;
+                Wb[(int64_t)k * ld + i] = v;
+            }
+            if (tid == 0) {
+                Vs[j * ld + k] = make_float2(1.f, 0.f);
+                Wb[(int64_t)k * ld + k] = s_h[0];
+                tau[B.coff + k] = s_tau;
+            }
+            __syncthreads();
+            // 4. y = V[k:, 0:j]^T v_j
+            for (int jj = warp; jj < j; jj += NW) {
+                float h = 0.f, l = 0.f;
+                for (int i = k + lane; i < m; i += 32) df_acc(Vs[jj * ld + i], Vs[j * ld + i], h, l);
+                float2 d = make_float2(h, l);
+                for (int o = 16; o; o >>= 1) d = df_xor_add(d, o);
+                if (lane == 0) s_y[jj] = d;
+            }
+            __syncthreads();
+            // 5. trailing columns: F[c][j], the row-k entry (of R), the norm downdate
+            float2 yv[NB], vk[NB];
+#pragma unroll
+            for (int jj = 0; jj < NB; ++jj) {
+                yv[jj] = jj < j ? s_y[jj] : make_float2(0.f, 0.f);
+                vk[jj] = jj < j ? Vs[jj * ld + k] : make_float2(0.f, 0.f);
+            }
+            for (int c = k + 1 + warp; c < K; c += NW) {
+                float2 *a = Wb + (int64_t)c * ld;
+                float ph = 0.f, pl = 0.f;
+                for (int i = k + lane; i < m; i += 32) df_acc(Vs[j * ld + i], a[i], ph, pl);
+                float2 dot = make_float2(ph, pl);
+                for (int o = 16; o; o >>= 1) dot = df_xor_add(dot, o);
+                float2 fr[NB];
+#pragma unroll
+                for (int jj = 0; jj < NB; ++jj) fr[jj] = Fs[c * NB + jj];
+                float h = 0.f, l = 0.f;
+#pragma unroll
+                for (int jj = 0; jj < NB; ++jj)
+                    if (jj < j) df_acc(fr[jj], yv[jj], h, l);
+                const float2 fcj = df_mul(tk, df_sub(dot, df_add(make_float2(h, 0.f), make_float2(l, 0.f))));
+                h = 0.f;
+                l = 0.f;
+#pragma unroll
+                for (int jj = 0; jj < NB; ++jj)
+                    if (jj < j) df_acc(vk[jj], fr[jj], h, l);
+                const float2 akc = a[k];
+                const float2 rkc = df_sub(df_sub(akc, df_add(make_float2(h, 0.f), make_float2(l, 0.f))), fcj);
+                __syncwarp();
+                const float2 c2o = cn2[c];
+                float2 c2 = make_float2(0.f, 0.f);
+                bool again = false;
+                if (c2o.x != 0.f) {
+                    c2 = df_sub(c2o, df_mul(rkc, rkc));
+                    again = !(c2.x > thr[c]);
+                }
+                if (again) {   // the updated column below row k, formed on the fly
+                    float qh = 0.f, ql = 0.f;
+                    for (int i = k + 1 + lane; i < m; i += 32) {
+                        float uh = 0.f, ul = 0.f;
+#pragma unroll
+                        for (int jj = 0; jj < NB; ++jj)
+                            if (jj < j) df_acc(Vs[jj * ld + i], fr[jj], uh, ul);
+                        df_acc(Vs[j * ld + i], fcj, uh, ul);
+                        const float2 u = df_sub(a[i], df_add(make_float2(uh, 0.f), make_float2(ul, 0.f)));
+                        df_acc(u, u, qh, ql);
+                    }
+                    float2 q = make_float2(qh, ql);
+                    for (int o = 16; o; o >>= 1) q = df_xor_add(q, o);
+                    c2 = q;
+                }
+                if (lane == 0) {
+                    Fs[c * NB + j] = fcj;
+                    a[k] = rkc;
+                    cn2[c] = c2;
+                    if (again) thr[c] = tol3z * c2.x;
+                }
+            }
+            __syncthreads();
+        }
+        if (stop) break;
+        // 6. the panel's update of the trailing columns below its rows, A0 -= V F^T
+        const int kend = k0 + nbp;
+        for (int c = kend + warp; c < K; c += NW) {
+            float2 *a = Wb + (int64_t)c * ld;
+            float2 fr[NB];
+#pragma unroll
+            for (int jj = 0; jj < NB; ++jj) fr[jj] = Fs[c * NB + jj];
+            for (int i = kend + lane; i < m; i += 32) {
+                float h = 0.f, l = 0.f;
+#pragma unroll
+                for (int jj = 0; jj < NB; ++jj)
+                    if (jj < nbp) df_acc(Vs[jj * ld + i], fr[jj], h, l);
+                a[i] = df_sub(a[i], df_add(make_float2(h, 0.f), make_float2(l, 0.f)));
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < (K - kend) * NB; e += NT) Fs[(size_t)kend * NB + e] = make_float2(0.f, 0.f);
+        __syncthreads();
+    }
+    __syncthreads();
+    // the layout of k_qrcp: every element to FP64 in place (same 8 bytes, same thread)
+    for (int c = warp; c < K; c += NW)
+        for (int i = lane; i < m; i += 32) {
+            const float2 v = Wb[(int64_t)c * ld + i];
+            W[B.moff + (int64_t)c * ld + i] = df_to_double(v);
+        }
+    if (tid == 0) {
+        rank_out[blockIdx.x] = rank;
+        r11_out[blockIdx.x] = R11;
+    }
+    for (int c = tid; c < K; c += NT) perm_out[B.coff + c] = perm[c];
+}
+
 // Q_hat = H_0 ... H_{r-1} [I_r; 0] of k_form_q in double-float arithmetic,
 // for the FP32 operator (rounded to FP32 at the end): the working columns as
 // double-floats in the FP64 operator arena (which the FP32 operator leaves
@@ -1383,7 +1660,7 @@ static rfm_status launch_cluster_c(int C, const FilterBufs &F, double tol, cudaS
 static int g_autotune = 0;
 static int g_qr_warps = 32;  // warps per CTA of the global-memory QR kernels
 void set_qr_warps(int v) { g_qr_warps = v; }
-static int g_qr_panel = 8;   // reflectors per pass of the double-float Q_hat formation (1, 2, 4 or 8)
+static int g_qr_panel = 8;   // panel width of the double-float global QR and Q_hat formation (1, 2, 4 or 8)
 void set_qr_panel(int v) { g_qr_panel = v; }
 struct TuneEntry {
     int64_t max_m, max_K, n_blocks;
@@ -1518,9 +1795,10 @@ static rfm_status autotune_global(const FilterBufs &F, int kind, cudaStream_t st
     return RFM_OK;
 }
 
-// Panel-width tuner of the double-float Q_hat formation: times each
-// candidate once, keeps the fastest for the process and leaves its Q_hat
-// (the candidate last timed is re-run when it is not the fastest).
+// Panel-width tuner of the double-float global kernels (QR and Q_hat
+// formation): times each candidate once, keeps the fastest for the process
+// and leaves its factors (the candidate last timed is re-run when it is not
+// the fastest).
 template <typename Run>
 static rfm_status autotune_panel(const FilterBufs &F, int kind, cudaStream_t st, Run run, const std::vector<int> &cands,
                                  int *best) {
@@ -1586,6 +1864,18 @@ static rfm_status launch_filter_t(const FilterBufs &F, double tol, cudaStream_t 
         // per pass; 2, 4, 8 = compact WY panels in shared memory)
         const size_t ldmax = (size_t)((F.max_m + kLdAlign - 1) / kLdAlign * kLdAlign);
         auto panel_fits = [&](int pw) { return pw == 1 || sizeof(float2) * (size_t)pw * ldmax <= 200 * 1024; };
+        // the panel QR's shared memory: V (pw x ld), F (K x pw), norms, thresholds, permutation
+        auto qr_panel_smem = [&](int pw) {
+            return sizeof(float2) * ((size_t)pw * ldmax + (size_t)F.max_K * pw + (size_t)F.max_K) +
+                   (size_t)F.max_K * (sizeof(float) + sizeof(int));
+        };
+        // (the QR's panels stop at 4 steps: with 8 its 1024-thread CTAs spill
+        // under their 64 registers per thread, 618 against 596 ms on heat)
+        auto qr_panel_for = [&](int pw) {
+            for (int q : {4, 2})
+                if (q <= pw && qr_panel_smem(q) <= 225 * 1024) return q;
+            return 1;
+        };
         auto form_gdf = [&](auto nwc, int pw) -> rfm_status {
             constexpr int NW = decltype(nwc)::value;
             ProfScope ps(F.fit ? "k_form_q_fit" : "k_form_q", st);
@@ -1612,11 +1902,24 @@ static rfm_status launch_filter_t(const FilterBufs &F, double tol, cudaStream_t 
         auto global_qr = [&](auto nwc) -> rfm_status {
             constexpr int NW = decltype(nwc)::value;
             if (gdf) {
-                // FP32-assembled blocks in double-float arithmetic (the pivot column in shared memory)
-                const size_t smd = sizeof(float2) * (size_t)F.max_m + (size_t)F.max_K * (sizeof(float2) + sizeof(float) + sizeof(int));
+                // FP32-assembled blocks in double-float arithmetic: one step at
+                // a time (the pivot column in shared memory) or in panels of
+                // qp steps with the trailing update deferred
                 ProfScope ps(F.fit ? "k_qrcp_fit" : "k_qrcp", st);
-                RFM_CUDA_CHECK(cudaFuncSetAttribute(k_qrcp_gdf<TM, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd));
-                k_qrcp_gdf<TM, NW><<<nb, NW * 32, smd, st>>>(F.blk, (const TM *)F.M, F.W, F.tau, F.perm, F.rank, F.r11, tol);
+                const int qp = qr_panel_for(panel);
+                if (qp == 1) {
+                    const size_t smd = sizeof(float2) * (size_t)F.max_m + (size_t)F.max_K * (sizeof(float2) + sizeof(float) + sizeof(int));
+                    RFM_CUDA_CHECK(cudaFuncSetAttribute(k_qrcp_gdf<TM, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd));
+                    k_qrcp_gdf<TM, NW><<<nb, NW * 32, smd, st>>>(F.blk, (const TM *)F.M, F.W, F.tau, F.perm, F.rank, F.r11, tol);
+                } else {
+                    const size_t smd = qr_panel_smem(qp);
+                    auto launch = [&](auto kern) {
+                        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd);
+                        kern<<<nb, NW * 32, smd, st>>>(F.blk, (const TM *)F.M, F.W, F.tau, F.perm, F.rank, F.r11, tol);
+                    };
+                    if (qp == 2) launch(k_qrcp_gdf_blk<TM, NW, 2>);
+                    else launch(k_qrcp_gdf_blk<TM, NW, 4>);
+                }
                 RFM_CUDA_CHECK(cudaGetLastError());
             } else {
                 ProfScope ps(F.fit ? "k_qrcp_fit" : "k_qrcp", st);
@@ -1659,20 +1962,18 @@ static rfm_status launch_filter_t(const FilterBufs &F, double tol, cudaStream_t 
             rc = autotune_global(F, kind, st, run_warps, &nw);
             if (rc == RFM_OK && nw != 32) rc = run_warps(nw);
             if (rc == RFM_OK && tune_panel) {
-                // then the Q_hat panel width with those warps (the formation
-                // alone, which starts from the reflectors every time)
-                auto run_form = [&](int pw) -> rfm_status {
-                    switch (nw) {
-                    case 4: return form_gdf(std::integral_constant<int, 4>{}, pw);
-                    case 8: return form_gdf(std::integral_constant<int, 8>{}, pw);
-                    case 16: return form_gdf(std::integral_constant<int, 16>{}, pw);
-                    default: return form_gdf(std::integral_constant<int, 32>{}, pw);
-                    }
+                // then the panel width of the QR and the Q_hat formation with
+                // those warps (each run starts again from the assembled blocks)
+                auto run_pw = [&](int pw) -> rfm_status {
+                    panel = pw;
+                    return run_warps(nw);
                 };
                 std::vector<int> cands;
                 for (int pw : {1, 2, 4, 8})
                     if (panel_fits(pw)) cands.push_back(pw);
-                rc = autotune_panel(F, pkind, st, run_form, cands, &panel);
+                int best_pw = panel;
+                rc = autotune_panel(F, pkind, st, run_pw, cands, &best_pw);
+                panel = best_pw;
             }
         } else {
             rc = run_warps(nw);

@@ -157,14 +157,17 @@ def test_double_float_kept_operator(rfm):
         assert np.array_equal(Op, Mg[:, perm[j, : rank[j]]]), j
 
 
-@pytest.mark.parametrize("name", ["heat", "p2d_wide"])
-def test_double_float_q_hat_panel_widths(rfm, name):
-    """The global kernel's double-float Q_hat formation with 1, 2, 4 and 8
-    reflectors per pass over each column (compact WY panels I - V T V^T).
-    The factorisation is not touched: kept columns and R bitwise the same.
-    Q_hat is the product of the same reflectors in any grouping (rounding of
-    about r 2^-48 apart, then FP32 storage): within 2e-7 of one another, and
-    each within the oracle bound of test_double_float_filter_matches_oracle."""
+@pytest.mark.parametrize("name", ["heat", "p2d_wide", "p2d"])
+@pytest.mark.parametrize("tol", [1e-6, 1e-2])
+def test_double_float_panel_widths(rfm, name, tol):
+    """The global double-float kernels with panels of 1, 2, 4 and 8 steps:
+    the QR with column pivoting defers the trailing update over the panel
+    (F = tau A^T v per step, one rank-nb update per panel) and Q_hat is
+    formed from compact WY panels.  Every width is checked against the oracle
+    as in test_double_float_filter_matches_oracle (a valid greedy pivot order
+    with the threshold stop; R and Q_hat of the kept columns in that order);
+    where two widths take the same pivot order, R agrees to 1e-10 |R_11| and
+    Q_hat to 2e-7 (FP32 storage)."""
     from paper_2506_17626_gb300 import _native as N
     p = CASES[name]()
     prm = synth.feature_params(p)
@@ -172,29 +175,31 @@ def test_double_float_q_hat_panel_widths(rfm, name):
     for pw in (1, 2, 4, 8):
         N.set_qr_panel(pw)
         try:
-            S, rank, perm = _system(rfm, p, prm, "q32", 1e-6, "global")
-            Q = [S.block_matrix(j, which=5)[:, : rank[j]].double().cpu().numpy() for j in range(p.J)]
-            R = [S.block_matrix(j, which=3).cpu().numpy()[: rank[j], : rank[j]] for j in range(p.J)]
-            Mg = [np.asfortranarray(S.block_matrix(j).double().cpu().numpy()) for j in range(p.J)]
-            res[pw] = (rank, perm, Q, R, Mg)
+            S, rank, perm = _system(rfm, p, prm, "q32", tol, "global")
+            r11 = S.r11().cpu().numpy()
+            out = []
+            for j in range(p.J):
+                rk = rank[j]
+                Mg = np.asfortranarray(S.block_matrix(j).double().cpu().numpy())
+                Rg = np.triu(S.block_matrix(j, which=3).cpu().numpy()[:rk, :rk])
+                Qg = S.block_matrix(j, which=5)[:, :rk].double().cpu().numpy()
+                f = check_kept(Mg, tol, rk, perm[j])
+                assert r11[j] == pytest.approx(np.linalg.norm(Mg[:, perm[j, 0]]), rel=1e-12)
+                if rk:
+                    Qn, Rn = np.linalg.qr(Mg[:, perm[j, :rk]])
+                    d = signs(Rg, Rn)
+                    assert np.abs(Rg - d[:, None] * Rn).max() <= 1e-10 * f.r11, (pw, j)
+                    bound = 2e-7 + 256 * U_DF * f.r11 / np.abs(np.diag(Rn))
+                    assert np.all(np.abs(Qg - Qn * d).max(axis=0) <= bound), (pw, j)
+                out.append((list(perm[j, :rk]), Rg, Qg, f.r11))
+            res[pw] = out
         finally:
             N.set_qr_panel(8)
-    r1, p1, Q1, R1, M1 = res[1]
     for pw in (2, 4, 8):
-        r, pp, Q, R, _ = res[pw]
-        assert np.array_equal(r, r1) and np.array_equal(pp, p1), pw
         for j in range(p.J):
-            assert np.array_equal(np.triu(R[j]), np.triu(R1[j])), (pw, j)
-            if r1[j]:
-                assert np.abs(Q[j] - Q1[j]).max() <= 2e-7, (pw, j)
-    for pw in (1, 8):
-        r, pp, Q, _, _ = res[pw]
-        for j in range(p.J):
-            rk = r[j]
-            if not rk:
-                continue
-            Qn, Rn = np.linalg.qr(M1[j][:, pp[j, :rk]])
-            d = signs(np.triu(R1[j]), Rn)
-            r11 = np.linalg.norm(M1[j][:, pp[j, 0]])
-            bound = 2e-7 + 256 * U_DF * r11 / np.abs(np.diag(Rn))
-            assert np.all(np.abs(Q[j] - Qn * d).max(axis=0) <= bound), (pw, j)
+            k1, R1, Q1, r11 = res[1][j]
+            kp, Rp, Qp, _ = res[pw][j]
+            if kp == k1 and k1:
+                d = signs(Rp, R1)
+                assert np.abs(Rp - d[:, None] * R1).max() <= 1e-10 * r11, (pw, j)
+                assert np.abs(Qp - Q1 * d).max() <= 2e-7, (pw, j)
