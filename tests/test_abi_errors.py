@@ -174,6 +174,20 @@ def test_unknown_option_is_rejected(native):
     _expect(native, native.load().rfm_set_option(12345, 1), native.RFM_EINVAL)
 
 
+def test_option_values_are_checked(native):
+    """Warps per block and panel widths outside their sets are rejected; the
+    defaults (32 warps, panels of 8) are put back afterwards."""
+    L = native.load()
+    for opt, bad, good, default in ((9, [0, 3, 64], [4, 8, 16], 32), (10, [0, 3, 16], [1, 2, 4], 8)):
+        for v in bad:
+            _expect(native, L.rfm_set_option(opt, v), native.RFM_EINVAL)
+        try:
+            for v in good:
+                assert L.rfm_set_option(opt, v) == native.RFM_OK
+        finally:
+            assert L.rfm_set_option(opt, default) == native.RFM_OK
+
+
 @pytest.mark.parametrize("case", ["depth", "deep_width", "act", "hard_bc_negative", "hard_bc_heat", "osc_2d",
                                   "osc_family"])
 def test_invalid_networks_and_problem_kinds_are_rejected(native, case):
