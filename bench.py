@@ -913,9 +913,9 @@ def run_learned(args, dev):
         torch.cuda.synchronize()
         t_fit = ev0.elapsed_time(ev1)
         cps = (100, 300, 1000, 3000)
-        res, kept, ms_multi = {}, 0, {}
+        res, kept, ms_multi, resid = {}, 0, {}, {}
         for name, yy in (("zero_start", None), ("learned_start", Y0)):
-            res[name] = {}
+            res[name], resid[name] = {}, {}
             for it in cps:
                 ev0.record()
                 A, rep = Sm.solve_multi(Hm, atol=0, btol=0, max_iter=it, Y0=yy)
@@ -929,16 +929,32 @@ def run_learned(args, dev):
                                     torch.linalg.norm(uref[j])) for j in range(nh)])
                 res[name][str(it)] = {"median": float(np.median(e)), "max": float(e.max()),
                                       "p90": float(np.percentile(e, 90))}
+                rr = np.array([R.report_dict(rep, j)["rnorm"] / R.report_dict(rep, j)["bnorm"] for j in range(nh)])
+                resid[name][str(it)] = {"median": float(np.median(rr)), "max": float(rr.max())}
             if yy is not None:
                 e0m = np.array([float(torch.linalg.norm(Sm.evaluate(d1, Sm.coefficients(Y0[j].contiguous()), [grid],
                                                                     with_error=False)[0][0] - uref[j]) /
                                       torch.linalg.norm(uref[j])) for j in range(nh)])
+        # LSQR's own stopping rule (atol = btol = tau, ||b|| = ||h|| for both
+        # starts): iterations each data set takes to stop, at most 3000
+        stop = {}
+        for tau in (1e-2, 1e-3):
+            stop[f"{tau:g}"] = {}
+            for name, yy in (("zero_start", None), ("learned_start", Y0)):
+                _, rep = Sm.solve_multi(Hm, atol=tau, btol=tau, max_iter=3000, Y0=yy)
+                torch.cuda.synchronize()
+                itn = np.array([R.report_dict(rep, j)["itn"] for j in range(nh)])
+                ist = np.array([R.report_dict(rep, j)["istop"] for j in range(nh)])
+                stop[f"{tau:g}"][name] = {"median": float(np.median(itn)), "p90": float(np.percentile(itn, 90)),
+                                          "max": float(itn.max()), "stopped": int(np.sum((ist == 1) | (ist == 2)))}
         many = {"instances": nh, "seeds": f"20000-{20000 + nh - 1}",
                 "solver": "rfm_lsqr_multi, all instances in one call per checkpoint (Y0 = the fitted starts)",
                 "reference": "mixed path, 10000 iterations, the same many-data-set solver",
                 "reference_ms": t_ref, "fit_ms": t_fit, "fit_systems": "32 instances per fitting system",
                 "start_error": {"median": float(np.median(e0m)), "max": float(e0m.max())},
-                "learned_starts_kept": kept, "rel_l2_after_iterations": res, "solve_ms": ms_multi}
+                "learned_starts_kept": kept, "rel_l2_after_iterations": res,
+                "relative_residual_after_iterations": resid,
+                "iterations_to_stopping_tolerance": stop, "solve_ms": ms_multi}
 
     return {
         "workload": f"2D Poisson, f = sin(a pi x) sin(b pi y) + c sin(d pi x + e pi y), {S_}x{S_} subdomains, "
