@@ -308,8 +308,10 @@ rfm_status rfm_rhs_many(const rfm_problem *probs, int nrhs, const rfm_config *cf
  * back to zero otherwise (report fields start, r0norm).  Without d_Y0 every
  * set starts from zero.  Every set stops on the tests of rfm_lsqr_solve, with
  * ||y|| of the previous iteration.  The call issues a fixed sequence of
- * launches per iteration (max_iter of them; sets that have stopped keep their
- * iterate) and uploads its tile lists from pageable host memory.
+ * launches per iteration (max_iter of them, without waiting on the host;
+ * sets that have stopped keep their iterate, and once every set has stopped
+ * the block products and vector passes of the remaining iterations return at
+ * once) and uploads its tile lists from pageable host memory.
  * Errors: RFM_EINVAL for another operator, more than one instance, nrhs
  * outside 1..256 or bad options; RFM_ENOSPACE for a short workspace. */
 rfm_status rfm_lsqr_multi(const rfm_problem *prob, const rfm_config *cfg, const rfm_lsqr_opts *opts, int nrhs,

@@ -35,6 +35,7 @@ constexpr int kMR = 64;     // right-hand sides of a CTA tile
 constexpr int kMK = 16;     // reduction depth of one shared-memory stage
 constexpr int kMaxRhs = 256;
 constexpr int kRedCtas = 512;   // CTAs of the row / column phases (partial sums)
+constexpr int kMSets = 64, kMSub = 8;   // scalar kernels: sets per CTA, threads per set (m_sum)
 
 struct MScal {
     double alpha, beta, rhobar, phibar, anorm2, bnorm, rnorm, arnorm, ynorm;
@@ -47,6 +48,7 @@ struct MLayout {
     int R;
     int64_t n_fitems, n_titems;
     size_t off_inst, off_fitems, off_titems, off_vt, off_w, off_y, off_z, off_u, off_t, off_out, off_part, off_scal;
+    size_t off_alive;
     size_t off_v32, off_u32;   // FP32 copies of v~ and u~ for the tensor-core products
     size_t total;
 };
@@ -82,6 +84,7 @@ static MLayout multi_layout(const HostPlan &P, int R) {
     M.off_v32 = take((size_t)L.n_cols * R * sizeof(float));
     M.off_u32 = take((size_t)L.n_rows * R * sizeof(float));
     M.off_scal = take(sizeof(MScal) * R);
+    M.off_alive = take(sizeof(int) * ((R + kMSets - 1) / kMSets));
     M.total = o;
     return M;
 }
@@ -115,13 +118,24 @@ __global__ void __launch_bounds__(256) k_m_load(const double *__restrict__ H, in
     }
 }
 
+// true once every right-hand side has stopped: k_m_beta writes one flag per
+// CTA of 64 sets (nonzero while one of them still iterates); the heavy
+// kernels then return at once (uniform over the CTA)
+__device__ inline bool m_all_done(const int *__restrict__ alive, int ngs) {
+    for (int g = 0; g < ngs; ++g)
+        if (alive[g]) return false;
+    return true;
+}
+
 // T = Q_hat_b (V / alpha) for one 64-row tile of one block and 64 right-hand
 // sides (blockIdx.y); rows past the block and slots past its rank read 0.
 template <typename TA>
 __global__ void __launch_bounds__(256) k_m_fwd(const BlkRec *__restrict__ blks, const int32_t *__restrict__ items,
                                                const int32_t *__restrict__ rank, const TA *__restrict__ Q,
                                                const double *__restrict__ VT, const MScal *__restrict__ sc, int R,
-                                               double *__restrict__ T) {
+                                               double *__restrict__ T,
+                                               const int *__restrict__ alive, int ngs) {
+    if (m_all_done(alive, ngs)) return;   // every right-hand side has stopped (uniform)
     __shared__ TA As[kMK][kMT], Bs[kMK][kMR];
     const int b = items[2 * blockIdx.x], r0 = items[2 * blockIdx.x + 1];
     const BlkRec &B = blks[b];
@@ -167,7 +181,9 @@ __global__ void __launch_bounds__(256) k_m_trans(const BlkRec *__restrict__ blks
                                                  const int32_t *__restrict__ rank, const int32_t *__restrict__ grow,
                                                  const TA *__restrict__ Q, const double *__restrict__ U,
                                                  const MScal *__restrict__ sc, int R, int64_t row_base,
-                                                 double *__restrict__ Z) {
+                                                 double *__restrict__ Z,
+                                                 const int *__restrict__ alive, int ngs) {
+    if (m_all_done(alive, ngs)) return;   // every right-hand side has stopped (uniform)
     __shared__ TA As[kMK][kMT], Bs[kMK][kMR];
     __shared__ int64_t s_g[kMK];
     const int b = items[2 * blockIdx.x], c0 = items[2 * blockIdx.x + 1];
@@ -337,7 +353,9 @@ __device__ inline void tcm_teardown(uint32_t tmem) {
 __global__ void __launch_bounds__(256, 2) k_m_fwd_tc(const BlkRec *__restrict__ blks, const int32_t *__restrict__ items,
                                                      const int32_t *__restrict__ rank, const float *__restrict__ Q,
                                                      const float *__restrict__ V32, const MScal *__restrict__ sc, int R,
-                                                     double *__restrict__ T) {
+                                                     double *__restrict__ T,
+                                                     const int *__restrict__ alive, int ngs) {
+    if (m_all_done(alive, ngs)) return;   // every right-hand side has stopped (uniform)
     extern __shared__ __align__(128) unsigned char tsm[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
@@ -408,7 +426,9 @@ __global__ void __launch_bounds__(256, 2) k_m_fwd_tc(const BlkRec *__restrict__ 
 __global__ void __launch_bounds__(256, 2) k_m_trans_tc(const BlkRec *__restrict__ blks, const int32_t *__restrict__ items,
                                                        const int32_t *__restrict__ rank, const int32_t *__restrict__ grow,
                                                        const float *__restrict__ Q, const float *__restrict__ U32,
-                                                       const MScal *__restrict__ sc, int R, double *__restrict__ Z) {
+                                                       const MScal *__restrict__ sc, int R, double *__restrict__ Z,
+                                                       const int *__restrict__ alive, int ngs) {
+    if (m_all_done(alive, ngs)) return;   // every right-hand side has stopped (uniform)
     extern __shared__ __align__(128) unsigned char tsm[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
@@ -504,8 +524,6 @@ __device__ inline void m_partials(double v, int R, double *red, double *part) {
 // and the kMSub sums are combined in sub order, so the result is fixed for a
 // given partial count; valid in the sub = 0 threads.  Every thread of the CTA
 // calls it (it synchronises).
-constexpr int kMSets = 64, kMSub = 8;
-
 __device__ inline double m_sum(const double *part, int nctas, int R, int j, double (*red)[kMSets]) {
     const int js = threadIdx.x % kMSets, sub = threadIdx.x / kMSets;
     double t = 0.0;
@@ -626,7 +644,9 @@ __global__ void k_m_fixb(MScal *__restrict__ sc, int R) {
 __global__ void __launch_bounds__(256) k_m_rows(const InstRec *__restrict__ insts, const int32_t *__restrict__ rowlist,
                                                 const double *__restrict__ T, double *__restrict__ U,
                                                 const MScal *__restrict__ sc, int R, double *__restrict__ part,
-                                                float *__restrict__ U32) {
+                                                float *__restrict__ U32,
+                                                const int *__restrict__ alive, int ngs) {
+    if (m_all_done(alive, ngs)) return;   // every right-hand side has stopped (uniform)
     __shared__ double red[256];
     const InstRec &I = insts[0];
     const int Rp = pow2_at_least(R), j = threadIdx.x % Rp, sub = threadIdx.x / Rp, nsub = 256 / Rp;
@@ -653,7 +673,9 @@ __global__ void __launch_bounds__(256) k_m_rows(const InstRec *__restrict__ inst
 __global__ void __launch_bounds__(256) k_m_cols(const int32_t *__restrict__ rank,
                                                 int64_t n_cols, int K, const double *__restrict__ Z,
                                                 double *__restrict__ VT, const MScal *__restrict__ sc, int R,
-                                                int first, double *__restrict__ part, float *__restrict__ V32) {
+                                                int first, double *__restrict__ part, float *__restrict__ V32,
+                                                const int *__restrict__ alive, int ngs) {
+    if (m_all_done(alive, ngs)) return;   // every right-hand side has stopped (uniform)
     __shared__ double red[256];
     const int Rp = pow2_at_least(R), j = threadIdx.x % Rp, sub = threadIdx.x / Rp, nsub = 256 / Rp;
     double ss = 0.0;
@@ -677,38 +699,46 @@ __global__ void __launch_bounds__(256) k_m_cols(const int32_t *__restrict__ rank
 // its update's partials; the tests of rfm_lsqr_solve), then beta = ||u~||.
 __global__ void __launch_bounds__(kMSets * kMSub) k_m_beta(MScal *__restrict__ sc, const double *__restrict__ part,
                                                             int nctas, const double *__restrict__ ypart, int ynctas,
-                                                            int R, int first, double atol, double btol) {
+                                                            int R, int first, double atol, double btol,
+                                                            int *__restrict__ alive) {
     __shared__ double red[kMSub][kMSets];
     const int j = blockIdx.x * kMSets + threadIdx.x % kMSets;
     const double b2 = m_sum(part, nctas, R, j, red);
     const double y2 = ypart ? m_sum(ypart, ynctas, R, j, red) : 0.0;
-    if (threadIdx.x >= kMSets || j >= R) return;
-    MScal &q = sc[j];
-    if (!first && ypart) q.ynorm = sqrt(y2);
-    if (q.done == 2) q.done = 1;
-    if (!first && !q.done && q.itn > 0) {
-        const double anorm = sqrt(q.anorm2);
-        if (q.rnorm <= btol * q.bnorm + atol * anorm * q.ynorm) {
-            q.done = 1;
-            q.istop = 1;
-        } else if (q.arnorm <= atol * anorm * q.rnorm) {
-            q.done = 1;
-            q.istop = 2;
+    auto set = [&]() {
+        MScal &q = sc[j];
+        if (!first && ypart) q.ynorm = sqrt(y2);
+        if (q.done == 2) q.done = 1;
+        if (!first && !q.done && q.itn > 0) {
+            const double anorm = sqrt(q.anorm2);
+            if (q.rnorm <= btol * q.bnorm + atol * anorm * q.ynorm) {
+                q.done = 1;
+                q.istop = 1;
+            } else if (q.arnorm <= atol * anorm * q.rnorm) {
+                q.done = 1;
+                q.istop = 2;
+            }
         }
-    }
-    if (q.done) return;
-    q.beta_old = q.beta;
-    q.beta = sqrt(b2);
-    q.inv_beta = q.beta > 0.0 ? 1.0 / q.beta : 0.0;
-    if (first) {
-        q.bnorm = q.beta;
-        q.r0norm = q.beta;
-        q.phibar = q.beta;
-        q.rnorm = q.beta;
-        q.istop = 7;
-        q.itn = 0;
-        q.done = 0;
-    }
+        if (q.done) return;
+        q.beta_old = q.beta;
+        q.beta = sqrt(b2);
+        q.inv_beta = q.beta > 0.0 ? 1.0 / q.beta : 0.0;
+        if (first) {
+            q.bnorm = q.beta;
+            q.r0norm = q.beta;
+            q.phibar = q.beta;
+            q.rnorm = q.beta;
+            q.istop = 7;
+            q.itn = 0;
+            q.done = 0;
+        }
+    };
+    const bool mine = threadIdx.x < kMSets && j < R;
+    if (mine) set();
+    // a set that has stopped (done = 1) never iterates again: once no set of
+    // the CTA is live, the flag stays 0 for the rest of the call
+    const int live = __syncthreads_or(mine && sc[j].done == 0);
+    if (threadIdx.x == 0) alive[blockIdx.x] = live;
 }
 
 // alpha = ||v~||, then the plane rotation of the iteration and the estimates
@@ -771,7 +801,9 @@ __global__ void __launch_bounds__(kMSets * kMSub) k_m_alpha(MScal *__restrict__ 
 __global__ void __launch_bounds__(256) k_m_update(const int32_t *__restrict__ rank, int64_t n_cols, int K,
                                                   const double *__restrict__ VT, double *__restrict__ W,
                                                   double *__restrict__ Y, const MScal *__restrict__ sc, int R,
-                                                  int first, double *__restrict__ part) {
+                                                  int first, double *__restrict__ part,
+                                                  const int *__restrict__ alive, int ngs) {
+    if (m_all_done(alive, ngs)) return;   // every right-hand side has stopped (uniform)
     __shared__ double red[256];
     const int Rp = pow2_at_least(R), j = threadIdx.x % Rp, sub = threadIdx.x / Rp, nsub = 256 / Rp;
     double ss = 0.0;
@@ -871,9 +903,11 @@ rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *o
     double *Z = ws_ptr<double>(mws, M.off_z), *U = ws_ptr<double>(mws, M.off_u), *T = ws_ptr<double>(mws, M.off_t);
     double *part = ws_ptr<double>(mws, M.off_part), *ypart = part + (size_t)kRedCtas * R;
     MScal *sc = ws_ptr<MScal>(mws, M.off_scal);
+    int *alive = ws_ptr<int>(mws, M.off_alive);
     float *V32 = tc ? ws_ptr<float>(mws, M.off_v32) : nullptr, *U32 = tc ? ws_ptr<float>(mws, M.off_u32) : nullptr;
     const size_t cols = (size_t)L.n_cols * R * sizeof(double);
     RFM_CUDA_CHECK(cudaMemsetAsync(sc, 0, sizeof(MScal) * R, st));
+    RFM_CUDA_CHECK(cudaMemsetAsync(alive, 1, sizeof(int) * ((R + kMSets - 1) / kMSets), st));   // nonzero: every set live
     RFM_CUDA_CHECK(cudaMemsetAsync(Y, 0, cols, st));
     RFM_CUDA_CHECK(cudaMemsetAsync(VT, 0, cols, st));
     RFM_CUDA_CHECK(cudaMemsetAsync(W, 0, cols, st));
@@ -895,22 +929,22 @@ rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *o
     auto fwd = [&]() -> rfm_status {
         ProfScope ps("k_m_fwd", st);
         if (tc)
-            k_m_fwd_tc<<<gf, 256, kTSmem, st>>>(blks, d_fi, rank, (const float *)Q, V32, sc, R, T);
+            k_m_fwd_tc<<<gf, 256, kTSmem, st>>>(blks, d_fi, rank, (const float *)Q, V32, sc, R, T, alive, (int)gs);
         else if (q32)
-            k_m_fwd<float><<<gf, 256, 0, st>>>(blks, d_fi, rank, (const float *)Q, VT, sc, R, T);
+            k_m_fwd<float><<<gf, 256, 0, st>>>(blks, d_fi, rank, (const float *)Q, VT, sc, R, T, alive, (int)gs);
         else
-            k_m_fwd<double><<<gf, 256, 0, st>>>(blks, d_fi, rank, (const double *)Q, VT, sc, R, T);
+            k_m_fwd<double><<<gf, 256, 0, st>>>(blks, d_fi, rank, (const double *)Q, VT, sc, R, T, alive, (int)gs);
         RFM_CUDA_CHECK(cudaGetLastError());
         return RFM_OK;
     };
     auto trans = [&]() -> rfm_status {
         ProfScope ps("k_m_trans", st);
         if (tc)
-            k_m_trans_tc<<<gt, 256, kTSmem, st>>>(blks, d_ti, rank, grow, (const float *)Q, U32, sc, R, Z);
+            k_m_trans_tc<<<gt, 256, kTSmem, st>>>(blks, d_ti, rank, grow, (const float *)Q, U32, sc, R, Z, alive, (int)gs);
         else if (q32)
-            k_m_trans<float><<<gt, 256, 0, st>>>(blks, d_ti, rank, grow, (const float *)Q, U, sc, R, 0, Z);
+            k_m_trans<float><<<gt, 256, 0, st>>>(blks, d_ti, rank, grow, (const float *)Q, U, sc, R, 0, Z, alive, (int)gs);
         else
-            k_m_trans<double><<<gt, 256, 0, st>>>(blks, d_ti, rank, grow, (const double *)Q, U, sc, R, 0, Z);
+            k_m_trans<double><<<gt, 256, 0, st>>>(blks, d_ti, rank, grow, (const double *)Q, U, sc, R, 0, Z, alive, (int)gs);
         RFM_CUDA_CHECK(cudaGetLastError());
         return RFM_OK;
     };
@@ -932,27 +966,27 @@ rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *o
         k_m_load<<<gr, 256, 0, st>>>(H, L.n_rows, R, U, part, U32);
         RFM_CUDA_CHECK(cudaGetLastError());
     }
-    k_m_beta<<<gs, kMSets * kMSub, 0, st>>>(sc, part, (int)gr, nullptr, 0, R, 1, opts->atol, opts->btol);
+    k_m_beta<<<gs, kMSets * kMSub, 0, st>>>(sc, part, (int)gr, nullptr, 0, R, 1, opts->atol, opts->btol, alive);
     if (Y0) k_m_fixb<<<gs, 64, 0, st>>>(sc, R);
     if ((rc = trans()) != RFM_OK) return rc;
-    k_m_cols<<<gc, 256, 0, st>>>(rank, L.n_cols, K, Z, VT, sc, R, 1, part, V32);
+    k_m_cols<<<gc, 256, 0, st>>>(rank, L.n_cols, K, Z, VT, sc, R, 1, part, V32, alive, (int)gs);
     k_m_alpha<<<gs, kMSets * kMSub, 0, st>>>(sc, part, (int)gc, R, 1, opts->atol, opts->btol, opts->max_iter);
-    k_m_update<<<gc, 256, 0, st>>>(rank, L.n_cols, K, VT, W, Y, sc, R, 1, ypart);
+    k_m_update<<<gc, 256, 0, st>>>(rank, L.n_cols, K, VT, W, Y, sc, R, 1, ypart, alive, (int)gs);
     RFM_CUDA_CHECK(cudaGetLastError());
     for (int it = 0; it < opts->max_iter; ++it) {
         if ((rc = fwd()) != RFM_OK) return rc;
         {
             ProfScope ps("k_m_rows", st);
-            k_m_rows<<<gr, 256, 0, st>>>(insts, rowlist, T, U, sc, R, part, U32);
+            k_m_rows<<<gr, 256, 0, st>>>(insts, rowlist, T, U, sc, R, part, U32, alive, (int)gs);
         }
         {
             ProfScope ps("k_m_beta", st);
-            k_m_beta<<<gs, kMSets * kMSub, 0, st>>>(sc, part, (int)gr, ypart, (int)gc, R, 0, opts->atol, opts->btol);
+            k_m_beta<<<gs, kMSets * kMSub, 0, st>>>(sc, part, (int)gr, ypart, (int)gc, R, 0, opts->atol, opts->btol, alive);
         }
         if ((rc = trans()) != RFM_OK) return rc;
         {
             ProfScope ps("k_m_cols", st);
-            k_m_cols<<<gc, 256, 0, st>>>(rank, L.n_cols, K, Z, VT, sc, R, 0, part, V32);
+            k_m_cols<<<gc, 256, 0, st>>>(rank, L.n_cols, K, Z, VT, sc, R, 0, part, V32, alive, (int)gs);
         }
         {
             ProfScope ps("k_m_alpha", st);
@@ -960,7 +994,7 @@ rfm_status launch_lsqr_multi(const HostPlan &P, void *ws, const rfm_lsqr_opts *o
         }
         {
             ProfScope ps("k_m_update", st);
-            k_m_update<<<gc, 256, 0, st>>>(rank, L.n_cols, K, VT, W, Y, sc, R, 0, ypart);
+            k_m_update<<<gc, 256, 0, st>>>(rank, L.n_cols, K, VT, W, Y, sc, R, 0, ypart, alive, (int)gs);
         }
         RFM_CUDA_CHECK(cudaGetLastError());
     }

@@ -9,7 +9,8 @@ call runs LSQR for all of them.  Checks per data set:
     the same iteration count: the residual estimate and the FP64 residual of
     the assembled system at the coefficients (1e-5, the mixed path's
     tolerance);
-  * the stopping test per data set (a data set with h = 0 stops at once).
+  * the stopping test per data set (a data set with h = 0 stops at once),
+    and a loop that runs on after every set has stopped changing nothing.
 """
 import numpy as np
 import pytest
@@ -114,6 +115,44 @@ def test_multi_rhs_stopping_per_data_set(rfm):
                                                                             max_iter=2000)
     for itn in (r2["itn"], rfm.report_dict(rep1)["itn"]):
         assert abs(itn - ref["itn"]) <= 0.1 * ref["itn"], (itn, ref["itn"])
+
+
+@pytest.mark.parametrize("op", ["q64", "q32"])
+def test_multi_rhs_after_every_set_stopped(rfm, op):
+    """Once every data set has stopped, the remaining iterations' products and
+    vector passes return at once: a call with max_iter far beyond the last
+    stop gives bitwise the result and the reports of a call that ends just
+    after it, and takes a fraction of the time the full loop would."""
+    probs = _family(4)
+    prm = synth.feature_params(probs[0])
+    d = torch.from_numpy(prm.ravel()).cuda()
+    S = rfm.System([probs[0]], asm="fp64" if op == "q64" else "fp32", op=op, tol=1e-6)
+    S.assemble(d)
+    S.filter()
+    H = S.rhs_many(probs)
+    tol = 1e-4
+    A1, rep1 = S.solve_multi(H, atol=tol, btol=tol, max_iter=3000)
+    r1 = [rfm.report_dict(rep1, j) for j in range(len(probs))]
+    last = max(r["itn"] for r in r1)
+    assert all(r["istop"] in (1, 2) for r in r1) and last < 3000
+    A0, rep0 = S.solve_multi(H, atol=tol, btol=tol, max_iter=last + 1)
+    r0 = [rfm.report_dict(rep0, j) for j in range(len(probs))]
+    assert torch.equal(A0, A1)
+    assert r0 == r1
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    S.solve_multi(H, atol=tol, btol=tol, max_iter=last + 1)
+    ev[1].record()
+    S.solve_multi(H, atol=tol, btol=tol, max_iter=3000)
+    ev[2].record()
+    S.solve_multi(H, atol=0, btol=0, max_iter=last + 1)
+    ev[3].record()
+    torch.cuda.synchronize()
+    t_stop, t_long, t_run = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])
+    print(f"\nlast stop at {last}: {t_stop:.1f} ms; max_iter 3000: {t_long:.1f} ms; "
+          f"{last + 1} iterations without stopping: {t_run:.1f} ms")
+    # the full loop would take about (3000 / (last + 1)) t_run
+    assert t_long < 0.5 * t_run * 3000 / (last + 1)
 
 
 @pytest.mark.parametrize("op", ["q64", "q32"])
