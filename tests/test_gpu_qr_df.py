@@ -37,6 +37,8 @@ CASES = {
     "heat": lambda: synth.heat3d(S=3, K=30, n=9),
     "p2d_d29": lambda: synth.poisson2d(S=4, K=20, n=17, delta=2.9),
     "p2d_wide": lambda: synth.poisson2d(S=3, K=120, n=36, delta=1.6),
+    # fewer rows than features in every block (min(m, K) = m steps)
+    "p2d_short": lambda: synth.poisson2d(S=4, K=60, n=16, delta=1.25),
 }
 
 
@@ -157,7 +159,7 @@ def test_double_float_kept_operator(rfm):
         assert np.array_equal(Op, Mg[:, perm[j, : rank[j]]]), j
 
 
-@pytest.mark.parametrize("name", ["heat", "p2d_wide", "p2d"])
+@pytest.mark.parametrize("name", ["heat", "p2d_wide", "p2d", "p2d_short"])
 @pytest.mark.parametrize("tol", [1e-6, 1e-2])
 def test_double_float_panel_widths(rfm, name, tol):
     """The global double-float kernels with panels of 1, 2, 4 and 8 steps:
