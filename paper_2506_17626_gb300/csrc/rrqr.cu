@@ -1885,13 +1885,14 @@ static rfm_status launch_filter_t(const FilterBufs &F, double tol, cudaStream_t 
                 k_form_q_gdf<NW><<<nb, NW * 32, smq, st>>>(F.blk, F.W, F.tau, F.rank, F.Op, F.Q32);
             } else {
                 const size_t smq = sizeof(float2) * (size_t)pw * ldmax;
-                auto launch = [&](auto kern) {
-                    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
+                auto launch = [&](auto kern) -> rfm_status {
+                    RFM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq));
                     kern<<<nb, NW * 32, smq, st>>>(F.blk, F.W, F.tau, F.rank, F.Op, F.Q32);
+                    return RFM_OK;
                 };
-                if (pw == 2) launch(k_form_q_gdf_blk<NW, 2>);
-                else if (pw == 4) launch(k_form_q_gdf_blk<NW, 4>);
-                else launch(k_form_q_gdf_blk<NW, 8>);
+                const rfm_status lr = pw == 2 ? launch(k_form_q_gdf_blk<NW, 2>)
+                                    : pw == 4 ? launch(k_form_q_gdf_blk<NW, 4>) : launch(k_form_q_gdf_blk<NW, 8>);
+                if (lr != RFM_OK) return lr;
             }
             RFM_CUDA_CHECK(cudaGetLastError());
             return RFM_OK;
@@ -1913,12 +1914,13 @@ static rfm_status launch_filter_t(const FilterBufs &F, double tol, cudaStream_t 
                     k_qrcp_gdf<TM, NW><<<nb, NW * 32, smd, st>>>(F.blk, (const TM *)F.M, F.W, F.tau, F.perm, F.rank, F.r11, tol);
                 } else {
                     const size_t smd = qr_panel_smem(qp);
-                    auto launch = [&](auto kern) {
-                        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd);
+                    auto launch = [&](auto kern) -> rfm_status {
+                        RFM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd));
                         kern<<<nb, NW * 32, smd, st>>>(F.blk, (const TM *)F.M, F.W, F.tau, F.perm, F.rank, F.r11, tol);
+                        return RFM_OK;
                     };
-                    if (qp == 2) launch(k_qrcp_gdf_blk<TM, NW, 2>);
-                    else launch(k_qrcp_gdf_blk<TM, NW, 4>);
+                    const rfm_status lr = qp == 2 ? launch(k_qrcp_gdf_blk<TM, NW, 2>) : launch(k_qrcp_gdf_blk<TM, NW, 4>);
+                    if (lr != RFM_OK) return lr;
                 }
                 RFM_CUDA_CHECK(cudaGetLastError());
             } else {
