@@ -649,7 +649,8 @@ def run_poisson1d(args, dev):
     1e-8 with three operators: the paper's form (FP64 kept columns and
     R_hat^-1 substitution, ar64), the explicit FP64 Q_hat (q64, FP64 path),
     and the mixed path's FP32 Q_hat (FP64 blocks factored in double-float;
-    also with three refinement steps on the FP64 residual).  Timed (CUDA
+    also with one to three refinement steps on the FP64 residual, each
+    correction solve as long as the first).  Timed (CUDA
     events, after warm-up): assemble -> filter -> LSQR for the first
     recorded iteration count at 1e-6 -> a = S^-1 y -> u_hat and its error,
     for each run that reaches 1e-6."""
@@ -699,8 +700,19 @@ def run_poisson1d(args, dev):
                 t, e = timed_step(S, k)
                 row.update({"iterations": k, "time_to_target_ms": t, "rel_l2_reached": e})
             if op == "q32":
-                t, e = timed_step(S, 3000, refine=3, refine_iters=1000)
-                row["refined"] = {"iterations": "3000 + 3 x 1000", "ms": t, "rel_l2": e, "reaches_target": e <= 1e-6}
+                # correction solves as long as the first one (this operator's
+                # own iteration count to 1e-4): shorter ones stop before LSQR
+                # has started to converge on it
+                k1 = r["iterations_to"]["0.0001"] or 3000
+                ref = []
+                for nref in (1, 2, 3):
+                    t, e = timed_step(S, k1, refine=nref, refine_iters=k1)
+                    ref.append({"iterations": f"{k1} + {nref} x {k1}", "ms": t, "rel_l2": e})
+                    if e <= 1e-6:
+                        break
+                row["refined"] = {"runs": ref, "reaches_target": ref[-1]["rel_l2"] <= 1e-6}
+                if ref[-1]["rel_l2"] <= 1e-6:
+                    row["time_to_target_ms_refined"] = ref[-1]["ms"]
             del S
         finally:
             N.set_qr_double_float(1)
