@@ -125,3 +125,28 @@ def test_clock_sampler_watches_the_ranks_own_gpu():
     assert bench.smi_device_id({"LOCAL_RANK": "3"}) == "3"
     assert bench.smi_device_id({"LOCAL_RANK": "1", "CUDA_VISIBLE_DEVICES": "4,5,6"}) == "5"
     assert bench.smi_device_id({"CUDA_VISIBLE_DEVICES": "GPU-abc, GPU-def", "LOCAL_RANK": "1"}) == "GPU-def"
+
+
+def test_reference_arm_prints_the_contract_line(monkeypatch):
+    """Rank 0 of the reference arm times the oracle on a bounded sample and
+    prints one JSON line with the benchmark's keys: the metric, its unit and
+    direction, an extrapolated value, a cpu_baseline of kind oracle on one
+    core, and an e2e object without host-device copies."""
+    import argparse
+    import json
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        bench.run_reference(argparse.Namespace(case="small", steps=1, warmup=0, ref_iters=10, cpu_stride=100))
+    lines = [ln for ln in buf.getvalue().splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "ms" and d["higher_is_better"] is False
+    assert d["metric"] == "solve time to fixed error (mixed FP32/FP64, zero start)"
+    assert d["value"] > 0 and d["value"] == d["ms_per_step"] == d["cpu_baseline"]["value"] == d["e2e"]["value"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["extrapolated"] is True and d["cpu_baseline"]["extrapolated"] is True
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["steps"] == 1 and d["warmup"] == 0 and d["vs_baseline"] is None
